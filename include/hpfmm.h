@@ -1,0 +1,164 @@
+/*
+ * hpfmm.h -- C ABI of the half-plane Robin Laplace FMM (arXiv 2507.21913)
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * The library evaluates, for N points r_j = (x_j, y_j) with y_j > 0 and real
+ * charges Q_j (Section 2.2, Eqs. potential1, 1.2, reactioncomp1,
+ * reactioncomp2),
+ *
+ *   u(r_i) = sum_{j != i} Q_j (-1/2pi) ln|r_i - r_j|
+ *          + sum_j        Q_j (+1/2pi) ln|r_i - r_j^im|,   r_j^im = (x_j, -y_j)
+ *          + sum_j        Q_j [ I_0(x_i - x_j, y_i + y_j) + I_0(x_j - x_i, y_i + y_j) ]
+ *
+ * with I_n(x, y) = 1/(2 pi n!) int_0^inf e^{-lambda (y - i x)} lambda^n /
+ * (lambda - kappa) d lambda (Eq. generalintegral; real kappa: the lambda path
+ * passes below the pole, Eq. dzGreensfunimplossless), i.e. u = sum_j Q_j
+ * G(r_i, r_j) for the Robin Green's function of Eq. ddGreensfunimp with
+ * boundary condition dG/dy + kappa G = 0 on y = 0.  The sum is computed by the
+ * FMM of Algorithms 1 and 2: one quadtree over the points whose mirror covers
+ * the image sources, the classic log expansions for the free and image parts
+ * and the paper's S2M / M2M / M2L / L2L / LE-evaluation operators for the
+ * reaction parts (Eqs. MEcoefficients, metome, metoleimage, letole1,
+ * truncatedLE).
+ *
+ * Conventions for every entry point
+ *   - Pointers may be host or device memory (the library asks the CUDA
+ *     runtime which); host buffers are staged through plan-owned device
+ *     memory with stream-ordered copies.  All work is issued on `stream`
+ *     (a cudaStream_t, NULL = legacy default stream).
+ *   - Outputs are in the caller's point order.  Complex values are stored as
+ *     interleaved (re, im) doubles.
+ *   - The caller owns every input and output buffer; a plan owns its tree,
+ *     tables and workspace and never aliases caller memory after a call
+ *     returns.
+ *   - No exception crosses the ABI.  A non-OK status is returned
+ *     synchronously; hpfmm_last_error() gives a one-line reason (per thread).
+ *   - Device failures inside a kernel (bounded waits that gave up, bad sizes)
+ *     are reported through the plan's status word by the next synchronising
+ *     call (hpfmm_sync) rather than by faulting the GPU.
+ */
+#ifndef HPFMM_H
+#define HPFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpfmm_plan hpfmm_plan; /* opaque */
+
+typedef enum {
+  HPFMM_OK = 0,
+  HPFMM_EINVAL = 1,      /* invalid argument (y <= 0, non-finite, kappa or p out of range) */
+  HPFMM_ENOMEM = 2,      /* device allocation failed */
+  HPFMM_ECUDA = 3,       /* a CUDA runtime call failed */
+  HPFMM_ETIMEOUT = 4,    /* a bounded device wait gave up */
+  HPFMM_EUNSUPPORTED = 5 /* valid but outside what this build implements */
+} hpfmm_status;
+
+typedef enum {
+  HPFMM_FP64 = 0,  /* every step in double precision (the plain path) */
+  HPFMM_FP32 = 1,  /* P2P, M2L and expansions in single precision; translation
+                      tables generated in double and rounded */
+  HPFMM_MIXED = 2  /* as FP32, plus double precision for reaction P2P pairs
+                      with y_i + y_j < tau_fp64 (close to the boundary) */
+} hpfmm_precision;
+
+typedef struct {
+  hpfmm_precision prec; /* default HPFMM_FP64 */
+  double tau_fp64;      /* MIXED only: boundary-distance threshold, default 0.05 */
+  int levels;           /* 0: choose the uniform tree depth from leaf_size;
+                           otherwise force the leaf level (1..15) */
+  int reserved[5];      /* must be zero */
+} hpfmm_options;
+
+/* Fill *opt with the defaults. */
+void hpfmm_default_options(hpfmm_options *opt);
+
+/*
+ * hpfmm_create -- build the tree and the translation tables for one point set
+ * (Algorithm 1: images, tree over targets and image sources, tables).
+ *   x, y       : n doubles each, host or device; y[i] > 0, all finite.
+ *   n          : number of points, 1 <= n <= 2^31 - 1.
+ *   kappa      : Robin parameter Z_eps = kappa_re + i kappa_im with
+ *                kappa_re > 0, kappa_im >= 0 (Section 2.1); kappa_im == 0 is
+ *                the lossless case.
+ *   p          : expansion order, 1 <= p <= 40.
+ *   leaf_size  : target mean number of points per leaf box, >= 1; the tree is
+ *                uniform with depth round(log4(n / leaf_size)) clamped to
+ *                [1, 12] unless opt->levels forces it.
+ *   opt        : may be NULL (defaults).
+ *   stream     : cudaStream_t for all device work of this call.
+ *   out        : receives the plan.
+ * The points are copied and sorted by Morton key; the plan keeps no pointer
+ * to x or y.  Returns EUNSUPPORTED when |kappa| * sqrt(5) * (tree side) > 60,
+ * the range in which the device evaluation of I_n is accurate to ~1e-13.
+ */
+hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n, double kappa_re,
+                          double kappa_im, int p, int leaf_size, const hpfmm_options *opt,
+                          void *stream, hpfmm_plan **out);
+
+/*
+ * hpfmm_eval -- u = G q for nrhs charge vectors on the plan's points
+ * (Algorithm 2: free FMM + image FMM + reaction FMM for Phi_2^+ and Phi_2^-,
+ * summed).
+ *   q     : nrhs * n doubles, row r = charge vector r (caller order).
+ *   nrhs  : >= 1.
+ *   pot   : nrhs * n complex doubles (2 * nrhs * n doubles): u.
+ *   grad  : NULL, or nrhs * n * 2 complex doubles: (du/dx_i, du/dy_i) per
+ *           point (the field is minus this).
+ * Stream-ordered; returns without synchronising unless host buffers are
+ * involved (then the results are in host memory when it returns).
+ */
+hpfmm_status hpfmm_eval(hpfmm_plan *plan, const double *q, int nrhs, double *pot, double *grad,
+                        void *stream);
+
+/* Release every device allocation of the plan (synchronises its stream). */
+hpfmm_status hpfmm_destroy(hpfmm_plan *plan);
+
+/*
+ * hpfmm_direct -- O(N_t N_s) all-pairs evaluation of the same sum on the
+ * device (no tree), in double precision.  Targets may differ from sources;
+ * self_index[i] is the source index equal to target i (excluded from the
+ * free part, Eq. 1.2) or -1, and may be NULL when targets are not sources.
+ * Targets need y_t >= 0, sources y_s > 0.  grad may be NULL.
+ */
+hpfmm_status hpfmm_direct(const double *xs, const double *ys, const double *qs, int64_t ns,
+                          const double *xt, const double *yt, const int64_t *self_index,
+                          int64_t nt, double kappa_re, double kappa_im, double *pot,
+                          double *grad, void *stream);
+
+/* Plan geometry (host-side values). */
+typedef struct {
+  int64_t n;
+  int levels;      /* leaf level H (boxes per side 2^H) */
+  int p;
+  int prec;
+  double x0, side; /* bounding square [x0, x0 + side] x [0, side] */
+  int64_t workspace_bytes;
+} hpfmm_plan_info;
+hpfmm_status hpfmm_get_info(const hpfmm_plan *plan, hpfmm_plan_info *info);
+
+/*
+ * hpfmm_get_order -- copy the plan's Morton ordering (for checks): keys[k] is
+ * the 60-bit key of the k-th point in tree order and perm[k] its index in the
+ * caller's order.  Either pointer may be NULL; host or device memory.
+ * Synchronises the stream.
+ */
+hpfmm_status hpfmm_get_order(const hpfmm_plan *plan, uint64_t *keys, int64_t *perm, void *stream);
+
+/* Wait for the plan's outstanding work on `stream` and report any device-side
+ * status (HPFMM_ETIMEOUT) recorded by its kernels. */
+hpfmm_status hpfmm_sync(hpfmm_plan *plan, void *stream);
+
+const char *hpfmm_status_string(hpfmm_status s);
+const char *hpfmm_last_error(void);
+
+/* Library version and build target, e.g. "hpfmm 0.1 sm_103a". */
+const char *hpfmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPFMM_H */

@@ -1,0 +1,218 @@
+"""Python binding of the hpfmm C ABI (``include/hpfmm.h``): argument
+marshalling only.  Every step of the evaluation runs in the CUDA library
+``_lib/libhpfmm.so`` (built by ``_build.build()``); there is no CPU fallback,
+and importing the functions without the built library raises.
+
+Inputs may be torch tensors (CUDA or CPU) or numpy arrays; CPU inputs go
+through the library's host-pointer path (stream-ordered staging copies).
+Outputs are complex128 torch tensors on the device of the inputs.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+HPFMM_OK, HPFMM_EINVAL, HPFMM_ENOMEM, HPFMM_ECUDA, HPFMM_ETIMEOUT, HPFMM_EUNSUPPORTED = range(6)
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+_LIB = None
+
+
+class HpfmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("hpfmm status %d (%s): %s" % (status, _LIB.hpfmm_status_string(status).decode()
+                                                        if _LIB else "?", msg))
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("tau_fp64", ctypes.c_double), ("levels", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("levels", ctypes.c_int), ("p", ctypes.c_int),
+                ("prec", ctypes.c_int), ("x0", ctypes.c_double), ("side", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load the CUDA library.  Raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("hpfmm CUDA library not built (%s); run "
+                               "__graft_entry__.build() or paper_2507_21913_gb300._build.build()"
+                               % path)
+    L = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.hpfmm_create.argtypes = [vp, vp, i64, dbl, dbl, i32, i32, ctypes.POINTER(Options), vp,
+                               ctypes.POINTER(vp)]
+    L.hpfmm_eval.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.hpfmm_destroy.argtypes = [vp]
+    L.hpfmm_direct.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, dbl, dbl, vp, vp, vp]
+    L.hpfmm_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    L.hpfmm_get_order.argtypes = [vp, vp, vp, vp]
+    L.hpfmm_sync.argtypes = [vp, vp]
+    L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.hpfmm_default_options.restype = None
+    for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
+              "hpfmm_get_order", "hpfmm_sync"):
+        getattr(L, f).restype = ctypes.c_int
+    L.hpfmm_status_string.argtypes = [ctypes.c_int]
+    L.hpfmm_status_string.restype = ctypes.c_char_p
+    L.hpfmm_last_error.restype = ctypes.c_char_p
+    L.hpfmm_version.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def _check(status):
+    if status != HPFMM_OK:
+        raise HpfmmError(status, lib().hpfmm_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _as_tensor(a, device=None):
+    torch = _torch()
+    if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+        a = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64))
+    if a.dtype != torch.float64:
+        a = a.to(torch.float64)
+    if device is not None and a.device != device:
+        a = a.to(device)
+    return a.contiguous()
+
+
+def _stream(device):
+    torch = _torch()
+    if device.type == "cuda":
+        return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Plan:
+    """An hpfmm plan (tree, tables and workspace for one point set)."""
+
+    def __init__(self, handle, n, device):
+        self.handle = handle
+        self.n = n
+        self.device = device
+
+    def info(self):
+        return hpfmm_get_info(self)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().hpfmm_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau_fp64=0.05):
+    """Build a plan for the points (x, y); see hpfmm_create in include/hpfmm.h."""
+    x = _as_tensor(x)
+    y = _as_tensor(y, x.device)
+    kappa = complex(kappa)
+    opt = Options()
+    lib().hpfmm_default_options(ctypes.byref(opt))
+    opt.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    opt.levels = int(levels)
+    opt.tau_fp64 = float(tau_fp64)
+    h = ctypes.c_void_p()
+    _check(lib().hpfmm_create(x.data_ptr(), y.data_ptr(), x.numel(), kappa.real, kappa.imag,
+                              int(p), int(leaf_size), ctypes.byref(opt), _stream(x.device),
+                              ctypes.byref(h)))
+    return Plan(h, x.numel(), x.device)
+
+
+def hpfmm_eval(plan, q, grad=True):
+    """u = G q (and grad u) for q of shape (n,) or (nrhs, n).  Returns complex128
+    tensors pot (nrhs, n) and grad (nrhs, n, 2) (or None), squeezed for 1-D q."""
+    torch = _torch()
+    q = _as_tensor(q)
+    squeeze = q.dim() == 1
+    q2 = q.reshape(-1, plan.n)
+    nrhs = q2.shape[0]
+    pot = torch.empty((nrhs, plan.n), dtype=torch.complex128, device=q.device)
+    g = torch.empty((nrhs, plan.n, 2), dtype=torch.complex128, device=q.device) if grad else None
+    _check(lib().hpfmm_eval(plan.handle, q2.data_ptr(), nrhs, pot.data_ptr(),
+                            g.data_ptr() if grad else None, _stream(q.device)))
+    if squeeze:
+        return pot[0], (g[0] if grad else None)
+    return pot, g
+
+
+def hpfmm_destroy(plan):
+    if plan.handle:
+        _check(lib().hpfmm_destroy(plan.handle))
+        plan.handle = None
+
+
+def hpfmm_direct(xs, ys, qs, xt=None, yt=None, kappa=1.0, self_index=None, grad=True):
+    """All-pairs device evaluation (double precision).  With xt/yt omitted the
+    targets are the sources and the free part skips j == i."""
+    torch = _torch()
+    xs = _as_tensor(xs)
+    dev = xs.device
+    ys = _as_tensor(ys, dev)
+    qs = _as_tensor(qs, dev)
+    if xt is None:
+        xt, yt = xs, ys
+        if self_index is None:
+            self_index = torch.arange(xs.numel(), dtype=torch.int64, device=dev)
+    else:
+        xt = _as_tensor(xt, dev)
+        yt = _as_tensor(yt, dev)
+    si = None
+    if self_index is not None:
+        si = torch.as_tensor(self_index, dtype=torch.int64, device=dev).contiguous()
+    nt = xt.numel()
+    kappa = complex(kappa)
+    pot = torch.empty(nt, dtype=torch.complex128, device=dev)
+    g = torch.empty((nt, 2), dtype=torch.complex128, device=dev) if grad else None
+    _check(lib().hpfmm_direct(xs.data_ptr(), ys.data_ptr(), qs.data_ptr(), xs.numel(),
+                              xt.data_ptr(), yt.data_ptr(), si.data_ptr() if si is not None else None,
+                              nt, kappa.real, kappa.imag, pot.data_ptr(),
+                              g.data_ptr() if grad else None, _stream(dev)))
+    return pot, g
+
+
+def hpfmm_get_info(plan):
+    info = PlanInfo()
+    _check(lib().hpfmm_get_info(plan.handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def hpfmm_get_order(plan):
+    """(keys uint64 numpy, perm int64 numpy) of the plan's tree order."""
+    keys = np.zeros(plan.n, np.uint64)
+    perm = np.zeros(plan.n, np.int64)
+    _check(lib().hpfmm_get_order(plan.handle, keys.ctypes.data, perm.ctypes.data,
+                                 _stream(plan.device)))
+    return keys, perm
+
+
+def hpfmm_sync(plan):
+    _check(lib().hpfmm_sync(plan.handle, _stream(plan.device)))
+
+
+def hpfmm_version():
+    return lib().hpfmm_version().decode()

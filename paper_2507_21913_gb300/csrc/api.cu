@@ -1,0 +1,299 @@
+// api.cu -- the C ABI of include/hpfmm.h: argument checks, host/device
+// staging, plan allocation, and the order of the passes.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+
+hpfmm_status fmm_set_smem_limits(int p);
+
+static thread_local char g_err[512] = "";
+
+void set_last_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+bool is_device_pointer(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error state
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" const char *hpfmm_status_string(hpfmm_status s) {
+  switch (s) {
+    case HPFMM_OK: return "ok";
+    case HPFMM_EINVAL: return "invalid argument";
+    case HPFMM_ENOMEM: return "device out of memory";
+    case HPFMM_ECUDA: return "CUDA runtime error";
+    case HPFMM_ETIMEOUT: return "bounded device wait gave up";
+    case HPFMM_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *hpfmm_last_error(void) { return g_err; }
+
+extern "C" const char *hpfmm_version(void) { return "hpfmm 0.1 sm_103a"; }
+
+extern "C" void hpfmm_default_options(hpfmm_options *opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof *opt);
+  opt->prec = HPFMM_FP64;
+  opt->tau_fp64 = 0.05;
+}
+
+static void free_plan(hpfmm_plan *pl) {
+  if (!pl) return;
+  void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
+                  pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
+                  pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete pl;
+}
+
+static hpfmm_status dalloc(hpfmm_plan *pl, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HPFMM_ENOMEM : HPFMM_ECUDA;
+  }
+  pl->workspace_bytes += (int64_t)bytes;
+  return HPFMM_OK;
+}
+
+static int choose_levels(int64_t n, int leaf) {
+  double r = (double)n / (double)leaf;
+  int H = r > 1.0 ? (int)floor(log(r) / log(4.0) + 0.5) : 1;
+  if (H < 1) H = 1;
+  if (H > 12) H = 12;
+  return H;
+}
+
+extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n,
+                                     double kappa_re, double kappa_im, int p, int leaf_size,
+                                     const hpfmm_options *opt, void *stream, hpfmm_plan **out) {
+  if (!out) {
+    set_last_error("hpfmm_create: out is NULL");
+    return HPFMM_EINVAL;
+  }
+  *out = nullptr;
+  if (!x || !y || n < 1 || n > INT32_MAX) {
+    set_last_error("hpfmm_create: need x, y and 1 <= n < 2^31");
+    return HPFMM_EINVAL;
+  }
+  if (!(kappa_re > 0) || !(kappa_im >= 0) || !isfinite(kappa_re) || !isfinite(kappa_im)) {
+    set_last_error("hpfmm_create: kappa must satisfy Re > 0, Im >= 0 (Z > 0, eps >= 0)");
+    return HPFMM_EINVAL;
+  }
+  if (p < 1 || p > HPFMM_MAX_P || leaf_size < 1) {
+    set_last_error("hpfmm_create: need 1 <= p <= %d and leaf_size >= 1", HPFMM_MAX_P);
+    return HPFMM_EINVAL;
+  }
+  hpfmm_options o;
+  hpfmm_default_options(&o);
+  if (opt) o = *opt;
+  for (int r : o.reserved)
+    if (r != 0) {
+      set_last_error("hpfmm_create: reserved option fields must be zero");
+      return HPFMM_EINVAL;
+    }
+  if (o.prec != HPFMM_FP64 && o.prec != HPFMM_FP32 && o.prec != HPFMM_MIXED) {
+    set_last_error("hpfmm_create: unknown precision %d", (int)o.prec);
+    return HPFMM_EINVAL;
+  }
+  if (o.levels < 0 || o.levels > 15 || !(o.tau_fp64 >= 0)) {
+    set_last_error("hpfmm_create: levels must be in 0..15 and tau_fp64 >= 0");
+    return HPFMM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  hpfmm_plan *pl = new hpfmm_plan();
+  pl->n = n;
+  pl->p = p;
+  pl->prec = o.prec;
+  pl->tau_fp64 = o.tau_fp64;
+  pl->kre = kappa_re;
+  pl->kim = kappa_im;
+  pl->H = o.levels > 0 ? o.levels : choose_levels(n, leaf_size);
+  pl->nleaf = 1 << (2 * pl->H);
+  pl->nbox = level_offset(pl->H + 1);
+  const int P1 = p + 1;
+  const size_t m2 = (size_t)P1 * P1;
+  const bool f32 = pl->prec != HPFMM_FP64;
+  const size_t csz = f32 ? sizeof(cf) : sizeof(cd);
+  const size_t tf = f32 ? (sizeof(cd) + sizeof(cf)) : sizeof(cd);  // bytes per table entry
+  hpfmm_status s = HPFMM_OK;
+#define ALLOC(ptr, bytes)                                       \
+  do {                                                          \
+    s = dalloc(pl, (void **)&(ptr), (bytes));                   \
+    if (s != HPFMM_OK) { free_plan(pl); return s; }             \
+  } while (0)
+  ALLOC(pl->xs, sizeof(double) * n);
+  ALLOC(pl->ys, sizeof(double) * n);
+  ALLOC(pl->perm, sizeof(int64_t) * n);
+  ALLOC(pl->keys, sizeof(uint64_t) * n);
+  ALLOC(pl->leaf_start, sizeof(int) * (pl->nleaf + 1));
+  if (f32) ALLOC(pl->loc32, sizeof(float2) * n);
+  ALLOC(pl->t_m2m, tf * 4 * m2);
+  ALLOC(pl->t_l2l, tf * 4 * m2);
+  ALLOC(pl->t_m2l, tf * 49 * m2);
+  ALLOC(pl->t_rlog, tf * 21 * m2);
+  ALLOC(pl->t_refl, tf * (size_t)pl->H * 42 * m2);
+  ALLOC(pl->t_rlog0, sizeof(cd) * 70);
+  ALLOC(pl->qs, (f32 ? sizeof(float) : sizeof(double)) * n);
+  ALLOC(pl->M, csz * (size_t)pl->nbox * P1);
+  ALLOC(pl->A, csz * (size_t)pl->nbox * P1);
+  ALLOC(pl->B, csz * (size_t)pl->nbox * P1);
+  ALLOC(pl->status, sizeof(int));
+#undef ALLOC
+  s = fmm_set_smem_limits(p);
+  if (s != HPFMM_OK) { free_plan(pl); return s; }
+  cudaError_t e = cudaMemsetAsync(pl->status, 0, sizeof(int), st);
+  if (e != cudaSuccess) {
+    set_last_error("hpfmm_create: %s", cudaGetErrorString(e));
+    free_plan(pl);
+    return HPFMM_ECUDA;
+  }
+  // stage host coordinates
+  const double *dx = x, *dy = y;
+  double *tmp = nullptr;
+  if (!is_device_pointer(x) || !is_device_pointer(y)) {
+    e = cudaMallocAsync((void **)&tmp, 2 * sizeof(double) * n, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp, x, sizeof(double) * n, cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp + n, y, sizeof(double) * n, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) {
+      set_last_error("hpfmm_create: staging: %s", cudaGetErrorString(e));
+      free_plan(pl);
+      return HPFMM_ECUDA;
+    }
+    dx = tmp;
+    dy = tmp + n;
+  }
+  s = tree_build(pl, dx, dy, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (s != HPFMM_OK) { free_plan(pl); return s; }
+  double kabs = sqrt(kappa_re * kappa_re + kappa_im * kappa_im);
+  if (kabs * sqrt(5.0) * pl->side > 60.0) {
+    set_last_error("hpfmm_create: |kappa| * sqrt(5) * side = %g exceeds 60, the range of the "
+                   "device I_n evaluation", kabs * sqrt(5.0) * pl->side);
+    cudaStreamSynchronize(st);
+    free_plan(pl);
+    return HPFMM_EUNSUPPORTED;
+  }
+  s = tables_build(pl, st);
+  if (s != HPFMM_OK) { free_plan(pl); return s; }
+  *out = pl;
+  return HPFMM_OK;
+}
+
+static hpfmm_status ensure_stage(hpfmm_plan *pl, int nrhs) {
+  if (pl->stage_rhs >= nrhs) return HPFMM_OK;
+  if (pl->in_q) cudaFree(pl->in_q);
+  if (pl->out_pot) cudaFree(pl->out_pot);
+  if (pl->out_grad) cudaFree(pl->out_grad);
+  pl->in_q = nullptr;
+  pl->out_pot = pl->out_grad = nullptr;
+  pl->stage_rhs = 0;
+  HP_TRY(dalloc(pl, (void **)&pl->in_q, sizeof(double) * pl->n * nrhs));
+  HP_TRY(dalloc(pl, &pl->out_pot, 2 * sizeof(double) * pl->n * nrhs));
+  HP_TRY(dalloc(pl, &pl->out_grad, 4 * sizeof(double) * pl->n * nrhs));
+  pl->stage_rhs = nrhs;
+  return HPFMM_OK;
+}
+
+extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, double *pot,
+                                   double *grad, void *stream) {
+  if (!pl || !q || !pot || nrhs < 1) {
+    set_last_error("hpfmm_eval: need plan, q, pot and nrhs >= 1");
+    return HPFMM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = pl->n;
+  bool qd = is_device_pointer(q), pd = is_device_pointer(pot);
+  bool gd = !grad || is_device_pointer(grad);
+  const double *dq = q;
+  double *dpot = pot, *dgrad = grad;
+  if (!qd || !pd || !gd) HP_TRY(ensure_stage(pl, nrhs));
+  if (!qd) {
+    HP_CUDA(cudaMemcpyAsync(pl->in_q, q, sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
+    dq = pl->in_q;
+  }
+  if (!pd) dpot = (double *)pl->out_pot;
+  if (!gd) dgrad = (double *)pl->out_grad;
+  for (int r = 0; r < nrhs; ++r) {
+    HP_TRY(fmm_eval(pl, dq + (size_t)r * n, dpot + (size_t)2 * r * n,
+                    dgrad ? dgrad + (size_t)4 * r * n : nullptr, st));
+  }
+  if (!pd)
+    HP_CUDA(cudaMemcpyAsync(pot, dpot, 2 * sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
+  if (!gd)
+    HP_CUDA(cudaMemcpyAsync(grad, dgrad, 4 * sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
+  if (!pd || !gd) HP_CUDA(cudaStreamSynchronize(st));
+  return HPFMM_OK;
+}
+
+extern "C" hpfmm_status hpfmm_destroy(hpfmm_plan *pl) {
+  if (!pl) return HPFMM_OK;
+  cudaDeviceSynchronize();
+  free_plan(pl);
+  return HPFMM_OK;
+}
+
+extern "C" hpfmm_status hpfmm_get_info(const hpfmm_plan *pl, hpfmm_plan_info *info) {
+  if (!pl || !info) {
+    set_last_error("hpfmm_get_info: null argument");
+    return HPFMM_EINVAL;
+  }
+  info->n = pl->n;
+  info->levels = pl->H;
+  info->p = pl->p;
+  info->prec = pl->prec;
+  info->x0 = pl->x0;
+  info->side = pl->side;
+  info->workspace_bytes = pl->workspace_bytes;
+  return HPFMM_OK;
+}
+
+extern "C" hpfmm_status hpfmm_get_order(const hpfmm_plan *pl, uint64_t *keys, int64_t *perm,
+                                        void *stream) {
+  if (!pl) {
+    set_last_error("hpfmm_get_order: null plan");
+    return HPFMM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (keys)
+    HP_CUDA(cudaMemcpyAsync(keys, pl->keys, sizeof(uint64_t) * pl->n, cudaMemcpyDefault, st));
+  if (perm)
+    HP_CUDA(cudaMemcpyAsync(perm, pl->perm, sizeof(int64_t) * pl->n, cudaMemcpyDefault, st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  return HPFMM_OK;
+}
+
+extern "C" hpfmm_status hpfmm_sync(hpfmm_plan *pl, void *stream) {
+  if (!pl) {
+    set_last_error("hpfmm_sync: null plan");
+    return HPFMM_EINVAL;
+  }
+  int hs = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  HP_CUDA(cudaMemcpyAsync(&hs, pl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  if (hs != 0) {
+    set_last_error("device status word = %d", hs);
+    return HPFMM_ETIMEOUT;
+  }
+  return HPFMM_OK;
+}

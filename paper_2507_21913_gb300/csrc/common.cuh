@@ -1,0 +1,196 @@
+// common.cuh -- shared definitions of the GB300 half-plane Robin FMM library:
+// complex arithmetic, the plan object, error plumbing, tree geometry helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hpfmm.h"
+
+#ifndef HPFMM_MAX_P
+#define HPFMM_MAX_P 40
+#endif
+
+// ---------------------------------------------------------------------------
+// complex numbers (interleaved re, im)
+template <typename R>
+struct alignas(sizeof(R) * 2) cpx {
+  R x, y;
+};
+using cd = cpx<double>;
+using cf = cpx<float>;
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) {
+  cpx<R> z;
+  z.x = a;
+  z.y = b;
+  return z;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x + b.x, a.y + b.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x - b.x, a.y - b.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a) {
+  return mk<R>(-a.x, -a.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) {
+  return mk<R>(s * a.x, s * a.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> conj(cpx<R> a) {
+  return mk<R>(a.x, -a.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mul_i(cpx<R> a) {  // i * a
+  return mk<R>(-a.y, a.x);
+}
+template <typename R>
+__host__ __device__ __forceinline__ R abs2(cpx<R> a) {
+  return a.x * a.x + a.y * a.y;
+}
+// a += b * c
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cpx<R> &a, cpx<R> b, cpx<R> c) {
+  a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+  a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> cdiv(cpx<R> a, cpx<R> b) {
+  // Smith's algorithm (scaled), adequate for the moderate ranges used here
+  R s = fabs(b.x) + fabs(b.y);
+  R bx = b.x / s, by = b.y / s;
+  R d = bx * bx + by * by;
+  R ax = a.x / s, ay = a.y / s;
+  return mk<R>((ax * bx + ay * by) / d, (ay * bx - ax * by) / d);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> cinv(cpx<R> b) {
+  return cdiv(mk<R>(R(1), R(0)), b);
+}
+__device__ __forceinline__ cd cexp_d(cd z) {
+  double s, c;
+  sincos(z.y, &s, &c);
+  double e = exp(z.x);
+  return mk<double>(e * c, e * s);
+}
+__device__ __forceinline__ cd clog_d(cd z) {
+  return mk<double>(0.5 * log(z.x * z.x + z.y * z.y), atan2(z.y, z.x));
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> to(cd z) {
+  return mk<R>(R(z.x), R(z.y));
+}
+
+// ---------------------------------------------------------------------------
+// Morton geometry.  Key bit 2b holds bit b of ix, bit 2b+1 bit b of iy; the
+// level-l box of a point is key >> (60 - 2l), its Morton index within level l.
+__host__ __device__ __forceinline__ uint32_t compact1(uint64_t m) {
+  // gather the even bits of m into the low 32 bits
+  m &= 0x5555555555555555ull;
+  m = (m | (m >> 1)) & 0x3333333333333333ull;
+  m = (m | (m >> 2)) & 0x0f0f0f0f0f0f0f0full;
+  m = (m | (m >> 4)) & 0x00ff00ff00ff00ffull;
+  m = (m | (m >> 8)) & 0x0000ffff0000ffffull;
+  m = (m | (m >> 16)) & 0x00000000ffffffffull;
+  return (uint32_t)m;
+}
+__host__ __device__ __forceinline__ uint64_t spread1(uint32_t v) {
+  uint64_t m = v;
+  m = (m | (m << 16)) & 0x0000ffff0000ffffull;
+  m = (m | (m << 8)) & 0x00ff00ff00ff00ffull;
+  m = (m | (m << 4)) & 0x0f0f0f0f0f0f0f0full;
+  m = (m | (m << 2)) & 0x3333333333333333ull;
+  m = (m | (m << 1)) & 0x5555555555555555ull;
+  return m;
+}
+__host__ __device__ __forceinline__ int box_ix(uint64_t m) { return (int)compact1(m); }
+__host__ __device__ __forceinline__ int box_iy(uint64_t m) { return (int)compact1(m >> 1); }
+__host__ __device__ __forceinline__ uint64_t box_morton(int ix, int iy) {
+  return spread1((uint32_t)ix) | (spread1((uint32_t)iy) << 1);
+}
+// first box of level l in the level-concatenated box arrays: (4^l - 1) / 3
+__host__ __device__ __forceinline__ int64_t level_offset(int l) {
+  return ((int64_t(1) << (2 * l)) - 1) / 3;
+}
+
+// ---------------------------------------------------------------------------
+// the plan
+struct hpfmm_plan {
+  int64_t n = 0;
+  int H = 0;  // leaf level
+  int p = 0;
+  int prec = HPFMM_FP64;
+  double tau_fp64 = 0.05;
+  double kre = 1, kim = 0;
+  double x0 = 0, side = 1;
+  int64_t nbox = 0;  // boxes over levels 0..H
+  int nleaf = 0;     // 4^H
+
+  // tree (device)
+  double *xs = nullptr, *ys = nullptr;  // sorted coordinates
+  int64_t *perm = nullptr;              // sorted position -> caller index
+  uint64_t *keys = nullptr;             // sorted keys
+  int *leaf_start = nullptr;            // nleaf + 1 offsets into the sorted order
+  float2 *loc32 = nullptr;              // FP32 path: (x, y) relative to the leaf centre
+
+  // tables (device, double); FP32 copies when prec != FP64
+  void *t_m2m = nullptr;   // 4 x (p+1)^2 complex: child c -> parent
+  void *t_l2l = nullptr;   // 4 x (p+1)^2 complex: parent -> child c (analytic part)
+  void *t_m2l = nullptr;   // 49 offset classes x (p+1)^2 complex: free-space log M2L
+  void *t_refl = nullptr;  // per level: 7 x 3 classes x (2p+1) complex: scaled I_k tables
+  void *t_rlog = nullptr;  // per level: 7 x 3 classes x (p+1)^2 complex: image-log M2L
+  void *t_rlog0 = nullptr;    // logs of the 49 free and 21 image class displacements
+
+  // workspace (device)
+  void *qs = nullptr;  // sorted charges (R)
+  void *M = nullptr;   // multipole moments, nbox x (p+1) complex (R)
+  void *A = nullptr;   // analytic local expansion, nbox x (p+1) complex
+  void *B = nullptr;   // anti-analytic local expansion
+  void *out_pot = nullptr, *out_grad = nullptr;  // staging for host outputs
+  double *in_q = nullptr;                         // staging for host charges
+  int64_t stage_rhs = 0;
+  int *status = nullptr;  // device status word
+  int64_t workspace_bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// error plumbing (host)
+void set_last_error(const char *fmt, ...);
+#define HP_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_last_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return HPFMM_ECUDA;                                                               \
+    }                                                                                   \
+  } while (0)
+#define HP_LAUNCH_CHECK()                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) {                                                            \
+      set_last_error("%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+      return HPFMM_ECUDA;                                                               \
+    }                                                                                   \
+  } while (0)
+#define HP_TRY(call)                       \
+  do {                                     \
+    hpfmm_status s_ = (call);              \
+    if (s_ != HPFMM_OK) return s_;         \
+  } while (0)
+
+// internal entry points shared between translation units
+hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st);
+hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st);
+hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad, cudaStream_t st);
+bool is_device_pointer(const void *p);

@@ -1,0 +1,649 @@
+// fmm.cu -- the FMM passes of Algorithms 1 and 2 on a uniform quadtree.
+//
+// One quadtree over the points (levels 0..H, box side d_l = L / 2^l) serves
+// all four components of Algorithm 2: its boxes are the source and target
+// boxes of the free-space FMM, and their mirrors (x, y) -> (x, -y) are the
+// image-source boxes of Algorithm 1 (the tree "over targets and image
+// sources"), for both Phi_2^+ and the x-mirrored Phi_2^-.
+//
+// Lists (uniform grid, level l):
+//   free V-list of box t: children of the neighbours of parent(t) that are not
+//     neighbours of t (levels l >= 2, the classic 2-D FMM);
+//   mirror list of box t: boxes s with parent(s) a mirror-neighbour of
+//     parent(t) and s not a mirror-neighbour of t, where boxes a, b are
+//     mirror-neighbours when both lie in the bottom row (iy = 0) and
+//     |ix_a - ix_b| <= 1, i.e. when a touches the mirror of b.  Only boxes in
+//     rows 0 and 1 have a mirror list (levels l >= 1): the reaction and image
+//     parts are far field everywhere else, which is why the paper finds the
+//     reaction components much cheaper than the free-space ones (Section 4,
+//     Example 2);
+//   near field at the leaves: the 3x3 neighbourhood (free part, j != i) and,
+//     for bottom-row leaves, the bottom-row neighbours (image and reaction).
+// The admissibility of both lists is |r_c - r_c'| >= 2d, which satisfies the
+// M2L condition |r_c - r_c'| > sqrt(2)(d_s + d_t)/2 of Theorem 3.7.
+//
+// Per box: one multipole vector M (power moments of the charges, scaled by d;
+// the image and reaction moments are conj(M_n) and (-+i)^n conj/M_n, see
+// tables.cu) and two local vectors A (analytic) and B (anti-analytic): the
+// log parts, which are real parts of analytic functions, contribute L/2 to A
+// and conj(L)/2 to B; Phi_2^+ contributes to A and Phi_2^- to B.
+#include <math.h>
+
+#include "common.cuh"
+#include "pairs.cuh"
+#include "special.cuh"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+template <typename R>
+__device__ __forceinline__ cpx<R> ldc(const cpx<R> *p) {
+  return *p;
+}
+
+// --------------------------------------------------------------------------
+// gather the charges into tree order
+template <typename R>
+__global__ void k_gather_q(const double *__restrict__ q, const int64_t *__restrict__ perm,
+                           int64_t n, R *__restrict__ qs) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) qs[k] = (R)q[perm[k]];
+}
+
+// point position relative to its leaf centre, in units of the leaf side
+template <typename R>
+struct LeafPoints;
+
+template <>
+struct LeafPoints<double> {
+  const double *xs, *ys;
+  double x0;
+  __device__ __forceinline__ void rel(int64_t k, double cx, double cy, double &rx,
+                                      double &ry) const {
+    rx = xs[k] - cx;
+    ry = ys[k] - cy;
+  }
+};
+template <>
+struct LeafPoints<float> {
+  const float2 *loc;
+  __device__ __forceinline__ void rel(int64_t k, double, double, float &rx, float &ry) const {
+    float2 v = loc[k];
+    rx = v.x;
+    ry = v.y;
+  }
+};
+
+// --------------------------------------------------------------------------
+// P2M (S2M, Eq. MEcoefficients up to the phase and conjugation, see tables.cu):
+// M_n = sum_{j in leaf} Q_j ((z_j - z_c)/d)^n.  One warp per leaf; lanes take
+// 32 points at a time, write q w^n into a shared buffer, then lanes sum the
+// buffer column by column.
+template <typename R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_p2m(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
+      double x0, double side, int p, cpx<R> *__restrict__ M) {
+  extern __shared__ unsigned char smem_raw[];
+  int P1 = p + 1;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw) + (size_t)warp * P1 * 33;
+  int leaf = blockIdx.x * kWarpsPerBlock + warp;
+  int nleaf = 1 << (2 * H);
+  if (leaf >= nleaf) return;
+  double d = side / (double)(1 << H);
+  double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
+  R invd = (R)(1.0 / d);
+  int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  cpx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+  for (int base = b0; base < b1; base += 32) {
+    int k = base + lane;
+    int cnt = min(32, b1 - base);
+    if (k < b1) {
+      R rx, ry;
+      pts.rel(k, cx, cy, rx, ry);
+      cpx<R> w = mk<R>(rx * invd, ry * invd);
+      cpx<R> t = mk<R>(qs[k], 0);
+      for (int n = 0; n < P1; ++n) {
+        buf[n * 33 + lane] = t;
+        t = t * w;
+      }
+    }
+    __syncwarp();
+    for (int n = lane; n < P1; n += 32) {
+      cpx<R> s = mk<R>(0, 0);
+      for (int j = 0; j < cnt; ++j) s = s + buf[n * 33 + j];
+      if (n == lane) acc0 = acc0 + s;
+      else acc1 = acc1 + s;
+    }
+    __syncwarp();
+  }
+  cpx<R> *out = M + (size_t)(level_offset(H) + leaf) * P1;
+  if (lane < P1) out[lane] = acc0;
+  if (lane + 32 < P1) out[lane + 32] = acc1;
+}
+
+// --------------------------------------------------------------------------
+// M2M (Eq. metome): parent M_n = sum_c sum_{m<=n} T_c[n][m] M^{(c)}_m.
+// One warp per parent box of level l; lanes over n.
+template <typename R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_m2m(int l, int p, const cpx<R> *__restrict__ T, cpx<R> *__restrict__ M) {
+  int P1 = p + 1;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t box = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (box >= (int64_t(1) << (2 * l))) return;
+  const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * box) * P1;
+  for (int n = lane; n < P1; n += 32) {
+    cpx<R> acc = mk<R>(0, 0);
+    for (int c = 0; c < 4; ++c) {
+      const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)n * P1;
+      const cpx<R> *mc = child + (size_t)c * P1;
+      for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], mc[m]);
+    }
+    M[(size_t)(level_offset(l) + box) * P1 + n] = acc;
+  }
+}
+
+// --------------------------------------------------------------------------
+// free-space M2L over the V-list.  Block = 32 target boxes of one child type
+// (ix & 1, iy & 1), so that all of them share the same 27 source offsets;
+// for each offset the (p+1)^2 translation matrix is staged in shared memory
+// and applied to the 32 gathered source vectors (a small complex GEMM).
+// Warp g accumulates the coefficients l = g, g + 4, g + 8, ... of its lane's
+// target.
+constexpr int kM2LMaxRows = (HPFMM_MAX_P + 1 + 3) / 4;
+
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
+           const cd *__restrict__ logt, const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A,
+           cpx<R> *__restrict__ B) {
+  extern __shared__ unsigned char smem_raw[];
+  int P1 = p + 1;
+  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);
+  cpx<R> *Ms = Ts + P1 * P1;  // [k][33]
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int type = blockIdx.y;
+  int a = type & 1, b = type >> 1;
+  int64_t nparent = int64_t(1) << (2 * (l - 1));
+  int64_t j = (int64_t)blockIdx.x * 32 + lane;
+  bool valid = j < nparent;
+  int64_t m = 4 * j + type;
+  int ix = valid ? box_ix(m) : 0, iy = valid ? box_iy(m) : 0;
+  int side_n = 1 << l;
+  cpx<R> acc[kM2LMaxRows];
+#pragma unroll
+  for (int r = 0; r < kM2LMaxRows; ++r) acc[r] = mk<R>(0, 0);
+  const int64_t off = level_offset(l);
+
+  for (int dy = -2 - b; dy <= 3 - b; ++dy) {
+    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      int cls = (dy + 3) * 7 + (dx + 3);
+      __syncthreads();
+      const cpx<R> *Tc = Tfree + (size_t)cls * P1 * P1;
+      for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) Ts[e] = Tc[e];
+      for (int e = threadIdx.x; e < 32 * P1; e += blockDim.x) {
+        int t = e / P1, k = e % P1;
+        int64_t jt = (int64_t)blockIdx.x * 32 + t;
+        cpx<R> v = mk<R>(0, 0);
+        if (jt < nparent) {
+          int64_t mt = 4 * jt + type;
+          int sx = box_ix(mt) + dx, sy = box_iy(mt) + dy;
+          if (sx >= 0 && sy >= 0 && sx < side_n && sy < side_n)
+            v = M[(size_t)(off + box_morton(sx, sy)) * P1 + k];
+        }
+        Ms[k * 33 + t] = v;
+      }
+      __syncthreads();
+      for (int k = 0; k < P1; ++k) {
+        cpx<R> mv = Ms[k * 33 + lane];
+#pragma unroll
+        for (int r = 0; r < kM2LMaxRows; ++r) {
+          int row = warp + 4 * r;
+          if (row < P1) cfma(acc[r], Ts[row * P1 + k], mv);
+        }
+      }
+      if (warp == 0) {  // M_0 log(t d) term of L_0
+        cd lt = logt[cls];
+        R m0 = Ms[lane].x;  // M_0 is real for real charges
+        acc[0] = acc[0] + mk<R>(m0 * (R)(lt.x + logd), m0 * (R)lt.y);
+      }
+    }
+  }
+  if (!valid) return;
+  // L = -(1/2pi) sum ...; A = L/2, B = conj(L)/2
+  const R s = (R)(-0.5 / HP_TWO_PI);
+  cpx<R> *Ao = A + (size_t)(off + m) * P1;
+  cpx<R> *Bo = B + (size_t)(off + m) * P1;
+#pragma unroll
+  for (int r = 0; r < kM2LMaxRows; ++r) {
+    int row = warp + 4 * r;
+    if (row < P1) {
+      cpx<R> v = s * acc[r];
+      Ao[row] = v;
+      Bo[row] = conj(v);
+    }
+  }
+  (void)iy;
+  (void)ix;
+}
+
+// --------------------------------------------------------------------------
+// mirror M2L (image log + reaction Phi_2^+ and Phi_2^-) for the boxes of rows
+// 0 and 1 of level l.  One warp per target; lanes over the output index.
+template <typename R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_m2l_mirror(int l, int p, double logd, const cpx<R> *__restrict__ Timg,
+             const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
+             const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B,
+             int accumulate) {
+  extern __shared__ unsigned char smem_raw[];
+  int P1 = p + 1;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cpx<R> *ms = reinterpret_cast<cpx<R> *>(smem_raw) + (size_t)warp * P1;
+  int nx = 1 << l;
+  int t = blockIdx.x * kWarpsPerBlock + warp;
+  if (t >= 2 * nx) return;
+  int ixt = t % nx, iyt = t / nx;  // rows 0 and 1
+  int px = ixt >> 1;
+  const int64_t off = level_offset(l);
+  cpx<R> aL0 = mk<R>(0, 0), aL1 = mk<R>(0, 0), aC0 = mk<R>(0, 0), aC1 = mk<R>(0, 0);
+  cpx<R> aD0 = mk<R>(0, 0), aD1 = mk<R>(0, 0);
+  for (int iys = 0; iys <= 1; ++iys) {
+    for (int ixs = 2 * (px - 1); ixs <= 2 * (px + 1) + 1; ++ixs) {
+      if (ixs < 0 || ixs >= nx) continue;
+      if (iyt == 0 && iys == 0 && abs(ixs - ixt) <= 1) continue;  // mirror-neighbours
+      int dx = ixs - ixt, ysum = iyt + iys + 1;
+      int cls = (ysum - 1) * 7 + (dx + 3);
+      const cpx<R> *src = M + (size_t)(off + box_morton(ixs, iys)) * P1;
+      __syncwarp();
+      for (int k = lane; k < P1; k += 32) ms[k] = src[k];
+      __syncwarp();
+      const cpx<R> *Ti = Timg + (size_t)cls * P1 * P1;
+      const cpx<R> *Tp = Treact + ((size_t)((l - 1) * 21 + cls) * 2 + 0) * P1 * P1;
+      const cpx<R> *Tm = Treact + ((size_t)((l - 1) * 21 + cls) * 2 + 1) * P1 * P1;
+      for (int n = lane; n < P1; n += 32) {
+        cpx<R> sL = mk<R>(0, 0), sC = mk<R>(0, 0), sD = mk<R>(0, 0);
+        for (int k = 0; k < P1; ++k) {
+          cpx<R> mk_ = ms[k], mc = conj(mk_);
+          cfma(sL, Ti[n * P1 + k], mc);
+          cfma(sC, Tp[n * P1 + k], mc);
+          cfma(sD, Tm[n * P1 + k], mk_);
+        }
+        if (n == 0) {  // log(t d) M_0 term of the image log expansion
+          cd lt = logimg[cls];
+          R m0 = ms[0].x;
+          sL = sL + mk<R>(m0 * (R)(lt.x + logd), m0 * (R)lt.y);
+        }
+        if (n == lane) { aL0 = aL0 + sL; aC0 = aC0 + sC; aD0 = aD0 + sD; }
+        else { aL1 = aL1 + sL; aC1 = aC1 + sC; aD1 = aD1 + sD; }
+      }
+    }
+  }
+  // image log: L = +(1/2pi) sum ...; A += L/2 + C, B += conj(L)/2 + D
+  const R s = (R)(0.5 / HP_TWO_PI);
+  int64_t m = off + box_morton(ixt, iyt);
+  for (int n = lane; n < P1; n += 32) {
+    cpx<R> L = s * (n == lane ? aL0 : aL1);
+    cpx<R> C = n == lane ? aC0 : aC1;
+    cpx<R> D = n == lane ? aD0 : aD1;
+    cpx<R> va = L + C, vb = conj(L) + D;
+    size_t e = (size_t)m * P1 + n;
+    if (accumulate) {
+      A[e] = A[e] + va;
+      B[e] = B[e] + vb;
+    } else {
+      A[e] = va;
+      B[e] = vb;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// L2L (Eq. letole1, truncated at p): child A_m += sum_{n>=m} T_c[m][n] A^P_n and
+// B_m += sum conj(T_c[m][n]) B^P_n.  One warp per child box of level l.
+template <typename R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_l2l(int l, int p, const cpx<R> *__restrict__ T, cpx<R> *__restrict__ A,
+      cpx<R> *__restrict__ B) {
+  int P1 = p + 1;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t box = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (box >= (int64_t(1) << (2 * l))) return;
+  int c = (int)(box & 3);
+  const size_t pe = (size_t)(level_offset(l - 1) + (box >> 2)) * P1;
+  const size_t ce = (size_t)(level_offset(l) + box) * P1;
+  const cpx<R> *Tc = T + (size_t)c * P1 * P1;
+  cpx<R> ra[2], rb[2];
+  int cnt = 0;
+  for (int mm = lane; mm < P1; mm += 32, ++cnt) {
+    cpx<R> sa = A[ce + mm], sb = B[ce + mm];
+    for (int n = mm; n < P1; ++n) {
+      cpx<R> t = Tc[mm * P1 + n];
+      cfma(sa, t, A[pe + n]);
+      cfma(sb, conj(t), B[pe + n]);
+    }
+    ra[cnt] = sa;
+    rb[cnt] = sb;
+  }
+  cnt = 0;
+  for (int mm = lane; mm < P1; mm += 32, ++cnt) {
+    A[ce + mm] = ra[cnt];
+    B[ce + mm] = rb[cnt];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Leaf evaluation: L2P of A and B (Eq. truncatedLE) plus the near field
+// (free part over the 3x3 neighbourhood, image and reaction parts over the
+// bottom-row neighbours), written in the caller's order.
+// One warp per leaf, lanes over 32 targets at a time; source points staged
+// per warp in shared memory.
+struct SrcPt64 { double x, y, q; };
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_eval64(const double *__restrict__ xs, const double *__restrict__ ys,
+         const double *__restrict__ qs, const int64_t *__restrict__ perm,
+         const int *__restrict__ leaf_start, int H, double x0, double side, int p, cd kappa,
+         const cd *__restrict__ A, const cd *__restrict__ B, double *__restrict__ pot,
+         double *__restrict__ grad) {
+  __shared__ SrcPt64 sp[kWarpsPerBlock][32];
+  int P1 = p + 1;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int leaf = blockIdx.x * kWarpsPerBlock + warp;
+  int nx = 1 << H;
+  if (leaf >= nx * nx) return;
+  int ix = box_ix(leaf), iy = box_iy(leaf);
+  double d = side / (double)nx;
+  double cx = x0 + (ix + 0.5) * d, cy = (iy + 0.5) * d;
+  const cd *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+  const cd *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+  int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  for (int tb = b0; tb < b1; tb += 32) {
+    int i = tb + lane;
+    bool act = i < b1;
+    double x = act ? xs[i] : cx, y = act ? ys[i] : cy;
+    // L2P: Horner for the value and the derivative in w and conj(w)
+    cd w = mk((x - cx) / d, (y - cy) / d), wb = conj(w);
+    cd va = Al[p], da = mk(0.0, 0.0), vb = Bl[p], db = mk(0.0, 0.0);
+    for (int n = p - 1; n >= 0; --n) {
+      da = da * w + va;
+      va = va * w + Al[n];
+      db = db * wb + vb;
+      vb = vb * wb + Bl[n];
+    }
+    cd u = va + vb;
+    cd gx = (1.0 / d) * (da + db);
+    cd gy = (1.0 / d) * (mul_i(da) - mul_i(db));
+    PairAcc<double> acc;
+    for (int ny = iy - 1; ny <= iy + 1; ++ny) {
+      if (ny < 0 || ny >= nx) continue;
+      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
+        if (mxx < 0 || mxx >= nx) continue;
+        uint64_t sl = box_morton(mxx, ny);
+        int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+        bool mirror = (iy == 0 && ny == 0);
+        for (int sb = s0; sb < s1; sb += 32) {
+          __syncwarp();
+          int js = sb + lane;
+          if (js < s1) sp[warp][lane] = SrcPt64{xs[js], ys[js], qs[js]};
+          __syncwarp();
+          int cnt = min(32, s1 - sb);
+          if (!act) continue;
+          for (int k = 0; k < cnt; ++k) {
+            SrcPt64 s = sp[warp][k];
+            double dx = x - s.x;
+            if (sb + k != i) pair_free(acc, dx, y - s.y, s.q);
+            if (mirror) {
+              double Y = y + s.y;
+              pair_image(acc, dx, Y, s.q);
+              pair_reaction_d(acc, dx, Y, s.q, kappa);
+            }
+          }
+        }
+      }
+    }
+    if (!act) continue;
+    cd un, gxn, gyn;
+    acc.finish(un, gxn, gyn);
+    u = u + un;
+    gx = gx + gxn;
+    gy = gy + gyn;
+    int64_t o = perm[i];
+    pot[2 * o] = u.x;
+    pot[2 * o + 1] = u.y;
+    if (grad) {
+      grad[4 * o + 0] = gx.x;
+      grad[4 * o + 1] = gx.y;
+      grad[4 * o + 2] = gy.x;
+      grad[4 * o + 3] = gy.y;
+    }
+  }
+}
+
+// Single-precision leaf evaluation.  Coordinates are relative to the leaf
+// centre (exact leaf offsets are added per source leaf), so that the pair
+// differences keep full relative precision.  log via the SFU log2, the
+// reaction pairs by the single-precision series when |P| <= 1 and the double
+// routine otherwise (and always below tau_fp64 in MIXED mode).
+struct SrcPt32 { float x, y, q, pad; };
+
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_eval32(const float2 *__restrict__ loc, const float *__restrict__ qs,
+         const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
+         double side, int p, cd kappa, float tau, const cf *__restrict__ A,
+         const cf *__restrict__ B, double *__restrict__ pot, double *__restrict__ grad) {
+  __shared__ SrcPt32 sp[kWarpsPerBlock][32];
+  int P1 = p + 1;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int leaf = blockIdx.x * kWarpsPerBlock + warp;
+  int nx = 1 << H;
+  if (leaf >= nx * nx) return;
+  int ix = box_ix(leaf), iy = box_iy(leaf);
+  float d = (float)(side / (double)nx);
+  float invd = (float)((double)nx / side);
+  cf kap = mk((float)kappa.x, (float)kappa.y);
+  const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+  const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+  int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  for (int tb = b0; tb < b1; tb += 32) {
+    int i = tb + lane;
+    bool act = i < b1;
+    float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+    cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
+    cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
+    for (int n = p - 1; n >= 0; --n) {
+      da = da * w + va;
+      va = va * w + Al[n];
+      db = db * wb + vb;
+      vb = vb * wb + Bl[n];
+    }
+    float lf = 0.f, gfx = 0.f, gfy = 0.f;      // free: sum q log2 r^2, q (dx, dy)/r^2
+    float li = 0.f, gix = 0.f, giy = 0.f;      // image
+    cf ur = mk(0.f, 0.f), grx = mk(0.f, 0.f), gry = mk(0.f, 0.f);
+    cd ur64 = mk(0.0, 0.0), grx64 = mk(0.0, 0.0), gry64 = mk(0.0, 0.0);
+    for (int ny = iy - 1; ny <= iy + 1; ++ny) {
+      if (ny < 0 || ny >= nx) continue;
+      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
+        if (mxx < 0 || mxx >= nx) continue;
+        uint64_t sl = box_morton(mxx, ny);
+        int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+        float ox = (float)(mxx - ix) * d, oy = (float)(ny - iy) * d;
+        bool mirror = (iy == 0 && ny == 0);
+        for (int sb = s0; sb < s1; sb += 32) {
+          __syncwarp();
+          int js = sb + lane;
+          if (js < s1) {
+            float2 v = loc[js];
+            sp[warp][lane] = SrcPt32{v.x + ox, v.y + oy, qs[js], 0.f};
+          }
+          __syncwarp();
+          int cnt = min(32, s1 - sb);
+          if (!act) continue;
+          for (int k = 0; k < cnt; ++k) {
+            SrcPt32 s = sp[warp][k];
+            float dx = me.x - s.x, dy = me.y - s.y;
+            if (sb + k != i) {
+              float r2 = fmaf(dx, dx, dy * dy);
+              float qi = s.q * fast_rcp(r2);
+              lf = fmaf(s.q, __log2f(r2), lf);
+              gfx = fmaf(qi, dx, gfx);
+              gfy = fmaf(qi, dy, gfy);
+            }
+            if (mirror) {
+              // bottom row: leaf centres at y = d/2, so Y = y_i + y_j = ly + sy + d
+              float Y = me.y + s.y + d;
+              float R2 = fmaf(dx, dx, Y * Y);
+              float qi = s.q * fast_rcp(R2);
+              li = fmaf(s.q, __log2f(R2), li);
+              gix = fmaf(qi, dx, gix);
+              giy = fmaf(qi, Y, giy);
+              cf sp_ = mk(Y, -dx), sm_ = mk(Y, dx);
+              cf Pp = kap * sp_, Pm = kap * sm_;
+              bool small = abs2(Pp) <= 1.f && Y >= tau;
+              if (small) {
+                cf J0p, J1p, J0m, J1m;
+                j01_f(Pp, J0p, J1p);
+                j01_f(Pm, J0m, J1m);
+                ur = ur + s.q * (J0p + J0m);
+                cf tp = cdiv(J1p, sp_), tm = cdiv(J1m, sm_);
+                grx = grx + s.q * mul_i(tp - tm);
+                gry = gry - s.q * (tp + tm);
+              } else {
+                cd spd = mk((double)Y, -(double)dx), smd = mk((double)Y, (double)dx);
+                cd J0p, J1p, J0m, J1m;
+                j01(kappa * spd, J0p, J1p);
+                j01(kappa * smd, J0m, J1m);
+                double q = s.q;
+                ur64 = ur64 + q * (J0p + J0m);
+                cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
+                grx64 = grx64 + q * mul_i(tp - tm);
+                gry64 = gry64 - q * (tp + tm);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (!act) continue;
+    // ln r^2 = log2(r^2) ln 2
+    const double c4 = 0.69314718055994530942 / (4.0 * HP_PI), i2pi = 1.0 / HP_TWO_PI;
+    cd u = mk((double)va.x + vb.x + ((double)li - lf) * c4 + ((double)ur.x + ur64.x) * i2pi,
+              (double)va.y + vb.y + ((double)ur.y + ur64.y) * i2pi);
+    cd ga = mk((double)da.x, (double)da.y), gb = mk((double)db.x, (double)db.y);
+    double id = 1.0 / (double)d;
+    cd gx = id * (ga + gb), gy = id * (mul_i(ga) - mul_i(gb));
+    gx = gx + mk(((double)gix - gfx + grx.x + grx64.x) * i2pi, ((double)grx.y + grx64.y) * i2pi);
+    gy = gy + mk(((double)giy - gfy + gry.x + gry64.x) * i2pi, ((double)gry.y + gry64.y) * i2pi);
+    int64_t o = perm[i];
+    pot[2 * o] = u.x;
+    pot[2 * o + 1] = u.y;
+    if (grad) {
+      grad[4 * o + 0] = gx.x;
+      grad[4 * o + 1] = gx.y;
+      grad[4 * o + 2] = gy.x;
+      grad[4 * o + 3] = gy.y;
+    }
+  }
+}
+
+inline unsigned cdiv_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+template <typename R>
+hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *grad,
+                        cudaStream_t st) {
+  const int p = pl->p, P1 = p + 1, H = pl->H;
+  const int64_t n = pl->n;
+  const size_t m2 = (size_t)P1 * P1;
+  // table pointers (FP32 copies follow the double block)
+  auto tab = [&](void *base, size_t count) -> const cpx<R> * {
+    if (sizeof(R) == 8) return (const cpx<R> *)base;
+    return (const cpx<R> *)((cd *)base + count);
+  };
+  const cpx<R> *Tm2m = tab(pl->t_m2m, 4 * m2);
+  const cpx<R> *Tl2l = tab(pl->t_l2l, 4 * m2);
+  const cpx<R> *Tfree = tab(pl->t_m2l, 49 * m2);
+  const cpx<R> *Timg = tab(pl->t_rlog, 21 * m2);
+  const cpx<R> *Treact = tab(pl->t_refl, (size_t)H * 42 * m2);
+  const cd *logs = (const cd *)pl->t_rlog0;
+  R *qs = (R *)pl->qs;
+  cpx<R> *M = (cpx<R> *)pl->M, *A = (cpx<R> *)pl->A, *B = (cpx<R> *)pl->B;
+
+  k_gather_q<R><<<cdiv_u(n, 256), 256, 0, st>>>(q, pl->perm, n, qs);
+  // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
+  size_t shp2m = sizeof(cpx<R>) * P1 * 33 * kWarpsPerBlock;
+  if (sizeof(R) == 8) {
+    LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
+    k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
+        lp, (const double *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cd *)M);
+  } else {
+    LeafPoints<float> lp{pl->loc32};
+    k_p2m<float><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
+        lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cf *)M);
+  }
+  for (int l = H - 1; l >= 1; --l)
+    k_m2m<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
+        l, p, Tm2m, M);
+  // downward pass: M2L at every level (free V-list from level 2, mirror list
+  // from level 1), then L2L from level 1 down to the leaves
+  size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
+  size_t shmir = sizeof(cpx<R>) * P1 * kWarpsPerBlock;
+  for (int l = 1; l <= H; ++l) {
+    double logd = log(pl->side / (double)(1 << l));
+    if (l >= 2) {
+      dim3 g(cdiv_u(int64_t(1) << (2 * (l - 1)), 32), 4);
+      k_m2l_free<R><<<g, 128, shfree, st>>>(l, p, logd, Tfree, logs, M, A, B);
+    }
+    k_m2l_mirror<R><<<cdiv_u(2 << l, kWarpsPerBlock), 32 * kWarpsPerBlock, shmir, st>>>(
+        l, p, logd, Timg, logs + 49, Treact, M, A, B, l >= 2 ? 1 : 0);
+  }
+  for (int l = 2; l <= H; ++l)
+    k_l2l<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
+        l, p, Tl2l, A, B);
+  // evaluation at the leaves + near field
+  cd kappa = mk(pl->kre, pl->kim);
+  if (sizeof(R) == 8) {
+    k_eval64<<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
+        pl->xs, pl->ys, (const double *)qs, pl->perm, pl->leaf_start, H, pl->x0, pl->side, p,
+        kappa, (const cd *)A, (const cd *)B, pot, grad);
+  } else {
+    float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
+    k_eval32<<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
+        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p, kappa, tau,
+        (const cf *)A, (const cf *)B, pot, grad);
+  }
+  HP_LAUNCH_CHECK();
+  return HPFMM_OK;
+}
+
+}  // namespace
+
+size_t fmm_shared_bytes_max(int p, bool fp64) {
+  size_t c = fp64 ? sizeof(cd) : sizeof(cf);
+  size_t P1 = p + 1;
+  size_t a = c * P1 * 33 * kWarpsPerBlock, b = c * (P1 * P1 + P1 * 33);
+  return a > b ? a : b;
+}
+
+hpfmm_status fmm_set_smem_limits(int p) {
+  size_t s64 = fmm_shared_bytes_max(p, true), s32 = fmm_shared_bytes_max(p, false);
+  HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+  HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
+  HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+  HP_CUDA(cudaFuncSetAttribute(k_m2l_free<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
+  return HPFMM_OK;
+}
+
+hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
+                      cudaStream_t st) {
+  if (pl->prec == HPFMM_FP64) return run_passes<double>(pl, q, pot, grad, st);
+  return run_passes<float>(pl, q, pot, grad, st);
+}

@@ -1,0 +1,164 @@
+// special.cuh -- device evaluation of the integrals I_n of Eq. generalintegral.
+//
+// With s = y - i x and P = kappa s (the substitution t = lambda s of Lemma 3.2
+// and Appendix A),
+//     I_n(x, y) = J_n(P) / (2 pi n! s^n),
+//     J_n(P)    = int_S t^n e^{-t} / (t - P) dt,
+// where S is the ray through s and, for real kappa, the path passes below the
+// pole (Eq. dzGreensfunimplossless).  J_n satisfies the recursion of
+// Eq. integralrecursion in the form J_n = (n-1)! + P J_{n-1}.
+//
+// Closed forms used (derived from the contour rotation of Appendix A):
+//   J_0(P) = e^{-P} [ i pi - Ei(P) ],  Ei(P) = gamma + Log P + sum_{k>=1} P^k/(k k!)
+// with the principal Log (arg P lies in (-pi/2, pi) for Re kappa > 0,
+// Im kappa >= 0, y > 0), and for n >= 1 the same function continued term by term:
+//   J_n(P) = e^{-P} [ P^n (i pi - Log P + psi(n+1)) - n! sum_{k != n} P^k / ((k-n) k!) ]
+// (the exponential-integral series, A&S 5.1.12, with E_{n+1}(-P) and the residue
+// term combined).  These power series are used where they do not cancel:
+// |P| <= 1/2 or |P| - Re P <= 3/2 (P near the positive real axis; the
+// cancellation factor is at most e^{|P| - Re P}).  Elsewhere the continued
+// fraction of A&S 5.1.22 for e^{z} E_{n+1}(z) at z = -P (modified Lentz
+// algorithm) gives K_n = n! e^{-P} E_{n+1}(-P), and
+//   J_n = K_n + 2 pi i H P^n e^{-P},  H = 1 (Im P < 0), 1/2 (Im P = 0), 0 (Im P > 0),
+// the residue rule of Appendix A.  J_n for all n <= K is obtained from J_{n*},
+// n* = min(K, floor |P|), by the recursion run downwards (stable for n <= |P|)
+// and upwards (stable for n >= |P|); the forward recursion from J_0 alone
+// loses about |P|/2.3 digits (Lemma 3.2's regime n >= e|P| is where it is
+// safe).  Supported range: |P| <= 60 (relative error ~1e-13 or better).
+#pragma once
+#include "common.cuh"
+
+#define HP_EULER_GAMMA 0.57721566490153286061
+#define HP_PI 3.14159265358979323846
+#define HP_TWO_PI 6.28318530717958647692
+
+__device__ __forceinline__ bool jn_use_series(cd P) {
+  double a = sqrt(abs2(P));
+  return a <= 0.5 || (a - P.x) <= 1.5;
+}
+
+// J_n by the power series (valid for all P; used where it does not cancel)
+__device__ inline cd jn_series(cd P, int n) {
+  double a = sqrt(abs2(P));
+  double psi = -HP_EULER_GAMMA;
+  double nfact = 1.0;
+  for (int k = 1; k <= n; ++k) {
+    psi += 1.0 / k;
+    nfact *= k;
+  }
+  cd term = mk(1.0, 0.0);  // P^k / k!
+  cd tot = mk(0.0, 0.0);
+  cd Pn = mk(1.0, 0.0);
+  for (int k = 0; k < 400; ++k) {
+    if (k == n) {
+      Pn = term;  // P^n / n!
+    } else {
+      double inv = 1.0 / (double)(k - n);
+      cd c = inv * term;
+      tot = tot + c;
+      if (k > n && k > a && abs2(c) < 1e-34 * abs2(tot)) break;
+    }
+    term = (1.0 / (k + 1)) * (term * P);
+  }
+  // P^n (i pi - Log P + psi) - n! tot = n! [ (P^n/n!)(i pi - Log P + psi) - tot ]
+  cd L = clog_d(P);
+  cd br = mk(psi - L.x, HP_PI - L.y);
+  cd v = nfact * (Pn * br - tot);
+  return cexp_d(-P) * v;
+}
+
+// J_n by the continued fraction for E_{n+1} plus the residue rule
+__device__ inline cd jn_cf(cd P, int n) {
+  const double tiny = 1e-300;
+  cd z = -P;
+  double m = n + 1;
+  // e^{z} E_m(z) = 1 / (z + m - 1*m / (z + m + 2 - 2(m+1) / (z + m + 4 - ...)))
+  cd b = mk(z.x + m, z.y);
+  cd f = (abs2(b) == 0) ? mk(tiny, 0.0) : b;
+  cd C = f, D = mk(0.0, 0.0);
+  for (int k = 1; k < 400; ++k) {
+    double ak = -(double)k * (m + k - 1);
+    b = mk(z.x + m + 2.0 * k, z.y);
+    D = b + ak * D;
+    if (abs2(D) == 0) D = mk(tiny, 0.0);
+    D = cinv(D);
+    C = b + ak * cinv(C);
+    if (abs2(C) == 0) C = mk(tiny, 0.0);
+    cd delta = C * D;
+    f = f * delta;
+    if (fabs(delta.x - 1.0) + fabs(delta.y) < 1e-16) break;
+  }
+  double nfact = 1.0;
+  for (int k = 2; k <= n; ++k) nfact *= k;
+  cd K = nfact * cinv(f);
+  double H = (P.y < 0) ? 1.0 : ((P.y == 0) ? 0.5 : 0.0);
+  if (H != 0.0) {
+    cd Pn = mk(1.0, 0.0);
+    for (int k = 0; k < n; ++k) Pn = Pn * P;
+    cd r = (HP_TWO_PI * H) * mul_i(Pn * cexp_d(-P));
+    K = K + r;
+  }
+  return K;
+}
+
+__device__ inline cd jn_direct(cd P, int n) {
+  return jn_use_series(P) ? jn_series(P, n) : jn_cf(P, n);
+}
+
+// J_0 .. J_K into J[0..K]
+__device__ inline void jn_range(cd P, int K, cd *J) {
+  double a = sqrt(abs2(P));
+  int ns = (int)floor(a);
+  if (ns > K) ns = K;
+  J[ns] = jn_direct(P, ns);
+  double fact = 1.0;  // (m-1)!
+  for (int k = 2; k < ns; ++k) fact *= k;
+  cd Pinv = cinv(P);
+  for (int m = ns; m >= 1; --m) {  // J_{m-1} = (J_m - (m-1)!) / P
+    J[m - 1] = Pinv * mk(J[m].x - fact, J[m].y);
+    if (m - 1 >= 1) fact /= (m - 1);
+  }
+  fact = 1.0;  // m!
+  for (int k = 2; k <= ns; ++k) fact *= k;
+  for (int m = ns; m < K; ++m) {  // J_{m+1} = m! + P J_m
+    cd v = P * J[m];
+    J[m + 1] = mk(v.x + fact, v.y);
+    fact *= (m + 1);
+  }
+}
+
+// J_0 and J_1 = 1 + P J_0 (direct and near-field kernels), double precision
+__device__ inline void j01(cd P, cd &J0, cd &J1) {
+  double a = sqrt(abs2(P));
+  if (a < 1.0) {
+    J0 = jn_direct(P, 0);
+    cd v = P * J0;
+    J1 = mk(1.0 + v.x, v.y);
+  } else {
+    // 1 + P J_0 cancels for large |P|: evaluate J_1 directly and take one
+    // downward step of the recursion (stable for n <= |P|)
+    J1 = jn_direct(P, 1);
+    J0 = cinv(P) * mk(J1.x - 1.0, J1.y);
+  }
+}
+
+// Single-precision J_0, J_1 for |P| <= 1 (near-field pairs of the fast path):
+// J_0 = e^{-P}[i pi - gamma - Log P - sum_{k>=1} P^k/(k k!)], 11 terms.
+__device__ __forceinline__ void j01_f(cf P, cf &J0, cf &J1) {
+  cf term = P;
+  cf s = P;
+#pragma unroll
+  for (int k = 2; k <= 11; ++k) {
+    term = (1.0f / k) * (term * P);
+    s = s + (1.0f / k) * term;
+  }
+  float lr = 0.5f * __logf(P.x * P.x + P.y * P.y);
+  float th = atan2f(P.y, P.x);
+  cf br = mk(-(float)HP_EULER_GAMMA - lr - s.x, (float)HP_PI - th - s.y);
+  float e = __expf(-P.x), sn, cs;
+  __sincosf(-P.y, &sn, &cs);
+  cf eP = mk(e * cs, e * sn);
+  J0 = eP * br;
+  cf v = P * J0;
+  J1 = mk(1.0f + v.x, v.y);
+}

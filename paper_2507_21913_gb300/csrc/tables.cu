@@ -1,0 +1,178 @@
+// tables.cu -- translation tables of the half-plane FMM ("pre-compute some
+// tables", Algorithm 1), generated on the device in double precision.
+//
+// Expansions are scaled by the box side d of their level: multipole moments
+// M_n = sum_j Q_j ((z_j - z_c)/d)^n (z = x + i y), local expansions in powers of
+// w = (z - z_c)/d (analytic part A_n w^n) and of conj(w) (anti-analytic part
+// B_n conj(w)^n).  The tables are:
+//
+//  * M2M, child quadrant c -> parent (Eq. metome, which is the classic shift):
+//      T[c][n][m] = C(n,m) delta_c^{n-m} 2^{-m},  delta_c = (z_child - z_parent)/d_parent
+//  * L2L, parent -> child c (Eq. letole1):  T[c][m][n] = C(n,m) delta_c^{n-m} 2^{-m}
+//    (the anti-analytic part uses the complex conjugate table).
+//  * free-space log M2L (Remark after Theorem 2.1: Eq. logexpansion re-expanded
+//    about the target centre), 49 offset classes (dx, dy) in [-3, 3]^2 of the
+//    source box relative to the target box, t = (z_t - z_s)/d = -(dx + i dy):
+//      T[l][k] = (-1)^{l+1} (k+l-1)!/(l! k!) t^{-(k+l)},  (l, k) != (0, 0)
+//    for sum_j Q_j log(z - z_j) = sum_l L_l w^l; the l = k = 0 entry is the
+//    log(t d) M_0 term, added in the kernel.
+//  * image-log M2L: the same T at t = (z_t - conj(z_s))/d = -dx + i Ysum,
+//    Ysum = iy_t + iy_s + 1 in {1, 2, 3}, dx in [-3, 3] (21 classes), applied
+//    to the image moments conj(M_n).
+//  * reaction M2L, per level l and the same 21 classes (Eq. metoleimage /
+//    truncatedM2Lcoef rewritten for scaled expansions):
+//      Phi_2^+ :  C_n += sum_m i^{n-m} C(n+m, m) It_{n+m}( x_t - x_s, y_t + y_s) conj(M_m)
+//      Phi_2^- :  D_n += sum_m i^{m-n} C(n+m, m) It_{n+m}(-(x_t - x_s), y_t + y_s) M_m
+//    with It_k = I_k d^k; here alpha_m = (-i)^m conj(M_m) d^m (Eq. MEcoefficients
+//    with z_j^im - z_c^im = conj(z_j - z_c)), alpha^-_m = i^m M_m d^m (the
+//    x-mirrored problem of Algorithm 2), C_n = (-1)^n beta_n d^n and
+//    D_n = beta^-_n d^n (Eq. LEformula in powers of z_i - z_c).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "special.cuh"
+
+namespace {
+
+__host__ __device__ inline double binom(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+__global__ void k_m2m_l2l(int p, cd *m2m, cd *l2l) {
+  int c = blockIdx.x;  // child quadrant
+  int P1 = p + 1;
+  cd delta = mk((c & 1) ? 0.25 : -0.25, (c >> 1) ? 0.25 : -0.25);
+  for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) {
+    int n = e / P1, m = e % P1;
+    cd v = mk(0.0, 0.0), w = mk(0.0, 0.0);
+    if (m <= n) {  // T[n][m] for M2M, T[m][n] for L2L (same value)
+      cd dp = mk(1.0, 0.0);
+      for (int k = 0; k < n - m; ++k) dp = dp * delta;
+      double s = binom(n, m) * ldexp(1.0, -m);
+      v = s * dp;
+    }
+    m2m[(size_t)c * P1 * P1 + n * P1 + m] = v;
+    // L2L entry [m'][n'] with m' = row; reuse (n, m) as (row, col) = (m', n')
+    int row = n, col = m;  // T_l2l[row][col] = C(col,row) delta^{col-row} 2^{-row}
+    if (col >= row) {
+      cd dp = mk(1.0, 0.0);
+      for (int k = 0; k < col - row; ++k) dp = dp * delta;
+      w = (binom(col, row) * ldexp(1.0, -row)) * dp;
+    }
+    l2l[(size_t)c * P1 * P1 + row * P1 + col] = w;
+  }
+}
+
+// log-kernel M2L matrix for displacement t (scaled): T[l][k]
+__device__ void log_m2l_fill(cd t, int p, cd *T) {
+  int P1 = p + 1;
+  cd ti = cinv(t);
+  for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) {
+    int l = e / P1, k = e % P1;
+    cd v = mk(0.0, 0.0);
+    if (l + k > 0) {
+      // (k+l-1)! / (l! k!) = C(k+l-1, l) / k   (k >= 1);  1/l  (k = 0)
+      double c = (k == 0) ? 1.0 / l : binom(k + l - 1, l) / k;
+      if (!(l & 1)) c = -c;  // (-1)^{l+1}
+      cd tp = mk(1.0, 0.0);
+      for (int j = 0; j < k + l; ++j) tp = tp * ti;
+      v = c * tp;
+    }
+    T[e] = v;
+  }
+}
+
+__global__ void k_free_m2l(int p, cd *T, cd *logt) {
+  int cls = blockIdx.x;  // (dy+3)*7 + (dx+3)
+  int dx = cls % 7 - 3, dy = cls / 7 - 3;
+  int P1 = p + 1;
+  cd t = mk(-(double)dx, -(double)dy);
+  if (dx == 0 && dy == 0) t = mk(1.0, 0.0);  // unused class
+  log_m2l_fill(t, p, T + (size_t)cls * P1 * P1);
+  if (threadIdx.x == 0) logt[cls] = clog_d(t);
+}
+
+__global__ void k_img_m2l(int p, cd *T, cd *logt) {
+  int cls = blockIdx.x;  // (Ysum-1)*7 + (dx+3)
+  int dx = cls % 7 - 3, ysum = cls / 7 + 1;
+  int P1 = p + 1;
+  cd t = mk(-(double)dx, (double)ysum);
+  log_m2l_fill(t, p, T + (size_t)cls * P1 * P1);
+  if (threadIdx.x == 0) logt[cls] = clog_d(t);
+}
+
+// reaction M2L matrices, block = (level, class, sign); Tp/Tm: [level][cls][n][m]
+__global__ void k_reaction_m2l(int p, int H, double side, cd kappa, cd *Tr) {
+  extern __shared__ cd sh[];
+  int P1 = p + 1, K = 2 * p;
+  int b = blockIdx.x;
+  int sign = b & 1;  // 0: Phi_2^+, 1: Phi_2^-
+  int cls = (b >> 1) % 21;
+  int lev = (b >> 1) / 21 + 1;  // 1..H
+  int dx = cls % 7 - 3, ysum = cls / 7 + 1;
+  double d = side / (double)(1 << lev);
+  // I_k at (x, y) = (+-(x_t - x_s), y_t + y_s) = (-+dx d, ysum d); s/d = ysum + -i(x/d)
+  double xs_ = sign ? (double)dx : -(double)dx;  // x / d
+  cd shat = mk((double)ysum, -xs_);
+  cd *J = sh;         // K+1
+  cd *h = sh + K + 1; // K+1: It_k = J_k / (2 pi k! shat^k)
+  if (threadIdx.x == 0) {
+    cd P = (d * kappa) * shat;
+    jn_range(P, K, J);
+    cd sinv = cinv(shat);
+    cd f = mk(1.0 / HP_TWO_PI, 0.0);
+    for (int k = 0; k <= K; ++k) {
+      if (k > 0) f = (1.0 / k) * (f * sinv);
+      h[k] = J[k] * f;
+    }
+  }
+  __syncthreads();
+  cd *out = Tr + ((size_t)((lev - 1) * 21 + cls) * 2 + sign) * P1 * P1;
+  for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) {
+    int n = e / P1, m = e % P1;
+    cd v = binom(n + m, m) * h[n + m];
+    int ph = sign ? (m - n) : (n - m);  // i^{ph}
+    ph &= 3;
+    for (int r = 0; r < ph; ++r) v = mul_i(v);
+    out[e] = v;
+  }
+}
+
+__global__ void k_to_float(const cd *a, cf *b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    b[i] = to<float>(a[i]);
+}
+
+}  // namespace
+
+// Table layout inside pl->t_* (double complex unless prec != FP64, then the
+// FP32 copies live right after the double block of the same allocation).
+hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
+  int p = pl->p, P1 = p + 1, H = pl->H;
+  size_t m2 = (size_t)P1 * P1;
+  cd *m2m = (cd *)pl->t_m2m, *l2l = (cd *)pl->t_l2l, *fm2l = (cd *)pl->t_m2l;
+  cd *img = (cd *)pl->t_rlog, *rea = (cd *)pl->t_refl;
+  cd *logs = (cd *)pl->t_rlog0;  // 49 free + 21 image logs
+  k_m2m_l2l<<<4, 256, 0, st>>>(p, m2m, l2l);
+  k_free_m2l<<<49, 256, 0, st>>>(p, fm2l, logs);
+  k_img_m2l<<<21, 256, 0, st>>>(p, img, logs + 49);
+  size_t shm = sizeof(cd) * 2 * (2 * p + 1);
+  k_reaction_m2l<<<H * 21 * 2, 256, shm, st>>>(p, H, pl->side, mk(pl->kre, pl->kim), rea);
+  HP_LAUNCH_CHECK();
+  if (pl->prec != HPFMM_FP64) {
+    struct { void *base; size_t n; } t[5] = {{pl->t_m2m, 4 * m2}, {pl->t_l2l, 4 * m2},
+                                               {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2},
+                                               {pl->t_refl, (size_t)H * 42 * m2}};
+    for (auto &e : t) {
+      k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
+    }
+    HP_LAUNCH_CHECK();
+  }
+  return HPFMM_OK;
+}

@@ -1,0 +1,131 @@
+"""Parity of the device FMM (hpfmm_create / hpfmm_eval) with the oracle.
+
+Error metric: relative L2 of the complex potential (and of the gradient) over
+all targets at N = 2000 (full oracle sum) and over sampled targets at
+N = 1e6.  The FMM is exact up to its truncation: its error must decay
+geometrically in p (Theorems 3.3-3.7) and reach the per-p bounds below,
+which carry margin over the measured values."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import oracle_cache
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2507_21913_gb300 as hp  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def run(x, y, q, kappa, p, leaf, prec="fp64", levels=0, host=False):
+    if host:
+        plan = hp.hpfmm_create(x, y, kappa=kappa, p=p, leaf_size=leaf, prec=prec, levels=levels)
+        u, g = hp.hpfmm_eval(plan, q)
+    else:
+        t = lambda a: torch.tensor(a, device=DEV)
+        plan = hp.hpfmm_create(t(x), t(y), kappa=kappa, p=p, leaf_size=leaf, prec=prec,
+                               levels=levels)
+        u, g = hp.hpfmm_eval(plan, t(q))
+    return u.cpu().numpy(), g.cpu().numpy(), plan
+
+
+# per-p bounds for the FP64 FMM at N = 2000, kappa = 1, leaf 32
+P_BOUNDS = {4: 2e-3, 8: 2e-5, 12: 4e-7, 16: 1e-8, 20: 3e-10, 24: 1e-11, 30: 1e-13, 40: 1e-14}
+
+
+def test_fmm_fp64_error_decays_in_p():
+    x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
+    errs = {}
+    for p in sorted(P_BOUNDS):
+        u, g, _ = run(x, y, q, 1.0, p, 32)
+        errs[p] = rel(u, u_ref)
+        gerr = rel(g, g_ref)
+        print("p=%d pot %.3e grad %.3e" % (p, errs[p], gerr))
+        assert errs[p] < P_BOUNDS[p], (p, errs[p])
+        assert gerr < 30 * P_BOUNDS[p]
+    ps = sorted(errs)
+    slope = np.polyfit(ps, np.log([errs[p] for p in ps]), 1)[0]
+    assert slope < -0.3
+
+
+@pytest.mark.parametrize("kappa", [10.0, 0.1, 1 + 0.5j])
+def test_fmm_fp64_kappas(kappa):
+    x, y, q = workloads.uniform(1500, seed=8)
+    u_ref, g_ref = oracle.direct(x, y, q, kappa=kappa)
+    u, g, _ = run(x, y, q, kappa, 24, 24)
+    assert rel(u, u_ref) < 1e-7
+    assert rel(g, g_ref) < 1e-6
+
+
+@pytest.mark.parametrize("levels", [1, 2, 4, 5])
+def test_fmm_fp64_tree_depths(levels):
+    x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
+    u, g, _ = run(x, y, q, 1.0, 24, 32, levels=levels)
+    assert rel(u, u_ref) < 1e-7
+    assert rel(g, g_ref) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_fmm_fp32_config1(prec):
+    x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
+    u, g, _ = run(x, y, q, 1.0, 16, 32, prec=prec)
+    assert rel(u, u_ref) < 5e-6
+    assert rel(g, g_ref) < 5e-5
+
+
+def test_host_pointer_path_matches_device_path():
+    x, y, q = workloads.uniform(3000, seed=9)
+    u1, g1, _ = run(x, y, q, 1.0, 12, 32)
+    u2, g2, _ = run(x, y, q, 1.0, 12, 32, host=True)
+    assert np.array_equal(u1, u2) and np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 333])
+def test_fmm_small_and_ragged(n):
+    x, y, q = workloads.uniform(n, seed=n)
+    u_ref, g_ref = oracle.direct(x, y, q, kappa=1.0)
+    u, g, _ = run(x, y, q, 1.0, 20, 8)
+    assert rel(u, u_ref) < 1e-7
+    if n > 1:
+        assert rel(g, g_ref) < 1e-6
+
+
+def test_points_close_to_boundary():
+    x, y, q = workloads.uniform(1200, seed=12)
+    y[::3] = 1e-5 * (1 + np.arange(400) / 400.0)  # a third of the points at y ~ 1e-5
+    u_ref, g_ref = oracle.direct(x, y, q, kappa=1.0)
+    u, g, _ = run(x, y, q, 1.0, 24, 16)
+    assert rel(u, u_ref) < 1e-7
+    assert rel(g, g_ref) < 1e-6
+
+
+def test_multiple_rhs_and_plan_reuse():
+    x, y, q, w = workloads.uniform(2500, seed=13, with_w=True)
+    t = lambda a: torch.tensor(a, device=DEV)
+    plan = hp.hpfmm_create(t(x), t(y), kappa=2.0, p=16, leaf_size=32)
+    u2, g2 = hp.hpfmm_eval(plan, t(np.stack([q, w])))
+    uq, gq = hp.hpfmm_eval(plan, t(q))
+    uw, gw = hp.hpfmm_eval(plan, t(w))
+    assert torch.equal(u2[0], uq) and torch.equal(u2[1], uw)
+    assert torch.equal(g2[0], gq) and torch.equal(g2[1], gw)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 2e-6)])
+def test_fmm_full_size_sampled(prec, tol):
+    """N = 1e6 in the benchmark's configuration, 32 sampled targets."""
+    n = 1_000_000
+    x, y, q = workloads.uniform(n, seed=0)
+    idx = workloads.sample_targets(n, 32, seed=1)
+    u_ref, g_ref = oracle_cache.sampled_closed(x, y, q, idx, 1.0)
+    p = 24 if prec == "fp64" else 16
+    leaf = 16 if prec == "fp64" else 64
+    u, g, _ = run(x, y, q, 1.0, p, leaf, prec=prec)
+    assert rel(u[idx], u_ref) < tol
+    assert rel(g[idx], g_ref) < 20 * tol
