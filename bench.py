@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the half-plane Robin FMM on GB300.
+
+One step = the whole evaluation path on one synthetic point set: validation,
+bounding square, Morton keys and sort, leaf offsets, translation tables
+(hpfmm_update_points), then the FMM passes and the near field with
+potentials and fields for one charge vector (hpfmm_eval).  Inputs stay
+resident in HBM; L2 is flushed (a 512 MiB write) between timed steps.
+
+Metric: particle interactions per second = N^2 / t_step at N = 1e6 (uniform
+points in [0,1) x (0,1], charges U[-1,1), kappa = 1 lossless), fast path
+(FP32, fields included) at a truncation order whose relative L2 error against
+the FP64 oracle (sampled targets) is at most 1e-6; the plain FP64 FMM on the
+same workload is timed beside it.
+
+--impl reference runs the oracle (the CPU direct sum with the quadrature
+reaction kernel) on a bounded sample of the same workload.
+Multi-GPU (torchrun, one process per GPU): independent replicas, no
+collective on the data path ("replicas only").
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "particle interactions/sec at N=1e6, rel err ≤1e-6, vs plain FP64 FMM on GB300"
+UNIT = "interactions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--kappa", type=float, default=1.0)
+    ap.add_argument("--p", type=int, default=12)
+    ap.add_argument("--levels", type=int, default=8)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--p64", type=int, default=12, help="order of the FP64 comparison run")
+    ap.add_argument("--levels64", type=int, default=8)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check-targets", type=int, default=16)
+    ap.add_argument("--cpu-targets", type=int, default=8)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# oracle pieces (CPU baseline, error check); spawn pool so no fork after CUDA
+def _oracle_chunk(args):
+    xs, ys, qs, idx, kappa = args
+    import oracle as o
+    return o.direct_closed(xs, ys, qs, idx, kappa)
+
+
+def oracle_sampled(x, y, q, idx, kappa):
+    import multiprocessing as mp
+    procs = min(16, os.cpu_count() or 1, len(idx))
+    chunks = [c for c in np.array_split(np.asarray(idx), procs) if len(c)]
+    with mp.get_context("spawn").Pool(len(chunks)) as pool:
+        res = pool.map(_oracle_chunk, [(x, y, q, c, kappa) for c in chunks])
+    return np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
+
+
+def cpu_baseline(x, y, q, kappa, ntargets):
+    """The oracle (C, OpenMP, quadrature reaction kernel) as it stands, timed on
+    ntargets sampled targets x all sources; returns interactions/s."""
+    import oracle
+    idx = workloads.sample_targets(len(x), ntargets, seed=1)
+    nthreads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.direct(x, y, q, x[idx], y[idx], kappa, self_index=idx, grad=True)
+    dt = time.perf_counter() - t0
+    pairs = len(idx) * len(x)
+    return {"value": pairs / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": "%d sampled targets x %d sources, potentials and fields, %.1f s"
+                      % (len(idx), len(x), dt)}
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.proc = None
+        self.dev = dev_index
+
+    def start(self):
+        try:
+            import torch
+            sel = ["-i", str(torch.cuda.get_device_properties(self.dev).uuid)]
+            sel[1] = sel[1] if sel[1].startswith("GPU-") else "GPU-" + sel[1]
+        except Exception:
+            sel = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", *sel, "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def leaf_pairs(keys, H):
+    """Near-field pair counts of the uniform level-H tree: free pairs (3x3
+    neighbourhood, j != i) and mirror pairs (bottom-row neighbours)."""
+    nx = 1 << H
+    leaf = (keys >> np.uint64(60 - 2 * H)).astype(np.int64)
+    ix = np.zeros_like(leaf); iy = np.zeros_like(leaf)
+    for b in range(H):
+        ix |= ((leaf >> (2 * b)) & 1) << b
+        iy |= ((leaf >> (2 * b + 1)) & 1) << b
+    grid = np.zeros((nx + 2, nx + 2), np.int64)
+    np.add.at(grid, (iy + 1, ix + 1), 1)
+    c = grid[1:-1, 1:-1]
+    nb = sum(grid[1 + dy:nx + 1 + dy, 1 + dx:nx + 1 + dx] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    free = int(np.sum(c * nb) - len(keys))
+    row = grid[1, :]
+    mirror = int(np.sum(row[1:-1] * (row[:-2] + row[1:-1] + row[2:])))
+    return free, mirror
+
+
+def roofline(passes_ms, launches, args, npairs, mpairs, H, peaks, clocks):
+    """Roofline entry for the dominant pass (per-launch algorithmic work /
+    per-launch CUDA-event duration)."""
+    dom = max(passes_ms, key=lambda k: passes_ms[k])
+    nl = max(1, launches.get(dom, 1))
+    t = passes_ms[dom] / 1e3 / nl  # seconds per launch
+    f_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    sms = 152
+    if dom == "eval":
+        # SFU (MUFU) bound: lg2 + rcp per free pair and per image pair
+        ops = 2.0 * npairs + 2.0 * mpairs
+        peak = 16 * sms * f_ghz * 1e9 / 1e12  # TOP/s
+        achieved = ops / t / 1e12
+        return {"kernel": "k_eval32 (L2P + near field)" if args.prec != "fp64" else "k_eval64",
+                "bound": "alu", "unit": "TOP/s (SFU ops)", "achieved": achieved, "peak": peak,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "16 SFU ops/clk/SM x 152 SMs x %.0f MHz" % (f_ghz * 1e3),
+                "per_launch_ms": t * 1e3}
+    if dom == "m2l_free":
+        P1 = args.p + 1
+        ntrans = sum(27 * (4 ** (l - 1)) * 4 for l in range(2, H + 1))  # upper bound ~ boxes x 27
+        flops = 8.0 * P1 * P1 * ntrans / max(1, H - 1)
+        peak = 128 * 2 * sms * f_ghz * 1e9 / 1e12
+        achieved = flops / t / 1e12
+        return {"kernel": "k_m2l_free", "bound": "alu", "unit": "TFLOP/s (FP32 FMA pipe)",
+                "achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": None,
+                "peak_source": "128 FMA/clk/SM x 2 x 152 SMs x %.0f MHz" % (f_ghz * 1e3),
+                "per_launch_ms": t * 1e3}
+    return {"kernel": dom, "bound": "alu", "unit": "ms", "achieved": t * 1e3, "peak": None,
+            "frac": None, "traffic": None}
+
+
+def run_ours(args):
+    import torch
+    import paper_2507_21913_gb300 as hp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hp.lib(build_if_missing=True)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+
+    n = args.n
+    x, y, q = workloads.uniform(n, seed=0)
+    xd = torch.tensor(x, device=dev); yd = torch.tensor(y, device=dev)
+    qd = torch.tensor(q, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_plan(prec, p, levels):
+        return hp.hpfmm_create(xd, yd, kappa=args.kappa, p=p, leaf_size=32, prec=prec,
+                               levels=levels)
+
+    def timed_steps(plan, k, w, timing):
+        pot = torch.empty(n, dtype=torch.complex128, device=dev)
+        grad = torch.empty((n, 2), dtype=torch.complex128, device=dev)
+        for _ in range(w):
+            hp.hpfmm_update_points(plan, xd, yd)
+            hp.hpfmm_eval(plan, qd, out=(pot, grad))
+        torch.cuda.synchronize(dev)
+        hp.hpfmm_read_timing(plan)
+        hp.hpfmm_set_timing(plan, timing)
+        _, l0 = hp.hpfmm_read_timing(plan)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for i in range(k):
+            flush.fill_(i & 0xff)  # evict L2 between steps (outside the events)
+            ev[i][0].record(stream)
+            hp.hpfmm_update_points(plan, xd, yd)
+            hp.hpfmm_eval(plan, qd, out=(pot, grad))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        pms, l1 = hp.hpfmm_read_timing(plan)
+        hp.hpfmm_set_timing(plan, False)
+        launches = {kk: l1[kk] - l0[kk] for kk in l1}
+        return ms, pms, launches, pot, grad
+
+    # fast path, timed
+    plan = make_plan(args.prec, args.p, args.levels)
+    info = plan.info()
+    clock = ClockSampler(local)
+    clock.start()
+    ms, pms, launches, pot, grad = timed_steps(plan, args.steps, args.warmup, True)
+    clocks = clock.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * float(n) * float(n) / (ms_step / 1e3)
+
+    # event-timed passes with the same clocks give the dominant kernel
+    keys, _ = hp.hpfmm_get_order(plan)
+    npairs, mpairs = leaf_pairs(keys, info["levels"])
+    launches_per_step = {k: v / args.steps for k, v in launches.items()}
+    pass_ms_step = {k: v / args.steps for k, v in pms.items()}
+    roof = roofline(pms, launches, args, npairs, mpairs, info["levels"], peaks, clocks)
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32" if args.prec != "fp64" else "f64",
+              "data": "synthetic (seeded uniform points, PCG64 seed 0)",
+              "config": {"workload": "uniform N=%d in [0,1)x(0,1], q~U[-1,1), kappa=%g lossless, "
+                                     "potential+field, one RHS, tree rebuilt every step" %
+                                     (n, args.kappa),
+                         "n": n, "kappa": args.kappa, "p": args.p, "levels": info["levels"],
+                         "mean_leaf": n / 4 ** info["levels"], "precision": args.prec,
+                         "l2": "flushed between steps (512 MiB write)",
+                         "parallelism": "replicas" if world > 1 else "single GPU"},
+              "gpu_launches": int(sum(launches.values())),
+              "passes_ms_per_step": pass_ms_step,
+              "launches_per_step": launches_per_step,
+              "near_field_pairs": {"free": npairs, "mirror": mpairs},
+              "roofline": roof, "clocks": clocks}
+
+    # accuracy of the timed configuration
+    if not args.no_check and rank == 0:
+        idx = workloads.sample_targets(n, args.check_targets, seed=1)
+        u_ref, g_ref = oracle_sampled(x, y, q, idx, args.kappa)
+        u = pot.cpu().numpy()[idx]; g = grad.cpu().numpy()[idx]
+        result["rel_err"] = {"pot": float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)),
+                             "grad": float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)),
+                             "targets": len(idx), "reference": "oracle (E1 closed form)"}
+
+    # plain FP64 FMM on the same workload
+    if not args.no_fp64:
+        plan64 = make_plan("fp64", args.p64, args.levels64)
+        k64 = max(2, min(args.steps, 5))
+        ms64, pms64, _, pot64, grad64 = timed_steps(plan64, k64, 2, True)
+        e = {"value": world * float(n) * n / (ms64 / k64 / 1e3), "unit": UNIT,
+             "ms_per_step": ms64 / k64, "p": args.p64, "levels": plan64.info()["levels"],
+             "passes_ms_per_step": {k: v / k64 for k, v in pms64.items()}}
+        if not args.no_check and rank == 0:
+            u64 = pot64.cpu().numpy()[idx]
+            e["rel_err_pot"] = float(np.linalg.norm(u64 - u_ref) / np.linalg.norm(u_ref))
+        result["fp64_fmm"] = e
+        result["speedup_vs_fp64_fmm"] = e["ms_per_step"] / ms_step
+        del plan64
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    if not args.no_e2e:
+        xh = torch.tensor(x).pin_memory(); yh = torch.tensor(y).pin_memory()
+        qh = torch.tensor(q).pin_memory()
+        poth = torch.empty(n, dtype=torch.complex128).pin_memory()
+        gradh = torch.empty((n, 2), dtype=torch.complex128).pin_memory()
+        for _ in range(2):
+            hp.hpfmm_update_points(plan, xh, yh)
+            hp.hpfmm_eval(plan, qh, out=(poth, gradh))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        k = args.steps
+        for _ in range(k):
+            hp.hpfmm_update_points(plan, xh, yh)
+            hp.hpfmm_eval(plan, qh, out=(poth, gradh))  # synchronises (host outputs)
+        dt = (time.perf_counter() - t0) / k
+        if dist:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        result["e2e"] = {"value": world * float(n) * n / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+                         "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": (16 + 32) * n}
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(x, y, q, args.kappa, args.cpu_targets)
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n = args.n
+    x, y, q = workloads.uniform(n, seed=0)
+    ntarg = max(1, args.cpu_targets // 4)
+    idx_all = workloads.sample_targets(n, ntarg * (args.steps + args.warmup), seed=1)
+    nthreads = oracle.max_threads()
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = idx_all[s * ntarg:(s + 1) * ntarg]
+        t0 = time.perf_counter()
+        oracle.direct(x, y, q, x[idx], y[idx], args.kappa, self_index=idx, grad=True)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.sum(times))
+    pairs = ntarg * n * args.steps
+    value = pairs / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded uniform points, PCG64 seed 0)",
+        "config": {"workload": "uniform N=%d, kappa=%g; each step %d sampled targets x all sources"
+                               % (n, args.kappa, ntarg), "n": n, "kappa": args.kappa},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": "%d targets x %d sources per step" % (ntarg, n)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

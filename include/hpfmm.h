@@ -100,6 +100,18 @@ hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n, double ka
                           void *stream, hpfmm_plan **out);
 
 /*
+ * hpfmm_update_points -- rebuild the plan's tree and tables for a new set of
+ * n points (same n as at creation, same kappa, p and options), reusing the
+ * plan's device memory: validation, bounding square, Morton keys and sort,
+ * leaf offsets and translation tables, as in hpfmm_create, without device
+ * allocations (host coordinates are staged through the stream-ordered pool).
+ * Returns EINVAL (synchronously) for invalid points; the plan then holds no
+ * valid tree until a successful update.
+ */
+hpfmm_status hpfmm_update_points(hpfmm_plan *plan, const double *x, const double *y,
+                                 void *stream);
+
+/*
  * hpfmm_eval -- u = G q for nrhs charge vectors on the plan's points
  * (Algorithm 2: free FMM + image FMM + reaction FMM for Phi_2^+ and Phi_2^-,
  * summed).
@@ -147,6 +159,19 @@ hpfmm_status hpfmm_get_info(const hpfmm_plan *plan, hpfmm_plan_info *info);
  * Synchronises the stream.
  */
 hpfmm_status hpfmm_get_order(const hpfmm_plan *plan, uint64_t *keys, int64_t *perm, void *stream);
+
+/*
+ * Pass timing.  hpfmm_set_timing(plan, 1) makes the plan record a CUDA event
+ * pair on the caller's stream around every pass it launches (tree build,
+ * tables, charge gather, P2M, M2M, free M2L, mirror M2L, L2L, leaf
+ * evaluation = L2P + near field, in this order of pass ids 0..8).
+ * hpfmm_read_timing synchronises with that work and returns, per pass, the
+ * device milliseconds recorded since the previous read (ms may be NULL) and the
+ * number of kernels the plan has launched in that pass since creation
+ * (launches may be NULL; counted whether or not timing is on).
+ */
+hpfmm_status hpfmm_set_timing(hpfmm_plan *plan, int enable);
+hpfmm_status hpfmm_read_timing(hpfmm_plan *plan, double ms[9], int64_t launches[9]);
 
 /* Wait for the plan's outstanding work on `stream` and report any device-side
  * status (HPFMM_ETIMEOUT) recorded by its kernels. */

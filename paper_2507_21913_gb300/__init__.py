@@ -60,15 +60,18 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_create.argtypes = [vp, vp, i64, dbl, dbl, i32, i32, ctypes.POINTER(Options), vp,
                                ctypes.POINTER(vp)]
     L.hpfmm_eval.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.hpfmm_update_points.argtypes = [vp, vp, vp, vp]
     L.hpfmm_destroy.argtypes = [vp]
     L.hpfmm_direct.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, dbl, dbl, vp, vp, vp]
     L.hpfmm_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.hpfmm_get_order.argtypes = [vp, vp, vp, vp]
     L.hpfmm_sync.argtypes = [vp, vp]
+    L.hpfmm_set_timing.argtypes = [vp, i32]
+    L.hpfmm_read_timing.argtypes = [vp, vp, vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
-    for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
-              "hpfmm_get_order", "hpfmm_sync"):
+    for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
+              "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -143,16 +146,32 @@ def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau
     return Plan(h, x.numel(), x.device)
 
 
-def hpfmm_eval(plan, q, grad=True):
+def hpfmm_update_points(plan, x, y):
+    """Rebuild the plan's tree and tables for new points (same n), no allocation."""
+    x = _as_tensor(x)
+    y = _as_tensor(y, x.device)
+    if x.numel() != plan.n or y.numel() != plan.n:
+        raise ValueError("hpfmm_update_points: expected %d points" % plan.n)
+    _check(lib().hpfmm_update_points(plan.handle, x.data_ptr(), y.data_ptr(), _stream(x.device)))
+
+
+def hpfmm_eval(plan, q, grad=True, out=None):
     """u = G q (and grad u) for q of shape (n,) or (nrhs, n).  Returns complex128
-    tensors pot (nrhs, n) and grad (nrhs, n, 2) (or None), squeezed for 1-D q."""
+    tensors pot (nrhs, n) and grad (nrhs, n, 2) (or None), squeezed for 1-D q.
+    out=(pot, grad) supplies the output tensors (e.g. pinned host memory)."""
     torch = _torch()
     q = _as_tensor(q)
     squeeze = q.dim() == 1
     q2 = q.reshape(-1, plan.n)
     nrhs = q2.shape[0]
-    pot = torch.empty((nrhs, plan.n), dtype=torch.complex128, device=q.device)
-    g = torch.empty((nrhs, plan.n, 2), dtype=torch.complex128, device=q.device) if grad else None
+    if out is not None:
+        pot, g = out
+        pot = pot.view(nrhs, plan.n)
+        g = g.view(nrhs, plan.n, 2) if (grad and g is not None) else None
+        grad = g is not None
+    else:
+        pot = torch.empty((nrhs, plan.n), dtype=torch.complex128, device=q.device)
+        g = torch.empty((nrhs, plan.n, 2), dtype=torch.complex128, device=q.device) if grad else None
     _check(lib().hpfmm_eval(plan.handle, q2.data_ptr(), nrhs, pot.data_ptr(),
                             g.data_ptr() if grad else None, _stream(q.device)))
     if squeeze:
@@ -208,6 +227,21 @@ def hpfmm_get_order(plan):
     _check(lib().hpfmm_get_order(plan.handle, keys.ctypes.data, perm.ctypes.data,
                                  _stream(plan.device)))
     return keys, perm
+
+
+PASS_NAMES = ("tree", "tables", "gather", "p2m", "m2m", "m2l_free", "m2l_mirror", "l2l", "eval")
+
+
+def hpfmm_set_timing(plan, enable=True):
+    _check(lib().hpfmm_set_timing(plan.handle, 1 if enable else 0))
+
+
+def hpfmm_read_timing(plan):
+    """({pass: device ms since the last read}, {pass: kernel launches since creation})."""
+    ms = np.zeros(9)
+    ln = np.zeros(9, np.int64)
+    _check(lib().hpfmm_read_timing(plan.handle, ms.ctypes.data, ln.ctypes.data))
+    return dict(zip(PASS_NAMES, ms.tolist())), dict(zip(PASS_NAMES, ln.tolist()))
 
 
 def hpfmm_sync(plan):

@@ -52,8 +52,88 @@ extern "C" void hpfmm_default_options(hpfmm_options *opt) {
   opt->tau_fp64 = 0.05;
 }
 
+#include <vector>
+
+struct TimingState {
+  std::vector<cudaEvent_t> pool;   // events, reused
+  size_t used = 0;
+  struct Rec { size_t a, b; int pass; };
+  std::vector<Rec> recs;
+  std::vector<int> open_pass;      // start event index per pass (one open at a time)
+};
+
+static cudaEvent_t next_event(TimingState *ts) {
+  if (ts->used == ts->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ts->pool.push_back(e);
+  }
+  return ts->pool[ts->used++];
+}
+
+void pass_begin(hpfmm_plan *pl, cudaStream_t st, int pass) {
+  if (!pl->timing || !pl->tstate) return;
+  TimingState *ts = (TimingState *)pl->tstate;
+  if (ts->open_pass.empty()) ts->open_pass.assign(HPFMM_NPASS, -1);
+  cudaEvent_t e = next_event(ts);
+  if (!e) return;
+  cudaEventRecord(e, st);
+  ts->open_pass[pass] = (int)(ts->used - 1);
+}
+
+void pass_end(hpfmm_plan *pl, cudaStream_t st, int pass, int nlaunch) {
+  pl->launches[pass] += nlaunch;
+  if (!pl->timing || !pl->tstate) return;
+  TimingState *ts = (TimingState *)pl->tstate;
+  if (ts->open_pass.empty() || ts->open_pass[pass] < 0) return;
+  cudaEvent_t e = next_event(ts);
+  if (!e) return;
+  cudaEventRecord(e, st);
+  ts->recs.push_back({(size_t)ts->open_pass[pass], ts->used - 1, pass});
+  ts->open_pass[pass] = -1;
+}
+
+extern "C" hpfmm_status hpfmm_set_timing(hpfmm_plan *pl, int enable) {
+  if (!pl) {
+    set_last_error("hpfmm_set_timing: null plan");
+    return HPFMM_EINVAL;
+  }
+  if (!pl->tstate) pl->tstate = new TimingState();
+  pl->timing = enable != 0;
+  return HPFMM_OK;
+}
+
+extern "C" hpfmm_status hpfmm_read_timing(hpfmm_plan *pl, double ms[9], int64_t launches[9]) {
+  if (!pl) {
+    set_last_error("hpfmm_read_timing: null plan");
+    return HPFMM_EINVAL;
+  }
+  if (ms)
+    for (int i = 0; i < HPFMM_NPASS; ++i) ms[i] = 0.0;
+  TimingState *ts = (TimingState *)pl->tstate;
+  if (ts && !ts->recs.empty()) {
+    HP_CUDA(cudaEventSynchronize(ts->pool[ts->recs.back().b]));
+    for (auto &r : ts->recs) {
+      float t = 0.f;
+      HP_CUDA(cudaEventElapsedTime(&t, ts->pool[r.a], ts->pool[r.b]));
+      if (ms) ms[r.pass] += t;
+    }
+    ts->recs.clear();
+    ts->used = 0;
+  }
+  if (launches)
+    for (int i = 0; i < HPFMM_NPASS; ++i) launches[i] = pl->launches[i];
+  return HPFMM_OK;
+}
+
 static void free_plan(hpfmm_plan *pl) {
   if (!pl) return;
+  if (pl->tstate) {
+    TimingState *ts = (TimingState *)pl->tstate;
+    for (cudaEvent_t e : ts->pool) cudaEventDestroy(e);
+    delete ts;
+    pl->tstate = nullptr;
+  }
   void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status};
@@ -79,6 +159,46 @@ static int choose_levels(int64_t n, int leaf) {
   if (H < 1) H = 1;
   if (H > 12) H = 12;
   return H;
+}
+
+// tree + tables for the points (x, y) of a plan whose buffers exist
+static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const double *dx = x, *dy = y;
+  double *tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!is_device_pointer(x) || !is_device_pointer(y)) {
+    e = cudaMallocAsync((void **)&tmp, 2 * sizeof(double) * n, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp, x, sizeof(double) * n, cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp + n, y, sizeof(double) * n, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) {
+      set_last_error("staging the coordinates: %s", cudaGetErrorString(e));
+      return HPFMM_ECUDA;
+    }
+    dx = tmp;
+    dy = tmp + n;
+  }
+  hpfmm_status s = tree_build(pl, dx, dy, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (s != HPFMM_OK) return s;
+  double kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
+  if (kabs * sqrt(5.0) * pl->side > 60.0) {
+    set_last_error("|kappa| * sqrt(5) * side = %g exceeds 60, the range of the device I_n "
+                   "evaluation", kabs * sqrt(5.0) * pl->side);
+    return HPFMM_EUNSUPPORTED;
+  }
+  return tables_build(pl, st);
+}
+
+extern "C" hpfmm_status hpfmm_update_points(hpfmm_plan *pl, const double *x, const double *y,
+                                            void *stream) {
+  if (!pl || !x || !y) {
+    set_last_error("hpfmm_update_points: null argument");
+    return HPFMM_EINVAL;
+  }
+  return rebuild(pl, x, y, (cudaStream_t)stream);
 }
 
 extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n,
@@ -165,36 +285,12 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     free_plan(pl);
     return HPFMM_ECUDA;
   }
-  // stage host coordinates
-  const double *dx = x, *dy = y;
-  double *tmp = nullptr;
-  if (!is_device_pointer(x) || !is_device_pointer(y)) {
-    e = cudaMallocAsync((void **)&tmp, 2 * sizeof(double) * n, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tmp, x, sizeof(double) * n, cudaMemcpyDefault, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tmp + n, y, sizeof(double) * n, cudaMemcpyDefault, st);
-    if (e != cudaSuccess) {
-      set_last_error("hpfmm_create: staging: %s", cudaGetErrorString(e));
-      free_plan(pl);
-      return HPFMM_ECUDA;
-    }
-    dx = tmp;
-    dy = tmp + n;
-  }
-  s = tree_build(pl, dx, dy, st);
-  if (tmp) cudaFreeAsync(tmp, st);
-  if (s != HPFMM_OK) { free_plan(pl); return s; }
-  double kabs = sqrt(kappa_re * kappa_re + kappa_im * kappa_im);
-  if (kabs * sqrt(5.0) * pl->side > 60.0) {
-    set_last_error("hpfmm_create: |kappa| * sqrt(5) * side = %g exceeds 60, the range of the "
-                   "device I_n evaluation", kabs * sqrt(5.0) * pl->side);
+  s = rebuild(pl, x, y, st);
+  if (s != HPFMM_OK) {
     cudaStreamSynchronize(st);
     free_plan(pl);
-    return HPFMM_EUNSUPPORTED;
+    return s;
   }
-  s = tables_build(pl, st);
-  if (s != HPFMM_OK) { free_plan(pl); return s; }
   *out = pl;
   return HPFMM_OK;
 }

@@ -10,6 +10,7 @@
 #ifndef HPFMM_MAX_P
 #define HPFMM_MAX_P 40
 #endif
+#define HPFMM_NPASS 9
 
 // ---------------------------------------------------------------------------
 // complex numbers (interleaved re, im)
@@ -162,7 +163,20 @@ struct hpfmm_plan {
   int64_t stage_rhs = 0;
   int *status = nullptr;  // device status word
   int64_t workspace_bytes = 0;
+
+  // pass timing (events on the caller's stream) and launch counts
+  bool timing = false;
+  int64_t launches[HPFMM_NPASS] = {};
+  void *tstate = nullptr;  // TimingState, see api.cu
 };
+
+// pass ids of hpfmm_read_timing
+enum { PASS_TREE = 0, PASS_TABLES, PASS_GATHER, PASS_P2M, PASS_M2M, PASS_M2L_FREE,
+       PASS_M2L_MIRROR, PASS_L2L, PASS_EVAL };
+// record the start / end of a pass on stream st (no-ops unless timing is on);
+// pass_end also adds nlaunch to the pass's launch count
+void pass_begin(hpfmm_plan *pl, cudaStream_t st, int pass);
+void pass_end(hpfmm_plan *pl, cudaStream_t st, int pass, int nlaunch);
 
 // ---------------------------------------------------------------------------
 // error plumbing (host)

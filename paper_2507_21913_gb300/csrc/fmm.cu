@@ -577,7 +577,10 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   R *qs = (R *)pl->qs;
   cpx<R> *M = (cpx<R> *)pl->M, *A = (cpx<R> *)pl->A, *B = (cpx<R> *)pl->B;
 
+  pass_begin(pl, st, PASS_GATHER);
   k_gather_q<R><<<cdiv_u(n, 256), 256, 0, st>>>(q, pl->perm, n, qs);
+  pass_end(pl, st, PASS_GATHER, 1);
+  pass_begin(pl, st, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
   size_t shp2m = sizeof(cpx<R>) * P1 * 33 * kWarpsPerBlock;
   if (sizeof(R) == 8) {
@@ -589,9 +592,12 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     k_p2m<float><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
         lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cf *)M);
   }
+  pass_end(pl, st, PASS_P2M, 1);
+  pass_begin(pl, st, PASS_M2M);
   for (int l = H - 1; l >= 1; --l)
     k_m2m<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
         l, p, Tm2m, M);
+  pass_end(pl, st, PASS_M2M, H - 1);
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
@@ -600,14 +606,21 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     double logd = log(pl->side / (double)(1 << l));
     if (l >= 2) {
       dim3 g(cdiv_u(int64_t(1) << (2 * (l - 1)), 32), 4);
+      pass_begin(pl, st, PASS_M2L_FREE);
       k_m2l_free<R><<<g, 128, shfree, st>>>(l, p, logd, Tfree, logs, M, A, B);
+      pass_end(pl, st, PASS_M2L_FREE, 1);
     }
+    pass_begin(pl, st, PASS_M2L_MIRROR);
     k_m2l_mirror<R><<<cdiv_u(2 << l, kWarpsPerBlock), 32 * kWarpsPerBlock, shmir, st>>>(
         l, p, logd, Timg, logs + 49, Treact, M, A, B, l >= 2 ? 1 : 0);
+    pass_end(pl, st, PASS_M2L_MIRROR, 1);
   }
+  pass_begin(pl, st, PASS_L2L);
   for (int l = 2; l <= H; ++l)
     k_l2l<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
         l, p, Tl2l, A, B);
+  pass_end(pl, st, PASS_L2L, H - 1);
+  pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
   cd kappa = mk(pl->kre, pl->kim);
   if (sizeof(R) == 8) {
@@ -620,6 +633,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p, kappa, tau,
         (const cf *)A, (const cf *)B, pot, grad);
   }
+  pass_end(pl, st, PASS_EVAL, 1);
   HP_LAUNCH_CHECK();
   return HPFMM_OK;
 }

@@ -159,6 +159,7 @@ hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
   cd *m2m = (cd *)pl->t_m2m, *l2l = (cd *)pl->t_l2l, *fm2l = (cd *)pl->t_m2l;
   cd *img = (cd *)pl->t_rlog, *rea = (cd *)pl->t_refl;
   cd *logs = (cd *)pl->t_rlog0;  // 49 free + 21 image logs
+  pass_begin(pl, st, PASS_TABLES);
   k_m2m_l2l<<<4, 256, 0, st>>>(p, m2m, l2l);
   k_free_m2l<<<49, 256, 0, st>>>(p, fm2l, logs);
   k_img_m2l<<<21, 256, 0, st>>>(p, img, logs + 49);
@@ -174,5 +175,6 @@ hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
     }
     HP_LAUNCH_CHECK();
   }
+  pass_end(pl, st, PASS_TABLES, pl->prec != HPFMM_FP64 ? 9 : 4);
   return HPFMM_OK;
 }

@@ -246,6 +246,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
 
   hpfmm_status status = HPFMM_OK;
   double hgeo[3];
+  pass_begin(pl, st, PASS_TREE);
   bbox_partial<<<nbR, kRedThreads, 0, st>>>(x, y, n, part);
   bbox_final<<<1, 32, 0, st>>>(part, nbR, geo);
   cudaError_t e = cudaMemcpyAsync(hgeo, geo, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -256,6 +257,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
     return HPFMM_ECUDA;
   }
   if (hgeo[2] != 0.0) {
+    pass_end(pl, st, PASS_TREE, 2);
     set_last_error("points must be finite with y > 0");
     cudaFreeAsync(tmp, st);
     return HPFMM_EINVAL;
@@ -282,6 +284,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
                                                             pl->leaf_start);
   gather_points<<<gb, tb, 0, st>>>(x, y, vin, pl->keys, n, pl->H, geo, pl->xs, pl->ys, pl->perm,
                                    pl->loc32);
+  pass_end(pl, st, PASS_TREE, 2 + 1 + 3 * 8 + 2);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error("tree_build launch: %s", cudaGetErrorString(e));
