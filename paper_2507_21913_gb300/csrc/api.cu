@@ -136,7 +136,8 @@ static void free_plan(hpfmm_plan *pl) {
   }
   void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
-                  pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status};
+                  pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
+                  pl->t_binom};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -271,6 +272,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->t_rlog, tf * 21 * m2);
   ALLOC(pl->t_refl, tf * (size_t)pl->H * 42 * m2);
   ALLOC(pl->t_rlog0, sizeof(cd) * 70);
+  ALLOC(pl->t_binom, sizeof(double) * (2 * p + 2) * (2 * p + 2));
   ALLOC(pl->qs, (f32 ? sizeof(float) : sizeof(double)) * n);
   ALLOC(pl->M, csz * (size_t)pl->nbox * P1);
   ALLOC(pl->A, csz * (size_t)pl->nbox * P1);
@@ -285,7 +287,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     free_plan(pl);
     return HPFMM_ECUDA;
   }
-  s = rebuild(pl, x, y, st);
+  s = tables_static(pl, st);
+  if (s == HPFMM_OK) s = rebuild(pl, x, y, st);
   if (s != HPFMM_OK) {
     cudaStreamSynchronize(st);
     free_plan(pl);

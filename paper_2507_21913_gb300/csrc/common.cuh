@@ -152,6 +152,7 @@ struct hpfmm_plan {
   void *t_refl = nullptr;  // per level: 7 x 3 classes x (2p+1) complex: scaled I_k tables
   void *t_rlog = nullptr;  // per level: 7 x 3 classes x (p+1)^2 complex: image-log M2L
   void *t_rlog0 = nullptr;    // logs of the 49 free and 21 image class displacements
+  double *t_binom = nullptr;  // binomial coefficients C(a, b), a, b < 2p + 2
 
   // workspace (device)
   void *qs = nullptr;  // sorted charges (R)
@@ -205,6 +206,7 @@ void set_last_error(const char *fmt, ...);
 
 // internal entry points shared between translation units
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st);
+hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad, cudaStream_t st);
 bool is_device_pointer(const void *p);

@@ -205,10 +205,12 @@ k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
           if (row < P1) cfma(acc[r], Ts[row * P1 + k], mv);
         }
       }
-      if (warp == 0) {  // M_0 log(t d) term of L_0
+      if (warp == 0) {  // M_0 log(t d) term of L_0; only Re L_0 reaches the
+                        // potential, so the arg part (large at coarse levels,
+                        // cancelling between A and B) is left out
         cd lt = logt[cls];
         R m0 = Ms[lane].x;  // M_0 is real for real charges
-        acc[0] = acc[0] + mk<R>(m0 * (R)(lt.x + logd), m0 * (R)lt.y);
+        acc[0].x += m0 * (R)(lt.x + logd);
       }
     }
   }
@@ -228,6 +230,158 @@ k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
   }
   (void)iy;
   (void)ix;
+}
+
+// --------------------------------------------------------------------------
+// Patch form of the free-space M2L, used when everything fits in shared
+// memory.  A block owns an 8 x 8 patch of parent boxes of one level (so 64
+// target boxes of each child type); it stages the 20 x 20 patch of source
+// boxes' multipoles and the 40 translation matrices once, then warp w applies
+// the 27 offsets of child type w to its 64 targets (two per lane): the matrix
+// entry T[l][k] is a broadcast read shared by the warp, the source moment a
+// per-lane read.  All levels 2..H are processed by one launch.
+constexpr int kPatch = 8;                 // parents per side
+constexpr int kPatchSrc = 2 * kPatch + 4; // source boxes per side
+__constant__ signed char c_slot[49];      // 7x7 offset class -> 0..39, -1 for the near 3x3
+
+template <typename R, int P1>
+__global__ void __launch_bounds__(128)
+k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
+                 const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
+                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][P1][P1]
+  cpx<R> *Mp = Ts + 40 * P1 * P1;                          // [20*20][P1]
+  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * P1);  // [40] ln|t|
+  // level and patch of this block
+  int b = blockIdx.x, l = 2;
+  for (; l <= H; ++l) {
+    int np = (1 << (l - 1)) / kPatch;
+    np = np < 1 ? 1 : np;
+    if (b < np * np) break;
+    b -= np * np;
+  }
+  int npl = (1 << (l - 1)) / kPatch;
+  npl = npl < 1 ? 1 : npl;
+  int px0 = (b % npl) * kPatch, py0 = (b / npl) * kPatch;  // first parent of the patch
+  int nparent_side = 1 << (l - 1), nside = 1 << l;
+  const int64_t off = level_offset(l);
+  const R logd = (R)log(side / (double)nside);
+  // stage tables and source patch
+  for (int e = threadIdx.x; e < 49 * P1 * P1; e += blockDim.x) {
+    int c = e / (P1 * P1), r = e % (P1 * P1);
+    int sl = c_slot[c];
+    if (sl >= 0) Ts[sl * P1 * P1 + r] = Tfree[e];
+  }
+  for (int c = threadIdx.x; c < 49; c += blockDim.x)
+    if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
+  int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
+  for (int e = threadIdx.x; e < kPatchSrc * kPatchSrc * P1; e += blockDim.x) {
+    int sb = e / P1, k = e % P1;
+    int sx = sx0 + sb % kPatchSrc, sy = sy0 + sb / kPatchSrc;
+    cpx<R> v = mk<R>(0, 0);
+    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside)
+      v = M[(size_t)(off + box_morton(sx, sy)) * P1 + k];
+    Mp[e] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = warp & 1, bb = warp >> 1;  // child type handled by this warp
+  // two targets per lane: parents (lane) and (lane + 32) of the 8x8 patch
+  int pxA = px0 + (lane & 7), pyA = py0 + (lane >> 3);
+  int pxB = pxA, pyB = pyA + 4;
+  bool vA = pxA < nparent_side && pyA < nparent_side;
+  bool vB = pxB < nparent_side && pyB < nparent_side;
+  int txA = 2 * pxA + a, tyA = 2 * pyA + bb, txB = 2 * pxB + a, tyB = 2 * pyB + bb;
+  cpx<R> accA[P1], accB[P1];
+#pragma unroll
+  for (int r = 0; r < P1; ++r) {
+    accA[r] = mk<R>(0, 0);
+    accB[r] = mk<R>(0, 0);
+  }
+  for (int dy = -2 - bb; dy <= 3 - bb; ++dy) {
+    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
+      const cpx<R> *T = Ts + slot * P1 * P1;
+      const cpx<R> *mA = Mp + ((tyA + dy - sy0) * kPatchSrc + (txA + dx - sx0)) * P1;
+      const cpx<R> *mB = Mp + ((tyB + dy - sy0) * kPatchSrc + (txB + dx - sx0)) * P1;
+#pragma unroll 2
+      for (int k = 0; k < P1; ++k) {
+        cpx<R> ma = mA[k], mb = mB[k];
+#pragma unroll
+        for (int r = 0; r < P1; ++r) {
+          cpx<R> t = T[r * P1 + k];
+          cfma(accA[r], t, ma);
+          cfma(accB[r], t, mb);
+        }
+      }
+      R lgc = lg[slot];
+      accA[0].x += mA[0].x * lgc;  // M_0 ln|t d| (Re L_0 only)
+      accB[0].x += mB[0].x * lgc;
+    }
+  }
+  const R s = (R)(-0.5 / HP_TWO_PI);
+  if (vA) {
+    size_t e0 = (size_t)(off + box_morton(txA, tyA)) * P1;
+#pragma unroll
+    for (int r = 0; r < P1; ++r) {
+      cpx<R> v = s * accA[r];
+      A[e0 + r] = v;
+      B[e0 + r] = conj(v);
+    }
+  }
+  if (vB) {
+    size_t e0 = (size_t)(off + box_morton(txB, tyB)) * P1;
+#pragma unroll
+    for (int r = 0; r < P1; ++r) {
+      cpx<R> v = s * accB[r];
+      A[e0 + r] = v;
+      B[e0 + r] = conj(v);
+    }
+  }
+}
+
+template <typename R, int P1>
+size_t patch_smem() {
+  return sizeof(cpx<R>) * (40 * P1 * P1 + kPatchSrc * kPatchSrc * P1) + sizeof(R) * 40;
+}
+
+int patch_blocks(int H) {
+  int nb = 0;
+  for (int l = 2; l <= H; ++l) {
+    int np = (1 << (l - 1)) / kPatch;
+    np = np < 1 ? 1 : np;
+    nb += np * np;
+  }
+  return nb;
+}
+
+// dispatch on the (compile-time) order; returns false when no patch kernel
+// exists for this order / precision or it does not fit in shared memory
+template <typename R>
+bool launch_m2l_patch(int p, int H, double side, const cpx<R> *Tfree, const cd *logt,
+                      const cpx<R> *M, cpx<R> *A, cpx<R> *B, cudaStream_t st) {
+  int nb = patch_blocks(H);
+#define HP_PATCH_CASE(PP)                                                                 \
+  case PP: {                                                                              \
+    size_t sm = patch_smem<R, PP + 1>();                                                  \
+    if (sm > 227 * 1024) return false;                                                    \
+    if (cudaFuncSetAttribute(k_m2l_free_patch<R, PP + 1>,                                 \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=     \
+        cudaSuccess) {                                                                    \
+      cudaGetLastError();                                                                 \
+      return false;                                                                       \
+    }                                                                                     \
+    k_m2l_free_patch<R, PP + 1><<<nb, 128, sm, st>>>(H, side, Tfree, logt, M, A, B);      \
+    return true;                                                                          \
+  }
+  switch (p) {
+    HP_PATCH_CASE(4) HP_PATCH_CASE(6) HP_PATCH_CASE(8) HP_PATCH_CASE(10) HP_PATCH_CASE(12)
+    HP_PATCH_CASE(14) HP_PATCH_CASE(16) HP_PATCH_CASE(18) HP_PATCH_CASE(20)
+    default: return false;
+  }
+#undef HP_PATCH_CASE
 }
 
 // --------------------------------------------------------------------------
@@ -272,10 +426,10 @@ k_m2l_mirror(int l, int p, double logd, const cpx<R> *__restrict__ Timg,
           cfma(sC, Tp[n * P1 + k], mc);
           cfma(sD, Tm[n * P1 + k], mk_);
         }
-        if (n == 0) {  // log(t d) M_0 term of the image log expansion
+        if (n == 0) {  // log|t d| M_0 term of the image log expansion (Re only)
           cd lt = logimg[cls];
           R m0 = ms[0].x;
-          sL = sL + mk<R>(m0 * (R)(lt.x + logd), m0 * (R)lt.y);
+          sL.x += m0 * (R)(lt.x + logd);
         }
         if (n == lane) { aL0 = aL0 + sL; aC0 = aC0 + sC; aD0 = aD0 + sD; }
         else { aL1 = aL1 + sL; aC1 = aC1 + sC; aD1 = aD1 + sD; }
@@ -292,6 +446,94 @@ k_m2l_mirror(int l, int p, double logd, const cpx<R> *__restrict__ Timg,
     cpx<R> va = L + C, vb = conj(L) + D;
     size_t e = (size_t)m * P1 + n;
     if (accumulate) {
+      A[e] = A[e] + va;
+      B[e] = B[e] + vb;
+    } else {
+      A[e] = va;
+      B[e] = vb;
+    }
+  }
+}
+
+// All-levels form of the mirror M2L: one block of 4 warps per target box of
+// rows 0 and 1 of every level 1..H; the warps split the (at most 12) sources
+// of the mirror list, lanes run over the output index, and the four partial
+// sums are reduced in shared memory.  Level 1 initialises A and B, deeper
+// levels add to the free-space result.
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_m2l_mirror_all(int H, int p, double side, const cpx<R> *__restrict__ Timg,
+                 const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
+                 const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
+  extern __shared__ unsigned char smem_raw[];
+  const int P1 = p + 1;
+  cpx<R> *red = reinterpret_cast<cpx<R> *>(smem_raw);  // [4 warps][3][P1]
+  cpx<R> *msh = red + 4 * 3 * P1;                      // [4 warps][P1]
+  int t = blockIdx.x, l = 1;
+  for (; l <= H; ++l) {
+    if (t < (2 << l)) break;
+    t -= 2 << l;
+  }
+  const int nx = 1 << l;
+  const int ixt = t % nx, iyt = t / nx, px = ixt >> 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t off = level_offset(l);
+  const R logd = (R)log(side / (double)nx);
+  cpx<R> *ms = msh + warp * P1;
+  cpx<R> aL[2], aC[2], aD[2];
+  for (int r = 0; r < 2; ++r) aL[r] = aC[r] = aD[r] = mk<R>(0, 0);
+  // enumerate the mirror list; source number j goes to warp j % 4
+  int j = 0;
+  for (int iys = 0; iys <= 1; ++iys) {
+    for (int ixs = 2 * (px - 1); ixs <= 2 * (px + 1) + 1; ++ixs) {
+      if (ixs < 0 || ixs >= nx) continue;
+      if (iyt == 0 && iys == 0 && abs(ixs - ixt) <= 1) continue;
+      if ((j++ & 3) != warp) continue;
+      const int dx = ixs - ixt, ysum = iyt + iys + 1;
+      const int cls = (ysum - 1) * 7 + (dx + 3);
+      const cpx<R> *src = M + (size_t)(off + box_morton(ixs, iys)) * P1;
+      __syncwarp();
+      for (int k = lane; k < P1; k += 32) ms[k] = src[k];
+      __syncwarp();
+      const cpx<R> *Ti = Timg + (size_t)cls * P1 * P1;
+      const cpx<R> *Tp = Treact + ((size_t)((l - 1) * 21 + cls) * 2 + 0) * P1 * P1;
+      const cpx<R> *Tm = Tp + (size_t)P1 * P1;
+      int r = 0;
+      for (int n = lane; n < P1; n += 32, ++r) {
+        cpx<R> sL = mk<R>(0, 0), sC = mk<R>(0, 0), sD = mk<R>(0, 0);
+        for (int k = 0; k < P1; ++k) {
+          cpx<R> mv = ms[k], mc = conj(mv);
+          cfma(sL, Ti[n * P1 + k], mc);
+          cfma(sC, Tp[n * P1 + k], mc);
+          cfma(sD, Tm[n * P1 + k], mv);
+        }
+        if (n == 0) sL.x += ms[0].x * ((R)logimg[cls].x + logd);  // M_0 ln|t d|
+        aL[r] = aL[r] + sL;
+        aC[r] = aC[r] + sC;
+        aD[r] = aD[r] + sD;
+      }
+    }
+  }
+  int r = 0;
+  for (int n = lane; n < P1; n += 32, ++r) {
+    red[(warp * 3 + 0) * P1 + n] = aL[r];
+    red[(warp * 3 + 1) * P1 + n] = aC[r];
+    red[(warp * 3 + 2) * P1 + n] = aD[r];
+  }
+  __syncthreads();
+  const R sc = (R)(0.5 / HP_TWO_PI);
+  const int64_t m = off + box_morton(ixt, iyt);
+  for (int n = threadIdx.x; n < P1; n += blockDim.x) {
+    cpx<R> L = mk<R>(0, 0), C = mk<R>(0, 0), D = mk<R>(0, 0);
+    for (int w = 0; w < 4; ++w) {
+      L = L + red[(w * 3 + 0) * P1 + n];
+      C = C + red[(w * 3 + 1) * P1 + n];
+      D = D + red[(w * 3 + 2) * P1 + n];
+    }
+    L = sc * L;
+    const cpx<R> va = L + C, vb = conj(L) + D;
+    const size_t e = (size_t)m * P1 + n;
+    if (l >= 2) {
       A[e] = A[e] + va;
       B[e] = B[e] + vb;
     } else {
@@ -555,6 +797,223 @@ k_eval32(const float2 *__restrict__ loc, const float *__restrict__ qs,
   }
 }
 
+// Single-precision leaf evaluation, lane-grouped.  A warp owns one target
+// leaf.  Its targets are spread over groups of gs = 32, 16, 8 or 4 lanes
+// (the smallest power of two >= the leaf size, at least 4): each group holds
+// all the targets of the current chunk, the 32/gs groups take interleaved
+// source subsets, and the partial sums are combined by shuffles.  Sources of
+// the 3x3 neighbourhood are staged in per-warp shared memory in batches,
+// with coordinates already shifted to the target leaf's frame.  The free part
+// skips coincident positions (r^2 = 0), i.e. the j = i pair.
+constexpr int kEvWarps = 8;
+constexpr int kEvBuf = 256;
+
+struct NearAcc {
+  float lf, gx, gy;                 // free: sum q log2 r^2, sum q (dx, dy) / r^2
+  float li, gix, giy;               // image
+  cf ur, grx, gry;                  // reaction, single-precision pairs
+  cd ur64, grx64, gry64;            // reaction, double-precision pairs
+};
+
+__device__ __forceinline__ void free_batch(const float4 *buf, int cnt, int g, int ng, float mx,
+                                           float my, NearAcc &a) {
+  float lf = 0.f, gx = 0.f, gy = 0.f;
+#pragma unroll 4
+  for (int k = g; k < cnt; k += ng) {
+    float4 s = buf[k];
+    float dx = mx - s.x, dy = my - s.y;
+    float r2 = fmaf(dx, dx, dy * dy);
+    bool ok = r2 > 0.f;
+    float q = ok ? s.z : 0.f;
+    r2 = ok ? r2 : 1.f;
+    float qi = q * fast_rcp(r2);
+    lf = fmaf(q, __log2f(r2), lf);
+    gx = fmaf(qi, dx, gx);
+    gy = fmaf(qi, dy, gy);
+  }
+  a.lf += lf;
+  a.gx += gx;
+  a.gy += gy;
+}
+
+__device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, int ng, float mx,
+                                             float my, float d, cf kap, cd kappa, float tau,
+                                             NearAcc &a) {
+  for (int k = g; k < cnt; k += ng) {
+    float4 s = buf[k];
+    float dx = mx - s.x;
+    // bottom row: leaf centres at y = d/2, so Y = y_i + y_j = ly + sy + d
+    float Y = my + s.y + d;
+    float R2 = fmaf(dx, dx, Y * Y);
+    float qi = s.z * fast_rcp(R2);
+    a.li = fmaf(s.z, __log2f(R2), a.li);
+    a.gix = fmaf(qi, dx, a.gix);
+    a.giy = fmaf(qi, Y, a.giy);
+    cf sp_ = mk(Y, -dx), sm_ = mk(Y, dx);
+    cf Pp = kap * sp_, Pm = kap * sm_;
+    if (abs2(Pp) <= 1.f && Y >= tau) {
+      cf J0p, J1p, J0m, J1m;
+      j01_f(Pp, J0p, J1p);
+      j01_f(Pm, J0m, J1m);
+      a.ur = a.ur + s.z * (J0p + J0m);
+      cf tp = cdiv(J1p, sp_), tm = cdiv(J1m, sm_);
+      a.grx = a.grx + s.z * mul_i(tp - tm);
+      a.gry = a.gry - s.z * (tp + tm);
+    } else {
+      cd spd = mk((double)Y, -(double)dx), smd = mk((double)Y, (double)dx);
+      cd J0p, J1p, J0m, J1m;
+      j01(kappa * spd, J0p, J1p);
+      j01(kappa * smd, J0m, J1m);
+      double q = s.z;
+      a.ur64 = a.ur64 + q * (J0p + J0m);
+      cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
+      a.grx64 = a.grx64 + q * mul_i(tp - tm);
+      a.gry64 = a.gry64 - q * (tp + tm);
+    }
+  }
+}
+
+__device__ __forceinline__ float xsum(float v, int from) {
+  for (int o = from; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double xsumd(double v, int from) {
+  for (int o = from; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kEvWarps * 32)
+k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
+          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
+          double side, int p, cd kappa, float tau, const cf *__restrict__ A,
+          const cf *__restrict__ B, double *__restrict__ pot, double *__restrict__ grad) {
+  __shared__ float4 sbuf[kEvWarps][kEvBuf];
+  const int P1 = p + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int leaf = blockIdx.x * kEvWarps + warp;
+  const int nx = 1 << H;
+  if (leaf >= nx * nx) return;
+  float4 *buf = sbuf[warp];
+  const int ix = box_ix(leaf), iy = box_iy(leaf);
+  const float d = (float)(side / (double)nx);
+  const float invd = (float)((double)nx / side);
+  const cf kap = mk((float)kappa.x, (float)kappa.y);
+  const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+  const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  const int T = b1 - b0;
+  const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
+  const int ng = 32 / gs, g = lane / gs, tl = lane % gs;
+  for (int tb = b0; tb < b1; tb += gs) {
+    const int i = tb + tl;
+    const bool act = i < b1;
+    const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+    NearAcc acc;
+    acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
+    acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
+    acc.ur64 = acc.grx64 = acc.gry64 = mk(0.0, 0.0);
+    // free part over the 3x3 neighbourhood
+    int fill = 0;
+    for (int ny = iy - 1; ny <= iy + 1; ++ny) {
+      if (ny < 0 || ny >= nx) continue;
+      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
+        if (mxx < 0 || mxx >= nx) continue;
+        const uint64_t sl = box_morton(mxx, ny);
+        const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+        const float ox = (float)(mxx - ix) * d, oy = (float)(ny - iy) * d;
+        for (int sb = s0; sb < s1; sb += 32) {
+          const int cnt = min(32, s1 - sb);
+          if (fill + cnt > kEvBuf) {
+            __syncwarp();
+            free_batch(buf, fill, g, ng, me.x, me.y, acc);
+            __syncwarp();
+            fill = 0;
+          }
+          if (lane < cnt) {
+            const float2 v = loc[sb + lane];
+            buf[fill + lane] = make_float4(v.x + ox, v.y + oy, qs[sb + lane], 0.f);
+          }
+          fill += cnt;
+        }
+      }
+    }
+    __syncwarp();
+    free_batch(buf, fill, g, ng, me.x, me.y, acc);
+    // image and reaction parts over the bottom-row neighbours
+    if (iy == 0) {
+      fill = 0;
+      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
+        if (mxx < 0 || mxx >= nx) continue;
+        const uint64_t sl = box_morton(mxx, 0);
+        const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+        const float ox = (float)(mxx - ix) * d;
+        for (int sb = s0; sb < s1; sb += 32) {
+          const int cnt = min(32, s1 - sb);
+          if (fill + cnt > kEvBuf) {
+            __syncwarp();
+            mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
+            __syncwarp();
+            fill = 0;
+          }
+          __syncwarp();
+          if (lane < cnt) {
+            const float2 v = loc[sb + lane];
+            buf[fill + lane] = make_float4(v.x + ox, v.y, qs[sb + lane], 0.f);
+          }
+          fill += cnt;
+        }
+      }
+      __syncwarp();
+      mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
+    }
+    __syncwarp();
+    // combine the groups
+    acc.lf = xsum(acc.lf, gs);
+    acc.gx = xsum(acc.gx, gs);
+    acc.gy = xsum(acc.gy, gs);
+    if (iy == 0) {
+      acc.li = xsum(acc.li, gs);
+      acc.gix = xsum(acc.gix, gs);
+      acc.giy = xsum(acc.giy, gs);
+      acc.ur.x = xsum(acc.ur.x, gs); acc.ur.y = xsum(acc.ur.y, gs);
+      acc.grx.x = xsum(acc.grx.x, gs); acc.grx.y = xsum(acc.grx.y, gs);
+      acc.gry.x = xsum(acc.gry.x, gs); acc.gry.y = xsum(acc.gry.y, gs);
+      acc.ur64.x = xsumd(acc.ur64.x, gs); acc.ur64.y = xsumd(acc.ur64.y, gs);
+      acc.grx64.x = xsumd(acc.grx64.x, gs); acc.grx64.y = xsumd(acc.grx64.y, gs);
+      acc.gry64.x = xsumd(acc.gry64.x, gs); acc.gry64.y = xsumd(acc.gry64.y, gs);
+    }
+    if (!act || g != 0) continue;
+    // L2P (Eq. truncatedLE for the reaction parts, the log expansions for the
+    // free and image parts): Horner for value and derivative in w, conj(w)
+    cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
+    cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
+    for (int n = p - 1; n >= 0; --n) {
+      da = da * w + va;
+      va = va * w + Al[n];
+      db = db * wb + vb;
+      vb = vb * wb + Bl[n];
+    }
+    const double c4 = 0.69314718055994530942 / (4.0 * HP_PI), i2pi = 1.0 / HP_TWO_PI;
+    cd u = mk((double)va.x + vb.x + ((double)acc.li - acc.lf) * c4 +
+                  ((double)acc.ur.x + acc.ur64.x) * i2pi,
+              (double)va.y + vb.y + ((double)acc.ur.y + acc.ur64.y) * i2pi);
+    cd ga = mk((double)da.x, (double)da.y), gb = mk((double)db.x, (double)db.y);
+    const double id = (double)invd;
+    cd gx = id * (ga + gb), gy = id * (mul_i(ga) - mul_i(gb));
+    gx = gx + mk(((double)acc.gix - acc.gx + acc.grx.x + acc.grx64.x) * i2pi,
+                 ((double)acc.grx.y + acc.grx64.y) * i2pi);
+    gy = gy + mk(((double)acc.giy - acc.gy + acc.gry.x + acc.gry64.x) * i2pi,
+                 ((double)acc.gry.y + acc.gry64.y) * i2pi);
+    const int64_t o = perm[i];
+    reinterpret_cast<double2 *>(pot)[o] = make_double2(u.x, u.y);
+    if (grad) {
+      double4 gv;
+      gv.x = gx.x; gv.y = gx.y; gv.z = gy.x; gv.w = gy.y;
+      reinterpret_cast<double4 *>(grad)[o] = gv;
+    }
+  }
+}
+
 inline unsigned cdiv_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 template <typename R>
@@ -602,19 +1061,29 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
   size_t shmir = sizeof(cpx<R>) * P1 * kWarpsPerBlock;
+  bool patched = false;
+  if (H >= 2 && sizeof(R) == 4) {
+    pass_begin(pl, st, PASS_M2L_FREE);
+    patched = launch_m2l_patch<R>(p, H, pl->side, Tfree, logs, M, A, B, st);
+    pass_end(pl, st, PASS_M2L_FREE, patched ? 1 : 0);
+  }
   for (int l = 1; l <= H; ++l) {
     double logd = log(pl->side / (double)(1 << l));
-    if (l >= 2) {
+    if (l >= 2 && !patched) {
       dim3 g(cdiv_u(int64_t(1) << (2 * (l - 1)), 32), 4);
       pass_begin(pl, st, PASS_M2L_FREE);
       k_m2l_free<R><<<g, 128, shfree, st>>>(l, p, logd, Tfree, logs, M, A, B);
       pass_end(pl, st, PASS_M2L_FREE, 1);
     }
-    pass_begin(pl, st, PASS_M2L_MIRROR);
-    k_m2l_mirror<R><<<cdiv_u(2 << l, kWarpsPerBlock), 32 * kWarpsPerBlock, shmir, st>>>(
-        l, p, logd, Timg, logs + 49, Treact, M, A, B, l >= 2 ? 1 : 0);
-    pass_end(pl, st, PASS_M2L_MIRROR, 1);
   }
+  // the mirror M2L of all levels, after the free-space M2L it adds to
+  pass_begin(pl, st, PASS_M2L_MIRROR);
+  {
+    unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
+    size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
+    k_m2l_mirror_all<R><<<nb, 128, sm, st>>>(H, p, pl->side, Timg, logs + 49, Treact, M, A, B);
+  }
+  pass_end(pl, st, PASS_M2L_MIRROR, 1);
   pass_begin(pl, st, PASS_L2L);
   for (int l = 2; l <= H; ++l)
     k_l2l<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
@@ -629,7 +1098,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         kappa, (const cd *)A, (const cd *)B, pot, grad);
   } else {
     float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
-    k_eval32<<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
+    k_eval32g<<<cdiv_u(pl->nleaf, kEvWarps), 32 * kEvWarps, 0, st>>>(
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p, kappa, tau,
         (const cf *)A, (const cf *)B, pot, grad);
   }
@@ -648,6 +1117,13 @@ size_t fmm_shared_bytes_max(int p, bool fp64) {
 }
 
 hpfmm_status fmm_set_smem_limits(int p) {
+  signed char slot[49];
+  int k = 0;
+  for (int c = 0; c < 49; ++c) {
+    int dx = c % 7 - 3, dy = c / 7 - 3;
+    slot[c] = (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) ? -1 : (signed char)k++;
+  }
+  HP_CUDA(cudaMemcpyToSymbol(c_slot, slot, sizeof slot));
   size_t s64 = fmm_shared_bytes_max(p, true), s32 = fmm_shared_bytes_max(p, false);
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));

@@ -43,6 +43,19 @@ __host__ __device__ inline double binom(int n, int k) {
   return r;
 }
 
+// C(a, b) for 0 <= b <= a < nb (row-major nb x nb), by Pascal's rule per row
+__global__ void k_binom(int nb, double *C) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int a = 0; a < nb; ++a) {
+    for (int b = 0; b < nb; ++b) {
+      double v = 0.0;
+      if (b == 0 || b == a) v = 1.0;
+      else if (b < a) v = C[(a - 1) * nb + b - 1] + C[(a - 1) * nb + b];
+      C[a * nb + b] = v;
+    }
+  }
+}
+
 __global__ void k_m2m_l2l(int p, cd *m2m, cd *l2l) {
   int c = blockIdx.x;  // child quadrant
   int P1 = p + 1;
@@ -107,7 +120,8 @@ __global__ void k_img_m2l(int p, cd *T, cd *logt) {
 }
 
 // reaction M2L matrices, block = (level, class, sign); Tp/Tm: [level][cls][n][m]
-__global__ void k_reaction_m2l(int p, int H, double side, cd kappa, cd *Tr) {
+__global__ void k_reaction_m2l(int p, int H, double side, cd kappa, const double *__restrict__ Cb,
+                               cd *Tr) {
   extern __shared__ cd sh[];
   int P1 = p + 1, K = 2 * p;
   int b = blockIdx.x;
@@ -135,7 +149,7 @@ __global__ void k_reaction_m2l(int p, int H, double side, cd kappa, cd *Tr) {
   cd *out = Tr + ((size_t)((lev - 1) * 21 + cls) * 2 + sign) * P1 * P1;
   for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) {
     int n = e / P1, m = e % P1;
-    cd v = binom(n + m, m) * h[n + m];
+    cd v = Cb[(n + m) * (2 * p + 2) + m] * h[n + m];
     int ph = sign ? (m - n) : (n - m);  // i^{ph}
     ph &= 3;
     for (int r = 0; r < ph; ++r) v = mul_i(v);
@@ -153,28 +167,45 @@ __global__ void k_to_float(const cd *a, cf *b, size_t n) {
 
 // Table layout inside pl->t_* (double complex unless prec != FP64, then the
 // FP32 copies live right after the double block of the same allocation).
-hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
-  int p = pl->p, P1 = p + 1, H = pl->H;
+// Static tables depend on p only (created once per plan); the reaction tables
+// depend on kappa and the box sides (rebuilt with the tree).
+hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
+  int p = pl->p, P1 = p + 1;
   size_t m2 = (size_t)P1 * P1;
   cd *m2m = (cd *)pl->t_m2m, *l2l = (cd *)pl->t_l2l, *fm2l = (cd *)pl->t_m2l;
-  cd *img = (cd *)pl->t_rlog, *rea = (cd *)pl->t_refl;
+  cd *img = (cd *)pl->t_rlog;
   cd *logs = (cd *)pl->t_rlog0;  // 49 free + 21 image logs
-  pass_begin(pl, st, PASS_TABLES);
+  k_binom<<<1, 32, 0, st>>>(2 * p + 2, pl->t_binom);
   k_m2m_l2l<<<4, 256, 0, st>>>(p, m2m, l2l);
   k_free_m2l<<<49, 256, 0, st>>>(p, fm2l, logs);
   k_img_m2l<<<21, 256, 0, st>>>(p, img, logs + 49);
-  size_t shm = sizeof(cd) * 2 * (2 * p + 1);
-  k_reaction_m2l<<<H * 21 * 2, 256, shm, st>>>(p, H, pl->side, mk(pl->kre, pl->kim), rea);
   HP_LAUNCH_CHECK();
   if (pl->prec != HPFMM_FP64) {
-    struct { void *base; size_t n; } t[5] = {{pl->t_m2m, 4 * m2}, {pl->t_l2l, 4 * m2},
-                                               {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2},
-                                               {pl->t_refl, (size_t)H * 42 * m2}};
-    for (auto &e : t) {
+    struct { void *base; size_t n; } t[4] = {{pl->t_m2m, 4 * m2}, {pl->t_l2l, 4 * m2},
+                                               {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2}};
+    for (auto &e : t)
       k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
-    }
     HP_LAUNCH_CHECK();
   }
-  pass_end(pl, st, PASS_TABLES, pl->prec != HPFMM_FP64 ? 9 : 4);
+  return HPFMM_OK;
+}
+
+hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
+  int p = pl->p, P1 = p + 1, H = pl->H;
+  size_t m2 = (size_t)P1 * P1;
+  cd *rea = (cd *)pl->t_refl;
+  pass_begin(pl, st, PASS_TABLES);
+  size_t shm = sizeof(cd) * 2 * (2 * p + 1);
+  k_reaction_m2l<<<H * 21 * 2, 256, shm, st>>>(p, H, pl->side, mk(pl->kre, pl->kim),
+                                                pl->t_binom, rea);
+  HP_LAUNCH_CHECK();
+  int nl = 1;
+  if (pl->prec != HPFMM_FP64) {
+    size_t ne = (size_t)H * 42 * m2;
+    k_to_float<<<256, 256, 0, st>>>((const cd *)rea, (cf *)(rea + ne), ne);
+    HP_LAUNCH_CHECK();
+    nl = 2;
+  }
+  pass_end(pl, st, PASS_TABLES, nl);
   return HPFMM_OK;
 }

@@ -117,37 +117,56 @@ radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, int nblocks,
   counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];  // digit-major
 }
 
-// exclusive scan of m = 256 * nblocks counts, one block of 1024 threads
-__global__ void __launch_bounds__(1024) radix_scan(unsigned *__restrict__ counts, int64_t m) {
-  __shared__ unsigned part[1024];
-  int64_t per = (m + 1023) / 1024;
-  int64_t lo = threadIdx.x * per, hi = min(m, lo + per);
-  unsigned s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += counts[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {  // Hillis-Steele inclusive scan
-    unsigned v = (threadIdx.x >= off) ? part[threadIdx.x - off] : 0u;
+// exclusive scan of the per-block counts of each digit (block d scans row d of
+// the digit-major table in place) and the digit totals
+__global__ void __launch_bounds__(256)
+radix_scan_digit(unsigned *__restrict__ counts, int nblocks, unsigned *__restrict__ totals) {
+  __shared__ unsigned ws[8];
+  unsigned *row = counts + (int64_t)blockIdx.x * nblocks;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned carry = 0;
+  for (int base = 0; base < nblocks; base += 256) {
+    int i = base + threadIdx.x;
+    unsigned v = (i < nblocks) ? row[i] : 0u;
+    unsigned x = v;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
     __syncthreads();
-    part[threadIdx.x] += v;
+    unsigned wpre = 0, tot = 0;
+    for (int w = 0; w < 8; ++w) {
+      if (w < warp) wpre += ws[w];
+      tot += ws[w];
+    }
+    if (i < nblocks) row[i] = carry + wpre + x - v;
+    carry += tot;
     __syncthreads();
   }
-  unsigned run = (threadIdx.x == 0) ? 0u : part[threadIdx.x - 1];
-  for (int64_t i = lo; i < hi; ++i) {
-    unsigned c = counts[i];
-    counts[i] = run;
-    run += c;
-  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
 radix_scatter(const uint64_t *__restrict__ kin, const int *__restrict__ vin, int64_t n, int shift,
-              int nblocks, const unsigned *__restrict__ offs, uint64_t *__restrict__ kout,
-              int *__restrict__ vout) {
+              int nblocks, const unsigned *__restrict__ offs, const unsigned *__restrict__ totals,
+              uint64_t *__restrict__ kout, int *__restrict__ vout) {
   __shared__ unsigned base_off[256];
   __shared__ unsigned whist[kWarps][256];
+  __shared__ unsigned wsum[kWarps];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  base_off[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  {  // digit base = exclusive prefix of the digit totals
+    unsigned t = totals[threadIdx.x], x = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    unsigned pre = 0;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    base_off[threadIdx.x] = pre + x - t + offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  }
   int64_t tile = (int64_t)blockIdx.x * kTile;
   unsigned lt_mask = (1u << lane) - 1u;
   for (int r = 0; r < kSortRounds; ++r) {
@@ -228,9 +247,9 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   unsigned *counts = nullptr;
   int nblocks = (int)((n + kTile - 1) / kTile);
   size_t bytes = sizeof(Geom) * nbR + 4 * sizeof(double) + sizeof(uint64_t) * n +
-                 2 * sizeof(int) * n + sizeof(unsigned) * 256 * (size_t)nblocks;
+                 2 * sizeof(int) * n + sizeof(unsigned) * 256 * ((size_t)nblocks + 1);
   char *tmp = nullptr;
-  HP_CUDA(cudaMallocAsync((void **)&tmp, bytes + 5 * 256, st));
+  HP_CUDA(cudaMallocAsync((void **)&tmp, bytes + 7 * 256, st));
   char *c = tmp;
   auto carve = [&](size_t b) {
     char *r = c;
@@ -243,6 +262,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   va = (int *)carve(sizeof(int) * n);
   vb = (int *)carve(sizeof(int) * n);
   counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)nblocks);
+  unsigned *totals = (unsigned *)carve(sizeof(unsigned) * 256);
 
   hpfmm_status status = HPFMM_OK;
   double hgeo[3];
@@ -273,9 +293,9 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   int *vin = va, *vout = vb;
   for (int shift = 0; shift < 60; shift += 8) {
     radix_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, counts);
-    radix_scan<<<1, 1024, 0, st>>>(counts, (int64_t)256 * nblocks);
-    radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts, kout,
-                                                     vout);
+    radix_scan_digit<<<256, 256, 0, st>>>(counts, nblocks, totals);
+    radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts, totals,
+                                                     kout, vout);
     uint64_t *tk = kin; kin = kout; kout = tk;
     int *tv = vin; vin = vout; vout = tv;
   }
