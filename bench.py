@@ -160,35 +160,63 @@ def leaf_pairs(keys, H):
     return free, mirror
 
 
-def roofline(passes_ms, launches, args, npairs, mpairs, H, peaks, clocks):
-    """Roofline entry for the dominant pass (per-launch algorithmic work /
-    per-launch CUDA-event duration)."""
-    dom = max(passes_ms, key=lambda k: passes_ms[k])
-    nl = max(1, launches.get(dom, 1))
-    t = passes_ms[dom] / 1e3 / nl  # seconds per launch
+def vlist_translations(H):
+    """Exact number of free-space M2L translations on the uniform tree: per box
+    of level l >= 2 and child type (a, b), the offsets (dx, dy) in
+    [-2-a, 3-a] x [-2-b, 3-b] minus the 3x3 near ones, inside the grid."""
+    tot = 0
+    for l in range(2, H + 1):
+        n = 1 << l
+        i = np.arange(n)
+        a = i & 1
+        far = np.zeros(n); near = np.zeros(n)
+        for d in range(-3, 4):
+            ok = (i + d >= 0) & (i + d < n) & (d >= -2 - a) & (d <= 3 - a)
+            far += ok
+            near += ok & (abs(d) <= 1)
+        tot += int(np.sum(np.outer(far, far) - np.outer(near, near)))
+    return tot
+
+
+# kernels that make up a pass with one launch per step (the candidates for the
+# dominant-kernel roofline)
+SINGLE_KERNEL = {"eval": ("k_eval32g", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
+                 "m2l_mirror": ("k_m2l_mirror_all", "k_m2l_mirror_all"),
+                 "p2m": ("k_p2m", "k_p2m"), "near_mirror": ("k_mirror32", None)}
+
+
+def roofline(passes_ms, launches, args, npairs, H, peaks):
+    """Roofline entry for the dominant kernel: the single-kernel pass with the
+    largest device time; achieved = algorithmic work per launch / per-launch
+    CUDA-event duration."""
+    cand = {k: v for k, v in passes_ms.items() if k in SINGLE_KERNEL and launches.get(k, 0) > 0}
+    dom = max(cand, key=lambda k: cand[k])
+    t = passes_ms[dom] / 1e3 / launches[dom]  # seconds per launch
     f_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
     sms = 152
-    if dom == "eval":
-        # SFU (MUFU) bound: lg2 + rcp per free pair and per image pair
-        ops = 2.0 * npairs + 2.0 * mpairs
-        peak = 16 * sms * f_ghz * 1e9 / 1e12  # TOP/s
+    name = SINGLE_KERNEL[dom][0 if args.prec != "fp64" else 1]
+    if dom == "eval" and args.prec != "fp64":
+        # SFU (MUFU) bound: one lg2 and one rcp per free-space near-field pair
+        ops = 2.0 * npairs
+        peak = 16 * sms * f_ghz * 1e9 / 1e12
         achieved = ops / t / 1e12
-        return {"kernel": "k_eval32 (L2P + near field)" if args.prec != "fp64" else "k_eval64",
-                "bound": "alu", "unit": "TOP/s (SFU ops)", "achieved": achieved, "peak": peak,
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "16 SFU ops/clk/SM x 152 SMs x %.0f MHz" % (f_ghz * 1e3),
-                "per_launch_ms": t * 1e3}
+        return {"kernel": name + " (L2P + free-space near field)", "bound": "alu",
+                "unit": "TOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "work": "2 SFU ops (lg2, rcp) per near-field pair, %d pairs"
+                % npairs, "peak_source": "16 SFU ops/clk/SM x 152 SMs x %.0f MHz (nominal)"
+                % (f_ghz * 1e3), "per_launch_ms": t * 1e3}
     if dom == "m2l_free":
         P1 = args.p + 1
-        ntrans = sum(27 * (4 ** (l - 1)) * 4 for l in range(2, H + 1))  # upper bound ~ boxes x 27
-        flops = 8.0 * P1 * P1 * ntrans / max(1, H - 1)
+        ntrans = vlist_translations(H)
+        flops = 8.0 * P1 * P1 * ntrans
         peak = 128 * 2 * sms * f_ghz * 1e9 / 1e12
         achieved = flops / t / 1e12
-        return {"kernel": "k_m2l_free", "bound": "alu", "unit": "TFLOP/s (FP32 FMA pipe)",
-                "achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": None,
-                "peak_source": "128 FMA/clk/SM x 2 x 152 SMs x %.0f MHz" % (f_ghz * 1e3),
-                "per_launch_ms": t * 1e3}
-    return {"kernel": dom, "bound": "alu", "unit": "ms", "achieved": t * 1e3, "peak": None,
+        return {"kernel": name, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
+                "peak": peak, "frac": achieved / peak, "traffic": None,
+                "work": "8 (p+1)^2 flops per V-list translation, %d translations" % ntrans,
+                "peak_source": "FP32 FMA: 128/clk/SM x 2 x 152 SMs x %.0f MHz (nominal)"
+                % (f_ghz * 1e3), "per_launch_ms": t * 1e3}
+    return {"kernel": name, "bound": "alu", "unit": "ms", "achieved": t * 1e3, "peak": None,
             "frac": None, "traffic": None}
 
 
@@ -273,7 +301,7 @@ def run_ours(args):
     npairs, mpairs = leaf_pairs(keys, info["levels"])
     launches_per_step = {k: v / args.steps for k, v in launches.items()}
     pass_ms_step = {k: v / args.steps for k, v in pms.items()}
-    roof = roofline(pms, launches, args, npairs, mpairs, info["levels"], peaks, clocks)
+    roof = roofline(pms, launches, args, npairs, info["levels"], peaks)
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

@@ -164,14 +164,16 @@ hpfmm_status hpfmm_get_order(const hpfmm_plan *plan, uint64_t *keys, int64_t *pe
  * Pass timing.  hpfmm_set_timing(plan, 1) makes the plan record a CUDA event
  * pair on the caller's stream around every pass it launches (tree build,
  * tables, charge gather, P2M, M2M, free M2L, mirror M2L, L2L, leaf
- * evaluation = L2P + near field, in this order of pass ids 0..8).
+ * evaluation = L2P + free-space near field (+ the image and reaction near
+ * field in double precision), image and reaction near field of the
+ * bottom-row leaves (single precision), in this order of pass ids 0..9).
  * hpfmm_read_timing synchronises with that work and returns, per pass, the
  * device milliseconds recorded since the previous read (ms may be NULL) and the
  * number of kernels the plan has launched in that pass since creation
  * (launches may be NULL; counted whether or not timing is on).
  */
 hpfmm_status hpfmm_set_timing(hpfmm_plan *plan, int enable);
-hpfmm_status hpfmm_read_timing(hpfmm_plan *plan, double ms[9], int64_t launches[9]);
+hpfmm_status hpfmm_read_timing(hpfmm_plan *plan, double ms[10], int64_t launches[10]);
 
 /* Wait for the plan's outstanding work on `stream` and report any device-side
  * status (HPFMM_ETIMEOUT) recorded by its kernels. */

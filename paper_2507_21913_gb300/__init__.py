@@ -229,7 +229,8 @@ def hpfmm_get_order(plan):
     return keys, perm
 
 
-PASS_NAMES = ("tree", "tables", "gather", "p2m", "m2m", "m2l_free", "m2l_mirror", "l2l", "eval")
+PASS_NAMES = ("tree", "tables", "gather", "p2m", "m2m", "m2l_free", "m2l_mirror", "l2l", "eval",
+              "near_mirror")
 
 
 def hpfmm_set_timing(plan, enable=True):
@@ -238,8 +239,8 @@ def hpfmm_set_timing(plan, enable=True):
 
 def hpfmm_read_timing(plan):
     """({pass: device ms since the last read}, {pass: kernel launches since creation})."""
-    ms = np.zeros(9)
-    ln = np.zeros(9, np.int64)
+    ms = np.zeros(len(PASS_NAMES))
+    ln = np.zeros(len(PASS_NAMES), np.int64)
     _check(lib().hpfmm_read_timing(plan.handle, ms.ctypes.data, ln.ctypes.data))
     return dict(zip(PASS_NAMES, ms.tolist())), dict(zip(PASS_NAMES, ln.tolist()))
 

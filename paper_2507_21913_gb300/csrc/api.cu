@@ -103,7 +103,7 @@ extern "C" hpfmm_status hpfmm_set_timing(hpfmm_plan *pl, int enable) {
   return HPFMM_OK;
 }
 
-extern "C" hpfmm_status hpfmm_read_timing(hpfmm_plan *pl, double ms[9], int64_t launches[9]) {
+extern "C" hpfmm_status hpfmm_read_timing(hpfmm_plan *pl, double ms[10], int64_t launches[10]) {
   if (!pl) {
     set_last_error("hpfmm_read_timing: null plan");
     return HPFMM_EINVAL;

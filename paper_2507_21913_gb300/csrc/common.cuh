@@ -10,7 +10,7 @@
 #ifndef HPFMM_MAX_P
 #define HPFMM_MAX_P 40
 #endif
-#define HPFMM_NPASS 9
+#define HPFMM_NPASS 10
 
 // ---------------------------------------------------------------------------
 // complex numbers (interleaved re, im)
@@ -173,7 +173,7 @@ struct hpfmm_plan {
 
 // pass ids of hpfmm_read_timing
 enum { PASS_TREE = 0, PASS_TABLES, PASS_GATHER, PASS_P2M, PASS_M2M, PASS_M2L_FREE,
-       PASS_M2L_MIRROR, PASS_L2L, PASS_EVAL };
+       PASS_M2L_MIRROR, PASS_L2L, PASS_EVAL, PASS_NEAR_MIRROR };
 // record the start / end of a pass on stream st (no-ops unless timing is on);
 // pass_end also adds nlaunch to the pass's launch count
 void pass_begin(hpfmm_plan *pl, cudaStream_t st, int pass);

@@ -811,8 +811,7 @@ constexpr int kEvBuf = 256;
 struct NearAcc {
   float lf, gx, gy;                 // free: sum q log2 r^2, sum q (dx, dy) / r^2
   float li, gix, giy;               // image
-  cf ur, grx, gry;                  // reaction, single-precision pairs
-  cd ur64, grx64, gry64;            // reaction, double-precision pairs
+  cf ur, grx, gry;                  // reaction (pairs evaluated in single or double)
 };
 
 __device__ __forceinline__ void free_batch(const float4 *buf, int cnt, int g, int ng, float mx,
@@ -865,24 +864,21 @@ __device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, 
       j01(kappa * spd, J0p, J1p);
       j01(kappa * smd, J0m, J1m);
       double q = s.z;
-      a.ur64 = a.ur64 + q * (J0p + J0m);
       cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
-      a.grx64 = a.grx64 + q * mul_i(tp - tm);
-      a.gry64 = a.gry64 - q * (tp + tm);
+      a.ur = a.ur + to<float>(q * (J0p + J0m));
+      a.grx = a.grx + to<float>(q * mul_i(tp - tm));
+      a.gry = a.gry - to<float>(q * (tp + tm));
     }
   }
 }
 
 __device__ __forceinline__ float xsum(float v, int from) {
-  for (int o = from; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double xsumd(double v, int from) {
+#pragma unroll 1
   for (int o = from; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__global__ void __launch_bounds__(kEvWarps * 32)
+__global__ void __launch_bounds__(kEvWarps * 32, 3)
 k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
           const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
           double side, int p, cd kappa, float tau, const cf *__restrict__ A,
@@ -911,7 +907,6 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
     NearAcc acc;
     acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
     acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
-    acc.ur64 = acc.grx64 = acc.gry64 = mk(0.0, 0.0);
     // free part over the 3x3 neighbourhood
     int fill = 0;
     for (int ny = iy - 1; ny <= iy + 1; ++ny) {
@@ -939,49 +934,11 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
     }
     __syncwarp();
     free_batch(buf, fill, g, ng, me.x, me.y, acc);
-    // image and reaction parts over the bottom-row neighbours
-    if (iy == 0) {
-      fill = 0;
-      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
-        if (mxx < 0 || mxx >= nx) continue;
-        const uint64_t sl = box_morton(mxx, 0);
-        const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-        const float ox = (float)(mxx - ix) * d;
-        for (int sb = s0; sb < s1; sb += 32) {
-          const int cnt = min(32, s1 - sb);
-          if (fill + cnt > kEvBuf) {
-            __syncwarp();
-            mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
-            __syncwarp();
-            fill = 0;
-          }
-          __syncwarp();
-          if (lane < cnt) {
-            const float2 v = loc[sb + lane];
-            buf[fill + lane] = make_float4(v.x + ox, v.y, qs[sb + lane], 0.f);
-          }
-          fill += cnt;
-        }
-      }
-      __syncwarp();
-      mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
-    }
     __syncwarp();
     // combine the groups
     acc.lf = xsum(acc.lf, gs);
     acc.gx = xsum(acc.gx, gs);
     acc.gy = xsum(acc.gy, gs);
-    if (iy == 0) {
-      acc.li = xsum(acc.li, gs);
-      acc.gix = xsum(acc.gix, gs);
-      acc.giy = xsum(acc.giy, gs);
-      acc.ur.x = xsum(acc.ur.x, gs); acc.ur.y = xsum(acc.ur.y, gs);
-      acc.grx.x = xsum(acc.grx.x, gs); acc.grx.y = xsum(acc.grx.y, gs);
-      acc.gry.x = xsum(acc.gry.x, gs); acc.gry.y = xsum(acc.gry.y, gs);
-      acc.ur64.x = xsumd(acc.ur64.x, gs); acc.ur64.y = xsumd(acc.ur64.y, gs);
-      acc.grx64.x = xsumd(acc.grx64.x, gs); acc.grx64.y = xsumd(acc.grx64.y, gs);
-      acc.gry64.x = xsumd(acc.gry64.x, gs); acc.gry64.y = xsumd(acc.gry64.y, gs);
-    }
     if (!act || g != 0) continue;
     // L2P (Eq. truncatedLE for the reaction parts, the log expansions for the
     // free and image parts): Horner for value and derivative in w, conj(w)
@@ -993,23 +950,93 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
       db = db * wb + vb;
       vb = vb * wb + Bl[n];
     }
-    const double c4 = 0.69314718055994530942 / (4.0 * HP_PI), i2pi = 1.0 / HP_TWO_PI;
-    cd u = mk((double)va.x + vb.x + ((double)acc.li - acc.lf) * c4 +
-                  ((double)acc.ur.x + acc.ur64.x) * i2pi,
-              (double)va.y + vb.y + ((double)acc.ur.y + acc.ur64.y) * i2pi);
-    cd ga = mk((double)da.x, (double)da.y), gb = mk((double)db.x, (double)db.y);
-    const double id = (double)invd;
-    cd gx = id * (ga + gb), gy = id * (mul_i(ga) - mul_i(gb));
-    gx = gx + mk(((double)acc.gix - acc.gx + acc.grx.x + acc.grx64.x) * i2pi,
-                 ((double)acc.grx.y + acc.grx64.y) * i2pi);
-    gy = gy + mk(((double)acc.giy - acc.gy + acc.gry.x + acc.gry64.x) * i2pi,
-                 ((double)acc.gry.y + acc.gry64.y) * i2pi);
+    // combine in single precision (the outputs are single-precision results)
+    const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+    const float i2pi = (float)(1.0 / HP_TWO_PI);
+    const float ur_ = va.x + vb.x - acc.lf * c4;
+    const float ui_ = va.y + vb.y;
+    const cf gx = invd * (da + db) + mk(-acc.gx * i2pi, 0.f);
+    const cf gy = invd * (mul_i(da) - mul_i(db)) + mk(-acc.gy * i2pi, 0.f);
+    const cd u = mk((double)ur_, (double)ui_);
     const int64_t o = perm[i];
     reinterpret_cast<double2 *>(pot)[o] = make_double2(u.x, u.y);
     if (grad) {
       double4 gv;
-      gv.x = gx.x; gv.y = gx.y; gv.z = gy.x; gv.w = gy.y;
+      gv.x = (double)gx.x; gv.y = (double)gx.y; gv.z = (double)gy.x; gv.w = (double)gy.y;
       reinterpret_cast<double4 *>(grad)[o] = gv;
+    }
+  }
+}
+
+// Image and reaction near field of the bottom-row leaves (single precision
+// with the double routine for |P| > 1 and, in MIXED mode, below tau), added
+// to the outputs written by k_eval32g.  One warp per bottom-row leaf, the
+// same lane grouping as k_eval32g.
+__global__ void __launch_bounds__(kEvWarps * 32)
+k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
+           const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
+           double side, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad) {
+  __shared__ float4 sbuf[kEvWarps][kEvBuf];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = 1 << H;
+  const int ix = blockIdx.x * kEvWarps + warp;  // leaf (ix, 0)
+  if (ix >= nx) return;
+  float4 *buf = sbuf[warp];
+  const float d = (float)ldexp(side, -H);
+  const cf kap = mk((float)kappa.x, (float)kappa.y);
+  const uint64_t leaf = box_morton(ix, 0);
+  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  const int T = b1 - b0;
+  const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
+  const int ng = 32 / gs, g = lane / gs, tl = lane % gs;
+  for (int tb = b0; tb < b1; tb += gs) {
+    const int i = tb + tl;
+    const bool act = i < b1;
+    const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+    NearAcc acc;
+    acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
+    acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
+    int fill = 0;
+    for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
+      if (mxx < 0 || mxx >= nx) continue;
+      const uint64_t sl = box_morton(mxx, 0);
+      const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+      const float ox = (float)(mxx - ix) * d;
+      for (int sb = s0; sb < s1; sb += 32) {
+        const int cnt = min(32, s1 - sb);
+        if (fill + cnt > kEvBuf) {
+          __syncwarp();
+          mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
+          __syncwarp();
+          fill = 0;
+        }
+        if (lane < cnt) {
+          const float2 v = loc[sb + lane];
+          buf[fill + lane] = make_float4(v.x + ox, v.y, qs[sb + lane], 0.f);
+        }
+        fill += cnt;
+      }
+    }
+    __syncwarp();
+    mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
+    __syncwarp();
+    acc.li = xsum(acc.li, gs);
+    acc.gix = xsum(acc.gix, gs);
+    acc.giy = xsum(acc.giy, gs);
+    acc.ur.x = xsum(acc.ur.x, gs); acc.ur.y = xsum(acc.ur.y, gs);
+    acc.grx.x = xsum(acc.grx.x, gs); acc.grx.y = xsum(acc.grx.y, gs);
+    acc.gry.x = xsum(acc.gry.x, gs); acc.gry.y = xsum(acc.gry.y, gs);
+    if (!act || g != 0) continue;
+    const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+    const float i2pi = (float)(1.0 / HP_TWO_PI);
+    const int64_t o = perm[i];
+    pot[2 * o] += (double)(acc.li * c4 + acc.ur.x * i2pi);
+    pot[2 * o + 1] += (double)(acc.ur.y * i2pi);
+    if (grad) {
+      grad[4 * o + 0] += (double)((acc.gix + acc.grx.x) * i2pi);
+      grad[4 * o + 1] += (double)(acc.grx.y * i2pi);
+      grad[4 * o + 2] += (double)((acc.giy + acc.gry.x) * i2pi);
+      grad[4 * o + 3] += (double)(acc.gry.y * i2pi);
     }
   }
 }
@@ -1101,8 +1128,14 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     k_eval32g<<<cdiv_u(pl->nleaf, kEvWarps), 32 * kEvWarps, 0, st>>>(
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p, kappa, tau,
         (const cf *)A, (const cf *)B, pot, grad);
+    pass_end(pl, st, PASS_EVAL, 1);
+    pass_begin(pl, st, PASS_NEAR_MIRROR);
+    k_mirror32<<<cdiv_u(int64_t(1) << H, kEvWarps), 32 * kEvWarps, 0, st>>>(
+        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, kappa, tau, pot,
+        grad);
+    pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
-  pass_end(pl, st, PASS_EVAL, 1);
+  if (sizeof(R) == 8) pass_end(pl, st, PASS_EVAL, 1);
   HP_LAUNCH_CHECK();
   return HPFMM_OK;
 }

@@ -7,6 +7,7 @@
 // Morton keys (30 bits per axis, bit-exact rule), stable LSD radix sort of
 // (key, index), leaf offsets of the uniform level-H grid, gathers.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -18,6 +19,15 @@ struct Geom {
 };
 
 constexpr int kRedThreads = 256;
+
+// unit in the last place of a positive finite double (its exponent's ulp)
+__device__ __forceinline__ double ulp_of(double s) {
+  s = fabs(s);
+  long long b = __double_as_longlong(s);
+  long long e = (b >> 52) & 0x7ff;
+  if (e <= 52) return 4.9406564584124654e-324 * 2;  // tiny: any positive bound works
+  return __longlong_as_double((e - 52) << 52);
+}
 
 __global__ void bbox_partial(const double *__restrict__ x, const double *__restrict__ y,
                              int64_t n, Geom *__restrict__ part) {
@@ -50,46 +60,204 @@ __global__ void bbox_partial(const double *__restrict__ x, const double *__restr
   if (threadIdx.x == 0) part[blockIdx.x] = Geom{s0[0], s1[0], s2[0], sb[0]};
 }
 
-// final reduction; geo[0] = x0, geo[1] = L (side), ((int*)(geo+2))[0] = bad
-__global__ void bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Geom g{INFINITY, -INFINITY, -INFINITY, 0};
-  for (int b = 0; b < nb; ++b) {
-    g.xmin = fmin(g.xmin, part[b].xmin);
-    g.xmax = fmax(g.xmax, part[b].xmax);
-    g.ymax = fmax(g.ymax, part[b].ymax);
-    g.bad |= part[b].bad;
+// final reduction (one block); geo[0] = x0, geo[1] = L (side), geo[2] = bad
+// flag, geo[3] = 2^30 / L rounded (the fast-path quantisation scale)
+__global__ void __launch_bounds__(kRedThreads)
+bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo) {
+  __shared__ double s0[kRedThreads], s1[kRedThreads], s2[kRedThreads];
+  __shared__ int sb[kRedThreads];
+  double xmn = INFINITY, xmx = -INFINITY, ymx = -INFINITY;
+  int bad = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    xmn = fmin(xmn, part[b].xmin);
+    xmx = fmax(xmx, part[b].xmax);
+    ymx = fmax(ymx, part[b].ymax);
+    bad |= part[b].bad;
   }
-  double w = __dsub_rn(g.xmax, g.xmin);
-  double L = (w > g.ymax) ? w : g.ymax;
+  s0[threadIdx.x] = xmn;
+  s1[threadIdx.x] = xmx;
+  s2[threadIdx.x] = ymx;
+  sb[threadIdx.x] = bad;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s0[threadIdx.x] = fmin(s0[threadIdx.x], s0[threadIdx.x + w]);
+      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + w]);
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+      sb[threadIdx.x] |= sb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double w = __dsub_rn(s1[0], s0[0]);
+  double L = (w > s2[0]) ? w : s2[0];
   L = __dmul_rn(L, 1.0 + 0x1p-40);
-  geo[0] = g.xmin;
+  geo[0] = s0[0];
   geo[1] = L;
-  geo[2] = g.bad ? 1.0 : 0.0;
+  geo[2] = sb[0] ? 1.0 : 0.0;
+  geo[3] = __ddiv_rn(1073741824.0, L);
 }
 
-// ix = min(floor((x - x0) / L * 2^30), 2^30 - 1), every operation correctly
-// rounded and uncontracted so that the result matches a plain IEEE host
-// computation bit for bit
-__device__ __forceinline__ uint64_t quantise(double v, double L) {
-  double q = __ddiv_rn(v, L);
-  double s = __dmul_rn(q, 1073741824.0);
+// ix = min(floor((x - x0) / L * 2^30), 2^30 - 1) with the quotient correctly
+// rounded, so that the key matches a plain IEEE host computation bit for bit.
+// Fast path: s' = v * RN(2^30 / L) is within 2 ulp of the exact scaled
+// quotient, and the correctly rounded RN(v / L) * 2^30 is within 1/2 ulp of
+// it; when no integer lies within 4 ulp of s', both floors agree.  Otherwise
+// (a fraction ~1e-7 of the points) the exact division decides.
+__device__ __forceinline__ uint64_t quantise(double v, double L, double scale) {
+  double s = __dmul_rn(v, scale);
+  double u = 4.0 * ulp_of(s);
   double f = floor(s);
+  if (!(floor(s - u) == f && floor(s + u) == f)) {
+    double q = __ddiv_rn(v, L);
+    f = floor(__dmul_rn(q, 1073741824.0));
+  }
   f = fmax(f, 0.0);
   f = fmin(f, 1073741823.0);
   return (uint64_t)f;
 }
 
+// keys, and the point count of each level-H leaf (the atomic's return value
+// is the point's slot inside its leaf bucket; the order within a bucket is
+// fixed later by the per-leaf sort)
 __global__ void morton_keys(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
-                            const double *__restrict__ geo, uint64_t *__restrict__ keys,
-                            int *__restrict__ idx) {
+                            const double *__restrict__ geo, int H, uint64_t *__restrict__ keys,
+                            int *__restrict__ idx, int *__restrict__ leaf_count,
+                            int *__restrict__ slot) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double x0 = geo[0], L = geo[1];
-  uint64_t ix = quantise(__dsub_rn(x[i], x0), L);
-  uint64_t iy = quantise(y[i], L);
-  keys[i] = spread1((uint32_t)ix) | (spread1((uint32_t)iy) << 1);
+  double x0 = geo[0], L = geo[1], sc = geo[3];
+  uint64_t ix = quantise(__dsub_rn(x[i], x0), L, sc);
+  uint64_t iy = quantise(y[i], L, sc);
+  uint64_t k = spread1((uint32_t)ix) | (spread1((uint32_t)iy) << 1);
+  keys[i] = k;
   idx[i] = (int)i;
+  if (leaf_count) slot[i] = atomicAdd(&leaf_count[k >> (60 - 2 * H)], 1);
+}
+
+// exclusive scan of the leaf counts into leaf_start (single block, chunked),
+// and the largest leaf
+__global__ void __launch_bounds__(1024)
+scan_leaves(const int *__restrict__ count, int nleaf, int *__restrict__ start,
+            int *__restrict__ maxleaf) {
+  __shared__ int ws[32];
+  __shared__ int wm[32];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int carry = 0, mx = 0;
+  for (int base = 0; base < nleaf; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = (i < nleaf) ? count[i] : 0;
+    mx = max(mx, v);
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    int wpre = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) wpre += ws[w];
+      tot += ws[w];
+    }
+    if (i < nleaf) start[i] = carry + wpre + x - v;
+    carry += tot;
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) wm[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < 32; ++w) m = max(m, wm[w]);
+    start[nleaf] = carry;
+    *maxleaf = m;
+  }
+}
+
+__global__ void bucket_scatter(const uint64_t *__restrict__ keys, const int *__restrict__ slot,
+                               int64_t n, int H, const int *__restrict__ start,
+                               uint64_t *__restrict__ kout, int *__restrict__ vout) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t k = keys[i];
+  int pos = start[k >> (60 - 2 * H)] + slot[i];
+  kout[pos] = k;
+  vout[pos] = (int)i;
+}
+
+// sort the leaf buckets of at most 32 points by (key, index): one warp per
+// leaf, one element per lane, bitonic network over shuffles
+__global__ void __launch_bounds__(256)
+leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
+               int *__restrict__ vals) {
+  int lane = threadIdx.x & 31;
+  int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (leaf >= nleaf) return;
+  int b0 = start[leaf], m = start[leaf + 1] - b0;
+  if (m <= 1 || m > 32) return;
+  uint64_t k = lane < m ? keys[b0 + lane] : ~0ull;
+  int v = lane < m ? vals[b0 + lane] : 0x7fffffff;
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      uint64_t ok = __shfl_xor_sync(0xffffffffu, k, j);
+      int ov = __shfl_xor_sync(0xffffffffu, v, j);
+      bool self_less = k < ok || (k == ok && v < ov);
+      bool want_min = ((lane & j) == 0) == ((lane & kk) == 0);
+      if (want_min != self_less) {
+        k = ok;
+        v = ov;
+      }
+    }
+  }
+  if (lane < m) {
+    keys[b0 + lane] = k;
+    vals[b0 + lane] = v;
+  }
+}
+
+// sort the leaf buckets of 33..kLeafSort points: bitonic sort in shared
+// memory, one block per leaf (blocks skip the small leaves)
+constexpr int kLeafSort = 1024;
+__global__ void __launch_bounds__(256)
+leaf_sort(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
+          int *__restrict__ vals) {
+  __shared__ uint64_t sk[kLeafSort];
+  __shared__ int sv[kLeafSort];
+  for (int leaf = blockIdx.x; leaf < nleaf; leaf += gridDim.x) {
+    int b0 = start[leaf], b1 = start[leaf + 1], m = b1 - b0;
+    if (m <= 32 || m > kLeafSort) continue;
+    int np2 = 1;
+    while (np2 < m) np2 <<= 1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+      sk[e] = e < m ? keys[b0 + e] : ~0ull;
+      sv[e] = e < m ? vals[b0 + e] : 0x7fffffff;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= np2; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+          int o = e ^ j;
+          if (o > e) {
+            bool up = (e & kk) == 0;
+            uint64_t ka = sk[e], kb = sk[o];
+            int va = sv[e], vb = sv[o];
+            bool gt = ka > kb || (ka == kb && va > vb);
+            if (gt == up) {
+              sk[e] = kb; sk[o] = ka;
+              sv[e] = vb; sv[o] = va;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+      keys[b0 + e] = sk[e];
+      vals[b0 + e] = sv[e];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -225,7 +393,7 @@ __global__ void gather_points(const double *__restrict__ x, const double *__rest
   perm[k] = j;
   if (loc32) {
     uint64_t leaf = keys[k] >> (60 - 2 * H);
-    double d = geo[1] / (double)(1 << H);
+    double d = ldexp(geo[1], -H);  // exact
     double cx = geo[0] + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
     loc32[k] = make_float2((float)(a - cx), (float)(b - cy));
   }
@@ -236,40 +404,49 @@ __global__ void gather_points(const double *__restrict__ x, const double *__rest
 // Build (or rebuild) the tree of pl for the n points (x, y) (device pointers).
 // Leaves pl->xs, ys, perm, keys, leaf_start, loc32 filled and pl->x0, side set;
 // returns EINVAL (synchronously) for non-finite input or y <= 0.
+//
+// Order: keys and leaf counts -> leaf offsets (scan) -> points bucketed by leaf
+// -> each bucket sorted by (key, index).  The result is the stable order by
+// (key, index) over all points.  When some leaf holds more than kLeafSort
+// points the full LSD radix sort of (key, index) is used instead.
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
   const int64_t n = pl->n;
+  const int H = pl->H, nleaf = pl->nleaf;
   int64_t nbR64 = (n + kRedThreads - 1) / kRedThreads;
   int nbR = nbR64 < 1024 ? (int)nbR64 : 1024;
-  Geom *part = nullptr;
-  double *geo = nullptr;
-  uint64_t *kb = nullptr;
-  int *va = nullptr, *vb = nullptr;
-  unsigned *counts = nullptr;
   int nblocks = (int)((n + kTile - 1) / kTile);
   size_t bytes = sizeof(Geom) * nbR + 4 * sizeof(double) + sizeof(uint64_t) * n +
-                 2 * sizeof(int) * n + sizeof(unsigned) * 256 * ((size_t)nblocks + 1);
+                 3 * sizeof(int) * n + sizeof(int) * ((size_t)nleaf + 1) +
+                 sizeof(unsigned) * 256 * ((size_t)nblocks + 1);
   char *tmp = nullptr;
-  HP_CUDA(cudaMallocAsync((void **)&tmp, bytes + 7 * 256, st));
+  HP_CUDA(cudaMallocAsync((void **)&tmp, bytes + 10 * 256, st));
   char *c = tmp;
   auto carve = [&](size_t b) {
     char *r = c;
     c += (b + 255) & ~size_t(255);
     return r;
   };
-  part = (Geom *)carve(sizeof(Geom) * nbR);
-  geo = (double *)carve(4 * sizeof(double));
-  kb = (uint64_t *)carve(sizeof(uint64_t) * n);
-  va = (int *)carve(sizeof(int) * n);
-  vb = (int *)carve(sizeof(int) * n);
-  counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)nblocks);
+  Geom *part = (Geom *)carve(sizeof(Geom) * nbR);
+  double *geo = (double *)carve(4 * sizeof(double) + sizeof(int));
+  int *maxleaf = (int *)(geo + 4);
+  uint64_t *kb = (uint64_t *)carve(sizeof(uint64_t) * n);
+  int *va = (int *)carve(sizeof(int) * n);
+  int *vb = (int *)carve(sizeof(int) * n);
+  int *slot = (int *)carve(sizeof(int) * n);
+  int *lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
+  unsigned *counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)nblocks);
   unsigned *totals = (unsigned *)carve(sizeof(unsigned) * 256);
 
-  hpfmm_status status = HPFMM_OK;
-  double hgeo[3];
+  int tb = 256;
+  unsigned gb = (unsigned)((n + tb - 1) / tb);
+  double hgeo[5];
   pass_begin(pl, st, PASS_TREE);
   bbox_partial<<<nbR, kRedThreads, 0, st>>>(x, y, n, part);
-  bbox_final<<<1, 32, 0, st>>>(part, nbR, geo);
-  cudaError_t e = cudaMemcpyAsync(hgeo, geo, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  bbox_final<<<1, kRedThreads, 0, st>>>(part, nbR, geo);
+  cudaError_t e = cudaMemsetAsync(lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
+  morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, kb, va, lcount, slot);
+  scan_leaves<<<1, 1024, 0, st>>>(lcount, nleaf, pl->leaf_start, maxleaf);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_last_error("tree_build: %s", cudaGetErrorString(e));
@@ -277,35 +454,48 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
     return HPFMM_ECUDA;
   }
   if (hgeo[2] != 0.0) {
-    pass_end(pl, st, PASS_TREE, 2);
+    pass_end(pl, st, PASS_TREE, 4);
     set_last_error("points must be finite with y > 0");
     cudaFreeAsync(tmp, st);
     return HPFMM_EINVAL;
   }
   pl->x0 = hgeo[0];
   pl->side = hgeo[1];
-  if (!(pl->side > 0)) pl->side = 1.0;  // single point: any square will do
-
-  int tb = 256;
-  unsigned gb = (unsigned)((n + tb - 1) / tb);
-  morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, pl->keys, va);
-  uint64_t *kin = pl->keys, *kout = kb;
-  int *vin = va, *vout = vb;
-  for (int shift = 0; shift < 60; shift += 8) {
-    radix_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, counts);
-    radix_scan_digit<<<256, 256, 0, st>>>(counts, nblocks, totals);
-    radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts, totals,
-                                                     kout, vout);
-    uint64_t *tk = kin; kin = kout; kout = tk;
-    int *tv = vin; vin = vout; vout = tv;
+  int hmax = 0;
+  memcpy(&hmax, &hgeo[4], sizeof(int));
+  int launches = 4;
+  int *sorted_idx = vb;
+  if (hmax <= kLeafSort) {
+    bucket_scatter<<<gb, tb, 0, st>>>(kb, slot, n, H, pl->leaf_start, pl->keys, vb);
+    leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
+        pl->leaf_start, nleaf, pl->keys, vb);
+    launches += 2;
+    if (hmax > 32) {
+      leaf_sort<<<nleaf < 4096 ? nleaf : 4096, 256, 0, st>>>(pl->leaf_start, nleaf, pl->keys, vb);
+      ++launches;
+    }
+  } else {
+    // stable LSD radix sort of (key, index) over all 60 key bits
+    uint64_t *kin = kb, *kout = pl->keys;
+    int *vin = va, *vout = vb;
+    for (int shift = 0; shift < 60; shift += 8) {
+      radix_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, counts);
+      radix_scan_digit<<<256, 256, 0, st>>>(counts, nblocks, totals);
+      radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts,
+                                                       totals, kout, vout);
+      uint64_t *tk = kin; kin = kout; kout = tk;
+      int *tv = vin; vin = vout; vout = tv;
+    }
+    // 8 passes: the result is back in kb / va
+    e = cudaMemcpyAsync(pl->keys, kb, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
+    sorted_idx = va;
+    launches += 3 * 8;
   }
-  // 8 passes: the sorted data is back in pl->keys / va
-  leaf_offsets<<<(pl->nleaf + 1 + 255) / 256, 256, 0, st>>>(pl->keys, n, pl->H, pl->nleaf,
-                                                            pl->leaf_start);
-  gather_points<<<gb, tb, 0, st>>>(x, y, vin, pl->keys, n, pl->H, geo, pl->xs, pl->ys, pl->perm,
-                                   pl->loc32);
-  pass_end(pl, st, PASS_TREE, 2 + 1 + 3 * 8 + 2);
-  e = cudaGetLastError();
+  gather_points<<<gb, tb, 0, st>>>(x, y, sorted_idx, pl->keys, n, H, geo, pl->xs, pl->ys,
+                                   pl->perm, pl->loc32);
+  pass_end(pl, st, PASS_TREE, launches + 1);
+  hpfmm_status status = HPFMM_OK;
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error("tree_build launch: %s", cudaGetErrorString(e));
     status = HPFMM_ECUDA;
