@@ -146,6 +146,195 @@ k_m2m(int l, int p, const cpx<R> *__restrict__ T, cpx<R> *__restrict__ M) {
 }
 
 // --------------------------------------------------------------------------
+// Fused upward pass.  The tree below level l0 = H - k (k = min(3, H - 1)) is
+// split into subtrees of 4^k leaves; one block per subtree forms the leaf
+// moments (S2M: M_n = sum_j Q_j ((z_j - z_c)/d)^n, one warp per leaf, lanes
+// over points, a shuffle reduction per n) and merges them level by level up
+// to l0 with the M2M shift (Eq. metome) in shared memory.  Levels l0 - 1 .. 1
+// are then done by one single-block kernel.
+template <typename R>
+__device__ __forceinline__ R wsum(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
+         int k, double x0, double side, int p, const cpx<R> *__restrict__ Tm2m,
+         cpx<R> *__restrict__ M) {
+  extern __shared__ unsigned char smem_raw[];
+  const int P1 = p + 1;
+  cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
+  cpx<R> *Ms = T + 4 * P1 * P1;                       // subtree boxes, level by level
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tm2m[e];
+  const int nl = 1 << (2 * k);                 // leaves per subtree
+  const int64_t first_leaf = (int64_t)blockIdx.x * nl;  // Morton order: subtree = contiguous
+  const double d = ldexp(side, -H);
+  const R invd = (R)(1.0 / d);
+  // leaf moments
+  for (int li = warp; li < nl; li += nw) {
+    const int64_t leaf = first_leaf + li;
+    const double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
+    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    cpx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+    for (int base = b0; base < b1; base += 32) {
+      const int j = base + lane;
+      cpx<R> w = mk<R>(0, 0), t = mk<R>(0, 0);
+      if (j < b1) {
+        R rx, ry;
+        pts.rel(j, cx, cy, rx, ry);
+        w = mk<R>(rx * invd, ry * invd);
+        t = mk<R>(qs[j], 0);
+      }
+      for (int n = 0; n < P1; ++n) {
+        const R sx = wsum(t.x), sy = wsum(t.y);
+        if (n == lane) { acc0.x += sx; acc0.y += sy; }
+        if (n == lane + 32) { acc1.x += sx; acc1.y += sy; }
+        t = t * w;
+      }
+    }
+    cpx<R> *o = Ms + (size_t)li * P1;
+    cpx<R> *g = M + (size_t)(level_offset(H) + leaf) * P1;
+    if (lane < P1) { o[lane] = acc0; g[lane] = acc0; }
+    if (lane + 32 < P1) { o[lane + 32] = acc1; g[lane + 32] = acc1; }
+  }
+  __syncthreads();
+  // M2M inside the subtree: level H-1 .. H-k
+  cpx<R> *child = Ms;
+  int nchild = nl;
+  for (int l = H - 1; l >= H - k; --l) {
+    cpx<R> *par = child + (size_t)nchild * P1;
+    const int npar = nchild >> 2;
+    const int64_t first = first_leaf >> (2 * (H - l));
+    for (int e = threadIdx.x; e < npar * P1; e += blockDim.x) {
+      const int b = e / P1, n = e % P1;
+      cpx<R> acc = mk<R>(0, 0);
+      for (int c = 0; c < 4; ++c) {
+        const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)n * P1;
+        const cpx<R> *mc = child + (size_t)(4 * b + c) * P1;
+        for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], mc[m]);
+      }
+      par[e] = acc;
+      M[(size_t)(level_offset(l) + first + b) * P1 + n] = acc;
+    }
+    __syncthreads();
+    child = par;
+    nchild = npar;
+  }
+}
+
+// M2M for the coarse levels l0 - 1 .. 1, one block, level by level
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k_m2m_coarse(int l0, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M) {
+  const int P1 = p + 1;
+  for (int l = l0 - 1; l >= 1; --l) {
+    const int nb = 1 << (2 * l);
+    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) {
+      const int b = e / P1, n = e % P1;
+      const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * b) * P1;
+      cpx<R> acc = mk<R>(0, 0);
+      for (int c = 0; c < 4; ++c) {
+        const cpx<R> *Tc = Tm2m + (size_t)c * P1 * P1 + (size_t)n * P1;
+        for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], child[(size_t)c * P1 + m]);
+      }
+      M[(size_t)(level_offset(l) + b) * P1 + n] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// L2L (Eq. letole1) for the coarse levels 2 .. l0, one block, level by level
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k_l2l_coarse(int l0, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
+             cpx<R> *__restrict__ B) {
+  const int P1 = p + 1;
+  for (int l = 2; l <= l0; ++l) {
+    const int nb = 1 << (2 * l);
+    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) {
+      const int b = e / P1, m = e % P1, c = b & 3;
+      const size_t pe = (size_t)(level_offset(l - 1) + (b >> 2)) * P1;
+      const size_t ce = (size_t)(level_offset(l) + b) * P1;
+      const cpx<R> *Tc = Tl2l + (size_t)c * P1 * P1 + (size_t)m * P1;
+      cpx<R> sa = A[ce + m], sb = B[ce + m];
+      for (int n = m; n < P1; ++n) {
+        cfma(sa, Tc[n], A[pe + n]);
+        cfma(sb, conj(Tc[n]), B[pe + n]);
+      }
+      A[ce + m] = sa;
+      B[ce + m] = sb;
+    }
+    __syncthreads();
+  }
+}
+
+// Fused downward pass below l0: one block per level-l0 box pushes its local
+// expansions down k levels in shared memory (child = L2L(parent) + the
+// child's own M2L result) and writes the leaf expansions only.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
+           cpx<R> *__restrict__ B) {
+  extern __shared__ unsigned char smem_raw[];
+  const int P1 = p + 1;
+  cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
+  cpx<R> *buf = T + 4 * P1 * P1;  // two ping-pong regions of 4^(k-1) boxes x (A, B);
+                                  // the leaf level goes straight to global memory
+  const int nmax = 1 << (2 * (k - 1));
+  cpx<R> *cur = buf, *nxt = buf + (size_t)2 * nmax * P1;
+  for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tl2l[e];
+  const int l0 = H - k;
+  const int64_t root = blockIdx.x;
+  for (int e = threadIdx.x; e < P1; e += blockDim.x) {
+    cur[e] = A[(size_t)(level_offset(l0) + root) * P1 + e];
+    cur[P1 + e] = B[(size_t)(level_offset(l0) + root) * P1 + e];
+  }
+  __syncthreads();
+  int np = 1;
+  for (int l = l0 + 1; l <= H; ++l) {
+    const int nc = np * 4;
+    const int64_t first = root << (2 * (l - l0));
+    for (int e = threadIdx.x; e < nc * P1; e += blockDim.x) {
+      const int b = e / P1, m = e % P1, c = b & 3;
+      const cpx<R> *pa = cur + (size_t)(b >> 2) * 2 * P1;
+      const cpx<R> *pb = pa + P1;
+      const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
+      const size_t ce = (size_t)(level_offset(l) + first + b) * P1 + m;
+      cpx<R> sa = A[ce], sb = B[ce];
+      for (int n = m; n < P1; ++n) {
+        cfma(sa, Tc[n], pa[n]);
+        cfma(sb, conj(Tc[n]), pb[n]);
+      }
+      if (l == H) {
+        A[ce] = sa;
+        B[ce] = sb;
+      } else {
+        nxt[(size_t)b * 2 * P1 + m] = sa;
+        nxt[(size_t)b * 2 * P1 + P1 + m] = sb;
+      }
+    }
+    __syncthreads();
+    cpx<R> *t = cur; cur = nxt; nxt = t;
+    np = nc;
+  }
+}
+
+template <typename R>
+size_t upward_smem(int p, int k) {
+  size_t P1 = p + 1, nb = 0;
+  for (int j = 0; j <= k; ++j) nb += size_t(1) << (2 * j);
+  return sizeof(cpx<R>) * (4 * P1 * P1 + nb * P1);
+}
+template <typename R>
+size_t downward_smem(int p, int k) {
+  size_t P1 = p + 1;
+  return sizeof(cpx<R>) * (4 * P1 * P1 + 4 * (size_t(1) << (2 * (k > 0 ? k - 1 : 0))) * P1);
+}
+
+// --------------------------------------------------------------------------
 // free-space M2L over the V-list.  Block = 32 target boxes of one child type
 // (ix & 1, iy & 1), so that all of them share the same 27 source offsets;
 // for each offset the (p+1)^2 translation matrix is staged in shared memory
@@ -970,74 +1159,88 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
 
 // Image and reaction near field of the bottom-row leaves (single precision
 // with the double routine for |P| > 1 and, in MIXED mode, below tau), added
-// to the outputs written by k_eval32g.  One warp per bottom-row leaf, the
-// same lane grouping as k_eval32g.
+// to the outputs written by k_eval32g.  One block per bottom-row leaf: the
+// sources of the three bottom-row neighbours are staged in shared memory,
+// lanes take 32 targets at a time and the 8 warps split the sources; the
+// partial sums are reduced in shared memory.
+constexpr int kMirSrc = 512;
 __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
            double side, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad) {
-  __shared__ float4 sbuf[kEvWarps][kEvBuf];
+  __shared__ float4 src[kMirSrc];
+  __shared__ float red[kEvWarps][9][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = 1 << H;
-  const int ix = blockIdx.x * kEvWarps + warp;  // leaf (ix, 0)
-  if (ix >= nx) return;
-  float4 *buf = sbuf[warp];
+  const int ix = blockIdx.x;  // leaf (ix, 0)
   const float d = (float)ldexp(side, -H);
   const cf kap = mk((float)kappa.x, (float)kappa.y);
   const uint64_t leaf = box_morton(ix, 0);
   const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-  const int T = b1 - b0;
-  const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
-  const int ng = 32 / gs, g = lane / gs, tl = lane % gs;
-  for (int tb = b0; tb < b1; tb += gs) {
-    const int i = tb + tl;
+  // source ranges of the bottom-row neighbours
+  int s0[3], s1[3];
+  float ox[3];
+  int ns = 0;
+  for (int k = 0; k < 3; ++k) {
+    int mxx = ix - 1 + k;
+    s0[k] = s1[k] = 0;
+    ox[k] = (float)(mxx - ix) * d;
+    if (mxx >= 0 && mxx < nx) {
+      uint64_t sl = box_morton(mxx, 0);
+      s0[k] = leaf_start[sl];
+      s1[k] = leaf_start[sl + 1];
+    }
+    ns += s1[k] - s0[k];
+  }
+  const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+  const float i2pi = (float)(1.0 / HP_TWO_PI);
+  for (int tb = b0; tb < b1; tb += 32) {
+    const int i = tb + lane;
     const bool act = i < b1;
     const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
     NearAcc acc;
     acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
     acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
-    int fill = 0;
-    for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
-      if (mxx < 0 || mxx >= nx) continue;
-      const uint64_t sl = box_morton(mxx, 0);
-      const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-      const float ox = (float)(mxx - ix) * d;
-      for (int sb = s0; sb < s1; sb += 32) {
-        const int cnt = min(32, s1 - sb);
-        if (fill + cnt > kEvBuf) {
-          __syncwarp();
-          mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
-          __syncwarp();
-          fill = 0;
-        }
-        if (lane < cnt) {
-          const float2 v = loc[sb + lane];
-          buf[fill + lane] = make_float4(v.x + ox, v.y, qs[sb + lane], 0.f);
-        }
-        fill += cnt;
+    for (int base = 0; base < ns; base += kMirSrc) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kMirSrc && base + e < ns; e += blockDim.x) {
+        int r = base + e, k = 0;
+        while (r >= s1[k] - s0[k]) { r -= s1[k] - s0[k]; ++k; }
+        const int js = s0[k] + r;
+        const float2 v = loc[js];
+        src[e] = make_float4(v.x + ox[k], v.y, qs[js], 0.f);
+      }
+      __syncthreads();
+      const int cnt = min(kMirSrc, ns - base);
+      mirror_batch(src, cnt, warp, kEvWarps, me.x, me.y, d, kap, kappa, tau, acc);
+    }
+    red[warp][0][lane] = acc.li;
+    red[warp][1][lane] = acc.gix;
+    red[warp][2][lane] = acc.giy;
+    red[warp][3][lane] = acc.ur.x;
+    red[warp][4][lane] = acc.ur.y;
+    red[warp][5][lane] = acc.grx.x;
+    red[warp][6][lane] = acc.grx.y;
+    red[warp][7][lane] = acc.gry.x;
+    red[warp][8][lane] = acc.gry.y;
+    __syncthreads();
+    if (warp == 0 && act) {
+      float v[9];
+      for (int c = 0; c < 9; ++c) {
+        v[c] = 0.f;
+        for (int w = 0; w < kEvWarps; ++w) v[c] += red[w][c][lane];
+      }
+      const int64_t o = perm[i];
+      pot[2 * o] += (double)(v[0] * c4 + v[3] * i2pi);
+      pot[2 * o + 1] += (double)(v[4] * i2pi);
+      if (grad) {
+        grad[4 * o + 0] += (double)((v[1] + v[5]) * i2pi);
+        grad[4 * o + 1] += (double)(v[6] * i2pi);
+        grad[4 * o + 2] += (double)((v[2] + v[7]) * i2pi);
+        grad[4 * o + 3] += (double)(v[8] * i2pi);
       }
     }
-    __syncwarp();
-    mirror_batch(buf, fill, g, ng, me.x, me.y, d, kap, kappa, tau, acc);
-    __syncwarp();
-    acc.li = xsum(acc.li, gs);
-    acc.gix = xsum(acc.gix, gs);
-    acc.giy = xsum(acc.giy, gs);
-    acc.ur.x = xsum(acc.ur.x, gs); acc.ur.y = xsum(acc.ur.y, gs);
-    acc.grx.x = xsum(acc.grx.x, gs); acc.grx.y = xsum(acc.grx.y, gs);
-    acc.gry.x = xsum(acc.gry.x, gs); acc.gry.y = xsum(acc.gry.y, gs);
-    if (!act || g != 0) continue;
-    const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
-    const float i2pi = (float)(1.0 / HP_TWO_PI);
-    const int64_t o = perm[i];
-    pot[2 * o] += (double)(acc.li * c4 + acc.ur.x * i2pi);
-    pot[2 * o + 1] += (double)(acc.ur.y * i2pi);
-    if (grad) {
-      grad[4 * o + 0] += (double)((acc.gix + acc.grx.x) * i2pi);
-      grad[4 * o + 1] += (double)(acc.grx.y * i2pi);
-      grad[4 * o + 2] += (double)((acc.giy + acc.gry.x) * i2pi);
-      grad[4 * o + 3] += (double)(acc.gry.y * i2pi);
-    }
+    __syncthreads();
   }
 }
 
@@ -1068,22 +1271,24 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   pass_end(pl, st, PASS_GATHER, 1);
   pass_begin(pl, st, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
-  size_t shp2m = sizeof(cpx<R>) * P1 * 33 * kWarpsPerBlock;
-  if (sizeof(R) == 8) {
-    LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
-    k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
-        lp, (const double *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cd *)M);
-  } else {
-    LeafPoints<float> lp{pl->loc32};
-    k_p2m<float><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
-        lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cf *)M);
+  const int ksub = H - 1 < 3 ? H - 1 : 3, l0 = H - ksub;
+  {
+    size_t sm = upward_smem<R>(p, ksub);
+    unsigned nb = (unsigned)(int64_t(1) << (2 * l0));
+    if (sizeof(R) == 8) {
+      LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
+      k_upward<double><<<nb, 256, sm, st>>>(lp, (const double *)qs, pl->leaf_start, H, ksub,
+                                            pl->x0, pl->side, p, (const cd *)Tm2m, (cd *)M);
+    } else {
+      LeafPoints<float> lp{pl->loc32};
+      k_upward<float><<<nb, 256, sm, st>>>(lp, (const float *)qs, pl->leaf_start, H, ksub,
+                                           pl->x0, pl->side, p, (const cf *)Tm2m, (cf *)M);
+    }
   }
   pass_end(pl, st, PASS_P2M, 1);
   pass_begin(pl, st, PASS_M2M);
-  for (int l = H - 1; l >= 1; --l)
-    k_m2m<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
-        l, p, Tm2m, M);
-  pass_end(pl, st, PASS_M2M, H - 1);
+  if (l0 > 1) k_m2m_coarse<R><<<1, 1024, 0, st>>>(l0, p, Tm2m, M);
+  pass_end(pl, st, PASS_M2M, l0 > 1 ? 1 : 0);
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
@@ -1112,10 +1317,11 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   }
   pass_end(pl, st, PASS_M2L_MIRROR, 1);
   pass_begin(pl, st, PASS_L2L);
-  for (int l = 2; l <= H; ++l)
-    k_l2l<R><<<cdiv_u(int64_t(1) << (2 * l), kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
-        l, p, Tl2l, A, B);
-  pass_end(pl, st, PASS_L2L, H - 1);
+  if (l0 >= 2) k_l2l_coarse<R><<<1, 1024, 0, st>>>(l0, p, Tl2l, A, B);
+  if (ksub > 0)
+    k_downward<R><<<(unsigned)(int64_t(1) << (2 * l0)), 256, downward_smem<R>(p, ksub), st>>>(
+        H, ksub, p, Tl2l, A, B);
+  pass_end(pl, st, PASS_L2L, (l0 >= 2 ? 1 : 0) + (ksub > 0 ? 1 : 0));
   pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
   cd kappa = mk(pl->kre, pl->kim);
@@ -1130,7 +1336,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         (const cf *)A, (const cf *)B, pot, grad);
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
-    k_mirror32<<<cdiv_u(int64_t(1) << H, kEvWarps), 32 * kEvWarps, 0, st>>>(
+    k_mirror32<<<(unsigned)(1 << H), 32 * kEvWarps, 0, st>>>(
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, kappa, tau, pot,
         grad);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
@@ -1161,6 +1367,14 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+  HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)upward_smem<double>(p, 3)));
+  HP_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)upward_smem<float>(p, 3)));
+  HP_CUDA(cudaFuncSetAttribute(k_downward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)downward_smem<double>(p, 3)));
+  HP_CUDA(cudaFuncSetAttribute(k_downward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)downward_smem<float>(p, 3)));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   return HPFMM_OK;
 }

@@ -119,7 +119,10 @@ __global__ void k_img_m2l(int p, cd *T, cd *logt) {
   if (threadIdx.x == 0) logt[cls] = clog_d(t);
 }
 
-// reaction M2L matrices, block = (level, class, sign); Tp/Tm: [level][cls][n][m]
+// reaction M2L matrices, block = (level, class, sign); Tp/Tm: [level][cls][n][m].
+// Thread k evaluates It_k = J_k(P) / (2 pi k! shat^k) directly (series or
+// continued fraction for that k; no recursion between threads), then the
+// block fills the matrix.
 __global__ void k_reaction_m2l(int p, int H, double side, cd kappa, const double *__restrict__ Cb,
                                cd *Tr) {
   extern __shared__ cd sh[];
@@ -129,21 +132,18 @@ __global__ void k_reaction_m2l(int p, int H, double side, cd kappa, const double
   int cls = (b >> 1) % 21;
   int lev = (b >> 1) / 21 + 1;  // 1..H
   int dx = cls % 7 - 3, ysum = cls / 7 + 1;
-  double d = side / (double)(1 << lev);
-  // I_k at (x, y) = (+-(x_t - x_s), y_t + y_s) = (-+dx d, ysum d); s/d = ysum + -i(x/d)
+  double d = ldexp(side, -lev);
+  // I_k at (x, y) = (+-(x_t - x_s), y_t + y_s) = (-+dx d, ysum d); s/d = ysum - i(x/d)
   double xs_ = sign ? (double)dx : -(double)dx;  // x / d
   cd shat = mk((double)ysum, -xs_);
-  cd *J = sh;         // K+1
-  cd *h = sh + K + 1; // K+1: It_k = J_k / (2 pi k! shat^k)
-  if (threadIdx.x == 0) {
-    cd P = (d * kappa) * shat;
-    jn_range(P, K, J);
+  cd *h = sh;  // K+1: It_k
+  cd P = (d * kappa) * shat;
+  for (int k = threadIdx.x; k <= K; k += blockDim.x) {
+    cd J = jn_direct(P, k);
     cd sinv = cinv(shat);
     cd f = mk(1.0 / HP_TWO_PI, 0.0);
-    for (int k = 0; k <= K; ++k) {
-      if (k > 0) f = (1.0 / k) * (f * sinv);
-      h[k] = J[k] * f;
-    }
+    for (int j = 1; j <= k; ++j) f = (1.0 / j) * (f * sinv);
+    h[k] = J * f;
   }
   __syncthreads();
   cd *out = Tr + ((size_t)((lev - 1) * 21 + cls) * 2 + sign) * P1 * P1;
@@ -195,9 +195,9 @@ hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
   size_t m2 = (size_t)P1 * P1;
   cd *rea = (cd *)pl->t_refl;
   pass_begin(pl, st, PASS_TABLES);
-  size_t shm = sizeof(cd) * 2 * (2 * p + 1);
-  k_reaction_m2l<<<H * 21 * 2, 256, shm, st>>>(p, H, pl->side, mk(pl->kre, pl->kim),
-                                                pl->t_binom, rea);
+  size_t shm = sizeof(cd) * (2 * p + 1);
+  k_reaction_m2l<<<H * 21 * 2, 96, shm, st>>>(p, H, pl->side, mk(pl->kre, pl->kim),
+                                               pl->t_binom, rea);
   HP_LAUNCH_CHECK();
   int nl = 1;
   if (pl->prec != HPFMM_FP64) {
