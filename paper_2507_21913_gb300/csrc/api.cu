@@ -137,7 +137,7 @@ static void free_plan(hpfmm_plan *pl) {
   void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
-                  pl->t_binom};
+                  pl->t_binom, pl->geo};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -182,6 +182,19 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
     dy = tmp + n;
   }
   hpfmm_status s = tree_build(pl, dx, dy, st);
+  if (s == HPFMM_OK) s = tables_build(pl, st);
+  // the one host synchronisation of a rebuild: geometry, validity, largest leaf
+  double hgeo[5] = {0, 0, 1, 0, 0};
+  if (s == HPFMM_OK) {
+    e = cudaMemcpyAsync(hgeo, pl->geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_last_error("rebuild: %s", cudaGetErrorString(e));
+      s = HPFMM_ECUDA;
+    }
+  }
+  hpfmm_status s2 = tree_finish(pl, dx, dy, hgeo, st);
+  if (s == HPFMM_OK) s = s2;
   if (tmp) cudaFreeAsync(tmp, st);
   if (s != HPFMM_OK) return s;
   double kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
@@ -190,7 +203,7 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
                    "evaluation", kabs * sqrt(5.0) * pl->side);
     return HPFMM_EUNSUPPORTED;
   }
-  return tables_build(pl, st);
+  return HPFMM_OK;
 }
 
 extern "C" hpfmm_status hpfmm_update_points(hpfmm_plan *pl, const double *x, const double *y,
@@ -278,6 +291,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->A, csz * (size_t)pl->nbox * P1);
   ALLOC(pl->B, csz * (size_t)pl->nbox * P1);
   ALLOC(pl->status, sizeof(int));
+  ALLOC(pl->geo, 8 * sizeof(double));
 #undef ALLOC
   s = fmm_set_smem_limits(p);
   if (s != HPFMM_OK) { free_plan(pl); return s; }

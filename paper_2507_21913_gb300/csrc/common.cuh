@@ -163,6 +163,9 @@ struct hpfmm_plan {
   double *in_q = nullptr;                         // staging for host charges
   int64_t stage_rhs = 0;
   int *status = nullptr;  // device status word
+  double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
+  void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
+  int64_t tree_tmp_bytes = 0;
   int64_t workspace_bytes = 0;
 
   // pass timing (events on the caller's stream) and launch counts
@@ -206,6 +209,8 @@ void set_last_error(const char *fmt, ...);
 
 // internal entry points shared between translation units
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st);
+hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const double *hgeo,
+                         cudaStream_t st);
 hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad, cudaStream_t st);

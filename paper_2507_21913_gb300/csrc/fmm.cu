@@ -322,6 +322,8 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
   }
 }
 
+constexpr size_t kFusedSmem = 200 * 1024;
+
 template <typename R>
 size_t upward_smem(int p, int k) {
   size_t P1 = p + 1, nb = 0;
@@ -1271,7 +1273,10 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   pass_end(pl, st, PASS_GATHER, 1);
   pass_begin(pl, st, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
-  const int ksub = H - 1 < 3 ? H - 1 : 3, l0 = H - ksub;
+  int ksub = H - 1 < 4 ? H - 1 : 4;
+  while (ksub > 1 && (upward_smem<R>(p, ksub) > kFusedSmem || downward_smem<R>(p, ksub) > kFusedSmem))
+    --ksub;
+  const int l0 = H - ksub;
   {
     size_t sm = upward_smem<R>(p, ksub);
     unsigned nb = (unsigned)(int64_t(1) << (2 * l0));
@@ -1368,13 +1373,13 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)upward_smem<double>(p, 3)));
+                               (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)upward_smem<float>(p, 3)));
+                               (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_downward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)downward_smem<double>(p, 3)));
+                               (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_downward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)downward_smem<float>(p, 3)));
+                               (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   return HPFMM_OK;
 }

@@ -123,8 +123,9 @@ __global__ void k_img_m2l(int p, cd *T, cd *logt) {
 // Thread k evaluates It_k = J_k(P) / (2 pi k! shat^k) directly (series or
 // continued fraction for that k; no recursion between threads), then the
 // block fills the matrix.
-__global__ void k_reaction_m2l(int p, int H, double side, cd kappa, const double *__restrict__ Cb,
-                               cd *Tr) {
+__global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd kappa,
+                               const double *__restrict__ Cb, cd *Tr) {
+  const double side = geo[1];
   extern __shared__ cd sh[];
   int P1 = p + 1, K = 2 * p;
   int b = blockIdx.x;
@@ -196,7 +197,7 @@ hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
   cd *rea = (cd *)pl->t_refl;
   pass_begin(pl, st, PASS_TABLES);
   size_t shm = sizeof(cd) * (2 * p + 1);
-  k_reaction_m2l<<<H * 21 * 2, 96, shm, st>>>(p, H, pl->side, mk(pl->kre, pl->kim),
+  k_reaction_m2l<<<H * 21 * 2, 96, shm, st>>>(p, H, pl->geo, mk(pl->kre, pl->kim),
                                                pl->t_binom, rea);
   HP_LAUNCH_CHECK();
   int nl = 1;

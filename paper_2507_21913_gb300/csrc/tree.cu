@@ -135,44 +135,77 @@ __global__ void morton_keys(const double *__restrict__ x, const double *__restri
   if (leaf_count) slot[i] = atomicAdd(&leaf_count[k >> (60 - 2 * H)], 1);
 }
 
-// exclusive scan of the leaf counts into leaf_start (single block, chunked),
-// and the largest leaf
+// exclusive scan of the leaf counts into leaf_start, in three phases: block
+// partial scans (1024 leaves per block) with block totals and maxima, a scan
+// of the totals (one block), the block offsets added back
+__device__ __forceinline__ int block_scan_1024(int v, int *ws, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  int wpre = 0, tot = 0;
+  for (int w = 0; w < 32; ++w) {
+    if (w < warp) wpre += ws[w];
+    tot += ws[w];
+  }
+  __syncthreads();
+  total = tot;
+  return wpre + x - v;  // exclusive
+}
+
 __global__ void __launch_bounds__(1024)
-scan_leaves(const int *__restrict__ count, int nleaf, int *__restrict__ start,
-            int *__restrict__ maxleaf) {
+scan_part(const int *__restrict__ count, int nleaf, int *__restrict__ start,
+          int *__restrict__ btot, int *__restrict__ bmax) {
   __shared__ int ws[32];
-  __shared__ int wm[32];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  const int v = i < nleaf ? count[i] : 0;
+  int tot;
+  const int ex = block_scan_1024(v, ws, tot);
+  if (i < nleaf) start[i] = ex;
+  int m = v;
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int mm = 0;
+    for (int w = 0; w < 32; ++w) mm = max(mm, ws[w]);
+    btot[blockIdx.x] = tot;
+    bmax[blockIdx.x] = mm;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+scan_top(int *__restrict__ btot, const int *__restrict__ bmax, int nb, int nleaf,
+         int *__restrict__ start, int *__restrict__ maxleaf) {
+  __shared__ int ws[32];
   int carry = 0, mx = 0;
-  for (int base = 0; base < nleaf; base += 1024) {
-    int i = base + threadIdx.x;
-    int v = (i < nleaf) ? count[i] : 0;
-    mx = max(mx, v);
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[warp] = x;
-    __syncthreads();
-    int wpre = 0, tot = 0;
-    for (int w = 0; w < 32; ++w) {
-      if (w < warp) wpre += ws[w];
-      tot += ws[w];
-    }
-    if (i < nleaf) start[i] = carry + wpre + x - v;
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? btot[i] : 0;
+    if (i < nb) mx = max(mx, bmax[i]);
+    int tot;
+    const int ex = block_scan_1024(v, ws, tot);
+    if (i < nb) btot[i] = carry + ex;
     carry += tot;
-    __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) wm[warp] = mx;
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     int m = 0;
-    for (int w = 0; w < 32; ++w) m = max(m, wm[w]);
-    start[nleaf] = carry;
+    for (int w = 0; w < 32; ++w) m = max(m, ws[w]);
     *maxleaf = m;
+    start[nleaf] = carry;
   }
+}
+
+__global__ void scan_add(const int *__restrict__ btot, int nleaf, int *__restrict__ start) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < nleaf) start[i] += btot[blockIdx.x];
 }
 
 __global__ void bucket_scatter(const uint64_t *__restrict__ keys, const int *__restrict__ slot,
@@ -402,104 +435,140 @@ __global__ void gather_points(const double *__restrict__ x, const double *__rest
 }  // namespace
 
 // Build (or rebuild) the tree of pl for the n points (x, y) (device pointers).
-// Leaves pl->xs, ys, perm, keys, leaf_start, loc32 filled and pl->x0, side set;
-// returns EINVAL (synchronously) for non-finite input or y <= 0.
+// Leaves pl->xs, ys, perm, keys, leaf_start, loc32 filled and pl->geo (x0,
+// side, invalid flag, 2^30/side, largest leaf) on the device; the host values
+// pl->x0 / side are set by tree_finish after the caller's single sync.
 //
 // Order: keys and leaf counts -> leaf offsets (scan) -> points bucketed by leaf
 // -> each bucket sorted by (key, index).  The result is the stable order by
-// (key, index) over all points.  When some leaf holds more than kLeafSort
-// points the full LSD radix sort of (key, index) is used instead.
-hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
+// (key, index) over all points.  This path is launched without waiting for
+// the host; tree_finish checks afterwards that no leaf exceeded kLeafSort
+// points and otherwise redoes the sort with the full LSD radix sort of
+// (key, index).
+namespace {
+struct TreeTmp {
+  char *base = nullptr;
+  Geom *part;
+  uint64_t *kb;
+  int *va, *vb, *slot, *lcount, *btot, *bmax;
+  unsigned *counts, *totals;
+  int nbR, nblocks;
+};
+}  // namespace
+
+static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
   const int64_t n = pl->n;
-  const int H = pl->H, nleaf = pl->nleaf;
+  const int nleaf = pl->nleaf;
   int64_t nbR64 = (n + kRedThreads - 1) / kRedThreads;
-  int nbR = nbR64 < 1024 ? (int)nbR64 : 1024;
-  int nblocks = (int)((n + kTile - 1) / kTile);
-  size_t bytes = sizeof(Geom) * nbR + 4 * sizeof(double) + sizeof(uint64_t) * n +
-                 3 * sizeof(int) * n + sizeof(int) * ((size_t)nleaf + 1) +
-                 sizeof(unsigned) * 256 * ((size_t)nblocks + 1);
-  char *tmp = nullptr;
-  HP_CUDA(cudaMallocAsync((void **)&tmp, bytes + 10 * 256, st));
-  char *c = tmp;
+  t.nbR = nbR64 < 1024 ? (int)nbR64 : 1024;
+  t.nblocks = (int)((n + kTile - 1) / kTile);
+  const int nsb = (nleaf + 1023) / 1024;
+  size_t bytes = sizeof(Geom) * t.nbR + sizeof(uint64_t) * n + 4 * sizeof(int) * n +
+                 sizeof(int) * ((size_t)nleaf + 1) + 2 * sizeof(int) * nsb +
+                 sizeof(unsigned) * 256 * ((size_t)t.nblocks + 1);
+  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 12 * 256, st));
+  char *c = t.base;
   auto carve = [&](size_t b) {
     char *r = c;
     c += (b + 255) & ~size_t(255);
     return r;
   };
-  Geom *part = (Geom *)carve(sizeof(Geom) * nbR);
-  double *geo = (double *)carve(4 * sizeof(double) + sizeof(int));
-  int *maxleaf = (int *)(geo + 4);
-  uint64_t *kb = (uint64_t *)carve(sizeof(uint64_t) * n);
-  int *va = (int *)carve(sizeof(int) * n);
-  int *vb = (int *)carve(sizeof(int) * n);
-  int *slot = (int *)carve(sizeof(int) * n);
-  int *lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
-  unsigned *counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)nblocks);
-  unsigned *totals = (unsigned *)carve(sizeof(unsigned) * 256);
+  t.part = (Geom *)carve(sizeof(Geom) * t.nbR);
+  t.kb = (uint64_t *)carve(sizeof(uint64_t) * n);
+  t.va = (int *)carve(sizeof(int) * n);
+  t.vb = (int *)carve(sizeof(int) * n);
+  t.slot = (int *)carve(sizeof(int) * n);
+  t.lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
+  t.btot = (int *)carve(sizeof(int) * nsb);
+  t.bmax = (int *)carve(sizeof(int) * nsb);
+  t.counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)t.nblocks);
+  t.totals = (unsigned *)carve(sizeof(unsigned) * 256);
+  return HPFMM_OK;
+}
 
+static void radix_path(hpfmm_plan *pl, TreeTmp &t, const double *x, const double *y,
+                       cudaStream_t st) {
+  const int64_t n = pl->n;
+  // keys again into kb / va (the bucket path consumed them)
+  unsigned gb = (unsigned)((n + 255) / 256);
+  morton_keys<<<gb, 256, 0, st>>>(x, y, n, pl->geo, pl->H, t.kb, t.va, nullptr, nullptr);
+  uint64_t *kin = t.kb, *kout = pl->keys;
+  int *vin = t.va, *vout = t.vb;
+  for (int shift = 0; shift < 60; shift += 8) {
+    radix_hist<<<t.nblocks, kSortThreads, 0, st>>>(kin, n, shift, t.nblocks, t.counts);
+    radix_scan_digit<<<256, 256, 0, st>>>(t.counts, t.nblocks, t.totals);
+    radix_scatter<<<t.nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, t.nblocks, t.counts,
+                                                       t.totals, kout, vout);
+    uint64_t *tk = kin; kin = kout; kout = tk;
+    int *tv = vin; vin = vout; vout = tv;
+  }
+  // 8 passes: the result is back in kb / va
+  cudaMemcpyAsync(pl->keys, t.kb, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
+  gather_points<<<gb, 256, 0, st>>>(x, y, t.va, pl->keys, n, pl->H, pl->geo, pl->xs, pl->ys,
+                                    pl->perm, pl->loc32);
+  pass_end(pl, st, PASS_TREE, 2 + 3 * 8);
+}
+
+hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
+  const int64_t n = pl->n;
+  const int H = pl->H, nleaf = pl->nleaf;
+  TreeTmp t;
+  HP_TRY(tree_alloc(pl, t, st));
+  pl->tree_tmp_bytes = 0;
   int tb = 256;
   unsigned gb = (unsigned)((n + tb - 1) / tb);
-  double hgeo[5];
+  const int nsb = (nleaf + 1023) / 1024;
+  double *geo = pl->geo;
+  int *maxleaf = (int *)(geo + 4);
   pass_begin(pl, st, PASS_TREE);
-  bbox_partial<<<nbR, kRedThreads, 0, st>>>(x, y, n, part);
-  bbox_final<<<1, kRedThreads, 0, st>>>(part, nbR, geo);
-  cudaError_t e = cudaMemsetAsync(lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
-  morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, kb, va, lcount, slot);
-  scan_leaves<<<1, 1024, 0, st>>>(lcount, nleaf, pl->leaf_start, maxleaf);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) {
-    set_last_error("tree_build: %s", cudaGetErrorString(e));
-    cudaFreeAsync(tmp, st);
-    return HPFMM_ECUDA;
-  }
-  if (hgeo[2] != 0.0) {
-    pass_end(pl, st, PASS_TREE, 4);
-    set_last_error("points must be finite with y > 0");
-    cudaFreeAsync(tmp, st);
-    return HPFMM_EINVAL;
-  }
-  pl->x0 = hgeo[0];
-  pl->side = hgeo[1];
-  int hmax = 0;
-  memcpy(&hmax, &hgeo[4], sizeof(int));
-  int launches = 4;
-  int *sorted_idx = vb;
-  if (hmax <= kLeafSort) {
-    bucket_scatter<<<gb, tb, 0, st>>>(kb, slot, n, H, pl->leaf_start, pl->keys, vb);
-    leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
-        pl->leaf_start, nleaf, pl->keys, vb);
-    launches += 2;
-    if (hmax > 32) {
-      leaf_sort<<<nleaf < 4096 ? nleaf : 4096, 256, 0, st>>>(pl->leaf_start, nleaf, pl->keys, vb);
-      ++launches;
-    }
-  } else {
-    // stable LSD radix sort of (key, index) over all 60 key bits
-    uint64_t *kin = kb, *kout = pl->keys;
-    int *vin = va, *vout = vb;
-    for (int shift = 0; shift < 60; shift += 8) {
-      radix_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, counts);
-      radix_scan_digit<<<256, 256, 0, st>>>(counts, nblocks, totals);
-      radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts,
-                                                       totals, kout, vout);
-      uint64_t *tk = kin; kin = kout; kout = tk;
-      int *tv = vin; vin = vout; vout = tv;
-    }
-    // 8 passes: the result is back in kb / va
-    e = cudaMemcpyAsync(pl->keys, kb, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
-    sorted_idx = va;
-    launches += 3 * 8;
-  }
-  gather_points<<<gb, tb, 0, st>>>(x, y, sorted_idx, pl->keys, n, H, geo, pl->xs, pl->ys,
-                                   pl->perm, pl->loc32);
-  pass_end(pl, st, PASS_TREE, launches + 1);
-  hpfmm_status status = HPFMM_OK;
+  bbox_partial<<<t.nbR, kRedThreads, 0, st>>>(x, y, n, t.part);
+  bbox_final<<<1, kRedThreads, 0, st>>>(t.part, t.nbR, geo);
+  cudaError_t e = cudaMemsetAsync(t.lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
+  morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, t.kb, t.va, t.lcount, t.slot);
+  scan_part<<<nsb, 1024, 0, st>>>(t.lcount, nleaf, pl->leaf_start, t.btot, t.bmax);
+  scan_top<<<1, 1024, 0, st>>>(t.btot, t.bmax, nsb, nleaf, pl->leaf_start, maxleaf);
+  scan_add<<<nsb, 1024, 0, st>>>(t.btot, nleaf, pl->leaf_start);
+  bucket_scatter<<<gb, tb, 0, st>>>(t.kb, t.slot, n, H, pl->leaf_start, pl->keys, t.vb);
+  leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
+      pl->leaf_start, nleaf, pl->keys, t.vb);
+  leaf_sort<<<nleaf < 4096 ? nleaf : 4096, 256, 0, st>>>(pl->leaf_start, nleaf, pl->keys, t.vb);
+  gather_points<<<gb, tb, 0, st>>>(x, y, t.vb, pl->keys, n, H, geo, pl->xs, pl->ys, pl->perm,
+                                   pl->loc32);
+  pass_end(pl, st, PASS_TREE, 10);
   if (e == cudaSuccess) e = cudaGetLastError();
+  // keep the temporaries until tree_finish has decided on the fallback
+  pl->tree_tmp = t.base;
   if (e != cudaSuccess) {
     set_last_error("tree_build launch: %s", cudaGetErrorString(e));
-    status = HPFMM_ECUDA;
+    return HPFMM_ECUDA;
   }
-  cudaFreeAsync(tmp, st);
-  return status;
+  return HPFMM_OK;
+}
+
+// After the caller's sync: host geometry, invalid-input check, large-leaf
+// fallback (radix sort), release of the temporaries.
+hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const double *hgeo,
+                         cudaStream_t st) {
+  hpfmm_status s = HPFMM_OK;
+  if (hgeo[2] != 0.0) {
+    set_last_error("points must be finite with y > 0");
+    s = HPFMM_EINVAL;
+  } else {
+    pl->x0 = hgeo[0];
+    pl->side = hgeo[1];
+    int hmax = 0;
+    memcpy(&hmax, &hgeo[4], sizeof(int));
+    if (hmax > kLeafSort) {
+      TreeTmp t;
+      s = tree_alloc(pl, t, st);
+      if (s == HPFMM_OK) {
+        pass_begin(pl, st, PASS_TREE);
+        radix_path(pl, t, x, y, st);
+        cudaFreeAsync(t.base, st);
+      }
+    }
+  }
+  if (pl->tree_tmp) cudaFreeAsync(pl->tree_tmp, st);
+  pl->tree_tmp = nullptr;
+  return s;
 }
