@@ -146,6 +146,44 @@ k_m2m(int l, int p, const cpx<R> *__restrict__ T, cpx<R> *__restrict__ M) {
 }
 
 // --------------------------------------------------------------------------
+// S2M with one thread per (leaf, n): M_n = sum_j Q_j w_j^n, w_j = (z_j - z_c)/d,
+// w^n by repeated squaring.  No cross-thread reduction, so the short leaves
+// of a deep tree keep every lane busy.
+template <typename R>
+__device__ __forceinline__ cpx<R> cpow_int(cpx<R> w, int n) {
+  cpx<R> r = mk<R>(1, 0);
+  while (n) {
+    if (n & 1) r = r * w;
+    w = w * w;
+    n >>= 1;
+  }
+  return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
+             int H, double x0, double side, int p, cpx<R> *__restrict__ M) {
+  const int P1 = p + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nleaf = int64_t(1) << (2 * H);
+  if (t >= nleaf * P1) return;
+  const int64_t leaf = t / P1;
+  const int n = (int)(t - leaf * P1);
+  const double d = ldexp(side, -H);
+  const double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
+  const R invd = (R)(1.0 / d);
+  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  cpx<R> acc = mk<R>(0, 0);
+  for (int j = b0; j < b1; ++j) {
+    R rx, ry;
+    pts.rel(j, cx, cy, rx, ry);
+    cfma(acc, mk<R>(qs[j], 0), cpow_int(mk<R>(rx * invd, ry * invd), n));
+  }
+  M[(size_t)(level_offset(H)) * P1 + t] = acc;
+}
+
+// --------------------------------------------------------------------------
 // Fused upward pass.  The tree below level l0 = H - k (k = min(3, H - 1)) is
 // split into subtrees of 4^k leaves; one block per subtree forms the leaf
 // moments (S2M: M_n = sum_j Q_j ((z_j - z_c)/d)^n, one warp per leaf, lanes
@@ -173,33 +211,10 @@ k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ le
   const int64_t first_leaf = (int64_t)blockIdx.x * nl;  // Morton order: subtree = contiguous
   const double d = ldexp(side, -H);
   const R invd = (R)(1.0 / d);
-  // leaf moments
-  for (int li = warp; li < nl; li += nw) {
-    const int64_t leaf = first_leaf + li;
-    const double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
-    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-    cpx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
-    for (int base = b0; base < b1; base += 32) {
-      const int j = base + lane;
-      cpx<R> w = mk<R>(0, 0), t = mk<R>(0, 0);
-      if (j < b1) {
-        R rx, ry;
-        pts.rel(j, cx, cy, rx, ry);
-        w = mk<R>(rx * invd, ry * invd);
-        t = mk<R>(qs[j], 0);
-      }
-      for (int n = 0; n < P1; ++n) {
-        const R sx = wsum(t.x), sy = wsum(t.y);
-        if (n == lane) { acc0.x += sx; acc0.y += sy; }
-        if (n == lane + 32) { acc1.x += sx; acc1.y += sy; }
-        t = t * w;
-      }
-    }
-    cpx<R> *o = Ms + (size_t)li * P1;
-    cpx<R> *g = M + (size_t)(level_offset(H) + leaf) * P1;
-    if (lane < P1) { o[lane] = acc0; g[lane] = acc0; }
-    if (lane + 32 < P1) { o[lane + 32] = acc1; g[lane + 32] = acc1; }
-  }
+  // leaf moments (computed by the S2M kernel) into shared memory
+  for (int e = threadIdx.x; e < nl * P1; e += blockDim.x)
+    Ms[e] = M[(size_t)(level_offset(H) + first_leaf) * P1 + e];
+  (void)pts; (void)qs; (void)leaf_start; (void)x0; (void)side; (void)warp; (void)lane; (void)nw;
   __syncthreads();
   // M2M inside the subtree: level H-1 .. H-k
   cpx<R> *child = Ms;
@@ -1273,11 +1288,25 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   pass_end(pl, st, PASS_GATHER, 1);
   pass_begin(pl, st, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
-  int ksub = H - 1 < 4 ? H - 1 : 4;
+  int ksub = H - 4;  // subtrees of 4^ksub leaves, at least 256 of them
+  if (ksub > 4) ksub = 4;
+  if (ksub < 1) ksub = H - 1 < 1 ? H - 1 : 1;
   while (ksub > 1 && (upward_smem<R>(p, ksub) > kFusedSmem || downward_smem<R>(p, ksub) > kFusedSmem))
     --ksub;
   const int l0 = H - ksub;
-  {
+  if (sizeof(R) == 8) {
+    LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
+    size_t shp2m = sizeof(cd) * P1 * 33 * kWarpsPerBlock;
+    k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
+        lp, (const double *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cd *)M);
+  } else {
+    LeafPoints<float> lp{pl->loc32};
+    k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * P1, 256), 256, 0, st>>>(
+        lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cf *)M);
+  }
+  pass_end(pl, st, PASS_P2M, 1);
+  pass_begin(pl, st, PASS_M2M);
+  if (ksub > 0) {
     size_t sm = upward_smem<R>(p, ksub);
     unsigned nb = (unsigned)(int64_t(1) << (2 * l0));
     if (sizeof(R) == 8) {
@@ -1290,10 +1319,9 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
                                            pl->x0, pl->side, p, (const cf *)Tm2m, (cf *)M);
     }
   }
-  pass_end(pl, st, PASS_P2M, 1);
-  pass_begin(pl, st, PASS_M2M);
+
   if (l0 > 1) k_m2m_coarse<R><<<1, 1024, 0, st>>>(l0, p, Tm2m, M);
-  pass_end(pl, st, PASS_M2M, l0 > 1 ? 1 : 0);
+  pass_end(pl, st, PASS_M2M, (ksub > 0 ? 1 : 0) + (l0 > 1 ? 1 : 0));
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
