@@ -174,11 +174,18 @@ k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict_
   const double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
   const R invd = (R)(1.0 / d);
   const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-  cpx<R> acc = mk<R>(0, 0);
+  // compensated (Kahan) summation: the moments of a leaf are sums of up to
+  // hundreds of terms of both signs, and their rounding error is inherited
+  // by every far-field coefficient built from them
+  cpx<R> acc = mk<R>(0, 0), cmp = mk<R>(0, 0);
   for (int j = b0; j < b1; ++j) {
     R rx, ry;
     pts.rel(j, cx, cy, rx, ry);
-    cfma(acc, mk<R>(qs[j], 0), cpow_int(mk<R>(rx * invd, ry * invd), n));
+    const cpx<R> term = qs[j] * cpow_int(mk<R>(rx * invd, ry * invd), n);
+    const cpx<R> yv = term - cmp;
+    const cpx<R> tv = acc + yv;
+    cmp = (tv - acc) - yv;
+    acc = tv;
   }
   M[(size_t)(level_offset(H)) * P1 + t] = acc;
 }
@@ -455,10 +462,16 @@ __global__ void __launch_bounds__(128)
 k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
                  const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
                  cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
+  // rows padded to an even length PP so that k, k+1 pairs are one 16-byte
+  // (single precision) shared-memory load; the source patch is stored with
+  // even columns first, so that the sources of a warp's x-consecutive
+  // targets (all of one column parity) are consecutive boxes
+  constexpr int PP = (P1 + 1) & ~1;
+  constexpr int HALF = kPatchSrc / 2;
   extern __shared__ unsigned char smem_raw[];
-  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][P1][P1]
-  cpx<R> *Mp = Ts + 40 * P1 * P1;                          // [20*20][P1]
-  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * P1);  // [40] ln|t|
+  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][P1][PP]
+  cpx<R> *Mp = Ts + 40 * P1 * PP;                          // [20][20][PP]
+  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * PP);  // [40] ln|t d|
   // level and patch of this block
   int b = blockIdx.x, l = 2;
   for (; l <= H; ++l) {
@@ -469,36 +482,37 @@ k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
   }
   int npl = (1 << (l - 1)) / kPatch;
   npl = npl < 1 ? 1 : npl;
-  int px0 = (b % npl) * kPatch, py0 = (b / npl) * kPatch;  // first parent of the patch
-  int nparent_side = 1 << (l - 1), nside = 1 << l;
+  const int px0 = (b % npl) * kPatch, py0 = (b / npl) * kPatch;
+  const int nparent_side = 1 << (l - 1), nside = 1 << l;
   const int64_t off = level_offset(l);
-  const R logd = (R)log(side / (double)nside);
-  // stage tables and source patch
-  for (int e = threadIdx.x; e < 49 * P1 * P1; e += blockDim.x) {
-    int c = e / (P1 * P1), r = e % (P1 * P1);
-    int sl = c_slot[c];
-    if (sl >= 0) Ts[sl * P1 * P1 + r] = Tfree[e];
+  const R logd = (R)log(ldexp(side, -l));
+  for (int e = threadIdx.x; e < 49 * P1 * PP; e += blockDim.x) {
+    const int c = e / (P1 * PP), r = (e / PP) % P1, k = e % PP;
+    const int sl = c_slot[c];
+    if (sl >= 0) Ts[e - (c - sl) * P1 * PP] = (k < P1) ? Tfree[(size_t)c * P1 * P1 + r * P1 + k]
+                                                         : mk<R>(0, 0);
   }
   for (int c = threadIdx.x; c < 49; c += blockDim.x)
     if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
-  int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
-  for (int e = threadIdx.x; e < kPatchSrc * kPatchSrc * P1; e += blockDim.x) {
-    int sb = e / P1, k = e % P1;
-    int sx = sx0 + sb % kPatchSrc, sy = sy0 + sb / kPatchSrc;
+  const int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
+  for (int e = threadIdx.x; e < kPatchSrc * kPatchSrc * PP; e += blockDim.x) {
+    const int sb = e / PP, k = e % PP;
+    const int row = sb / kPatchSrc, colp = sb % kPatchSrc;  // colp: parity-split column
+    const int col = (colp < HALF) ? 2 * colp : 2 * (colp - HALF) + 1;
+    const int sx = sx0 + col, sy = sy0 + row;
     cpx<R> v = mk<R>(0, 0);
-    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside)
+    if (k < P1 && sx >= 0 && sy >= 0 && sx < nside && sy < nside)
       v = M[(size_t)(off + box_morton(sx, sy)) * P1 + k];
     Mp[e] = v;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = warp & 1, bb = warp >> 1;  // child type handled by this warp
-  // two targets per lane: parents (lane) and (lane + 32) of the 8x8 patch
-  int pxA = px0 + (lane & 7), pyA = py0 + (lane >> 3);
-  int pxB = pxA, pyB = pyA + 4;
-  bool vA = pxA < nparent_side && pyA < nparent_side;
-  bool vB = pxB < nparent_side && pyB < nparent_side;
-  int txA = 2 * pxA + a, tyA = 2 * pyA + bb, txB = 2 * pxB + a, tyB = 2 * pyB + bb;
+  const int pxA = px0 + (lane & 7), pyA = py0 + (lane >> 3);
+  const int pxB = pxA, pyB = pyA + 4;
+  const bool vA = pxA < nparent_side && pyA < nparent_side;
+  const bool vB = pxB < nparent_side && pyB < nparent_side;
+  const int txA = 2 * pxA + a, tyA = 2 * pyA + bb, txB = 2 * pxB + a, tyB = 2 * pyB + bb;
   cpx<R> accA[P1], accB[P1];
 #pragma unroll
   for (int r = 0; r < P1; ++r) {
@@ -508,40 +522,44 @@ k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
   for (int dy = -2 - bb; dy <= 3 - bb; ++dy) {
     for (int dx = -2 - a; dx <= 3 - a; ++dx) {
       if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-      int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
-      const cpx<R> *T = Ts + slot * P1 * P1;
-      const cpx<R> *mA = Mp + ((tyA + dy - sy0) * kPatchSrc + (txA + dx - sx0)) * P1;
-      const cpx<R> *mB = Mp + ((tyB + dy - sy0) * kPatchSrc + (txB + dx - sx0)) * P1;
-#pragma unroll 2
-      for (int k = 0; k < P1; ++k) {
-        cpx<R> ma = mA[k], mb = mB[k];
+      const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
+      const cpx<R> *T = Ts + slot * P1 * PP;
+      const int colA = txA + dx - sx0, colB = txB + dx - sx0;  // same parity
+      const int cpA = (colA & 1) * HALF + (colA >> 1), cpB = (colB & 1) * HALF + (colB >> 1);
+      const cpx<R> *mA = Mp + ((tyA + dy - sy0) * kPatchSrc + cpA) * PP;
+      const cpx<R> *mB = Mp + ((tyB + dy - sy0) * kPatchSrc + cpB) * PP;
+#pragma unroll 1
+      for (int k = 0; k < PP; k += 2) {
+        const cpx<R> ma0 = mA[k], ma1 = mA[k + 1], mb0 = mB[k], mb1 = mB[k + 1];
 #pragma unroll
         for (int r = 0; r < P1; ++r) {
-          cpx<R> t = T[r * P1 + k];
-          cfma(accA[r], t, ma);
-          cfma(accB[r], t, mb);
+          const cpx<R> t0 = T[r * PP + k], t1 = T[r * PP + k + 1];
+          cfma(accA[r], t0, ma0);
+          cfma(accA[r], t1, ma1);
+          cfma(accB[r], t0, mb0);
+          cfma(accB[r], t1, mb1);
         }
       }
-      R lgc = lg[slot];
+      const R lgc = lg[slot];
       accA[0].x += mA[0].x * lgc;  // M_0 ln|t d| (Re L_0 only)
       accB[0].x += mB[0].x * lgc;
     }
   }
   const R s = (R)(-0.5 / HP_TWO_PI);
   if (vA) {
-    size_t e0 = (size_t)(off + box_morton(txA, tyA)) * P1;
+    const size_t e0 = (size_t)(off + box_morton(txA, tyA)) * P1;
 #pragma unroll
     for (int r = 0; r < P1; ++r) {
-      cpx<R> v = s * accA[r];
+      const cpx<R> v = s * accA[r];
       A[e0 + r] = v;
       B[e0 + r] = conj(v);
     }
   }
   if (vB) {
-    size_t e0 = (size_t)(off + box_morton(txB, tyB)) * P1;
+    const size_t e0 = (size_t)(off + box_morton(txB, tyB)) * P1;
 #pragma unroll
     for (int r = 0; r < P1; ++r) {
-      cpx<R> v = s * accB[r];
+      const cpx<R> v = s * accB[r];
       A[e0 + r] = v;
       B[e0 + r] = conj(v);
     }
@@ -550,7 +568,8 @@ k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
 
 template <typename R, int P1>
 size_t patch_smem() {
-  return sizeof(cpx<R>) * (40 * P1 * P1 + kPatchSrc * kPatchSrc * P1) + sizeof(R) * 40;
+  constexpr int PP = (P1 + 1) & ~1;
+  return sizeof(cpx<R>) * (40 * P1 * PP + kPatchSrc * kPatchSrc * PP) + sizeof(R) * 40;
 }
 
 int patch_blocks(int H) {
@@ -1090,6 +1109,8 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
           double side, int p, cd kappa, float tau, const cf *__restrict__ A,
           const cf *__restrict__ B, double *__restrict__ pot, double *__restrict__ grad) {
   __shared__ float4 sbuf[kEvWarps][kEvBuf];
+  __shared__ int nb_s0[kEvWarps][9], nb_ex[kEvWarps][10];
+  __shared__ float nb_ox[kEvWarps][9], nb_oy[kEvWarps][9];
   const int P1 = p + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int leaf = blockIdx.x * kEvWarps + warp;
@@ -1106,6 +1127,29 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
   const int T = b1 - b0;
   const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
   const int ng = 32 / gs, g = lane / gs, tl = lane % gs;
+  // neighbour table: lane k < 9 looks up neighbour k = (ix-1 + k%3, iy-1 + k/3)
+  int cnt_k = 0;
+  if (lane < 9) {
+    const int mxx = ix - 1 + lane % 3, ny = iy - 1 + lane / 3;
+    int s0 = 0;
+    if (mxx >= 0 && mxx < nx && ny >= 0 && ny < nx) {
+      const uint64_t sl = box_morton(mxx, ny);
+      s0 = leaf_start[sl];
+      cnt_k = leaf_start[sl + 1] - s0;
+    }
+    nb_s0[warp][lane] = s0;
+    nb_ox[warp][lane] = (float)(mxx - ix) * d;
+    nb_oy[warp][lane] = (float)(ny - iy) * d;
+  }
+  int pre = cnt_k;
+  for (int o = 1; o < 16; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, pre, o);
+    if (lane >= o) pre += v;
+  }
+  if (lane < 9) nb_ex[warp][lane] = pre - cnt_k;
+  const int nsrc = __shfl_sync(0xffffffffu, pre, 8);
+  if (lane == 9) nb_ex[warp][9] = nsrc;
+  __syncwarp();
   for (int tb = b0; tb < b1; tb += gs) {
     const int i = tb + tl;
     const bool act = i < b1;
@@ -1113,33 +1157,23 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
     NearAcc acc;
     acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
     acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
-    // free part over the 3x3 neighbourhood
-    int fill = 0;
-    for (int ny = iy - 1; ny <= iy + 1; ++ny) {
-      if (ny < 0 || ny >= nx) continue;
-      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
-        if (mxx < 0 || mxx >= nx) continue;
-        const uint64_t sl = box_morton(mxx, ny);
-        const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-        const float ox = (float)(mxx - ix) * d, oy = (float)(ny - iy) * d;
-        for (int sb = s0; sb < s1; sb += 32) {
-          const int cnt = min(32, s1 - sb);
-          if (fill + cnt > kEvBuf) {
-            __syncwarp();
-            free_batch(buf, fill, g, ng, me.x, me.y, acc);
-            __syncwarp();
-            fill = 0;
-          }
-          if (lane < cnt) {
-            const float2 v = loc[sb + lane];
-            buf[fill + lane] = make_float4(v.x + ox, v.y + oy, qs[sb + lane], 0.f);
-          }
-          fill += cnt;
-        }
+    // free part over the 3x3 neighbourhood: the sources of the (up to 9)
+    // neighbour leaves are staged batch by batch, every lane loading its own
+    // entries of the concatenated list
+    for (int base = 0; base < nsrc; base += kEvBuf) {
+      const int cnt = min(kEvBuf, nsrc - base);
+      __syncwarp();
+      for (int e = lane; e < cnt; e += 32) {
+        const int f = base + e;
+        int k = 0;
+        while (k < 8 && f >= nb_ex[warp][k + 1]) ++k;
+        const int js = nb_s0[warp][k] + (f - nb_ex[warp][k]);
+        const float2 v = loc[js];
+        buf[e] = make_float4(v.x + nb_ox[warp][k], v.y + nb_oy[warp][k], qs[js], 0.f);
       }
+      __syncwarp();
+      free_batch(buf, cnt, g, ng, me.x, me.y, acc);
     }
-    __syncwarp();
-    free_batch(buf, fill, g, ng, me.x, me.y, acc);
     __syncwarp();
     // combine the groups
     acc.lf = xsum(acc.lf, gs);

@@ -105,16 +105,30 @@ bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo) {
 // it; when no integer lies within 4 ulp of s', both floors agree.  Otherwise
 // (a fraction ~1e-7 of the points) the exact division decides.
 __device__ __forceinline__ uint64_t quantise(double v, double L, double scale) {
-  double s = __dmul_rn(v, scale);
-  double u = 4.0 * ulp_of(s);
-  double f = floor(s);
-  if (!(floor(s - u) == f && floor(s + u) == f)) {
-    double q = __ddiv_rn(v, L);
-    f = floor(__dmul_rn(q, 1073741824.0));
+  const double s = __dmul_rn(v, scale);
+  // floor(s) and the distance of s to the nearest integers, in ulps of s,
+  // from the bit pattern (s >= 0, s < 2^31)
+  const long long b = __double_as_longlong(s);
+  const int E = (int)((b >> 52) & 0x7ff) - 1023;
+  bool safe;
+  uint64_t f;
+  if (E < 0) {  // s < 1
+    f = 0;
+    safe = s < 0.999999;
+  } else {
+    const uint64_t m = (uint64_t)(b & 0xfffffffffffffull) | (1ull << 52);
+    const int fb = 52 - E;  // fraction bits (>= 21 here)
+    f = m >> fb;
+    const uint64_t frac = m & ((1ull << fb) - 1);
+    safe = frac >= 4 && frac <= (1ull << fb) - 5;
   }
-  f = fmax(f, 0.0);
-  f = fmin(f, 1073741823.0);
-  return (uint64_t)f;
+  if (!safe) {
+    const double q = __ddiv_rn(v, L);
+    double fl = floor(__dmul_rn(q, 1073741824.0));
+    fl = fmax(fl, 0.0);
+    f = (uint64_t)fl;
+  }
+  return f > 1073741823ull ? 1073741823ull : f;
 }
 
 // keys, and the point count of each level-H leaf (the atomic's return value
@@ -223,12 +237,16 @@ __global__ void bucket_scatter(const uint64_t *__restrict__ keys, const int *__r
 // leaf, one element per lane, bitonic network over shuffles
 __global__ void __launch_bounds__(256)
 leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
-               int *__restrict__ vals) {
+               int *__restrict__ vals, int *__restrict__ big, int *__restrict__ nbig) {
   int lane = threadIdx.x & 31;
   int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (leaf >= nleaf) return;
   int b0 = start[leaf], m = start[leaf + 1] - b0;
-  if (m <= 1 || m > 32) return;
+  if (m > 32) {
+    if (lane == 0 && big) big[atomicAdd(nbig, 1)] = leaf;
+    return;
+  }
+  if (m <= 1) return;
   uint64_t k = lane < m ? keys[b0 + lane] : ~0ull;
   int v = lane < m ? vals[b0 + lane] : 0x7fffffff;
   for (int kk = 2; kk <= 32; kk <<= 1) {
@@ -253,11 +271,13 @@ leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ 
 // memory, one block per leaf (blocks skip the small leaves)
 constexpr int kLeafSort = 1024;
 __global__ void __launch_bounds__(256)
-leaf_sort(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
-          int *__restrict__ vals) {
+leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int *__restrict__ nbig,
+          uint64_t *__restrict__ keys, int *__restrict__ vals) {
   __shared__ uint64_t sk[kLeafSort];
   __shared__ int sv[kLeafSort];
-  for (int leaf = blockIdx.x; leaf < nleaf; leaf += gridDim.x) {
+  const int nb = *nbig;
+  for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+    const int leaf = big[bi];
     int b0 = start[leaf], b1 = start[leaf + 1], m = b1 - b0;
     if (m <= 32 || m > kLeafSort) continue;
     int np2 = 1;
@@ -450,7 +470,7 @@ struct TreeTmp {
   char *base = nullptr;
   Geom *part;
   uint64_t *kb;
-  int *va, *vb, *slot, *lcount, *btot, *bmax;
+  int *va, *vb, *slot, *lcount, *btot, *bmax, *big;
   unsigned *counts, *totals;
   int nbR, nblocks;
 };
@@ -464,9 +484,9 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
   t.nblocks = (int)((n + kTile - 1) / kTile);
   const int nsb = (nleaf + 1023) / 1024;
   size_t bytes = sizeof(Geom) * t.nbR + sizeof(uint64_t) * n + 4 * sizeof(int) * n +
-                 sizeof(int) * ((size_t)nleaf + 1) + 2 * sizeof(int) * nsb +
+                 sizeof(int) * (2 * (size_t)nleaf + 2) + 2 * sizeof(int) * nsb +
                  sizeof(unsigned) * 256 * ((size_t)t.nblocks + 1);
-  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 12 * 256, st));
+  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 13 * 256, st));
   char *c = t.base;
   auto carve = [&](size_t b) {
     char *r = c;
@@ -478,7 +498,8 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
   t.va = (int *)carve(sizeof(int) * n);
   t.vb = (int *)carve(sizeof(int) * n);
   t.slot = (int *)carve(sizeof(int) * n);
-  t.lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
+  t.lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));  // [nleaf] = big-leaf count
+  t.big = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
   t.btot = (int *)carve(sizeof(int) * nsb);
   t.bmax = (int *)carve(sizeof(int) * nsb);
   t.counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)t.nblocks);
@@ -530,8 +551,8 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   scan_add<<<nsb, 1024, 0, st>>>(t.btot, nleaf, pl->leaf_start);
   bucket_scatter<<<gb, tb, 0, st>>>(t.kb, t.slot, n, H, pl->leaf_start, pl->keys, t.vb);
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
-      pl->leaf_start, nleaf, pl->keys, t.vb);
-  leaf_sort<<<nleaf < 4096 ? nleaf : 4096, 256, 0, st>>>(pl->leaf_start, nleaf, pl->keys, t.vb);
+      pl->leaf_start, nleaf, pl->keys, t.vb, t.big, t.lcount + nleaf);
+  leaf_sort<<<160, 256, 0, st>>>(pl->leaf_start, t.big, t.lcount + nleaf, pl->keys, t.vb);
   gather_points<<<gb, tb, 0, st>>>(x, y, t.vb, pl->keys, n, H, geo, pl->xs, pl->ys, pl->perm,
                                    pl->loc32);
   pass_end(pl, st, PASS_TREE, 10);
