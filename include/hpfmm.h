@@ -179,6 +179,16 @@ hpfmm_status hpfmm_read_timing(hpfmm_plan *plan, double ms[10], int64_t launches
  * status (HPFMM_ETIMEOUT) recorded by its kernels. */
 hpfmm_status hpfmm_sync(hpfmm_plan *plan, void *stream);
 
+/*
+ * hpfmm_selftest_wait_timeout -- failure-path check of the library's bounded
+ * device waits (no counterpart in the paper): launches one kernel whose
+ * bulk-copy barrier can never complete, so its wait runs out of polls and the
+ * kernel records a timeout in a status word instead of hanging.  Returns
+ * HPFMM_ETIMEOUT when the timeout was reported (the expected outcome, after
+ * about a second), HPFMM_OK if the wait somehow completed.  Synchronises.
+ */
+hpfmm_status hpfmm_selftest_wait_timeout(void *stream);
+
 const char *hpfmm_status_string(hpfmm_status s);
 const char *hpfmm_last_error(void);
 

@@ -67,11 +67,13 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_get_order.argtypes = [vp, vp, vp, vp]
     L.hpfmm_sync.argtypes = [vp, vp]
     L.hpfmm_set_timing.argtypes = [vp, i32]
+    L.hpfmm_selftest_wait_timeout.argtypes = [vp]
     L.hpfmm_read_timing.argtypes = [vp, vp, vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
-              "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing"):
+              "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing",
+              "hpfmm_selftest_wait_timeout"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -247,6 +249,14 @@ def hpfmm_read_timing(plan):
 
 def hpfmm_sync(plan):
     _check(lib().hpfmm_sync(plan.handle, _stream(plan.device)))
+
+
+def hpfmm_selftest_wait_timeout(device=None):
+    """Run the bounded-wait failure self-test; returns the status code
+    (HPFMM_ETIMEOUT is the expected outcome)."""
+    import torch
+    dev = torch.device(device or "cuda:0")
+    return int(lib().hpfmm_selftest_wait_timeout(_stream(dev)))
 
 
 def hpfmm_version():

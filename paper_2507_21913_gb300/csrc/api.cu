@@ -137,7 +137,7 @@ static void free_plan(hpfmm_plan *pl) {
   void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
-                  pl->t_binom, pl->geo};
+                  pl->t_binom, pl->geo, pl->t_m2l_pad};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -282,6 +282,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);
+  if (f32) ALLOC(pl->t_m2l_pad, sizeof(cf) * 40 * (size_t)P1 * ((P1 + 1) & ~1));
   ALLOC(pl->t_rlog, tf * 21 * m2);
   ALLOC(pl->t_refl, tf * (size_t)pl->H * 42 * m2);
   ALLOC(pl->t_rlog0, sizeof(cd) * 70);

@@ -94,6 +94,54 @@ __host__ __device__ __forceinline__ cpx<R> to(cd z) {
 }
 
 // ---------------------------------------------------------------------------
+// Bulk (TMA) copies into shared memory tracked by an mbarrier.  Waits are
+// bounded: after kMbarSpin unsuccessful polls the caller records a timeout in
+// the plan's status word instead of spinning for ever.
+constexpr int kMbarSpin = 1 << 20;
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy: both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on phase `parity`; false when it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+  for (int it = 0; it < kMbarSpin; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+// device status bits (the plan's status word)
+enum { HPFMM_DEV_TIMEOUT = 1 };
+
+// ---------------------------------------------------------------------------
 // Morton geometry.  Key bit 2b holds bit b of ix, bit 2b+1 bit b of iy; the
 // level-l box of a point is key >> (60 - 2l), its Morton index within level l.
 __host__ __device__ __forceinline__ uint32_t compact1(uint64_t m) {
@@ -149,6 +197,7 @@ struct hpfmm_plan {
   void *t_m2m = nullptr;   // 4 x (p+1)^2 complex: child c -> parent
   void *t_l2l = nullptr;   // 4 x (p+1)^2 complex: parent -> child c (analytic part)
   void *t_m2l = nullptr;   // 49 offset classes x (p+1)^2 complex: free-space log M2L
+  void *t_m2l_pad = nullptr;  // FP32 path: the 40 far classes, rows padded to even length
   void *t_refl = nullptr;  // per level: 7 x 3 classes x (2p+1) complex: scaled I_k tables
   void *t_rlog = nullptr;  // per level: 7 x 3 classes x (p+1)^2 complex: image-log M2L
   void *t_rlog0 = nullptr;    // logs of the 49 free and 21 image class displacements

@@ -459,16 +459,17 @@ __constant__ signed char c_slot[49];      // 7x7 offset class -> 0..39, -1 for t
 
 template <typename R, int P1>
 __global__ void __launch_bounds__(128)
-k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
+k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tpad,
                  const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
-                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
+                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status) {
   // rows padded to an even length PP so that k, k+1 pairs are one 16-byte
   // (single precision) shared-memory load; the source patch is stored with
   // even columns first, so that the sources of a warp's x-consecutive
   // targets (all of one column parity) are consecutive boxes
   constexpr int PP = (P1 + 1) & ~1;
   constexpr int HALF = kPatchSrc / 2;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
   cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][P1][PP]
   cpx<R> *Mp = Ts + 40 * P1 * PP;                          // [20][20][PP]
   R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * PP);  // [40] ln|t d|
@@ -486,24 +487,40 @@ k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tfree,
   const int nparent_side = 1 << (l - 1), nside = 1 << l;
   const int64_t off = level_offset(l);
   const R logd = (R)log(ldexp(side, -l));
-  for (int e = threadIdx.x; e < 49 * P1 * PP; e += blockDim.x) {
-    const int c = e / (P1 * PP), r = (e / PP) % P1, k = e % PP;
-    const int sl = c_slot[c];
-    if (sl >= 0) Ts[e - (c - sl) * P1 * PP] = (k < P1) ? Tfree[(size_t)c * P1 * P1 + r * P1 + k]
-                                                         : mk<R>(0, 0);
+  // the 40 translation matrices: one bulk copy (TMA) from the padded table
+  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * P1 * PP);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, tbytes);
+    bulk_g2s(Ts, Tpad, tbytes, &bar);
   }
   for (int c = threadIdx.x; c < 49; c += blockDim.x)
     if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
+  // source patch: one box per thread and iteration, P1 independent loads each
   const int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
-  for (int e = threadIdx.x; e < kPatchSrc * kPatchSrc * PP; e += blockDim.x) {
-    const int sb = e / PP, k = e % PP;
+  for (int sb = threadIdx.x; sb < kPatchSrc * kPatchSrc; sb += blockDim.x) {
     const int row = sb / kPatchSrc, colp = sb % kPatchSrc;  // colp: parity-split column
     const int col = (colp < HALF) ? 2 * colp : 2 * (colp - HALF) + 1;
     const int sx = sx0 + col, sy = sy0 + row;
-    cpx<R> v = mk<R>(0, 0);
-    if (k < P1 && sx >= 0 && sy >= 0 && sx < nside && sy < nside)
-      v = M[(size_t)(off + box_morton(sx, sy)) * P1 + k];
-    Mp[e] = v;
+    cpx<R> *dst = Mp + (size_t)sb * PP;
+    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
+      const cpx<R> *src = M + (size_t)(off + box_morton(sx, sy)) * P1;
+      cpx<R> v[P1];
+#pragma unroll
+      for (int k = 0; k < P1; ++k) v[k] = src[k];
+#pragma unroll
+      for (int k = 0; k < P1; ++k) dst[k] = v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < P1; ++k) dst[k] = mk<R>(0, 0);
+    }
+    if (PP > P1) dst[PP - 1] = mk<R>(0, 0);
+  }
+  __syncthreads();  // also publishes the mbarrier initialisation
+  if (!mbar_wait_bounded(&bar, 0)) {
+    if (threadIdx.x == 0) atomicOr(status, HPFMM_DEV_TIMEOUT);
+    mbar_wait_bounded(&bar, 0);  // give the copy a second bounded chance to land
+    return;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -585,8 +602,9 @@ int patch_blocks(int H) {
 // dispatch on the (compile-time) order; returns false when no patch kernel
 // exists for this order / precision or it does not fit in shared memory
 template <typename R>
-bool launch_m2l_patch(int p, int H, double side, const cpx<R> *Tfree, const cd *logt,
-                      const cpx<R> *M, cpx<R> *A, cpx<R> *B, cudaStream_t st) {
+bool launch_m2l_patch(int p, int H, double side, const cpx<R> *Tpad, const cd *logt,
+                      const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st) {
+  if (!Tpad) return false;
   int nb = patch_blocks(H);
 #define HP_PATCH_CASE(PP)                                                                 \
   case PP: {                                                                              \
@@ -598,7 +616,7 @@ bool launch_m2l_patch(int p, int H, double side, const cpx<R> *Tfree, const cd *
       cudaGetLastError();                                                                 \
       return false;                                                                       \
     }                                                                                     \
-    k_m2l_free_patch<R, PP + 1><<<nb, 128, sm, st>>>(H, side, Tfree, logt, M, A, B);      \
+    k_m2l_free_patch<R, PP + 1><<<nb, 128, sm, st>>>(H, side, Tpad, logt, M, A, B, status); \
     return true;                                                                          \
   }
   switch (p) {
@@ -902,6 +920,22 @@ __device__ __forceinline__ float fast_rcp(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+__device__ __forceinline__ float fast_lg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// float -> double by re-biasing the exponent with integer operations (the
+// FP64 conversion instruction runs on GB300's narrow FP64 pipe); denormal
+// single-precision inputs become 0, infinities and NaNs are kept
+__device__ __forceinline__ double f2d(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned long long r = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0xffu) r |= (0x7ffull << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  else if (e != 0) r |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)r);
+}
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_eval32(const float2 *__restrict__ loc, const float *__restrict__ qs,
@@ -1039,25 +1073,52 @@ struct NearAcc {
   cf ur, grx, gry;                  // reaction (pairs evaluated in single or double)
 };
 
-__device__ __forceinline__ void free_batch(const float4 *buf, int cnt, int g, int ng, float mx,
-                                           float my, NearAcc &a) {
-  float lf = 0.f, gx = 0.f, gy = 0.f;
+// sum over the staged sources [lo, hi) taken by group g of NG; CHECK: the
+// range may contain the target itself (r^2 = 0 is then skipped)
+template <int NG, bool CHECK>
+__device__ __forceinline__ void free_range(const float4 *buf, int lo, int hi, int g, float mx,
+                                           float my, float &lf, float &gx, float &gy) {
 #pragma unroll 4
-  for (int k = g; k < cnt; k += ng) {
-    float4 s = buf[k];
-    float dx = mx - s.x, dy = my - s.y;
+  for (int k = lo + g; k < hi; k += NG) {
+    const float4 s = buf[k];
+    const float dx = mx - s.x, dy = my - s.y;
     float r2 = fmaf(dx, dx, dy * dy);
-    bool ok = r2 > 0.f;
-    float q = ok ? s.z : 0.f;
-    r2 = ok ? r2 : 1.f;
-    float qi = q * fast_rcp(r2);
-    lf = fmaf(q, __log2f(r2), lf);
+    float q = s.z;
+    if (CHECK) {
+      const bool ok = r2 > 0.f;
+      q = ok ? q : 0.f;
+      r2 = ok ? r2 : 1.f;
+    }
+    const float qi = q * fast_rcp(r2);
+    lf = fmaf(q, fast_lg2(r2), lf);
     gx = fmaf(qi, dx, gx);
     gy = fmaf(qi, dy, gy);
   }
+}
+
+template <int NG>
+__device__ __forceinline__ void free_batch_t(const float4 *buf, int cnt, int g, int slo, int shi,
+                                             float mx, float my, NearAcc &a) {
+  float lf = 0.f, gx = 0.f, gy = 0.f;
+  slo = max(0, min(slo, cnt));
+  shi = max(slo, min(shi, cnt));
+  // each of the three ranges is split over the NG groups on its own
+  free_range<NG, false>(buf, 0, slo, g, mx, my, lf, gx, gy);
+  free_range<NG, true>(buf, slo, shi, g, mx, my, lf, gx, gy);
+  free_range<NG, false>(buf, shi, cnt, g, mx, my, lf, gx, gy);
   a.lf += lf;
   a.gx += gx;
   a.gy += gy;
+}
+
+__device__ __forceinline__ void free_batch(const float4 *buf, int cnt, int g, int ng, int slo,
+                                           int shi, float mx, float my, NearAcc &a) {
+  switch (ng) {
+    case 1: free_batch_t<1>(buf, cnt, g, slo, shi, mx, my, a); break;
+    case 2: free_batch_t<2>(buf, cnt, g, slo, shi, mx, my, a); break;
+    case 4: free_batch_t<4>(buf, cnt, g, slo, shi, mx, my, a); break;
+    default: free_batch_t<8>(buf, cnt, g, slo, shi, mx, my, a); break;
+  }
 }
 
 __device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, int ng, float mx,
@@ -1172,7 +1233,8 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
         buf[e] = make_float4(v.x + nb_ox[warp][k], v.y + nb_oy[warp][k], qs[js], 0.f);
       }
       __syncwarp();
-      free_batch(buf, cnt, g, ng, me.x, me.y, acc);
+      // the target's own leaf is neighbour 4: only its range needs the j != i test
+      free_batch(buf, cnt, g, ng, nb_ex[warp][4] - base, nb_ex[warp][5] - base, me.x, me.y, acc);
     }
     __syncwarp();
     // combine the groups
@@ -1197,12 +1259,11 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
     const float ui_ = va.y + vb.y;
     const cf gx = invd * (da + db) + mk(-acc.gx * i2pi, 0.f);
     const cf gy = invd * (mul_i(da) - mul_i(db)) + mk(-acc.gy * i2pi, 0.f);
-    const cd u = mk((double)ur_, (double)ui_);
     const int64_t o = perm[i];
-    reinterpret_cast<double2 *>(pot)[o] = make_double2(u.x, u.y);
+    reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
     if (grad) {
       double4 gv;
-      gv.x = (double)gx.x; gv.y = (double)gx.y; gv.z = (double)gy.x; gv.w = (double)gy.y;
+      gv.x = f2d(gx.x); gv.y = f2d(gx.y); gv.z = f2d(gy.x); gv.w = f2d(gy.y);
       reinterpret_cast<double4 *>(grad)[o] = gv;
     }
   }
@@ -1363,7 +1424,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   bool patched = false;
   if (H >= 2 && sizeof(R) == 4) {
     pass_begin(pl, st, PASS_M2L_FREE);
-    patched = launch_m2l_patch<R>(p, H, pl->side, Tfree, logs, M, A, B, st);
+    patched = launch_m2l_patch<R>(p, H, pl->side, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
+                                  pl->status, st);
     pass_end(pl, st, PASS_M2L_FREE, patched ? 1 : 0);
   }
   for (int l = 1; l <= H; ++l) {

@@ -158,6 +158,23 @@ __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd 
   }
 }
 
+// the 40 far offset classes of the free-space M2L, single precision, rows
+// padded with zeros to an even length (layout of the patch M2L kernel)
+__global__ void k_m2l_pad(int p, const cd *T, cf *out) {
+  const int P1 = p + 1, PP = (P1 + 1) & ~1;
+  int slot = 0;
+  for (int c = 0; c < 49; ++c) {
+    const int dx = c % 7 - 3, dy = c / 7 - 3;
+    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+    for (int e = threadIdx.x; e < P1 * PP; e += blockDim.x) {
+      const int r = e / PP, k = e % PP;
+      out[(size_t)slot * P1 * PP + e] =
+          k < P1 ? to<float>(T[(size_t)c * P1 * P1 + r * P1 + k]) : mk(0.f, 0.f);
+    }
+    ++slot;
+  }
+}
+
 __global__ void k_to_float(const cd *a, cf *b, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
@@ -186,6 +203,7 @@ hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
                                                {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2}};
     for (auto &e : t)
       k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
+    if (pl->t_m2l_pad) k_m2l_pad<<<1, 256, 0, st>>>(p, fm2l, (cf *)pl->t_m2l_pad);
     HP_LAUNCH_CHECK();
   }
   return HPFMM_OK;
