@@ -1269,6 +1269,169 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
   }
 }
 
+// Tiled form of the single-precision leaf evaluation.  A block owns a 4 x 4
+// tile of target leaves and stages the points of the surrounding 6 x 6 leaves
+// once in shared memory, in their own leaf-centred coordinates; the target
+// leaf of a warp then sums over its 9 neighbours as 9 contiguous ranges of
+// the staged array, shifting the target position by the exact leaf offset
+// once per range.  Blocks whose patch exceeds the staging buffer use the
+// per-warp path of k_eval32g.
+constexpr int kTl = 4;             // target leaves per tile side
+constexpr int kTlP = kTl + 2;      // patch leaves per side
+constexpr int kTlCap = 3072;       // staged points per block
+
+template <int NG>
+__device__ __forceinline__ void tile_ranges(const float4 *src, const int *pst, int pi0, int g,
+                                            float mx, float my, float d, float &lf, float &gx,
+                                            float &gy) {
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      const int pi = pi0 + r * kTlP + c;
+      const float ox = (float)(c - 1) * d, oy = (float)(r - 1) * d;
+      // sources are in their own leaf frame: shift the target instead
+      const float sx = mx - ox, sy = my - oy;
+      if (r == 1 && c == 1)
+        free_range<NG, true>(src, pst[pi], pst[pi + 1], g, sx, sy, lf, gx, gy);
+      else
+        free_range<NG, false>(src, pst[pi], pst[pi + 1], g, sx, sy, lf, gx, gy);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kEvWarps * 32, 3)
+k_eval32t(const float2 *__restrict__ loc, const float *__restrict__ qs,
+          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
+          double side, int p, const cf *__restrict__ A, const cf *__restrict__ B,
+          double *__restrict__ pot, double *__restrict__ grad) {
+  __shared__ float4 src[kTlCap];
+  __shared__ int pst[kTlP * kTlP + 1];
+  __shared__ int pbeg[kTlP * kTlP];
+  const int P1 = p + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = 1 << H;
+  const int tps = nx >= kTl ? nx / kTl : 1;
+  const int tx0 = (blockIdx.x % tps) * kTl, ty0 = (blockIdx.x / tps) * kTl;
+  const float d = (float)ldexp(side, -H);
+  const float invd = (float)((double)nx / side);
+  // patch leaf counts and prefix (warp 0)
+  if (warp == 0) {
+    int c0 = 0, c1 = 0;
+    for (int h = 0; h < 2; ++h) {
+      const int pi = lane + 32 * h;
+      if (pi < kTlP * kTlP) {
+        const int lx = tx0 - 1 + pi % kTlP, ly = ty0 - 1 + pi / kTlP;
+        int b0 = 0, cnt = 0;
+        if (lx >= 0 && ly >= 0 && lx < nx && ly < nx) {
+          const uint64_t lf = box_morton(lx, ly);
+          b0 = leaf_start[lf];
+          cnt = leaf_start[lf + 1] - b0;
+        }
+        pbeg[pi] = b0;
+        if (h == 0) c0 = cnt; else c1 = cnt;
+      }
+    }
+    int i0 = c0, i1 = c1;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
+      if (lane >= o) { i0 += a0; i1 += a1; }
+    }
+    const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
+    pst[lane] = i0 - c0;
+    if (lane + 32 < kTlP * kTlP) pst[lane + 32] = tot0 + i1 - c1;
+    if (lane == kTlP * kTlP - 32 - 1) pst[kTlP * kTlP] = tot0 + i1;
+  }
+  __syncthreads();
+  const int total = pst[kTlP * kTlP];
+  const bool staged = total <= kTlCap;
+  if (staged) {
+    for (int pi = warp; pi < kTlP * kTlP; pi += kEvWarps) {
+      const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
+      for (int j = lane; j < cnt; j += 32) {
+        const float2 v = loc[b0 + j];
+        src[o + j] = make_float4(v.x, v.y, qs[b0 + j], 0.f);
+      }
+    }
+  }
+  __syncthreads();
+  for (int tl = warp; tl < kTl * kTl; tl += kEvWarps) {
+    const int ix = tx0 + tl % kTl, iy = ty0 + tl / kTl;
+    if (ix >= nx || iy >= nx) continue;
+    const uint64_t leaf = box_morton(ix, iy);
+    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    const int T = b1 - b0;
+    const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
+    const int ng = 32 / gs, g = lane / gs, tli = lane % gs;
+    const int pi0 = (iy - ty0) * kTlP + (ix - tx0);  // patch index of the (-1, -1) neighbour
+    const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+    const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+    for (int tb = b0; tb < b1; tb += gs) {
+      const int i = tb + tli;
+      const bool act = i < b1;
+      const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+      float lf = 0.f, gx = 0.f, gy = 0.f;
+      if (staged) {
+        switch (ng) {
+          case 1: tile_ranges<1>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
+          case 2: tile_ranges<2>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
+          case 4: tile_ranges<4>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
+          default: tile_ranges<8>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
+        }
+      } else {
+        // patch too large for the buffer: read the sources from global memory
+        for (int r = 0; r < 3; ++r) {
+          for (int c = 0; c < 3; ++c) {
+            const int mx = ix - 1 + c, my = iy - 1 + r;
+            if (mx < 0 || my < 0 || mx >= nx || my >= nx) continue;
+            const uint64_t sl = box_morton(mx, my);
+            const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+            const float sx = me.x - (float)(c - 1) * d, sy = me.y - (float)(r - 1) * d;
+            for (int k = s0 + g; k < s1; k += ng) {
+              const float2 v = loc[k];
+              const float dx = sx - v.x, dy = sy - v.y;
+              float r2 = fmaf(dx, dx, dy * dy);
+              float q = qs[k];
+              const bool ok = r2 > 0.f;
+              q = ok ? q : 0.f;
+              r2 = ok ? r2 : 1.f;
+              const float qi = q * fast_rcp(r2);
+              lf = fmaf(q, fast_lg2(r2), lf);
+              gx = fmaf(qi, dx, gx);
+              gy = fmaf(qi, dy, gy);
+            }
+          }
+        }
+      }
+      lf = xsum(lf, gs);
+      gx = xsum(gx, gs);
+      gy = xsum(gy, gs);
+      if (!act || g != 0) continue;
+      cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
+      cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
+      for (int n = p - 1; n >= 0; --n) {
+        da = da * w + va;
+        va = va * w + Al[n];
+        db = db * wb + vb;
+        vb = vb * wb + Bl[n];
+      }
+      const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+      const float i2pi = (float)(1.0 / HP_TWO_PI);
+      const float ur_ = va.x + vb.x - lf * c4;
+      const float ui_ = va.y + vb.y;
+      const cf gxo = invd * (da + db) + mk(-gx * i2pi, 0.f);
+      const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-gy * i2pi, 0.f);
+      const int64_t o = perm[i];
+      reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
+      if (grad) {
+        double4 gv;
+        gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
+        reinterpret_cast<double4 *>(grad)[o] = gv;
+      }
+    }
+  }
+}
+
 // Image and reaction near field of the bottom-row leaves (single precision
 // with the double routine for |P| > 1 and, in MIXED mode, below tau), added
 // to the outputs written by k_eval32g.  One block per bottom-row leaf: the
@@ -1460,9 +1623,12 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         kappa, (const cd *)A, (const cd *)B, pot, grad);
   } else {
     float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
-    k_eval32g<<<cdiv_u(pl->nleaf, kEvWarps), 32 * kEvWarps, 0, st>>>(
-        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p, kappa, tau,
-        (const cf *)A, (const cf *)B, pot, grad);
+    {
+      const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
+      k_eval32t<<<(unsigned)(tps * tps), 32 * kEvWarps, 0, st>>>(
+          pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p,
+          (const cf *)A, (const cf *)B, pot, grad);
+    }
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
     k_mirror32<<<(unsigned)(1 << H), 32 * kEvWarps, 0, st>>>(

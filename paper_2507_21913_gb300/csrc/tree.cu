@@ -233,41 +233,91 @@ __global__ void bucket_scatter(const uint64_t *__restrict__ keys, const int *__r
   vout[pos] = (int)i;
 }
 
-// sort the leaf buckets of at most 32 points by (key, index): one warp per
-// leaf, one element per lane, bitonic network over shuffles
+// sort the leaf buckets of at most 128 points by (key, index): one warp per
+// leaf, E = 1, 2 or 4 elements per lane (element i = e * 32 + lane), bitonic
+// network with shuffles for partner distances < 32 and register swaps above
+__device__ __forceinline__ bool kv_less(uint64_t ka, int va, uint64_t kb, int vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+__device__ __forceinline__ void kv_cas(uint64_t &ka, int &va, uint64_t &kb, int &vb, bool asc) {
+  // after the call (ka, va) <= (kb, vb) when asc, >= otherwise
+  const bool gt = kv_less(kb, vb, ka, va);
+  if (gt == asc) {
+    uint64_t tk = ka; ka = kb; kb = tk;
+    int tv = va; va = vb; vb = tv;
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&k)[E], int (&v)[E], int lane) {
+  constexpr int N = 32 * E;
+  for (int kk = 2; kk <= N; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j < 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[e], j);
+          const int ov = __shfl_xor_sync(0xffffffffu, v[e], j);
+          const int i = e * 32 + lane;
+          const bool self_less = kv_less(k[e], v[e], ok, ov);
+          const bool want_min = ((i & j) == 0) == ((i & kk) == 0);
+          if (want_min != self_less) {
+            k[e] = ok;
+            v[e] = ov;
+          }
+        }
+      } else if (E >= 2 && j == 32) {
+#pragma unroll
+        for (int e = 0; e < E; e += 2)
+          kv_cas(k[e], v[e], k[e + 1], v[e + 1], ((e * 32 + lane) & kk) == 0);
+      } else if (E >= 4 && j == 64) {
+        kv_cas(k[0], v[0], k[2 % E], v[2 % E], (lane & kk) == 0);
+        kv_cas(k[1 % E], v[1 % E], k[3 % E], v[3 % E], ((32 + lane) & kk) == 0);
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_leaf(int b0, int m, int lane, uint64_t *keys,
+                                               int *vals) {
+  uint64_t k[E];
+  int v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * 32 + lane;
+    k[e] = i < m ? keys[b0 + i] : ~0ull;
+    v[e] = i < m ? vals[b0 + i] : 0x7fffffff;
+  }
+  warp_bitonic<E>(k, v, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * 32 + lane;
+    if (i < m) {
+      keys[b0 + i] = k[e];
+      vals[b0 + i] = v[e];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256)
 leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
                int *__restrict__ vals, int *__restrict__ big, int *__restrict__ nbig) {
-  int lane = threadIdx.x & 31;
-  int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (leaf >= nleaf) return;
-  int b0 = start[leaf], m = start[leaf + 1] - b0;
-  if (m > 32) {
+  const int b0 = start[leaf], m = start[leaf + 1] - b0;
+  if (m > 128) {
     if (lane == 0 && big) big[atomicAdd(nbig, 1)] = leaf;
     return;
   }
   if (m <= 1) return;
-  uint64_t k = lane < m ? keys[b0 + lane] : ~0ull;
-  int v = lane < m ? vals[b0 + lane] : 0x7fffffff;
-  for (int kk = 2; kk <= 32; kk <<= 1) {
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      uint64_t ok = __shfl_xor_sync(0xffffffffu, k, j);
-      int ov = __shfl_xor_sync(0xffffffffu, v, j);
-      bool self_less = k < ok || (k == ok && v < ov);
-      bool want_min = ((lane & j) == 0) == ((lane & kk) == 0);
-      if (want_min != self_less) {
-        k = ok;
-        v = ov;
-      }
-    }
-  }
-  if (lane < m) {
-    keys[b0 + lane] = k;
-    vals[b0 + lane] = v;
-  }
+  if (m <= 32) warp_sort_leaf<1>(b0, m, lane, keys, vals);
+  else if (m <= 64) warp_sort_leaf<2>(b0, m, lane, keys, vals);
+  else warp_sort_leaf<4>(b0, m, lane, keys, vals);
 }
 
-// sort the leaf buckets of 33..kLeafSort points: bitonic sort in shared
+// sort the leaf buckets of 129..kLeafSort points: bitonic sort in shared
 // memory, one block per leaf (blocks skip the small leaves)
 constexpr int kLeafSort = 1024;
 __global__ void __launch_bounds__(256)
@@ -279,7 +329,7 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
   for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {
     const int leaf = big[bi];
     int b0 = start[leaf], b1 = start[leaf + 1], m = b1 - b0;
-    if (m <= 32 || m > kLeafSort) continue;
+    if (m <= 128 || m > kLeafSort) continue;
     int np2 = 1;
     while (np2 < m) np2 <<= 1;
     __syncthreads();
