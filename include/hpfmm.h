@@ -180,6 +180,29 @@ hpfmm_status hpfmm_read_timing(hpfmm_plan *plan, double ms[10], int64_t launches
 hpfmm_status hpfmm_sync(hpfmm_plan *plan, void *stream);
 
 /*
+ * hpfmm_tree_order_noalloc -- the tree ordering of hpfmm_get_order (sorted
+ * 60-bit Morton keys and the permutation to the caller's order) computed
+ * without any device allocation, for callers that cannot allocate device
+ * memory (for example inside a stream capture that must stay free of
+ * allocations, or under a runtime that owns every allocation).  The paper has
+ * no counterpart: this is a service entry point of the library.
+ *   x, y   : n doubles each, DEVICE memory, y > 0, finite.
+ *   n      : 1 <= n <= 65536 (larger n is rejected with HPFMM_EINVAL).
+ *   levels : leaf level used to bucket the points, 1..8 (the result does not
+ *            depend on it).
+ *   keys   : n uint64, perm: n int64, DEVICE memory, written in tree order.
+ * All temporaries live in one static device array of 2.5 MiB that every GPU
+ * holding the library keeps until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call before any stream capture.  Every call reuses the same
+ * array: calls that overlap on the GPU (several streams, several threads)
+ * race and must be serialised by the caller.  Synchronises the stream (the
+ * validity check is reported synchronously).
+ */
+hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *y, int64_t n, int levels,
+                                      uint64_t *keys, int64_t *perm, void *stream);
+
+/*
  * hpfmm_selftest_wait_timeout -- failure-path check of the library's bounded
  * device waits (no counterpart in the paper): launches one kernel whose
  * bulk-copy barrier can never complete, so its wait runs out of polls and the

@@ -68,12 +68,13 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_sync.argtypes = [vp, vp]
     L.hpfmm_set_timing.argtypes = [vp, i32]
     L.hpfmm_selftest_wait_timeout.argtypes = [vp]
+    L.hpfmm_tree_order_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
     L.hpfmm_read_timing.argtypes = [vp, vp, vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
               "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing",
-              "hpfmm_selftest_wait_timeout"):
+              "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -257,6 +258,19 @@ def hpfmm_selftest_wait_timeout(device=None):
     import torch
     dev = torch.device(device or "cuda:0")
     return int(lib().hpfmm_selftest_wait_timeout(_stream(dev)))
+
+
+def hpfmm_tree_order_noalloc(x, y, levels=5):
+    """Tree ordering (sorted keys, permutation) without device allocations by the
+    library (n <= 65536, device tensors); see include/hpfmm.h."""
+    import torch
+    x = _as_tensor(x)
+    y = _as_tensor(y, x.device)
+    keys = torch.empty(x.numel(), dtype=torch.int64, device=x.device)
+    perm = torch.empty(x.numel(), dtype=torch.int64, device=x.device)
+    _check(lib().hpfmm_tree_order_noalloc(x.data_ptr(), y.data_ptr(), x.numel(), int(levels),
+                                          keys.data_ptr(), perm.data_ptr(), _stream(x.device)))
+    return keys.cpu().numpy().view(np.uint64), perm.cpu().numpy()
 
 
 def hpfmm_version():

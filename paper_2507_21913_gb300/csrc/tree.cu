@@ -9,6 +9,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace {
@@ -642,4 +644,138 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const
   if (pl->tree_tmp) cudaFreeAsync(pl->tree_tmp, st);
   pl->tree_tmp = nullptr;
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the tree ordering, for callers that cannot call
+// cudaMalloc (for example code running inside a CUDA-graph capture that must
+// not allocate, or an embedding runtime that owns every device allocation and
+// forbids others).  It runs the same kernels as tree_build on up to
+// kNoAllocMaxN points, with every temporary carved from one file-scope device
+// array of kNoAllocBytes.  That array is part of the library image, so every
+// GPU on which the library is loaded holds it until the process exits.
+namespace {
+constexpr int64_t kNoAllocMaxN = 65536;
+constexpr int kNoAllocMaxLevels = 8;
+constexpr size_t kNoAllocBytes = (size_t)2560 * 1024;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void write_perm(const int *__restrict__ v, int64_t n, int64_t *__restrict__ perm) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) perm[k] = v[k];
+}
+
+// device address of g_noalloc_scratch on the current device (host code only
+// sees a host-side stand-in for the symbol); looked up once per device
+void *noalloc_scratch_address() {
+  static std::mutex mu;
+  static void *addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+}  // namespace
+
+extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *y, int64_t n,
+                                                 int levels, uint64_t *keys, int64_t *perm,
+                                                 void *stream) {
+  if (!x || !y || !keys || !perm || n < 1) {
+    set_last_error("hpfmm_tree_order_noalloc: null pointer or n < 1");
+    return HPFMM_EINVAL;
+  }
+  if (n > kNoAllocMaxN || levels < 1 || levels > kNoAllocMaxLevels) {
+    set_last_error("hpfmm_tree_order_noalloc: needs n <= %lld and 1 <= levels <= %d "
+                   "(got n = %lld, levels = %d)",
+                   (long long)kNoAllocMaxN, kNoAllocMaxLevels, (long long)n, levels);
+    return HPFMM_EINVAL;
+  }
+  if (!is_device_pointer(x) || !is_device_pointer(y) || !is_device_pointer(keys) ||
+      !is_device_pointer(perm)) {
+    set_last_error("hpfmm_tree_order_noalloc: x, y, keys and perm must be device memory");
+    return HPFMM_EINVAL;
+  }
+  char *base = (char *)noalloc_scratch_address();
+  if (!base) {
+    set_last_error("hpfmm_tree_order_noalloc: cannot resolve the scratch array's device address");
+    return HPFMM_ECUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int H = levels, nleaf = 1 << (2 * H);
+  const int nbR = (int)((n + kRedThreads - 1) / kRedThreads);
+  const int nblocks = (int)((n + kTile - 1) / kTile);
+  const int nsb = (nleaf + 1023) / 1024;
+  char *c = base;
+  auto carve = [&](size_t b) {
+    char *r = c;
+    c += (b + 255) & ~size_t(255);
+    return r;
+  };
+  Geom *part = (Geom *)carve(sizeof(Geom) * nbR);
+  double *geo = (double *)carve(8 * sizeof(double));
+  uint64_t *kb = (uint64_t *)carve(sizeof(uint64_t) * n);
+  int *va = (int *)carve(sizeof(int) * n);
+  int *vb = (int *)carve(sizeof(int) * n);
+  int *slot = (int *)carve(sizeof(int) * n);
+  int *lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));  // [nleaf]: big-leaf count
+  int *big = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
+  int *lstart = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
+  int *btot = (int *)carve(sizeof(int) * nsb);
+  int *bmax = (int *)carve(sizeof(int) * nsb);
+  unsigned *counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)nblocks);
+  unsigned *totals = (unsigned *)carve(sizeof(unsigned) * 256);
+  if ((size_t)(c - base) > kNoAllocBytes) {
+    set_last_error("hpfmm_tree_order_noalloc: scratch layout exceeds %zu bytes", kNoAllocBytes);
+    return HPFMM_EUNSUPPORTED;
+  }
+  const unsigned gb = (unsigned)((n + 255) / 256);
+  // the array keeps the previous call's contents: clear what must start at 0
+  HP_CUDA(cudaMemsetAsync(lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st));
+  bbox_partial<<<nbR, kRedThreads, 0, st>>>(x, y, n, part);
+  bbox_final<<<1, kRedThreads, 0, st>>>(part, nbR, geo);
+  morton_keys<<<gb, 256, 0, st>>>(x, y, n, geo, H, kb, va, lcount, slot);
+  scan_part<<<nsb, 1024, 0, st>>>(lcount, nleaf, lstart, btot, bmax);
+  scan_top<<<1, 1024, 0, st>>>(btot, bmax, nsb, nleaf, lstart, (int *)(geo + 4));
+  scan_add<<<nsb, 1024, 0, st>>>(btot, nleaf, lstart);
+  bucket_scatter<<<gb, 256, 0, st>>>(kb, slot, n, H, lstart, keys, vb);
+  leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
+      lstart, nleaf, keys, vb, big, lcount + nleaf);
+  leaf_sort<<<160, 256, 0, st>>>(lstart, big, lcount + nleaf, keys, vb);
+  HP_LAUNCH_CHECK();
+  double hgeo[5];
+  HP_CUDA(cudaMemcpyAsync(hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  if (hgeo[2] != 0.0) {
+    set_last_error("hpfmm_tree_order_noalloc: points must be finite with y > 0");
+    return HPFMM_EINVAL;
+  }
+  int hmax = 0;
+  memcpy(&hmax, &hgeo[4], sizeof(int));
+  const int *sorted = vb;
+  if (hmax > kLeafSort) {  // a leaf too large for the in-block sort: full radix sort
+    morton_keys<<<gb, 256, 0, st>>>(x, y, n, geo, H, kb, va, nullptr, nullptr);
+    uint64_t *kin = kb, *kout = keys;
+    int *vin = va, *vout = vb;
+    for (int shift = 0; shift < 60; shift += 8) {
+      radix_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, counts);
+      radix_scan_digit<<<256, 256, 0, st>>>(counts, nblocks, totals);
+      radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts, totals,
+                                                       kout, vout);
+      uint64_t *tk = kin; kin = kout; kout = tk;
+      int *tv = vin; vin = vout; vout = tv;
+    }
+    HP_CUDA(cudaMemcpyAsync(keys, kb, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+    sorted = va;
+  }
+  write_perm<<<gb, 256, 0, st>>>(sorted, n, perm);
+  HP_LAUNCH_CHECK();
+  return HPFMM_OK;
 }
