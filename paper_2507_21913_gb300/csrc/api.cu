@@ -273,8 +273,10 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     s = dalloc(pl, (void **)&(ptr), (bytes));                   \
     if (s != HPFMM_OK) { free_plan(pl); return s; }             \
   } while (0)
-  ALLOC(pl->xs, sizeof(double) * n);
-  ALLOC(pl->ys, sizeof(double) * n);
+  if (!f32) {  // sorted coordinates: used by the double-precision passes only
+    ALLOC(pl->xs, sizeof(double) * n);
+    ALLOC(pl->ys, sizeof(double) * n);
+  }
   ALLOC(pl->perm, sizeof(int64_t) * n);
   ALLOC(pl->keys, sizeof(uint64_t) * n);
   ALLOC(pl->leaf_start, sizeof(int) * (pl->nleaf + 1));

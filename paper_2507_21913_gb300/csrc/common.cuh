@@ -67,17 +67,18 @@ __host__ __device__ __forceinline__ void cfma(cpx<R> &a, cpx<R> b, cpx<R> c) {
   a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
 }
 template <typename R>
-__host__ __device__ __forceinline__ cpx<R> cdiv(cpx<R> a, cpx<R> b) {
-  // Smith's algorithm (scaled), adequate for the moderate ranges used here
-  R s = fabs(b.x) + fabs(b.y);
-  R bx = b.x / s, by = b.y / s;
-  R d = bx * bx + by * by;
-  R ax = a.x / s, ay = a.y / s;
-  return mk<R>((ax * bx + ay * by) / d, (ay * bx - ax * by) / d);
+__host__ __device__ __forceinline__ cpx<R> cinv(cpx<R> b) {
+  // 1/b = conj(b')/|b'|^2 * (1/s) with b' = b/s, s = |re| + |im| (no overflow);
+  // two real divisions
+  const R s = fabs(b.x) + fabs(b.y);
+  const R is = R(1) / s;
+  const R bx = b.x * is, by = b.y * is;
+  const R id = is / (bx * bx + by * by);
+  return mk<R>(bx * id, -by * id);
 }
 template <typename R>
-__host__ __device__ __forceinline__ cpx<R> cinv(cpx<R> b) {
-  return cdiv(mk<R>(R(1), R(0)), b);
+__host__ __device__ __forceinline__ cpx<R> cdiv(cpx<R> a, cpx<R> b) {
+  return a * cinv(b);
 }
 __device__ __forceinline__ cd cexp_d(cd z) {
   double s, c;

@@ -79,6 +79,7 @@ extern "C" hpfmm_status hpfmm_direct(const double *xs, const double *ys, const d
     return HPFMM_EUNSUPPORTED;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  HP_TRY(special_init_here());
   int64_t blocks = (nt + kDirectThreads - 1) / kDirectThreads;
   direct_kernel<<<(unsigned)blocks, kDirectThreads, 0, st>>>(
       xs, ys, qs, ns, xt, yt, self_index, nt, mk(kappa_re, kappa_im), pot, grad);

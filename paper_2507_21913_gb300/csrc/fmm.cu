@@ -165,11 +165,11 @@ __global__ void __launch_bounds__(256)
 k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
              int H, double x0, double side, int p, cpx<R> *__restrict__ M) {
   const int P1 = p + 1;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nleaf = int64_t(1) << (2 * H);
-  if (t >= nleaf * P1) return;
-  const int64_t leaf = t / P1;
-  const int n = (int)(t - leaf * P1);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < 4^12 * 41 < 2^32
+  const unsigned nleaf = 1u << (2 * H);
+  if (t >= nleaf * (unsigned)P1) return;
+  const unsigned leaf = t / (unsigned)P1;
+  const int n = (int)(t - leaf * (unsigned)P1);
   const double d = ldexp(side, -H);
   const double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
   const R invd = (R)(1.0 / d);
@@ -1676,6 +1676,7 @@ hpfmm_status fmm_set_smem_limits(int p) {
 
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
                       cudaStream_t st) {
+  HP_TRY(special_init_here());
   if (pl->prec == HPFMM_FP64) return run_passes<double>(pl, q, pot, grad, st);
   return run_passes<float>(pl, q, pot, grad, st);
 }

@@ -26,11 +26,40 @@
 // loses about |P|/2.3 digits (Lemma 3.2's regime n >= e|P| is where it is
 // safe).  Supported range: |P| <= 60 (relative error ~1e-13 or better).
 #pragma once
+#include <mutex>
+
 #include "common.cuh"
 
 #define HP_EULER_GAMMA 0.57721566490153286061
 #define HP_PI 3.14159265358979323846
 #define HP_TWO_PI 6.28318530717958647692
+
+// reciprocals 1/k, k = 0..kRecip-1 (entry 0 unused).  Each translation unit
+// that includes this header has its own copy (no relocatable device code);
+// special_init_here() fills it once per device.
+constexpr int kRecip = 512;
+static __constant__ double c_recip[kRecip];
+static inline hpfmm_status special_init_here() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    set_last_error("special_init: no current device");
+    return HPFMM_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return HPFMM_OK;
+  static double host[kRecip];
+  host[0] = 0.0;
+  for (int k = 1; k < kRecip; ++k) host[k] = 1.0 / (double)k;
+  HP_CUDA(cudaMemcpyToSymbol(c_recip, host, sizeof host));
+  done[dev] = true;
+  return HPFMM_OK;
+}
+__device__ __forceinline__ double recip_int(int k) {  // 1/k for 0 < |k| < kRecip
+  return k > 0 ? c_recip[k] : -c_recip[-k];
+}
 
 __device__ __forceinline__ bool jn_use_series(cd P) {
   double a = sqrt(abs2(P));
@@ -43,22 +72,22 @@ __device__ inline cd jn_series(cd P, int n) {
   double psi = -HP_EULER_GAMMA;
   double nfact = 1.0;
   for (int k = 1; k <= n; ++k) {
-    psi += 1.0 / k;
+    psi += c_recip[k];
     nfact *= k;
   }
   cd term = mk(1.0, 0.0);  // P^k / k!
   cd tot = mk(0.0, 0.0);
   cd Pn = mk(1.0, 0.0);
-  for (int k = 0; k < 400; ++k) {
+  for (int k = 0; k < kRecip - 1 && k - n < kRecip; ++k) {
     if (k == n) {
       Pn = term;  // P^n / n!
     } else {
-      double inv = 1.0 / (double)(k - n);
+      const double inv = recip_int(k - n);
       cd c = inv * term;
       tot = tot + c;
       if (k > n && k > a && abs2(c) < 1e-34 * abs2(tot)) break;
     }
-    term = (1.0 / (k + 1)) * (term * P);
+    term = c_recip[k + 1] * (term * P);
   }
   // P^n (i pi - Log P + psi) - n! tot = n! [ (P^n/n!)(i pi - Log P + psi) - tot ]
   cd L = clog_d(P);

@@ -119,42 +119,43 @@ __global__ void k_img_m2l(int p, cd *T, cd *logt) {
   if (threadIdx.x == 0) logt[cls] = clog_d(t);
 }
 
-// reaction M2L matrices, block = (level, class, sign); Tp/Tm: [level][cls][n][m].
-// Thread k evaluates It_k = J_k(P) / (2 pi k! shat^k) directly (series or
-// continued fraction for that k; no recursion between threads), then the
-// block fills the matrix.
+// reaction M2L matrices Tr[level][cls][sign][n][m].  The Phi_2^- matrix of
+// offset dx uses I_k at (+dx d, Y), which is the argument of the Phi_2^+
+// matrix of offset -dx; so a block owns one (level, ysum, m) with
+// shat = ysum + i m, evaluates It_k = J_k(P) / (2 pi k! shat^k) (thread k,
+// series or continued fraction for that k, no recursion between threads) and
+// fills Tr[l][(ysum, dx = m)][+] and Tr[l][(ysum, dx = -m)][-].
 __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd kappa,
                                const double *__restrict__ Cb, cd *Tr) {
-  const double side = geo[1];
   extern __shared__ cd sh[];
-  int P1 = p + 1, K = 2 * p;
-  int b = blockIdx.x;
-  int sign = b & 1;  // 0: Phi_2^+, 1: Phi_2^-
-  int cls = (b >> 1) % 21;
-  int lev = (b >> 1) / 21 + 1;  // 1..H
-  int dx = cls % 7 - 3, ysum = cls / 7 + 1;
-  double d = ldexp(side, -lev);
-  // I_k at (x, y) = (+-(x_t - x_s), y_t + y_s) = (-+dx d, ysum d); s/d = ysum - i(x/d)
-  double xs_ = sign ? (double)dx : -(double)dx;  // x / d
-  cd shat = mk((double)ysum, -xs_);
+  const double side = geo[1];
+  const int P1 = p + 1, K = 2 * p;
+  const int b = blockIdx.x;
+  const int mcol = b % 7 - 3, ysum = (b / 7) % 3 + 1;
+  const int lev = b / 21 + 1;  // 1..H
+  const double d = ldexp(side, -lev);
+  const cd shat = mk((double)ysum, (double)mcol);
   cd *h = sh;  // K+1: It_k
-  cd P = (d * kappa) * shat;
+  const cd P = (d * kappa) * shat;
+  const cd sinv = cinv(shat);
   for (int k = threadIdx.x; k <= K; k += blockDim.x) {
-    cd J = jn_direct(P, k);
-    cd sinv = cinv(shat);
+    const cd J = jn_direct(P, k);
     cd f = mk(1.0 / HP_TWO_PI, 0.0);
-    for (int j = 1; j <= k; ++j) f = (1.0 / j) * (f * sinv);
+    for (int j = 1; j <= k; ++j) f = c_recip[j] * (f * sinv);
     h[k] = J * f;
   }
   __syncthreads();
-  cd *out = Tr + ((size_t)((lev - 1) * 21 + cls) * 2 + sign) * P1 * P1;
+  const int cls_p = (ysum - 1) * 7 + (mcol + 3), cls_m = (ysum - 1) * 7 + (-mcol + 3);
+  cd *outp = Tr + ((size_t)((lev - 1) * 21 + cls_p) * 2 + 0) * P1 * P1;
+  cd *outm = Tr + ((size_t)((lev - 1) * 21 + cls_m) * 2 + 1) * P1 * P1;
   for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) {
-    int n = e / P1, m = e % P1;
-    cd v = Cb[(n + m) * (2 * p + 2) + m] * h[n + m];
-    int ph = sign ? (m - n) : (n - m);  // i^{ph}
-    ph &= 3;
-    for (int r = 0; r < ph; ++r) v = mul_i(v);
-    out[e] = v;
+    const int n = e / P1, m = e % P1;
+    const cd v = Cb[(n + m) * (2 * p + 2) + m] * h[n + m];
+    cd vp = v, vm = v;
+    for (int r = 0; r < ((n - m) & 3); ++r) vp = mul_i(vp);  // i^{n-m}
+    for (int r = 0; r < ((m - n) & 3); ++r) vm = mul_i(vm);  // i^{m-n}
+    outp[e] = vp;
+    outm[e] = vm;
   }
 }
 
@@ -213,10 +214,11 @@ hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
   int p = pl->p, P1 = p + 1, H = pl->H;
   size_t m2 = (size_t)P1 * P1;
   cd *rea = (cd *)pl->t_refl;
+  HP_TRY(special_init_here());
   pass_begin(pl, st, PASS_TABLES);
   size_t shm = sizeof(cd) * (2 * p + 1);
-  k_reaction_m2l<<<H * 21 * 2, 96, shm, st>>>(p, H, pl->geo, mk(pl->kre, pl->kim),
-                                               pl->t_binom, rea);
+  k_reaction_m2l<<<H * 21, 96, shm, st>>>(p, H, pl->geo, mk(pl->kre, pl->kim), pl->t_binom,
+                                           rea);
   HP_LAUNCH_CHECK();
   int nl = 1;
   if (pl->prec != HPFMM_FP64) {

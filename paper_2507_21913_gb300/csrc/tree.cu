@@ -6,6 +6,7 @@
 // reflection).  Steps: validation and bounding square (reduction), 60-bit
 // Morton keys (30 bits per axis, bit-exact rule), stable LSD radix sort of
 // (key, index), leaf offsets of the uniform level-H grid, gathers.
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -31,19 +32,32 @@ __device__ __forceinline__ double ulp_of(double s) {
   return __longlong_as_double((e - 52) << 52);
 }
 
+// order-preserving integer image of a finite double (a < b <=> key(a) < key(b)),
+// so the min / max reductions run on the integer pipe
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffll));
+}
+
 __global__ void bbox_partial(const double *__restrict__ x, const double *__restrict__ y,
                              int64_t n, Geom *__restrict__ part) {
-  __shared__ double s0[kRedThreads], s1[kRedThreads], s2[kRedThreads];
+  __shared__ long long s0[kRedThreads], s1[kRedThreads], s2[kRedThreads];
   __shared__ int sb[kRedThreads];
-  double xmn = INFINITY, xmx = -INFINITY, ymx = -INFINITY;
+  long long xmn = LLONG_MAX, xmx = LLONG_MIN, ymx = LLONG_MIN;
   int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double a = x[i], b = y[i];
-    if (!isfinite(a) || !isfinite(b) || !(b > 0.0)) bad = 1;
-    xmn = fmin(xmn, a);
-    xmx = fmax(xmx, a);
-    ymx = fmax(ymx, b);
+    const long long a = __double_as_longlong(x[i]), b = __double_as_longlong(y[i]);
+    // finite: exponent field below 0x7ff; y > 0: sign clear and not +0
+    const bool fin = ((a >> 52) & 0x7ff) != 0x7ff && ((b >> 52) & 0x7ff) != 0x7ff;
+    if (!fin || b <= 0) bad = 1;
+    const long long ka = a >= 0 ? a : (a ^ 0x7fffffffffffffffll);
+    xmn = min(xmn, ka);
+    xmx = max(xmx, ka);
+    ymx = max(ymx, b);  // y > 0: the bit pattern orders like the value
   }
   s0[threadIdx.x] = xmn;
   s1[threadIdx.x] = xmx;
@@ -52,14 +66,15 @@ __global__ void bbox_partial(const double *__restrict__ x, const double *__restr
   __syncthreads();
   for (int w = kRedThreads / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
-      s0[threadIdx.x] = fmin(s0[threadIdx.x], s0[threadIdx.x + w]);
-      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + w]);
-      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+      s0[threadIdx.x] = min(s0[threadIdx.x], s0[threadIdx.x + w]);
+      s1[threadIdx.x] = max(s1[threadIdx.x], s1[threadIdx.x + w]);
+      s2[threadIdx.x] = max(s2[threadIdx.x], s2[threadIdx.x + w]);
       sb[threadIdx.x] |= sb[threadIdx.x + w];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = Geom{s0[0], s1[0], s2[0], sb[0]};
+  if (threadIdx.x == 0)
+    part[blockIdx.x] = Geom{dkey_inv(s0[0]), dkey_inv(s1[0]), dkey_inv(s2[0]), sb[0]};
 }
 
 // final reduction (one block); geo[0] = x0, geo[1] = L (side), geo[2] = bad
@@ -493,8 +508,10 @@ __global__ void gather_points(const double *__restrict__ x, const double *__rest
   if (k >= n) return;
   int j = idx[k];
   double a = x[j], b = y[j];
-  xs[k] = a;
-  ys[k] = b;
+  if (xs) {
+    xs[k] = a;
+    ys[k] = b;
+  }
   perm[k] = j;
   if (loc32) {
     uint64_t leaf = keys[k] >> (60 - 2 * H);
