@@ -37,6 +37,25 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 
+// box side, its reciprocal and log per level, computed once on the host and
+// passed by value, so that no kernel repeats double-precision set-up
+// arithmetic per thread (GB300's FP64 pipe is narrow)
+struct LevelGeom {
+  float d[16], invd[16];
+  double logd[16];
+};
+LevelGeom level_geom(double side, int H) {
+  LevelGeom g;
+  for (int l = 0; l < 16; ++l) {
+    const double d = ldexp(side, -l);
+    g.d[l] = (float)d;
+    g.invd[l] = (float)(1.0 / d);
+    g.logd[l] = log(d);
+  }
+  (void)H;
+  return g;
+}
+
 template <typename R>
 __device__ __forceinline__ cpx<R> ldc(const cpx<R> *p) {
   return *p;
@@ -163,16 +182,18 @@ __device__ __forceinline__ cpx<R> cpow_int(cpx<R> w, int n) {
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
-             int H, double x0, double side, int p, cpx<R> *__restrict__ M) {
+             int H, double x0, double side, R invd_leaf, int p, cpx<R> *__restrict__ M) {
   const int P1 = p + 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < 4^12 * 41 < 2^32
   const unsigned nleaf = 1u << (2 * H);
   if (t >= nleaf * (unsigned)P1) return;
   const unsigned leaf = t / (unsigned)P1;
   const int n = (int)(t - leaf * (unsigned)P1);
-  const double d = ldexp(side, -H);
-  const double cx = x0 + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
-  const R invd = (R)(1.0 / d);
+  // (the single-precision points are already relative to the leaf centre)
+  const double cx = 0.0, cy = 0.0;
+  const R invd = invd_leaf;
+  (void)x0;
+  (void)side;
   const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
   // compensated (Kahan) summation: the moments of a leaf are sums of up to
   // hundreds of terms of both signs, and their rounding error is inherited
@@ -459,7 +480,7 @@ __constant__ signed char c_slot[49];      // 7x7 offset class -> 0..39, -1 for t
 
 template <typename R, int P1>
 __global__ void __launch_bounds__(128)
-k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tpad,
+k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
                  const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
                  cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status) {
   // rows padded to an even length PP so that k, k+1 pairs are one 16-byte
@@ -486,7 +507,7 @@ k_m2l_free_patch(int H, double side, const cpx<R> *__restrict__ Tpad,
   const int px0 = (b % npl) * kPatch, py0 = (b / npl) * kPatch;
   const int nparent_side = 1 << (l - 1), nside = 1 << l;
   const int64_t off = level_offset(l);
-  const R logd = (R)log(ldexp(side, -l));
+  const R logd = (R)lgm.logd[l];
   // the 40 translation matrices: one bulk copy (TMA) from the padded table
   const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * P1 * PP);
   if (threadIdx.x == 0) {
@@ -602,7 +623,7 @@ int patch_blocks(int H) {
 // dispatch on the (compile-time) order; returns false when no patch kernel
 // exists for this order / precision or it does not fit in shared memory
 template <typename R>
-bool launch_m2l_patch(int p, int H, double side, const cpx<R> *Tpad, const cd *logt,
+bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, const cd *logt,
                       const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st) {
   if (!Tpad) return false;
   int nb = patch_blocks(H);
@@ -616,7 +637,7 @@ bool launch_m2l_patch(int p, int H, double side, const cpx<R> *Tpad, const cd *l
       cudaGetLastError();                                                                 \
       return false;                                                                       \
     }                                                                                     \
-    k_m2l_free_patch<R, PP + 1><<<nb, 128, sm, st>>>(H, side, Tpad, logt, M, A, B, status); \
+    k_m2l_free_patch<R, PP + 1><<<nb, 128, sm, st>>>(H, lgm, Tpad, logt, M, A, B, status); \
     return true;                                                                          \
   }
   switch (p) {
@@ -705,7 +726,7 @@ k_m2l_mirror(int l, int p, double logd, const cpx<R> *__restrict__ Timg,
 // levels add to the free-space result.
 template <typename R>
 __global__ void __launch_bounds__(128)
-k_m2l_mirror_all(int H, int p, double side, const cpx<R> *__restrict__ Timg,
+k_m2l_mirror_all(int H, int p, LevelGeom lgm, const cpx<R> *__restrict__ Timg,
                  const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
                  const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
   extern __shared__ unsigned char smem_raw[];
@@ -721,7 +742,7 @@ k_m2l_mirror_all(int H, int p, double side, const cpx<R> *__restrict__ Timg,
   const int ixt = t % nx, iyt = t / nx, px = ixt >> 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = level_offset(l);
-  const R logd = (R)log(side / (double)nx);
+  const R logd = (R)lgm.logd[l];
   cpx<R> *ms = msh + warp * P1;
   cpx<R> aL[2], aC[2], aD[2];
   for (int r = 0; r < 2; ++r) aL[r] = aC[r] = aD[r] = mk<R>(0, 0);
@@ -1279,6 +1300,8 @@ k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
 constexpr int kTl = 4;             // target leaves per tile side
 constexpr int kTlP = kTl + 2;      // patch leaves per side
 constexpr int kTlCap = 3072;       // staged points per block
+constexpr int kTlWB = 192;         // per-warp neighbourhood buffer
+constexpr size_t kTlSmem = sizeof(float4) * (kTlCap + 8 * kTlWB) + sizeof(int) * (2 * 36 + 1);
 
 template <int NG>
 __device__ __forceinline__ void tile_ranges(const float4 *src, const int *pst, int pi0, int g,
@@ -1302,19 +1325,20 @@ __device__ __forceinline__ void tile_ranges(const float4 *src, const int *pst, i
 
 __global__ void __launch_bounds__(kEvWarps * 32, 3)
 k_eval32t(const float2 *__restrict__ loc, const float *__restrict__ qs,
-          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-          double side, int p, const cf *__restrict__ A, const cf *__restrict__ B,
+          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
+          float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B,
           double *__restrict__ pot, double *__restrict__ grad) {
-  __shared__ float4 src[kTlCap];
-  __shared__ int pst[kTlP * kTlP + 1];
-  __shared__ int pbeg[kTlP * kTlP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *src = reinterpret_cast<float4 *>(smem_raw);         // [kTlCap]
+  float4 *wbuf = src + kTlCap;                                  // [kEvWarps][kTlWB]
+  int *pst = reinterpret_cast<int *>(wbuf + kEvWarps * kTlWB);  // [kTlP^2 + 1]
+  int *pbeg = pst + kTlP * kTlP + 1;                            // [kTlP^2]
   const int P1 = p + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4 *wb = wbuf + warp * kTlWB;
   const int nx = 1 << H;
   const int tps = nx >= kTl ? nx / kTl : 1;
   const int tx0 = (blockIdx.x % tps) * kTl, ty0 = (blockIdx.x / tps) * kTl;
-  const float d = (float)ldexp(side, -H);
-  const float invd = (float)((double)nx / side);
   // patch leaf counts and prefix (warp 0)
   if (warp == 0) {
     int c0 = 0, c1 = 0;
@@ -1370,14 +1394,45 @@ k_eval32t(const float2 *__restrict__ loc, const float *__restrict__ qs,
       const int i = tb + tli;
       const bool act = i < b1;
       const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+      NearAcc acc;
+      acc.lf = acc.gx = acc.gy = 0.f;
       float lf = 0.f, gx = 0.f, gy = 0.f;
       if (staged) {
-        switch (ng) {
-          case 1: tile_ranges<1>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
-          case 2: tile_ranges<2>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
-          case 4: tile_ranges<4>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
-          default: tile_ranges<8>(src, pst, pi0, g, me.x, me.y, d, lf, gx, gy); break;
+        // the 9 neighbour ranges of the patch, copied into this warp's buffer
+        // in the target leaf's frame, batch by batch; the target's own leaf
+        // is range 4 and its position in the batch is tracked for the j != i test
+        int fill = 0, slo = 0, shi = 0;
+        for (int r9 = 0; r9 < 9; ++r9) {
+          const int pi = pi0 + (r9 / 3) * kTlP + (r9 % 3);
+          const float ox = (float)(r9 % 3 - 1) * d, oy = (float)(r9 / 3 - 1) * d;
+          const int s0 = pst[pi], cnt = pst[pi + 1] - s0;
+          for (int off = 0; off < cnt;) {
+            const int take = min(cnt - off, kTlWB - fill);
+            for (int j = lane; j < take; j += 32) {
+              const float4 v = src[s0 + off + j];
+              wb[fill + j] = make_float4(v.x + ox, v.y + oy, v.z, 0.f);
+            }
+            if (r9 == 4) {
+              slo = fill;
+              shi = fill + take;
+            }
+            fill += take;
+            off += take;
+            if (fill == kTlWB) {
+              __syncwarp();
+              free_batch(wb, fill, g, ng, slo, shi, me.x, me.y, acc);
+              __syncwarp();
+              fill = 0;
+              slo = shi = 0;
+            }
+          }
         }
+        __syncwarp();
+        free_batch(wb, fill, g, ng, slo, shi, me.x, me.y, acc);
+        __syncwarp();
+        lf = acc.lf;
+        gx = acc.gx;
+        gy = acc.gy;
       } else {
         // patch too large for the buffer: read the sources from global memory
         for (int r = 0; r < 3; ++r) {
@@ -1442,13 +1497,12 @@ constexpr int kMirSrc = 512;
 __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-           double side, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad) {
+           float d, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad) {
   __shared__ float4 src[kMirSrc];
   __shared__ float red[kEvWarps][9][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = 1 << H;
   const int ix = blockIdx.x;  // leaf (ix, 0)
-  const float d = (float)ldexp(side, -H);
   const cf kap = mk((float)kappa.x, (float)kappa.y);
   const uint64_t leaf = box_morton(ix, 0);
   const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
@@ -1540,6 +1594,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   const cd *logs = (const cd *)pl->t_rlog0;
   R *qs = (R *)pl->qs;
   cpx<R> *M = (cpx<R> *)pl->M, *A = (cpx<R> *)pl->A, *B = (cpx<R> *)pl->B;
+  const LevelGeom lg = level_geom(pl->side, H);
 
   pass_begin(pl, st, PASS_GATHER);
   k_gather_q<R><<<cdiv_u(n, 256), 256, 0, st>>>(q, pl->perm, n, qs);
@@ -1560,7 +1615,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   } else {
     LeafPoints<float> lp{pl->loc32};
     k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * P1, 256), 256, 0, st>>>(
-        lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cf *)M);
+        lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, lg.invd[H], p, (cf *)M);
   }
   pass_end(pl, st, PASS_P2M, 1);
   pass_begin(pl, st, PASS_M2M);
@@ -1587,7 +1642,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   bool patched = false;
   if (H >= 2 && sizeof(R) == 4) {
     pass_begin(pl, st, PASS_M2L_FREE);
-    patched = launch_m2l_patch<R>(p, H, pl->side, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
+    patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
                                   pl->status, st);
     pass_end(pl, st, PASS_M2L_FREE, patched ? 1 : 0);
   }
@@ -1605,7 +1660,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   {
     unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
     size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
-    k_m2l_mirror_all<R><<<nb, 128, sm, st>>>(H, p, pl->side, Timg, logs + 49, Treact, M, A, B);
+    k_m2l_mirror_all<R><<<nb, 128, sm, st>>>(H, p, lg, Timg, logs + 49, Treact, M, A, B);
   }
   pass_end(pl, st, PASS_M2L_MIRROR, 1);
   pass_begin(pl, st, PASS_L2L);
@@ -1625,14 +1680,14 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
     {
       const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
-      k_eval32t<<<(unsigned)(tps * tps), 32 * kEvWarps, 0, st>>>(
-          pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, p,
+      k_eval32t<<<(unsigned)(tps * tps), 32 * kEvWarps, kTlSmem, st>>>(
+          pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
           (const cf *)A, (const cf *)B, pot, grad);
     }
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
     k_mirror32<<<(unsigned)(1 << H), 32 * kEvWarps, 0, st>>>(
-        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, pl->side, kappa, tau, pot,
+        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], kappa, tau, pot,
         grad);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
@@ -1662,6 +1717,8 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+  HP_CUDA(cudaFuncSetAttribute(k_eval32t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTlSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
