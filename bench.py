@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--points", dest="n", type=int, default=1_000_000)
     ap.add_argument("--kappa", type=float, default=1.0)
     ap.add_argument("--p", type=int, default=12)
     ap.add_argument("--levels", type=int, default=8)
@@ -220,18 +220,51 @@ def roofline(passes_ms, launches, args, npairs, H, peaks):
             "frac": None, "traffic": None}
 
 
+def ranks():
+    """(world, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_replicas(backend="nccl"):
+    """Process group of the replicas (None for a single process).  The data
+    path has no collective: the group only carries the barriers around the
+    timed region and the max-over-ranks reduction of the timings."""
+    import torch
+    world, _, local = ranks()
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(v, dist, device=None):
+    """Maximum of a per-rank float over all ranks (the slowest replica)."""
+    if dist is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, n, seconds_per_step):
+    """Whole-job interactions/s: every replica evaluates its own N-point
+    problem (N^2 interactions) per step; the step time is the slowest rank's."""
+    return world * float(n) * float(n) / seconds_per_step
+
+
 def run_ours(args):
     import torch
     import paper_2507_21913_gb300 as hp
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    world, rank, local = ranks()
+    dist = init_replicas("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     hp.lib(build_if_missing=True)
@@ -289,12 +322,9 @@ def run_ours(args):
     clock.start()
     ms, pms, launches, pot, grad = timed_steps(plan, args.steps, args.warmup, True)
     clocks = clock.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
-    value = world * float(n) * float(n) / (ms_step / 1e3)
+    value = replica_throughput(world, n, ms_step / 1e3)
 
     # event-timed passes with the same clocks give the dominant kernel
     keys, _ = hp.hpfmm_get_order(plan)
@@ -335,7 +365,8 @@ def run_ours(args):
         plan64 = make_plan("fp64", args.p64, args.levels64)
         k64 = max(2, min(args.steps, 5))
         ms64, pms64, _, pot64, grad64 = timed_steps(plan64, k64, 2, True)
-        e = {"value": world * float(n) * n / (ms64 / k64 / 1e3), "unit": UNIT,
+        ms64 = max_over_ranks(ms64, dist, dev)
+        e = {"value": replica_throughput(world, n, ms64 / k64 / 1e3), "unit": UNIT,
              "ms_per_step": ms64 / k64, "p": args.p64, "levels": plan64.info()["levels"],
              "passes_ms_per_step": {k: v / k64 for k, v in pms64.items()}}
         if not args.no_check and rank == 0:
@@ -362,12 +393,9 @@ def run_ours(args):
         for _ in range(k):
             hp.hpfmm_update_points(plan, xh, yh)
             hp.hpfmm_eval(plan, qh, out=(poth, gradh))  # synchronises (host outputs)
-        dt = (time.perf_counter() - t0) / k
-        if dist:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        result["e2e"] = {"value": world * float(n) * n / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+        dt = max_over_ranks((time.perf_counter() - t0) / k, dist, dev)
+        result["e2e"] = {"value": replica_throughput(world, n, dt), "unit": UNIT,
+                         "ms_per_step": dt * 1e3,
                          "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": (16 + 32) * n}
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -380,7 +408,7 @@ def run_ours(args):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = ranks()
     if rank != 0:
         return
     import oracle
