@@ -126,6 +126,59 @@ hpfmm_status hpfmm_update_points(hpfmm_plan *plan, const double *x, const double
 hpfmm_status hpfmm_eval(hpfmm_plan *plan, const double *q, int nrhs, double *pot, double *grad,
                         void *stream);
 
+/*
+ * hpfmm_eval_adjoint -- gradient of a real functional L of u = G q with
+ * respect to the charges and the positions of the plan's points (the
+ * backward pass of hpfmm_eval for one charge vector).  The paper states the
+ * kernel's symmetry G(r, r') = G(r', r) (Eq. greensfunsymm); with it the
+ * transpose sums are forward sums with the charges Re g and Im g:
+ *   dL/dq_j = Re u[Re g]_j + Im u[Im g]_j
+ *   dL/dr_k = Re(conj(g_k) grad u[q]_k) + q_k (Re grad u[Re g]_k + Im grad u[Im g]_k)
+ *   q      : n doubles, the charges of the forward evaluation (caller order);
+ *            may be NULL when dxy is NULL.
+ *   g      : n complex doubles (2n doubles), g_i = dL/dRe u_i + i dL/dIm u_i.
+ *   grad_q : NULL, or the forward's grad output for q (n * 2 complex doubles);
+ *            when NULL and dxy is wanted, one more evaluation computes it.
+ *   dq     : NULL, or n doubles: dL/dq.
+ *   dxy    : NULL, or n * 2 doubles: (dL/dx_k, dL/dy_k).
+ * All arrays are device memory (EINVAL otherwise); at least one output.
+ * Costs two evaluations (three without grad_q) and allocates a 20 n double
+ * workspace in the plan on first use.  Stream-ordered.
+ */
+hpfmm_status hpfmm_eval_adjoint(hpfmm_plan *plan, const double *q, const double *g,
+                                const double *grad_q, double *dq, double *dxy, void *stream);
+
+/*
+ * Batched evaluation of independent problems (one plan and one charge vector
+ * each) as one CUDA graph.  The paper treats one problem at a time; this
+ * entry point has no counterpart there: it issues the problems' evaluations
+ * (hpfmm_eval's passes, unchanged) on nbranch parallel branches of one graph,
+ * problems assigned to branches largest first, so that small problems share
+ * the GPU.
+ *   hpfmm_batch_create : plans[nprob] (distinct; the batch does not own them and
+ *                        they must outlive it); nbranch = parallel branches
+ *                        (0: min(nprob, 8)); creates the batch's streams.
+ *   hpfmm_eval_batched : q[i] (n_i doubles), pot[i] (n_i complex), grad NULL or
+ *                        grad[i] (n_i * 2 complex) -- device memory only, as in
+ *                        hpfmm_eval.  The first call captures the graph; later
+ *                        calls replay it while the pointers and the plans'
+ *                        bounding squares are unchanged, else capture it again.
+ *                        Ordered after earlier work on `stream`, and later work
+ *                        on `stream` is ordered after it.  Plans with pass timing
+ *                        on are rejected (EINVAL).  Calls on one batch must not
+ *                        overlap, and the plans must not be evaluated elsewhere
+ *                        meanwhile (they share the plans' workspaces).
+ *   hpfmm_batch_captures : how many times the graph has been captured.
+ *   hpfmm_batch_destroy  : waits for the batch's work and frees its streams.
+ */
+typedef struct hpfmm_batch hpfmm_batch;
+hpfmm_status hpfmm_batch_create(hpfmm_plan *const *plans, int nprob, int nbranch,
+                                hpfmm_batch **out);
+hpfmm_status hpfmm_eval_batched(hpfmm_batch *batch, const double *const *q, double *const *pot,
+                                double *const *grad, void *stream);
+hpfmm_status hpfmm_batch_captures(const hpfmm_batch *batch, int64_t *captures);
+hpfmm_status hpfmm_batch_destroy(hpfmm_batch *batch);
+
 /* Release every device allocation of the plan (synchronises its stream). */
 hpfmm_status hpfmm_destroy(hpfmm_plan *plan);
 

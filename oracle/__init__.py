@@ -14,6 +14,9 @@ Contents
                                          exponential-integral form of Appendix A
                                          (scipy's E1 as a library primitive),
                                          vectorised for sampled targets at large N.
+* ``adjoint_direct``                  -- gradient of L = Re sum_i conj(g_i) u_i with
+                                         respect to the charges and the positions,
+                                         from direct sums and the symmetry of G.
 * ``morton_order``                    -- the tree ordering, for bit-exact checks.
 * paper operators (S2M, ME evaluation, S2L, LE evaluation, M2M, L2L, M2L)
   written literally from Section 2.2, for operator-level pins (Example 1).
@@ -201,6 +204,49 @@ def direct_closed(xs, ys, qs, target_index, kappa, grad=True, parts=PART_ALL, ch
                         g[k, 0] += np.sum(q * sign * 1j * I1)
                         g[k, 1] += np.sum(-q * I1)
     return u, (g if grad else None)
+
+
+# --------------------------------------------------------------------------
+# adjoint of u = G q
+def adjoint_direct(xs, ys, qs, gc, target_index, kappa, sums=None):
+    """Gradient of the real functional L = Re sum_i conj(g_i) u_i, with
+    u_i = sum_j q_j G(r_i, r_j) over the point set (sources = targets), at the
+    points j in target_index.  With the symmetry G(r, r') = G(r', r)
+    (Eq. greensfunsymm) the transpose sum is again a direct sum:
+
+        dL/dq_j   = Re u[Re g](r_j) + Im u[Im g](r_j)
+        dL/dr_j   = Re(conj(g_j) grad u[q](r_j))
+                    + q_j (Re grad u[Re g](r_j) + Im grad u[Im g](r_j))
+
+    where u[c] is the sum with charges c and grad acts on the target position.
+    ``sums(xs, ys, charges, idx, kappa) -> (u, grad)`` evaluates the direct
+    sums (default ``direct_closed``).  Returns (dq, dx, dy) at target_index."""
+    sums = sums or direct_closed
+    ti = np.asarray(target_index, np.int64)
+    gc = np.asarray(gc, np.complex128)
+    qs = np.asarray(qs, np.float64)
+    _, gq = sums(xs, ys, qs, ti, kappa)
+    ur, gr = sums(xs, ys, np.ascontiguousarray(gc.real), ti, kappa)
+    ui, gi = sums(xs, ys, np.ascontiguousarray(gc.imag), ti, kappa)
+    dq = ur.real + ui.imag
+    dr = (np.conj(gc[ti])[:, None] * gq).real + qs[ti][:, None] * (gr.real + gi.imag)
+    return dq, dr[:, 0], dr[:, 1]
+
+
+def loss_terms_of_point(xs, ys, qs, gc, k, xk, yk, kappa):
+    """The part of L = Re sum_i conj(g_i) u_i that depends on point k, with
+    point k moved to (xk, yk): the pairs (k, j) for all j (the free part skips
+    j = k; the image and reaction parts include it) and (i, k) for i != k.
+    Terms without point k cancel in a finite difference in r_k or q_k."""
+    xs = np.array(xs, np.float64); ys = np.array(ys, np.float64)
+    gc = np.asarray(gc, np.complex128)
+    xs[k] = xk; ys[k] = yk
+    u1, _ = direct(xs, ys, qs, xt=xs[k:k + 1], yt=ys[k:k + 1], kappa=kappa,
+                   self_index=np.array([k]), grad=False)
+    others = np.concatenate([np.arange(k), np.arange(k + 1, len(xs))])
+    u2, _ = direct(xs[k:k + 1], ys[k:k + 1], np.asarray(qs, np.float64)[k:k + 1],
+                   xt=xs[others], yt=ys[others], kappa=kappa, grad=False)
+    return float((np.conj(gc[k]) * u1[0]).real + np.sum((np.conj(gc[others]) * u2).real))
 
 
 # --------------------------------------------------------------------------

@@ -70,11 +70,18 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_selftest_wait_timeout.argtypes = [vp]
     L.hpfmm_tree_order_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
     L.hpfmm_read_timing.argtypes = [vp, vp, vp]
+    L.hpfmm_eval_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.hpfmm_batch_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
+    L.hpfmm_eval_batched.argtypes = [vp, vp, vp, vp, vp]
+    L.hpfmm_batch_captures.argtypes = [vp, ctypes.POINTER(i64)]
+    L.hpfmm_batch_destroy.argtypes = [vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
               "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing",
-              "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc"):
+              "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc", "hpfmm_eval_adjoint",
+              "hpfmm_batch_create", "hpfmm_eval_batched", "hpfmm_batch_captures",
+              "hpfmm_batch_destroy"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -180,6 +187,130 @@ def hpfmm_eval(plan, q, grad=True, out=None):
     if squeeze:
         return pot[0], (g[0] if grad else None)
     return pot, g
+
+
+def hpfmm_eval_adjoint(plan, q, g, grad_q=None, want_q=True, want_r=True):
+    """Gradient of a real functional L of u = G q (see hpfmm_eval_adjoint in
+    include/hpfmm.h): g = dL/dRe u + i dL/dIm u (complex, shape (n,)).
+    Returns (dq (n,) or None, dxy (n, 2) or None) as float64 device tensors."""
+    torch = _torch()
+    dev = plan.device
+    if dev.type != "cuda":
+        raise ValueError("hpfmm_eval_adjoint needs device tensors")
+    g = torch.as_tensor(g, device=dev).to(torch.complex128).contiguous().reshape(plan.n)
+    q = _as_tensor(q, dev).reshape(plan.n) if q is not None else None
+    if grad_q is not None:
+        grad_q = torch.as_tensor(grad_q, device=dev).to(torch.complex128).contiguous()
+    dq = torch.empty(plan.n, dtype=torch.float64, device=dev) if want_q else None
+    dxy = torch.empty((plan.n, 2), dtype=torch.float64, device=dev) if want_r else None
+    _check(lib().hpfmm_eval_adjoint(plan.handle, q.data_ptr() if q is not None else None,
+                                    g.data_ptr(), grad_q.data_ptr() if grad_q is not None else None,
+                                    dq.data_ptr() if dq is not None else None,
+                                    dxy.data_ptr() if dxy is not None else None, _stream(dev)))
+    return dq, dxy
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class HalfPlanePotential(torch.autograd.Function):
+        """u = G q on the plan's points; backward by hpfmm_eval_adjoint."""
+
+        @staticmethod
+        def forward(ctx, x, y, q, plan):
+            want_r = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+            pot, gq = hpfmm_eval(plan, q.detach(), grad=want_r)
+            ctx.plan = plan
+            ctx.save_for_backward(q.detach(), gq if want_r else None)
+            return pot
+
+        @staticmethod
+        def backward(ctx, g):
+            q, gq = ctx.saved_tensors
+            want_r = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+            dq, dxy = hpfmm_eval_adjoint(ctx.plan, q, g, grad_q=gq,
+                                         want_q=ctx.needs_input_grad[2], want_r=want_r)
+            dx = dxy[:, 0] if (want_r and ctx.needs_input_grad[0]) else None
+            dy = dxy[:, 1] if (want_r and ctx.needs_input_grad[1]) else None
+            return dx, dy, dq, None
+
+    return HalfPlanePotential
+
+
+_HPP = None
+
+
+def potential(x, y, q, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, plan=None):
+    """Differentiable u = G q (complex128, shape (n,)) for float64 device tensors
+    x, y, q.  The plan (tree, tables) is built on x, y, or, when given, rebuilt
+    in place for them; gradients with respect to x, y and q come from
+    hpfmm_eval_adjoint."""
+    global _HPP
+    if _HPP is None:
+        _HPP = _autograd_function()
+    if plan is None:
+        plan = hpfmm_create(x.detach(), y.detach(), kappa=kappa, p=p, leaf_size=leaf_size,
+                            prec=prec, levels=levels)
+    else:
+        hpfmm_update_points(plan, x.detach(), y.detach())
+    return _HPP.apply(x, y, q, plan)
+
+
+class Batch:
+    """Independent problems evaluated as one CUDA graph (hpfmm_batch_* in
+    include/hpfmm.h).  Holds references to its plans and its output tensors,
+    which stay the same between calls so that the graph is replayed."""
+
+    def __init__(self, handle, plans):
+        self.handle = handle
+        self.plans = list(plans)
+        self.out = {}
+
+    def captures(self):
+        c = ctypes.c_int64()
+        _check(lib().hpfmm_batch_captures(self.handle, ctypes.byref(c)))
+        return c.value
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().hpfmm_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def hpfmm_batch_create(plans, nbranch=0):
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value if isinstance(p.handle, ctypes.c_void_p)
+                                            else p.handle for p in plans])
+    h = ctypes.c_void_p()
+    _check(lib().hpfmm_batch_create(arr, len(plans), int(nbranch), ctypes.byref(h)))
+    return Batch(h, plans)
+
+
+def hpfmm_eval_batched(batch, qs, grad=True):
+    """Evaluate every problem of the batch (qs[i]: float64 device tensor of the
+    plan's n).  Returns lists (pot[i], grad[i] or None); the tensors belong to
+    the batch and are overwritten by its next call with the same grad flag."""
+    torch = _torch()
+    plans = batch.plans
+    if len(qs) != len(plans):
+        raise ValueError("hpfmm_eval_batched: %d charge vectors for %d plans" % (len(qs), len(plans)))
+    qs = [_as_tensor(q, p.device).reshape(p.n) for q, p in zip(qs, plans)]
+    key = bool(grad)
+    if key not in batch.out:
+        batch.out[key] = (
+            [torch.empty(p.n, dtype=torch.complex128, device=p.device) for p in plans],
+            [torch.empty((p.n, 2), dtype=torch.complex128, device=p.device) for p in plans]
+            if grad else None)
+    pots, grads = batch.out[key]
+    vp = ctypes.c_void_p
+    qa = (vp * len(plans))(*[q.data_ptr() for q in qs])
+    pa = (vp * len(plans))(*[t.data_ptr() for t in pots])
+    ga = (vp * len(plans))(*[t.data_ptr() for t in grads]) if grad else None
+    batch._keep = qs  # the graph reads these until the call has run
+    _check(lib().hpfmm_eval_batched(batch.handle, qa, pa, ga, _stream(plans[0].device)))
+    return pots, grads
 
 
 def hpfmm_destroy(plan):

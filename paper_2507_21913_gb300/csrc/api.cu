@@ -137,13 +137,13 @@ static void free_plan(hpfmm_plan *pl) {
   void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
-                  pl->t_binom, pl->geo, pl->t_m2l_pad};
+                  pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
 }
 
-static hpfmm_status dalloc(hpfmm_plan *pl, void **p, size_t bytes) {
+hpfmm_status plan_dalloc(hpfmm_plan *pl, void **p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -270,7 +270,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   hpfmm_status s = HPFMM_OK;
 #define ALLOC(ptr, bytes)                                       \
   do {                                                          \
-    s = dalloc(pl, (void **)&(ptr), (bytes));                   \
+    s = plan_dalloc(pl, (void **)&(ptr), (bytes));                   \
     if (s != HPFMM_OK) { free_plan(pl); return s; }             \
   } while (0)
   if (!f32) {  // sorted coordinates: used by the double-precision passes only
@@ -323,9 +323,9 @@ static hpfmm_status ensure_stage(hpfmm_plan *pl, int nrhs) {
   pl->in_q = nullptr;
   pl->out_pot = pl->out_grad = nullptr;
   pl->stage_rhs = 0;
-  HP_TRY(dalloc(pl, (void **)&pl->in_q, sizeof(double) * pl->n * nrhs));
-  HP_TRY(dalloc(pl, &pl->out_pot, 2 * sizeof(double) * pl->n * nrhs));
-  HP_TRY(dalloc(pl, &pl->out_grad, 4 * sizeof(double) * pl->n * nrhs));
+  HP_TRY(plan_dalloc(pl, (void **)&pl->in_q, sizeof(double) * pl->n * nrhs));
+  HP_TRY(plan_dalloc(pl, &pl->out_pot, 2 * sizeof(double) * pl->n * nrhs));
+  HP_TRY(plan_dalloc(pl, &pl->out_grad, 4 * sizeof(double) * pl->n * nrhs));
   pl->stage_rhs = nrhs;
   return HPFMM_OK;
 }

@@ -212,6 +212,7 @@ struct hpfmm_plan {
   void *out_pot = nullptr, *out_grad = nullptr;  // staging for host outputs
   double *in_q = nullptr;                         // staging for host charges
   int64_t stage_rhs = 0;
+  double *adj = nullptr;  // adjoint workspace (20 n doubles), allocated on first use
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
   void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
@@ -265,3 +266,4 @@ hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad, cudaStream_t st);
 bool is_device_pointer(const void *p);
+hpfmm_status plan_dalloc(hpfmm_plan *pl, void **p, size_t bytes);

@@ -129,3 +129,40 @@ def test_fmm_full_size_sampled(prec, tol):
     u, g, _ = run(x, y, q, 1.0, p, leaf, prec=prec)
     assert rel(u[idx], u_ref) < tol
     assert rel(g[idx], g_ref) < 20 * tol
+
+
+@pytest.mark.parametrize("kappa,p", [(0.1, 16), (10.0, 16), (1.0, 24), (1.0, 32)])
+def test_fmm_full_size_kappa_p_sweep_fp64(kappa, p):
+    """The FP64 sweep workload: N = 1e6 uniform, kappa in {0.1, 1, 10},
+    p in {16, 24, 32}; 16 sampled targets.  The reaction bounds carry an extra
+    factor max(|kappa|^2 |Delta|^2, 1) (Theorems 3.3-3.7), so kappa = 10 loses
+    about two digits at equal p."""
+    n = 1_000_000
+    x, y, q = workloads.uniform(n, seed=0)
+    idx = workloads.sample_targets(n, 16, seed=1)
+    u_ref, g_ref = oracle_cache.sampled_closed(x, y, q, idx, kappa)
+    u, g, _ = run(x, y, q, kappa, p, 32, levels=7)
+    tol = {16: 1e-8, 24: 1e-10, 32: 1e-11}[p] * (100 if kappa == 10.0 else 1)
+    assert rel(u[idx], u_ref) < tol
+    assert rel(g[idx], g_ref) < 20 * tol
+
+
+def test_clustered_4m_mixed_complex_kappa():
+    """Clustered workload: N = 4e6, 80% in 64 Gaussian clusters (sigma 0.01)
+    with centres at y in (0.001, 0.05], 20% uniform; kappa = 1 + 0.5i, p = 20,
+    single precision with the double-precision reaction near field for pairs
+    with y_i + y_j < tau.  64 sampled targets, half of them with y < 0.06."""
+    n = 4_000_000
+    x, y, q = workloads.clustered(n, seed=0)
+    near = np.flatnonzero(y < 0.06)
+    far = np.flatnonzero(y >= 0.06)
+    g0 = np.random.Generator(np.random.PCG64(1))
+    idx = np.sort(np.concatenate([g0.choice(near, 32, replace=False),
+                                  g0.choice(far, 32, replace=False)]))
+    kappa = 1.0 + 0.5j
+    u_ref, g_ref = oracle_cache.sampled_closed(x, y, q, idx, kappa)
+    u, g, plan = run(x, y, q, kappa, 20, 32, prec="mixed", levels=10)
+    assert rel(u[idx], u_ref) < 5e-6
+    assert rel(g[idx], g_ref) < 2e-5
+    m = y[idx] < 0.06  # the near-boundary half on its own
+    assert rel(u[idx][m], u_ref[m]) < 5e-6
