@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--check-targets", type=int, default=16)
     ap.add_argument("--cpu-targets", type=int, default=8)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the clustered / adjoint / multi-RHS / batched lines")
     return ap.parse_args()
 
 
@@ -180,7 +182,7 @@ def vlist_translations(H):
 
 # kernels that make up a pass with one launch per step (the candidates for the
 # dominant-kernel roofline)
-SINGLE_KERNEL = {"eval": ("k_eval32g", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
+SINGLE_KERNEL = {"eval": ("k_eval32t", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
                  "m2l_mirror": ("k_m2l_mirror_all", "k_m2l_mirror_all"),
                  "p2m": ("k_p2m", "k_p2m"), "near_mirror": ("k_mirror32", None)}
 
@@ -257,6 +259,125 @@ def replica_throughput(world, n, seconds_per_step):
     """Whole-job interactions/s: every replica evaluates its own N-point
     problem (N^2 interactions) per step; the step time is the slowest rank's."""
     return world * float(n) * float(n) / seconds_per_step
+
+
+# --------------------------------------------------------------------------
+# the other workloads: each timed on its own (CUDA events, W warm-ups), inputs
+# resident, potentials and fields
+def _event_time(fn, k, w, flush):
+    import torch
+    for _ in range(w):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for i in range(k):
+        flush.fill_(i & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / k
+
+
+def extra_workloads(args, dev, flush, check):
+    import torch
+    import paper_2507_21913_gb300 as hp
+    t = lambda a: torch.tensor(a, device=dev)
+    out = {}
+    k, w = 3, 2
+
+    # clustered: 4e6 points, kappa = 1 + 0.5i, mixed precision, p = 20
+    n = 4_000_000
+    x, y, q = workloads.clustered(n, seed=0)
+    xd, yd, qd = t(x), t(y), t(q)
+    kap = 1.0 + 0.5j
+    plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec="mixed", levels=10)
+    pot = torch.empty(n, dtype=torch.complex128, device=dev)
+    grad = torch.empty((n, 2), dtype=torch.complex128, device=dev)
+
+    def step():
+        hp.hpfmm_update_points(plan, xd, yd)
+        hp.hpfmm_eval(plan, qd, out=(pot, grad))
+    ms = _event_time(step, k, w, flush)
+    e = {"workload": "clustered N=4e6 (80%% in 64 clusters sigma 0.01 near y=0), kappa=1+0.5i, "
+                     "mixed precision, p=20, L=10, tree rebuilt every step", "ms_per_step": ms,
+         "value": float(n) * n / (ms / 1e3), "unit": UNIT}
+    if check:
+        near = np.flatnonzero(y < 0.06)
+        far = np.flatnonzero(y >= 0.06)
+        g0 = np.random.Generator(np.random.PCG64(1))
+        idx = np.sort(np.concatenate([g0.choice(near, 4, replace=False),
+                                      g0.choice(far, 4, replace=False)]))
+        u_ref, _ = oracle_sampled(x, y, q, idx, kap)
+        u = pot.cpu().numpy()[idx]
+        e["rel_err_pot"] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+        e["check_targets"] = len(idx)
+    out["clustered"] = e
+    del plan, pot, grad, xd, yd, qd
+
+    # adjoint: N = 1e6, kappa = 2, p = 16, single precision; forward (with field)
+    # then backward for E = w . u
+    n = 1_000_000
+    x, y, q, wv = workloads.uniform(n, seed=0, with_w=True)
+    xd, yd, qd = t(x), t(y), t(q)
+    g = t(wv.astype(np.complex128))
+    plan = hp.hpfmm_create(xd, yd, kappa=2.0, p=16, leaf_size=64, prec="fp32")
+    pot = torch.empty(n, dtype=torch.complex128, device=dev)
+    grad = torch.empty((n, 2), dtype=torch.complex128, device=dev)
+    ms_f = _event_time(lambda: hp.hpfmm_eval(plan, qd, out=(pot, grad)), k, w, flush)
+    ms_b = _event_time(lambda: hp.hpfmm_eval_adjoint(plan, qd, g, grad_q=grad), k, w, flush)
+    out["adjoint"] = {"workload": "uniform N=1e6, kappa=2, p=16, fp32; E = w.u, dE/dq and dE/dr",
+                      "forward_ms": ms_f, "backward_ms": ms_b,
+                      "backward_over_forward": ms_b / ms_f}
+    del plan, pot, grad
+
+    # many charge vectors on one tree: 64 RHS on N = 5e5, p = 16, single precision
+    n = 500_000
+    x, y, _ = workloads.uniform(n, seed=0)
+    Q = t(np.random.Generator(np.random.PCG64(8)).uniform(-1.0, 1.0, (64, n)))
+    plan = hp.hpfmm_create(t(x), t(y), kappa=1.0, p=16, leaf_size=32, prec="fp32")
+    pot = torch.empty((64, n), dtype=torch.complex128, device=dev)
+    grad = torch.empty((64, n, 2), dtype=torch.complex128, device=dev)
+    ms_m = _event_time(lambda: hp.hpfmm_eval(plan, Q, out=(pot, grad)), k, w, flush)
+
+    def looped():
+        for r in range(64):
+            hp.hpfmm_eval(plan, Q[r], out=(pot[r], grad[r]))
+    ms_l = _event_time(looped, 2, 1, flush)
+    out["multi_rhs"] = {"workload": "64 charge vectors on uniform N=5e5, kappa=1, p=16, fp32, "
+                                    "potentials and fields", "ms_shared_passes": ms_m,
+                        "ms_one_at_a_time": ms_l, "speedup": ms_l / ms_m,
+                        "value": 64.0 * n * n / (ms_m / 1e3), "unit": UNIT}
+    del plan, pot, grad, Q
+
+    # independent problems of uneven size as one CUDA graph
+    sizes, kappas = workloads.batched_sizes(32, seed=0)
+    plans, qs = [], []
+    for i, (nn, kk) in enumerate(zip(sizes, kappas)):
+        xx, yy, qq = workloads.uniform(int(nn), seed=100 + i)
+        plans.append(hp.hpfmm_create(t(xx), t(yy), kappa=float(kk), p=16, leaf_size=32,
+                                     prec="fp32"))
+        qs.append(t(qq))
+    outs = [(torch.empty(p_.n, dtype=torch.complex128, device=dev),
+             torch.empty((p_.n, 2), dtype=torch.complex128, device=dev)) for p_ in plans]
+    batch = hp.hpfmm_batch_create(plans)
+    ms_g = _event_time(lambda: hp.hpfmm_eval_batched(batch, qs), k, w, flush)
+
+    def one_by_one():
+        for p_, q_, o_ in zip(plans, qs, outs):
+            hp.hpfmm_eval(p_, q_, out=o_)
+    ms_o = _event_time(one_by_one, k, w, flush)
+    pairs = float(np.sum(sizes.astype(np.float64) ** 2))
+    out["batched"] = {"workload": "32 problems, N=floor(10^U[4,log10 4e5]) (sum %d), "
+                                  "kappa=U[0.1,10], p=16, fp32, one CUDA graph" % int(sizes.sum()),
+                      "ms_graph": ms_g, "ms_one_by_one": ms_o, "speedup": ms_o / ms_g,
+                      "value": pairs / (ms_g / 1e3), "unit": UNIT,
+                      "graph_captures": batch.captures()}
+    del batch, plans
+    return out
 
 
 def run_ours(args):
@@ -397,6 +518,9 @@ def run_ours(args):
         result["e2e"] = {"value": replica_throughput(world, n, dt), "unit": UNIT,
                          "ms_per_step": dt * 1e3,
                          "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": (16 + 32) * n}
+
+    if not args.no_extra:
+        result["extra"] = extra_workloads(args, dev, flush, check=not args.no_check and rank == 0)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(x, y, q, args.kappa, args.cpu_targets)

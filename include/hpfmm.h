@@ -70,7 +70,14 @@ typedef struct {
   double tau_fp64;      /* MIXED only: boundary-distance threshold, default 0.05 */
   int levels;           /* 0: choose the uniform tree depth from leaf_size;
                            otherwise force the leaf level (1..15) */
-  int reserved[5];      /* must be zero */
+  int subtree_levels;   /* 0: automatic; otherwise the depth (1..4) of the subtree
+                           tiles of the fused upward / downward passes (one block per
+                           subtree of 4^k leaves), clamped to what fits in shared memory */
+  int m2l_mode;         /* free-space M2L of multi-RHS single-precision evaluations
+                           (16 or more charge vectors): 0 the FP32 FMA kernel,
+                           1 the tensor cores (tcgen05 kind::tf32, three-term split
+                           products accumulated in tensor memory) */
+  int reserved[3];      /* must be zero */
 } hpfmm_options;
 
 /* Fill *opt with the defaults. */
@@ -179,6 +186,39 @@ hpfmm_status hpfmm_eval_batched(hpfmm_batch *batch, const double *const *q, doub
 hpfmm_status hpfmm_batch_captures(const hpfmm_batch *batch, int64_t *captures);
 hpfmm_status hpfmm_batch_destroy(hpfmm_batch *batch);
 
+/*
+ * hpfmm_autotune -- choose p, the leaf level and the subtree tile depth for
+ * one point set by measurement (the paper fixes p from its error theorems and
+ * does not tune the tree; this entry point has no counterpart there).
+ *   x, y     : n device doubles (the points), n >= 64.
+ *   prec     : HPFMM_FP64 / HPFMM_FP32 / HPFMM_MIXED.
+ *   tol      : target relative L2 error of the potential.
+ *   nsample  : number of sampled targets (>= 8) for the error estimate.
+ * A probe charge vector (a hash of the point index, uniform in [-1, 1)) is
+ * evaluated by the FMM and, at every (n / nsample)-th point, by hpfmm_direct in
+ * double precision.  The smallest even p (4..40 in FP64, 4..20 otherwise)
+ * whose sampled error meets tol is taken (met = 1); if none does, the most
+ * accurate one (met = 0).  Then the leaf level (default level +-1) and the
+ * subtree depth (automatic or 1..4) are chosen as the fastest
+ * hpfmm_update_points + hpfmm_eval, timed with CUDA events, among the
+ * configurations whose error stays within tol.  Allocates and frees its own
+ * device memory and synchronises the stream.  Use the result with
+ * hpfmm_create(p, opt.levels = levels, opt.subtree_levels = subtree_levels).
+ */
+typedef struct {
+  int p;
+  int levels;
+  int subtree_levels;
+  int met;             /* 1 if est_rel_err <= tol */
+  double mean_leaf;    /* n / 4^levels */
+  double est_rel_err;  /* sampled relative L2 error of the chosen configuration */
+  double ms_per_eval;  /* update_points + eval, potentials only */
+  int nsample;
+} hpfmm_tuning;
+hpfmm_status hpfmm_autotune(const double *x, const double *y, int64_t n, double kappa_re,
+                            double kappa_im, int prec, double tol, int nsample, void *stream,
+                            hpfmm_tuning *out);
+
 /* Release every device allocation of the plan (synchronises its stream). */
 hpfmm_status hpfmm_destroy(hpfmm_plan *plan);
 
@@ -264,6 +304,18 @@ hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *y, int64_t 
  * about a second), HPFMM_OK if the wait somehow completed.  Synchronises.
  */
 hpfmm_status hpfmm_selftest_wait_timeout(void *stream);
+
+/*
+ * hpfmm_selftest_tc_gemm -- check of the library's tensor-core building blocks
+ * (no counterpart in the paper): one CTA computes D[128 x n] = A[128 x k] B^T
+ * (B is n x k) with tcgen05 kind::tf32 MMAs accumulating in tensor memory,
+ * in plain tf32 (split = 0) or as the three-term tf32 split product
+ * hi*hi + hi*lo + lo*hi (split = 1).  All arrays row-major float, device
+ * memory; 16 <= n <= 128 with n % 16 == 0, 8 <= k <= 64 with k % 8 == 0.
+ * Returns ETIMEOUT if the MMA completion wait gave up.  Synchronises.
+ */
+hpfmm_status hpfmm_selftest_tc_gemm(const float *A, const float *B, float *D, int n, int k,
+                                    int split, void *stream);
 
 const char *hpfmm_status_string(hpfmm_status s);
 const char *hpfmm_last_error(void);

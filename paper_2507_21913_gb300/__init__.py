@@ -29,7 +29,15 @@ class HpfmmError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tau_fp64", ctypes.c_double), ("levels", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("subtree_levels", ctypes.c_int), ("m2l_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("levels", ctypes.c_int), ("subtree_levels", ctypes.c_int),
+                ("met", ctypes.c_int), ("mean_leaf", ctypes.c_double),
+                ("est_rel_err", ctypes.c_double), ("ms_per_eval", ctypes.c_double),
+                ("nsample", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -75,13 +83,15 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_eval_batched.argtypes = [vp, vp, vp, vp, vp]
     L.hpfmm_batch_captures.argtypes = [vp, ctypes.POINTER(i64)]
     L.hpfmm_batch_destroy.argtypes = [vp]
+    L.hpfmm_autotune.argtypes = [vp, vp, i64, dbl, dbl, i32, dbl, i32, vp, ctypes.POINTER(Tuning)]
+    L.hpfmm_selftest_tc_gemm.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
               "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing",
               "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc", "hpfmm_eval_adjoint",
               "hpfmm_batch_create", "hpfmm_eval_batched", "hpfmm_batch_captures",
-              "hpfmm_batch_destroy"):
+              "hpfmm_batch_destroy", "hpfmm_autotune", "hpfmm_selftest_tc_gemm"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -139,7 +149,8 @@ class Plan:
             pass
 
 
-def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau_fp64=0.05):
+def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau_fp64=0.05,
+                 subtree_levels=0, m2l_mode=0):
     """Build a plan for the points (x, y); see hpfmm_create in include/hpfmm.h."""
     x = _as_tensor(x)
     y = _as_tensor(y, x.device)
@@ -149,6 +160,8 @@ def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau
     opt.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     opt.levels = int(levels)
     opt.tau_fp64 = float(tau_fp64)
+    opt.subtree_levels = int(subtree_levels)
+    opt.m2l_mode = int(m2l_mode)
     h = ctypes.c_void_p()
     _check(lib().hpfmm_create(x.data_ptr(), y.data_ptr(), x.numel(), kappa.real, kappa.imag,
                               int(p), int(leaf_size), ctypes.byref(opt), _stream(x.device),
@@ -313,6 +326,19 @@ def hpfmm_eval_batched(batch, qs, grad=True):
     return pots, grads
 
 
+def hpfmm_autotune(x, y, kappa=1.0, prec="fp32", tol=1e-6, nsample=256):
+    """Pick p, levels and subtree_levels by measurement (see include/hpfmm.h).
+    Returns a dict; pass p, levels and subtree_levels on to hpfmm_create."""
+    x = _as_tensor(x)
+    y = _as_tensor(y, x.device)
+    kappa = complex(kappa)
+    t = Tuning()
+    _check(lib().hpfmm_autotune(x.data_ptr(), y.data_ptr(), x.numel(), kappa.real, kappa.imag,
+                                PRECISIONS[prec] if isinstance(prec, str) else int(prec),
+                                float(tol), int(nsample), _stream(x.device), ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+
 def hpfmm_destroy(plan):
     if plan.handle:
         _check(lib().hpfmm_destroy(plan.handle))
@@ -402,6 +428,18 @@ def hpfmm_tree_order_noalloc(x, y, levels=5):
     _check(lib().hpfmm_tree_order_noalloc(x.data_ptr(), y.data_ptr(), x.numel(), int(levels),
                                           keys.data_ptr(), perm.data_ptr(), _stream(x.device)))
     return keys.cpu().numpy().view(np.uint64), perm.cpu().numpy()
+
+
+def hpfmm_selftest_tc_gemm(A, B, split=True):
+    """D = A B^T on the tensor cores (tf32, or the three-term split); A: 128 x k,
+    B: n x k float32 device tensors.  Returns D (128 x n float32)."""
+    torch = _torch()
+    A = A.to(torch.float32).contiguous()
+    B = B.to(torch.float32).contiguous()
+    D = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32, device=A.device)
+    _check(lib().hpfmm_selftest_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), B.shape[0],
+                                        A.shape[1], 1 if split else 0, _stream(A.device)))
+    return D
 
 
 def hpfmm_version():

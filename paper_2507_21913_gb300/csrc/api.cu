@@ -137,7 +137,8 @@ static void free_plan(hpfmm_plan *pl) {
   void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
-                  pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj};
+                  pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj, pl->mq, pl->mqsm,
+                  pl->mM, pl->mA, pl->mB};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -247,8 +248,10 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     set_last_error("hpfmm_create: unknown precision %d", (int)o.prec);
     return HPFMM_EINVAL;
   }
-  if (o.levels < 0 || o.levels > 15 || !(o.tau_fp64 >= 0)) {
-    set_last_error("hpfmm_create: levels must be in 0..15 and tau_fp64 >= 0");
+  if (o.levels < 0 || o.levels > 15 || !(o.tau_fp64 >= 0) || o.subtree_levels < 0 ||
+      o.subtree_levels > 4 || o.m2l_mode < 0 || o.m2l_mode > 1) {
+    set_last_error("hpfmm_create: levels must be in 0..15, subtree_levels in 0..4, m2l_mode in "
+                   "0..1, tau_fp64 >= 0");
     return HPFMM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -257,6 +260,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   pl->p = p;
   pl->prec = o.prec;
   pl->tau_fp64 = o.tau_fp64;
+  pl->subtree = o.subtree_levels;
+  pl->m2l_mode = o.m2l_mode;
   pl->kre = kappa_re;
   pl->kim = kappa_im;
   pl->H = o.levels > 0 ? o.levels : choose_levels(n, leaf_size);
@@ -330,6 +335,27 @@ static hpfmm_status ensure_stage(hpfmm_plan *pl, int nrhs) {
   return HPFMM_OK;
 }
 
+// charge vectors per multi-RHS pass set
+constexpr int kMultiMax = 64;
+
+static hpfmm_status ensure_multi(hpfmm_plan *pl, int nr) {
+  if (pl->mcap >= nr) return HPFMM_OK;
+  void **bufs[] = {&pl->mq, &pl->mqsm, &pl->mM, &pl->mA, &pl->mB};
+  for (void **b : bufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  pl->mcap = 0;
+  const size_t n = (size_t)pl->n, ncoef = (size_t)pl->nbox * (pl->p + 1);
+  HP_TRY(plan_dalloc(pl, &pl->mq, sizeof(float) * n * nr));
+  HP_TRY(plan_dalloc(pl, &pl->mqsm, sizeof(float) * n * fmm_multi_rp(nr)));
+  HP_TRY(plan_dalloc(pl, &pl->mM, 2 * sizeof(float) * ncoef * nr));
+  HP_TRY(plan_dalloc(pl, &pl->mA, 2 * sizeof(float) * ncoef * nr));
+  HP_TRY(plan_dalloc(pl, &pl->mB, 2 * sizeof(float) * ncoef * nr));
+  pl->mcap = nr;
+  return HPFMM_OK;
+}
+
 extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, double *pot,
                                    double *grad, void *stream) {
   if (!pl || !q || !pot || nrhs < 1) {
@@ -349,9 +375,21 @@ extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, do
   }
   if (!pd) dpot = (double *)pl->out_pot;
   if (!gd) dgrad = (double *)pl->out_grad;
-  for (int r = 0; r < nrhs; ++r) {
-    HP_TRY(fmm_eval(pl, dq + (size_t)r * n, dpot + (size_t)2 * r * n,
-                    dgrad ? dgrad + (size_t)4 * r * n : nullptr, st));
+  if (nrhs > 1 && fmm_multi_supported(pl)) {
+    // single precision: the charge vectors share one set of passes, kMultiMax at a time
+    const int chunk = nrhs < kMultiMax ? nrhs : kMultiMax;
+    HP_TRY(ensure_multi(pl, chunk));
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+      const int nr = nrhs - r0 < chunk ? nrhs - r0 : chunk;
+      HP_TRY(fmm_eval_multi(pl, dq + (size_t)r0 * n, nr, dpot + (size_t)2 * r0 * n,
+                            dgrad ? dgrad + (size_t)4 * r0 * n : nullptr, pl->mq, pl->mqsm,
+                            pl->mM, pl->mA, pl->mB, st));
+    }
+  } else {
+    for (int r = 0; r < nrhs; ++r) {
+      HP_TRY(fmm_eval(pl, dq + (size_t)r * n, dpot + (size_t)2 * r * n,
+                      dgrad ? dgrad + (size_t)4 * r * n : nullptr, st));
+    }
   }
   if (!pd)
     HP_CUDA(cudaMemcpyAsync(pot, dpot, 2 * sizeof(double) * n * nrhs, cudaMemcpyDefault, st));

@@ -182,6 +182,8 @@ struct hpfmm_plan {
   int p = 0;
   int prec = HPFMM_FP64;
   double tau_fp64 = 0.05;
+  int subtree = 0;   // fused upward/downward subtree depth (0: automatic)
+  int m2l_mode = 0;  // multi-RHS free M2L (16+ RHS): 0 FP32 FMA kernel, 1 tensor cores
   double kre = 1, kim = 0;
   double x0 = 0, side = 1;
   int64_t nbox = 0;  // boxes over levels 0..H
@@ -213,6 +215,9 @@ struct hpfmm_plan {
   double *in_q = nullptr;                         // staging for host charges
   int64_t stage_rhs = 0;
   double *adj = nullptr;  // adjoint workspace (20 n doubles), allocated on first use
+  // multi-RHS workspace (single precision), for up to mcap charge vectors at once
+  void *mq = nullptr, *mqsm = nullptr, *mM = nullptr, *mA = nullptr, *mB = nullptr;
+  int mcap = 0;
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
   void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
@@ -265,5 +270,12 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const
 hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad, cudaStream_t st);
+// multi-RHS evaluation of nr charge vectors in one set of passes (single
+// precision); qs: nr n floats, qsm: n fmm_multi_rp(nr) floats, M/A/B: nr nbox
+// (p+1) complex floats each
+bool fmm_multi_supported(const hpfmm_plan *pl);
+int fmm_multi_rp(int nr);
+hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot, double *grad,
+                            void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st);
 bool is_device_pointer(const void *p);
 hpfmm_status plan_dalloc(hpfmm_plan *pl, void **p, size_t bytes);

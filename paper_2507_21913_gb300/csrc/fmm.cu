@@ -29,9 +29,12 @@
 // and conj(L)/2 to B; Phi_2^+ contributes to A and Phi_2^- to B.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "pairs.cuh"
 #include "special.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -40,6 +43,13 @@ constexpr int kWarpsPerBlock = 4;
 // box side, its reciprocal and log per level, computed once on the host and
 // passed by value, so that no kernel repeats double-precision set-up
 // arithmetic per thread (GB300's FP64 pipe is narrow)
+// strides between the right-hand sides of a multi-RHS evaluation (blockIdx.y
+// = RHS index): q in charges, m in expansion coefficients, out in doubles of
+// the potential (the gradient has twice that)
+struct RhsStride {
+  int64_t q, m, out;
+};
+
 struct LevelGeom {
   float d[16], invd[16];
   double logd[16];
@@ -63,11 +73,17 @@ __device__ __forceinline__ cpx<R> ldc(const cpx<R> *p) {
 
 // --------------------------------------------------------------------------
 // gather the charges into tree order
+// (blockIdx.y = RHS; qsm, when given, also receives the charges point-major:
+// qsm[k * rp + r], for the multi-RHS near field)
 template <typename R>
 __global__ void k_gather_q(const double *__restrict__ q, const int64_t *__restrict__ perm,
-                           int64_t n, R *__restrict__ qs) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) qs[k] = (R)q[perm[k]];
+                           int64_t n, R *__restrict__ qs, R *__restrict__ qsm, int rp) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int r = blockIdx.y;
+  const R v = (R)q[(size_t)r * n + perm[k]];
+  qs[(size_t)r * n + k] = v;
+  if (qsm) qsm[(size_t)k * rp + r] = v;
 }
 
 // point position relative to its leaf centre, in units of the leaf side
@@ -182,8 +198,11 @@ __device__ __forceinline__ cpx<R> cpow_int(cpx<R> w, int n) {
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
-             int H, double x0, double side, R invd_leaf, int p, cpx<R> *__restrict__ M) {
+             int H, double x0, double side, R invd_leaf, int p, cpx<R> *__restrict__ M,
+             RhsStride rs) {
   const int P1 = p + 1;
+  qs += blockIdx.y * rs.q;
+  M += blockIdx.y * rs.m;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < 4^12 * 41 < 2^32
   const unsigned nleaf = 1u << (2 * H);
   if (t >= nleaf * (unsigned)P1) return;
@@ -211,6 +230,50 @@ k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict_
   M[(size_t)(level_offset(H)) * P1 + t] = acc;
 }
 
+// Multi-RHS S2M (single precision): the powers ((z_j - z_c)/d)^n of a point
+// are formed once and applied to RC charge vectors (blockIdx.y selects RHS
+// r0 .. r0 + RC - 1; charges point-major, qsm[k * rp + r]), with the same
+// compensated summation per RHS as k_s2m_thread.
+template <int RC>
+__global__ void __launch_bounds__(256)
+k_s2m_multi(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp, int nr,
+            const int *__restrict__ leaf_start, int H, float invd, int p, cf *__restrict__ M,
+            RhsStride rs) {
+  const int P1 = p + 1;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nleaf = 1u << (2 * H);
+  if (t >= nleaf * (unsigned)P1) return;
+  const unsigned leaf = t / (unsigned)P1;
+  const int n = (int)(t - leaf * (unsigned)P1);
+  const int r0 = blockIdx.y * RC;
+  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  cf acc[RC], cmp[RC];
+#pragma unroll
+  for (int c = 0; c < RC; ++c) acc[c] = cmp[c] = mk(0.f, 0.f);
+  for (int j = b0; j < b1; ++j) {
+    const float2 v = loc[j];
+    const cf wn = cpow_int(mk(v.x * invd, v.y * invd), n);
+    const float4 *qv = reinterpret_cast<const float4 *>(qsm + (size_t)j * rp + r0);
+#pragma unroll
+    for (int c4 = 0; c4 < RC / 4; ++c4) {
+      const float4 qq = __ldg(qv + c4);
+      const float qa[4] = {qq.x, qq.y, qq.z, qq.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = 4 * c4 + u;
+        const cf yv = qa[u] * wn - cmp[c];
+        const cf tv = acc[c] + yv;
+        cmp[c] = (tv - acc[c]) - yv;
+        acc[c] = tv;
+      }
+    }
+  }
+  const size_t e = (size_t)level_offset(H) * P1 + t;
+#pragma unroll
+  for (int c = 0; c < RC; ++c)
+    if (r0 + c < nr) M[(r0 + c) * rs.m + e] = acc[c];
+}
+
 // --------------------------------------------------------------------------
 // Fused upward pass.  The tree below level l0 = H - k (k = min(3, H - 1)) is
 // split into subtrees of 4^k leaves; one block per subtree forms the leaf
@@ -228,9 +291,10 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
          int k, double x0, double side, int p, const cpx<R> *__restrict__ Tm2m,
-         cpx<R> *__restrict__ M) {
+         cpx<R> *__restrict__ M, RhsStride rs) {
   extern __shared__ unsigned char smem_raw[];
   const int P1 = p + 1;
+  M += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
   cpx<R> *Ms = T + 4 * P1 * P1;                       // subtree boxes, level by level
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -271,8 +335,10 @@ k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ le
 // M2M for the coarse levels l0 - 1 .. 1, one block, level by level
 template <typename R>
 __global__ void __launch_bounds__(1024)
-k_m2m_coarse(int l0, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M) {
+k_m2m_coarse(int l0, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M,
+             RhsStride rs) {
   const int P1 = p + 1;
+  M += blockIdx.y * rs.m;
   for (int l = l0 - 1; l >= 1; --l) {
     const int nb = 1 << (2 * l);
     for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) {
@@ -293,8 +359,10 @@ k_m2m_coarse(int l0, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict_
 template <typename R>
 __global__ void __launch_bounds__(1024)
 k_l2l_coarse(int l0, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
-             cpx<R> *__restrict__ B) {
+             cpx<R> *__restrict__ B, RhsStride rs) {
   const int P1 = p + 1;
+  A += blockIdx.y * rs.m;
+  B += blockIdx.y * rs.m;
   for (int l = 2; l <= l0; ++l) {
     const int nb = 1 << (2 * l);
     for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) {
@@ -320,9 +388,11 @@ k_l2l_coarse(int l0, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict_
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
-           cpx<R> *__restrict__ B) {
+           cpx<R> *__restrict__ B, RhsStride rs) {
   extern __shared__ unsigned char smem_raw[];
   const int P1 = p + 1;
+  A += blockIdx.y * rs.m;
+  B += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
   cpx<R> *buf = T + 4 * P1 * P1;  // two ping-pong regions of 4^(k-1) boxes x (A, B);
                                   // the leaf level goes straight to global memory
@@ -482,7 +552,11 @@ template <typename R, int P1>
 __global__ void __launch_bounds__(128)
 k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
                  const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
-                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status) {
+                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status,
+                 RhsStride rs) {
+  M += blockIdx.y * rs.m;
+  A += blockIdx.y * rs.m;
+  B += blockIdx.y * rs.m;
   // rows padded to an even length PP so that k, k+1 pairs are one 16-byte
   // (single precision) shared-memory load; the source patch is stored with
   // even columns first, so that the sources of a warp's x-consecutive
@@ -624,20 +698,34 @@ int patch_blocks(int H) {
 // exists for this order / precision or it does not fit in shared memory
 template <typename R>
 bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, const cd *logt,
-                      const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st) {
+                      const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st,
+                      int nr, RhsStride rs) {
   if (!Tpad) return false;
   int nb = patch_blocks(H);
+  // the shared-memory attribute is set once per device and order (so that a
+  // stream capture of an evaluation issues launches only)
+  static std::mutex mu;
+  static signed char attr[64][2][41];  // 0 unknown, 1 set, -1 failed
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || p < 0 || p > 40) return false;
+  const int pr = sizeof(R) == 8 ? 1 : 0;
 #define HP_PATCH_CASE(PP)                                                                 \
   case PP: {                                                                              \
     size_t sm = patch_smem<R, PP + 1>();                                                  \
     if (sm > 227 * 1024) return false;                                                    \
-    if (cudaFuncSetAttribute(k_m2l_free_patch<R, PP + 1>,                                 \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=     \
-        cudaSuccess) {                                                                    \
-      cudaGetLastError();                                                                 \
-      return false;                                                                       \
+    {                                                                                     \
+      std::lock_guard<std::mutex> lock(mu);                                               \
+      if (attr[dev][pr][p] == 0) {                                                        \
+        bool ok = cudaFuncSetAttribute(k_m2l_free_patch<R, PP + 1>,                       \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                       (int)sm) == cudaSuccess;                           \
+        if (!ok) cudaGetLastError();                                                      \
+        attr[dev][pr][p] = ok ? 1 : -1;                                                   \
+      }                                                                                   \
+      if (attr[dev][pr][p] < 0) return false;                                             \
     }                                                                                     \
-    k_m2l_free_patch<R, PP + 1><<<nb, 128, sm, st>>>(H, lgm, Tpad, logt, M, A, B, status); \
+    k_m2l_free_patch<R, PP + 1><<<dim3(nb, nr), 128, sm, st>>>(H, lgm, Tpad, logt, M, A, B,  \
+                                                               status, rs);                \
     return true;                                                                          \
   }
   switch (p) {
@@ -646,6 +734,209 @@ bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, co
     default: return false;
   }
 #undef HP_PATCH_CASE
+}
+
+// --------------------------------------------------------------------------
+// Free-space M2L for many charge vectors on the tensor cores (single
+// precision path).  With R charge vectors the translations of one level are
+// a batch of small dense products that share their matrices: for a V-list
+// offset class delta, L_t[r] += T_delta M_{t + delta}[r] for every target t of
+// one child type and every RHS r.  In real form (K = 2(p+1) inputs Re M, Im M;
+// 2(p+1) outputs Re L, Im L) one CTA computes a tile of 128 rows -- G target
+// boxes of one child type x 128/G RHS -- as D = sum_delta A_delta B_delta^T
+// with tcgen05 kind::tf32 MMAs accumulating in tensor memory, where A_delta
+// holds the source moments of the tile's rows and B_delta the real form of
+// T_delta (plus the level's M_0 ln|t d| term on Re L_0).  Operands are split
+// into tf32 hi + lo parts and multiplied as hi*hi + hi*lo + lo*hi, which keeps
+// about 21 bits -- the accuracy of the FP32 FMA kernel.  The 27 classes of the
+// child type are taken one after the other: stage A and B in shared memory
+// (all threads), one thread issues the MMAs and commits them to an mbarrier,
+// every thread waits (bounded) before the buffers are reused.
+template <int P1>
+__global__ void __launch_bounds__(128)
+k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
+              const cd *__restrict__ logt, const cf *__restrict__ M, cf *__restrict__ A,
+              cf *__restrict__ B, RhsStride rs, int *__restrict__ status) {
+  constexpr int PP = (P1 + 1) & ~1;
+  constexpr int KP = (2 * P1 + 7) / 8 * 8;
+  constexpr int NP = (2 * P1 + 15) / 16 * 16;
+  constexpr unsigned NCOL = NP <= 32 ? 32u : (NP <= 64 ? 64u : 128u);
+  extern __shared__ __align__(1024) float tsm[];
+  float *ahi = tsm, *alo = ahi + 128 * KP, *bhi = alo + 128 * KP, *blo = bhi + NP * KP;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ unsigned tslot;
+  __shared__ int failed;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int G = 128 / rct;
+  const int type = blockIdx.x & 3, grp = blockIdx.x >> 2;
+  const int a = type & 1, bb = type >> 1;
+  const int r0 = blockIdx.y * rct;
+  const int nside = 1 << l, npar = 1 << (2 * (l - 1));
+  const int64_t off = level_offset(l);
+  const int g = tid / rct, rr = tid % rct;
+  const int pm = grp * G + g;
+  const bool rvalid = pm < npar && r0 + rr < nr;
+  const int tx = pm < npar ? 2 * box_ix(pm) + a : 0, ty = pm < npar ? 2 * box_iy(pm) + bb : 0;
+  const cf *Mr = M + (size_t)(r0 + rr) * rs.m;
+  if (warp == 0) tc_alloc(&tslot, NCOL);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    failed = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tbase = tslot;
+  const uint32_t idesc = tc_idesc_tf32(128, NP);
+  const unsigned sbo_a = (unsigned)(KP / 4) * 128u;
+  int it = 0;
+  for (int dy = -2 - bb; dy <= 3 - bb; ++dy) {
+    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      const int c = (dy + 3) * 7 + (dx + 3);
+      const int slot = c_slot[c];
+      // A: this thread's row -- the source moments of (target, RHS) in real form
+      {
+        const int sx = tx + dx, sy = ty + dy;
+        const bool ok = rvalid && sx >= 0 && sy >= 0 && sx < nside && sy < nside;
+        const cf *src = Mr + (size_t)(off + (ok ? box_morton(sx, sy) : 0)) * P1;
+        float re[P1], im[P1];
+#pragma unroll
+        for (int m = 0; m < P1; ++m) {
+          const cf v = ok ? src[m] : mk(0.f, 0.f);
+          re[m] = v.x;
+          im[m] = v.y;
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+          const float v = k < P1 ? re[k] : (k < 2 * P1 ? im[k - P1] : 0.f);
+          float h, lo;
+          tc_split(v, h, lo);
+          ahi[tc_off(tid, k, KP)] = h;
+          alo[tc_off(tid, k, KP)] = lo;
+        }
+      }
+      // B: the real form of T_delta, K-major (row = output, column = input)
+      const cf *T = Tpad + (size_t)slot * P1 * PP;
+      const float lgc = (float)logt[c].x + logd;
+      for (int e = tid; e < NP * KP; e += 128) {
+        const int no = e / KP, k = e % KP;
+        float v = 0.f;
+        if (no < 2 * P1 && k < 2 * P1) {
+          const int n = no < P1 ? no : no - P1, m = k < P1 ? k : k - P1;
+          const cf t = T[n * PP + m];
+          const bool imo = no >= P1, imi = k >= P1;
+          v = imo == imi ? t.x : (imo ? t.y : -t.y);
+          if (no == 0 && k == 0) v += lgc;  // M_0 ln|t d| on Re L_0
+        }
+        float h, lo;
+        tc_split(v, h, lo);
+        bhi[tc_off(no, k, KP)] = h;
+        blo[tc_off(no, k, KP)] = lo;
+      }
+      tc_fence_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+#pragma unroll 1
+        for (int s = 0; s < KP / 8; ++s) {
+          const unsigned o = (unsigned)s * 256u;
+          const uint64_t dah = tc_sdesc(smem_u32(ahi) + o, 128u, sbo_a);
+          const uint64_t dal = tc_sdesc(smem_u32(alo) + o, 128u, sbo_a);
+          const uint64_t dbh = tc_sdesc(smem_u32(bhi) + o, 128u, sbo_a);
+          const uint64_t dbl = tc_sdesc(smem_u32(blo) + o, 128u, sbo_a);
+          tc_mma_tf32(tbase, dah, dbh, idesc, it > 0 || s > 0);
+          tc_mma_tf32(tbase, dah, dbl, idesc, true);
+          tc_mma_tf32(tbase, dal, dbh, idesc, true);
+        }
+        tc_commit(&bar);
+      }
+      __syncwarp();
+      if (!mbar_wait_bounded(&bar, (unsigned)(it & 1))) {
+        if (!mbar_wait_bounded(&bar, (unsigned)(it & 1))) failed = 1;
+      }
+      tc_fence_after();
+      __syncthreads();
+      ++it;
+      if (failed) break;
+    }
+    if (failed) break;
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(status, HPFMM_DEV_TIMEOUT);
+  } else {
+    // epilogue: row tid of D -> L_n = D[n] + i D[P1 + n]; A = s L, B = conj(s L)
+    float d[NP];
+#pragma unroll
+    for (int cc = 0; cc < NP; cc += 8)
+      tc_ld8(tbase + ((unsigned)(32 * warp) << 16) + (unsigned)cc, d + cc);
+    if (rvalid) {
+      const float sc = (float)(-0.5 / HP_TWO_PI);
+      const size_t e0 = (size_t)(r0 + rr) * rs.m + (size_t)(off + box_morton(tx, ty)) * P1;
+#pragma unroll
+      for (int n = 0; n < P1; ++n) {
+        const cf v = mk(sc * d[n], sc * d[P1 + n]);
+        A[e0 + n] = v;
+        B[e0 + n] = conj(v);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tbase, NCOL);
+}
+
+template <int P1>
+size_t m2l_tc_smem() {
+  constexpr int KP = (2 * P1 + 7) / 8 * 8;
+  constexpr int NP = (2 * P1 + 15) / 16 * 16;
+  return sizeof(float) * 2 * (size_t)(128 + NP) * KP;
+}
+
+// RHS per tile row group: 16, 32 or 64
+int m2l_tc_rct(int nr) { return nr > 32 ? 64 : (nr > 16 ? 32 : 16); }
+
+// launches the tensor-core M2L for levels 2..H; false if p has no instance
+bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const cf *Tpad, const cd *logt,
+                   const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
+                   RhsStride rs) {
+  if (!Tpad) return false;
+  static std::mutex mu;
+  static signed char attr[64][41];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || p < 0 || p > 40) return false;
+  const int rct = m2l_tc_rct(nr);
+  const int G = 128 / rct;
+  const unsigned ny = (unsigned)((nr + rct - 1) / rct);
+#define HP_TC_CASE(PP)                                                                      \
+  case PP: {                                                                                \
+    const size_t sm = m2l_tc_smem<PP + 1>();                                                \
+    {                                                                                       \
+      std::lock_guard<std::mutex> lock(mu);                                                 \
+      if (attr[dev][p] == 0) {                                                              \
+        bool ok = cudaFuncSetAttribute(k_m2l_free_tc<PP + 1>,                               \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                       (int)sm) == cudaSuccess;                             \
+        if (!ok) cudaGetLastError();                                                        \
+        attr[dev][p] = ok ? 1 : -1;                                                         \
+      }                                                                                     \
+      if (attr[dev][p] < 0) return false;                                                   \
+    }                                                                                       \
+    for (int l = 2; l <= H; ++l) {                                                          \
+      const int npar = 1 << (2 * (l - 1));                                                  \
+      const unsigned nx = (unsigned)(4 * ((npar + G - 1) / G));                             \
+      k_m2l_free_tc<PP + 1><<<dim3(nx, ny), 128, sm, st>>>(l, rct, nr, (float)lgm.logd[l],  \
+                                                           Tpad, logt, M, A, B, rs, status); \
+    }                                                                                       \
+    return true;                                                                            \
+  }
+  switch (p) {
+    HP_TC_CASE(4) HP_TC_CASE(6) HP_TC_CASE(8) HP_TC_CASE(10) HP_TC_CASE(12)
+    HP_TC_CASE(14) HP_TC_CASE(16) HP_TC_CASE(18) HP_TC_CASE(20)
+    default: return false;
+  }
+#undef HP_TC_CASE
 }
 
 // --------------------------------------------------------------------------
@@ -728,9 +1019,13 @@ template <typename R>
 __global__ void __launch_bounds__(128)
 k_m2l_mirror_all(int H, int p, LevelGeom lgm, const cpx<R> *__restrict__ Timg,
                  const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
-                 const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
+                 const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B,
+                 RhsStride rs) {
   extern __shared__ unsigned char smem_raw[];
   const int P1 = p + 1;
+  M += blockIdx.y * rs.m;
+  A += blockIdx.y * rs.m;
+  B += blockIdx.y * rs.m;
   cpx<R> *red = reinterpret_cast<cpx<R> *>(smem_raw);  // [4 warps][3][P1]
   cpx<R> *msh = red + 4 * 3 * P1;                      // [4 warps][P1]
   int t = blockIdx.x, l = 1;
@@ -1487,6 +1782,377 @@ k_eval32t(const float2 *__restrict__ loc, const float *__restrict__ qs,
   }
 }
 
+// Single-precision leaf evaluation with one target per lane.  A block takes
+// a 4 x 4 tile of leaves -- 16 consecutive Morton leaves, so its targets are
+// one contiguous range of the sorted points -- and stages the 6 x 6 leaves
+// around it in shared memory as (x, y, q) in each point's own leaf frame.
+// Warps take 32 consecutive targets of the tile at a time; a lane finds its
+// target's leaf and sums over that leaf's 3 x 3 neighbourhood in the staged
+// patch (each neighbour range shifted by its exact leaf offset), skipping
+// itself by index.  Lanes of one warp may belong to two or three leaves: they
+// run the same loops with their own bounds.  No per-group split of the
+// sources and no cross-lane reduction.  Then L2P with the target's leaf
+// expansions.  Patches larger than the buffer read from global memory.
+__device__ __forceinline__ void pair_loop(const float4 *__restrict__ src, int lo, int hi,
+                                          float sx, float sy, float &lf, float &gx, float &gy) {
+#pragma unroll 4
+  for (int k = lo; k < hi; ++k) {
+    const float4 s = src[k];
+    const float dx = sx - s.x, dy = sy - s.y;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float qi = s.z * fast_rcp(r2);
+    lf = fmaf(s.z, fast_lg2(r2), lf);
+    gx = fmaf(qi, dx, gx);
+    gy = fmaf(qi, dy, gy);
+  }
+}
+
+__global__ void __launch_bounds__(kEvWarps * 32, 4)
+k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
+          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
+          float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B,
+          double *__restrict__ pot, double *__restrict__ grad) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *src = reinterpret_cast<float4 *>(smem_raw);  // [kTlCap]
+  int *pst = reinterpret_cast<int *>(src + kTlCap);    // [kTlP^2 + 1]
+  int *pbeg = pst + kTlP * kTlP + 1;                   // [kTlP^2]
+  int *ls = pbeg + kTlP * kTlP;                        // [kTl^2 + 1] tile leaf starts
+  const int P1 = p + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = 1 << H;
+  const int tps = nx >= kTl ? nx / kTl : 1;
+  const int tx0 = (blockIdx.x % tps) * kTl, ty0 = (blockIdx.x / tps) * kTl;
+  const int side = nx < kTl ? nx : kTl, nlt = side * side;
+  const uint64_t L0 = box_morton(tx0, ty0);
+  if (warp == 0) {
+    int c0 = 0, c1 = 0;
+    for (int h = 0; h < 2; ++h) {
+      const int pi = lane + 32 * h;
+      if (pi < kTlP * kTlP) {
+        const int lx = tx0 - 1 + pi % kTlP, ly = ty0 - 1 + pi / kTlP;
+        int b0 = 0, cnt = 0;
+        if (lx >= 0 && ly >= 0 && lx < nx && ly < nx) {
+          const uint64_t lf = box_morton(lx, ly);
+          b0 = leaf_start[lf];
+          cnt = leaf_start[lf + 1] - b0;
+        }
+        pbeg[pi] = b0;
+        if (h == 0) c0 = cnt; else c1 = cnt;
+      }
+    }
+    int i0 = c0, i1 = c1;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
+      if (lane >= o) { i0 += a0; i1 += a1; }
+    }
+    const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
+    pst[lane] = i0 - c0;
+    if (lane + 32 < kTlP * kTlP) pst[lane + 32] = tot0 + i1 - c1;
+    if (lane == kTlP * kTlP - 32 - 1) pst[kTlP * kTlP] = tot0 + i1;
+  } else if (warp == 1 && lane <= nlt) {
+    ls[lane] = leaf_start[L0 + lane];
+  }
+  __syncthreads();
+  const bool staged = pst[kTlP * kTlP] <= kTlCap;
+  if (staged) {
+    for (int pi = warp; pi < kTlP * kTlP; pi += kEvWarps) {
+      const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
+      for (int j = lane; j < cnt; j += 32) {
+        const float2 v = loc[b0 + j];
+        src[o + j] = make_float4(v.x, v.y, qs[b0 + j], 0.f);
+      }
+    }
+  }
+  __syncthreads();
+  const int t0 = ls[0], t1 = ls[nlt];
+  const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+  const float i2pi = (float)(1.0 / HP_TWO_PI);
+  for (int tb = t0 + 32 * warp; tb < t1; tb += 32 * kEvWarps) {
+    const int i = tb + lane;
+    const bool act = i < t1;
+    // the target's leaf: the last tile leaf whose start is <= i
+    int li = 0;
+    for (int step = 8; step > 0; step >>= 1)
+      if (li + step < nlt && ls[li + step] <= i) li += step;
+    const uint64_t leaf = L0 + li;
+    const int ix = box_ix(leaf), iy = box_iy(leaf);
+    const int px = ix - tx0 + 1, py = iy - ty0 + 1;
+    float lf = 0.f, gx = 0.f, gy = 0.f;
+    float2 me = make_float2(0.f, 0.f);
+    if (staged) {
+      const int kself = pst[py * kTlP + px] + (i - ls[li]);
+      if (act) {
+        const float4 m4 = src[kself];
+        me = make_float2(m4.x, m4.y);
+      }
+#pragma unroll 1
+      for (int r = -1; r <= 1; ++r) {
+#pragma unroll 1
+        for (int c = -1; c <= 1; ++c) {
+          const int pi = (py + r) * kTlP + (px + c);
+          int lo = pst[pi], hi = pst[pi + 1];
+          if (!act) hi = lo;
+          const float sx = me.x - (float)c * d, sy = me.y - (float)r * d;
+          if (r == 0 && c == 0) {
+            pair_loop(src, lo, act ? kself : lo, sx, sy, lf, gx, gy);
+            pair_loop(src, act ? kself + 1 : hi, hi, sx, sy, lf, gx, gy);
+          } else {
+            pair_loop(src, lo, hi, sx, sy, lf, gx, gy);
+          }
+        }
+      }
+    } else if (act) {
+      me = loc[i];
+      for (int r = -1; r <= 1; ++r) {
+        for (int c = -1; c <= 1; ++c) {
+          const int mx = ix + c, my = iy + r;
+          if (mx < 0 || my < 0 || mx >= nx || my >= nx) continue;
+          const uint64_t sl = box_morton(mx, my);
+          const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+          const float sx = me.x - (float)c * d, sy = me.y - (float)r * d;
+          for (int k = s0; k < s1; ++k) {
+            if (k == i) continue;
+            const float2 v = loc[k];
+            const float q = qs[k];
+            const float dx = sx - v.x, dy = sy - v.y;
+            const float r2 = fmaf(dx, dx, dy * dy);
+            const float qi = q * fast_rcp(r2);
+            lf = fmaf(q, fast_lg2(r2), lf);
+            gx = fmaf(qi, dx, gx);
+            gy = fmaf(qi, dy, gy);
+          }
+        }
+      }
+    }
+    if (!act) continue;
+    const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+    const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+    const cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
+    cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
+    for (int n = p - 1; n >= 0; --n) {
+      da = da * w + va;
+      va = va * w + Al[n];
+      db = db * wb + vb;
+      vb = vb * wb + Bl[n];
+    }
+    const float ur_ = va.x + vb.x - lf * c4;
+    const float ui_ = va.y + vb.y;
+    const cf gxo = invd * (da + db) + mk(-gx * i2pi, 0.f);
+    const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-gy * i2pi, 0.f);
+    const int64_t o = perm[i];
+    reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
+    if (grad) {
+      double4 gv;
+      gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
+      reinterpret_cast<double4 *>(grad)[o] = gv;
+    }
+  }
+}
+constexpr size_t kTpSmem = sizeof(float4) * kTlCap + sizeof(int) * (3 * kTlP * kTlP + 1 + kTl * kTl + 1);
+
+// Multi-RHS leaf evaluation (single precision).  The free-space near-field
+// pair kernel -- log2 r^2 and (dx, dy) / r^2 -- is formed once per pair and
+// applied to RC charge vectors (blockIdx.y selects RHS r0 .. r0 + RC - 1),
+// then the local expansions of each RHS are evaluated (L2P).  A block takes
+// eight Morton-consecutive leaves (a 4 x 2 tile, one warp per leaf) and stages
+// the 6 x 4 leaves around it in shared memory: positions (leaf frame) and the
+// RC charges of each point (point-major rows of qsm, qsm[k * rp + r], so one
+// 16-byte load carries four RHS).  Patches larger than the buffer read the
+// same data from global memory.  Padded RHS r >= nr carry arbitrary charges
+// and are not written.
+constexpr int kMpW = 6, kMpH = 4, kMpCap = 1024;
+
+template <int RC>
+struct MultiAcc {
+  float lf[RC], gx[RC], gy[RC];
+};
+
+template <int RC, bool CHECK>
+__device__ __forceinline__ void multi_range(const float2 *pos, const float4 *qv, int lo, int hi,
+                                            int g, int ng, float sx, float sy, MultiAcc<RC> &a) {
+#pragma unroll 2
+  for (int k = lo + g; k < hi; k += ng) {
+    const float2 v = pos[k];
+    const float dx = sx - v.x, dy = sy - v.y;
+    float r2 = fmaf(dx, dx, dy * dy);
+    float lg, ir;
+    if (CHECK) {
+      const bool ok = r2 > 0.f;
+      r2 = ok ? r2 : 1.f;
+      lg = ok ? fast_lg2(r2) : 0.f;
+      ir = ok ? fast_rcp(r2) : 0.f;
+    } else {
+      lg = fast_lg2(r2);
+      ir = fast_rcp(r2);
+    }
+    const float ex = dx * ir, ey = dy * ir;
+#pragma unroll
+    for (int c = 0; c < RC / 4; ++c) {
+      const float4 qq = qv[(size_t)k * (RC / 4) + c];
+      a.lf[4 * c] = fmaf(qq.x, lg, a.lf[4 * c]);
+      a.lf[4 * c + 1] = fmaf(qq.y, lg, a.lf[4 * c + 1]);
+      a.lf[4 * c + 2] = fmaf(qq.z, lg, a.lf[4 * c + 2]);
+      a.lf[4 * c + 3] = fmaf(qq.w, lg, a.lf[4 * c + 3]);
+      a.gx[4 * c] = fmaf(qq.x, ex, a.gx[4 * c]);
+      a.gx[4 * c + 1] = fmaf(qq.y, ex, a.gx[4 * c + 1]);
+      a.gx[4 * c + 2] = fmaf(qq.z, ex, a.gx[4 * c + 2]);
+      a.gx[4 * c + 3] = fmaf(qq.w, ex, a.gx[4 * c + 3]);
+      a.gy[4 * c] = fmaf(qq.x, ey, a.gy[4 * c]);
+      a.gy[4 * c + 1] = fmaf(qq.y, ey, a.gy[4 * c + 1]);
+      a.gy[4 * c + 2] = fmaf(qq.z, ey, a.gy[4 * c + 2]);
+      a.gy[4 * c + 3] = fmaf(qq.w, ey, a.gy[4 * c + 3]);
+    }
+  }
+}
+
+template <int RC>
+__global__ void __launch_bounds__(kEvWarps * 32, 2)
+k_eval32m(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp, int nr,
+          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
+          float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B, RhsStride rs,
+          double *__restrict__ pot, double *__restrict__ grad) {
+  constexpr int NP = kMpW * kMpH;
+  __shared__ float2 spos[kMpCap];
+  __shared__ float4 sq[kMpCap * (RC / 4)];
+  __shared__ int pst[NP + 1], pbeg[NP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = 1 << H;
+  const int r0 = blockIdx.y * RC;
+  const int leaf0 = blockIdx.x * kEvWarps;
+  const int tx0 = box_ix(leaf0), ty0 = box_iy(leaf0);  // the tile is x0..x0+3, y0..y0+1
+  if (warp == 0) {
+    int cnt = 0, b0 = 0;
+    if (lane < NP) {
+      const int lx = tx0 - 1 + lane % kMpW, ly = ty0 - 1 + lane / kMpW;
+      if (lx >= 0 && ly >= 0 && lx < nx && ly < nx) {
+        const uint64_t lf = box_morton(lx, ly);
+        b0 = leaf_start[lf];
+        cnt = leaf_start[lf + 1] - b0;
+      }
+    }
+    int inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane < NP) {
+      pst[lane] = inc - cnt;
+      pbeg[lane] = b0;
+    }
+    if (lane == NP - 1) pst[NP] = inc;
+  }
+  __syncthreads();
+  const bool staged = pst[NP] <= kMpCap;
+  if (staged) {
+    for (int pi = warp; pi < NP; pi += kEvWarps) {
+      const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
+      for (int j = lane; j < cnt; j += 32) spos[o + j] = loc[b0 + j];
+      for (int e = lane; e < cnt * (RC / 4); e += 32) {
+        const int j = e / (RC / 4), c = e % (RC / 4);
+        sq[(size_t)(o + j) * (RC / 4) + c] =
+            __ldg(reinterpret_cast<const float4 *>(qsm + (size_t)(b0 + j) * rp + r0) + c);
+      }
+    }
+  }
+  __syncthreads();
+  const int leaf = leaf0 + warp;
+  if (leaf >= nx * nx) return;
+  const int P1 = p + 1;
+  const int ix = box_ix(leaf), iy = box_iy(leaf);
+  const int px = ix - tx0 + 1, py = iy - ty0 + 1;  // patch coordinates of the leaf
+  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+  const int T = b1 - b0;
+  const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
+  const int ng = 32 / gs, g = lane / gs, tli = lane % gs;
+  const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+  const float i2pi = (float)(1.0 / HP_TWO_PI);
+  for (int tb = b0; tb < b1; tb += gs) {
+    const int i = tb + tli;
+    const bool act = i < b1;
+    const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+    MultiAcc<RC> a;
+#pragma unroll
+    for (int c = 0; c < RC; ++c) a.lf[c] = a.gx[c] = a.gy[c] = 0.f;
+#pragma unroll 1
+    for (int rr = -1; rr <= 1; ++rr) {
+      const int ny = iy + rr;
+      if (ny < 0 || ny >= nx) continue;
+#pragma unroll 1
+      for (int cc = -1; cc <= 1; ++cc) {
+        const int nxx = ix + cc;
+        if (nxx < 0 || nxx >= nx) continue;
+        const float sx = me.x - (float)cc * d, sy = me.y - (float)rr * d;
+        if (staged) {
+          const int pi = (py + rr) * kMpW + (px + cc);
+          if (rr == 0 && cc == 0)
+            multi_range<RC, true>(spos, sq, pst[pi], pst[pi + 1], g, ng, sx, sy, a);
+          else
+            multi_range<RC, false>(spos, sq, pst[pi], pst[pi + 1], g, ng, sx, sy, a);
+        } else {
+          const uint64_t sl = box_morton(nxx, ny);
+          const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+          // global rows are rp wide: view them as float4 rows of rp / 4 from r0
+          for (int k = s0 + g; k < s1; k += ng) {
+            const float2 v = loc[k];
+            const float dx = sx - v.x, dy = sy - v.y;
+            float r2 = fmaf(dx, dx, dy * dy);
+            const bool ok = !(rr == 0 && cc == 0) || r2 > 0.f;
+            r2 = ok ? r2 : 1.f;
+            const float lg = ok ? fast_lg2(r2) : 0.f;
+            const float ir = ok ? fast_rcp(r2) : 0.f;
+            const float ex = dx * ir, ey = dy * ir;
+            const float4 *qv = reinterpret_cast<const float4 *>(qsm + (size_t)k * rp + r0);
+#pragma unroll
+            for (int c = 0; c < RC / 4; ++c) {
+              const float4 qq = __ldg(qv + c);
+              const float qa[4] = {qq.x, qq.y, qq.z, qq.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                a.lf[4 * c + u] = fmaf(qa[u], lg, a.lf[4 * c + u]);
+                a.gx[4 * c + u] = fmaf(qa[u], ex, a.gx[4 * c + u]);
+                a.gy[4 * c + u] = fmaf(qa[u], ey, a.gy[4 * c + u]);
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+      a.lf[c] = xsum(a.lf[c], gs);
+      a.gx[c] = xsum(a.gx[c], gs);
+      a.gy[c] = xsum(a.gy[c], gs);
+    }
+    if (!act || g != 0) continue;
+    const cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
+    const int64_t o = perm[i];
+    const size_t le = (size_t)(level_offset(H) + leaf) * P1;
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+      const int r = r0 + c;
+      if (r >= nr) break;
+      const cf *Al = A + r * rs.m + le, *Bl = B + r * rs.m + le;
+      cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
+      for (int n = p - 1; n >= 0; --n) {
+        da = da * w + va;
+        va = va * w + Al[n];
+        db = db * wb + vb;
+        vb = vb * wb + Bl[n];
+      }
+      const float ur_ = va.x + vb.x - a.lf[c] * c4;
+      const float ui_ = va.y + vb.y;
+      const cf gxo = invd * (da + db) + mk(-a.gx[c] * i2pi, 0.f);
+      const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-a.gy[c] * i2pi, 0.f);
+      reinterpret_cast<double2 *>(pot + r * rs.out)[o] = make_double2(f2d(ur_), f2d(ui_));
+      if (grad) {
+        double4 gv;
+        gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
+        reinterpret_cast<double4 *>(grad + 2 * r * rs.out)[o] = gv;
+      }
+    }
+  }
+}
+
 // Image and reaction near field of the bottom-row leaves (single precision
 // with the double routine for |P| > 1 and, in MIXED mode, below tau), added
 // to the outputs written by k_eval32g.  One block per bottom-row leaf: the
@@ -1497,7 +2163,11 @@ constexpr int kMirSrc = 512;
 __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-           float d, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad) {
+           float d, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad,
+           RhsStride rs) {
+  qs += blockIdx.y * rs.q;
+  pot += blockIdx.y * rs.out;
+  if (grad) grad += blockIdx.y * 2 * rs.out;
   __shared__ float4 src[kMirSrc];
   __shared__ float red[kEvWarps][9][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1575,9 +2245,17 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
 
 inline unsigned cdiv_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// workspace of a multi-RHS evaluation: nr right-hand sides, rp = nr rounded
+// up to the leaf kernel's RHS chunk; arrays of the evaluation's real type
+struct MultiWork {
+  int nr, rp;
+  void *qs, *qsm, *M, *A, *B;
+};
+constexpr int kRhsChunk = 8;
+
 template <typename R>
 hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *grad,
-                        cudaStream_t st) {
+                        cudaStream_t st, const MultiWork *mw) {
   const int p = pl->p, P1 = p + 1, H = pl->H;
   const int64_t n = pl->n;
   const size_t m2 = (size_t)P1 * P1;
@@ -1592,18 +2270,27 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   const cpx<R> *Timg = tab(pl->t_rlog, 21 * m2);
   const cpx<R> *Treact = tab(pl->t_refl, (size_t)H * 42 * m2);
   const cd *logs = (const cd *)pl->t_rlog0;
-  R *qs = (R *)pl->qs;
-  cpx<R> *M = (cpx<R> *)pl->M, *A = (cpx<R> *)pl->A, *B = (cpx<R> *)pl->B;
+  const int nr = mw ? mw->nr : 1;
+  R *qs = (R *)(mw ? mw->qs : pl->qs);
+  cpx<R> *M = (cpx<R> *)(mw ? mw->M : pl->M), *A = (cpx<R> *)(mw ? mw->A : pl->A);
+  cpx<R> *B = (cpx<R> *)(mw ? mw->B : pl->B);
+  const RhsStride rs{n, pl->nbox * (int64_t)P1, 2 * n};
+  if (mw && (sizeof(R) == 8 || H < 2)) {
+    set_last_error("multi-RHS passes need the single-precision path and >= 2 levels");
+    return HPFMM_EUNSUPPORTED;
+  }
   const LevelGeom lg = level_geom(pl->side, H);
 
   pass_begin(pl, st, PASS_GATHER);
-  k_gather_q<R><<<cdiv_u(n, 256), 256, 0, st>>>(q, pl->perm, n, qs);
+  k_gather_q<R><<<dim3(cdiv_u(n, 256), nr), 256, 0, st>>>(
+      q, pl->perm, n, qs, mw ? (R *)mw->qsm : (R *)nullptr, mw ? mw->rp : 0);
   pass_end(pl, st, PASS_GATHER, 1);
   pass_begin(pl, st, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
   int ksub = H - 4;  // subtrees of 4^ksub leaves, at least 256 of them
   if (ksub > 4) ksub = 4;
   if (ksub < 1) ksub = H - 1 < 1 ? H - 1 : 1;
+  if (pl->subtree > 0) ksub = pl->subtree < H - 1 ? pl->subtree : H - 1;
   while (ksub > 1 && (upward_smem<R>(p, ksub) > kFusedSmem || downward_smem<R>(p, ksub) > kFusedSmem))
     --ksub;
   const int l0 = H - ksub;
@@ -1614,8 +2301,13 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         lp, (const double *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cd *)M);
   } else {
     LeafPoints<float> lp{pl->loc32};
-    k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * P1, 256), 256, 0, st>>>(
-        lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, lg.invd[H], p, (cf *)M);
+    if (mw)
+      k_s2m_multi<kRhsChunk><<<dim3(cdiv_u((int64_t)pl->nleaf * P1, 256), mw->rp / kRhsChunk),
+                               256, 0, st>>>(pl->loc32, (const float *)mw->qsm, mw->rp, nr,
+                                             pl->leaf_start, H, lg.invd[H], p, (cf *)M, rs);
+    else
+      k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * P1, 256), 256, 0, st>>>(
+          lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, lg.invd[H], p, (cf *)M, rs);
   }
   pass_end(pl, st, PASS_P2M, 1);
   pass_begin(pl, st, PASS_M2M);
@@ -1625,26 +2317,35 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     if (sizeof(R) == 8) {
       LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
       k_upward<double><<<nb, 256, sm, st>>>(lp, (const double *)qs, pl->leaf_start, H, ksub,
-                                            pl->x0, pl->side, p, (const cd *)Tm2m, (cd *)M);
+                                            pl->x0, pl->side, p, (const cd *)Tm2m, (cd *)M, rs);
     } else {
       LeafPoints<float> lp{pl->loc32};
-      k_upward<float><<<nb, 256, sm, st>>>(lp, (const float *)qs, pl->leaf_start, H, ksub,
-                                           pl->x0, pl->side, p, (const cf *)Tm2m, (cf *)M);
+      k_upward<float><<<dim3(nb, nr), 256, sm, st>>>(lp, (const float *)qs, pl->leaf_start, H,
+                                                     ksub, pl->x0, pl->side, p,
+                                                     (const cf *)Tm2m, (cf *)M, rs);
     }
   }
 
-  if (l0 > 1) k_m2m_coarse<R><<<1, 1024, 0, st>>>(l0, p, Tm2m, M);
+  if (l0 > 1) k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(l0, p, Tm2m, M, rs);
   pass_end(pl, st, PASS_M2M, (ksub > 0 ? 1 : 0) + (l0 > 1 ? 1 : 0));
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
   size_t shmir = sizeof(cpx<R>) * P1 * kWarpsPerBlock;
-  bool patched = false;
+  bool patched = false, tc_m2l = false;
   if (H >= 2 && sizeof(R) == 4) {
     pass_begin(pl, st, PASS_M2L_FREE);
-    patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
-                                  pl->status, st);
-    pass_end(pl, st, PASS_M2L_FREE, patched ? 1 : 0);
+    if (mw && nr >= 16 && pl->m2l_mode == 1)
+      tc_m2l = patched = launch_m2l_tc(p, H, lg, (const cf *)pl->t_m2l_pad, logs, (const cf *)M, (cf *)A,
+                              (cf *)B, pl->status, st, nr, rs);
+    if (!patched)
+      patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
+                                    pl->status, st, nr, rs);
+    pass_end(pl, st, PASS_M2L_FREE, patched ? (tc_m2l ? H - 1 : 1) : 0);
+  }
+  if (mw && !patched) {
+    set_last_error("multi-RHS passes need the patch M2L kernel (even p in 4..20)");
+    return HPFMM_EUNSUPPORTED;
   }
   for (int l = 1; l <= H; ++l) {
     double logd = log(pl->side / (double)(1 << l));
@@ -1660,14 +2361,15 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   {
     unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
     size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
-    k_m2l_mirror_all<R><<<nb, 128, sm, st>>>(H, p, lg, Timg, logs + 49, Treact, M, A, B);
+    k_m2l_mirror_all<R><<<dim3(nb, nr), 128, sm, st>>>(H, p, lg, Timg, logs + 49, Treact, M, A,
+                                                         B, rs);
   }
   pass_end(pl, st, PASS_M2L_MIRROR, 1);
   pass_begin(pl, st, PASS_L2L);
-  if (l0 >= 2) k_l2l_coarse<R><<<1, 1024, 0, st>>>(l0, p, Tl2l, A, B);
+  if (l0 >= 2) k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(l0, p, Tl2l, A, B, rs);
   if (ksub > 0)
-    k_downward<R><<<(unsigned)(int64_t(1) << (2 * l0)), 256, downward_smem<R>(p, ksub), st>>>(
-        H, ksub, p, Tl2l, A, B);
+    k_downward<R><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256, downward_smem<R>(p, ksub),
+                    st>>>(H, ksub, p, Tl2l, A, B, rs);
   pass_end(pl, st, PASS_L2L, (l0 >= 2 ? 1 : 0) + (ksub > 0 ? 1 : 0));
   pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
@@ -1678,7 +2380,12 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         kappa, (const cd *)A, (const cd *)B, pot, grad);
   } else {
     float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
-    {
+    if (mw) {
+      k_eval32m<kRhsChunk><<<dim3(cdiv_u(pl->nleaf, kEvWarps), mw->rp / kRhsChunk),
+                             32 * kEvWarps, 0, st>>>(
+          pl->loc32, (const float *)mw->qsm, mw->rp, nr, pl->perm, pl->leaf_start, H, lg.d[H],
+          lg.invd[H], p, (const cf *)A, (const cf *)B, rs, pot, grad);
+    } else {
       const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
       k_eval32t<<<(unsigned)(tps * tps), 32 * kEvWarps, kTlSmem, st>>>(
           pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
@@ -1686,9 +2393,9 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     }
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
-    k_mirror32<<<(unsigned)(1 << H), 32 * kEvWarps, 0, st>>>(
+    k_mirror32<<<dim3((unsigned)(1 << H), nr), 32 * kEvWarps, 0, st>>>(
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], kappa, tau, pot,
-        grad);
+        grad, rs);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
   if (sizeof(R) == 8) pass_end(pl, st, PASS_EVAL, 1);
@@ -1719,6 +2426,8 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_eval32t, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTlSmem));
+  HP_CUDA(cudaFuncSetAttribute(k_eval32p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1734,6 +2443,23 @@ hpfmm_status fmm_set_smem_limits(int p) {
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
                       cudaStream_t st) {
   HP_TRY(special_init_here());
-  if (pl->prec == HPFMM_FP64) return run_passes<double>(pl, q, pot, grad, st);
-  return run_passes<float>(pl, q, pot, grad, st);
+  if (pl->prec == HPFMM_FP64) return run_passes<double>(pl, q, pot, grad, st, nullptr);
+  return run_passes<float>(pl, q, pot, grad, st, nullptr);
+}
+
+bool fmm_multi_supported(const hpfmm_plan *pl) {
+  return pl->prec != HPFMM_FP64 && pl->H >= 2 && pl->p >= 4 && pl->p <= 20 && pl->p % 2 == 0;
+}
+
+int fmm_multi_rp(int nr) { return (nr + kRhsChunk - 1) / kRhsChunk * kRhsChunk; }
+
+hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot, double *grad,
+                            void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st) {
+  HP_TRY(special_init_here());
+  if (!fmm_multi_supported(pl)) {
+    set_last_error("multi-RHS passes need single precision, >= 2 levels and even p in 4..20");
+    return HPFMM_EUNSUPPORTED;
+  }
+  const MultiWork mw{nr, fmm_multi_rp(nr), qs, qsm, M, A, B};
+  return run_passes<float>(pl, q, pot, grad, st, &mw);
 }
