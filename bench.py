@@ -182,7 +182,7 @@ def vlist_translations(H):
 
 # kernels that make up a pass with one launch per step (the candidates for the
 # dominant-kernel roofline)
-SINGLE_KERNEL = {"eval": ("k_eval32t", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
+SINGLE_KERNEL = {"eval": ("k_eval32p", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
                  "m2l_mirror": ("k_m2l_mirror_all", "k_m2l_mirror_all"),
                  "p2m": ("k_p2m", "k_p2m"), "near_mirror": ("k_mirror32", None)}
 
@@ -294,7 +294,7 @@ def extra_workloads(args, dev, flush, check):
     x, y, q = workloads.clustered(n, seed=0)
     xd, yd, qd = t(x), t(y), t(q)
     kap = 1.0 + 0.5j
-    plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec="mixed", levels=10)
+    plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec="mixed", levels=11)
     pot = torch.empty(n, dtype=torch.complex128, device=dev)
     grad = torch.empty((n, 2), dtype=torch.complex128, device=dev)
 
@@ -303,7 +303,7 @@ def extra_workloads(args, dev, flush, check):
         hp.hpfmm_eval(plan, qd, out=(pot, grad))
     ms = _event_time(step, k, w, flush)
     e = {"workload": "clustered N=4e6 (80%% in 64 clusters sigma 0.01 near y=0), kappa=1+0.5i, "
-                     "mixed precision, p=20, L=10, tree rebuilt every step", "ms_per_step": ms,
+                     "mixed precision, p=20, L=11, tree rebuilt every step", "ms_per_step": ms,
          "value": float(n) * n / (ms / 1e3), "unit": UNIT}
     if check:
         near = np.flatnonzero(y < 0.06)
@@ -377,6 +377,36 @@ def extra_workloads(args, dev, flush, check):
                       "value": pairs / (ms_g / 1e3), "unit": UNIT,
                       "graph_captures": batch.captures()}
     del batch, plans
+
+    # separate targets: the Example 2 geometry (8 charged circles, field mesh
+    # including y = 0) at 2e5 sources and 1.25e5 field points
+    xs, ys, qs, xt, yt = workloads.example2(n_source=25_000, nfx=512, nfy=245)
+    plan = hp.hpfmm_create(t(xs), t(ys), kappa=1.0, p=16, leaf_size=32, prec="fp32", levels=9,
+                           root=(-4.4, 8.8))
+    qd, xtd, ytd = t(qs), t(xt), t(yt)
+    ms_t = _event_time(lambda: hp.hpfmm_eval_targets(plan, qd, xtd, ytd), k, w, flush)
+    e = {"workload": "Example 2 geometry: 8 circles x 25000 sources (charge 2pi/25000), "
+                     "512 x 245 field mesh on [-4.4,4.4]x[0,4.2], kappa=1, fp32 plan p=16, L=9",
+         "ms_per_eval": ms_t, "value": float(len(xs)) * len(xt) / (ms_t / 1e3), "unit": UNIT}
+    if check:
+        pot, _ = hp.hpfmm_eval_targets(plan, qd, xtd, ytd, grad=False)
+        idx = np.linspace(0, len(xt) - 1, 8).astype(np.int64)
+        import oracle
+        u_ref, _ = oracle.direct(xs, ys, qs, xt=xt[idx], yt=yt[idx], kappa=1.0, grad=False)
+        u = pot.cpu().numpy()[idx]
+        e["rel_err_pot"] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+        e["check_targets"] = len(idx)
+    out["targets"] = e
+    del plan
+
+    # the autotuner on the headline workload: its pick for single precision at 1e-6
+    n = 1_000_000
+    x, y, _ = workloads.uniform(n, seed=0)
+    t0 = time.perf_counter()
+    tun = hp.hpfmm_autotune(t(x), t(y), kappa=1.0, prec="fp32", tol=1e-6, nsample=256)
+    tun["tuning_seconds"] = time.perf_counter() - t0
+    tun["workload"] = "uniform N=1e6, kappa=1, fp32, tol 1e-6 (probe charges, 256 sampled targets)"
+    out["autotune"] = tun
     return out
 
 

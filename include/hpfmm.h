@@ -78,6 +78,12 @@ typedef struct {
                            1 the tensor cores (tcgen05 kind::tf32, three-term split
                            products accumulated in tensor memory) */
   int reserved[3];      /* must be zero */
+  double root_x0;       /* with root_side > 0: the root square of the tree is
+                           [root_x0, root_x0 + root_side] x [0, root_side] instead of the
+                           points' bounding square; it must contain every point
+                           (EINVAL otherwise).  Used to cover separate targets
+                           (hpfmm_eval_targets). */
+  double root_side;
 } hpfmm_options;
 
 /* Fill *opt with the defaults. */
@@ -218,6 +224,25 @@ typedef struct {
 hpfmm_status hpfmm_autotune(const double *x, const double *y, int64_t n, double kappa_re,
                             double kappa_im, int prec, double tol, int nsample, void *stream,
                             hpfmm_tuning *out);
+
+/*
+ * hpfmm_eval_targets -- u and its gradient at nt separate targets (the paper's
+ * Example 2: field points on a mesh, including points on y = 0), from the
+ * plan's sources with charges q (Algorithm 2 with the evaluation moved from
+ * the sources to the targets: the far field from the local expansion of the
+ * leaf containing the target, the near field -- free part, and image and
+ * reaction parts next to y = 0 -- from the sources of the 3 x 3 neighbouring
+ * leaves, summed in double precision).
+ *   q      : n doubles, the sources' charges (caller order).
+ *   xt, yt : nt doubles, finite, y_t >= 0, inside the plan's root square (create
+ *            the plan with opt.root_x0 / root_side covering them); EINVAL otherwise.
+ *   pot    : nt complex doubles; grad: NULL or nt x 2 complex doubles.
+ * A target that coincides with a source skips that pair's free term.  All
+ * arrays device memory.  Validates the targets with one synchronisation.
+ */
+hpfmm_status hpfmm_eval_targets(hpfmm_plan *plan, const double *q, const double *xt,
+                                const double *yt, int64_t nt, double *pot, double *grad,
+                                void *stream);
 
 /* Release every device allocation of the plan (synchronises its stream). */
 hpfmm_status hpfmm_destroy(hpfmm_plan *plan);

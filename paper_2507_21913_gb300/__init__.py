@@ -30,7 +30,8 @@ class HpfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tau_fp64", ctypes.c_double), ("levels", ctypes.c_int),
                 ("subtree_levels", ctypes.c_int), ("m2l_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("reserved", ctypes.c_int * 3), ("root_x0", ctypes.c_double),
+                ("root_side", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -85,13 +86,15 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_batch_destroy.argtypes = [vp]
     L.hpfmm_autotune.argtypes = [vp, vp, i64, dbl, dbl, i32, dbl, i32, vp, ctypes.POINTER(Tuning)]
     L.hpfmm_selftest_tc_gemm.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    L.hpfmm_eval_targets.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
               "hpfmm_get_order", "hpfmm_sync", "hpfmm_set_timing", "hpfmm_read_timing",
               "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc", "hpfmm_eval_adjoint",
               "hpfmm_batch_create", "hpfmm_eval_batched", "hpfmm_batch_captures",
-              "hpfmm_batch_destroy", "hpfmm_autotune", "hpfmm_selftest_tc_gemm"):
+              "hpfmm_batch_destroy", "hpfmm_autotune", "hpfmm_selftest_tc_gemm",
+              "hpfmm_eval_targets"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -150,7 +153,7 @@ class Plan:
 
 
 def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau_fp64=0.05,
-                 subtree_levels=0, m2l_mode=0):
+                 subtree_levels=0, m2l_mode=0, root=None):
     """Build a plan for the points (x, y); see hpfmm_create in include/hpfmm.h."""
     x = _as_tensor(x)
     y = _as_tensor(y, x.device)
@@ -162,6 +165,8 @@ def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau
     opt.tau_fp64 = float(tau_fp64)
     opt.subtree_levels = int(subtree_levels)
     opt.m2l_mode = int(m2l_mode)
+    if root is not None:  # (x0, side): the tree's root square
+        opt.root_x0, opt.root_side = float(root[0]), float(root[1])
     h = ctypes.c_void_p()
     _check(lib().hpfmm_create(x.data_ptr(), y.data_ptr(), x.numel(), kappa.real, kappa.imag,
                               int(p), int(leaf_size), ctypes.byref(opt), _stream(x.device),
@@ -337,6 +342,23 @@ def hpfmm_autotune(x, y, kappa=1.0, prec="fp32", tol=1e-6, nsample=256):
                                 PRECISIONS[prec] if isinstance(prec, str) else int(prec),
                                 float(tol), int(nsample), _stream(x.device), ctypes.byref(t)))
     return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+
+def hpfmm_eval_targets(plan, q, xt, yt, grad=True):
+    """u (and grad u) at separate targets (xt, yt) from the plan's sources with
+    charges q; see include/hpfmm.h.  Device tensors; returns complex128
+    (nt,) and (nt, 2) or None."""
+    torch = _torch()
+    dev = plan.device
+    q = _as_tensor(q, dev).reshape(plan.n)
+    xt = _as_tensor(xt, dev).reshape(-1)
+    yt = _as_tensor(yt, dev).reshape(-1)
+    nt = xt.numel()
+    pot = torch.empty(nt, dtype=torch.complex128, device=dev)
+    g = torch.empty((nt, 2), dtype=torch.complex128, device=dev) if grad else None
+    _check(lib().hpfmm_eval_targets(plan.handle, q.data_ptr(), xt.data_ptr(), yt.data_ptr(), nt,
+                                    pot.data_ptr(), g.data_ptr() if grad else None, _stream(dev)))
+    return pot, g
 
 
 def hpfmm_destroy(plan):

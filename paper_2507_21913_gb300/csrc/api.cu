@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 hpfmm_status fmm_set_smem_limits(int p);
 
@@ -138,7 +139,7 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
                   pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj, pl->mq, pl->mqsm,
-                  pl->mM, pl->mA, pl->mB};
+                  pl->mM, pl->mA, pl->mB, pl->tflag, pl->t_m2l_tc};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -249,7 +250,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     return HPFMM_EINVAL;
   }
   if (o.levels < 0 || o.levels > 15 || !(o.tau_fp64 >= 0) || o.subtree_levels < 0 ||
-      o.subtree_levels > 4 || o.m2l_mode < 0 || o.m2l_mode > 1) {
+      o.subtree_levels > 4 || o.m2l_mode < 0 || o.m2l_mode > 1 || !(o.root_side >= 0) ||
+      !isfinite(o.root_x0) || !isfinite(o.root_side)) {
     set_last_error("hpfmm_create: levels must be in 0..15, subtree_levels in 0..4, m2l_mode in "
                    "0..1, tau_fp64 >= 0");
     return HPFMM_EINVAL;
@@ -262,6 +264,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   pl->tau_fp64 = o.tau_fp64;
   pl->subtree = o.subtree_levels;
   pl->m2l_mode = o.m2l_mode;
+  pl->root_x0 = o.root_x0;
+  pl->root_side = o.root_side;
   pl->kre = kappa_re;
   pl->kim = kappa_im;
   pl->H = o.levels > 0 ? o.levels : choose_levels(n, leaf_size);
@@ -290,6 +294,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);
   if (f32) ALLOC(pl->t_m2l_pad, sizeof(cf) * 40 * (size_t)P1 * ((P1 + 1) & ~1));
+  if (f32 && pl->m2l_mode == 1)
+    ALLOC(pl->t_m2l_tc, sizeof(float) * 40 * 2 * (size_t)tc_np(P1) * tc_kp(P1));
   ALLOC(pl->t_rlog, tf * 21 * m2);
   ALLOC(pl->t_refl, tf * (size_t)pl->H * 42 * m2);
   ALLOC(pl->t_rlog0, sizeof(cd) * 70);
@@ -397,6 +403,51 @@ extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, do
     HP_CUDA(cudaMemcpyAsync(grad, dgrad, 4 * sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
   if (!pd || !gd) HP_CUDA(cudaStreamSynchronize(st));
   return HPFMM_OK;
+}
+
+// targets must be finite, on y >= 0 and inside the plan's root square
+__global__ void k_check_targets(const double *__restrict__ xt, const double *__restrict__ yt,
+                                int64_t nt, double x0, double side, int *__restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  const double x = xt[i], y = yt[i];
+  const bool ok = isfinite(x) && isfinite(y) && y >= 0.0 && x >= x0 && x <= x0 + side &&
+                  y <= side;
+  if (!ok) atomicOr(flag, 1);
+}
+
+extern "C" hpfmm_status hpfmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
+                                           const double *yt, int64_t nt, double *pot,
+                                           double *grad, void *stream) {
+  if (!pl || !q || nt < 0 || (nt > 0 && (!xt || !yt || !pot))) {
+    set_last_error("hpfmm_eval_targets: need plan, q, nt >= 0 and, for nt > 0, xt, yt, pot");
+    return HPFMM_EINVAL;
+  }
+  if (nt == 0) return HPFMM_OK;
+  const void *ptrs[] = {q, xt, yt, pot, grad};
+  for (const void *p : ptrs)
+    if (p && !is_device_pointer(p)) {
+      set_last_error("hpfmm_eval_targets: arrays must be device memory");
+      return HPFMM_EINVAL;
+    }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!pl->tflag) HP_TRY(plan_dalloc(pl, (void **)&pl->tflag, sizeof(int)));
+  int hflag = 0;
+  if (nt > 0) {
+    HP_CUDA(cudaMemsetAsync(pl->tflag, 0, sizeof(int), st));
+    k_check_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(xt, yt, nt, pl->x0, pl->side,
+                                                                  pl->tflag);
+    HP_LAUNCH_CHECK();
+    HP_CUDA(cudaMemcpyAsync(&hflag, pl->tflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HP_CUDA(cudaStreamSynchronize(st));
+  }
+  if (hflag) {
+    set_last_error("hpfmm_eval_targets: targets must be finite, with y >= 0, inside the root "
+                   "square [%g, %g] x [0, %g]",
+                   pl->x0, pl->x0 + pl->side, pl->side);
+    return HPFMM_EINVAL;
+  }
+  return fmm_eval_targets(pl, q, xt, yt, nt, pot, grad, st);
 }
 
 extern "C" hpfmm_status hpfmm_destroy(hpfmm_plan *pl) {

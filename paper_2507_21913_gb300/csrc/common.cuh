@@ -184,6 +184,7 @@ struct hpfmm_plan {
   double tau_fp64 = 0.05;
   int subtree = 0;   // fused upward/downward subtree depth (0: automatic)
   int m2l_mode = 0;  // multi-RHS free M2L (16+ RHS): 0 FP32 FMA kernel, 1 tensor cores
+  double root_x0 = 0, root_side = 0;  // root square override (root_side > 0)
   double kre = 1, kim = 0;
   double x0 = 0, side = 1;
   int64_t nbox = 0;  // boxes over levels 0..H
@@ -201,6 +202,7 @@ struct hpfmm_plan {
   void *t_l2l = nullptr;   // 4 x (p+1)^2 complex: parent -> child c (analytic part)
   void *t_m2l = nullptr;   // 49 offset classes x (p+1)^2 complex: free-space log M2L
   void *t_m2l_pad = nullptr;  // FP32 path: the 40 far classes, rows padded to even length
+  void *t_m2l_tc = nullptr;   // tensor-core M2L: the 40 far classes as tf32 hi/lo operands
   void *t_refl = nullptr;  // per level: 7 x 3 classes x (2p+1) complex: scaled I_k tables
   void *t_rlog = nullptr;  // per level: 7 x 3 classes x (p+1)^2 complex: image-log M2L
   void *t_rlog0 = nullptr;    // logs of the 49 free and 21 image class displacements
@@ -218,6 +220,7 @@ struct hpfmm_plan {
   // multi-RHS workspace (single precision), for up to mcap charge vectors at once
   void *mq = nullptr, *mqsm = nullptr, *mM = nullptr, *mA = nullptr, *mB = nullptr;
   int mcap = 0;
+  int *tflag = nullptr;  // target validation flag (hpfmm_eval_targets)
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
   void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
@@ -274,6 +277,10 @@ hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad
 // precision); qs: nr n floats, qsm: n fmm_multi_rp(nr) floats, M/A/B: nr nbox
 // (p+1) complex floats each
 bool fmm_multi_supported(const hpfmm_plan *pl);
+// evaluation at nt separate targets (device arrays inside the root square)
+hpfmm_status fmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
+                              const double *yt, int64_t nt, double *pot, double *grad,
+                              cudaStream_t st);
 int fmm_multi_rp(int nr);
 hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot, double *grad,
                             void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st);

@@ -159,28 +159,6 @@ k_p2m(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_
 }
 
 // --------------------------------------------------------------------------
-// M2M (Eq. metome): parent M_n = sum_c sum_{m<=n} T_c[n][m] M^{(c)}_m.
-// One warp per parent box of level l; lanes over n.
-template <typename R>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_m2m(int l, int p, const cpx<R> *__restrict__ T, cpx<R> *__restrict__ M) {
-  int P1 = p + 1;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t box = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (box >= (int64_t(1) << (2 * l))) return;
-  const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * box) * P1;
-  for (int n = lane; n < P1; n += 32) {
-    cpx<R> acc = mk<R>(0, 0);
-    for (int c = 0; c < 4; ++c) {
-      const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)n * P1;
-      const cpx<R> *mc = child + (size_t)c * P1;
-      for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], mc[m]);
-    }
-    M[(size_t)(level_offset(l) + box) * P1 + n] = acc;
-  }
-}
-
-// --------------------------------------------------------------------------
 // S2M with one thread per (leaf, n): M_n = sum_j Q_j w_j^n, w_j = (z_j - z_c)/d,
 // w^n by repeated squaring.  No cross-thread reduction, so the short leaves
 // of a deep tree keep every lane busy.
@@ -754,16 +732,17 @@ bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, co
 // every thread waits (bounded) before the buffers are reused.
 template <int P1>
 __global__ void __launch_bounds__(128)
-k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
+k_m2l_free_tc(int l, int rct, int nr, float logd, const float *__restrict__ Btab,
               const cd *__restrict__ logt, const cf *__restrict__ M, cf *__restrict__ A,
               cf *__restrict__ B, RhsStride rs, int *__restrict__ status) {
-  constexpr int PP = (P1 + 1) & ~1;
-  constexpr int KP = (2 * P1 + 7) / 8 * 8;
-  constexpr int NP = (2 * P1 + 15) / 16 * 16;
+  constexpr int KP = tc_kp(P1), NP = tc_np(P1);
   constexpr unsigned NCOL = NP <= 32 ? 32u : (NP <= 64 ? 64u : 128u);
+  constexpr int ASZ = 128 * KP, BSZ = NP * KP;  // floats per operand half
+  constexpr unsigned BBYTES = 2u * BSZ * sizeof(float);
   extern __shared__ __align__(1024) float tsm[];
-  float *ahi = tsm, *alo = ahi + 128 * KP, *bhi = alo + 128 * KP, *blo = bhi + NP * KP;
-  __shared__ __align__(8) uint64_t bar;
+  // [2 buffers] x (A hi, A lo), then [2 buffers] x (B hi, B lo)
+  float *abuf = tsm, *bbuf = tsm + 4 * ASZ;
+  __shared__ __align__(8) uint64_t mbar[2], tbar[2];
   __shared__ unsigned tslot;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -778,9 +757,17 @@ k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
   const bool rvalid = pm < npar && r0 + rr < nr;
   const int tx = pm < npar ? 2 * box_ix(pm) + a : 0, ty = pm < npar ? 2 * box_iy(pm) + bb : 0;
   const cf *Mr = M + (size_t)(r0 + rr) * rs.m;
+  __shared__ int cls[27];  // the 27 classes of this child type, in a fixed order
   if (warp == 0) tc_alloc(&tslot, NCOL);
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    int ncls = 0;
+    for (int dy = -2 - bb; dy <= 3 - bb; ++dy)
+      for (int dx = -2 - a; dx <= 3 - a; ++dx)
+        if (!(dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1)) cls[ncls++] = (dy + 3) * 7 + (dx + 3);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    mbar_init(&tbar[0], 1);
+    mbar_init(&tbar[1], 1);
     failed = 0;
   }
   tc_fence_before();
@@ -788,85 +775,90 @@ k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
   tc_fence_after();
   const unsigned tbase = tslot;
   const uint32_t idesc = tc_idesc_tf32(128, NP);
-  const unsigned sbo_a = (unsigned)(KP / 4) * 128u;
-  int it = 0;
-  for (int dy = -2 - bb; dy <= 3 - bb; ++dy) {
-    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
-      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-      const int c = (dy + 3) * 7 + (dx + 3);
-      const int slot = c_slot[c];
-      // A: this thread's row -- the source moments of (target, RHS) in real form
-      {
-        const int sx = tx + dx, sy = ty + dy;
-        const bool ok = rvalid && sx >= 0 && sy >= 0 && sx < nside && sy < nside;
-        const cf *src = Mr + (size_t)(off + (ok ? box_morton(sx, sy) : 0)) * P1;
-        float re[P1], im[P1];
+  const unsigned sbo = (unsigned)(KP / 4) * 128u;
+  float lgacc = 0.f;  // sum over classes of Re M_0 ln|t d| (added to Re L_0)
+  // operand staging of class index it into buffer it & 1: B by one bulk copy,
+  // A by every thread (its row: the source moments in real form, split)
+  auto stage = [&](int it) {
+    const int buf = it & 1, c = cls[it];
+    if (tid == 0) {
+      mbar_expect_tx(&tbar[buf], BBYTES);
+      bulk_g2s(bbuf + buf * 2 * BSZ, Btab + (size_t)c_slot[c] * 2 * BSZ, BBYTES, &tbar[buf]);
+    }
+    const int dx = c % 7 - 3, dy = c / 7 - 3;
+    const int sx = tx + dx, sy = ty + dy;
+    const bool ok = rvalid && sx >= 0 && sy >= 0 && sx < nside && sy < nside;
+    float v[KP];
 #pragma unroll
-        for (int m = 0; m < P1; ++m) {
-          const cf v = ok ? src[m] : mk(0.f, 0.f);
-          re[m] = v.x;
-          im[m] = v.y;
-        }
+    for (int k = 0; k < KP; ++k) v[k] = 0.f;
+    if (ok) {
+      const cf *src = Mr + (size_t)(off + box_morton(sx, sy)) * P1;
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
-          const float v = k < P1 ? re[k] : (k < 2 * P1 ? im[k - P1] : 0.f);
-          float h, lo;
-          tc_split(v, h, lo);
-          ahi[tc_off(tid, k, KP)] = h;
-          alo[tc_off(tid, k, KP)] = lo;
-        }
+      for (int m = 0; m < P1; ++m) {
+        const cf z = src[m];
+        v[m] = z.x;
+        v[P1 + m] = z.y;
       }
-      // B: the real form of T_delta, K-major (row = output, column = input)
-      const cf *T = Tpad + (size_t)slot * P1 * PP;
-      const float lgc = (float)logt[c].x + logd;
-      for (int e = tid; e < NP * KP; e += 128) {
-        const int no = e / KP, k = e % KP;
-        float v = 0.f;
-        if (no < 2 * P1 && k < 2 * P1) {
-          const int n = no < P1 ? no : no - P1, m = k < P1 ? k : k - P1;
-          const cf t = T[n * PP + m];
-          const bool imo = no >= P1, imi = k >= P1;
-          v = imo == imi ? t.x : (imo ? t.y : -t.y);
-          if (no == 0 && k == 0) v += lgc;  // M_0 ln|t d| on Re L_0
-        }
-        float h, lo;
-        tc_split(v, h, lo);
-        bhi[tc_off(no, k, KP)] = h;
-        blo[tc_off(no, k, KP)] = lo;
-      }
-      tc_fence_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (tid == 0) {
+      lgacc = fmaf(v[0], (float)logt[c].x + logd, lgacc);
+    }
+    float *ah = abuf + buf * 2 * ASZ, *al = ah + ASZ;
+#pragma unroll
+    for (int kg = 0; kg < KP / 4; ++kg) {
+      float4 h, lo;
+      tc_split(v[4 * kg], h.x, lo.x);
+      tc_split(v[4 * kg + 1], h.y, lo.y);
+      tc_split(v[4 * kg + 2], h.z, lo.z);
+      tc_split(v[4 * kg + 3], h.w, lo.w);
+      const int o = tc_off(tid, 4 * kg, KP);
+      *reinterpret_cast<float4 *>(ah + o) = h;
+      *reinterpret_cast<float4 *>(al + o) = lo;
+    }
+  };
+  stage(0);
+  for (int it = 0; it < 27; ++it) {
+    const int buf = it & 1;
+    tc_fence_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      if (!mbar_wait_bounded(&tbar[buf], (unsigned)((it >> 1) & 1))) {
+        failed = 1;
+      } else {
+        const float *ah = abuf + buf * 2 * ASZ, *al = ah + ASZ;
+        const float *bh = bbuf + buf * 2 * BSZ, *bl = bh + BSZ;
 #pragma unroll 1
         for (int s = 0; s < KP / 8; ++s) {
           const unsigned o = (unsigned)s * 256u;
-          const uint64_t dah = tc_sdesc(smem_u32(ahi) + o, 128u, sbo_a);
-          const uint64_t dal = tc_sdesc(smem_u32(alo) + o, 128u, sbo_a);
-          const uint64_t dbh = tc_sdesc(smem_u32(bhi) + o, 128u, sbo_a);
-          const uint64_t dbl = tc_sdesc(smem_u32(blo) + o, 128u, sbo_a);
+          const uint64_t dah = tc_sdesc(smem_u32(ah) + o, 128u, sbo);
+          const uint64_t dal = tc_sdesc(smem_u32(al) + o, 128u, sbo);
+          const uint64_t dbh = tc_sdesc(smem_u32(bh) + o, 128u, sbo);
+          const uint64_t dbl = tc_sdesc(smem_u32(bl) + o, 128u, sbo);
           tc_mma_tf32(tbase, dah, dbh, idesc, it > 0 || s > 0);
           tc_mma_tf32(tbase, dah, dbl, idesc, true);
           tc_mma_tf32(tbase, dal, dbh, idesc, true);
         }
-        tc_commit(&bar);
+        tc_commit(&mbar[buf]);
       }
-      __syncwarp();
-      if (!mbar_wait_bounded(&bar, (unsigned)(it & 1))) {
-        if (!mbar_wait_bounded(&bar, (unsigned)(it & 1))) failed = 1;
-      }
-      tc_fence_after();
-      __syncthreads();
-      ++it;
-      if (failed) break;
     }
+    __syncthreads();
     if (failed) break;
+    if (it + 1 < 27) {
+      // the other buffer was read by the MMAs of class it - 1: wait for them
+      if (it >= 1 && !mbar_wait_bounded(&mbar[buf ^ 1], (unsigned)(((it - 1) >> 1) & 1)))
+        failed = 1;
+      __syncthreads();
+      if (failed) break;
+      stage(it + 1);
+    }
   }
-  if (failed) {
-    if (tid == 0) atomicOr(status, HPFMM_DEV_TIMEOUT);
-  } else {
-    // epilogue: row tid of D -> L_n = D[n] + i D[P1 + n]; A = s L, B = conj(s L)
+  // completion of the last class's MMAs (class 26 used buffer 0)
+  bool done = !failed && mbar_wait_bounded(&mbar[0], (unsigned)((26 >> 1) & 1));
+  if (!done && tid == 0) atomicOr(status, HPFMM_DEV_TIMEOUT);
+  tc_fence_after();
+  if (done) {
+    // epilogue: row tid of D -> L_n = D[n] + i D[P1 + n] (+ the log term on
+    // Re L_0); A = s L, B = conj(s L)
     float d[NP];
 #pragma unroll
     for (int cc = 0; cc < NP; cc += 8)
@@ -874,6 +866,7 @@ k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
     if (rvalid) {
       const float sc = (float)(-0.5 / HP_TWO_PI);
       const size_t e0 = (size_t)(r0 + rr) * rs.m + (size_t)(off + box_morton(tx, ty)) * P1;
+      d[0] += lgacc;
 #pragma unroll
       for (int n = 0; n < P1; ++n) {
         const cf v = mk(sc * d[n], sc * d[P1 + n]);
@@ -881,6 +874,10 @@ k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
         B[e0 + n] = conj(v);
       }
     }
+  } else {
+    // make sure nothing is still writing TMEM or reading the buffers
+    mbar_wait_bounded(&mbar[0], (unsigned)((26 >> 1) & 1));
+    mbar_wait_bounded(&mbar[1], (unsigned)((25 >> 1) & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -889,19 +886,17 @@ k_m2l_free_tc(int l, int rct, int nr, float logd, const cf *__restrict__ Tpad,
 
 template <int P1>
 size_t m2l_tc_smem() {
-  constexpr int KP = (2 * P1 + 7) / 8 * 8;
-  constexpr int NP = (2 * P1 + 15) / 16 * 16;
-  return sizeof(float) * 2 * (size_t)(128 + NP) * KP;
+  return sizeof(float) * 4 * (size_t)(128 + tc_np(P1)) * tc_kp(P1);
 }
 
 // RHS per tile row group: 16, 32 or 64
 int m2l_tc_rct(int nr) { return nr > 32 ? 64 : (nr > 16 ? 32 : 16); }
 
 // launches the tensor-core M2L for levels 2..H; false if p has no instance
-bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const cf *Tpad, const cd *logt,
+bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const float *Btab, const cd *logt,
                    const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
                    RhsStride rs) {
-  if (!Tpad) return false;
+  if (!Btab) return false;
   static std::mutex mu;
   static signed char attr[64][41];
   int dev = 0;
@@ -927,7 +922,7 @@ bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const cf *Tpad, const cd 
       const int npar = 1 << (2 * (l - 1));                                                  \
       const unsigned nx = (unsigned)(4 * ((npar + G - 1) / G));                             \
       k_m2l_free_tc<PP + 1><<<dim3(nx, ny), 128, sm, st>>>(l, rct, nr, (float)lgm.logd[l],  \
-                                                           Tpad, logt, M, A, B, rs, status); \
+                                                           Btab, logt, M, A, B, rs, status); \
     }                                                                                       \
     return true;                                                                            \
   }
@@ -937,77 +932,6 @@ bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const cf *Tpad, const cd 
     default: return false;
   }
 #undef HP_TC_CASE
-}
-
-// --------------------------------------------------------------------------
-// mirror M2L (image log + reaction Phi_2^+ and Phi_2^-) for the boxes of rows
-// 0 and 1 of level l.  One warp per target; lanes over the output index.
-template <typename R>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_m2l_mirror(int l, int p, double logd, const cpx<R> *__restrict__ Timg,
-             const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
-             const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B,
-             int accumulate) {
-  extern __shared__ unsigned char smem_raw[];
-  int P1 = p + 1;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cpx<R> *ms = reinterpret_cast<cpx<R> *>(smem_raw) + (size_t)warp * P1;
-  int nx = 1 << l;
-  int t = blockIdx.x * kWarpsPerBlock + warp;
-  if (t >= 2 * nx) return;
-  int ixt = t % nx, iyt = t / nx;  // rows 0 and 1
-  int px = ixt >> 1;
-  const int64_t off = level_offset(l);
-  cpx<R> aL0 = mk<R>(0, 0), aL1 = mk<R>(0, 0), aC0 = mk<R>(0, 0), aC1 = mk<R>(0, 0);
-  cpx<R> aD0 = mk<R>(0, 0), aD1 = mk<R>(0, 0);
-  for (int iys = 0; iys <= 1; ++iys) {
-    for (int ixs = 2 * (px - 1); ixs <= 2 * (px + 1) + 1; ++ixs) {
-      if (ixs < 0 || ixs >= nx) continue;
-      if (iyt == 0 && iys == 0 && abs(ixs - ixt) <= 1) continue;  // mirror-neighbours
-      int dx = ixs - ixt, ysum = iyt + iys + 1;
-      int cls = (ysum - 1) * 7 + (dx + 3);
-      const cpx<R> *src = M + (size_t)(off + box_morton(ixs, iys)) * P1;
-      __syncwarp();
-      for (int k = lane; k < P1; k += 32) ms[k] = src[k];
-      __syncwarp();
-      const cpx<R> *Ti = Timg + (size_t)cls * P1 * P1;
-      const cpx<R> *Tp = Treact + ((size_t)((l - 1) * 21 + cls) * 2 + 0) * P1 * P1;
-      const cpx<R> *Tm = Treact + ((size_t)((l - 1) * 21 + cls) * 2 + 1) * P1 * P1;
-      for (int n = lane; n < P1; n += 32) {
-        cpx<R> sL = mk<R>(0, 0), sC = mk<R>(0, 0), sD = mk<R>(0, 0);
-        for (int k = 0; k < P1; ++k) {
-          cpx<R> mk_ = ms[k], mc = conj(mk_);
-          cfma(sL, Ti[n * P1 + k], mc);
-          cfma(sC, Tp[n * P1 + k], mc);
-          cfma(sD, Tm[n * P1 + k], mk_);
-        }
-        if (n == 0) {  // log|t d| M_0 term of the image log expansion (Re only)
-          cd lt = logimg[cls];
-          R m0 = ms[0].x;
-          sL.x += m0 * (R)(lt.x + logd);
-        }
-        if (n == lane) { aL0 = aL0 + sL; aC0 = aC0 + sC; aD0 = aD0 + sD; }
-        else { aL1 = aL1 + sL; aC1 = aC1 + sC; aD1 = aD1 + sD; }
-      }
-    }
-  }
-  // image log: L = +(1/2pi) sum ...; A += L/2 + C, B += conj(L)/2 + D
-  const R s = (R)(0.5 / HP_TWO_PI);
-  int64_t m = off + box_morton(ixt, iyt);
-  for (int n = lane; n < P1; n += 32) {
-    cpx<R> L = s * (n == lane ? aL0 : aL1);
-    cpx<R> C = n == lane ? aC0 : aC1;
-    cpx<R> D = n == lane ? aD0 : aD1;
-    cpx<R> va = L + C, vb = conj(L) + D;
-    size_t e = (size_t)m * P1 + n;
-    if (accumulate) {
-      A[e] = A[e] + va;
-      B[e] = B[e] + vb;
-    } else {
-      A[e] = va;
-      B[e] = vb;
-    }
-  }
 }
 
 // All-levels form of the mirror M2L: one block of 4 warps per target box of
@@ -1099,40 +1023,6 @@ k_m2l_mirror_all(int H, int p, LevelGeom lgm, const cpx<R> *__restrict__ Timg,
       A[e] = va;
       B[e] = vb;
     }
-  }
-}
-
-// --------------------------------------------------------------------------
-// L2L (Eq. letole1, truncated at p): child A_m += sum_{n>=m} T_c[m][n] A^P_n and
-// B_m += sum conj(T_c[m][n]) B^P_n.  One warp per child box of level l.
-template <typename R>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_l2l(int l, int p, const cpx<R> *__restrict__ T, cpx<R> *__restrict__ A,
-      cpx<R> *__restrict__ B) {
-  int P1 = p + 1;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t box = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (box >= (int64_t(1) << (2 * l))) return;
-  int c = (int)(box & 3);
-  const size_t pe = (size_t)(level_offset(l - 1) + (box >> 2)) * P1;
-  const size_t ce = (size_t)(level_offset(l) + box) * P1;
-  const cpx<R> *Tc = T + (size_t)c * P1 * P1;
-  cpx<R> ra[2], rb[2];
-  int cnt = 0;
-  for (int mm = lane; mm < P1; mm += 32, ++cnt) {
-    cpx<R> sa = A[ce + mm], sb = B[ce + mm];
-    for (int n = mm; n < P1; ++n) {
-      cpx<R> t = Tc[mm * P1 + n];
-      cfma(sa, t, A[pe + n]);
-      cfma(sb, conj(t), B[pe + n]);
-    }
-    ra[cnt] = sa;
-    rb[cnt] = sb;
-  }
-  cnt = 0;
-  for (int mm = lane; mm < P1; mm += 32, ++cnt) {
-    A[ce + mm] = ra[cnt];
-    B[ce + mm] = rb[cnt];
   }
 }
 
@@ -1253,125 +1143,6 @@ __device__ __forceinline__ double f2d(float v) {
   return __longlong_as_double((long long)r);
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_eval32(const float2 *__restrict__ loc, const float *__restrict__ qs,
-         const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-         double side, int p, cd kappa, float tau, const cf *__restrict__ A,
-         const cf *__restrict__ B, double *__restrict__ pot, double *__restrict__ grad) {
-  __shared__ SrcPt32 sp[kWarpsPerBlock][32];
-  int P1 = p + 1;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int leaf = blockIdx.x * kWarpsPerBlock + warp;
-  int nx = 1 << H;
-  if (leaf >= nx * nx) return;
-  int ix = box_ix(leaf), iy = box_iy(leaf);
-  float d = (float)(side / (double)nx);
-  float invd = (float)((double)nx / side);
-  cf kap = mk((float)kappa.x, (float)kappa.y);
-  const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
-  const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
-  int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-  for (int tb = b0; tb < b1; tb += 32) {
-    int i = tb + lane;
-    bool act = i < b1;
-    float2 me = act ? loc[i] : make_float2(0.f, 0.f);
-    cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
-    cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
-    for (int n = p - 1; n >= 0; --n) {
-      da = da * w + va;
-      va = va * w + Al[n];
-      db = db * wb + vb;
-      vb = vb * wb + Bl[n];
-    }
-    float lf = 0.f, gfx = 0.f, gfy = 0.f;      // free: sum q log2 r^2, q (dx, dy)/r^2
-    float li = 0.f, gix = 0.f, giy = 0.f;      // image
-    cf ur = mk(0.f, 0.f), grx = mk(0.f, 0.f), gry = mk(0.f, 0.f);
-    cd ur64 = mk(0.0, 0.0), grx64 = mk(0.0, 0.0), gry64 = mk(0.0, 0.0);
-    for (int ny = iy - 1; ny <= iy + 1; ++ny) {
-      if (ny < 0 || ny >= nx) continue;
-      for (int mxx = ix - 1; mxx <= ix + 1; ++mxx) {
-        if (mxx < 0 || mxx >= nx) continue;
-        uint64_t sl = box_morton(mxx, ny);
-        int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-        float ox = (float)(mxx - ix) * d, oy = (float)(ny - iy) * d;
-        bool mirror = (iy == 0 && ny == 0);
-        for (int sb = s0; sb < s1; sb += 32) {
-          __syncwarp();
-          int js = sb + lane;
-          if (js < s1) {
-            float2 v = loc[js];
-            sp[warp][lane] = SrcPt32{v.x + ox, v.y + oy, qs[js], 0.f};
-          }
-          __syncwarp();
-          int cnt = min(32, s1 - sb);
-          if (!act) continue;
-          for (int k = 0; k < cnt; ++k) {
-            SrcPt32 s = sp[warp][k];
-            float dx = me.x - s.x, dy = me.y - s.y;
-            if (sb + k != i) {
-              float r2 = fmaf(dx, dx, dy * dy);
-              float qi = s.q * fast_rcp(r2);
-              lf = fmaf(s.q, __log2f(r2), lf);
-              gfx = fmaf(qi, dx, gfx);
-              gfy = fmaf(qi, dy, gfy);
-            }
-            if (mirror) {
-              // bottom row: leaf centres at y = d/2, so Y = y_i + y_j = ly + sy + d
-              float Y = me.y + s.y + d;
-              float R2 = fmaf(dx, dx, Y * Y);
-              float qi = s.q * fast_rcp(R2);
-              li = fmaf(s.q, __log2f(R2), li);
-              gix = fmaf(qi, dx, gix);
-              giy = fmaf(qi, Y, giy);
-              cf sp_ = mk(Y, -dx), sm_ = mk(Y, dx);
-              cf Pp = kap * sp_, Pm = kap * sm_;
-              bool small = abs2(Pp) <= 1.f && Y >= tau;
-              if (small) {
-                cf J0p, J1p, J0m, J1m;
-                j01_f(Pp, J0p, J1p);
-                j01_f(Pm, J0m, J1m);
-                ur = ur + s.q * (J0p + J0m);
-                cf tp = cdiv(J1p, sp_), tm = cdiv(J1m, sm_);
-                grx = grx + s.q * mul_i(tp - tm);
-                gry = gry - s.q * (tp + tm);
-              } else {
-                cd spd = mk((double)Y, -(double)dx), smd = mk((double)Y, (double)dx);
-                cd J0p, J1p, J0m, J1m;
-                j01(kappa * spd, J0p, J1p);
-                j01(kappa * smd, J0m, J1m);
-                double q = s.q;
-                ur64 = ur64 + q * (J0p + J0m);
-                cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
-                grx64 = grx64 + q * mul_i(tp - tm);
-                gry64 = gry64 - q * (tp + tm);
-              }
-            }
-          }
-        }
-      }
-    }
-    if (!act) continue;
-    // ln r^2 = log2(r^2) ln 2
-    const double c4 = 0.69314718055994530942 / (4.0 * HP_PI), i2pi = 1.0 / HP_TWO_PI;
-    cd u = mk((double)va.x + vb.x + ((double)li - lf) * c4 + ((double)ur.x + ur64.x) * i2pi,
-              (double)va.y + vb.y + ((double)ur.y + ur64.y) * i2pi);
-    cd ga = mk((double)da.x, (double)da.y), gb = mk((double)db.x, (double)db.y);
-    double id = 1.0 / (double)d;
-    cd gx = id * (ga + gb), gy = id * (mul_i(ga) - mul_i(gb));
-    gx = gx + mk(((double)gix - gfx + grx.x + grx64.x) * i2pi, ((double)grx.y + grx64.y) * i2pi);
-    gy = gy + mk(((double)giy - gfy + gry.x + gry64.x) * i2pi, ((double)gry.y + gry64.y) * i2pi);
-    int64_t o = perm[i];
-    pot[2 * o] = u.x;
-    pot[2 * o + 1] = u.y;
-    if (grad) {
-      grad[4 * o + 0] = gx.x;
-      grad[4 * o + 1] = gx.y;
-      grad[4 * o + 2] = gy.x;
-      grad[4 * o + 3] = gy.y;
-    }
-  }
-}
-
 // Single-precision leaf evaluation, lane-grouped.  A warp owns one target
 // leaf.  Its targets are spread over groups of gs = 32, 16, 8 or 4 lanes
 // (the smallest power of two >= the leaf size, at least 4): each group holds
@@ -1381,61 +1152,12 @@ k_eval32(const float2 *__restrict__ loc, const float *__restrict__ qs,
 // with coordinates already shifted to the target leaf's frame.  The free part
 // skips coincident positions (r^2 = 0), i.e. the j = i pair.
 constexpr int kEvWarps = 8;
-constexpr int kEvBuf = 256;
 
 struct NearAcc {
   float lf, gx, gy;                 // free: sum q log2 r^2, sum q (dx, dy) / r^2
   float li, gix, giy;               // image
   cf ur, grx, gry;                  // reaction (pairs evaluated in single or double)
 };
-
-// sum over the staged sources [lo, hi) taken by group g of NG; CHECK: the
-// range may contain the target itself (r^2 = 0 is then skipped)
-template <int NG, bool CHECK>
-__device__ __forceinline__ void free_range(const float4 *buf, int lo, int hi, int g, float mx,
-                                           float my, float &lf, float &gx, float &gy) {
-#pragma unroll 4
-  for (int k = lo + g; k < hi; k += NG) {
-    const float4 s = buf[k];
-    const float dx = mx - s.x, dy = my - s.y;
-    float r2 = fmaf(dx, dx, dy * dy);
-    float q = s.z;
-    if (CHECK) {
-      const bool ok = r2 > 0.f;
-      q = ok ? q : 0.f;
-      r2 = ok ? r2 : 1.f;
-    }
-    const float qi = q * fast_rcp(r2);
-    lf = fmaf(q, fast_lg2(r2), lf);
-    gx = fmaf(qi, dx, gx);
-    gy = fmaf(qi, dy, gy);
-  }
-}
-
-template <int NG>
-__device__ __forceinline__ void free_batch_t(const float4 *buf, int cnt, int g, int slo, int shi,
-                                             float mx, float my, NearAcc &a) {
-  float lf = 0.f, gx = 0.f, gy = 0.f;
-  slo = max(0, min(slo, cnt));
-  shi = max(slo, min(shi, cnt));
-  // each of the three ranges is split over the NG groups on its own
-  free_range<NG, false>(buf, 0, slo, g, mx, my, lf, gx, gy);
-  free_range<NG, true>(buf, slo, shi, g, mx, my, lf, gx, gy);
-  free_range<NG, false>(buf, shi, cnt, g, mx, my, lf, gx, gy);
-  a.lf += lf;
-  a.gx += gx;
-  a.gy += gy;
-}
-
-__device__ __forceinline__ void free_batch(const float4 *buf, int cnt, int g, int ng, int slo,
-                                           int shi, float mx, float my, NearAcc &a) {
-  switch (ng) {
-    case 1: free_batch_t<1>(buf, cnt, g, slo, shi, mx, my, a); break;
-    case 2: free_batch_t<2>(buf, cnt, g, slo, shi, mx, my, a); break;
-    case 4: free_batch_t<4>(buf, cnt, g, slo, shi, mx, my, a); break;
-    default: free_batch_t<8>(buf, cnt, g, slo, shi, mx, my, a); break;
-  }
-}
 
 __device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, int ng, float mx,
                                              float my, float d, cf kap, cd kappa, float tau,
@@ -1480,307 +1202,10 @@ __device__ __forceinline__ float xsum(float v, int from) {
   return v;
 }
 
-__global__ void __launch_bounds__(kEvWarps * 32, 3)
-k_eval32g(const float2 *__restrict__ loc, const float *__restrict__ qs,
-          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-          double side, int p, cd kappa, float tau, const cf *__restrict__ A,
-          const cf *__restrict__ B, double *__restrict__ pot, double *__restrict__ grad) {
-  __shared__ float4 sbuf[kEvWarps][kEvBuf];
-  __shared__ int nb_s0[kEvWarps][9], nb_ex[kEvWarps][10];
-  __shared__ float nb_ox[kEvWarps][9], nb_oy[kEvWarps][9];
-  const int P1 = p + 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int leaf = blockIdx.x * kEvWarps + warp;
-  const int nx = 1 << H;
-  if (leaf >= nx * nx) return;
-  float4 *buf = sbuf[warp];
-  const int ix = box_ix(leaf), iy = box_iy(leaf);
-  const float d = (float)(side / (double)nx);
-  const float invd = (float)((double)nx / side);
-  const cf kap = mk((float)kappa.x, (float)kappa.y);
-  const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
-  const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
-  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-  const int T = b1 - b0;
-  const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
-  const int ng = 32 / gs, g = lane / gs, tl = lane % gs;
-  // neighbour table: lane k < 9 looks up neighbour k = (ix-1 + k%3, iy-1 + k/3)
-  int cnt_k = 0;
-  if (lane < 9) {
-    const int mxx = ix - 1 + lane % 3, ny = iy - 1 + lane / 3;
-    int s0 = 0;
-    if (mxx >= 0 && mxx < nx && ny >= 0 && ny < nx) {
-      const uint64_t sl = box_morton(mxx, ny);
-      s0 = leaf_start[sl];
-      cnt_k = leaf_start[sl + 1] - s0;
-    }
-    nb_s0[warp][lane] = s0;
-    nb_ox[warp][lane] = (float)(mxx - ix) * d;
-    nb_oy[warp][lane] = (float)(ny - iy) * d;
-  }
-  int pre = cnt_k;
-  for (int o = 1; o < 16; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, pre, o);
-    if (lane >= o) pre += v;
-  }
-  if (lane < 9) nb_ex[warp][lane] = pre - cnt_k;
-  const int nsrc = __shfl_sync(0xffffffffu, pre, 8);
-  if (lane == 9) nb_ex[warp][9] = nsrc;
-  __syncwarp();
-  for (int tb = b0; tb < b1; tb += gs) {
-    const int i = tb + tl;
-    const bool act = i < b1;
-    const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
-    NearAcc acc;
-    acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
-    acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
-    // free part over the 3x3 neighbourhood: the sources of the (up to 9)
-    // neighbour leaves are staged batch by batch, every lane loading its own
-    // entries of the concatenated list
-    for (int base = 0; base < nsrc; base += kEvBuf) {
-      const int cnt = min(kEvBuf, nsrc - base);
-      __syncwarp();
-      for (int e = lane; e < cnt; e += 32) {
-        const int f = base + e;
-        int k = 0;
-        while (k < 8 && f >= nb_ex[warp][k + 1]) ++k;
-        const int js = nb_s0[warp][k] + (f - nb_ex[warp][k]);
-        const float2 v = loc[js];
-        buf[e] = make_float4(v.x + nb_ox[warp][k], v.y + nb_oy[warp][k], qs[js], 0.f);
-      }
-      __syncwarp();
-      // the target's own leaf is neighbour 4: only its range needs the j != i test
-      free_batch(buf, cnt, g, ng, nb_ex[warp][4] - base, nb_ex[warp][5] - base, me.x, me.y, acc);
-    }
-    __syncwarp();
-    // combine the groups
-    acc.lf = xsum(acc.lf, gs);
-    acc.gx = xsum(acc.gx, gs);
-    acc.gy = xsum(acc.gy, gs);
-    if (!act || g != 0) continue;
-    // L2P (Eq. truncatedLE for the reaction parts, the log expansions for the
-    // free and image parts): Horner for value and derivative in w, conj(w)
-    cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
-    cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
-    for (int n = p - 1; n >= 0; --n) {
-      da = da * w + va;
-      va = va * w + Al[n];
-      db = db * wb + vb;
-      vb = vb * wb + Bl[n];
-    }
-    // combine in single precision (the outputs are single-precision results)
-    const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
-    const float i2pi = (float)(1.0 / HP_TWO_PI);
-    const float ur_ = va.x + vb.x - acc.lf * c4;
-    const float ui_ = va.y + vb.y;
-    const cf gx = invd * (da + db) + mk(-acc.gx * i2pi, 0.f);
-    const cf gy = invd * (mul_i(da) - mul_i(db)) + mk(-acc.gy * i2pi, 0.f);
-    const int64_t o = perm[i];
-    reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
-    if (grad) {
-      double4 gv;
-      gv.x = f2d(gx.x); gv.y = f2d(gx.y); gv.z = f2d(gy.x); gv.w = f2d(gy.y);
-      reinterpret_cast<double4 *>(grad)[o] = gv;
-    }
-  }
-}
-
-// Tiled form of the single-precision leaf evaluation.  A block owns a 4 x 4
-// tile of target leaves and stages the points of the surrounding 6 x 6 leaves
-// once in shared memory, in their own leaf-centred coordinates; the target
-// leaf of a warp then sums over its 9 neighbours as 9 contiguous ranges of
-// the staged array, shifting the target position by the exact leaf offset
-// once per range.  Blocks whose patch exceeds the staging buffer use the
-// per-warp path of k_eval32g.
+// tile geometry of the single-precision leaf kernel
 constexpr int kTl = 4;             // target leaves per tile side
 constexpr int kTlP = kTl + 2;      // patch leaves per side
 constexpr int kTlCap = 3072;       // staged points per block
-constexpr int kTlWB = 192;         // per-warp neighbourhood buffer
-constexpr size_t kTlSmem = sizeof(float4) * (kTlCap + 8 * kTlWB) + sizeof(int) * (2 * 36 + 1);
-
-template <int NG>
-__device__ __forceinline__ void tile_ranges(const float4 *src, const int *pst, int pi0, int g,
-                                            float mx, float my, float d, float &lf, float &gx,
-                                            float &gy) {
-#pragma unroll 1
-  for (int r = 0; r < 3; ++r) {
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      const int pi = pi0 + r * kTlP + c;
-      const float ox = (float)(c - 1) * d, oy = (float)(r - 1) * d;
-      // sources are in their own leaf frame: shift the target instead
-      const float sx = mx - ox, sy = my - oy;
-      if (r == 1 && c == 1)
-        free_range<NG, true>(src, pst[pi], pst[pi + 1], g, sx, sy, lf, gx, gy);
-      else
-        free_range<NG, false>(src, pst[pi], pst[pi + 1], g, sx, sy, lf, gx, gy);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kEvWarps * 32, 3)
-k_eval32t(const float2 *__restrict__ loc, const float *__restrict__ qs,
-          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
-          float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B,
-          double *__restrict__ pot, double *__restrict__ grad) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *src = reinterpret_cast<float4 *>(smem_raw);         // [kTlCap]
-  float4 *wbuf = src + kTlCap;                                  // [kEvWarps][kTlWB]
-  int *pst = reinterpret_cast<int *>(wbuf + kEvWarps * kTlWB);  // [kTlP^2 + 1]
-  int *pbeg = pst + kTlP * kTlP + 1;                            // [kTlP^2]
-  const int P1 = p + 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4 *wb = wbuf + warp * kTlWB;
-  const int nx = 1 << H;
-  const int tps = nx >= kTl ? nx / kTl : 1;
-  const int tx0 = (blockIdx.x % tps) * kTl, ty0 = (blockIdx.x / tps) * kTl;
-  // patch leaf counts and prefix (warp 0)
-  if (warp == 0) {
-    int c0 = 0, c1 = 0;
-    for (int h = 0; h < 2; ++h) {
-      const int pi = lane + 32 * h;
-      if (pi < kTlP * kTlP) {
-        const int lx = tx0 - 1 + pi % kTlP, ly = ty0 - 1 + pi / kTlP;
-        int b0 = 0, cnt = 0;
-        if (lx >= 0 && ly >= 0 && lx < nx && ly < nx) {
-          const uint64_t lf = box_morton(lx, ly);
-          b0 = leaf_start[lf];
-          cnt = leaf_start[lf + 1] - b0;
-        }
-        pbeg[pi] = b0;
-        if (h == 0) c0 = cnt; else c1 = cnt;
-      }
-    }
-    int i0 = c0, i1 = c1;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
-      if (lane >= o) { i0 += a0; i1 += a1; }
-    }
-    const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
-    pst[lane] = i0 - c0;
-    if (lane + 32 < kTlP * kTlP) pst[lane + 32] = tot0 + i1 - c1;
-    if (lane == kTlP * kTlP - 32 - 1) pst[kTlP * kTlP] = tot0 + i1;
-  }
-  __syncthreads();
-  const int total = pst[kTlP * kTlP];
-  const bool staged = total <= kTlCap;
-  if (staged) {
-    for (int pi = warp; pi < kTlP * kTlP; pi += kEvWarps) {
-      const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
-      for (int j = lane; j < cnt; j += 32) {
-        const float2 v = loc[b0 + j];
-        src[o + j] = make_float4(v.x, v.y, qs[b0 + j], 0.f);
-      }
-    }
-  }
-  __syncthreads();
-  for (int tl = warp; tl < kTl * kTl; tl += kEvWarps) {
-    const int ix = tx0 + tl % kTl, iy = ty0 + tl / kTl;
-    if (ix >= nx || iy >= nx) continue;
-    const uint64_t leaf = box_morton(ix, iy);
-    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-    const int T = b1 - b0;
-    const int gs = T > 16 ? 32 : (T > 8 ? 16 : (T > 4 ? 8 : 4));
-    const int ng = 32 / gs, g = lane / gs, tli = lane % gs;
-    const int pi0 = (iy - ty0) * kTlP + (ix - tx0);  // patch index of the (-1, -1) neighbour
-    const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
-    const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
-    for (int tb = b0; tb < b1; tb += gs) {
-      const int i = tb + tli;
-      const bool act = i < b1;
-      const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
-      NearAcc acc;
-      acc.lf = acc.gx = acc.gy = 0.f;
-      float lf = 0.f, gx = 0.f, gy = 0.f;
-      if (staged) {
-        // the 9 neighbour ranges of the patch, copied into this warp's buffer
-        // in the target leaf's frame, batch by batch; the target's own leaf
-        // is range 4 and its position in the batch is tracked for the j != i test
-        int fill = 0, slo = 0, shi = 0;
-        for (int r9 = 0; r9 < 9; ++r9) {
-          const int pi = pi0 + (r9 / 3) * kTlP + (r9 % 3);
-          const float ox = (float)(r9 % 3 - 1) * d, oy = (float)(r9 / 3 - 1) * d;
-          const int s0 = pst[pi], cnt = pst[pi + 1] - s0;
-          for (int off = 0; off < cnt;) {
-            const int take = min(cnt - off, kTlWB - fill);
-            for (int j = lane; j < take; j += 32) {
-              const float4 v = src[s0 + off + j];
-              wb[fill + j] = make_float4(v.x + ox, v.y + oy, v.z, 0.f);
-            }
-            if (r9 == 4) {
-              slo = fill;
-              shi = fill + take;
-            }
-            fill += take;
-            off += take;
-            if (fill == kTlWB) {
-              __syncwarp();
-              free_batch(wb, fill, g, ng, slo, shi, me.x, me.y, acc);
-              __syncwarp();
-              fill = 0;
-              slo = shi = 0;
-            }
-          }
-        }
-        __syncwarp();
-        free_batch(wb, fill, g, ng, slo, shi, me.x, me.y, acc);
-        __syncwarp();
-        lf = acc.lf;
-        gx = acc.gx;
-        gy = acc.gy;
-      } else {
-        // patch too large for the buffer: read the sources from global memory
-        for (int r = 0; r < 3; ++r) {
-          for (int c = 0; c < 3; ++c) {
-            const int mx = ix - 1 + c, my = iy - 1 + r;
-            if (mx < 0 || my < 0 || mx >= nx || my >= nx) continue;
-            const uint64_t sl = box_morton(mx, my);
-            const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-            const float sx = me.x - (float)(c - 1) * d, sy = me.y - (float)(r - 1) * d;
-            for (int k = s0 + g; k < s1; k += ng) {
-              const float2 v = loc[k];
-              const float dx = sx - v.x, dy = sy - v.y;
-              float r2 = fmaf(dx, dx, dy * dy);
-              float q = qs[k];
-              const bool ok = r2 > 0.f;
-              q = ok ? q : 0.f;
-              r2 = ok ? r2 : 1.f;
-              const float qi = q * fast_rcp(r2);
-              lf = fmaf(q, fast_lg2(r2), lf);
-              gx = fmaf(qi, dx, gx);
-              gy = fmaf(qi, dy, gy);
-            }
-          }
-        }
-      }
-      lf = xsum(lf, gs);
-      gx = xsum(gx, gs);
-      gy = xsum(gy, gs);
-      if (!act || g != 0) continue;
-      cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
-      cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
-      for (int n = p - 1; n >= 0; --n) {
-        da = da * w + va;
-        va = va * w + Al[n];
-        db = db * wb + vb;
-        vb = vb * wb + Bl[n];
-      }
-      const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
-      const float i2pi = (float)(1.0 / HP_TWO_PI);
-      const float ur_ = va.x + vb.x - lf * c4;
-      const float ui_ = va.y + vb.y;
-      const cf gxo = invd * (da + db) + mk(-gx * i2pi, 0.f);
-      const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-gy * i2pi, 0.f);
-      const int64_t o = perm[i];
-      reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
-      if (grad) {
-        double4 gv;
-        gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
-        reinterpret_cast<double4 *>(grad)[o] = gv;
-      }
-    }
-  }
-}
 
 // Single-precision leaf evaluation with one target per lane.  A block takes
 // a 4 x 4 tile of leaves -- 16 consecutive Morton leaves, so its targets are
@@ -2153,13 +1578,103 @@ k_eval32m(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp,
   }
 }
 
+// Evaluation at separate targets (Example 2: field points that are not
+// sources, on y >= 0).  One thread per target, in the caller's order: the
+// target's leaf comes from the plan's geometry (targets lie in the root
+// square); the leaf's local expansions give the far field (L2P), and the
+// sources of the 3 x 3 neighbour leaves the near field -- free part for all,
+// image and reaction parts for bottom-row leaves, as for the sources
+// themselves.  The near field is summed in double precision for both plan
+// precisions (single-precision plans store sources relative to their leaf
+// centre; the absolute position is rebuilt in double).  A target that
+// coincides with a source skips that pair's free term (log singularity).
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_eval_targets(const double *__restrict__ xt, const double *__restrict__ yt, int64_t nt,
+               const double *__restrict__ xs, const double *__restrict__ ys,
+               const float2 *__restrict__ loc, const R *__restrict__ qs,
+               const int *__restrict__ leaf_start, int H, double x0, double side, int p,
+               cd kappa, const cpx<R> *__restrict__ A, const cpx<R> *__restrict__ B,
+               double *__restrict__ pot, double *__restrict__ grad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int P1 = p + 1, nx = 1 << H;
+  const double d = side / (double)nx;
+  const double x = xt[t], y = yt[t];
+  int ix = (int)floor((x - x0) / d), iy = (int)floor(y / d);
+  ix = ix < 0 ? 0 : (ix >= nx ? nx - 1 : ix);
+  iy = iy < 0 ? 0 : (iy >= nx ? nx - 1 : iy);
+  const uint64_t leaf = box_morton(ix, iy);
+  const double cx = x0 + (ix + 0.5) * d, cy = (iy + 0.5) * d;
+  // far field: L2P with the leaf's expansions (Horner in w and conj(w))
+  const cpx<R> *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+  const cpx<R> *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+  const cd w = mk((x - cx) / d, (y - cy) / d), wb = conj(w);
+  auto c64 = [](cpx<R> z) { return mk((double)z.x, (double)z.y); };
+  cd va = c64(Al[p]), da = mk(0.0, 0.0), vb = c64(Bl[p]), db = mk(0.0, 0.0);
+  for (int n = p - 1; n >= 0; --n) {
+    da = da * w + va;
+    va = va * w + c64(Al[n]);
+    db = db * wb + vb;
+    vb = vb * wb + c64(Bl[n]);
+  }
+  cd u = va + vb;
+  cd gx = (1.0 / d) * (da + db);
+  cd gy = (1.0 / d) * (mul_i(da) - mul_i(db));
+  // near field
+  PairAcc<double> acc;
+  for (int ny = iy - 1; ny <= iy + 1; ++ny) {
+    if (ny < 0 || ny >= nx) continue;
+    for (int mx = ix - 1; mx <= ix + 1; ++mx) {
+      if (mx < 0 || mx >= nx) continue;
+      const uint64_t sl = box_morton(mx, ny);
+      const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+      const double scx = x0 + (mx + 0.5) * d, scy = (ny + 0.5) * d;
+      const bool mirror = iy == 0 && ny == 0;
+      for (int k = s0; k < s1; ++k) {
+        double sx, sy;
+        if (sizeof(R) == 8) {
+          sx = xs[k];
+          sy = ys[k];
+        } else {
+          const float2 v = loc[k];
+          sx = scx + (double)v.x;
+          sy = scy + (double)v.y;
+        }
+        const double q = (double)qs[k];
+        const double dx = x - sx, dy = y - sy;
+        if (dx != 0.0 || dy != 0.0) pair_free(acc, dx, dy, q);
+        if (mirror) {
+          const double Y = y + sy;
+          pair_image(acc, dx, Y, q);
+          pair_reaction_d(acc, dx, Y, q, kappa);
+        }
+      }
+    }
+  }
+  cd un, gxn, gyn;
+  acc.finish(un, gxn, gyn);
+  u = u + un;
+  gx = gx + gxn;
+  gy = gy + gyn;
+  pot[2 * t] = u.x;
+  pot[2 * t + 1] = u.y;
+  if (grad) {
+    grad[4 * t + 0] = gx.x;
+    grad[4 * t + 1] = gx.y;
+    grad[4 * t + 2] = gy.x;
+    grad[4 * t + 3] = gy.y;
+  }
+}
+
 // Image and reaction near field of the bottom-row leaves (single precision
 // with the double routine for |P| > 1 and, in MIXED mode, below tau), added
-// to the outputs written by k_eval32g.  One block per bottom-row leaf: the
+// to the outputs written by the leaf kernel.  One block per bottom-row leaf: the
 // sources of the three bottom-row neighbours are staged in shared memory,
 // lanes take 32 targets at a time and the 8 warps split the sources; the
 // partial sums are reduced in shared memory.
 constexpr int kMirSrc = 512;
+constexpr int kMirSplit = 8;  // blocks per bottom-row leaf
 __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
@@ -2193,7 +1708,9 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
   }
   const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
   const float i2pi = (float)(1.0 / HP_TWO_PI);
-  for (int tb = b0; tb < b1; tb += 32) {
+  // target tiles of 32 are spread over gridDim.z blocks (leaves next to a
+  // cluster hold many points)
+  for (int tb = b0 + 32 * (int)blockIdx.z; tb < b1; tb += 32 * (int)gridDim.z) {
     const int i = tb + lane;
     const bool act = i < b1;
     const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
@@ -2253,9 +1770,15 @@ struct MultiWork {
 };
 constexpr int kRhsChunk = 8;
 
+// separate targets: evaluate at (xt, yt) instead of at the sources
+struct TargetWork {
+  const double *xt, *yt;
+  int64_t nt;
+};
+
 template <typename R>
 hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *grad,
-                        cudaStream_t st, const MultiWork *mw) {
+                        cudaStream_t st, const MultiWork *mw, const TargetWork *tw = nullptr) {
   const int p = pl->p, P1 = p + 1, H = pl->H;
   const int64_t n = pl->n;
   const size_t m2 = (size_t)P1 * P1;
@@ -2331,12 +1854,11 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
-  size_t shmir = sizeof(cpx<R>) * P1 * kWarpsPerBlock;
   bool patched = false, tc_m2l = false;
   if (H >= 2 && sizeof(R) == 4) {
     pass_begin(pl, st, PASS_M2L_FREE);
     if (mw && nr >= 16 && pl->m2l_mode == 1)
-      tc_m2l = patched = launch_m2l_tc(p, H, lg, (const cf *)pl->t_m2l_pad, logs, (const cf *)M, (cf *)A,
+      tc_m2l = patched = launch_m2l_tc(p, H, lg, (const float *)pl->t_m2l_tc, logs, (const cf *)M, (cf *)A,
                               (cf *)B, pl->status, st, nr, rs);
     if (!patched)
       patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
@@ -2374,6 +1896,15 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
   cd kappa = mk(pl->kre, pl->kim);
+  if (tw) {
+    if (tw->nt > 0)
+      k_eval_targets<R><<<cdiv_u(tw->nt, 128), 128, 0, st>>>(
+          tw->xt, tw->yt, tw->nt, pl->xs, pl->ys, pl->loc32, (const R *)qs, pl->leaf_start, H,
+          pl->x0, pl->side, p, kappa, A, B, pot, grad);
+    pass_end(pl, st, PASS_EVAL, tw->nt > 0 ? 1 : 0);
+    HP_LAUNCH_CHECK();
+    return HPFMM_OK;
+  }
   if (sizeof(R) == 8) {
     k_eval64<<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
         pl->xs, pl->ys, (const double *)qs, pl->perm, pl->leaf_start, H, pl->x0, pl->side, p,
@@ -2387,13 +1918,13 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
           lg.invd[H], p, (const cf *)A, (const cf *)B, rs, pot, grad);
     } else {
       const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
-      k_eval32t<<<(unsigned)(tps * tps), 32 * kEvWarps, kTlSmem, st>>>(
+      k_eval32p<<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
           pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
           (const cf *)A, (const cf *)B, pot, grad);
     }
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
-    k_mirror32<<<dim3((unsigned)(1 << H), nr), 32 * kEvWarps, 0, st>>>(
+    k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], kappa, tau, pot,
         grad, rs);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
@@ -2424,8 +1955,6 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
-  HP_CUDA(cudaFuncSetAttribute(k_eval32t, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kTlSmem));
   HP_CUDA(cudaFuncSetAttribute(k_eval32p, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2452,6 +1981,15 @@ bool fmm_multi_supported(const hpfmm_plan *pl) {
 }
 
 int fmm_multi_rp(int nr) { return (nr + kRhsChunk - 1) / kRhsChunk * kRhsChunk; }
+
+hpfmm_status fmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
+                              const double *yt, int64_t nt, double *pot, double *grad,
+                              cudaStream_t st) {
+  HP_TRY(special_init_here());
+  const TargetWork tw{xt, yt, nt};
+  if (pl->prec == HPFMM_FP64) return run_passes<double>(pl, q, pot, grad, st, nullptr, &tw);
+  return run_passes<float>(pl, q, pot, grad, st, nullptr, &tw);
+}
 
 hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot, double *grad,
                             void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st) {

@@ -34,6 +34,7 @@
 
 #include "common.cuh"
 #include "special.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -188,6 +189,38 @@ __global__ void k_to_float(const cd *a, cf *b, size_t n) {
 // FP32 copies live right after the double block of the same allocation).
 // Static tables depend on p only (created once per plan); the reaction tables
 // depend on kappa and the box sides (rebuilt with the tree).
+// Tensor-core operand B of the free-space M2L (multi-RHS, m2l_mode 1): for
+// each of the 40 far classes the real form of T (rows: outputs Re L_n then
+// Im L_n; columns: inputs Re M_m then Im M_m), zero-padded to NP x KP, split
+// into tf32 hi and lo parts (lo = the rounded remainder of the double value),
+// each in the K-major core-matrix layout; per class [hi | lo].  The level's
+// M_0 ln|t d| term is added by the kernel, so the table is level-free.
+__global__ void k_m2l_tc_table(int p, const cd *__restrict__ T, float *__restrict__ out) {
+  const int P1 = p + 1, KP = tc_kp(P1), NP = tc_np(P1);
+  const int slot = blockIdx.x;  // 0..39
+  int c = 0, k40 = -1;
+  for (; c < 49; ++c) {
+    const int dx = c % 7 - 3, dy = c / 7 - 3;
+    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+    if (++k40 == slot) break;
+  }
+  float *hi = out + (size_t)slot * 2 * NP * KP, *lo = hi + NP * KP;
+  for (int e = threadIdx.x; e < NP * KP; e += blockDim.x) {
+    const int no = e / KP, k = e % KP;
+    double v = 0.0;
+    if (no < 2 * P1 && k < 2 * P1) {
+      const int n = no < P1 ? no : no - P1, m = k < P1 ? k : k - P1;
+      const cd t = T[(size_t)c * P1 * P1 + n * P1 + m];
+      const bool imo = no >= P1, imi = k >= P1;
+      v = imo == imi ? t.x : (imo ? t.y : -t.y);
+    }
+    const float h = tc_round((float)v);
+    const float l = tc_round((float)(v - (double)h));
+    hi[tc_off(no, k, KP)] = h;
+    lo[tc_off(no, k, KP)] = l;
+  }
+}
+
 hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
   int p = pl->p, P1 = p + 1;
   size_t m2 = (size_t)P1 * P1;
@@ -205,6 +238,7 @@ hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
     for (auto &e : t)
       k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
     if (pl->t_m2l_pad) k_m2l_pad<<<1, 256, 0, st>>>(p, fm2l, (cf *)pl->t_m2l_pad);
+    if (pl->t_m2l_tc) k_m2l_tc_table<<<40, 256, 0, st>>>(p, fm2l, (float *)pl->t_m2l_tc);
     HP_LAUNCH_CHECK();
   }
   return HPFMM_OK;

@@ -19,6 +19,11 @@ __host__ __device__ __forceinline__ int tc_off(int row, int k, int kdim) {
   return (((row >> 3) * (kdim >> 2) + (k >> 2)) << 5) + ((row & 7) << 2) + (k & 3);
 }
 
+// padded real-form sizes of a complex (p+1) x (p+1) translation: K (inputs
+// Re, Im) to the MMA step of 8, N (outputs) to 16
+__host__ __device__ constexpr int tc_kp(int p1) { return (2 * p1 + 7) / 8 * 8; }
+__host__ __device__ constexpr int tc_np(int p1) { return (2 * p1 + 15) / 16 * 16; }
+
 // shared-memory matrix descriptor (no swizzle)
 __device__ __forceinline__ uint64_t tc_sdesc(unsigned saddr, unsigned lbo, unsigned sbo) {
   uint64_t d = 0;
@@ -91,6 +96,12 @@ __device__ __forceinline__ void tc_ld8(unsigned taddr, float v[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tc_round(float x) {
+  unsigned h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
 }
 
 // split x = hi + lo with hi and lo representable in tf32 (round to nearest):

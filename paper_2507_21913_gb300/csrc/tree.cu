@@ -80,7 +80,8 @@ __global__ void bbox_partial(const double *__restrict__ x, const double *__restr
 // final reduction (one block); geo[0] = x0, geo[1] = L (side), geo[2] = bad
 // flag, geo[3] = 2^30 / L rounded (the fast-path quantisation scale)
 __global__ void __launch_bounds__(kRedThreads)
-bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo) {
+bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo, double root_x0,
+           double root_side) {
   __shared__ double s0[kRedThreads], s1[kRedThreads], s2[kRedThreads];
   __shared__ int sb[kRedThreads];
   double xmn = INFINITY, xmx = -INFINITY, ymx = -INFINITY;
@@ -112,6 +113,12 @@ bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo) {
   geo[0] = s0[0];
   geo[1] = L;
   geo[2] = sb[0] ? 1.0 : 0.0;
+  if (root_side > 0) {  // caller's root square: it must contain the points
+    const bool inside = root_x0 <= s0[0] && s1[0] <= root_x0 + root_side && s2[0] <= root_side;
+    if (!inside && !sb[0]) geo[2] = 2.0;
+    geo[0] = root_x0;
+    geo[1] = L = root_side;
+  }
   geo[3] = __ddiv_rn(1073741824.0, L);
 }
 
@@ -612,7 +619,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   int *maxleaf = (int *)(geo + 4);
   pass_begin(pl, st, PASS_TREE);
   bbox_partial<<<t.nbR, kRedThreads, 0, st>>>(x, y, n, t.part);
-  bbox_final<<<1, kRedThreads, 0, st>>>(t.part, t.nbR, geo);
+  bbox_final<<<1, kRedThreads, 0, st>>>(t.part, t.nbR, geo, pl->root_x0, pl->root_side);
   cudaError_t e = cudaMemsetAsync(t.lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
   morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, t.kb, t.va, t.lcount, t.slot);
   scan_part<<<nsb, 1024, 0, st>>>(t.lcount, nleaf, pl->leaf_start, t.btot, t.bmax);
@@ -641,7 +648,8 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const
                          cudaStream_t st) {
   hpfmm_status s = HPFMM_OK;
   if (hgeo[2] != 0.0) {
-    set_last_error("points must be finite with y > 0");
+    set_last_error(hgeo[2] == 2.0 ? "the root square does not contain the points"
+                                  : "points must be finite with y > 0");
     s = HPFMM_EINVAL;
   } else {
     pl->x0 = hgeo[0];
@@ -757,7 +765,7 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
   // the array keeps the previous call's contents: clear what must start at 0
   HP_CUDA(cudaMemsetAsync(lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st));
   bbox_partial<<<nbR, kRedThreads, 0, st>>>(x, y, n, part);
-  bbox_final<<<1, kRedThreads, 0, st>>>(part, nbR, geo);
+  bbox_final<<<1, kRedThreads, 0, st>>>(part, nbR, geo, 0.0, 0.0);
   morton_keys<<<gb, 256, 0, st>>>(x, y, n, geo, H, kb, va, lcount, slot);
   scan_part<<<nsb, 1024, 0, st>>>(lcount, nleaf, lstart, btot, bmax);
   scan_top<<<1, 1024, 0, st>>>(btot, bmax, nsb, nleaf, lstart, (int *)(geo + 4));

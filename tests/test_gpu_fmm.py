@@ -161,7 +161,7 @@ def test_clustered_4m_mixed_complex_kappa():
                                   g0.choice(far, 32, replace=False)]))
     kappa = 1.0 + 0.5j
     u_ref, g_ref = oracle_cache.sampled_closed(x, y, q, idx, kappa)
-    u, g, plan = run(x, y, q, kappa, 20, 32, prec="mixed", levels=10)
+    u, g, plan = run(x, y, q, kappa, 20, 32, prec="mixed", levels=11)
     assert rel(u[idx], u_ref) < 5e-6
     assert rel(g[idx], g_ref) < 2e-5
     m = y[idx] < 0.06  # the near-boundary half on its own

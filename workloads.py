@@ -93,3 +93,23 @@ EXAMPLE1 = dict(
     image_center=(0.03125, -0.46875), image_parent_center=(0.1875, -0.3125),
     child_side=0.3125, parent_side=0.625,
 )
+
+
+def example2(n_source=250, nfx=64, nfy=31):
+    """The paper's Example 2 geometry: 8 circles of radius 1 centred at
+    (-3.3 + 2.2 n, 1.01) and (-3.3 + 2.2 n, 3.2), n = 0..3 (the lower ones 0.01
+    above y = 0), each cut into n_source equal arcs whose midpoints carry the
+    charge 2 pi / n_source; field points on a uniform nfx x nfy Cartesian mesh
+    of [-4.4, 4.4] x [0, 4.2], whose bottom row lies on y = 0.
+    Returns (xs, ys, qs, xt, yt)."""
+    th = 2.0 * np.pi * (np.arange(n_source) + 0.5) / n_source
+    xs, ys = [], []
+    for cy in (1.01, 3.2):
+        for n in range(4):
+            xs.append(-3.3 + 2.2 * n + np.cos(th))
+            ys.append(cy + np.sin(th))
+    xs = np.concatenate(xs)
+    ys = np.concatenate(ys)
+    qs = np.full(xs.size, 2.0 * np.pi / n_source)
+    gx, gy = np.meshgrid(np.linspace(-4.4, 4.4, nfx), np.linspace(0.0, 4.2, nfy))
+    return xs, ys, qs, gx.ravel(), gy.ravel()
