@@ -187,6 +187,18 @@ SINGLE_KERNEL = {"eval": ("k_eval32p", "k_eval64"), "m2l_free": ("k_m2l_free_pat
                  "p2m": ("k_p2m", "k_p2m"), "near_mirror": ("k_mirror32", None)}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised in profiles/, keyed by kernel and configuration
+# (n, p, levels, precision); only reported for that configuration, and to be
+# re-measured whenever the kernel changes
+NCU_TRAFFIC = {("k_eval32p", 1_000_000, 12, 8, "fp32"): 41_965_824 + 9_208_320,
+               ("k_m2l_free_patch", 1_000_000, 12, 8, "fp32"): 9_438_464 + 272_896}
+
+
+def _traffic(name, args, H):
+    return NCU_TRAFFIC.get((name, args.n, args.p, H, args.prec))
+
+
 def roofline(passes_ms, launches, args, npairs, H, peaks):
     """Roofline entry for the dominant kernel: the single-kernel pass with the
     largest device time; achieved = algorithmic work per launch / per-launch
@@ -204,7 +216,10 @@ def roofline(passes_ms, launches, args, npairs, H, peaks):
         achieved = ops / t / 1e12
         return {"kernel": name + " (L2P + free-space near field)", "bound": "alu",
                 "unit": "TOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "traffic": None, "work": "2 SFU ops (lg2, rcp) per near-field pair, %d pairs"
+                "traffic": _traffic(name, args, H),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                  "(profiles/k_eval32p_uniform1M_fp32_p12_L8.md)",
+                "work": "2 SFU ops (lg2, rcp) per near-field pair, %d pairs"
                 % npairs, "peak_source": "16 SFU ops/clk/SM x 152 SMs x %.0f MHz (nominal)"
                 % (f_ghz * 1e3), "per_launch_ms": t * 1e3}
     if dom == "m2l_free":
@@ -214,7 +229,7 @@ def roofline(passes_ms, launches, args, npairs, H, peaks):
         peak = 128 * 2 * sms * f_ghz * 1e9 / 1e12
         achieved = flops / t / 1e12
         return {"kernel": name, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
-                "peak": peak, "frac": achieved / peak, "traffic": None,
+                "peak": peak, "frac": achieved / peak, "traffic": _traffic(name, args, H),
                 "work": "8 (p+1)^2 flops per V-list translation, %d translations" % ntrans,
                 "peak_source": "FP32 FMA: 128/clk/SM x 2 x 152 SMs x %.0f MHz (nominal)"
                 % (f_ghz * 1e3), "per_launch_ms": t * 1e3}
