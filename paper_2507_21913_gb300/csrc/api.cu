@@ -129,6 +129,12 @@ extern "C" hpfmm_status hpfmm_read_timing(hpfmm_plan *pl, double ms[10], int64_t
 
 static void free_plan(hpfmm_plan *pl) {
   if (!pl) return;
+  if (pl->side_stream) {
+    cudaStreamSynchronize(pl->side_stream);
+    cudaStreamDestroy(pl->side_stream);
+  }
+  if (pl->ev_geo) cudaEventDestroy(pl->ev_geo);
+  if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
   if (pl->tstate) {
     TimingState *ts = (TimingState *)pl->tstate;
     for (cudaEvent_t e : ts->pool) cudaEventDestroy(e);
@@ -184,7 +190,17 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
     dy = tmp + n;
   }
   hpfmm_status s = tree_build(pl, dx, dy, st);
-  if (s == HPFMM_OK) s = tables_build(pl, st);
+  if (s == HPFMM_OK) {
+    // reaction tables on the side stream, concurrent with the rest of the tree build
+    e = cudaStreamWaitEvent(pl->side_stream, pl->ev_geo, 0);
+    if (e == cudaSuccess) s = tables_build(pl, pl->side_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pl->ev_tables, pl->side_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, pl->ev_tables, 0);
+    if (e != cudaSuccess) {
+      set_last_error("rebuild: table stream: %s", cudaGetErrorString(e));
+      s = HPFMM_ECUDA;
+    }
+  }
   // the one host synchronisation of a rebuild: geometry, validity, largest leaf
   double hgeo[5] = {0, 0, 1, 0, 0};
   if (s == HPFMM_OK) {
@@ -293,7 +309,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);
-  if (f32) ALLOC(pl->t_m2l_pad, sizeof(cf) * 40 * (size_t)P1 * ((P1 + 1) & ~1));
+  if (f32) ALLOC(pl->t_m2l_pad, sizeof(cf) * 40 * 2 * 2 * (size_t)P1);
   if (f32 && pl->m2l_mode == 1)
     ALLOC(pl->t_m2l_tc, sizeof(float) * 40 * 2 * (size_t)tc_np(P1) * tc_kp(P1));
   ALLOC(pl->t_rlog, tf * 21 * m2);
@@ -309,6 +325,16 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
 #undef ALLOC
   s = fmm_set_smem_limits(p);
   if (s != HPFMM_OK) { free_plan(pl); return s; }
+  {
+    cudaError_t ce = cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_geo, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      set_last_error("hpfmm_create: %s", cudaGetErrorString(ce));
+      free_plan(pl);
+      return HPFMM_ECUDA;
+    }
+  }
   cudaError_t e = cudaMemsetAsync(pl->status, 0, sizeof(int), st);
   if (e != cudaSuccess) {
     set_last_error("hpfmm_create: %s", cudaGetErrorString(e));

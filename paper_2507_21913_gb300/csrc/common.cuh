@@ -201,7 +201,7 @@ struct hpfmm_plan {
   void *t_m2m = nullptr;   // 4 x (p+1)^2 complex: child c -> parent
   void *t_l2l = nullptr;   // 4 x (p+1)^2 complex: parent -> child c (analytic part)
   void *t_m2l = nullptr;   // 49 offset classes x (p+1)^2 complex: free-space log M2L
-  void *t_m2l_pad = nullptr;  // FP32 path: the 40 far classes, rows padded to even length
+  void *t_m2l_pad = nullptr;  // FP32 path: Hankel form of the 40 far classes (2 x 2(p+1) each)
   void *t_m2l_tc = nullptr;   // tensor-core M2L: the 40 far classes as tf32 hi/lo operands
   void *t_refl = nullptr;  // per level: 7 x 3 classes x (2p+1) complex: scaled I_k tables
   void *t_rlog = nullptr;  // per level: 7 x 3 classes x (p+1)^2 complex: image-log M2L
@@ -221,6 +221,11 @@ struct hpfmm_plan {
   void *mq = nullptr, *mqsm = nullptr, *mM = nullptr, *mA = nullptr, *mB = nullptr;
   int mcap = 0;
   int *tflag = nullptr;  // target validation flag (hpfmm_eval_targets)
+  // the reaction tables of a rebuild run on a side stream, overlapping the
+  // tree build: forked once the bounding square is known, joined before the
+  // rebuild's synchronisation
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_geo = nullptr, ev_tables = nullptr;
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
   void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish

@@ -535,16 +535,22 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   M += blockIdx.y * rs.m;
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
-  // rows padded to an even length PP so that k, k+1 pairs are one 16-byte
-  // (single precision) shared-memory load; the source patch is stored with
-  // even columns first, so that the sources of a warp's x-consecutive
-  // targets (all of one column parity) are consecutive boxes
+  // The translation of each class is applied in its Hankel form (see the
+  // table builder): moments scaled by 1/k! when staged, T'[l][k] = g_{l+k},
+  // outputs scaled by (-1)^{l+1}/l!.  Moment rows are padded to an even length
+  // PP so that k, k+1 pairs are one 16-byte (single precision) shared-memory
+  // load, and so are (g_j, g_{j+1}) -- from the second, shifted copy of g when
+  // j is odd.  The source patch is stored with even columns first, so that the
+  // sources of a warp's x-consecutive targets (all of one column parity) are
+  // consecutive boxes.
   constexpr int PP = (P1 + 1) & ~1;
+  constexpr int GP = 2 * P1;
   constexpr int HALF = kPatchSrc / 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
-  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][P1][PP]
-  cpx<R> *Mp = Ts + 40 * P1 * PP;                          // [20][20][PP]
+  __shared__ R fac_in[P1], fac_out[P1];                    // 1/k!, (-1)^{l+1}/l!
+  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][2][GP]
+  cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [20][20][PP]
   R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * PP);  // [40] ln|t d|
   // level and patch of this block
   int b = blockIdx.x, l = 2;
@@ -560,8 +566,8 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   const int nparent_side = 1 << (l - 1), nside = 1 << l;
   const int64_t off = level_offset(l);
   const R logd = (R)lgm.logd[l];
-  // the 40 translation matrices: one bulk copy (TMA) from the padded table
-  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * P1 * PP);
+  // the 40 Hankel vectors: one bulk copy (TMA) from the table
+  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * 2 * GP);
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_expect_tx(&bar, tbytes);
@@ -569,6 +575,13 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   }
   for (int c = threadIdx.x; c < 49; c += blockDim.x)
     if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
+  if (threadIdx.x < P1) {
+    double f = 1.0;
+    for (int i = 2; i <= (int)threadIdx.x; ++i) f *= (double)i;
+    fac_in[threadIdx.x] = (R)(1.0 / f);
+    fac_out[threadIdx.x] = (R)(((threadIdx.x & 1) ? 1.0 : -1.0) / f);
+  }
+  __syncthreads();
   // source patch: one box per thread and iteration, P1 independent loads each
   const int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
   for (int sb = threadIdx.x; sb < kPatchSrc * kPatchSrc; sb += blockDim.x) {
@@ -582,7 +595,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
 #pragma unroll
       for (int k = 0; k < P1; ++k) v[k] = src[k];
 #pragma unroll
-      for (int k = 0; k < P1; ++k) dst[k] = v[k];
+      for (int k = 0; k < P1; ++k) dst[k] = fac_in[k] * v[k];
     } else {
 #pragma unroll
       for (int k = 0; k < P1; ++k) dst[k] = mk<R>(0, 0);
@@ -613,7 +626,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
     for (int dx = -2 - a; dx <= 3 - a; ++dx) {
       if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
       const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
-      const cpx<R> *T = Ts + slot * P1 * PP;
+      const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
       const int colA = txA + dx - sx0, colB = txB + dx - sx0;  // same parity
       const int cpA = (colA & 1) * HALF + (colA >> 1), cpB = (colB & 1) * HALF + (colB >> 1);
       const cpx<R> *mA = Mp + ((tyA + dy - sy0) * kPatchSrc + cpA) * PP;
@@ -623,16 +636,19 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
         const cpx<R> ma0 = mA[k], ma1 = mA[k + 1], mb0 = mB[k], mb1 = mB[k + 1];
 #pragma unroll
         for (int r = 0; r < P1; ++r) {
-          const cpx<R> t0 = T[r * PP + k], t1 = T[r * PP + k + 1];
+          // (g_{r+k}, g_{r+k+1}): an aligned pair of copy 0 (r even) or copy 1 (r odd)
+          const cpx<R> *gp = (r & 1) ? G1 + (r + k - 1) : G0 + (r + k);
+          const cpx<R> t0 = gp[0], t1 = gp[1];
           cfma(accA[r], t0, ma0);
           cfma(accA[r], t1, ma1);
           cfma(accB[r], t0, mb0);
           cfma(accB[r], t1, mb1);
         }
       }
+      // M_0 ln|t d| on Re L_0, in the scaled outputs (L_0 = -L'_0; M'_0 = M_0)
       const R lgc = lg[slot];
-      accA[0].x += mA[0].x * lgc;  // M_0 ln|t d| (Re L_0 only)
-      accB[0].x += mB[0].x * lgc;
+      accA[0].x -= mA[0].x * lgc;
+      accB[0].x -= mB[0].x * lgc;
     }
   }
   const R s = (R)(-0.5 / HP_TWO_PI);
@@ -640,7 +656,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
     const size_t e0 = (size_t)(off + box_morton(txA, tyA)) * P1;
 #pragma unroll
     for (int r = 0; r < P1; ++r) {
-      const cpx<R> v = s * accA[r];
+      const cpx<R> v = (s * fac_out[r]) * accA[r];
       A[e0 + r] = v;
       B[e0 + r] = conj(v);
     }
@@ -649,7 +665,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
     const size_t e0 = (size_t)(off + box_morton(txB, tyB)) * P1;
 #pragma unroll
     for (int r = 0; r < P1; ++r) {
-      const cpx<R> v = s * accB[r];
+      const cpx<R> v = (s * fac_out[r]) * accB[r];
       A[e0 + r] = v;
       B[e0 + r] = conj(v);
     }
@@ -659,7 +675,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
 template <typename R, int P1>
 size_t patch_smem() {
   constexpr int PP = (P1 + 1) & ~1;
-  return sizeof(cpx<R>) * (40 * P1 * PP + kPatchSrc * kPatchSrc * PP) + sizeof(R) * 40;
+  return sizeof(cpx<R>) * (40 * 2 * 2 * P1 + kPatchSrc * kPatchSrc * PP) + sizeof(R) * 40;
 }
 
 int patch_blocks(int H) {

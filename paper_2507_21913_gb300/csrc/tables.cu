@@ -127,7 +127,7 @@ __global__ void k_img_m2l(int p, cd *T, cd *logt) {
 // series or continued fraction for that k, no recursion between threads) and
 // fills Tr[l][(ysum, dx = m)][+] and Tr[l][(ysum, dx = -m)][-].
 __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd kappa,
-                               const double *__restrict__ Cb, cd *Tr) {
+                               const double *__restrict__ Cb, cd *Tr, cf *Tf) {
   extern __shared__ cd sh[];
   const double side = geo[1];
   const int P1 = p + 1, K = 2 * p;
@@ -157,21 +157,42 @@ __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd 
     for (int r = 0; r < ((m - n) & 3); ++r) vm = mul_i(vm);  // i^{m-n}
     outp[e] = vp;
     outm[e] = vm;
+    if (Tf) {  // single-precision copy, same layout
+      Tf[(outp - Tr) + e] = to<float>(vp);
+      Tf[(outm - Tr) + e] = to<float>(vm);
+    }
   }
 }
 
 // the 40 far offset classes of the free-space M2L, single precision, rows
 // padded with zeros to an even length (layout of the patch M2L kernel)
-__global__ void k_m2l_pad(int p, const cd *T, cf *out) {
-  const int P1 = p + 1, PP = (P1 + 1) & ~1;
+// Single-precision free-space M2L in Hankel form.  The log M2L matrix factors
+// as T[l][k] = a_l g_{l+k} b_k with a_l = (-1)^{l+1}/l!, b_k = 1/k! and
+// g_j = (j-1)! t^{-j} (g_0 = 0: the l = k = 0 entry is the separate log term),
+// so with moments scaled by b_k and outputs by a_l only the 2p+1 values g_j of
+// a class are needed.  Per far class (40, in class order): two copies of g,
+// the second shifted by one (g_{j+1}), each padded to 2(p+1) entries, so that
+// the pairs (g_j, g_{j+1}) the kernel reads are 16-byte aligned for either
+// parity of j.  Computed in double and rounded.
+__global__ void k_m2l_pad(int p, cf *out) {
+  const int P1 = p + 1, GP = 2 * P1;
   int slot = 0;
   for (int c = 0; c < 49; ++c) {
     const int dx = c % 7 - 3, dy = c / 7 - 3;
     if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-    for (int e = threadIdx.x; e < P1 * PP; e += blockDim.x) {
-      const int r = e / PP, k = e % PP;
-      out[(size_t)slot * P1 * PP + e] =
-          k < P1 ? to<float>(T[(size_t)c * P1 * P1 + r * P1 + k]) : mk(0.f, 0.f);
+    const cd t = mk(-(double)dx, -(double)dy);
+    const cd ti = cinv(t);
+    for (int e = threadIdx.x; e < 2 * GP; e += blockDim.x) {
+      const int j = e < GP ? e : e - GP + 1;  // second copy: shifted by one
+      cd g = mk(0.0, 0.0);
+      if (j >= 1 && j <= 2 * p) {
+        g = mk(1.0, 0.0);
+        for (int i = 1; i <= j; ++i) g = g * ti;  // t^{-j}
+        double f = 1.0;
+        for (int i = 2; i < j; ++i) f *= (double)i;  // (j-1)!
+        g = f * g;
+      }
+      out[(size_t)slot * 2 * GP + e] = to<float>(g);
     }
     ++slot;
   }
@@ -237,7 +258,7 @@ hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
                                                {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2}};
     for (auto &e : t)
       k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
-    if (pl->t_m2l_pad) k_m2l_pad<<<1, 256, 0, st>>>(p, fm2l, (cf *)pl->t_m2l_pad);
+    if (pl->t_m2l_pad) k_m2l_pad<<<1, 256, 0, st>>>(p, (cf *)pl->t_m2l_pad);
     if (pl->t_m2l_tc) k_m2l_tc_table<<<40, 256, 0, st>>>(p, fm2l, (float *)pl->t_m2l_tc);
     HP_LAUNCH_CHECK();
   }
@@ -251,16 +272,10 @@ hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st) {
   HP_TRY(special_init_here());
   pass_begin(pl, st, PASS_TABLES);
   size_t shm = sizeof(cd) * (2 * p + 1);
+  const size_t ne = (size_t)H * 42 * m2;
   k_reaction_m2l<<<H * 21, 96, shm, st>>>(p, H, pl->geo, mk(pl->kre, pl->kim), pl->t_binom,
-                                           rea);
+                                           rea, pl->prec != HPFMM_FP64 ? (cf *)(rea + ne) : nullptr);
   HP_LAUNCH_CHECK();
-  int nl = 1;
-  if (pl->prec != HPFMM_FP64) {
-    size_t ne = (size_t)H * 42 * m2;
-    k_to_float<<<256, 256, 0, st>>>((const cd *)rea, (cf *)(rea + ne), ne);
-    HP_LAUNCH_CHECK();
-    nl = 2;
-  }
-  pass_end(pl, st, PASS_TABLES, nl);
+  pass_end(pl, st, PASS_TABLES, 1);
   return HPFMM_OK;
 }

@@ -620,7 +620,9 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   pass_begin(pl, st, PASS_TREE);
   bbox_partial<<<t.nbR, kRedThreads, 0, st>>>(x, y, n, t.part);
   bbox_final<<<1, kRedThreads, 0, st>>>(t.part, t.nbR, geo, pl->root_x0, pl->root_side);
-  cudaError_t e = cudaMemsetAsync(t.lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
+  cudaError_t e = cudaSuccess;
+  if (pl->ev_geo) e = cudaEventRecord(pl->ev_geo, st);  // the geometry is known from here on
+  if (e == cudaSuccess) e = cudaMemsetAsync(t.lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
   morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, t.kb, t.va, t.lcount, t.slot);
   scan_part<<<nsb, 1024, 0, st>>>(t.lcount, nleaf, pl->leaf_start, t.btot, t.bmax);
   scan_top<<<1, 1024, 0, st>>>(t.btot, t.bmax, nsb, nleaf, pl->leaf_start, maxleaf);
