@@ -135,6 +135,7 @@ static void free_plan(hpfmm_plan *pl) {
   }
   if (pl->ev_geo) cudaEventDestroy(pl->ev_geo);
   if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
+  if (pl->hgeo) cudaFreeHost(pl->hgeo);
   if (pl->tstate) {
     TimingState *ts = (TimingState *)pl->tstate;
     for (cudaEvent_t e : ts->pool) cudaEventDestroy(e);
@@ -201,17 +202,19 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
       s = HPFMM_ECUDA;
     }
   }
-  // the one host synchronisation of a rebuild: geometry, validity, largest leaf
+  // the one host wait of a rebuild: for the bounding square (validity, root
+  // geometry), right after its reduction; the rest of the build stays queued
   double hgeo[5] = {0, 0, 1, 0, 0};
   if (s == HPFMM_OK) {
-    e = cudaMemcpyAsync(hgeo, pl->geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    e = cudaEventSynchronize(pl->ev_geo);
     if (e != cudaSuccess) {
       set_last_error("rebuild: %s", cudaGetErrorString(e));
       s = HPFMM_ECUDA;
+    } else {
+      memcpy(hgeo, pl->hgeo, sizeof hgeo);
     }
   }
-  hpfmm_status s2 = tree_finish(pl, dx, dy, hgeo, st);
+  hpfmm_status s2 = tree_finish(pl, hgeo, st);
   if (s == HPFMM_OK) s = s2;
   if (tmp) cudaFreeAsync(tmp, st);
   if (s != HPFMM_OK) return s;
@@ -329,6 +332,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     cudaError_t ce = cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_geo, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaMallocHost((void **)&pl->hgeo, 8 * sizeof(double));
     if (ce != cudaSuccess) {
       set_last_error("hpfmm_create: %s", cudaGetErrorString(ce));
       free_plan(pl);

@@ -226,6 +226,7 @@ struct hpfmm_plan {
   // rebuild's synchronisation
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_geo = nullptr, ev_tables = nullptr;
+  double *hgeo = nullptr;  // pinned host copy of geo, written by the tree build
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
   void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
@@ -273,8 +274,7 @@ void set_last_error(const char *fmt, ...);
 
 // internal entry points shared between translation units
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st);
-hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const double *hgeo,
-                         cudaStream_t st);
+hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st);
 hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status tables_build(hpfmm_plan *pl, cudaStream_t st);
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad, cudaStream_t st);

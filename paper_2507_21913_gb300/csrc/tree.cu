@@ -341,9 +341,50 @@ leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ 
   else warp_sort_leaf<4>(b0, m, lane, keys, vals);
 }
 
-// sort the leaf buckets of 129..kLeafSort points: bitonic sort in shared
-// memory, one block per leaf (blocks skip the small leaves)
+// sort the leaf buckets of more than 128 points, one block per leaf (blocks
+// skip the small leaves): up to kLeafSort points by a bitonic sort in shared
+// memory; larger leaves in place in global memory by the bitonic network whose
+// comparators all put the minimum at the lower index (each merge starts by
+// comparing an element with its mirror in the block), so that the virtual
+// +infinity padding up to the next power of two never moves into the leaf
+// and comparators that touch it are skipped
 constexpr int kLeafSort = 1024;
+
+__device__ __forceinline__ void cmp_lo_hi(uint64_t *__restrict__ keys, int *__restrict__ vals,
+                                          int lo, int hi) {
+  const uint64_t ka = keys[lo], kb = keys[hi];
+  const int va = vals[lo], vb = vals[hi];
+  if (ka > kb || (ka == kb && va > vb)) {
+    keys[lo] = kb;
+    keys[hi] = ka;
+    vals[lo] = vb;
+    vals[hi] = va;
+  }
+}
+
+__device__ void sort_leaf_global(uint64_t *__restrict__ keys, int *__restrict__ vals, int m) {
+  int np2 = 1;
+  while (np2 < m) np2 <<= 1;
+  for (int kk = 2; kk <= np2; kk <<= 1) {
+    // merge: element e of the lower half of each kk-block against its mirror
+    for (int e = threadIdx.x; e < np2 / 2; e += blockDim.x) {
+      const int lo = (e / (kk >> 1)) * kk + (e % (kk >> 1));
+      const int hi = lo ^ (kk - 1);
+      if (hi < m) cmp_lo_hi(keys, vals, lo, hi);
+    }
+    __threadfence_block();
+    __syncthreads();
+    for (int j = kk >> 2; j > 0; j >>= 1) {
+      for (int e = threadIdx.x; e < np2 / 2; e += blockDim.x) {
+        const int lo = (e / j) * 2 * j + (e % j);
+        const int hi = lo + j;
+        if (hi < m) cmp_lo_hi(keys, vals, lo, hi);
+      }
+      __threadfence_block();
+      __syncthreads();
+    }
+  }
+}
 __global__ void __launch_bounds__(256)
 leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int *__restrict__ nbig,
           uint64_t *__restrict__ keys, int *__restrict__ vals) {
@@ -353,7 +394,12 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
   for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {
     const int leaf = big[bi];
     int b0 = start[leaf], b1 = start[leaf + 1], m = b1 - b0;
-    if (m <= 128 || m > kLeafSort) continue;
+    if (m <= 128) continue;
+    if (m > kLeafSort) {
+      __syncthreads();
+      sort_leaf_global(keys + b0, vals + b0, m);
+      continue;
+    }
     int np2 = 1;
     while (np2 < m) np2 <<= 1;
     __syncthreads();
@@ -532,15 +578,14 @@ __global__ void gather_points(const double *__restrict__ x, const double *__rest
 
 // Build (or rebuild) the tree of pl for the n points (x, y) (device pointers).
 // Leaves pl->xs, ys, perm, keys, leaf_start, loc32 filled and pl->geo (x0,
-// side, invalid flag, 2^30/side, largest leaf) on the device; the host values
-// pl->x0 / side are set by tree_finish after the caller's single sync.
+// side, invalid flag, 2^30/side, largest leaf) on the device, and a copy of
+// geo in the plan's pinned host buffer followed by the event ev_geo; the host
+// values pl->x0 / side are set by tree_finish once that event has completed.
 //
 // Order: keys and leaf counts -> leaf offsets (scan) -> points bucketed by leaf
 // -> each bucket sorted by (key, index).  The result is the stable order by
-// (key, index) over all points.  This path is launched without waiting for
-// the host; tree_finish checks afterwards that no leaf exceeded kLeafSort
-// points and otherwise redoes the sort with the full LSD radix sort of
-// (key, index).
+// (key, index) over all points.  Nothing waits for the host: leaves of any
+// size are sorted on the device.
 namespace {
 struct TreeTmp {
   char *base = nullptr;
@@ -583,29 +628,6 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
   return HPFMM_OK;
 }
 
-static void radix_path(hpfmm_plan *pl, TreeTmp &t, const double *x, const double *y,
-                       cudaStream_t st) {
-  const int64_t n = pl->n;
-  // keys again into kb / va (the bucket path consumed them)
-  unsigned gb = (unsigned)((n + 255) / 256);
-  morton_keys<<<gb, 256, 0, st>>>(x, y, n, pl->geo, pl->H, t.kb, t.va, nullptr, nullptr);
-  uint64_t *kin = t.kb, *kout = pl->keys;
-  int *vin = t.va, *vout = t.vb;
-  for (int shift = 0; shift < 60; shift += 8) {
-    radix_hist<<<t.nblocks, kSortThreads, 0, st>>>(kin, n, shift, t.nblocks, t.counts);
-    radix_scan_digit<<<256, 256, 0, st>>>(t.counts, t.nblocks, t.totals);
-    radix_scatter<<<t.nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, t.nblocks, t.counts,
-                                                       t.totals, kout, vout);
-    uint64_t *tk = kin; kin = kout; kout = tk;
-    int *tv = vin; vin = vout; vout = tv;
-  }
-  // 8 passes: the result is back in kb / va
-  cudaMemcpyAsync(pl->keys, t.kb, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
-  gather_points<<<gb, 256, 0, st>>>(x, y, t.va, pl->keys, n, pl->H, pl->geo, pl->xs, pl->ys,
-                                    pl->perm, pl->loc32);
-  pass_end(pl, st, PASS_TREE, 2 + 3 * 8);
-}
-
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
   const int64_t n = pl->n;
   const int H = pl->H, nleaf = pl->nleaf;
@@ -620,8 +642,10 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   pass_begin(pl, st, PASS_TREE);
   bbox_partial<<<t.nbR, kRedThreads, 0, st>>>(x, y, n, t.part);
   bbox_final<<<1, kRedThreads, 0, st>>>(t.part, t.nbR, geo, pl->root_x0, pl->root_side);
+  // the geometry, for the host and for the table stream, is known from here on
   cudaError_t e = cudaSuccess;
-  if (pl->ev_geo) e = cudaEventRecord(pl->ev_geo, st);  // the geometry is known from here on
+  if (pl->hgeo) e = cudaMemcpyAsync(pl->hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && pl->ev_geo) e = cudaEventRecord(pl->ev_geo, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
   morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, t.kb, t.va, t.lcount, t.slot);
   scan_part<<<nsb, 1024, 0, st>>>(t.lcount, nleaf, pl->leaf_start, t.btot, t.bmax);
@@ -635,7 +659,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
                                    pl->loc32);
   pass_end(pl, st, PASS_TREE, 10);
   if (e == cudaSuccess) e = cudaGetLastError();
-  // keep the temporaries until tree_finish has decided on the fallback
+  // released (stream-ordered) by tree_finish
   pl->tree_tmp = t.base;
   if (e != cudaSuccess) {
     set_last_error("tree_build launch: %s", cudaGetErrorString(e));
@@ -644,10 +668,10 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   return HPFMM_OK;
 }
 
-// After the caller's sync: host geometry, invalid-input check, large-leaf
-// fallback (radix sort), release of the temporaries.
-hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const double *hgeo,
-                         cudaStream_t st) {
+// Once the geometry has reached the host (hgeo): invalid-input check, host
+// copies of the root square, stream-ordered release of the temporaries.  Leaves
+// of any size are sorted on the device, so nothing here waits for the sort.
+hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st) {
   hpfmm_status s = HPFMM_OK;
   if (hgeo[2] != 0.0) {
     set_last_error(hgeo[2] == 2.0 ? "the root square does not contain the points"
@@ -656,17 +680,6 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *x, const double *y, const
   } else {
     pl->x0 = hgeo[0];
     pl->side = hgeo[1];
-    int hmax = 0;
-    memcpy(&hmax, &hgeo[4], sizeof(int));
-    if (hmax > kLeafSort) {
-      TreeTmp t;
-      s = tree_alloc(pl, t, st);
-      if (s == HPFMM_OK) {
-        pass_begin(pl, st, PASS_TREE);
-        radix_path(pl, t, x, y, st);
-        cudaFreeAsync(t.base, st);
-      }
-    }
   }
   if (pl->tree_tmp) cudaFreeAsync(pl->tree_tmp, st);
   pl->tree_tmp = nullptr;

@@ -36,3 +36,40 @@ def test_clustered_order_bit_exact():
                            kappa=1.0, p=4, leaf_size=64)
     keys, perm = hp.hpfmm_get_order(plan)
     assert np.array_equal(keys, keys_ref) and np.array_equal(perm, perm_ref)
+
+
+@pytest.mark.parametrize("n,levels,seed", [(40_000, 2, 3), (300_000, 3, 4), (5000, 1, 5)])
+def test_large_leaves_sorted_on_device(n, levels, seed):
+    """Leaves of thousands of points (beyond the shared-memory sort) are
+    sorted on the device by the global-memory bitonic network: the order still
+    equals the oracle's, ties included, and an update keeps it."""
+    x, y, _ = workloads.uniform(n, seed=seed)
+    x[100:400] = x[3]; y[100:400] = y[3]  # equal keys in one large leaf
+    keys_ref, perm_ref, _, _ = oracle.morton_order(x, y)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(a, device=dev)
+    plan = hp.hpfmm_create(t(x), t(y), kappa=1.0, p=4, levels=levels)
+    keys, perm = hp.hpfmm_get_order(plan)
+    assert np.array_equal(keys, keys_ref) and np.array_equal(perm, perm_ref)
+    x2, y2, _ = workloads.uniform(n, seed=seed + 10)
+    hp.hpfmm_update_points(plan, t(x2), t(y2))
+    keys_ref2, perm_ref2, _, _ = oracle.morton_order(x2, y2)
+    keys, perm = hp.hpfmm_get_order(plan)
+    assert np.array_equal(keys, keys_ref2) and np.array_equal(perm, perm_ref2)
+
+
+def test_update_points_reports_invalid_points():
+    x, y, _ = workloads.uniform(1000, seed=6)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(a, device=dev)
+    plan = hp.hpfmm_create(t(x), t(y), p=6)
+    y_bad = y.copy(); y_bad[17] = -0.5
+    with pytest.raises(hp.HpfmmError):
+        hp.hpfmm_update_points(plan, t(x), t(y_bad))
+    x_bad = x.copy(); x_bad[3] = np.nan
+    with pytest.raises(hp.HpfmmError):
+        hp.hpfmm_update_points(plan, t(x_bad), t(y))
+    hp.hpfmm_update_points(plan, t(x), t(y))  # a valid update restores the plan
+    keys, perm = hp.hpfmm_get_order(plan)
+    keys_ref, perm_ref, _, _ = oracle.morton_order(x, y)
+    assert np.array_equal(perm, perm_ref)
