@@ -366,9 +366,14 @@ k_l2l_coarse(int l0, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict_
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
-           cpx<R> *__restrict__ B, RhsStride rs) {
+           cpx<R> *__restrict__ B, RhsStride rs, const int *__restrict__ leaf_start,
+           int skip_empty) {
   extern __shared__ unsigned char smem_raw[];
   const int P1 = p + 1;
+  if (skip_empty) {  // a subtree without points needs no leaf expansions
+    const int64_t lf0 = (int64_t)blockIdx.x << (2 * k);
+    if (leaf_start[lf0 + (int64_t(1) << (2 * k))] == leaf_start[lf0]) return;
+  }
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
@@ -531,7 +536,7 @@ __global__ void __launch_bounds__(128)
 k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
                  const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
                  cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status,
-                 RhsStride rs) {
+                 RhsStride rs, const int *__restrict__ leaf_start, int skip_empty) {
   M += blockIdx.y * rs.m;
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
@@ -549,6 +554,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ R fac_in[P1], fac_out[P1];                    // 1/k!, (-1)^{l+1}/l!
+  __shared__ unsigned char sempty[kPatchSrc * kPatchSrc];  // source box holds no point
   cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][2][GP]
   cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [20][20][PP]
   R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * PP);  // [40] ln|t d|
@@ -589,6 +595,14 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
     const int col = (colp < HALF) ? 2 * colp : 2 * (colp - HALF) + 1;
     const int sx = sx0 + col, sy = sy0 + row;
     cpx<R> *dst = Mp + (size_t)sb * PP;
+    bool empty = true;
+    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
+      // points of the box: its leaves are contiguous in Morton order
+      const uint64_t mb = box_morton(sx, sy);
+      const int sh = 2 * (H - l);
+      empty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
+    }
+    sempty[sb] = empty ? 1 : 0;
     if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
       const cpx<R> *src = M + (size_t)(off + box_morton(sx, sy)) * P1;
       cpx<R> v[P1];
@@ -622,15 +636,35 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
     accA[r] = mk<R>(0, 0);
     accB[r] = mk<R>(0, 0);
   }
-  for (int dy = -2 - bb; dy <= 3 - bb; ++dy) {
+  // boxes holding no point need no local expansion (nothing is evaluated in
+  // them or below them); a warp whose targets are all empty skips the
+  // translations, and so does a warp whose sources of a class are all empty
+  // (their moments are zero).  Not for evaluation at separate targets, which
+  // may lie in empty boxes.
+  bool tempty = true;
+  if (skip_empty) {
+    const int sh = 2 * (H - l);
+    if (vA) {
+      const uint64_t mb = box_morton(txA, tyA);
+      tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
+    }
+    if (vB && tempty) {
+      const uint64_t mb = box_morton(txB, tyB);
+      tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
+    }
+  }
+  const bool skip_warp = skip_empty && __all_sync(0xffffffffu, tempty);
+  for (int dy = -2 - bb; dy <= 3 - bb && !skip_warp; ++dy) {
     for (int dx = -2 - a; dx <= 3 - a; ++dx) {
       if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
       const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
       const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
       const int colA = txA + dx - sx0, colB = txB + dx - sx0;  // same parity
       const int cpA = (colA & 1) * HALF + (colA >> 1), cpB = (colB & 1) * HALF + (colB >> 1);
-      const cpx<R> *mA = Mp + ((tyA + dy - sy0) * kPatchSrc + cpA) * PP;
-      const cpx<R> *mB = Mp + ((tyB + dy - sy0) * kPatchSrc + cpB) * PP;
+      const int sbA = (tyA + dy - sy0) * kPatchSrc + cpA, sbB = (tyB + dy - sy0) * kPatchSrc + cpB;
+      if (skip_empty && __all_sync(0xffffffffu, sempty[sbA] && sempty[sbB])) continue;
+      const cpx<R> *mA = Mp + sbA * PP;
+      const cpx<R> *mB = Mp + sbB * PP;
 #pragma unroll 1
       for (int k = 0; k < PP; k += 2) {
         const cpx<R> ma0 = mA[k], ma1 = mA[k + 1], mb0 = mB[k], mb1 = mB[k + 1];
@@ -693,7 +727,7 @@ int patch_blocks(int H) {
 template <typename R>
 bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, const cd *logt,
                       const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st,
-                      int nr, RhsStride rs) {
+                      int nr, RhsStride rs, const int *leaf_start, int skip_empty) {
   if (!Tpad) return false;
   int nb = patch_blocks(H);
   // the shared-memory attribute is set once per device and order (so that a
@@ -718,8 +752,8 @@ bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, co
       }                                                                                   \
       if (attr[dev][pr][p] < 0) return false;                                             \
     }                                                                                     \
-    k_m2l_free_patch<R, PP + 1><<<dim3(nb, nr), 128, sm, st>>>(H, lgm, Tpad, logt, M, A, B,  \
-                                                               status, rs);                \
+    k_m2l_free_patch<R, PP + 1><<<dim3(nb, nr), 128, sm, st>>>(                           \
+        H, lgm, Tpad, logt, M, A, B, status, rs, leaf_start, skip_empty);                    \
     return true;                                                                          \
   }
   switch (p) {
@@ -1878,7 +1912,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
                               (cf *)B, pl->status, st, nr, rs);
     if (!patched)
       patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
-                                    pl->status, st, nr, rs);
+                                    pl->status, st, nr, rs, pl->leaf_start, tw ? 0 : 1);
     pass_end(pl, st, PASS_M2L_FREE, patched ? (tc_m2l ? H - 1 : 1) : 0);
   }
   if (mw && !patched) {
@@ -1907,7 +1941,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (l0 >= 2) k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(l0, p, Tl2l, A, B, rs);
   if (ksub > 0)
     k_downward<R><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256, downward_smem<R>(p, ksub),
-                    st>>>(H, ksub, p, Tl2l, A, B, rs);
+                    st>>>(H, ksub, p, Tl2l, A, B, rs, pl->leaf_start, tw ? 0 : 1);
   pass_end(pl, st, PASS_L2L, (l0 >= 2 ? 1 : 0) + (ksub > 0 ? 1 : 0));
   pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field

@@ -166,3 +166,21 @@ def test_clustered_4m_mixed_complex_kappa():
     assert rel(g[idx], g_ref) < 2e-5
     m = y[idx] < 0.06  # the near-boundary half on its own
     assert rel(u[idx][m], u_ref[m]) < 5e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 5e-6), ("fp64", 1e-9)])
+def test_mostly_empty_tree(prec, tol):
+    """N = 2000 on a level-7 tree (16384 leaves, most of them empty): boxes
+    without points skip their translations, which must not change any result;
+    then the same plan evaluates at separate targets, including points in
+    empty leaves, where every box needs its local expansion."""
+    x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
+    u, g, plan = run(x, y, q, 1.0, 20, 32, prec=prec, levels=7)
+    assert rel(u, u_ref) < tol
+    assert rel(g, g_ref) < 20 * tol
+    gx, gy = np.meshgrid(np.linspace(0.01, 0.99, 20), np.linspace(0.0, 0.99, 20))
+    xt, yt = gx.ravel(), gy.ravel()
+    ut_ref, _ = oracle.direct(x, y, q, xt=xt, yt=yt, kappa=1.0, grad=False)
+    t = lambda a: torch.tensor(a, device=DEV)
+    ut, _ = hp.hpfmm_eval_targets(plan, t(q), t(xt), t(yt), grad=False)
+    assert rel(ut.cpu().numpy(), ut_ref) < tol
