@@ -173,19 +173,24 @@ __device__ __forceinline__ cpx<R> cpow_int(cpx<R> w, int n) {
   return r;
 }
 
+constexpr int kS2mGroup = 4;  // orders per thread of the single-precision S2M
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
              int H, double x0, double side, R invd_leaf, int p, cpx<R> *__restrict__ M,
              RhsStride rs) {
-  const int P1 = p + 1;
+  // one thread per leaf and group of kS2mGroup consecutive orders n0 .. n0+3:
+  // w^n0 = (w^4)^(n0/4) from two squarings, then one product per further n
+  constexpr int G = kS2mGroup;
+  const int P1 = p + 1, NB = (P1 + G - 1) / G;
   qs += blockIdx.y * rs.q;
   M += blockIdx.y * rs.m;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < 4^12 * 41 < 2^32
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < 4^12 * 11 < 2^32
   const unsigned nleaf = 1u << (2 * H);
-  if (t >= nleaf * (unsigned)P1) return;
-  const unsigned leaf = t / (unsigned)P1;
-  const int n = (int)(t - leaf * (unsigned)P1);
+  if (t >= nleaf * (unsigned)NB) return;
+  const unsigned leaf = t / (unsigned)NB;
+  const int nb = (int)(t - leaf * (unsigned)NB), n0 = G * nb;
   // (the single-precision points are already relative to the leaf centre)
   const double cx = 0.0, cy = 0.0;
   const R invd = invd_leaf;
@@ -195,17 +200,29 @@ k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict_
   // compensated (Kahan) summation: the moments of a leaf are sums of up to
   // hundreds of terms of both signs, and their rounding error is inherited
   // by every far-field coefficient built from them
-  cpx<R> acc = mk<R>(0, 0), cmp = mk<R>(0, 0);
+  cpx<R> acc[G], cmp[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) acc[g] = cmp[g] = mk<R>(0, 0);
   for (int j = b0; j < b1; ++j) {
     R rx, ry;
     pts.rel(j, cx, cy, rx, ry);
-    const cpx<R> term = qs[j] * cpow_int(mk<R>(rx * invd, ry * invd), n);
-    const cpx<R> yv = term - cmp;
-    const cpx<R> tv = acc + yv;
-    cmp = (tv - acc) - yv;
-    acc = tv;
+    const cpx<R> w = mk<R>(rx * invd, ry * invd);
+    const cpx<R> w2 = w * w, w4 = w2 * w2;
+    cpx<R> wn = mk<R>(qs[j], 0);
+    for (int i = 0; i < nb; ++i) wn = wn * w4;  // q w^n0
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const cpx<R> yv = wn - cmp[g];
+      const cpx<R> tv = acc[g] + yv;
+      cmp[g] = (tv - acc[g]) - yv;
+      acc[g] = tv;
+      wn = wn * w;
+    }
   }
-  M[(size_t)(level_offset(H)) * P1 + t] = acc;
+  const size_t e0 = ((size_t)level_offset(H) + leaf) * P1;
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    if (n0 + g < P1) M[e0 + n0 + g] = acc[g];
 }
 
 // Multi-RHS S2M (single precision): the powers ((z_j - z_c)/d)^n of a point
@@ -1879,7 +1896,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
                                256, 0, st>>>(pl->loc32, (const float *)mw->qsm, mw->rp, nr,
                                              pl->leaf_start, H, lg.invd[H], p, (cf *)M, rs);
     else
-      k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * P1, 256), 256, 0, st>>>(
+      k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * ((P1 + kS2mGroup - 1) / kS2mGroup), 256),
+                            256, 0, st>>>(
           lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, lg.invd[H], p, (cf *)M, rs);
   }
   pass_end(pl, st, PASS_P2M, 1);

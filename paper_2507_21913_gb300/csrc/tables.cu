@@ -176,10 +176,15 @@ __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd 
 // parity of j.  Computed in double and rounded.
 __global__ void k_m2l_pad(int p, cf *out) {
   const int P1 = p + 1, GP = 2 * P1;
-  int slot = 0;
-  for (int c = 0; c < 49; ++c) {
+  const int slot = blockIdx.x;  // one block per far class
+  int c = 0, k40 = -1;
+  for (; c < 49; ++c) {
     const int dx = c % 7 - 3, dy = c / 7 - 3;
     if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+    if (++k40 == slot) break;
+  }
+  {
+    const int dx = c % 7 - 3, dy = c / 7 - 3;
     const cd t = mk(-(double)dx, -(double)dy);
     const cd ti = cinv(t);
     for (int e = threadIdx.x; e < 2 * GP; e += blockDim.x) {
@@ -194,7 +199,6 @@ __global__ void k_m2l_pad(int p, cf *out) {
       }
       out[(size_t)slot * 2 * GP + e] = to<float>(g);
     }
-    ++slot;
   }
 }
 
@@ -258,7 +262,7 @@ hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
                                                {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2}};
     for (auto &e : t)
       k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
-    if (pl->t_m2l_pad) k_m2l_pad<<<1, 256, 0, st>>>(p, (cf *)pl->t_m2l_pad);
+    if (pl->t_m2l_pad) k_m2l_pad<<<40, 64, 0, st>>>(p, (cf *)pl->t_m2l_pad);
     if (pl->t_m2l_tc) k_m2l_tc_table<<<40, 256, 0, st>>>(p, fm2l, (float *)pl->t_m2l_tc);
     HP_LAUNCH_CHECK();
   }
