@@ -23,21 +23,9 @@ struct Geom {
 
 constexpr int kRedThreads = 256;
 
-// unit in the last place of a positive finite double (its exponent's ulp)
-__device__ __forceinline__ double ulp_of(double s) {
-  s = fabs(s);
-  long long b = __double_as_longlong(s);
-  long long e = (b >> 52) & 0x7ff;
-  if (e <= 52) return 4.9406564584124654e-324 * 2;  // tiny: any positive bound works
-  return __longlong_as_double((e - 52) << 52);
-}
-
-// order-preserving integer image of a finite double (a < b <=> key(a) < key(b)),
-// so the min / max reductions run on the integer pipe
-__device__ __forceinline__ long long dkey(double v) {
-  const long long b = __double_as_longlong(v);
-  return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
-}
+// order-preserving integer image of a finite double (a < b <=> key(a) < key(b),
+// key = b >= 0 ? b : b ^ 0x7ff..f), so the min / max reductions run on the
+// integer pipe; dkey_inv maps a key back to its double
 __device__ __forceinline__ double dkey_inv(long long k) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffll));
 }
@@ -302,9 +290,35 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&k)[E], int (&v)[E], int 
   }
 }
 
+// Points of a sorted leaf into tree order: the permutation, the leaf-centred
+// single-precision coordinates and (double precision) the sorted coordinates.
+// Done by the warp or block that sorted the leaf, from the sorted indices it
+// holds.  x == nullptr: order only (no gather).
+struct LeafGather {
+  const double *x, *y, *geo;
+  int H;
+  double *xs, *ys;
+  int64_t *perm;
+  float2 *loc32;
+};
+
+__device__ __forceinline__ void gather_one(const LeafGather &g, int leaf, int k, int j) {
+  const double a = g.x[j], b = g.y[j];
+  if (g.xs) {
+    g.xs[k] = a;
+    g.ys[k] = b;
+  }
+  g.perm[k] = j;
+  if (g.loc32) {
+    const double d = ldexp(g.geo[1], -g.H);  // exact
+    const double cx = g.geo[0] + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
+    g.loc32[k] = make_float2((float)(a - cx), (float)(b - cy));
+  }
+}
+
 template <int E>
 __device__ __forceinline__ void warp_sort_leaf(int b0, int m, int lane, uint64_t *keys,
-                                               int *vals) {
+                                               int *vals, const LeafGather &g, int leaf) {
   uint64_t k[E];
   int v[E];
 #pragma unroll
@@ -320,13 +334,15 @@ __device__ __forceinline__ void warp_sort_leaf(int b0, int m, int lane, uint64_t
     if (i < m) {
       keys[b0 + i] = k[e];
       vals[b0 + i] = v[e];
+      if (g.x) gather_one(g, leaf, b0 + i, v[e]);
     }
   }
 }
 
 __global__ void __launch_bounds__(256)
 leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
-               int *__restrict__ vals, int *__restrict__ big, int *__restrict__ nbig) {
+               int *__restrict__ vals, int *__restrict__ big, int *__restrict__ nbig,
+               LeafGather g) {
   const int lane = threadIdx.x & 31;
   const int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (leaf >= nleaf) return;
@@ -335,10 +351,14 @@ leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ 
     if (lane == 0 && big) big[atomicAdd(nbig, 1)] = leaf;
     return;
   }
-  if (m <= 1) return;
-  if (m <= 32) warp_sort_leaf<1>(b0, m, lane, keys, vals);
-  else if (m <= 64) warp_sort_leaf<2>(b0, m, lane, keys, vals);
-  else warp_sort_leaf<4>(b0, m, lane, keys, vals);
+  if (m == 0) return;
+  if (m == 1) {
+    if (lane == 0 && g.x) gather_one(g, leaf, b0, vals[b0]);
+    return;
+  }
+  if (m <= 32) warp_sort_leaf<1>(b0, m, lane, keys, vals, g, leaf);
+  else if (m <= 64) warp_sort_leaf<2>(b0, m, lane, keys, vals, g, leaf);
+  else warp_sort_leaf<4>(b0, m, lane, keys, vals, g, leaf);
 }
 
 // sort the leaf buckets of more than 128 points, one block per leaf (blocks
@@ -387,7 +407,7 @@ __device__ void sort_leaf_global(uint64_t *__restrict__ keys, int *__restrict__ 
 }
 __global__ void __launch_bounds__(256)
 leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int *__restrict__ nbig,
-          uint64_t *__restrict__ keys, int *__restrict__ vals) {
+          uint64_t *__restrict__ keys, int *__restrict__ vals, LeafGather g) {
   __shared__ uint64_t sk[kLeafSort];
   __shared__ int sv[kLeafSort];
   const int nb = *nbig;
@@ -398,6 +418,8 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
     if (m > kLeafSort) {
       __syncthreads();
       sort_leaf_global(keys + b0, vals + b0, m);
+      if (g.x)
+        for (int e = threadIdx.x; e < m; e += blockDim.x) gather_one(g, leaf, b0 + e, vals[b0 + e]);
       continue;
     }
     int np2 = 1;
@@ -429,6 +451,7 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
     for (int e = threadIdx.x; e < m; e += blockDim.x) {
       keys[b0 + e] = sk[e];
       vals[b0 + e] = sv[e];
+      if (g.x) gather_one(g, leaf, b0 + e, sv[e]);
     }
   }
 }
@@ -537,42 +560,7 @@ radix_scatter(const uint64_t *__restrict__ kin, const int *__restrict__ vin, int
   }
 }
 
-// leaf_start[b] = first sorted position whose level-H box index is >= b
-__global__ void leaf_offsets(const uint64_t *__restrict__ keys, int64_t n, int H, int nleaf,
-                             int *__restrict__ start) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b > nleaf) return;
-  int shift = 60 - 2 * H;
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)(keys[mid] >> shift) < b) lo = mid + 1;
-    else hi = mid;
-  }
-  start[b] = (int)lo;
-}
 
-__global__ void gather_points(const double *__restrict__ x, const double *__restrict__ y,
-                              const int *__restrict__ idx, const uint64_t *__restrict__ keys,
-                              int64_t n, int H, const double *__restrict__ geo,
-                              double *__restrict__ xs, double *__restrict__ ys,
-                              int64_t *__restrict__ perm, float2 *__restrict__ loc32) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  int j = idx[k];
-  double a = x[j], b = y[j];
-  if (xs) {
-    xs[k] = a;
-    ys[k] = b;
-  }
-  perm[k] = j;
-  if (loc32) {
-    uint64_t leaf = keys[k] >> (60 - 2 * H);
-    double d = ldexp(geo[1], -H);  // exact
-    double cx = geo[0] + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
-    loc32[k] = make_float2((float)(a - cx), (float)(b - cy));
-  }
-}
 
 }  // namespace
 
@@ -652,12 +640,12 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   scan_top<<<1, 1024, 0, st>>>(t.btot, t.bmax, nsb, nleaf, pl->leaf_start, maxleaf);
   scan_add<<<nsb, 1024, 0, st>>>(t.btot, nleaf, pl->leaf_start);
   bucket_scatter<<<gb, tb, 0, st>>>(t.kb, t.slot, n, H, pl->leaf_start, pl->keys, t.vb);
+  // the leaf sorts also put the points into tree order (permutation, coordinates)
+  const LeafGather lg{x, y, geo, H, pl->xs, pl->ys, pl->perm, pl->loc32};
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
-      pl->leaf_start, nleaf, pl->keys, t.vb, t.big, t.lcount + nleaf);
-  leaf_sort<<<160, 256, 0, st>>>(pl->leaf_start, t.big, t.lcount + nleaf, pl->keys, t.vb);
-  gather_points<<<gb, tb, 0, st>>>(x, y, t.vb, pl->keys, n, H, geo, pl->xs, pl->ys, pl->perm,
-                                   pl->loc32);
-  pass_end(pl, st, PASS_TREE, 10);
+      pl->leaf_start, nleaf, pl->keys, t.vb, t.big, t.lcount + nleaf, lg);
+  leaf_sort<<<160, 256, 0, st>>>(pl->leaf_start, t.big, t.lcount + nleaf, pl->keys, t.vb, lg);
+  pass_end(pl, st, PASS_TREE, 9);
   if (e == cudaSuccess) e = cudaGetLastError();
   // released (stream-ordered) by tree_finish
   pl->tree_tmp = t.base;
@@ -786,9 +774,10 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
   scan_top<<<1, 1024, 0, st>>>(btot, bmax, nsb, nleaf, lstart, (int *)(geo + 4));
   scan_add<<<nsb, 1024, 0, st>>>(btot, nleaf, lstart);
   bucket_scatter<<<gb, 256, 0, st>>>(kb, slot, n, H, lstart, keys, vb);
+  const LeafGather none{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr};
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
-      lstart, nleaf, keys, vb, big, lcount + nleaf);
-  leaf_sort<<<160, 256, 0, st>>>(lstart, big, lcount + nleaf, keys, vb);
+      lstart, nleaf, keys, vb, big, lcount + nleaf, none);
+  leaf_sort<<<160, 256, 0, st>>>(lstart, big, lcount + nleaf, keys, vb, none);
   HP_LAUNCH_CHECK();
   double hgeo[5];
   HP_CUDA(cudaMemcpyAsync(hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
