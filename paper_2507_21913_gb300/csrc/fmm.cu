@@ -327,54 +327,89 @@ k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ le
   }
 }
 
-// M2M for the coarse levels l0 - 1 .. 1, one block, level by level
+// coarse levels with at least 4^kCoarseBig boxes get a multi-block launch each
+constexpr int kCoarseBig = 5;
+
+// M2M of output (box b, order n) of level l from its four children (Eq. metome)
+template <typename R>
+__device__ __forceinline__ void m2m_item(int l, int e, int P1, const cpx<R> *__restrict__ Tm2m,
+                                         cpx<R> *__restrict__ M) {
+  const int b = e / P1, n = e % P1;
+  const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * (int64_t)b) * P1;
+  cpx<R> acc = mk<R>(0, 0);
+  for (int c = 0; c < 4; ++c) {
+    const cpx<R> *Tc = Tm2m + (size_t)c * P1 * P1 + (size_t)n * P1;
+    for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], child[(size_t)c * P1 + m]);
+  }
+  M[(size_t)(level_offset(l) + b) * P1 + n] = acc;
+}
+
+// M2M for the small coarse levels lhi .. 1, one block, level by level
 template <typename R>
 __global__ void __launch_bounds__(1024)
-k_m2m_coarse(int l0, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M,
+k_m2m_coarse(int lhi, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M,
              RhsStride rs) {
   const int P1 = p + 1;
   M += blockIdx.y * rs.m;
-  for (int l = l0 - 1; l >= 1; --l) {
+  for (int l = lhi; l >= 1; --l) {
     const int nb = 1 << (2 * l);
-    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) {
-      const int b = e / P1, n = e % P1;
-      const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * b) * P1;
-      cpx<R> acc = mk<R>(0, 0);
-      for (int c = 0; c < 4; ++c) {
-        const cpx<R> *Tc = Tm2m + (size_t)c * P1 * P1 + (size_t)n * P1;
-        for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], child[(size_t)c * P1 + m]);
-      }
-      M[(size_t)(level_offset(l) + b) * P1 + n] = acc;
-    }
+    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) m2m_item<R>(l, e, P1, Tm2m, M);
     __syncthreads();
   }
 }
 
-// L2L (Eq. letole1) for the coarse levels 2 .. l0, one block, level by level
+// the same for one level with many boxes, one thread per (box, n) over many blocks
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_m2m_level(int l, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M, RhsStride rs) {
+  const int P1 = p + 1;
+  M += blockIdx.y * rs.m;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ((int64_t)1 << (2 * l)) * P1) m2m_item<R>(l, (int)e, P1, Tm2m, M);
+}
+
+// L2L (Eq. letole1) of coefficient (box b, order m) of level l from its parent
+template <typename R>
+__device__ __forceinline__ void l2l_item(int l, int e, int P1, const cpx<R> *__restrict__ Tl2l,
+                                         cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
+  const int b = e / P1, m = e % P1, c = b & 3;
+  const size_t pe = (size_t)(level_offset(l - 1) + (b >> 2)) * P1;
+  const size_t ce = (size_t)(level_offset(l) + b) * P1;
+  const cpx<R> *Tc = Tl2l + (size_t)c * P1 * P1 + (size_t)m * P1;
+  cpx<R> sa = A[ce + m], sb = B[ce + m];
+  for (int n = m; n < P1; ++n) {
+    cfma(sa, Tc[n], A[pe + n]);
+    cfma(sb, conj(Tc[n]), B[pe + n]);
+  }
+  A[ce + m] = sa;
+  B[ce + m] = sb;
+}
+
+// L2L for the small coarse levels 2 .. lhi, one block, level by level
 template <typename R>
 __global__ void __launch_bounds__(1024)
-k_l2l_coarse(int l0, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
+k_l2l_coarse(int lhi, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
              cpx<R> *__restrict__ B, RhsStride rs) {
   const int P1 = p + 1;
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
-  for (int l = 2; l <= l0; ++l) {
+  for (int l = 2; l <= lhi; ++l) {
     const int nb = 1 << (2 * l);
-    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) {
-      const int b = e / P1, m = e % P1, c = b & 3;
-      const size_t pe = (size_t)(level_offset(l - 1) + (b >> 2)) * P1;
-      const size_t ce = (size_t)(level_offset(l) + b) * P1;
-      const cpx<R> *Tc = Tl2l + (size_t)c * P1 * P1 + (size_t)m * P1;
-      cpx<R> sa = A[ce + m], sb = B[ce + m];
-      for (int n = m; n < P1; ++n) {
-        cfma(sa, Tc[n], A[pe + n]);
-        cfma(sb, conj(Tc[n]), B[pe + n]);
-      }
-      A[ce + m] = sa;
-      B[ce + m] = sb;
-    }
+    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) l2l_item<R>(l, e, P1, Tl2l, A, B);
     __syncthreads();
   }
+}
+
+// the same for one level with many boxes, one thread per (box, m) over many blocks
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_l2l_level(int l, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
+            cpx<R> *__restrict__ B, RhsStride rs) {
+  const int P1 = p + 1;
+  A += blockIdx.y * rs.m;
+  B += blockIdx.y * rs.m;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ((int64_t)1 << (2 * l)) * P1) l2l_item<R>(l, (int)e, P1, Tl2l, A, B);
 }
 
 // Fused downward pass below l0: one block per level-l0 box pushes its local
@@ -1917,8 +1952,18 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     }
   }
 
-  if (l0 > 1) k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(l0, p, Tm2m, M, rs);
-  pass_end(pl, st, PASS_M2M, (ksub > 0 ? 1 : 0) + (l0 > 1 ? 1 : 0));
+  // coarse levels l0 - 1 .. 1: levels of 1024 boxes and more one launch each,
+  // the small top levels in one block
+  int nm2m = ksub > 0 ? 1 : 0;
+  for (int l = l0 - 1; l >= kCoarseBig; --l, ++nm2m)
+    k_m2m_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, st>>>(
+        l, p, Tm2m, M, rs);
+  const int lsmall = l0 - 1 < kCoarseBig - 1 ? l0 - 1 : kCoarseBig - 1;
+  if (lsmall >= 1) {
+    k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(lsmall, p, Tm2m, M, rs);
+    ++nm2m;
+  }
+  pass_end(pl, st, PASS_M2M, nm2m);
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
@@ -1956,11 +2001,21 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   }
   pass_end(pl, st, PASS_M2L_MIRROR, 1);
   pass_begin(pl, st, PASS_L2L);
-  if (l0 >= 2) k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(l0, p, Tl2l, A, B, rs);
+  int nl2l = 0;
+  {
+    const int lsmall2 = l0 < kCoarseBig - 1 ? l0 : kCoarseBig - 1;
+    if (lsmall2 >= 2) {
+      k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(lsmall2, p, Tl2l, A, B, rs);
+      ++nl2l;
+    }
+    for (int l = kCoarseBig; l <= l0; ++l, ++nl2l)
+      k_l2l_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, st>>>(
+          l, p, Tl2l, A, B, rs);
+  }
   if (ksub > 0)
     k_downward<R><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256, downward_smem<R>(p, ksub),
                     st>>>(H, ksub, p, Tl2l, A, B, rs, pl->leaf_start, tw ? 0 : 1);
-  pass_end(pl, st, PASS_L2L, (l0 >= 2 ? 1 : 0) + (ksub > 0 ? 1 : 0));
+  pass_end(pl, st, PASS_L2L, nl2l + (ksub > 0 ? 1 : 0));
   pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
   cd kappa = mk(pl->kre, pl->kim);

@@ -184,3 +184,17 @@ def test_mostly_empty_tree(prec, tol):
     t = lambda a: torch.tensor(a, device=DEV)
     ut, _ = hp.hpfmm_eval_targets(plan, t(q), t(xt), t(yt), grad=False)
     assert rel(ut.cpu().numpy(), ut_ref) < tol
+
+
+@pytest.mark.parametrize("prec,p,tol", [("fp64", 16, 1e-8), ("fp32", 12, 5e-6)])
+def test_deep_tree_coarse_levels(prec, p, tol):
+    """A level-10 tree: the coarse upward and downward levels with 1024 boxes
+    and more run as one multi-block launch per level, the top levels in one
+    block; N = 30000 uniform, 32 sampled targets against the oracle."""
+    n = 30_000
+    x, y, q = workloads.uniform(n, seed=21)
+    idx = workloads.sample_targets(n, 32, seed=1)
+    u_ref, g_ref = oracle_cache.sampled_closed(x, y, q, idx, 1.0)
+    u, g, plan = run(x, y, q, 1.0, p, 32, prec=prec, levels=10)
+    assert rel(u[idx], u_ref) < tol
+    assert rel(g[idx], g_ref) < 20 * tol
