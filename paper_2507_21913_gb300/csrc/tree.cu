@@ -302,18 +302,30 @@ struct LeafGather {
   float2 *loc32;
 };
 
-__device__ __forceinline__ void gather_one(const LeafGather &g, int leaf, int k, int j) {
+// centre of a leaf (double precision; the leaf side d = side / 2^H is exact)
+__device__ __forceinline__ double2 leaf_centre(const LeafGather &g, int leaf) {
+  const double d = ldexp(g.geo[1], -g.H);
+  return make_double2(g.geo[0] + (box_ix(leaf) + 0.5) * d, (box_iy(leaf) + 0.5) * d);
+}
+
+__device__ __forceinline__ void gather_one(const LeafGather &g, double2 c, int k, int j) {
   const double a = g.x[j], b = g.y[j];
   if (g.xs) {
     g.xs[k] = a;
     g.ys[k] = b;
   }
   g.perm[k] = j;
-  if (g.loc32) {
-    const double d = ldexp(g.geo[1], -g.H);  // exact
-    const double cx = g.geo[0] + (box_ix(leaf) + 0.5) * d, cy = (box_iy(leaf) + 0.5) * d;
-    g.loc32[k] = make_float2((float)(a - cx), (float)(b - cy));
-  }
+  if (g.loc32) g.loc32[k] = make_float2((float)(a - c.x), (float)(b - c.y));
+}
+
+// a warp's leaf centre: computed by lane 0 and broadcast (the double-precision
+// pipe is slow; the other lanes would compute the same value)
+__device__ __forceinline__ double2 warp_leaf_centre(const LeafGather &g, int leaf, int lane) {
+  double2 c = make_double2(0.0, 0.0);
+  if (lane == 0 && g.loc32) c = leaf_centre(g, leaf);
+  c.x = __shfl_sync(0xffffffffu, c.x, 0);
+  c.y = __shfl_sync(0xffffffffu, c.y, 0);
+  return c;
 }
 
 template <int E>
@@ -328,13 +340,14 @@ __device__ __forceinline__ void warp_sort_leaf(int b0, int m, int lane, uint64_t
     v[e] = i < m ? vals[b0 + i] : 0x7fffffff;
   }
   warp_bitonic<E>(k, v, lane);
+  const double2 c = g.x ? warp_leaf_centre(g, leaf, lane) : make_double2(0.0, 0.0);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int i = e * 32 + lane;
     if (i < m) {
       keys[b0 + i] = k[e];
       vals[b0 + i] = v[e];
-      if (g.x) gather_one(g, leaf, b0 + i, v[e]);
+      if (g.x) gather_one(g, c, b0 + i, v[e]);
     }
   }
 }
@@ -353,7 +366,7 @@ leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ 
   }
   if (m == 0) return;
   if (m == 1) {
-    if (lane == 0 && g.x) gather_one(g, leaf, b0, vals[b0]);
+    if (lane == 0 && g.x) gather_one(g, g.loc32 ? leaf_centre(g, leaf) : make_double2(0, 0), b0, vals[b0]);
     return;
   }
   if (m <= 32) warp_sort_leaf<1>(b0, m, lane, keys, vals, g, leaf);
@@ -418,8 +431,10 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
     if (m > kLeafSort) {
       __syncthreads();
       sort_leaf_global(keys + b0, vals + b0, m);
-      if (g.x)
-        for (int e = threadIdx.x; e < m; e += blockDim.x) gather_one(g, leaf, b0 + e, vals[b0 + e]);
+      if (g.x) {
+        const double2 c = g.loc32 ? leaf_centre(g, leaf) : make_double2(0, 0);
+        for (int e = threadIdx.x; e < m; e += blockDim.x) gather_one(g, c, b0 + e, vals[b0 + e]);
+      }
       continue;
     }
     int np2 = 1;
@@ -448,10 +463,11 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
         __syncthreads();
       }
     }
+    const double2 c = (g.x && g.loc32) ? leaf_centre(g, leaf) : make_double2(0, 0);
     for (int e = threadIdx.x; e < m; e += blockDim.x) {
       keys[b0 + e] = sk[e];
       vals[b0 + e] = sv[e];
-      if (g.x) gather_one(g, leaf, b0 + e, sv[e]);
+      if (g.x) gather_one(g, c, b0 + e, sv[e]);
     }
   }
 }
