@@ -579,8 +579,10 @@ k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
 // the 27 offsets of child type w to its 64 targets (two per lane): the matrix
 // entry T[l][k] is a broadcast read shared by the warp, the source moment a
 // per-lane read.  All levels 2..H are processed by one launch.
-constexpr int kPatch = 8;                 // parents per side
-constexpr int kPatchSrc = 2 * kPatch + 4; // source boxes per side
+constexpr int kPatch = 8;                  // parents per block in x
+constexpr int kPatchRows = 4;              // parents per block in y
+constexpr int kPatchSrc = 2 * kPatch + 4;  // source boxes per block in x
+constexpr int kSrcRows = 2 * kPatchRows + 4;  // source boxes per block in y
 __constant__ signed char c_slot[49];      // 7x7 offset class -> 0..39, -1 for the near 3x3
 
 template <typename R, int P1>
@@ -606,21 +608,21 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ R fac_in[P1], fac_out[P1];                    // 1/k!, (-1)^{l+1}/l!
-  __shared__ unsigned char sempty[kPatchSrc * kPatchSrc];  // source box holds no point
+  __shared__ unsigned char sempty[kPatchSrc * kSrcRows];  // source box holds no point
   cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][2][GP]
-  cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [20][20][PP]
-  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kPatchSrc * PP);  // [40] ln|t d|
-  // level and patch of this block
+  cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [12][20][PP]
+  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kSrcRows * PP);  // [40] ln|t d|
+  // level and patch of this block: kPatch x kPatchRows parents, whose four
+  // children of each type are the block's targets (one per thread)
   int b = blockIdx.x, l = 2;
   for (; l <= H; ++l) {
-    int np = (1 << (l - 1)) / kPatch;
-    np = np < 1 ? 1 : np;
-    if (b < np * np) break;
-    b -= np * np;
+    const int nps = 1 << (l - 1);
+    const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
+    if (b < npx * npy) break;
+    b -= npx * npy;
   }
-  int npl = (1 << (l - 1)) / kPatch;
-  npl = npl < 1 ? 1 : npl;
-  const int px0 = (b % npl) * kPatch, py0 = (b / npl) * kPatch;
+  const int npx = (1 << (l - 1)) / kPatch < 1 ? 1 : (1 << (l - 1)) / kPatch;
+  const int px0 = (b % npx) * kPatch, py0 = (b / npx) * kPatchRows;
   const int nparent_side = 1 << (l - 1), nside = 1 << l;
   const int64_t off = level_offset(l);
   const R logd = (R)lgm.logd[l];
@@ -642,7 +644,7 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   __syncthreads();
   // source patch: one box per thread and iteration, P1 independent loads each
   const int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
-  for (int sb = threadIdx.x; sb < kPatchSrc * kPatchSrc; sb += blockDim.x) {
+  for (int sb = threadIdx.x; sb < kPatchSrc * kSrcRows; sb += blockDim.x) {
     const int row = sb / kPatchSrc, colp = sb % kPatchSrc;  // colp: parity-split column
     const int col = (colp < HALF) ? 2 * colp : 2 * (colp - HALF) + 1;
     const int sx = sx0 + col, sy = sy0 + row;
@@ -678,32 +680,21 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = warp & 1, bb = warp >> 1;  // child type handled by this warp
   const int pxA = px0 + (lane & 7), pyA = py0 + (lane >> 3);
-  const int pxB = pxA, pyB = pyA + 4;
   const bool vA = pxA < nparent_side && pyA < nparent_side;
-  const bool vB = pxB < nparent_side && pyB < nparent_side;
-  const int txA = 2 * pxA + a, tyA = 2 * pyA + bb, txB = 2 * pxB + a, tyB = 2 * pyB + bb;
-  cpx<R> accA[P1], accB[P1];
+  const int txA = 2 * pxA + a, tyA = 2 * pyA + bb;
+  cpx<R> accA[P1];
 #pragma unroll
-  for (int r = 0; r < P1; ++r) {
-    accA[r] = mk<R>(0, 0);
-    accB[r] = mk<R>(0, 0);
-  }
+  for (int r = 0; r < P1; ++r) accA[r] = mk<R>(0, 0);
   // boxes holding no point need no local expansion (nothing is evaluated in
   // them or below them); a warp whose targets are all empty skips the
   // translations, and so does a warp whose sources of a class are all empty
   // (their moments are zero).  Not for evaluation at separate targets, which
   // may lie in empty boxes.
   bool tempty = true;
-  if (skip_empty) {
+  if (skip_empty && vA) {
     const int sh = 2 * (H - l);
-    if (vA) {
-      const uint64_t mb = box_morton(txA, tyA);
-      tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
-    }
-    if (vB && tempty) {
-      const uint64_t mb = box_morton(txB, tyB);
-      tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
-    }
+    const uint64_t mb = box_morton(txA, tyA);
+    tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
   }
   const bool skip_warp = skip_empty && __all_sync(0xffffffffu, tempty);
   for (int dy = -2 - bb; dy <= 3 - bb && !skip_warp; ++dy) {
@@ -711,15 +702,14 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
       if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
       const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
       const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
-      const int colA = txA + dx - sx0, colB = txB + dx - sx0;  // same parity
-      const int cpA = (colA & 1) * HALF + (colA >> 1), cpB = (colB & 1) * HALF + (colB >> 1);
-      const int sbA = (tyA + dy - sy0) * kPatchSrc + cpA, sbB = (tyB + dy - sy0) * kPatchSrc + cpB;
-      if (skip_empty && __all_sync(0xffffffffu, sempty[sbA] && sempty[sbB])) continue;
+      const int colA = txA + dx - sx0;
+      const int cpA = (colA & 1) * HALF + (colA >> 1);
+      const int sbA = (tyA + dy - sy0) * kPatchSrc + cpA;
+      if (skip_empty && __all_sync(0xffffffffu, sempty[sbA])) continue;
       const cpx<R> *mA = Mp + sbA * PP;
-      const cpx<R> *mB = Mp + sbB * PP;
 #pragma unroll 1
       for (int k = 0; k < PP; k += 2) {
-        const cpx<R> ma0 = mA[k], ma1 = mA[k + 1], mb0 = mB[k], mb1 = mB[k + 1];
+        const cpx<R> ma0 = mA[k], ma1 = mA[k + 1];
 #pragma unroll
         for (int r = 0; r < P1; ++r) {
           // (g_{r+k}, g_{r+k+1}): an aligned pair of copy 0 (r even) or copy 1 (r odd)
@@ -727,14 +717,10 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
           const cpx<R> t0 = gp[0], t1 = gp[1];
           cfma(accA[r], t0, ma0);
           cfma(accA[r], t1, ma1);
-          cfma(accB[r], t0, mb0);
-          cfma(accB[r], t1, mb1);
         }
       }
       // M_0 ln|t d| on Re L_0, in the scaled outputs (L_0 = -L'_0; M'_0 = M_0)
-      const R lgc = lg[slot];
-      accA[0].x -= mA[0].x * lgc;
-      accB[0].x -= mB[0].x * lgc;
+      accA[0].x -= mA[0].x * lg[slot];
     }
   }
   const R s = (R)(-0.5 / HP_TWO_PI);
@@ -747,29 +733,20 @@ k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
       B[e0 + r] = conj(v);
     }
   }
-  if (vB) {
-    const size_t e0 = (size_t)(off + box_morton(txB, tyB)) * P1;
-#pragma unroll
-    for (int r = 0; r < P1; ++r) {
-      const cpx<R> v = (s * fac_out[r]) * accB[r];
-      A[e0 + r] = v;
-      B[e0 + r] = conj(v);
-    }
-  }
 }
 
 template <typename R, int P1>
 size_t patch_smem() {
   constexpr int PP = (P1 + 1) & ~1;
-  return sizeof(cpx<R>) * (40 * 2 * 2 * P1 + kPatchSrc * kPatchSrc * PP) + sizeof(R) * 40;
+  return sizeof(cpx<R>) * (40 * 2 * 2 * P1 + kPatchSrc * kSrcRows * PP) + sizeof(R) * 40;
 }
 
 int patch_blocks(int H) {
   int nb = 0;
   for (int l = 2; l <= H; ++l) {
-    int np = (1 << (l - 1)) / kPatch;
-    np = np < 1 ? 1 : np;
-    nb += np * np;
+    const int nps = 1 << (l - 1);
+    const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
+    nb += npx * npy;
   }
   return nb;
 }
