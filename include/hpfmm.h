@@ -119,7 +119,11 @@ hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n, double ka
  * leaf offsets and translation tables, as in hpfmm_create, without device
  * allocations (host coordinates are staged through the stream-ordered pool).
  * Returns EINVAL (synchronously) for invalid points; the plan then holds no
- * valid tree until a successful update.
+ * valid tree until a successful update.  The call waits only until the
+ * bounding square is known on the device (its validity and size reach the
+ * host through a pinned buffer); the rest of the rebuild stays queued on
+ * `stream`, and the reaction tables are built on a plan-owned side stream
+ * that `stream` waits for.
  */
 hpfmm_status hpfmm_update_points(hpfmm_plan *plan, const double *x, const double *y,
                                  void *stream);
