@@ -396,12 +396,12 @@ def extra_workloads(args, dev, flush, check):
     # separate targets: the Example 2 geometry (8 charged circles, field mesh
     # including y = 0) at 2e5 sources and 1.25e5 field points
     xs, ys, qs, xt, yt = workloads.example2(n_source=25_000, nfx=512, nfy=245)
-    plan = hp.hpfmm_create(t(xs), t(ys), kappa=1.0, p=16, leaf_size=32, prec="fp32", levels=9,
+    plan = hp.hpfmm_create(t(xs), t(ys), kappa=1.0, p=16, leaf_size=32, prec="fp32", levels=8,
                            root=(-4.4, 8.8))
     qd, xtd, ytd = t(qs), t(xt), t(yt)
     ms_t = _event_time(lambda: hp.hpfmm_eval_targets(plan, qd, xtd, ytd), k, w, flush)
     e = {"workload": "Example 2 geometry: 8 circles x 25000 sources (charge 2pi/25000), "
-                     "512 x 245 field mesh on [-4.4,4.4]x[0,4.2], kappa=1, fp32 plan p=16, L=9",
+                     "512 x 245 field mesh on [-4.4,4.4]x[0,4.2], kappa=1, fp32 plan p=16, L=8",
          "ms_per_eval": ms_t, "value": float(len(xs)) * len(xt) / (ms_t / 1e3), "unit": UNIT}
     if check:
         pot, _ = hp.hpfmm_eval_targets(plan, qd, xtd, ytd, grad=False)

@@ -146,7 +146,7 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
                   pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj, pl->mq, pl->mqsm,
-                  pl->mM, pl->mA, pl->mB, pl->tflag, pl->t_m2l_tc};
+                  pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -435,15 +435,22 @@ extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, do
   return HPFMM_OK;
 }
 
-// targets must be finite, on y >= 0 and inside the plan's root square
+// targets must be finite, on y >= 0 and inside the plan's root square; the
+// valid targets in the bottom leaf row (by the sources' quantisation) are
+// appended to list, when there is one, for the image/reaction kernel
 __global__ void k_check_targets(const double *__restrict__ xt, const double *__restrict__ yt,
-                                int64_t nt, double x0, double side, int *__restrict__ flag) {
+                                int64_t nt, double x0, double side, double qscale, int H,
+                                int *__restrict__ flag, int64_t *__restrict__ list) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nt) return;
   const double x = xt[i], y = yt[i];
   const bool ok = isfinite(x) && isfinite(y) && y >= 0.0 && x >= x0 && x <= x0 + side &&
                   y <= side;
-  if (!ok) atomicOr(flag, 1);
+  if (!ok) {
+    atomicOr(flag, 1);
+    return;
+  }
+  if (list && (quantise(y, side, qscale) >> (30 - H)) == 0) list[atomicAdd(flag + 1, 1)] = i;
 }
 
 extern "C" hpfmm_status hpfmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
@@ -461,23 +468,34 @@ extern "C" hpfmm_status hpfmm_eval_targets(hpfmm_plan *pl, const double *q, cons
       return HPFMM_EINVAL;
     }
   cudaStream_t st = (cudaStream_t)stream;
-  if (!pl->tflag) HP_TRY(plan_dalloc(pl, (void **)&pl->tflag, sizeof(int)));
-  int hflag = 0;
-  if (nt > 0) {
-    HP_CUDA(cudaMemsetAsync(pl->tflag, 0, sizeof(int), st));
-    k_check_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(xt, yt, nt, pl->x0, pl->side,
-                                                                  pl->tflag);
-    HP_LAUNCH_CHECK();
-    HP_CUDA(cudaMemcpyAsync(&hflag, pl->tflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  const bool single = pl->prec != HPFMM_FP64;
+  if (!pl->tflag) HP_TRY(plan_dalloc(pl, (void **)&pl->tflag, 2 * sizeof(int)));
+  if (single && nt > pl->tlist_cap) {
     HP_CUDA(cudaStreamSynchronize(st));
+    if (pl->tlist) {
+      cudaFree(pl->tlist);
+      pl->workspace_bytes -= (int64_t)sizeof(int64_t) * pl->tlist_cap;
+      pl->tlist = nullptr;
+      pl->tlist_cap = 0;
+    }
+    HP_TRY(plan_dalloc(pl, (void **)&pl->tlist, sizeof(int64_t) * (size_t)nt));
+    pl->tlist_cap = nt;
   }
-  if (hflag) {
+  int hflag[2] = {0, 0};
+  HP_CUDA(cudaMemsetAsync(pl->tflag, 0, 2 * sizeof(int), st));
+  k_check_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+      xt, yt, nt, pl->x0, pl->side, pl->qscale, pl->H, pl->tflag, single ? pl->tlist : nullptr);
+  HP_LAUNCH_CHECK();
+  HP_CUDA(cudaMemcpyAsync(hflag, pl->tflag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  if (hflag[0]) {
     set_last_error("hpfmm_eval_targets: targets must be finite, with y >= 0, inside the root "
                    "square [%g, %g] x [0, %g]",
                    pl->x0, pl->x0 + pl->side, pl->side);
     return HPFMM_EINVAL;
   }
-  return fmm_eval_targets(pl, q, xt, yt, nt, pot, grad, st);
+  return fmm_eval_targets(pl, q, xt, yt, nt, single ? pl->tlist : nullptr, hflag[1], pot, grad,
+                          st);
 }
 
 extern "C" hpfmm_status hpfmm_destroy(hpfmm_plan *pl) {

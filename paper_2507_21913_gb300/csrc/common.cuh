@@ -169,6 +169,46 @@ __host__ __device__ __forceinline__ int box_iy(uint64_t m) { return (int)compact
 __host__ __device__ __forceinline__ uint64_t box_morton(int ix, int iy) {
   return spread1((uint32_t)ix) | (spread1((uint32_t)iy) << 1);
 }
+// ix = min(floor((x - x0) / L * 2^30), 2^30 - 1) with the quotient correctly
+// rounded, so that the key matches a plain IEEE host computation bit for bit.
+// Fast path: s' = v * RN(2^30 / L) is within 2 ulp of the exact scaled
+// quotient, and the correctly rounded RN(v / L) * 2^30 is within 1/2 ulp of
+// it; when no integer lies within 4 ulp of s', both floors agree.  Otherwise
+// (a fraction ~1e-7 of the points) the exact division decides.
+__device__ __forceinline__ uint64_t quantise(double v, double L, double scale) {
+  const double s = __dmul_rn(v, scale);
+  // floor(s) and the distance of s to the nearest integers, in ulps of s,
+  // from the bit pattern (s >= 0, s < 2^31)
+  const long long b = __double_as_longlong(s);
+  const int E = (int)((b >> 52) & 0x7ff) - 1023;
+  bool safe;
+  uint64_t f;
+  if (E < 0) {  // s < 1
+    f = 0;
+    safe = s < 0.999999;
+  } else {
+    const uint64_t m = (uint64_t)(b & 0xfffffffffffffull) | (1ull << 52);
+    const int fb = 52 - E;  // fraction bits (>= 21 here)
+    f = m >> fb;
+    const uint64_t frac = m & ((1ull << fb) - 1);
+    safe = frac >= 4 && frac <= (1ull << fb) - 5;
+  }
+  if (!safe) {
+    const double q = __ddiv_rn(v, L);
+    double fl = floor(__dmul_rn(q, 1073741824.0));
+    fl = fmax(fl, 0.0);
+    f = (uint64_t)fl;
+  }
+  return f > 1073741823ull ? 1073741823ull : f;
+}
+
+// centre of leaf (ix, iy) of side d in the root square starting at x0, with
+// explicit roundings: the single-precision leaf frames of the sources and of
+// separate targets must use bit-identical centres
+__device__ __forceinline__ double2 leaf_centre_at(double x0, double d, int ix, int iy) {
+  return make_double2(__fma_rn(ix + 0.5, d, x0), __dmul_rn(iy + 0.5, d));
+}
+
 // first box of level l in the level-concatenated box arrays: (4^l - 1) / 3
 __host__ __device__ __forceinline__ int64_t level_offset(int l) {
   return ((int64_t(1) << (2 * l)) - 1) / 3;
@@ -187,6 +227,7 @@ struct hpfmm_plan {
   double root_x0 = 0, root_side = 0;  // root square override (root_side > 0)
   double kre = 1, kim = 0;
   double x0 = 0, side = 1;
+  double qscale = 1073741824.0;  // 2^30 / side rounded: the key quantisation scale
   int64_t nbox = 0;  // boxes over levels 0..H
   int nleaf = 0;     // 4^H
 
@@ -220,7 +261,11 @@ struct hpfmm_plan {
   // multi-RHS workspace (single precision), for up to mcap charge vectors at once
   void *mq = nullptr, *mqsm = nullptr, *mM = nullptr, *mA = nullptr, *mB = nullptr;
   int mcap = 0;
-  int *tflag = nullptr;  // target validation flag (hpfmm_eval_targets)
+  // hpfmm_eval_targets: validation flag and bottom-row target count (int[2]);
+  // the list of targets in the bottom leaf row (single-precision plans)
+  int *tflag = nullptr;
+  int64_t *tlist = nullptr;
+  int64_t tlist_cap = 0;
   // the reaction tables of a rebuild run on a side stream, overlapping the
   // tree build: forked once the bounding square is known, joined before the
   // rebuild's synchronisation
@@ -284,8 +329,8 @@ hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad
 bool fmm_multi_supported(const hpfmm_plan *pl);
 // evaluation at nt separate targets (device arrays inside the root square)
 hpfmm_status fmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
-                              const double *yt, int64_t nt, double *pot, double *grad,
-                              cudaStream_t st);
+                              const double *yt, int64_t nt, const int64_t *blist,
+                              int64_t nbottom, double *pot, double *grad, cudaStream_t st);
 int fmm_multi_rp(int nr);
 hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot, double *grad,
                             void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st);

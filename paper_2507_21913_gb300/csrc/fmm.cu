@@ -1238,41 +1238,46 @@ struct NearAcc {
   cf ur, grx, gry;                  // reaction (pairs evaluated in single or double)
 };
 
+// one image + reaction pair of a bottom-row target (mx, my in the target's
+// leaf frame) and a bottom-row source s = (x in the same frame, y in its own
+// leaf frame, q): single precision where the series is accurate, else double
+__device__ __forceinline__ void mirror_pair(const float4 s, float mx, float my, float d, cf kap,
+                                            cd kappa, float tau, NearAcc &a) {
+  float dx = mx - s.x;
+  // bottom row: leaf centres at y = d/2, so Y = y_i + y_j = ly + sy + d
+  float Y = my + s.y + d;
+  float R2 = fmaf(dx, dx, Y * Y);
+  float qi = s.z * fast_rcp(R2);
+  a.li = fmaf(s.z, __log2f(R2), a.li);
+  a.gix = fmaf(qi, dx, a.gix);
+  a.giy = fmaf(qi, Y, a.giy);
+  cf sp_ = mk(Y, -dx), sm_ = mk(Y, dx);
+  cf Pp = kap * sp_, Pm = kap * sm_;
+  if (abs2(Pp) <= 1.f && Y >= tau) {
+    cf J0p, J1p, J0m, J1m;
+    j01_f(Pp, J0p, J1p);
+    j01_f(Pm, J0m, J1m);
+    a.ur = a.ur + s.z * (J0p + J0m);
+    cf tp = cdiv(J1p, sp_), tm = cdiv(J1m, sm_);
+    a.grx = a.grx + s.z * mul_i(tp - tm);
+    a.gry = a.gry - s.z * (tp + tm);
+  } else {
+    cd spd = mk((double)Y, -(double)dx), smd = mk((double)Y, (double)dx);
+    cd J0p, J1p, J0m, J1m;
+    j01(kappa * spd, J0p, J1p);
+    j01(kappa * smd, J0m, J1m);
+    double q = s.z;
+    cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
+    a.ur = a.ur + to<float>(q * (J0p + J0m));
+    a.grx = a.grx + to<float>(q * mul_i(tp - tm));
+    a.gry = a.gry - to<float>(q * (tp + tm));
+  }
+}
+
 __device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, int ng, float mx,
                                              float my, float d, cf kap, cd kappa, float tau,
                                              NearAcc &a) {
-  for (int k = g; k < cnt; k += ng) {
-    float4 s = buf[k];
-    float dx = mx - s.x;
-    // bottom row: leaf centres at y = d/2, so Y = y_i + y_j = ly + sy + d
-    float Y = my + s.y + d;
-    float R2 = fmaf(dx, dx, Y * Y);
-    float qi = s.z * fast_rcp(R2);
-    a.li = fmaf(s.z, __log2f(R2), a.li);
-    a.gix = fmaf(qi, dx, a.gix);
-    a.giy = fmaf(qi, Y, a.giy);
-    cf sp_ = mk(Y, -dx), sm_ = mk(Y, dx);
-    cf Pp = kap * sp_, Pm = kap * sm_;
-    if (abs2(Pp) <= 1.f && Y >= tau) {
-      cf J0p, J1p, J0m, J1m;
-      j01_f(Pp, J0p, J1p);
-      j01_f(Pm, J0m, J1m);
-      a.ur = a.ur + s.z * (J0p + J0m);
-      cf tp = cdiv(J1p, sp_), tm = cdiv(J1m, sm_);
-      a.grx = a.grx + s.z * mul_i(tp - tm);
-      a.gry = a.gry - s.z * (tp + tm);
-    } else {
-      cd spd = mk((double)Y, -(double)dx), smd = mk((double)Y, (double)dx);
-      cd J0p, J1p, J0m, J1m;
-      j01(kappa * spd, J0p, J1p);
-      j01(kappa * smd, J0m, J1m);
-      double q = s.z;
-      cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
-      a.ur = a.ur + to<float>(q * (J0p + J0m));
-      a.grx = a.grx + to<float>(q * mul_i(tp - tm));
-      a.gry = a.gry - to<float>(q * (tp + tm));
-    }
-  }
+  for (int k = g; k < cnt; k += ng) mirror_pair(buf[k], mx, my, d, kap, kappa, tau, a);
 }
 
 __device__ __forceinline__ float xsum(float v, int from) {
@@ -1658,81 +1663,161 @@ k_eval32m(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp,
 }
 
 // Evaluation at separate targets (Example 2: field points that are not
-// sources, on y >= 0).  One thread per target, in the caller's order: the
-// target's leaf comes from the plan's geometry (targets lie in the root
-// square); the leaf's local expansions give the far field (L2P), and the
-// sources of the 3 x 3 neighbour leaves the near field -- free part for all,
-// image and reaction parts for bottom-row leaves, as for the sources
-// themselves.  The near field is summed in double precision for both plan
-// precisions (single-precision plans store sources relative to their leaf
-// centre; the absolute position is rebuilt in double).  A target that
-// coincides with a source skips that pair's free term (log singularity).
+// sources, on y >= 0).  Targets stay in the caller's order and a warp takes
+// 32 of them.  Each lane finds its target's leaf by the sources' own
+// quantisation, so that a target placed on a source gets that source's leaf
+// and leaf frame, and evaluates the leaf's local expansions (L2P, in the
+// plan's precision).  The near field is then summed by the whole warp, one
+// target at a time: lanes stride over the sources of the target's 3 x 3
+// neighbour leaves and a butterfly reduction hands the sums to the target's
+// lane.  Only targets whose neighbourhood holds sources take part, so the
+// few field points next to dense leaves do not hold up the other lanes of
+// their warp.  The free part is summed in the plan's precision (single
+// precision in the leaf frames, as for the sources, with each neighbour
+// leaf's exact offset).  The image and reaction parts of bottom-row pairs
+// are summed here in double for double-precision plans, and by
+// k_mirror_targets for single-precision ones.  A pair at zero distance skips
+// its free term (log singularity).
 template <typename R>
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
 k_eval_targets(const double *__restrict__ xt, const double *__restrict__ yt, int64_t nt,
                const double *__restrict__ xs, const double *__restrict__ ys,
                const float2 *__restrict__ loc, const R *__restrict__ qs,
-               const int *__restrict__ leaf_start, int H, double x0, double side, int p,
-               cd kappa, const cpx<R> *__restrict__ A, const cpx<R> *__restrict__ B,
-               double *__restrict__ pot, double *__restrict__ grad) {
+               const int *__restrict__ leaf_start, int H, double x0, double side,
+               double qscale, int p, cd kappa, const cpx<R> *__restrict__ A,
+               const cpx<R> *__restrict__ B, double *__restrict__ pot,
+               double *__restrict__ grad) {
+  const int lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
+  const bool act = t < nt;
   const int P1 = p + 1, nx = 1 << H;
-  const double d = side / (double)nx;
-  const double x = xt[t], y = yt[t];
-  int ix = (int)floor((x - x0) / d), iy = (int)floor(y / d);
-  ix = ix < 0 ? 0 : (ix >= nx ? nx - 1 : ix);
-  iy = iy < 0 ? 0 : (iy >= nx ? nx - 1 : iy);
-  const uint64_t leaf = box_morton(ix, iy);
-  const double cx = x0 + (ix + 0.5) * d, cy = (iy + 0.5) * d;
+  const double d = ldexp(side, -H);
+  const double x = act ? xt[t] : x0, y = act ? yt[t] : 0.0;
+  const int ix = (int)(quantise(__dsub_rn(x, x0), side, qscale) >> (30 - H));
+  const int iy = (int)(quantise(y, side, qscale) >> (30 - H));
+  const double2 c = leaf_centre_at(x0, d, ix, iy);
+  const double lx = x - c.x, ly = y - c.y;  // target in its leaf frame
+  const R rd = (R)d, rinvd = (R)(1.0 / d);
   // far field: L2P with the leaf's expansions (Horner in w and conj(w))
-  const cpx<R> *Al = A + (size_t)(level_offset(H) + leaf) * P1;
-  const cpx<R> *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
-  const cd w = mk((x - cx) / d, (y - cy) / d), wb = conj(w);
-  auto c64 = [](cpx<R> z) { return mk((double)z.x, (double)z.y); };
-  cd va = c64(Al[p]), da = mk(0.0, 0.0), vb = c64(Bl[p]), db = mk(0.0, 0.0);
-  for (int n = p - 1; n >= 0; --n) {
-    da = da * w + va;
-    va = va * w + c64(Al[n]);
-    db = db * wb + vb;
-    vb = vb * wb + c64(Bl[n]);
+  cd u = mk(0.0, 0.0), gx = u, gy = u;
+  int cnt = 0;
+  if (act) {
+    const uint64_t leaf = box_morton(ix, iy);
+    const cpx<R> *Al = A + (size_t)(level_offset(H) + leaf) * P1;
+    const cpx<R> *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
+    const cpx<R> w = mk((R)lx * rinvd, (R)ly * rinvd), wb = conj(w);
+    cpx<R> va = Al[p], da = mk<R>(0, 0), vb = Bl[p], db = mk<R>(0, 0);
+    for (int n = p - 1; n >= 0; --n) {
+      da = da * w + va;
+      va = va * w + Al[n];
+      db = db * wb + vb;
+      vb = vb * wb + Bl[n];
+    }
+    auto c64 = [](cpx<R> z) { return mk((double)z.x, (double)z.y); };
+    u = c64(va + vb);
+    gx = (1.0 / d) * c64(da + db);
+    gy = (1.0 / d) * c64(mul_i(da) - mul_i(db));
+    for (int r = -1; r <= 1; ++r)
+      for (int cc = -1; cc <= 1; ++cc) {
+        const int mx = ix + cc, my = iy + r;
+        if (mx < 0 || my < 0 || mx >= nx || my >= nx) continue;
+        const uint64_t sl = box_morton(mx, my);
+        cnt += leaf_start[sl + 1] - leaf_start[sl];
+      }
   }
-  cd u = va + vb;
-  cd gx = (1.0 / d) * (da + db);
-  cd gy = (1.0 / d) * (mul_i(da) - mul_i(db));
-  // near field
-  PairAcc<double> acc;
-  for (int ny = iy - 1; ny <= iy + 1; ++ny) {
-    if (ny < 0 || ny >= nx) continue;
-    for (int mx = ix - 1; mx <= ix + 1; ++mx) {
-      if (mx < 0 || mx >= nx) continue;
-      const uint64_t sl = box_morton(mx, ny);
-      const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-      const double scx = x0 + (mx + 0.5) * d, scy = (ny + 0.5) * d;
-      const bool mirror = iy == 0 && ny == 0;
-      for (int k = s0; k < s1; ++k) {
-        double sx, sy;
-        if (sizeof(R) == 8) {
-          sx = xs[k];
-          sy = ys[k];
-        } else {
-          const float2 v = loc[k];
-          sx = scx + (double)v.x;
-          sy = scy + (double)v.y;
-        }
-        const double q = (double)qs[k];
-        const double dx = x - sx, dy = y - sy;
-        if (dx != 0.0 || dy != 0.0) pair_free(acc, dx, dy, q);
-        if (mirror) {
-          const double Y = y + sy;
-          pair_image(acc, dx, Y, q);
-          pair_reaction_d(acc, dx, Y, q, kappa);
+  // near field, one target of the warp at a time
+  constexpr bool kSingle = sizeof(R) == 4;
+  PairAcc<double> mine;  // the sums of this lane's own target
+  unsigned hot = __ballot_sync(0xffffffffu, act && cnt > 0);
+  while (hot) {
+    const int h = __ffs(hot) - 1;
+    hot &= hot - 1;
+    const int hix = __shfl_sync(0xffffffffu, ix, h), hiy = __shfl_sync(0xffffffffu, iy, h);
+    const double hx = __shfl_sync(0xffffffffu, x, h), hy = __shfl_sync(0xffffffffu, y, h);
+    const R hlx = (R)__shfl_sync(0xffffffffu, lx, h), hly = (R)__shfl_sync(0xffffffffu, ly, h);
+    R lf = 0, fx = 0, fy = 0;
+    PairAcc<double> ma;
+#pragma unroll 1
+    for (int r = -1; r <= 1; ++r) {
+      const int my = hiy + r;
+      if (my < 0 || my >= nx) continue;
+#pragma unroll 1
+      for (int cc = -1; cc <= 1; ++cc) {
+        const int mx = hix + cc;
+        if (mx < 0 || mx >= nx) continue;
+        const uint64_t sl = box_morton(mx, my);
+        const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+        const bool mirror = hiy == 0 && my == 0;
+        // the target in the frame of this source leaf (exact leaf offset)
+        const R ox = hlx - (R)cc * rd, oy = hly - (R)r * rd;
+        for (int k = s0 + lane; k < s1; k += 32) {
+          const R q = qs[k];
+          R dx, dy;
+          double sxa = 0.0, sya = 0.0;
+          if constexpr (kSingle) {
+            const float2 v = loc[k];
+            dx = ox - v.x;
+            dy = oy - v.y;
+          } else {
+            sxa = xs[k];
+            sya = ys[k];
+            dx = hx - sxa;
+            dy = hy - sya;
+          }
+          const R r2 = dx * dx + dy * dy;
+          if (r2 > R(0)) {
+            if constexpr (kSingle) {
+              const float qi = q * fast_rcp(r2);
+              lf = fmaf(q, fast_lg2(r2), lf);
+              fx = fmaf(qi, dx, fx);
+              fy = fmaf(qi, dy, fy);
+            } else {
+              const double qi = q / r2;
+              lf += q * log(r2);
+              fx += qi * dx;
+              fy += qi * dy;
+            }
+          }
+          if (!kSingle && mirror) {
+            const double ddx = hx - sxa, Y = hy + sya;
+            pair_image(ma, ddx, Y, (double)q);
+            pair_reaction_d(ma, ddx, Y, (double)q, kappa);
+          }
         }
       }
     }
+    lf = warp_sum(lf);
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    if (!kSingle && hiy == 0) {
+      ma.li = warp_sum(ma.li);
+      ma.gix = warp_sum(ma.gix);
+      ma.giy = warp_sum(ma.giy);
+      ma.ur.x = warp_sum(ma.ur.x);
+      ma.ur.y = warp_sum(ma.ur.y);
+      ma.grx.x = warp_sum(ma.grx.x);
+      ma.grx.y = warp_sum(ma.grx.y);
+      ma.gry.x = warp_sum(ma.gry.x);
+      ma.gry.y = warp_sum(ma.gry.y);
+    }
+    if (lane == h) {
+      mine = ma;
+      // single precision sums q log2 r^2: the accumulator holds q ln r^2
+      mine.lf = kSingle ? (double)lf * 0.69314718055994530942 : (double)lf;
+      mine.gfx = (double)fx;
+      mine.gfy = (double)fy;
+    }
   }
+  if (!act) return;
   cd un, gxn, gyn;
-  acc.finish(un, gxn, gyn);
+  mine.finish(un, gxn, gyn);
   u = u + un;
   gx = gx + gxn;
   gy = gy + gyn;
@@ -1839,6 +1924,70 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
   }
 }
 
+// Image and reaction near field of separate targets in the bottom leaf row
+// (single-precision plans), added to the outputs of k_eval_targets.  The
+// targets come listed by the validation pass; one block per target, whose
+// threads stride over the sources of the three bottom-row neighbour leaves
+// (single precision where the series is accurate, else double, as in
+// k_mirror32), then a block reduction.  A few field points next to a dense
+// bottom-row leaf thus spread over many warps instead of serialising.
+__global__ void __launch_bounds__(kEvWarps * 32)
+k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt,
+                 const double *__restrict__ yt, const float2 *__restrict__ loc,
+                 const float *__restrict__ qs, const int *__restrict__ leaf_start, int H,
+                 double x0, double side, double qscale, cd kappa, float tau,
+                 double *__restrict__ pot, double *__restrict__ grad) {
+  __shared__ float red[kEvWarps][9];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = list[blockIdx.x];
+  const int nx = 1 << H;
+  const double dd = ldexp(side, -H);
+  const float d = (float)dd;
+  const double x = xt[t], y = yt[t];
+  const int ix = (int)(quantise(__dsub_rn(x, x0), side, qscale) >> (30 - H));
+  const double2 c = leaf_centre_at(x0, dd, ix, 0);
+  const float mx = (float)(x - c.x), my = (float)(y - c.y);
+  const cf kap = mk((float)kappa.x, (float)kappa.y);
+  NearAcc acc;
+  acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
+  acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
+  for (int k = 0; k < 3; ++k) {
+    const int sx = ix - 1 + k;
+    if (sx < 0 || sx >= nx) continue;
+    const uint64_t sl = box_morton(sx, 0);
+    const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
+    const float ox = (float)(k - 1) * d;
+    for (int j = s0 + (int)threadIdx.x; j < s1; j += blockDim.x) {
+      const float2 v = loc[j];
+      mirror_pair(make_float4(v.x + ox, v.y, qs[j], 0.f), mx, my, d, kap, kappa, tau, acc);
+    }
+  }
+  float v[9] = {acc.li,    acc.gix,   acc.giy,   acc.ur.x, acc.ur.y,
+                acc.grx.x, acc.grx.y, acc.gry.x, acc.gry.y};
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    v[e] = warp_sum(v[e]);
+    if (lane == 0) red[warp][e] = v[e];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    v[e] = 0.f;
+    for (int w = 0; w < kEvWarps; ++w) v[e] += red[w][e];
+  }
+  const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+  const float i2pi = (float)(1.0 / HP_TWO_PI);
+  pot[2 * t] += (double)(v[0] * c4 + v[3] * i2pi);
+  pot[2 * t + 1] += (double)(v[4] * i2pi);
+  if (grad) {
+    grad[4 * t + 0] += (double)((v[1] + v[5]) * i2pi);
+    grad[4 * t + 1] += (double)(v[6] * i2pi);
+    grad[4 * t + 2] += (double)((v[2] + v[7]) * i2pi);
+    grad[4 * t + 3] += (double)(v[8] * i2pi);
+  }
+}
+
 inline unsigned cdiv_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // workspace of a multi-RHS evaluation: nr right-hand sides, rp = nr rounded
@@ -1853,6 +2002,8 @@ constexpr int kRhsChunk = 8;
 struct TargetWork {
   const double *xt, *yt;
   int64_t nt;
+  const int64_t *blist;  // targets in the bottom leaf row (single precision)
+  int64_t nbottom;
 };
 
 template <typename R>
@@ -1998,10 +2149,18 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   cd kappa = mk(pl->kre, pl->kim);
   if (tw) {
     if (tw->nt > 0)
-      k_eval_targets<R><<<cdiv_u(tw->nt, 128), 128, 0, st>>>(
+      k_eval_targets<R><<<cdiv_u(tw->nt, 256), 256, 0, st>>>(
           tw->xt, tw->yt, tw->nt, pl->xs, pl->ys, pl->loc32, (const R *)qs, pl->leaf_start, H,
-          pl->x0, pl->side, p, kappa, A, B, pot, grad);
+          pl->x0, pl->side, pl->qscale, p, kappa, A, B, pot, grad);
     pass_end(pl, st, PASS_EVAL, tw->nt > 0 ? 1 : 0);
+    if (sizeof(R) == 4 && tw->nbottom > 0) {
+      pass_begin(pl, st, PASS_NEAR_MIRROR);
+      const float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
+      k_mirror_targets<<<(unsigned)tw->nbottom, 32 * kEvWarps, 0, st>>>(
+          tw->blist, tw->xt, tw->yt, pl->loc32, (const float *)qs, pl->leaf_start, H, pl->x0,
+          pl->side, pl->qscale, kappa, tau, pot, grad);
+      pass_end(pl, st, PASS_NEAR_MIRROR, 1);
+    }
     HP_LAUNCH_CHECK();
     return HPFMM_OK;
   }
@@ -2083,10 +2242,10 @@ bool fmm_multi_supported(const hpfmm_plan *pl) {
 int fmm_multi_rp(int nr) { return (nr + kRhsChunk - 1) / kRhsChunk * kRhsChunk; }
 
 hpfmm_status fmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
-                              const double *yt, int64_t nt, double *pot, double *grad,
-                              cudaStream_t st) {
+                              const double *yt, int64_t nt, const int64_t *blist,
+                              int64_t nbottom, double *pot, double *grad, cudaStream_t st) {
   HP_TRY(special_init_here());
-  const TargetWork tw{xt, yt, nt};
+  const TargetWork tw{xt, yt, nt, blist, nbottom};
   if (pl->prec == HPFMM_FP64) return run_passes<double>(pl, q, pot, grad, st, nullptr, &tw);
   return run_passes<float>(pl, q, pot, grad, st, nullptr, &tw);
 }

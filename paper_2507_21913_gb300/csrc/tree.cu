@@ -110,38 +110,6 @@ bbox_final(const Geom *__restrict__ part, int nb, double *__restrict__ geo, doub
   geo[3] = __ddiv_rn(1073741824.0, L);
 }
 
-// ix = min(floor((x - x0) / L * 2^30), 2^30 - 1) with the quotient correctly
-// rounded, so that the key matches a plain IEEE host computation bit for bit.
-// Fast path: s' = v * RN(2^30 / L) is within 2 ulp of the exact scaled
-// quotient, and the correctly rounded RN(v / L) * 2^30 is within 1/2 ulp of
-// it; when no integer lies within 4 ulp of s', both floors agree.  Otherwise
-// (a fraction ~1e-7 of the points) the exact division decides.
-__device__ __forceinline__ uint64_t quantise(double v, double L, double scale) {
-  const double s = __dmul_rn(v, scale);
-  // floor(s) and the distance of s to the nearest integers, in ulps of s,
-  // from the bit pattern (s >= 0, s < 2^31)
-  const long long b = __double_as_longlong(s);
-  const int E = (int)((b >> 52) & 0x7ff) - 1023;
-  bool safe;
-  uint64_t f;
-  if (E < 0) {  // s < 1
-    f = 0;
-    safe = s < 0.999999;
-  } else {
-    const uint64_t m = (uint64_t)(b & 0xfffffffffffffull) | (1ull << 52);
-    const int fb = 52 - E;  // fraction bits (>= 21 here)
-    f = m >> fb;
-    const uint64_t frac = m & ((1ull << fb) - 1);
-    safe = frac >= 4 && frac <= (1ull << fb) - 5;
-  }
-  if (!safe) {
-    const double q = __ddiv_rn(v, L);
-    double fl = floor(__dmul_rn(q, 1073741824.0));
-    fl = fmax(fl, 0.0);
-    f = (uint64_t)fl;
-  }
-  return f > 1073741823ull ? 1073741823ull : f;
-}
 
 // keys, and the point count of each level-H leaf (the atomic's return value
 // is the point's slot inside its leaf bucket; the order within a bucket is
@@ -304,8 +272,7 @@ struct LeafGather {
 
 // centre of a leaf (double precision; the leaf side d = side / 2^H is exact)
 __device__ __forceinline__ double2 leaf_centre(const LeafGather &g, int leaf) {
-  const double d = ldexp(g.geo[1], -g.H);
-  return make_double2(g.geo[0] + (box_ix(leaf) + 0.5) * d, (box_iy(leaf) + 0.5) * d);
+  return leaf_centre_at(g.geo[0], ldexp(g.geo[1], -g.H), box_ix(leaf), box_iy(leaf));
 }
 
 __device__ __forceinline__ void gather_one(const LeafGather &g, double2 c, int k, int j) {
@@ -684,6 +651,7 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st) {
   } else {
     pl->x0 = hgeo[0];
     pl->side = hgeo[1];
+    pl->qscale = hgeo[3];
   }
   if (pl->tree_tmp) cudaFreeAsync(pl->tree_tmp, st);
   pl->tree_tmp = nullptr;
