@@ -309,17 +309,8 @@ def extra_workloads(args, dev, flush, check):
     x, y, q = workloads.clustered(n, seed=0)
     xd, yd, qd = t(x), t(y), t(q)
     kap = 1.0 + 0.5j
-    plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec="mixed", levels=11)
     pot = torch.empty(n, dtype=torch.complex128, device=dev)
     grad = torch.empty((n, 2), dtype=torch.complex128, device=dev)
-
-    def step():
-        hp.hpfmm_update_points(plan, xd, yd)
-        hp.hpfmm_eval(plan, qd, out=(pot, grad))
-    ms = _event_time(step, k, w, flush)
-    e = {"workload": "clustered N=4e6 (80%% in 64 clusters sigma 0.01 near y=0), kappa=1+0.5i, "
-                     "mixed precision, p=20, L=11, tree rebuilt every step", "ms_per_step": ms,
-         "value": float(n) * n / (ms / 1e3), "unit": UNIT}
     if check:
         near = np.flatnonzero(y < 0.06)
         far = np.flatnonzero(y >= 0.06)
@@ -327,11 +318,31 @@ def extra_workloads(args, dev, flush, check):
         idx = np.sort(np.concatenate([g0.choice(near, 4, replace=False),
                                       g0.choice(far, 4, replace=False)]))
         u_ref, _ = oracle_sampled(x, y, q, idx, kap)
-        u = pot.cpu().numpy()[idx]
-        e["rel_err_pot"] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
-        e["check_targets"] = len(idx)
+    e = {}
+    # the configured mixed-precision path, then single precision throughout
+    # (no double-precision reaction pairs) for comparison
+    for prec in ("mixed", "fp32"):
+        plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec=prec, levels=11)
+
+        def step():
+            hp.hpfmm_update_points(plan, xd, yd)
+            hp.hpfmm_eval(plan, qd, out=(pot, grad))
+        ms = _event_time(step, k, w, flush)
+        if prec == "mixed":
+            e = {"workload": "clustered N=4e6 (80% in 64 clusters sigma 0.01 near y=0), "
+                             "kappa=1+0.5i, mixed precision, p=20, L=11, tree rebuilt every step",
+                 "ms_per_step": ms, "value": float(n) * n / (ms / 1e3), "unit": UNIT}
+            key = ""
+        else:
+            e["fp32_ms_per_step"] = ms
+            key = "fp32_"
+        if check:
+            u = pot.cpu().numpy()[idx]
+            e[key + "rel_err_pot"] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+            e["check_targets"] = len(idx)
+        del plan
     out["clustered"] = e
-    del plan, pot, grad, xd, yd, qd
+    del pot, grad, xd, yd, qd
 
     # adjoint: N = 1e6, kappa = 2, p = 16, single precision; forward (with field)
     # then backward for E = w . u

@@ -142,7 +142,7 @@ static void free_plan(hpfmm_plan *pl) {
     delete ts;
     pl->tstate = nullptr;
   }
-  void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->t_m2m,
+  void *bufs[] = {pl->xs, pl->ys, pl->perm, pl->keys, pl->leaf_start, pl->loc32, pl->yabs, pl->t_m2m,
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
                   pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj, pl->mq, pl->mqsm,
@@ -309,6 +309,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->keys, sizeof(uint64_t) * n);
   ALLOC(pl->leaf_start, sizeof(int) * (pl->nleaf + 1));
   if (f32) ALLOC(pl->loc32, sizeof(float2) * n);
+  if (f32) ALLOC(pl->yabs, sizeof(float) * n);
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);

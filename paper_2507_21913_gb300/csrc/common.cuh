@@ -237,6 +237,7 @@ struct hpfmm_plan {
   uint64_t *keys = nullptr;             // sorted keys
   int *leaf_start = nullptr;            // nleaf + 1 offsets into the sorted order
   float2 *loc32 = nullptr;              // FP32 path: (x, y) relative to the leaf centre
+  float *yabs = nullptr;                // FP32 path: y itself (bottom-row image/reaction pairs)
 
   // tables (device, double); FP32 copies when prec != FP64
   void *t_m2m = nullptr;   // 4 x (p+1)^2 complex: child c -> parent

@@ -1238,14 +1238,15 @@ struct NearAcc {
   cf ur, grx, gry;                  // reaction (pairs evaluated in single or double)
 };
 
-// one image + reaction pair of a bottom-row target (mx, my in the target's
-// leaf frame) and a bottom-row source s = (x in the same frame, y in its own
-// leaf frame, q): single precision where the series is accurate, else double
-__device__ __forceinline__ void mirror_pair(const float4 s, float mx, float my, float d, cf kap,
+// one image + reaction pair of a bottom-row target (x in its leaf frame, y
+// itself) and a bottom-row source s = (x in the same frame, y itself, q):
+// single precision where the series is accurate, else double.  The y values
+// are not taken from the leaf frames: near the boundary Y = y_i + y_j would
+// lose its relative precision to the rounding of the leaf offsets.
+__device__ __forceinline__ void mirror_pair(const float4 s, float mx, float my, cf kap,
                                             cd kappa, float tau, NearAcc &a) {
   float dx = mx - s.x;
-  // bottom row: leaf centres at y = d/2, so Y = y_i + y_j = ly + sy + d
-  float Y = my + s.y + d;
+  float Y = my + s.y;
   float R2 = fmaf(dx, dx, Y * Y);
   float qi = s.z * fast_rcp(R2);
   a.li = fmaf(s.z, __log2f(R2), a.li);
@@ -1275,9 +1276,8 @@ __device__ __forceinline__ void mirror_pair(const float4 s, float mx, float my, 
 }
 
 __device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, int ng, float mx,
-                                             float my, float d, cf kap, cd kappa, float tau,
-                                             NearAcc &a) {
-  for (int k = g; k < cnt; k += ng) mirror_pair(buf[k], mx, my, d, kap, kappa, tau, a);
+                                             float my, cf kap, cd kappa, float tau, NearAcc &a) {
+  for (int k = g; k < cnt; k += ng) mirror_pair(buf[k], mx, my, kap, kappa, tau, a);
 }
 
 __device__ __forceinline__ float xsum(float v, int from) {
@@ -1840,7 +1840,8 @@ k_eval_targets(const double *__restrict__ xt, const double *__restrict__ yt, int
 constexpr int kMirSrc = 512;
 constexpr int kMirSplit = 8;  // blocks per bottom-row leaf
 __global__ void __launch_bounds__(kEvWarps * 32)
-k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
+k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
+           const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
            float d, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad,
            RhsStride rs) {
@@ -1877,7 +1878,7 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
   for (int tb = b0 + 32 * (int)blockIdx.z; tb < b1; tb += 32 * (int)gridDim.z) {
     const int i = tb + lane;
     const bool act = i < b1;
-    const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+    const float2 me = act ? make_float2(loc[i].x, yabs[i]) : make_float2(0.f, 0.f);
     NearAcc acc;
     acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
     acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
@@ -1888,11 +1889,11 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
         while (r >= s1[k] - s0[k]) { r -= s1[k] - s0[k]; ++k; }
         const int js = s0[k] + r;
         const float2 v = loc[js];
-        src[e] = make_float4(v.x + ox[k], v.y, qs[js], 0.f);
+        src[e] = make_float4(v.x + ox[k], yabs[js], qs[js], 0.f);
       }
       __syncthreads();
       const int cnt = min(kMirSrc, ns - base);
-      mirror_batch(src, cnt, warp, kEvWarps, me.x, me.y, d, kap, kappa, tau, acc);
+      mirror_batch(src, cnt, warp, kEvWarps, me.x, me.y, kap, kappa, tau, acc);
     }
     red[warp][0][lane] = acc.li;
     red[warp][1][lane] = acc.gix;
@@ -1934,7 +1935,8 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ qs,
 __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt,
                  const double *__restrict__ yt, const float2 *__restrict__ loc,
-                 const float *__restrict__ qs, const int *__restrict__ leaf_start, int H,
+                 const float *__restrict__ yabs, const float *__restrict__ qs,
+                 const int *__restrict__ leaf_start, int H,
                  double x0, double side, double qscale, cd kappa, float tau,
                  double *__restrict__ pot, double *__restrict__ grad) {
   __shared__ float red[kEvWarps][9];
@@ -1946,7 +1948,7 @@ k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt
   const double x = xt[t], y = yt[t];
   const int ix = (int)(quantise(__dsub_rn(x, x0), side, qscale) >> (30 - H));
   const double2 c = leaf_centre_at(x0, dd, ix, 0);
-  const float mx = (float)(x - c.x), my = (float)(y - c.y);
+  const float mx = (float)(x - c.x), my = (float)y;
   const cf kap = mk((float)kappa.x, (float)kappa.y);
   NearAcc acc;
   acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
@@ -1959,7 +1961,7 @@ k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt
     const float ox = (float)(k - 1) * d;
     for (int j = s0 + (int)threadIdx.x; j < s1; j += blockDim.x) {
       const float2 v = loc[j];
-      mirror_pair(make_float4(v.x + ox, v.y, qs[j], 0.f), mx, my, d, kap, kappa, tau, acc);
+      mirror_pair(make_float4(v.x + ox, yabs[j], qs[j], 0.f), mx, my, kap, kappa, tau, acc);
     }
   }
   float v[9] = {acc.li,    acc.gix,   acc.giy,   acc.ur.x, acc.ur.y,
@@ -2157,8 +2159,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
       pass_begin(pl, st, PASS_NEAR_MIRROR);
       const float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
       k_mirror_targets<<<(unsigned)tw->nbottom, 32 * kEvWarps, 0, st>>>(
-          tw->blist, tw->xt, tw->yt, pl->loc32, (const float *)qs, pl->leaf_start, H, pl->x0,
-          pl->side, pl->qscale, kappa, tau, pot, grad);
+          tw->blist, tw->xt, tw->yt, pl->loc32, pl->yabs, (const float *)qs, pl->leaf_start, H,
+          pl->x0, pl->side, pl->qscale, kappa, tau, pot, grad);
       pass_end(pl, st, PASS_NEAR_MIRROR, 1);
     }
     HP_LAUNCH_CHECK();
@@ -2184,8 +2186,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
     k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
-        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], kappa, tau, pot,
-        grad, rs);
+        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], kappa, tau,
+        pot, grad, rs);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
   if (sizeof(R) == 8) pass_end(pl, st, PASS_EVAL, 1);

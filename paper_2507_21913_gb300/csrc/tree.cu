@@ -268,6 +268,7 @@ struct LeafGather {
   double *xs, *ys;
   int64_t *perm;
   float2 *loc32;
+  float *yabs;  // y rounded to single precision (with loc32)
 };
 
 // centre of a leaf (double precision; the leaf side d = side / 2^H is exact)
@@ -282,7 +283,10 @@ __device__ __forceinline__ void gather_one(const LeafGather &g, double2 c, int k
     g.ys[k] = b;
   }
   g.perm[k] = j;
-  if (g.loc32) g.loc32[k] = make_float2((float)(a - c.x), (float)(b - c.y));
+  if (g.loc32) {
+    g.loc32[k] = make_float2((float)(a - c.x), (float)(b - c.y));
+    g.yabs[k] = (float)b;
+  }
 }
 
 // a warp's leaf centre: computed by lane 0 and broadcast (the double-precision
@@ -624,7 +628,7 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   scan_add<<<nsb, 1024, 0, st>>>(t.btot, nleaf, pl->leaf_start);
   bucket_scatter<<<gb, tb, 0, st>>>(t.kb, t.slot, n, H, pl->leaf_start, pl->keys, t.vb);
   // the leaf sorts also put the points into tree order (permutation, coordinates)
-  const LeafGather lg{x, y, geo, H, pl->xs, pl->ys, pl->perm, pl->loc32};
+  const LeafGather lg{x, y, geo, H, pl->xs, pl->ys, pl->perm, pl->loc32, pl->yabs};
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
       pl->leaf_start, nleaf, pl->keys, t.vb, t.big, t.lcount + nleaf, lg);
   leaf_sort<<<160, 256, 0, st>>>(pl->leaf_start, t.big, t.lcount + nleaf, pl->keys, t.vb, lg);
@@ -758,7 +762,7 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
   scan_top<<<1, 1024, 0, st>>>(btot, bmax, nsb, nleaf, lstart, (int *)(geo + 4));
   scan_add<<<nsb, 1024, 0, st>>>(btot, nleaf, lstart);
   bucket_scatter<<<gb, 256, 0, st>>>(kb, slot, n, H, lstart, keys, vb);
-  const LeafGather none{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr};
+  const LeafGather none{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
       lstart, nleaf, keys, vb, big, lcount + nleaf, none);
   leaf_sort<<<160, 256, 0, st>>>(lstart, big, lcount + nleaf, keys, vb, none);

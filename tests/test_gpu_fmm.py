@@ -168,6 +168,35 @@ def test_clustered_4m_mixed_complex_kappa():
     assert rel(u[idx][m], u_ref[m]) < 5e-6
 
 
+@pytest.fixture(scope="module")
+def very_close():
+    """20000 uniform points, 200 of them moved to y = 10^U[-8, -6]; the oracle
+    at those 200 and at 56 sampled others."""
+    n = 20_000
+    x, y, q = workloads.uniform(n, seed=11)
+    y = y.copy()
+    y[:200] = 10.0 ** np.random.Generator(np.random.PCG64(12)).uniform(-8, -6, 200)
+    idx = np.unique(np.concatenate([np.arange(200), workloads.sample_targets(n, 56, seed=1)]))
+    u_ref, g_ref = oracle.direct(x, y, q, xt=x[idx], yt=y[idx], kappa=1.0 + 0.5j, self_index=idx)
+    return x, y, q, idx, u_ref, g_ref
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_points_very_close_to_the_boundary(very_close, prec):
+    """Single-precision plans on a tree of level 4 (leaves 1/16 high) with
+    points at y down to 1e-8: Y = y_i + y_j of their bottom-row pairs lies far
+    below the rounding of leaf-frame coordinates (~1e-9 here), so the image
+    and reaction pairs must take y itself.  Potentials and gradients at those
+    points against the oracle, and over the whole sample."""
+    x, y, q, idx, u_ref, g_ref = very_close
+    u, g, _ = run(x, y, q, 1.0 + 0.5j, 16, 32, prec=prec, levels=4)
+    low = idx < 200
+    assert rel(u[idx][low], u_ref[low]) < 5e-6
+    assert rel(g[idx][low], g_ref[low]) < 5e-6
+    assert rel(u[idx], u_ref) < 5e-6
+    assert rel(g[idx], g_ref) < 2e-5
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 5e-6), ("fp64", 1e-9)])
 def test_mostly_empty_tree(prec, tol):
     """N = 2000 on a level-7 tree (16384 leaves, most of them empty): boxes
