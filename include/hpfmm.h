@@ -77,7 +77,16 @@ typedef struct {
                            (16 or more charge vectors): 0 the FP32 FMA kernel,
                            1 the tensor cores (tcgen05 kind::tf32, three-term split
                            products accumulated in tensor memory) */
-  int reserved[3];      /* must be zero */
+  int adaptive;         /* 0: uniform tree (depth `levels`); 1: adaptive quadtree, in
+                           which a box is split while it holds more than leaf_size
+                           points, down to depth `levels` (0: automatic, at most 13).
+                           Free-space M2L over same-level V-lists, near field over
+                           the U-list extended by the W/X pairs (Section 3, the
+                           paper's adaptive tree over targets and image sources).
+                           Single and mixed precision; hpfmm_eval with one charge
+                           vector and hpfmm_update_points (other entry points return
+                           HPFMM_EUNSUPPORTED for adaptive plans). */
+  int reserved[2];      /* must be zero */
   double root_x0;       /* with root_side > 0: the root square of the tree is
                            [root_x0, root_x0 + root_side] x [0, root_side] instead of the
                            points' bounding square; it must contain every point
@@ -273,6 +282,17 @@ typedef struct {
   int64_t workspace_bytes;
 } hpfmm_plan_info;
 hpfmm_status hpfmm_get_info(const hpfmm_plan *plan, hpfmm_plan_info *info);
+
+/*
+ * hpfmm_get_adaptive_counts -- shape of an adaptive plan's tree (for checks):
+ * boxes[l] and leaves[l], l = 0..maxlev (host arrays of maxlev + 1 entries,
+ * zero beyond the tree), and in *depth (may be NULL) the deepest level that
+ * has a box.  A box is split into its non-empty children while it holds more
+ * than leaf_size points and its level is below opt.levels.  EINVAL for a
+ * uniform plan.  Synchronises the stream.
+ */
+hpfmm_status hpfmm_get_adaptive_counts(const hpfmm_plan *plan, int maxlev, int64_t *boxes,
+                                       int64_t *leaves, int *depth, void *stream);
 
 /*
  * hpfmm_get_order -- copy the plan's Morton ordering (for checks): keys[k] is

@@ -18,6 +18,9 @@ Contents
                                          respect to the charges and the positions,
                                          from direct sums and the symmetry of G.
 * ``morton_order``                    -- the tree ordering, for bit-exact checks.
+* ``adaptive_tree``                   -- boxes and leaves per level of the adaptive
+                                         quadtree (split while a box holds more than
+                                         leaf_size points), for bit-exact checks.
 * paper operators (S2M, ME evaluation, S2L, LE evaluation, M2M, L2L, M2L)
   written literally from Section 2.2, for operator-level pins (Example 1).
 
@@ -273,6 +276,30 @@ def morton_keys(x, y, x0, L):
     lib().hpo_morton_keys(len(x), _dp(x), _dp(y), float(x0), float(L),
                           keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
     return keys
+
+
+def adaptive_tree(keys, leaf_size, H):
+    """Shape of the adaptive quadtree over points with the given 60-bit Morton
+    keys (the paper's adaptive tree, Algorithm 1, with the leaf rule it leaves
+    unstated read as: the root holds every point; box (l, k), the points whose
+    key has the 2l-bit prefix k, is split into its non-empty children while it
+    holds more than leaf_size points and l < H).  Returns (boxes, leaves),
+    int64 arrays over the levels 0..H."""
+    keys = np.asarray(keys, np.uint64)
+    boxes = np.zeros(H + 1, np.int64)
+    leaves = np.zeros(H + 1, np.int64)
+    pref = np.zeros(1, np.uint64)
+    cnt = np.array([len(keys)], np.int64)
+    for l in range(H + 1):
+        boxes[l] = len(pref)
+        split = (cnt > leaf_size) & (l < H)
+        leaves[l] = int(np.count_nonzero(~split))
+        if not split.any():
+            break
+        # children: the distinct (l+1)-prefixes of the points of split boxes
+        inside = np.isin(keys >> np.uint64(2 * (30 - l)), pref[split])
+        pref, cnt = np.unique(keys[inside] >> np.uint64(2 * (30 - (l + 1))), return_counts=True)
+    return boxes, leaves
 
 
 # --------------------------------------------------------------------------

@@ -30,7 +30,8 @@ class HpfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tau_fp64", ctypes.c_double), ("levels", ctypes.c_int),
                 ("subtree_levels", ctypes.c_int), ("m2l_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3), ("root_x0", ctypes.c_double),
+                ("adaptive", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+                ("root_x0", ctypes.c_double),
                 ("root_side", ctypes.c_double)]
 
 
@@ -87,6 +88,7 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_autotune.argtypes = [vp, vp, i64, dbl, dbl, i32, dbl, i32, vp, ctypes.POINTER(Tuning)]
     L.hpfmm_selftest_tc_gemm.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     L.hpfmm_eval_targets.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+    L.hpfmm_get_adaptive_counts.argtypes = [vp, i32, vp, vp, vp, vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
@@ -94,7 +96,7 @@ def lib(build_if_missing: bool = False):
               "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc", "hpfmm_eval_adjoint",
               "hpfmm_batch_create", "hpfmm_eval_batched", "hpfmm_batch_captures",
               "hpfmm_batch_destroy", "hpfmm_autotune", "hpfmm_selftest_tc_gemm",
-              "hpfmm_eval_targets"):
+              "hpfmm_eval_targets", "hpfmm_get_adaptive_counts"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -153,7 +155,7 @@ class Plan:
 
 
 def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau_fp64=0.05,
-                 subtree_levels=0, m2l_mode=0, root=None):
+                 subtree_levels=0, m2l_mode=0, root=None, adaptive=False):
     """Build a plan for the points (x, y); see hpfmm_create in include/hpfmm.h."""
     x = _as_tensor(x)
     y = _as_tensor(y, x.device)
@@ -165,6 +167,7 @@ def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau
     opt.tau_fp64 = float(tau_fp64)
     opt.subtree_levels = int(subtree_levels)
     opt.m2l_mode = int(m2l_mode)
+    opt.adaptive = 1 if adaptive else 0
     if root is not None:  # (x0, side): the tree's root square
         opt.root_x0, opt.root_side = float(root[0]), float(root[1])
     h = ctypes.c_void_p()
@@ -394,6 +397,17 @@ def hpfmm_direct(xs, ys, qs, xt=None, yt=None, kappa=1.0, self_index=None, grad=
                               nt, kappa.real, kappa.imag, pot.data_ptr(),
                               g.data_ptr() if grad else None, _stream(dev)))
     return pot, g
+
+
+def hpfmm_get_adaptive_counts(plan, maxlev=13):
+    """(boxes[l], leaves[l]) for l = 0..maxlev and the depth of an adaptive plan's tree."""
+    boxes = np.zeros(maxlev + 1, np.int64)
+    leaves = np.zeros(maxlev + 1, np.int64)
+    depth = ctypes.c_int()
+    _check(lib().hpfmm_get_adaptive_counts(plan.handle, int(maxlev), boxes.ctypes.data,
+                                           leaves.ctypes.data, ctypes.byref(depth),
+                                           _stream(plan.device)))
+    return boxes, leaves, depth.value
 
 
 def hpfmm_get_info(plan):

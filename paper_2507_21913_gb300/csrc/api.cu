@@ -146,7 +146,10 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->t_l2l, pl->t_m2l, pl->t_refl, pl->t_rlog, pl->t_rlog0, pl->qs, pl->M,
                   pl->A, pl->B, pl->out_pot, pl->out_grad, pl->in_q, pl->status,
                   pl->t_binom, pl->geo, pl->t_m2l_pad, pl->adj, pl->mq, pl->mqsm,
-                  pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc};
+                  pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc,
+                  pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_parent, pl->ab_lvl, pl->ab_child,
+                  pl->ab_cut, pl->ab_off, pl->ab_idx, pl->ab_lev, pl->ab_btot, pl->ab_lrank,
+                  pl->ab_leaf};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -216,6 +219,9 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   }
   hpfmm_status s2 = tree_finish(pl, hgeo, st);
   if (s == HPFMM_OK) s = s2;
+  // the adaptive tree over the sorted points (it reads the coordinates for
+  // its leaf frames, so before the staging buffer goes)
+  if (s == HPFMM_OK && pl->adaptive) s = adaptive_build(pl, dx, dy, st);
   if (tmp) cudaFreeAsync(tmp, st);
   if (s != HPFMM_OK) return s;
   double kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
@@ -268,6 +274,18 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     set_last_error("hpfmm_create: unknown precision %d", (int)o.prec);
     return HPFMM_EINVAL;
   }
+  if (o.adaptive != 0 && o.adaptive != 1) {
+    set_last_error("hpfmm_create: adaptive must be 0 or 1");
+    return HPFMM_EINVAL;
+  }
+  if (o.adaptive && o.prec == HPFMM_FP64) {
+    set_last_error("hpfmm_create: the adaptive tree is implemented in single and mixed precision");
+    return HPFMM_EUNSUPPORTED;
+  }
+  if (o.adaptive && o.levels > kAdaptiveMaxLevel) {
+    set_last_error("hpfmm_create: an adaptive tree has at most %d levels", kAdaptiveMaxLevel);
+    return HPFMM_EINVAL;
+  }
   if (o.levels < 0 || o.levels > 15 || !(o.tau_fp64 >= 0) || o.subtree_levels < 0 ||
       o.subtree_levels > 4 || o.m2l_mode < 0 || o.m2l_mode > 1 || !(o.root_side >= 0) ||
       !isfinite(o.root_x0) || !isfinite(o.root_side)) {
@@ -287,9 +305,21 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   pl->root_side = o.root_side;
   pl->kre = kappa_re;
   pl->kim = kappa_im;
-  pl->H = o.levels > 0 ? o.levels : choose_levels(n, leaf_size);
-  pl->nleaf = 1 << (2 * pl->H);
-  pl->nbox = level_offset(pl->H + 1);
+  pl->adaptive = o.adaptive;
+  pl->leaf_cap = leaf_size;
+  if (pl->adaptive) {
+    // depth cap: the uniform depth for this leaf size plus five levels of
+    // refinement, at most kAdaptiveMaxLevel; the sort buckets at the uniform depth
+    const int hu = choose_levels(n, leaf_size);
+    pl->H = o.levels > 0 ? o.levels : (hu + 5 < kAdaptiveMaxLevel ? hu + 5 : kAdaptiveMaxLevel);
+    pl->Hsort = hu < pl->H ? hu : pl->H;
+    pl->nbox = 0;  // expansion arrays follow the tree (adaptive_build)
+  } else {
+    pl->H = o.levels > 0 ? o.levels : choose_levels(n, leaf_size);
+    pl->Hsort = pl->H;
+    pl->nbox = level_offset(pl->H + 1);
+  }
+  pl->nleaf = 1 << (2 * pl->Hsort);
   const int P1 = p + 1;
   const size_t m2 = (size_t)P1 * P1;
   const bool f32 = pl->prec != HPFMM_FP64;
@@ -321,12 +351,18 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->t_rlog0, sizeof(cd) * 70);
   ALLOC(pl->t_binom, sizeof(double) * (2 * p + 2) * (2 * p + 2));
   ALLOC(pl->qs, (f32 ? sizeof(float) : sizeof(double)) * n);
-  ALLOC(pl->M, csz * (size_t)pl->nbox * P1);
-  ALLOC(pl->A, csz * (size_t)pl->nbox * P1);
-  ALLOC(pl->B, csz * (size_t)pl->nbox * P1);
+  if (!pl->adaptive) {
+    ALLOC(pl->M, csz * (size_t)pl->nbox * P1);
+    ALLOC(pl->A, csz * (size_t)pl->nbox * P1);
+    ALLOC(pl->B, csz * (size_t)pl->nbox * P1);
+  }
   ALLOC(pl->status, sizeof(int));
   ALLOC(pl->geo, 8 * sizeof(double));
 #undef ALLOC
+  if (pl->adaptive) {
+    s = adaptive_alloc(pl);
+    if (s != HPFMM_OK) { free_plan(pl); return s; }
+  }
   s = fmm_set_smem_limits(p);
   if (s != HPFMM_OK) { free_plan(pl); return s; }
   {
@@ -468,6 +504,10 @@ extern "C" hpfmm_status hpfmm_eval_targets(hpfmm_plan *pl, const double *q, cons
       set_last_error("hpfmm_eval_targets: arrays must be device memory");
       return HPFMM_EINVAL;
     }
+  if (pl->adaptive) {
+    set_last_error("hpfmm_eval_targets: not implemented for adaptive plans");
+    return HPFMM_EUNSUPPORTED;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const bool single = pl->prec != HPFMM_FP64;
   if (!pl->tflag) HP_TRY(plan_dalloc(pl, (void **)&pl->tflag, 2 * sizeof(int)));

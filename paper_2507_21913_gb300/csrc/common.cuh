@@ -209,6 +209,10 @@ __device__ __forceinline__ double2 leaf_centre_at(double x0, double d, int ix, i
   return make_double2(__fma_rn(ix + 0.5, d, x0), __dmul_rn(iy + 0.5, d));
 }
 
+// deepest level of an adaptive tree (its dense per-level box index has
+// (4^(L+1) - 1) / 3 entries)
+constexpr int kAdaptiveMaxLevel = 13;
+
 // first box of level l in the level-concatenated box arrays: (4^l - 1) / 3
 __host__ __device__ __forceinline__ int64_t level_offset(int l) {
   return ((int64_t(1) << (2 * l)) - 1) / 3;
@@ -228,6 +232,29 @@ struct hpfmm_plan {
   double kre = 1, kim = 0;
   double x0 = 0, side = 1;
   double qscale = 1073741824.0;  // 2^30 / side rounded: the key quantisation scale
+  int Hsort = 0;     // level of the sort buckets (the leaf level H of a uniform tree)
+  // adaptive tree (hpfmm_options.adaptive): boxes level by level, Morton order
+  // within a level; see adaptive.cu
+  int adaptive = 0;
+  int leaf_cap = 32;       // split while a box holds more points than this
+  int64_t acap = 0;        // box capacity (a bound on the number of boxes)
+  int64_t ad_maxlev = 0;   // bound on the boxes of one level
+  int64_t ad_nbox = 0;     // boxes of the current tree
+  int64_t ad_mcap = 0;     // boxes the expansion arrays M, A, B hold
+  int ad_depth = 0;        // deepest level with a box
+  int ad_nleaf = 0;        // leaves of the current tree
+  int ad_lev[32] = {};     // host copy: first box of each level, levels 0..H+1
+  uint64_t *ab_key = nullptr;  // Morton key of a box at its level
+  int *ab_lo = nullptr, *ab_hi = nullptr;  // point range (tree order)
+  int *ab_parent = nullptr, *ab_lvl = nullptr;
+  int4 *ab_child = nullptr;    // children by type (ix & 1) | (iy & 1) << 1, -1: none
+  int4 *ab_cut = nullptr;      // split points of a box's range between its four children
+  int *ab_off = nullptr;       // build scratch: children offsets, leaf flags
+  int *ab_idx = nullptr;       // dense index per level: Morton key -> box (validated on use)
+  int *ab_lev = nullptr;       // device: first box of each level
+  int *ab_btot = nullptr;      // scan block totals
+  int *ab_lrank = nullptr;     // per point: rank of its leaf in tree order
+  int *ab_leaf = nullptr;      // leaves by rank
   int64_t nbox = 0;  // boxes over levels 0..H
   int nleaf = 0;     // 4^H
 
@@ -329,6 +356,10 @@ hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad
 // (p+1) complex floats each
 bool fmm_multi_supported(const hpfmm_plan *pl);
 // evaluation at nt separate targets (device arrays inside the root square)
+hpfmm_status adaptive_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st);
+hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
+                           cudaStream_t st);
+hpfmm_status adaptive_alloc(hpfmm_plan *pl);
 hpfmm_status fmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
                               const double *yt, int64_t nt, const int64_t *blist,
                               int64_t nbottom, double *pot, double *grad, cudaStream_t st);

@@ -605,7 +605,7 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
 
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
   const int64_t n = pl->n;
-  const int H = pl->H, nleaf = pl->nleaf;
+  const int H = pl->Hsort, nleaf = pl->nleaf;
   TreeTmp t;
   HP_TRY(tree_alloc(pl, t, st));
   pl->tree_tmp_bytes = 0;
@@ -628,7 +628,10 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   scan_add<<<nsb, 1024, 0, st>>>(t.btot, nleaf, pl->leaf_start);
   bucket_scatter<<<gb, tb, 0, st>>>(t.kb, t.slot, n, H, pl->leaf_start, pl->keys, t.vb);
   // the leaf sorts also put the points into tree order (permutation, coordinates)
-  const LeafGather lg{x, y, geo, H, pl->xs, pl->ys, pl->perm, pl->loc32, pl->yabs};
+  // (adaptive plans: only the permutation; their leaf frames follow the adaptive build)
+  const LeafGather lg = pl->adaptive
+                            ? LeafGather{x, y, geo, H, nullptr, nullptr, pl->perm, nullptr, nullptr}
+                            : LeafGather{x, y, geo, H, pl->xs, pl->ys, pl->perm, pl->loc32, pl->yabs};
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
       pl->leaf_start, nleaf, pl->keys, t.vb, t.big, t.lcount + nleaf, lg);
   leaf_sort<<<160, 256, 0, st>>>(pl->leaf_start, t.big, t.lcount + nleaf, pl->keys, t.vb, lg);

@@ -35,3 +35,17 @@ def sampled_closed(x, y, q, idx, kappa, procs=None):
     u = np.concatenate([r[0] for r in res])
     g = np.concatenate([r[1] for r in res])
     return u, g
+
+
+@functools.lru_cache(maxsize=None)
+def clustered_sampled(n, seed, kappa):
+    """The clustered workload and the oracle at 64 sampled points, half of
+    them with y < 0.06 (closed-form reaction kernel)."""
+    x, y, q = workloads.clustered(n, seed=seed)
+    near = np.flatnonzero(y < 0.06)
+    far = np.flatnonzero(y >= 0.06)
+    g0 = np.random.Generator(np.random.PCG64(1))
+    idx = np.sort(np.concatenate([g0.choice(near, 32, replace=False),
+                                  g0.choice(far, 32, replace=False)]))
+    u, g = sampled_closed(x, y, q, idx, kappa)
+    return x, y, q, idx, u, g

@@ -152,15 +152,8 @@ def test_clustered_4m_mixed_complex_kappa():
     with centres at y in (0.001, 0.05], 20% uniform; kappa = 1 + 0.5i, p = 20,
     single precision with the double-precision reaction near field for pairs
     with y_i + y_j < tau.  64 sampled targets, half of them with y < 0.06."""
-    n = 4_000_000
-    x, y, q = workloads.clustered(n, seed=0)
-    near = np.flatnonzero(y < 0.06)
-    far = np.flatnonzero(y >= 0.06)
-    g0 = np.random.Generator(np.random.PCG64(1))
-    idx = np.sort(np.concatenate([g0.choice(near, 32, replace=False),
-                                  g0.choice(far, 32, replace=False)]))
     kappa = 1.0 + 0.5j
-    u_ref, g_ref = oracle_cache.sampled_closed(x, y, q, idx, kappa)
+    x, y, q, idx, u_ref, g_ref = oracle_cache.clustered_sampled(4_000_000, 0, kappa)
     u, g, plan = run(x, y, q, kappa, 20, 32, prec="mixed", levels=11)
     assert rel(u[idx], u_ref) < 5e-6
     assert rel(g[idx], g_ref) < 2e-5
