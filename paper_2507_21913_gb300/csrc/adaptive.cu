@@ -38,6 +38,8 @@ namespace {
 
 constexpr int kScanB = 1024;
 constexpr int kAdWarps = 8;
+// the leaf kernel looks up 8 cells per ancestor level in at most four rounds of 32 lanes
+static_assert(8 * kAdaptiveMaxLevel <= 4 * 32, "ancestor-cell lookups exceed four rounds");
 
 inline unsigned cdiv_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -400,6 +402,102 @@ k_ad_m2l(int bfirst, int blast, int nbox, int p, AdGeom g, const cf *__restrict_
   B[e] = B[e] + conj(v);
 }
 
+// Free-space M2L in Hankel form (even p up to 20): moments scaled by 1/k!,
+// T'[r][k] = g_{r+k} of the offset class, outputs scaled by (-1)^{r+1}/r!
+// (the uniform tree's class vectors, staged in shared memory).  A block of
+// four warps takes 32 parent boxes and warp w their children of type w, so
+// that the lanes of a warp share every source offset and class vector (a
+// broadcast read); each lane accumulates its target's P1 outputs in
+// registers.  Parents of every level in one launch.
+__device__ __forceinline__ int ad_slot(int cls) {  // 7 x 7 offset class -> 0..39
+  const int r = cls / 7, c = cls % 7;
+  const int near_before = r < 2 ? 0 : (r > 4 ? 9 : (r - 2) * 3 + min(max(c - 2, 0), 3));
+  return cls - near_before;
+}
+
+template <int P1>
+__global__ void __launch_bounds__(128)
+k_ad_m2l_hk(int pfirst, int plast, int nbox, AdGeom g, const cf *__restrict__ Tpad,
+            const cd *__restrict__ logt, const int *__restrict__ idx,
+            const uint64_t *__restrict__ key, const int *__restrict__ lev,
+            const int *__restrict__ lvl, const int4 *__restrict__ child,
+            const cf *__restrict__ M, cf *__restrict__ A, cf *__restrict__ B) {
+  constexpr int GP = 2 * P1;
+  __shared__ cf Gs[40 * GP];
+  __shared__ float fac_in[P1], fac_out[P1], lgt[49];
+  for (int e = threadIdx.x; e < 40 * GP; e += blockDim.x)
+    Gs[e] = Tpad[(size_t)(e / GP) * 2 * GP + e % GP];
+  if (threadIdx.x < P1) {
+    double f = 1.0;
+    for (int i = 2; i <= (int)threadIdx.x; ++i) f *= (double)i;
+    fac_in[threadIdx.x] = (float)(1.0 / f);
+    fac_out[threadIdx.x] = (float)(((threadIdx.x & 1) ? 1.0 : -1.0) / f);
+  }
+  for (int c = threadIdx.x; c < 49; c += blockDim.x) lgt[c] = (float)logt[c].x;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = pfirst + (int)blockIdx.x * 32 + lane;
+  int c = -1;
+  if (P < plast) {
+    const int4 ch = child[P];
+    c = warp == 0 ? ch.x : (warp == 1 ? ch.y : (warp == 2 ? ch.z : ch.w));
+  }
+  if (!__any_sync(0xffffffffu, c >= 0)) return;
+  const int a = warp & 1, bb = warp >> 1;
+  int l = 2, ix = 0, iy = 0;
+  if (c >= 0) {
+    const uint64_t k = key[c];
+    l = lvl[c];
+    ix = box_ix(k);
+    iy = box_iy(k);
+  }
+  const float logd = (float)g.logd[l];
+  cf acc[P1];
+#pragma unroll
+  for (int r = 0; r < P1; ++r) acc[r] = mk(0.f, 0.f);
+  for (int dy = -2 - bb; dy <= 3 - bb; ++dy) {
+    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      const int s = c >= 0 ? ad_lookup(idx, key, lev, nbox, l, ix + dx, iy + dy) : -1;
+      if (!__any_sync(0xffffffffu, s >= 0)) continue;
+      if (s < 0) continue;
+      const int cls = (dy + 3) * 7 + (dx + 3);
+      const cf *G = Gs + ad_slot(cls) * GP;
+      cf m[P1];
+#pragma unroll
+      for (int k = 0; k < P1; ++k) m[k] = fac_in[k] * M[(size_t)s * P1 + k];
+      // anti-diagonals j = r + k: each g_j read once
+#pragma unroll
+      for (int j = 0; j < 2 * P1 - 1; ++j) {
+        const cf gj = G[j];
+#pragma unroll
+        for (int r = (j - P1 + 1 > 0 ? j - P1 + 1 : 0); r <= (j < P1 - 1 ? j : P1 - 1); ++r)
+          cfma(acc[r], gj, m[j - r]);
+      }
+      // M_0 ln|t d| on Re L_0 (in the scaled outputs L_0 = -L'_0)
+      acc[0].x -= m[0].x * (lgt[cls] + logd);
+    }
+  }
+  if (c < 0) return;
+  const float s = (float)(-0.5 / HP_TWO_PI);
+  const size_t e0 = (size_t)c * P1;
+#pragma unroll
+  for (int r = 0; r < P1; ++r) {
+    const cf v = (s * fac_out[r]) * acc[r];
+    A[e0 + r] = A[e0 + r] + v;
+    B[e0 + r] = B[e0 + r] + conj(v);
+  }
+}
+
+template <int P1>
+void launch_ad_m2l_hk(int pfirst, int plast, int nbox, const AdGeom &g, const cf *Tpad,
+                      const cd *logt, const hpfmm_plan *pl, const cf *M, cf *A, cf *B,
+                      cudaStream_t st) {
+  k_ad_m2l_hk<P1><<<cdiv_u(plast - pfirst, 32), 128, 0, st>>>(
+      pfirst, plast, nbox, g, Tpad, logt, pl->ab_idx, pl->ab_key, pl->ab_lev, pl->ab_lvl,
+      pl->ab_child, M, A, B);
+}
+
 // mirror M2L (image log and the reaction parts Phi_2^+ and Phi_2^-, Eqs.
 // metoleimage and truncatedM2Lcoef) for the boxes of rows 0 and 1, with the
 // tables of the uniform tree (21 classes per level)
@@ -530,6 +628,28 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
   const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
   const float i2pi = (float)(1.0 / HP_TWO_PI);
   (void)d;
+  // the near-field sources of D, looked up by the lanes in parallel: lane
+  // j < 9 takes cell j of the 3 x 3 around D (all leaves below it); the
+  // 8 cells around each ancestor of D (leaves only) in rounds of 32 lanes
+  const int nbA = lane < 9 ? ad_lookup(idx, key, lev, nbox, l, ix + lane % 3 - 1,
+                                       iy + lane / 3 - 1)
+                           : -1;
+  const unsigned maskA = __ballot_sync(0xffffffffu, nbA >= 0);
+  int candB[4];
+  unsigned maskB[4];
+#pragma unroll
+  for (int rd = 0; rd < 4; ++rd) {
+    const int j = rd * 32 + lane;
+    int cb = -1;
+    if (j < 8 * l) {
+      const int la = l - 1 - j / 8, o = j % 8, o9 = o < 4 ? o : o + 1;
+      const int C = ad_lookup(idx, key, lev, nbox, la, (ix >> (l - la)) + o9 % 3 - 1,
+                              (iy >> (l - la)) + o9 / 3 - 1);
+      if (C >= 0 && is_leaf(child[C])) cb = C;
+    }
+    candB[rd] = cb;
+    maskB[rd] = __ballot_sync(0xffffffffu, cb >= 0);
+  }
   for (int tb = lo[D]; tb < hi[D]; tb += 32) {
     const int i = tb + lane;
     const bool act = i < hi[D];
@@ -539,47 +659,46 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
     a.lf = a.gx = a.gy = a.li = a.gix = a.giy = 0.f;
     a.ur = a.grx = a.gry = mk(0.f, 0.f);
     // leaves at level >= l inside the 3 x 3 cells around D
-    for (int dy = -1; dy <= 1; ++dy) {
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int nb = ad_lookup(idx, key, lev, nbox, l, ix + dx, iy + dy);
-        if (nb < 0) continue;
-        const bool mir = iy == 0 && dy == 0;
-        const int r1 = min(rank[hi[nb]], nleaf);
-        for (int rr = rank[lo[nb]]; rr < r1; ++rr) {
-          const int C = leaf[rr];
-          const uint64_t kC = key[C];
-          const float2 o = ad_offset(g, lvl[C], box_ix(kC), box_iy(kC), l, ix, iy);
-          if (act) {
-            ad_free_range(loc, qs, lo[C], hi[C], i, me.x - o.x, me.y - o.y, a.lf, a.gx, a.gy);
-            if (mir)
-              for (int kk = lo[C]; kk < hi[C]; ++kk) {
-                const float2 v = loc[kk];
-                mirror_pair(make_float4(v.x + o.x, yabs[kk], qs[kk], 0.f), me.x, my, kap, kappa,
-                            tau, a);
-              }
-          }
+    for (unsigned mA = maskA; mA; mA &= mA - 1) {
+      const int jc = __ffs(mA) - 1;
+      const int nb = __shfl_sync(0xffffffffu, nbA, jc);
+      const bool mir = iy == 0 && jc / 3 == 1;
+      const int r1 = min(rank[hi[nb]], nleaf);
+      for (int rr = rank[lo[nb]]; rr < r1; ++rr) {
+        const int C = leaf[rr];
+        const uint64_t kC = key[C];
+        const float2 o = ad_offset(g, lvl[C], box_ix(kC), box_iy(kC), l, ix, iy);
+        if (act) {
+          ad_free_range(loc, qs, lo[C], hi[C], i, me.x - o.x, me.y - o.y, a.lf, a.gx, a.gy);
+          if (mir)
+            for (int kk = lo[C]; kk < hi[C]; ++kk) {
+              const float2 v = loc[kk];
+              mirror_pair(make_float4(v.x + o.x, yabs[kk], qs[kk], 0.f), me.x, my, kap, kappa,
+                          tau, a);
+            }
         }
       }
     }
     // coarser leaves next to an ancestor of D
-    for (int la = l - 1; la >= 0; --la) {
-      const int ax = ix >> (l - la), ay = iy >> (l - la);
-      for (int dy = -1; dy <= 1; ++dy) {
-        for (int dx = -1; dx <= 1; ++dx) {
-          if (dx == 0 && dy == 0) continue;
-          const int C = ad_lookup(idx, key, lev, nbox, la, ax + dx, ay + dy);
-          if (C < 0 || !is_leaf(child[C])) continue;
-          const float2 o = ad_offset(g, la, ax + dx, ay + dy, l, ix, iy);
-          const bool mir = ay == 0 && dy == 0;
-          if (act) {
-            ad_free_range(loc, qs, lo[C], hi[C], -1, me.x - o.x, me.y - o.y, a.lf, a.gx, a.gy);
-            if (mir)
-              for (int kk = lo[C]; kk < hi[C]; ++kk) {
-                const float2 v = loc[kk];
-                mirror_pair(make_float4(v.x + o.x, yabs[kk], qs[kk], 0.f), me.x, my, kap, kappa,
-                            tau, a);
-              }
-          }
+#pragma unroll
+    for (int rd = 0; rd < 4; ++rd) {
+      for (unsigned mB = maskB[rd]; mB; mB &= mB - 1) {
+        const int jl = __ffs(mB) - 1;
+        const int C = __shfl_sync(0xffffffffu, candB[rd], jl);
+        const int j = rd * 32 + jl;
+        const int la = l - 1 - j / 8, o = j % 8, o9 = o < 4 ? o : o + 1;
+        const int cy = (iy >> (l - la)) + o9 / 3 - 1;
+        const float2 off = ad_offset(g, la, (ix >> (l - la)) + o9 % 3 - 1, cy, l, ix, iy);
+        const bool mir = cy == 0 && (iy >> (l - la)) == 0;
+        if (act) {
+          ad_free_range(loc, qs, lo[C], hi[C], -1, me.x - off.x, me.y - off.y, a.lf, a.gx,
+                        a.gy);
+          if (mir)
+            for (int kk = lo[C]; kk < hi[C]; ++kk) {
+              const float2 v = loc[kk];
+              mirror_pair(make_float4(v.x + off.x, yabs[kk], qs[kk], 0.f), me.x, my, kap,
+                          kappa, tau, a);
+            }
         }
       }
     }
@@ -772,7 +891,23 @@ hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double 
   HP_CUDA(cudaMemsetAsync(B, 0, sizeof(cf) * (size_t)pl->ad_nbox * P1, st));
   pass_begin(pl, st, PASS_M2L_FREE);
   const int all0 = depth >= 2 ? lev[2] : 0, all1 = depth >= 2 ? lev[depth + 1] : 0;
-  if (all1 > all0)
+  // Hankel form over the parents of levels 1 .. depth - 1 (even p <= 20),
+  // else the dense form over the boxes of levels 2 .. depth
+  const int par0 = depth >= 2 ? lev[1] : 0, par1 = depth >= 2 ? lev[depth] : 0;
+  bool hankel = false;
+  if (all1 > all0 && p % 2 == 0 && p >= 4 && p <= 20) {
+    const cf *Tpad = (const cf *)pl->t_m2l_pad;
+    hankel = true;
+    switch (P1) {
+#define HP_AD_CASE(Q) \
+  case Q: launch_ad_m2l_hk<Q>(par0, par1, nbox, g, Tpad, logs, pl, M, A, B, st); break;
+      HP_AD_CASE(5) HP_AD_CASE(7) HP_AD_CASE(9) HP_AD_CASE(11) HP_AD_CASE(13)
+      HP_AD_CASE(15) HP_AD_CASE(17) HP_AD_CASE(19) HP_AD_CASE(21)
+#undef HP_AD_CASE
+      default: hankel = false;
+    }
+  }
+  if (all1 > all0 && !hankel)
     k_ad_m2l<<<cdiv_u((int64_t)(all1 - all0) * 32, kAdWarps * 32), kAdWarps * 32, 0, st>>>(
         all0, all1, nbox, p, g, Tfree, logs, pl->ab_idx, pl->ab_key, pl->ab_lev, pl->ab_lvl, M, A,
         B);
