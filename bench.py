@@ -319,26 +319,30 @@ def extra_workloads(args, dev, flush, check):
                                       g0.choice(far, 4, replace=False)]))
         u_ref, _ = oracle_sampled(x, y, q, idx, kap)
     e = {}
-    # the configured mixed-precision path, then single precision throughout
-    # (no double-precision reaction pairs) for comparison
-    for prec in ("mixed", "fp32"):
-        plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec=prec, levels=11)
+    # the configured mixed-precision path on the adaptive tree (the line's
+    # value), then single precision throughout and the uniform tree of depth
+    # 11 for comparison
+    for tag, prec, adaptive in (("", "mixed", True), ("fp32_", "fp32", True),
+                                ("uniform_", "mixed", False), ("uniform_fp32_", "fp32", False)):
+        plan = hp.hpfmm_create(xd, yd, kappa=kap, p=20, leaf_size=32, prec=prec,
+                               levels=0 if adaptive else 11, adaptive=adaptive)
 
         def step():
             hp.hpfmm_update_points(plan, xd, yd)
             hp.hpfmm_eval(plan, qd, out=(pot, grad))
         ms = _event_time(step, k, w, flush)
-        if prec == "mixed":
+        if not tag:
             e = {"workload": "clustered N=4e6 (80% in 64 clusters sigma 0.01 near y=0), "
-                             "kappa=1+0.5i, mixed precision, p=20, L=11, tree rebuilt every step",
+                             "kappa=1+0.5i, mixed precision, p=20, adaptive tree (leaves of at "
+                             "most 32 points), tree rebuilt every step",
                  "ms_per_step": ms, "value": float(n) * n / (ms / 1e3), "unit": UNIT}
-            key = ""
+            boxes, leaves, depth = hp.hpfmm_get_adaptive_counts(plan)
+            e["tree"] = {"boxes": int(boxes.sum()), "leaves": int(leaves.sum()), "depth": depth}
         else:
-            e["fp32_ms_per_step"] = ms
-            key = "fp32_"
+            e[tag + "ms_per_step"] = ms
         if check:
             u = pot.cpu().numpy()[idx]
-            e[key + "rel_err_pot"] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+            e[tag + "rel_err_pot"] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
             e["check_targets"] = len(idx)
         del plan
     out["clustered"] = e

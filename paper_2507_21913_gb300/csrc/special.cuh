@@ -156,10 +156,45 @@ __device__ inline void jn_range(cd P, int K, cd *J) {
   }
 }
 
+// J_0 and J_1 = 1 + P J_0 for |P| <= 1/8, double precision: the series form
+// of J_0 above, J_0 = e^{-P}[i pi - gamma - Log P - sum_{k>=1} P^k/(k k!)],
+// with e^{-P} and the sum as fixed-length polynomials in P (Horner).  At
+// |P| = 1/8 the first dropped terms are below 3e-18 relative.  Near-field
+// reaction pairs next to the boundary have |P| of a few leaf sides, so this
+// replaces a complex exponential and a loop of the general series there.
+__device__ __forceinline__ void j01_small(cd P, cd &J0, cd &J1) {
+  // sum_{k=1}^{10} P^k / (k k!)
+  cd S = mk(1.0 / (10.0 * 3628800.0), 0.0);
+  const double cs[9] = {1.0, 1.0 / 4.0, 1.0 / 18.0, 1.0 / 96.0, 1.0 / 600.0, 1.0 / 4320.0,
+                        1.0 / 35280.0, 1.0 / 322560.0, 1.0 / 3265920.0};
+#pragma unroll
+  for (int k = 8; k >= 0; --k) {
+    S = S * P;
+    S.x += cs[k];
+  }
+  S = S * P;
+  // e^{-P} = sum_{k=0}^{10} (-P)^k / k!
+  const cd mP = mk(-P.x, -P.y);
+  const double ce[10] = {1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0,
+                         1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0};
+  cd E = mk(1.0 / 3628800.0, 0.0);
+#pragma unroll
+  for (int k = 9; k >= 0; --k) {
+    E = E * mP;
+    E.x += ce[k];
+  }
+  const double lr = 0.5 * log(abs2(P)), th = atan2(P.y, P.x);
+  J0 = E * mk(-HP_EULER_GAMMA - lr - S.x, HP_PI - th - S.y);
+  const cd v = P * J0;
+  J1 = mk(1.0 + v.x, v.y);
+}
+
 // J_0 and J_1 = 1 + P J_0 (direct and near-field kernels), double precision
 __device__ inline void j01(cd P, cd &J0, cd &J1) {
   double a = sqrt(abs2(P));
-  if (a < 1.0) {
+  if (a <= 0.125) {
+    j01_small(P, J0, J1);
+  } else if (a < 1.0) {
     J0 = jn_direct(P, 0);
     cd v = P * J0;
     J1 = mk(1.0 + v.x, v.y);
