@@ -614,7 +614,7 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
           const int *__restrict__ idx, const uint64_t *__restrict__ key,
           const int *__restrict__ lev, const int *__restrict__ lo, const int *__restrict__ hi,
           const int *__restrict__ lvl, const int4 *__restrict__ child, AdGeom g, int p,
-          cd kappa, float tau, const cf *__restrict__ A, const cf *__restrict__ B,
+          KappaLog K, float tau, const cf *__restrict__ A, const cf *__restrict__ B,
           double *__restrict__ pot, double *__restrict__ grad) {
   const int lane = threadIdx.x & 31;
   const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -624,7 +624,7 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
   const int ix = box_ix(kD), iy = box_iy(kD);
   const int P1 = p + 1;
   const float d = g.d[l], invd = g.invd[l];
-  const cf kap = mk((float)kappa.x, (float)kappa.y);
+  const cf kap = mk((float)K.kappa.x, (float)K.kappa.y);
   const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
   const float i2pi = (float)(1.0 / HP_TWO_PI);
   (void)d;
@@ -673,8 +673,8 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
           if (mir)
             for (int kk = lo[C]; kk < hi[C]; ++kk) {
               const float2 v = loc[kk];
-              mirror_pair(make_float4(v.x + o.x, yabs[kk], qs[kk], 0.f), me.x, my, kap, kappa,
-                          tau, a);
+              mirror_pair(make_float4(v.x + o.x, yabs[kk], qs[kk], 0.f), me.x, my, kap, K, tau,
+                          a);
             }
         }
       }
@@ -697,7 +697,7 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
             for (int kk = lo[C]; kk < hi[C]; ++kk) {
               const float2 v = loc[kk];
               mirror_pair(make_float4(v.x + off.x, yabs[kk], qs[kk], 0.f), me.x, my, kap,
-                          kappa, tau, a);
+                          K, tau, a);
             }
         }
       }
@@ -934,7 +934,7 @@ hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double 
   k_ad_eval<<<cdiv_u((int64_t)nleaf * 32, kAdWarps * 32), kAdWarps * 32, 0, st>>>(
       pl->loc32, pl->yabs, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
       pl->ab_key, pl->ab_lev, pl->ab_lo, pl->ab_hi, pl->ab_lvl, pl->ab_child, g, p,
-      mk(pl->kre, pl->kim), tau, A, B, pot, grad);
+      kappa_log(pl->kre, pl->kim), tau, A, B, pot, grad);
   pass_end(pl, st, PASS_EVAL, 1);
   HP_LAUNCH_CHECK();
   return HPFMM_OK;

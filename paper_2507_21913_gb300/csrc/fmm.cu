@@ -1212,8 +1212,9 @@ struct SrcPt32 { float x, y, q, pad; };
 constexpr int kEvWarps = 8;
 
 __device__ __forceinline__ void mirror_batch(const float4 *buf, int cnt, int g, int ng, float mx,
-                                             float my, cf kap, cd kappa, float tau, NearAcc &a) {
-  for (int k = g; k < cnt; k += ng) mirror_pair(buf[k], mx, my, kap, kappa, tau, a);
+                                             float my, cf kap, const KappaLog &K, float tau,
+                                             NearAcc &a) {
+  for (int k = g; k < cnt; k += ng) mirror_pair(buf[k], mx, my, kap, K, tau, a);
 }
 
 __device__ __forceinline__ float xsum(float v, int from) {
@@ -1779,7 +1780,7 @@ __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
            const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-           float d, cd kappa, float tau, double *__restrict__ pot, double *__restrict__ grad,
+           float d, KappaLog K, float tau, double *__restrict__ pot, double *__restrict__ grad,
            RhsStride rs) {
   qs += blockIdx.y * rs.q;
   pot += blockIdx.y * rs.out;
@@ -1789,7 +1790,7 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = 1 << H;
   const int ix = blockIdx.x;  // leaf (ix, 0)
-  const cf kap = mk((float)kappa.x, (float)kappa.y);
+  const cf kap = mk((float)K.kappa.x, (float)K.kappa.y);
   const uint64_t leaf = box_morton(ix, 0);
   const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
   // source ranges of the bottom-row neighbours
@@ -1829,7 +1830,7 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
       }
       __syncthreads();
       const int cnt = min(kMirSrc, ns - base);
-      mirror_batch(src, cnt, warp, kEvWarps, me.x, me.y, kap, kappa, tau, acc);
+      mirror_batch(src, cnt, warp, kEvWarps, me.x, me.y, kap, K, tau, acc);
     }
     red[warp][0][lane] = acc.li;
     red[warp][1][lane] = acc.gix;
@@ -1873,7 +1874,7 @@ k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt
                  const double *__restrict__ yt, const float2 *__restrict__ loc,
                  const float *__restrict__ yabs, const float *__restrict__ qs,
                  const int *__restrict__ leaf_start, int H,
-                 double x0, double side, double qscale, cd kappa, float tau,
+                 double x0, double side, double qscale, KappaLog K, float tau,
                  double *__restrict__ pot, double *__restrict__ grad) {
   __shared__ float red[kEvWarps][9];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1885,7 +1886,7 @@ k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt
   const int ix = (int)(quantise(__dsub_rn(x, x0), side, qscale) >> (30 - H));
   const double2 c = leaf_centre_at(x0, dd, ix, 0);
   const float mx = (float)(x - c.x), my = (float)y;
-  const cf kap = mk((float)kappa.x, (float)kappa.y);
+  const cf kap = mk((float)K.kappa.x, (float)K.kappa.y);
   NearAcc acc;
   acc.lf = acc.gx = acc.gy = acc.li = acc.gix = acc.giy = 0.f;
   acc.ur = acc.grx = acc.gry = mk(0.f, 0.f);
@@ -1897,7 +1898,7 @@ k_mirror_targets(const int64_t *__restrict__ list, const double *__restrict__ xt
     const float ox = (float)(k - 1) * d;
     for (int j = s0 + (int)threadIdx.x; j < s1; j += blockDim.x) {
       const float2 v = loc[j];
-      mirror_pair(make_float4(v.x + ox, yabs[j], qs[j], 0.f), mx, my, kap, kappa, tau, acc);
+      mirror_pair(make_float4(v.x + ox, yabs[j], qs[j], 0.f), mx, my, kap, K, tau, acc);
     }
   }
   float v[9] = {acc.li,    acc.gix,   acc.giy,   acc.ur.x, acc.ur.y,
@@ -2096,7 +2097,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
       const float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
       k_mirror_targets<<<(unsigned)tw->nbottom, 32 * kEvWarps, 0, st>>>(
           tw->blist, tw->xt, tw->yt, pl->loc32, pl->yabs, (const float *)qs, pl->leaf_start, H,
-          pl->x0, pl->side, pl->qscale, kappa, tau, pot, grad);
+          pl->x0, pl->side, pl->qscale, kappa_log(pl->kre, pl->kim), tau, pot, grad);
       pass_end(pl, st, PASS_NEAR_MIRROR, 1);
     }
     HP_LAUNCH_CHECK();
@@ -2122,8 +2123,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     pass_end(pl, st, PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
     k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
-        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], kappa, tau,
-        pot, grad, rs);
+        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
+        kappa_log(pl->kre, pl->kim), tau, pot, grad, rs);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
   if (sizeof(R) == 8) pass_end(pl, st, PASS_EVAL, 1);

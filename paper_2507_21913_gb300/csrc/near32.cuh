@@ -40,7 +40,7 @@ struct NearAcc {
 // are not taken from the leaf frames: near the boundary Y = y_i + y_j would
 // lose its relative precision to the rounding of the leaf offsets.
 __device__ __forceinline__ void mirror_pair(const float4 s, float mx, float my, cf kap,
-                                            cd kappa, float tau, NearAcc &a) {
+                                            const KappaLog &K, float tau, NearAcc &a) {
   float dx = mx - s.x;
   float Y = my + s.y;
   float R2 = fmaf(dx, dx, Y * Y);
@@ -59,12 +59,13 @@ __device__ __forceinline__ void mirror_pair(const float4 s, float mx, float my, 
     a.grx = a.grx + s.z * mul_i(tp - tm);
     a.gry = a.gry - s.z * (tp + tm);
   } else {
-    cd spd = mk((double)Y, -(double)dx), smd = mk((double)Y, (double)dx);
+    const double X = dx, Yd = Y;
     cd J0p, J1p, J0m, J1m;
-    j01(kappa * spd, J0p, J1p);
-    j01(kappa * smd, J0m, J1m);
-    double q = s.z;
-    cd tp = cdiv(J1p, spd), tm = cdiv(J1m, smd);
+    j01_pm(K, X, Yd, J0p, J1p, J0m, J1m);
+    const double q = s.z;
+    // J_1 / s+- with s+- = Y -+ iX: one reciprocal of |s|^2 for both
+    const double inv = 1.0 / (X * X + Yd * Yd);
+    const cd tp = inv * (J1p * mk(Yd, X)), tm = inv * (J1m * mk(Yd, -X));
     a.ur = a.ur + to<float>(q * (J0p + J0m));
     a.grx = a.grx + to<float>(q * mul_i(tp - tm));
     a.gry = a.gry - to<float>(q * (tp + tm));

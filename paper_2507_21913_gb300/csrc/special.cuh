@@ -189,6 +189,75 @@ __device__ __forceinline__ void j01_small(cd P, cd &J0, cd &J1) {
   J1 = mk(1.0 + v.x, v.y);
 }
 
+// kappa with its logarithm ln|kappa| + i arg kappa, computed once on the host
+struct KappaLog {
+  cd kappa;
+  double lk, ak;
+};
+inline KappaLog kappa_log(double kre, double kim) {
+  KappaLog K;
+  K.kappa = mk(kre, kim);
+  K.lk = 0.5 * log(kre * kre + kim * kim);
+  K.ak = atan2(kim, kre);
+  return K;
+}
+
+__device__ inline void j01(cd P, cd &J0, cd &J1);
+
+// e^{-P} and sum_{k>=1} P^k/(k k!) by Horner, N + 1 and N terms (N <= 10)
+template <int N>
+__device__ __forceinline__ void exp_sum_poly(cd P, cd &E, cd &S) {
+  const double ce[11] = {1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0,
+                         1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0, 1.0 / 3628800.0};
+  const double cs[11] = {0.0, 1.0, 1.0 / 4.0, 1.0 / 18.0, 1.0 / 96.0, 1.0 / 600.0,
+                         1.0 / 4320.0, 1.0 / 35280.0, 1.0 / 322560.0, 1.0 / 3265920.0,
+                         1.0 / 36288000.0};
+  const cd mP = mk(-P.x, -P.y);
+  E = mk(ce[N], 0.0);
+  S = mk(cs[N], 0.0);
+#pragma unroll
+  for (int k = N - 1; k >= 1; --k) {
+    E = E * mP;
+    E.x += ce[k];
+    S = S * P;
+    S.x += cs[k];
+  }
+  E = E * mP;
+  E.x += 1.0;
+  S = S * P;
+}
+
+// J_0 and J_1 of both reaction arguments of one pair, P+ = kappa (Y - iX) and
+// P- = kappa (Y + iX) (Y > 0), double precision.  For |P| <= 1/8 the series
+// of j01_small, with Log P+- = Log kappa + ln|s| -+ i atan2(X, Y) (s+- = Y -+
+// iX are conjugate, and the sum of the arguments stays in (-pi/2, pi)), so
+// that one log and one atan2 serve both; 6 terms for |P| <= 1/64, 11 above
+// (dropped terms below 1e-16 relative).  Larger |P|: j01 twice.
+__device__ __forceinline__ void j01_pm(const KappaLog &K, double X, double Y, cd &J0p, cd &J1p,
+                                       cd &J0m, cd &J1m) {
+  const cd Pp = K.kappa * mk(Y, -X), Pm = K.kappa * mk(Y, X);
+  const double s2 = X * X + Y * Y, a2 = abs2(K.kappa) * s2;
+  if (a2 > 1.0 / 64.0) {
+    j01(Pp, J0p, J1p);
+    j01(Pm, J0m, J1m);
+    return;
+  }
+  const double lr = K.lk + 0.5 * log(s2), th = atan2(X, Y);
+  cd Ep, Sp, Em, Sm;
+  if (a2 <= 1.0 / 4096.0) {
+    exp_sum_poly<6>(Pp, Ep, Sp);
+    exp_sum_poly<6>(Pm, Em, Sm);
+  } else {
+    exp_sum_poly<10>(Pp, Ep, Sp);
+    exp_sum_poly<10>(Pm, Em, Sm);
+  }
+  J0p = Ep * mk(-HP_EULER_GAMMA - lr - Sp.x, HP_PI - (K.ak - th) - Sp.y);
+  J0m = Em * mk(-HP_EULER_GAMMA - lr - Sm.x, HP_PI - (K.ak + th) - Sm.y);
+  const cd vp = Pp * J0p, vm = Pm * J0m;
+  J1p = mk(1.0 + vp.x, vp.y);
+  J1m = mk(1.0 + vm.x, vm.y);
+}
+
 // J_0 and J_1 = 1 + P J_0 (direct and near-field kernels), double precision
 __device__ inline void j01(cd P, cd &J0, cd &J1) {
   double a = sqrt(abs2(P));
