@@ -135,6 +135,8 @@ static void free_plan(hpfmm_plan *pl) {
   }
   if (pl->ev_geo) cudaEventDestroy(pl->ev_geo);
   if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_join) cudaEventDestroy(pl->ev_join);
   if (pl->hgeo) cudaFreeHost(pl->hgeo);
   if (pl->tstate) {
     TimingState *ts = (TimingState *)pl->tstate;
@@ -149,7 +151,7 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc,
                   pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_parent, pl->ab_lvl, pl->ab_child,
                   pl->ab_cut, pl->ab_off, pl->ab_idx, pl->ab_lev, pl->ab_btot, pl->ab_lrank,
-                  pl->ab_leaf};
+                  pl->ab_leaf, pl->near};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -342,6 +344,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->leaf_start, sizeof(int) * (pl->nleaf + 1));
   if (f32) ALLOC(pl->loc32, sizeof(float2) * n);
   if (f32) ALLOC(pl->yabs, sizeof(float) * n);
+  if (f32 && !pl->adaptive) ALLOC(pl->near, sizeof(float4) * n);
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);
@@ -368,9 +371,16 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   s = fmm_set_smem_limits(p);
   if (s != HPFMM_OK) { free_plan(pl); return s; }
   {
-    cudaError_t ce = cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking);
+    // the side stream carries the reaction tables of a rebuild and the
+    // far-field chain of a split evaluation: the greatest priority
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t ce = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (ce == cudaSuccess)
+      ce = cudaStreamCreateWithPriority(&pl->side_stream, cudaStreamNonBlocking, prio_hi);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_geo, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaMallocHost((void **)&pl->hgeo, 8 * sizeof(double));
     if (ce != cudaSuccess) {
       set_last_error("hpfmm_create: %s", cudaGetErrorString(ce));

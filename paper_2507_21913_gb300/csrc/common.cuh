@@ -299,6 +299,9 @@ struct hpfmm_plan {
   // rebuild's synchronisation
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_geo = nullptr, ev_tables = nullptr;
+  // fork / join of the near field on the side stream (single precision)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  float4 *near = nullptr;  // near-field sums per point (sorted order)
   double *hgeo = nullptr;  // pinned host copy of geo, written by the tree build
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)

@@ -1227,6 +1227,7 @@ __device__ __forceinline__ float xsum(float v, int from) {
 constexpr int kTl = 4;             // target leaves per tile side
 constexpr int kTlP = kTl + 2;      // patch leaves per side
 constexpr int kTlCap = 3072;       // staged points per block
+constexpr int kLsBytes = 80;       // tile leaf starts (kTl^2 + 1 ints), 16-byte padded
 
 // Single-precision leaf evaluation with one target per lane.  A block takes
 // a 4 x 4 tile of leaves -- 16 consecutive Morton leaves, so its targets are
@@ -1253,16 +1254,22 @@ __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src, int lo
   }
 }
 
+// MODE 0: near field and L2P, outputs written.  MODE 1: near field only, its
+// three sums per point (sorted order) written to near[].  MODE 2: L2P plus
+// near[], outputs written (no staging).  Modes 1 and 2 split the kernel so
+// that the near field can run concurrently with the far-field passes.
+constexpr int kEvFused = 0, kEvNear = 1, kEvFar = 2;
+template <int MODE>
 __global__ void __launch_bounds__(kEvWarps * 32, 4)
 k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
           const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
           float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B,
-          double *__restrict__ pot, double *__restrict__ grad) {
+          double *__restrict__ pot, double *__restrict__ grad, float4 *__restrict__ near) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *src = reinterpret_cast<float4 *>(smem_raw);  // [kTlCap]
+  int *ls = reinterpret_cast<int *>(smem_raw);         // [kTl^2 + 1] tile leaf starts
+  float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap]
   int *pst = reinterpret_cast<int *>(src + kTlCap);    // [kTlP^2 + 1]
   int *pbeg = pst + kTlP * kTlP + 1;                   // [kTlP^2]
-  int *ls = pbeg + kTlP * kTlP;                        // [kTl^2 + 1] tile leaf starts
   const int P1 = p + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = 1 << H;
@@ -1270,7 +1277,7 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
   const int tx0 = (blockIdx.x % tps) * kTl, ty0 = (blockIdx.x / tps) * kTl;
   const int side = nx < kTl ? nx : kTl, nlt = side * side;
   const uint64_t L0 = box_morton(tx0, ty0);
-  if (warp == 0) {
+  if (MODE != kEvFar && warp == 0) {
     int c0 = 0, c1 = 0;
     for (int h = 0; h < 2; ++h) {
       const int pi = lane + 32 * h;
@@ -1299,7 +1306,7 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     ls[lane] = leaf_start[L0 + lane];
   }
   __syncthreads();
-  const bool staged = pst[kTlP * kTlP] <= kTlCap;
+  const bool staged = MODE != kEvFar && pst[kTlP * kTlP] <= kTlCap;
   if (staged) {
     for (int pi = warp; pi < kTlP * kTlP; pi += kEvWarps) {
       const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
@@ -1347,7 +1354,7 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
           }
         }
       }
-    } else if (act) {
+    } else if (MODE != kEvFar && act) {
       me = loc[i];
       for (int r = -1; r <= 1; ++r) {
         for (int c = -1; c <= 1; ++c) {
@@ -1371,6 +1378,17 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
       }
     }
     if (!act) continue;
+    if (MODE == kEvNear) {
+      near[i] = make_float4(lf, gx, gy, 0.f);
+      continue;
+    }
+    if (MODE == kEvFar) {
+      const float4 nv = near[i];
+      me = loc[i];
+      lf = nv.x;
+      gx = nv.y;
+      gy = nv.z;
+    }
     const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
     const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
     const cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
@@ -1394,7 +1412,7 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     }
   }
 }
-constexpr size_t kTpSmem = sizeof(float4) * kTlCap + sizeof(int) * (3 * kTlP * kTlP + 1 + kTl * kTl + 1);
+constexpr size_t kTpSmem = kLsBytes + sizeof(float4) * kTlCap + sizeof(int) * (2 * kTlP * kTlP + 1);
 
 // Multi-RHS leaf evaluation (single precision).  The free-space near-field
 // pair kernel -- log2 r^2 and (dx, dy) / r^2 -- is formed once per pair and
@@ -1977,7 +1995,26 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   k_gather_q<R><<<dim3(cdiv_u(n, 256), nr), 256, 0, st>>>(
       q, pl->perm, n, qs, mw ? (R *)mw->qsm : (R *)nullptr, mw ? mw->rp : 0);
   pass_end(pl, st, PASS_GATHER, 1);
-  pass_begin(pl, st, PASS_P2M);
+  // single precision, one RHS, the sources as targets: the free-space near
+  // field needs only the sorted points and charges, so it runs on the plan's
+  // side stream while this stream runs the far-field passes; L2P joins them
+  const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
+  const bool split = sizeof(R) == 4 && !mw && !tw && pl->near && pl->side_stream && pl->ev_fork;
+  // far-field chain: on the plan's high-priority side stream when split, so
+  // that its short dependent kernels take SMs first and the near field fills
+  // the rest
+  cudaStream_t fs = st;
+  if (split) {
+    HP_CUDA(cudaEventRecord(pl->ev_fork, st));
+    HP_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0));
+    fs = pl->side_stream;
+    pass_begin(pl, st, PASS_EVAL);
+    k_eval32p<kEvNear><<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
+        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
+        (const cf *)A, (const cf *)B, pot, grad, pl->near);
+    pass_end(pl, st, PASS_EVAL, 1);
+  }
+  pass_begin(pl, fs, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
   int ksub = H - 4;  // subtrees of 4^ksub leaves, at least 256 of them
   if (ksub > 4) ksub = 4;
@@ -1989,31 +2026,31 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (sizeof(R) == 8) {
     LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
     size_t shp2m = sizeof(cd) * P1 * 33 * kWarpsPerBlock;
-    k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, st>>>(
+    k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, fs>>>(
         lp, (const double *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cd *)M);
   } else {
     LeafPoints<float> lp{pl->loc32};
     if (mw)
       k_s2m_multi<kRhsChunk><<<dim3(cdiv_u((int64_t)pl->nleaf * P1, 256), mw->rp / kRhsChunk),
-                               256, 0, st>>>(pl->loc32, (const float *)mw->qsm, mw->rp, nr,
+                               256, 0, fs>>>(pl->loc32, (const float *)mw->qsm, mw->rp, nr,
                                              pl->leaf_start, H, lg.invd[H], p, (cf *)M, rs);
     else
       k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * ((P1 + kS2mGroup - 1) / kS2mGroup), 256),
-                            256, 0, st>>>(
+                            256, 0, fs>>>(
           lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, lg.invd[H], p, (cf *)M, rs);
   }
-  pass_end(pl, st, PASS_P2M, 1);
-  pass_begin(pl, st, PASS_M2M);
+  pass_end(pl, fs, PASS_P2M, 1);
+  pass_begin(pl, fs, PASS_M2M);
   if (ksub > 0) {
     size_t sm = upward_smem<R>(p, ksub);
     unsigned nb = (unsigned)(int64_t(1) << (2 * l0));
     if (sizeof(R) == 8) {
       LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
-      k_upward<double><<<nb, 256, sm, st>>>(lp, (const double *)qs, pl->leaf_start, H, ksub,
+      k_upward<double><<<nb, 256, sm, fs>>>(lp, (const double *)qs, pl->leaf_start, H, ksub,
                                             pl->x0, pl->side, p, (const cd *)Tm2m, (cd *)M, rs);
     } else {
       LeafPoints<float> lp{pl->loc32};
-      k_upward<float><<<dim3(nb, nr), 256, sm, st>>>(lp, (const float *)qs, pl->leaf_start, H,
+      k_upward<float><<<dim3(nb, nr), 256, sm, fs>>>(lp, (const float *)qs, pl->leaf_start, H,
                                                      ksub, pl->x0, pl->side, p,
                                                      (const cf *)Tm2m, (cf *)M, rs);
     }
@@ -2023,27 +2060,27 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // the small top levels in one block
   int nm2m = ksub > 0 ? 1 : 0;
   for (int l = l0 - 1; l >= kCoarseBig; --l, ++nm2m)
-    k_m2m_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, st>>>(
+    k_m2m_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, fs>>>(
         l, p, Tm2m, M, rs);
   const int lsmall = l0 - 1 < kCoarseBig - 1 ? l0 - 1 : kCoarseBig - 1;
   if (lsmall >= 1) {
-    k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(lsmall, p, Tm2m, M, rs);
+    k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, fs>>>(lsmall, p, Tm2m, M, rs);
     ++nm2m;
   }
-  pass_end(pl, st, PASS_M2M, nm2m);
+  pass_end(pl, fs, PASS_M2M, nm2m);
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
   bool patched = false, tc_m2l = false;
   if (H >= 2 && sizeof(R) == 4) {
-    pass_begin(pl, st, PASS_M2L_FREE);
+    pass_begin(pl, fs, PASS_M2L_FREE);
     if (mw && nr >= 16 && pl->m2l_mode == 1)
       tc_m2l = patched = launch_m2l_tc(p, H, lg, (const float *)pl->t_m2l_tc, logs, (const cf *)M, (cf *)A,
-                              (cf *)B, pl->status, st, nr, rs);
+                              (cf *)B, pl->status, fs, nr, rs);
     if (!patched)
       patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
-                                    pl->status, st, nr, rs, pl->leaf_start, tw ? 0 : 1);
-    pass_end(pl, st, PASS_M2L_FREE, patched ? (tc_m2l ? H - 1 : 1) : 0);
+                                    pl->status, fs, nr, rs, pl->leaf_start, tw ? 0 : 1);
+    pass_end(pl, fs, PASS_M2L_FREE, patched ? (tc_m2l ? H - 1 : 1) : 0);
   }
   if (mw && !patched) {
     set_last_error("multi-RHS passes need the patch M2L kernel (even p in 4..20)");
@@ -2053,37 +2090,40 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     double logd = log(pl->side / (double)(1 << l));
     if (l >= 2 && !patched) {
       dim3 g(cdiv_u(int64_t(1) << (2 * (l - 1)), 32), 4);
-      pass_begin(pl, st, PASS_M2L_FREE);
-      k_m2l_free<R><<<g, 128, shfree, st>>>(l, p, logd, Tfree, logs, M, A, B);
-      pass_end(pl, st, PASS_M2L_FREE, 1);
+      pass_begin(pl, fs, PASS_M2L_FREE);
+      k_m2l_free<R><<<g, 128, shfree, fs>>>(l, p, logd, Tfree, logs, M, A, B);
+      pass_end(pl, fs, PASS_M2L_FREE, 1);
     }
   }
   // the mirror M2L of all levels, after the free-space M2L it adds to
-  pass_begin(pl, st, PASS_M2L_MIRROR);
+  pass_begin(pl, fs, PASS_M2L_MIRROR);
   {
     unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
     size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
-    k_m2l_mirror_all<R><<<dim3(nb, nr), 128, sm, st>>>(H, p, lg, Timg, logs + 49, Treact, M, A,
+    k_m2l_mirror_all<R><<<dim3(nb, nr), 128, sm, fs>>>(H, p, lg, Timg, logs + 49, Treact, M, A,
                                                          B, rs);
   }
-  pass_end(pl, st, PASS_M2L_MIRROR, 1);
-  pass_begin(pl, st, PASS_L2L);
+  pass_end(pl, fs, PASS_M2L_MIRROR, 1);
+  pass_begin(pl, fs, PASS_L2L);
   int nl2l = 0;
   {
     const int lsmall2 = l0 < kCoarseBig - 1 ? l0 : kCoarseBig - 1;
     if (lsmall2 >= 2) {
-      k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, st>>>(lsmall2, p, Tl2l, A, B, rs);
+      k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, fs>>>(lsmall2, p, Tl2l, A, B, rs);
       ++nl2l;
     }
     for (int l = kCoarseBig; l <= l0; ++l, ++nl2l)
-      k_l2l_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, st>>>(
+      k_l2l_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, fs>>>(
           l, p, Tl2l, A, B, rs);
   }
   if (ksub > 0)
     k_downward<R><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256, downward_smem<R>(p, ksub),
-                    st>>>(H, ksub, p, Tl2l, A, B, rs, pl->leaf_start, tw ? 0 : 1);
-  pass_end(pl, st, PASS_L2L, nl2l + (ksub > 0 ? 1 : 0));
-  pass_begin(pl, st, PASS_EVAL);
+                    fs>>>(H, ksub, p, Tl2l, A, B, rs, pl->leaf_start, tw ? 0 : 1);
+  pass_end(pl, fs, PASS_L2L, nl2l + (ksub > 0 ? 1 : 0));
+  if (split) HP_CUDA(cudaEventRecord(pl->ev_join, fs));
+  // (split: the final L2P is timed with the downward pass, the near field on
+  // the side stream as the evaluation pass)
+  pass_begin(pl, st, split ? PASS_L2L : PASS_EVAL);
   // evaluation at the leaves + near field
   cd kappa = mk(pl->kre, pl->kim);
   if (tw) {
@@ -2114,13 +2154,17 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
                              32 * kEvWarps, 0, st>>>(
           pl->loc32, (const float *)mw->qsm, mw->rp, nr, pl->perm, pl->leaf_start, H, lg.d[H],
           lg.invd[H], p, (const cf *)A, (const cf *)B, rs, pot, grad);
-    } else {
-      const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
-      k_eval32p<<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
+    } else if (split) {
+      HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
+      k_eval32p<kEvFar><<<(unsigned)(tps * tps), 32 * kEvWarps, kLsBytes, st>>>(
           pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
-          (const cf *)A, (const cf *)B, pot, grad);
+          (const cf *)A, (const cf *)B, pot, grad, pl->near);
+    } else {
+      k_eval32p<kEvFused><<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
+          pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
+          (const cf *)A, (const cf *)B, pot, grad, nullptr);
     }
-    pass_end(pl, st, PASS_EVAL, 1);
+    pass_end(pl, st, split ? PASS_L2L : PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
     k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
         pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
@@ -2153,7 +2197,11 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
-  HP_CUDA(cudaFuncSetAttribute(k_eval32p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvFused>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTpSmem));
+  HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvNear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTpSmem));
+  HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvFar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFusedSmem));
