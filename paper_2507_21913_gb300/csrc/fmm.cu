@@ -1254,11 +1254,10 @@ __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src, int lo
   }
 }
 
-// MODE 0: near field and L2P, outputs written.  MODE 1: near field only, its
-// three sums per point (sorted order) written to near[].  MODE 2: L2P plus
-// near[], outputs written (no staging).  Modes 1 and 2 split the kernel so
-// that the near field can run concurrently with the far-field passes.
-constexpr int kEvFused = 0, kEvNear = 1, kEvFar = 2;
+// MODE 1: the near field only, its three sums per point (sorted order)
+// written to near[].  MODE 2: L2P plus near[], outputs written (no staging).
+// The split lets the near field run concurrently with the far-field passes.
+constexpr int kEvNear = 1, kEvFar = 2;
 template <int MODE>
 __global__ void __launch_bounds__(kEvWarps * 32, 4)
 k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
@@ -1999,7 +1998,11 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // field needs only the sorted points and charges, so it runs on the plan's
   // side stream while this stream runs the far-field passes; L2P joins them
   const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
-  const bool split = sizeof(R) == 4 && !mw && !tw && pl->near && pl->side_stream && pl->ev_fork;
+  const bool split = sizeof(R) == 4 && !mw && !tw;
+  if (split && !(pl->near && pl->side_stream && pl->ev_fork && pl->ev_join)) {
+    set_last_error("single-precision plan without its near-field buffer or side stream");
+    return HPFMM_ECUDA;
+  }
   // far-field chain: on the plan's high-priority side stream when split, so
   // that its short dependent kernels take SMs first and the near field fills
   // the rest
@@ -2154,15 +2157,11 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
                              32 * kEvWarps, 0, st>>>(
           pl->loc32, (const float *)mw->qsm, mw->rp, nr, pl->perm, pl->leaf_start, H, lg.d[H],
           lg.invd[H], p, (const cf *)A, (const cf *)B, rs, pot, grad);
-    } else if (split) {
+    } else {
       HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
       k_eval32p<kEvFar><<<(unsigned)(tps * tps), 32 * kEvWarps, kLsBytes, st>>>(
           pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
           (const cf *)A, (const cf *)B, pot, grad, pl->near);
-    } else {
-      k_eval32p<kEvFused><<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
-          pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
-          (const cf *)A, (const cf *)B, pot, grad, nullptr);
     }
     pass_end(pl, st, split ? PASS_L2L : PASS_EVAL, 1);
     pass_begin(pl, st, PASS_NEAR_MIRROR);
@@ -2197,8 +2196,6 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
-  HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvFused>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvNear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvFar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
