@@ -108,10 +108,13 @@ __global__ void k_ad_root(int n, uint64_t *key, int *lo, int *hi, int *parent, i
 }
 
 // boxes of level l: index entry, split decision and the split points of the
-// range between the four children (lower bounds of the child prefixes)
+// range between the four children: the first points of the child cells, read
+// from the sort's cell offsets down to its bucket level Hs, below that lower
+// bounds of the child key prefixes
 __global__ void __launch_bounds__(256)
 k_ad_split(int l, int H, int cap, int acap, int maxlev, const uint64_t *__restrict__ pkeys,
-           const int *__restrict__ lev, const uint64_t *__restrict__ key,
+           const int *__restrict__ cell_start, int Hs, const int *__restrict__ lev,
+           const uint64_t *__restrict__ key,
            const int *__restrict__ lo, const int *__restrict__ hi, int4 *__restrict__ cut,
            int *__restrict__ nch, int4 *__restrict__ child, int *__restrict__ idx) {
   const int b0 = lev[l], b1 = min(min(lev[l + 1], acap), b0 + maxlev);
@@ -129,6 +132,10 @@ k_ad_split(int l, int H, int cap, int acap, int maxlev, const uint64_t *__restri
       c[0] = a;
       c[4] = e;
       for (int t = 1; t <= 3; ++t) {
+        if (l + 1 <= Hs) {  // a cell of the sort's buckets or above: its first point
+          c[t] = cell_start[((k << 2) | (uint64_t)t) << (2 * (Hs - l - 1))];
+          continue;
+        }
         const uint64_t v = ((k << 2) | (uint64_t)t) << sh;
         int L = c[t - 1], R = e;
         while (L < R) {
@@ -614,7 +621,7 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
           const int *__restrict__ idx, const uint64_t *__restrict__ key,
           const int *__restrict__ lev, const int *__restrict__ lo, const int *__restrict__ hi,
           const int *__restrict__ lvl, const int4 *__restrict__ child, AdGeom g, int p,
-          KappaLog K, float tau, const cf *__restrict__ A, const cf *__restrict__ B,
+          const cf *__restrict__ A, const cf *__restrict__ B,
           double *__restrict__ pot, double *__restrict__ grad) {
   const int lane = threadIdx.x & 31;
   const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -624,7 +631,6 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
   const int ix = box_ix(kD), iy = box_iy(kD);
   const int P1 = p + 1;
   const float d = g.d[l], invd = g.invd[l];
-  const cf kap = mk((float)K.kappa.x, (float)K.kappa.y);
   const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
   const float i2pi = (float)(1.0 / HP_TWO_PI);
   (void)d;
@@ -654,7 +660,6 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
     const int i = tb + lane;
     const bool act = i < hi[D];
     const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
-    const float my = act ? yabs[i] : 0.f;
     NearAcc a;
     a.lf = a.gx = a.gy = a.li = a.gix = a.giy = 0.f;
     a.ur = a.grx = a.gry = mk(0.f, 0.f);
@@ -662,21 +667,13 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
     for (unsigned mA = maskA; mA; mA &= mA - 1) {
       const int jc = __ffs(mA) - 1;
       const int nb = __shfl_sync(0xffffffffu, nbA, jc);
-      const bool mir = iy == 0 && jc / 3 == 1;
       const int r1 = min(rank[hi[nb]], nleaf);
       for (int rr = rank[lo[nb]]; rr < r1; ++rr) {
         const int C = leaf[rr];
         const uint64_t kC = key[C];
         const float2 o = ad_offset(g, lvl[C], box_ix(kC), box_iy(kC), l, ix, iy);
-        if (act) {
+        if (act)
           ad_free_range(loc, qs, lo[C], hi[C], i, me.x - o.x, me.y - o.y, a.lf, a.gx, a.gy);
-          if (mir)
-            for (int kk = lo[C]; kk < hi[C]; ++kk) {
-              const float2 v = loc[kk];
-              mirror_pair(make_float4(v.x + o.x, yabs[kk], qs[kk], 0.f), me.x, my, kap, K, tau,
-                          a);
-            }
-        }
       }
     }
     // coarser leaves next to an ancestor of D
@@ -689,17 +686,9 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
         const int la = l - 1 - j / 8, o = j % 8, o9 = o < 4 ? o : o + 1;
         const int cy = (iy >> (l - la)) + o9 / 3 - 1;
         const float2 off = ad_offset(g, la, (ix >> (l - la)) + o9 % 3 - 1, cy, l, ix, iy);
-        const bool mir = cy == 0 && (iy >> (l - la)) == 0;
-        if (act) {
+        if (act)
           ad_free_range(loc, qs, lo[C], hi[C], -1, me.x - off.x, me.y - off.y, a.lf, a.gx,
                         a.gy);
-          if (mir)
-            for (int kk = lo[C]; kk < hi[C]; ++kk) {
-              const float2 v = loc[kk];
-              mirror_pair(make_float4(v.x + off.x, yabs[kk], qs[kk], 0.f), me.x, my, kap,
-                          K, tau, a);
-            }
-        }
       }
     }
     if (!act) continue;
@@ -714,11 +703,10 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
       db = db * wb + vb;
       vb = vb * wb + Bl[n];
     }
-    const float ur = va.x + vb.x - a.lf * c4 + a.li * c4 + a.ur.x * i2pi;
-    const float ui = va.y + vb.y + a.ur.y * i2pi;
-    const cf gxo = invd * (da + db) + mk((a.gix - a.gx + a.grx.x) * i2pi, a.grx.y * i2pi);
-    const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk((a.giy - a.gy + a.gry.x) * i2pi,
-                                                       a.gry.y * i2pi);
+    const float ur = va.x + vb.x - a.lf * c4;
+    const float ui = va.y + vb.y;
+    const cf gxo = invd * (da + db) + mk(-a.gx * i2pi, 0.f);
+    const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-a.gy * i2pi, 0.f);
     const int64_t o = perm[i];
     pot[2 * o] = f2d(ur);
     pot[2 * o + 1] = f2d(ui);
@@ -727,6 +715,88 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
       grad[4 * o + 1] = f2d(gxo.y);
       grad[4 * o + 2] = f2d(gyo.x);
       grad[4 * o + 3] = f2d(gyo.y);
+    }
+  }
+}
+
+// Image and reaction near field on the adaptive tree, added to the outputs of
+// k_ad_eval.  A leaf D of row 0 takes the leaves below the row-0 cells on both
+// sides of it at its level; every leaf takes the row-0 leaves next to its
+// row-0 ancestors (the near-field rule with the mirror image).  One warp per
+// leaf, one target per lane; a leaf without such sources returns after its
+// lookups (at most 3 + 2 per ancestor level, one round of the lanes).  Kept
+// apart from k_ad_eval, whose register count the double-precision branch of
+// the pair would otherwise raise.
+__global__ void __launch_bounds__(kAdWarps * 32)
+k_ad_mirror_near(const float2 *__restrict__ loc, const float *__restrict__ yabs,
+                 const float *__restrict__ qs, const int64_t *__restrict__ perm,
+                 const int *__restrict__ leaf, int nleaf, int nbox, const int *__restrict__ rank,
+                 const int *__restrict__ idx, const uint64_t *__restrict__ key,
+                 const int *__restrict__ lev, const int *__restrict__ lo,
+                 const int *__restrict__ hi, const int *__restrict__ lvl,
+                 const int4 *__restrict__ child, AdGeom g, KappaLog K, float tau,
+                 double *__restrict__ pot, double *__restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (r >= nleaf) return;
+  const int D = leaf[r], l = lvl[D];
+  const uint64_t kD = key[D];
+  const int ix = box_ix(kD), iy = box_iy(kD);
+  // row-0 cells beside D at its level (lanes 0..2), row-0 leaves beside its
+  // row-0 ancestors (lane j: level l - 1 - j/2, side -1 or +1)
+  const int nbA = (iy == 0 && lane < 3) ? ad_lookup(idx, key, lev, nbox, l, ix + lane - 1, 0) : -1;
+  const unsigned maskA = __ballot_sync(0xffffffffu, nbA >= 0);
+  int cb = -1;
+  if (lane < 2 * l) {
+    const int la = l - 1 - lane / 2, dx = (lane & 1) ? 1 : -1;
+    if ((iy >> (l - la)) == 0) {
+      const int C = ad_lookup(idx, key, lev, nbox, la, (ix >> (l - la)) + dx, 0);
+      if (C >= 0 && is_leaf(child[C])) cb = C;
+    }
+  }
+  const unsigned maskB = __ballot_sync(0xffffffffu, cb >= 0);
+  if (!maskA && !maskB) return;
+  const cf kap = mk((float)K.kappa.x, (float)K.kappa.y);
+  const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+  const float i2pi = (float)(1.0 / HP_TWO_PI);
+  for (int tb = lo[D]; tb < hi[D]; tb += 32) {
+    const int i = tb + lane;
+    const bool act = i < hi[D];
+    const float mx = act ? loc[i].x : 0.f, my = act ? yabs[i] : 0.f;
+    NearAcc a;
+    a.lf = a.gx = a.gy = a.li = a.gix = a.giy = 0.f;
+    a.ur = a.grx = a.gry = mk(0.f, 0.f);
+    for (unsigned m = maskA; m; m &= m - 1) {
+      const int nb = __shfl_sync(0xffffffffu, nbA, __ffs(m) - 1);
+      const int r1 = min(rank[hi[nb]], nleaf);
+      for (int rr = rank[lo[nb]]; rr < r1; ++rr) {
+        const int C = leaf[rr];
+        const uint64_t kC = key[C];
+        const float ox = ad_offset(g, lvl[C], box_ix(kC), box_iy(kC), l, ix, iy).x;
+        if (act)
+          for (int kk = lo[C]; kk < hi[C]; ++kk)
+            mirror_pair(make_float4(loc[kk].x + ox, yabs[kk], qs[kk], 0.f), mx, my, kap, K, tau,
+                        a);
+      }
+    }
+    for (unsigned m = maskB; m; m &= m - 1) {
+      const int j = __ffs(m) - 1;
+      const int C = __shfl_sync(0xffffffffu, cb, j);
+      const int la = l - 1 - j / 2, dx = (j & 1) ? 1 : -1;
+      const float ox = ad_offset(g, la, (ix >> (l - la)) + dx, 0, l, ix, iy).x;
+      if (act)
+        for (int kk = lo[C]; kk < hi[C]; ++kk)
+          mirror_pair(make_float4(loc[kk].x + ox, yabs[kk], qs[kk], 0.f), mx, my, kap, K, tau, a);
+    }
+    if (!act) continue;
+    const int64_t o = perm[i];
+    pot[2 * o] += (double)(a.li * c4 + a.ur.x * i2pi);
+    pot[2 * o + 1] += (double)(a.ur.y * i2pi);
+    if (grad) {
+      grad[4 * o + 0] += (double)((a.gix + a.grx.x) * i2pi);
+      grad[4 * o + 1] += (double)(a.grx.y * i2pi);
+      grad[4 * o + 2] += (double)((a.giy + a.gry.x) * i2pi);
+      grad[4 * o + 3] += (double)(a.gry.y * i2pi);
     }
   }
 }
@@ -783,9 +853,9 @@ hpfmm_status adaptive_build(hpfmm_plan *pl, const double *x, const double *y, cu
   for (int l = 0; l <= H; ++l) {
     const int64_t bound = level_bound(l, pl->n, cap);
     const unsigned gs = cdiv_u(bound, 256) < 4096 ? cdiv_u(bound, 256) : 4096;
-    k_ad_split<<<gs, 256, 0, st>>>(l, H, cap, acap, maxlev, pl->keys, pl->ab_lev, pl->ab_key,
-                                   pl->ab_lo, pl->ab_hi, pl->ab_cut, pl->ab_off, pl->ab_child,
-                                   pl->ab_idx);
+    k_ad_split<<<gs, 256, 0, st>>>(l, H, cap, acap, maxlev, pl->keys, pl->leaf_start, pl->Hsort,
+                                   pl->ab_lev, pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_cut,
+                                   pl->ab_off, pl->ab_child, pl->ab_idx);
     ++launches;
     if (l == H) break;
     k_ad_scan_part<<<cdiv_u(bound, kScanB), kScanB, 0, st>>>(pl->ab_lev, l, maxlev, pl->ab_off,
@@ -933,9 +1003,15 @@ hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double 
   const float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
   k_ad_eval<<<cdiv_u((int64_t)nleaf * 32, kAdWarps * 32), kAdWarps * 32, 0, st>>>(
       pl->loc32, pl->yabs, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
-      pl->ab_key, pl->ab_lev, pl->ab_lo, pl->ab_hi, pl->ab_lvl, pl->ab_child, g, p,
-      kappa_log(pl->kre, pl->kim), tau, A, B, pot, grad);
+      pl->ab_key, pl->ab_lev, pl->ab_lo, pl->ab_hi, pl->ab_lvl, pl->ab_child, g, p, A, B, pot,
+      grad);
   pass_end(pl, st, PASS_EVAL, 1);
+  pass_begin(pl, st, PASS_NEAR_MIRROR);
+  k_ad_mirror_near<<<cdiv_u((int64_t)nleaf * 32, kAdWarps * 32), kAdWarps * 32, 0, st>>>(
+      pl->loc32, pl->yabs, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
+      pl->ab_key, pl->ab_lev, pl->ab_lo, pl->ab_hi, pl->ab_lvl, pl->ab_child, g,
+      kappa_log(pl->kre, pl->kim), tau, pot, grad);
+  pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   HP_LAUNCH_CHECK();
   return HPFMM_OK;
 }
