@@ -580,14 +580,15 @@ k_ad_l2l(int b0, int nb, int p, const cf *__restrict__ Tl2l, const int *__restri
 }
 
 // offset of the centre of box (l, cx, cy) from the centre of box (lt, tx, ty)
-// in single precision: an exact integer multiple of half the finer side
+// in single precision: an exact integer multiple of half the finer side.
+// With levels <= 13 both products stay below 2^28 and the difference of two
+// touching boxes' centres below 2^15 half-sides, so 32-bit integers and the
+// conversion to float are exact (no 64-bit conversions on the FP64 pipe).
 __device__ __forceinline__ float2 ad_offset(const AdGeom &g, int l, int cx, int cy, int lt,
                                             int tx, int ty) {
   const int m = l > lt ? l : lt;
-  const long long nx = (long long)(2 * cx + 1) * (1ll << (m - l)) -
-                       (long long)(2 * tx + 1) * (1ll << (m - lt));
-  const long long ny = (long long)(2 * cy + 1) * (1ll << (m - l)) -
-                       (long long)(2 * ty + 1) * (1ll << (m - lt));
+  const int nx = (2 * cx + 1) * (1 << (m - l)) - (2 * tx + 1) * (1 << (m - lt));
+  const int ny = (2 * cy + 1) * (1 << (m - l)) - (2 * ty + 1) * (1 << (m - lt));
   const float h = 0.5f * g.d[m];
   return make_float2((float)nx * h, (float)ny * h);
 }
