@@ -922,6 +922,8 @@ hpfmm_status adaptive_build(hpfmm_plan *pl, const double *x, const double *y, cu
   return HPFMM_OK;
 }
 
+hpfmm_status adaptive_prepare() { return special_init_here(); }
+
 hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
                            cudaStream_t st) {
   HP_TRY(special_init_here());

@@ -369,6 +369,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     if (s != HPFMM_OK) { free_plan(pl); return s; }
   }
   s = fmm_set_smem_limits(p);
+  if (s == HPFMM_OK) s = fmm_prepare();
+  if (s == HPFMM_OK) s = adaptive_prepare();
   if (s != HPFMM_OK) { free_plan(pl); return s; }
   {
     // the side stream carries the reaction tables of a rebuild and the

@@ -363,6 +363,11 @@ hpfmm_status adaptive_build(hpfmm_plan *pl, const double *x, const double *y, cu
 hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
                            cudaStream_t st);
 hpfmm_status adaptive_alloc(hpfmm_plan *pl);
+// constant-memory set-up of the translation units that evaluate I_n on the
+// device (a synchronous copy, so done at plan creation and never inside a
+// stream capture such as the batched graph)
+hpfmm_status fmm_prepare();
+hpfmm_status adaptive_prepare();
 hpfmm_status fmm_eval_targets(hpfmm_plan *pl, const double *q, const double *xt,
                               const double *yt, int64_t nt, const int64_t *blist,
                               int64_t nbottom, double *pot, double *grad, cudaStream_t st);

@@ -2212,6 +2212,8 @@ hpfmm_status fmm_set_smem_limits(int p) {
   return HPFMM_OK;
 }
 
+hpfmm_status fmm_prepare() { return special_init_here(); }
+
 hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
                       cudaStream_t st) {
   if (pl->adaptive) return adaptive_eval(pl, q, pot, grad, st);

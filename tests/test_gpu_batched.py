@@ -115,3 +115,36 @@ def test_batch_rejects_duplicates_and_timed_plans():
     with pytest.raises(hp.HpfmmError):
         hp.hpfmm_eval_batched(batch, [q for _, q, _ in probs])
     hp.hpfmm_set_timing(p0, False)
+
+
+_FRESH = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_2507_21913_gb300 as hp, workloads
+t = lambda a: torch.tensor(a, device="cuda:0")
+plans, qs = [], []
+for i, (n, ad) in enumerate([(3000, False), (5000, True), (4000, False)]):
+    x, y, q = workloads.uniform(n, seed=40 + i)
+    plans.append(hp.hpfmm_create(t(x), t(y), kappa=1.0 + 0.5j, p=12, leaf_size=16,
+                                 prec="mixed", adaptive=ad))
+    qs.append(t(q))
+batch = hp.hpfmm_batch_create(plans)
+pots, grads = hp.hpfmm_eval_batched(batch, qs)       # the first evaluation of the process
+for plan, q, u in zip(plans, qs, pots):
+    u1, _ = hp.hpfmm_eval(plan, q)
+    assert torch.equal(u, u1)
+print("ok")
+"""
+
+
+def test_batched_graph_is_the_first_evaluation_of_a_process():
+    """A fresh process whose first evaluation is the captured graph, with a
+    uniform and an adaptive plan in it: the device constants of the I_n
+    evaluation are set up at plan creation, never inside the capture."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH.format(root=root)], capture_output=True,
+                       text=True, timeout=300, cwd=root)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
