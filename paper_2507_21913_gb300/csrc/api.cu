@@ -311,12 +311,12 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   pl->leaf_cap = leaf_size;
   if (pl->adaptive) {
     // depth cap: the uniform depth for this leaf size plus five levels of
-    // refinement, at most kAdaptiveMaxLevel.  The sort buckets lie three levels
+    // refinement, at most kAdaptiveMaxLevel.  The sort buckets lie two levels
     // below the uniform depth, so that clustered points still fall into
-    // buckets small enough for the warp sorts.
+    // buckets small enough for the warp and shared-memory sorts.
     const int hu = choose_levels(n, leaf_size);
     pl->H = o.levels > 0 ? o.levels : (hu + 5 < kAdaptiveMaxLevel ? hu + 5 : kAdaptiveMaxLevel);
-    pl->Hsort = hu + 3 < pl->H ? hu + 3 : pl->H;
+    pl->Hsort = hu + 2 < pl->H ? hu + 2 : pl->H;
     pl->nbox = 0;  // expansion arrays follow the tree (adaptive_build)
   } else {
     pl->H = o.levels > 0 ? o.levels : choose_levels(n, leaf_size);
