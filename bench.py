@@ -438,6 +438,39 @@ def extra_workloads(args, dev, flush, check):
     tun["tuning_seconds"] = time.perf_counter() - t0
     tun["workload"] = "uniform N=1e6, kappa=1, fp32, tol 1e-6 (probe charges, 256 sampled targets)"
     out["autotune"] = tun
+
+    # the configuration sweep of the uniform 1e6 workload: kappa x p in both
+    # precisions, tree rebuilt every step; errors at sampled targets (one
+    # oracle reference per kappa, shared by the orders and precisions)
+    xd, yd = t(x), t(y)
+    q = workloads.uniform(n, seed=0)[2]
+    qd = t(q)
+    pot = torch.empty(n, dtype=torch.complex128, device=dev)
+    grad = torch.empty((n, 2), dtype=torch.complex128, device=dev)
+    idx = workloads.sample_targets(n, 4, seed=1)
+    rows = []
+    for kap in (0.1, 1.0, 10.0):
+        u_ref = oracle_sampled(x, y, q, idx, kap)[0] if check else None
+        for prec in ("fp32", "fp64"):
+            for p in (8, 16, 24, 32):
+                plan = hp.hpfmm_create(xd, yd, kappa=kap, p=p, leaf_size=32, prec=prec)
+
+                def step():
+                    hp.hpfmm_update_points(plan, xd, yd)
+                    hp.hpfmm_eval(plan, qd, out=(pot, grad))
+                ms = _event_time(step, 3, 2, flush)
+                row = {"kappa": kap, "prec": prec, "p": p, "levels": plan.info()["levels"],
+                       "ms_per_step": ms, "value": float(n) * n / (ms / 1e3)}
+                if check:
+                    u = pot.cpu().numpy()[idx]
+                    err = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+                    row["rel_err_pot"] = err if np.isfinite(err) else None
+                rows.append(row)
+                del plan
+    out["sweep"] = {"workload": "uniform N=1e6, kappa in {0.1, 1, 10}, p in {8, 16, 24, 32}, fp32 "
+                                "and fp64, leaf_size 32, potentials and fields, tree rebuilt every "
+                                "step", "unit": UNIT, "check_targets": len(idx) if check else 0,
+                    "rows": rows}
     return out
 
 
