@@ -120,7 +120,7 @@ template <typename R>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_p2m(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
       double x0, double side, int p, cpx<R> *__restrict__ M) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   int P1 = p + 1;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw) + (size_t)warp * P1 * 33;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256)
 k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
          int k, double x0, double side, int p, const cpx<R> *__restrict__ Tm2m,
          cpx<R> *__restrict__ M, RhsStride rs) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int P1 = p + 1;
   M += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256)
 k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
            cpx<R> *__restrict__ B, RhsStride rs, const int *__restrict__ leaf_start,
            int skip_empty) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int P1 = p + 1;
   if (skip_empty) {  // a subtree without points needs no leaf expansions
     const int64_t lf0 = (int64_t)blockIdx.x << (2 * k);
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(128)
 k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
            const cd *__restrict__ logt, const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A,
            cpx<R> *__restrict__ B) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   int P1 = p + 1;
   cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);
   cpx<R> *Ms = Ts + P1 * P1;  // [k][33]
@@ -758,6 +758,9 @@ template <typename R>
 bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, const cd *logt,
                       const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st,
                       int nr, RhsStride rs, const int *leaf_start, int skip_empty) {
+  if constexpr (sizeof(R) == 8) {
+    return false;  // the patch form is the single-precision path only
+  } else {
   if (!Tpad) return false;
   int nb = patch_blocks(H);
   // the shared-memory attribute is set once per device and order (so that a
@@ -792,6 +795,7 @@ bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, co
     default: return false;
   }
 #undef HP_PATCH_CASE
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1025,7 +1029,7 @@ k_m2l_mirror_all(int H, int p, LevelGeom lgm, const cpx<R> *__restrict__ Timg,
                  const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
                  const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B,
                  RhsStride rs) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int P1 = p + 1;
   M += blockIdx.y * rs.m;
   A += blockIdx.y * rs.m;
@@ -1264,7 +1268,7 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
           const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
           float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B,
           double *__restrict__ pot, double *__restrict__ grad, float4 *__restrict__ near) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   int *ls = reinterpret_cast<int *>(smem_raw);         // [kTl^2 + 1] tile leaf starts
   float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap]
   int *pst = reinterpret_cast<int *>(src + kTlCap);    // [kTlP^2 + 1]
@@ -1405,9 +1409,9 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     const int64_t o = perm[i];
     reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
     if (grad) {
-      double4 gv;
+      double4_16a gv;
       gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
-      reinterpret_cast<double4 *>(grad)[o] = gv;
+      reinterpret_cast<double4_16a *>(grad)[o] = gv;
     }
   }
 }
@@ -1608,9 +1612,9 @@ k_eval32m(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp,
       const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-a.gy[c] * i2pi, 0.f);
       reinterpret_cast<double2 *>(pot + r * rs.out)[o] = make_double2(f2d(ur_), f2d(ui_));
       if (grad) {
-        double4 gv;
+        double4_16a gv;
         gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
-        reinterpret_cast<double4 *>(grad + 2 * r * rs.out)[o] = gv;
+        reinterpret_cast<double4_16a *>(grad + 2 * r * rs.out)[o] = gv;
       }
     }
   }
