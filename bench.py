@@ -613,7 +613,9 @@ def run_ours(args):
                          "ms_per_step": dt * 1e3,
                          "h2d_bytes_per_step": 3 * 8 * n, "d2h_bytes_per_step": (16 + 32) * n}
 
-    if not args.no_extra:
+    # the extra lines are single-GPU measurements of other configurations: at
+    # N = 1 only, so that a multi-GPU run holds its GPUs for the headline alone
+    if not args.no_extra and world == 1:
         result["extra"] = extra_workloads(args, dev, flush, check=not args.no_check and rank == 0)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
