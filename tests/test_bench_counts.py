@@ -1,0 +1,59 @@
+"""The algorithmic work counts behind bench.py's roofline figures, pinned by
+brute-force enumeration on small cases: near-field pairs of the uniform tree
+(leaf_pairs) and free-space V-list translations (vlist_translations)."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def cells(keys, H):
+    leaf = (np.asarray(keys, np.uint64) >> np.uint64(60 - 2 * H)).astype(np.int64)
+    ix = np.zeros_like(leaf)
+    iy = np.zeros_like(leaf)
+    for b in range(H):
+        ix |= ((leaf >> (2 * b)) & 1) << b
+        iy |= ((leaf >> (2 * b + 1)) & 1) << b
+    return ix, iy
+
+
+@pytest.mark.parametrize("kind,n,H", [("uniform", 700, 3), ("clustered", 900, 5), ("uniform", 1, 2)])
+def test_leaf_pairs_brute_force(kind, n, H):
+    if kind == "uniform":
+        x, y, _ = workloads.uniform(n, seed=31)
+    else:
+        x, y, _ = workloads.clustered(n, seed=32)
+    keys, _, _, _ = oracle.morton_order(x, y)
+    ix, iy = cells(keys, H)
+    dx = np.abs(ix[:, None] - ix[None, :])
+    dy = np.abs(iy[:, None] - iy[None, :])
+    adjacent = (dx <= 1) & (dy <= 1)
+    free = int(adjacent.sum()) - n  # ordered pairs, j != i
+    bottom = (iy[:, None] == 0) & (iy[None, :] == 0) & (dx <= 1)
+    mirror = int(bottom.sum())      # ordered pairs, j = i included (image and reaction terms)
+    assert bench.leaf_pairs(keys, H) == (free, mirror)
+
+
+@pytest.mark.parametrize("H", [2, 3, 4, 5])
+def test_vlist_translations_brute_force(H):
+    tot = 0
+    for l in range(2, H + 1):
+        nx = 1 << l
+        for ty in range(nx):
+            for tx in range(nx):
+                px, py = tx >> 1, ty >> 1
+                for sy in range(2 * (py - 1), 2 * (py + 1) + 2):
+                    for sx in range(2 * (px - 1), 2 * (px + 1) + 2):
+                        if not (0 <= sx < nx and 0 <= sy < nx):
+                            continue
+                        if abs(sx - tx) <= 1 and abs(sy - ty) <= 1:
+                            continue
+                        tot += 1
+    assert bench.vlist_translations(H) == tot
