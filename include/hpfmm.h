@@ -24,8 +24,13 @@
  * Conventions for every entry point
  *   - Pointers may be host or device memory (the library asks the CUDA
  *     runtime which); host buffers are staged through plan-owned device
- *     memory with stream-ordered copies.  All work is issued on `stream`
- *     (a cudaStream_t, NULL = legacy default stream).
+ *     memory with stream-ordered copies.  All work is ordered on `stream`
+ *     (a cudaStream_t, NULL = legacy default stream): parts of a rebuild
+ *     (reaction tables) and of a single-precision evaluation (the far-field
+ *     passes, concurrent with the near field) run on a plan-owned side stream
+ *     that is forked from `stream` and joined back into it with events, so
+ *     the results are complete when `stream` reaches the call's end.  A
+ *     plan's calls must not run concurrently with each other.
  *   - Outputs are in the caller's point order.  Complex values are stored as
  *     interleaved (re, im) doubles.
  *   - The caller owns every input and output buffer; a plan owns its tree,
