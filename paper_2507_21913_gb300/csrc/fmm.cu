@@ -1407,12 +1407,20 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     const cf gxo = invd * (da + db) + mk(-gx * i2pi, 0.f);
     const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-gy * i2pi, 0.f);
     const int64_t o = perm[i];
-    reinterpret_cast<double2 *>(pot)[o] = make_double2(f2d(ur_), f2d(ui_));
-    if (grad) {
-      double4_16a gv;
-      gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
-      reinterpret_cast<double4_16a *>(grad)[o] = gv;
+    double2 pv = make_double2(f2d(ur_), f2d(ui_));
+    double4_16a gv;
+    gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
+    if (MODE == kEvFar && iy == 0) {  // bottom row: the image/reaction sums are already there
+      const double2 pm = reinterpret_cast<const double2 *>(pot)[o];
+      pv.x += pm.x;
+      pv.y += pm.y;
+      if (grad) {
+        const double4_16a gm = reinterpret_cast<const double4_16a *>(grad)[o];
+        gv.x += gm.x; gv.y += gm.y; gv.z += gm.z; gv.w += gm.w;
+      }
     }
+    reinterpret_cast<double2 *>(pot)[o] = pv;
+    if (grad) reinterpret_cast<double4_16a *>(grad)[o] = gv;
   }
 }
 constexpr size_t kTpSmem = kLsBytes + sizeof(float4) * kTlCap + sizeof(int) * (2 * kTlP * kTlP + 1);
@@ -1802,7 +1810,7 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
            const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
            float d, KappaLog K, float tau, double *__restrict__ pot, double *__restrict__ grad,
-           RhsStride rs) {
+           RhsStride rs, int assign) {
   qs += blockIdx.y * rs.q;
   pot += blockIdx.y * rs.out;
   if (grad) grad += blockIdx.y * 2 * rs.out;
@@ -1870,13 +1878,18 @@ k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
         for (int w = 0; w < kEvWarps; ++w) v[c] += red[w][c][lane];
       }
       const int64_t o = perm[i];
-      pot[2 * o] += (double)(v[0] * c4 + v[3] * i2pi);
-      pot[2 * o + 1] += (double)(v[4] * i2pi);
+      // assign: written before the leaf outputs, which then add it (split
+      // evaluation); otherwise added to the leaf outputs
+      const double w0 = (double)(v[0] * c4 + v[3] * i2pi), w1 = (double)(v[4] * i2pi);
+      pot[2 * o] = assign ? w0 : pot[2 * o] + w0;
+      pot[2 * o + 1] = assign ? w1 : pot[2 * o + 1] + w1;
       if (grad) {
-        grad[4 * o + 0] += (double)((v[1] + v[5]) * i2pi);
-        grad[4 * o + 1] += (double)(v[6] * i2pi);
-        grad[4 * o + 2] += (double)((v[2] + v[7]) * i2pi);
-        grad[4 * o + 3] += (double)(v[8] * i2pi);
+        const double g0 = (double)((v[1] + v[5]) * i2pi), g1 = (double)(v[6] * i2pi);
+        const double g2 = (double)((v[2] + v[7]) * i2pi), g3 = (double)(v[8] * i2pi);
+        grad[4 * o + 0] = assign ? g0 : grad[4 * o + 0] + g0;
+        grad[4 * o + 1] = assign ? g1 : grad[4 * o + 1] + g1;
+        grad[4 * o + 2] = assign ? g2 : grad[4 * o + 2] + g2;
+        grad[4 * o + 3] = assign ? g3 : grad[4 * o + 3] + g3;
       }
     }
     __syncthreads();
@@ -2020,6 +2033,14 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
         (const cf *)A, (const cf *)B, pot, grad, pl->near);
     pass_end(pl, st, PASS_EVAL, 1);
+    // the bottom-row image/reaction sums need only the sources too: written
+    // now, added by the L2P kernel
+    pass_begin(pl, st, PASS_NEAR_MIRROR);
+    k_mirror32<<<dim3((unsigned)(1 << H), 1, kMirSplit), 32 * kEvWarps, 0, st>>>(
+        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
+        kappa_log(pl->kre, pl->kim), pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f, pot,
+        grad, rs, 1);
+    pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
   pass_begin(pl, fs, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
@@ -2168,11 +2189,13 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
           (const cf *)A, (const cf *)B, pot, grad, pl->near);
     }
     pass_end(pl, st, split ? PASS_L2L : PASS_EVAL, 1);
-    pass_begin(pl, st, PASS_NEAR_MIRROR);
-    k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
-        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
-        kappa_log(pl->kre, pl->kim), tau, pot, grad, rs);
-    pass_end(pl, st, PASS_NEAR_MIRROR, 1);
+    if (!split) {
+      pass_begin(pl, st, PASS_NEAR_MIRROR);
+      k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
+          pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
+          kappa_log(pl->kre, pl->kim), tau, pot, grad, rs, 0);
+      pass_end(pl, st, PASS_NEAR_MIRROR, 1);
+    }
   }
   if (sizeof(R) == 8) pass_end(pl, st, PASS_EVAL, 1);
   HP_LAUNCH_CHECK();
