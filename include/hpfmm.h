@@ -88,8 +88,9 @@ typedef struct {
                            Free-space M2L over same-level V-lists, near field over
                            the U-list extended by the W/X pairs (Section 3, the
                            paper's adaptive tree over targets and image sources).
-                           Single and mixed precision; hpfmm_eval with one charge
-                           vector and hpfmm_update_points (other entry points return
+                           Single and mixed precision, p <= 31; hpfmm_eval (one pass
+                           set per charge vector), hpfmm_eval_adjoint, batched graphs
+                           and hpfmm_update_points (hpfmm_eval_targets returns
                            HPFMM_EUNSUPPORTED for adaptive plans). */
   int reserved[2];      /* must be zero */
   double root_x0;       /* with root_side > 0: the root square of the tree is

@@ -616,8 +616,8 @@ __device__ __forceinline__ void ad_free_range(const float2 *__restrict__ loc,
 // to row 0.  One warp per leaf, one target per lane; every lane runs the same
 // source loops.  Outputs in the caller's order.
 __global__ void __launch_bounds__(kAdWarps * 32)
-k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ yabs,
-          const float *__restrict__ qs, const int64_t *__restrict__ perm,
+k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ qs,
+          const int64_t *__restrict__ perm,
           const int *__restrict__ leaf, int nleaf, int nbox, const int *__restrict__ rank,
           const int *__restrict__ idx, const uint64_t *__restrict__ key,
           const int *__restrict__ lev, const int *__restrict__ lo, const int *__restrict__ hi,
@@ -1005,7 +1005,7 @@ hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double 
   pass_begin(pl, st, PASS_EVAL);
   const float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
   k_ad_eval<<<cdiv_u((int64_t)nleaf * 32, kAdWarps * 32), kAdWarps * 32, 0, st>>>(
-      pl->loc32, pl->yabs, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
+      pl->loc32, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
       pl->ab_key, pl->ab_lev, pl->ab_lo, pl->ab_hi, pl->ab_lvl, pl->ab_child, g, p, A, B, pot,
       grad);
   pass_end(pl, st, PASS_EVAL, 1);

@@ -284,6 +284,10 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     set_last_error("hpfmm_create: the adaptive tree is implemented in single and mixed precision");
     return HPFMM_EUNSUPPORTED;
   }
+  if (o.adaptive && p > 31) {  // the adaptive M2L kernels map output orders to lanes
+    set_last_error("hpfmm_create: the adaptive tree supports p <= 31");
+    return HPFMM_EUNSUPPORTED;
+  }
   if (o.adaptive && o.levels > kAdaptiveMaxLevel) {
     set_last_error("hpfmm_create: an adaptive tree has at most %d levels", kAdaptiveMaxLevel);
     return HPFMM_EINVAL;

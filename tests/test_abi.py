@@ -118,6 +118,9 @@ def test_adaptive_option_checks_without_gpu(library):
     with pytest.raises(hp.HpfmmError) as e:
         hp.hpfmm_create(x, y, prec="fp32", levels=14, adaptive=True)
     assert e.value.status == hp.HPFMM_EINVAL
+    with pytest.raises(hp.HpfmmError) as e:
+        hp.hpfmm_create(x, y, prec="fp32", p=32, adaptive=True)
+    assert e.value.status == hp.HPFMM_EUNSUPPORTED
     opt = hp.Options()
     library.hpfmm_default_options(__import__("ctypes").byref(opt))
     assert opt.adaptive == 0 and list(opt.reserved) == [0, 0]

@@ -61,6 +61,16 @@ def test_uniform_2000_all_targets(prec, leaf):
     assert rel(g, g_ref) < 5e-5
 
 
+@pytest.mark.parametrize("p", [13, 25])
+def test_dense_form_m2l_odd_and_large_p(p):
+    """Odd p and p > 20 take the dense-form adaptive M2L (lanes over output
+    orders) instead of the Hankel-form kernel."""
+    x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
+    u, g, _ = run(x, y, q, 1.0, p, 8)
+    assert rel(u, u_ref) < 5e-6
+    assert rel(g, g_ref) < 5e-5
+
+
 @pytest.mark.parametrize("leaf", [4, 16, 64])
 def test_clustered_deep_tree_vs_oracle(leaf):
     """N = 20000 clustered at the boundary, kappa = 1 + 0.5i, p = 16: leaves
