@@ -57,3 +57,28 @@ def test_vlist_translations_brute_force(H):
                             continue
                         tot += 1
     assert bench.vlist_translations(H) == tot
+
+
+def test_roofline_arithmetic():
+    """achieved = algorithmic work per launch / per-launch time, frac =
+    achieved / peak; the dominant single-kernel pass is the one reported."""
+    class A:
+        n, p, prec = 1_000_000, 12, "fp32"
+    launches = {"eval": 10, "m2l_free": 10, "m2m": 20}
+    passes = {"eval": 1.5, "m2l_free": 1.2, "m2m": 3.0}  # ms over 10 steps; m2m is not single-kernel
+    peaks = {"sm_max_mhz": 2000.0}
+    npairs = 100_000_000
+    r = bench.roofline(passes, launches, A, npairs, 8, peaks)
+    t = 1.5e-3 / 10
+    assert r["kernel"].startswith(bench.SINGLE_KERNEL["eval"][0])
+    assert r["achieved"] == pytest.approx(2.0 * npairs / t / 1e12)
+    assert r["peak"] == pytest.approx(16 * 152 * 2.0e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["per_launch_ms"] == pytest.approx(0.15)
+    assert r["traffic"] == bench.NCU_TRAFFIC[(bench.SINGLE_KERNEL["eval"][0], A.n, A.p, 8, A.prec)]
+    # M2L dominant: 8 (p+1)^2 flops per translation against the FP32 FMA peak
+    passes = {"eval": 1.0, "m2l_free": 1.2}
+    r = bench.roofline(passes, launches, A, npairs, 8, peaks)
+    t = 1.2e-3 / 10
+    assert r["achieved"] == pytest.approx(8.0 * 13 * 13 * bench.vlist_translations(8) / t / 1e12)
+    assert r["peak"] == pytest.approx(128 * 2 * 152 * 2.0e9 / 1e12)
