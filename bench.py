@@ -214,8 +214,9 @@ def roofline(passes_ms, launches, args, npairs, H, peaks):
         ops = 2.0 * npairs
         peak = 16 * sms * f_ghz * 1e9 / 1e12
         achieved = ops / t / 1e12
-        return {"kernel": name + " (free-space near field, on the plan's side stream "
-                                 "concurrent with the far-field passes)", "bound": "alu",
+        return {"kernel": name + " (free-space near field, on the caller's stream concurrent "
+                                 "with the far-field passes on the plan's side stream)",
+                "bound": "alu",
                 "unit": "TOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                 "traffic": _traffic(name, args, H),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
