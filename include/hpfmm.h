@@ -92,7 +92,19 @@ typedef struct {
                            set per charge vector), hpfmm_eval_adjoint, batched graphs
                            and hpfmm_update_points (hpfmm_eval_targets returns
                            HPFMM_EUNSUPPORTED for adaptive plans). */
-  int reserved[2];      /* must be zero */
+  int async_update;     /* 0 (default): hpfmm_update_points waits for the device once,
+                           after the tree build, and returns EINVAL / EUNSUPPORTED
+                           for invalid points synchronously.  1: it does not wait;
+                           the tree build writes the root square and the level
+                           geometry on the device, where the evaluation kernels
+                           read them, invalid points (non-finite, y <= 0) and an
+                           out-of-range |kappa| * side are reported by the next
+                           hpfmm_sync (HPFMM_EINVAL / HPFMM_EUNSUPPORTED), and the
+                           outputs of an evaluation on such a tree are undefined
+                           (finite or not; no memory outside the plan's buffers is
+                           touched).  Uniform trees only (adaptive plans always
+                           wait). */
+  int reserved[1];      /* must be zero */
   double root_x0;       /* with root_side > 0: the root square of the tree is
                            [root_x0, root_x0 + root_side] x [0, root_side] instead of the
                            points' bounding square; it must contain every point
@@ -217,16 +229,18 @@ hpfmm_status hpfmm_batch_destroy(hpfmm_batch *batch);
  * does not tune the tree; this entry point has no counterpart there).
  *   x, y     : n device doubles (the points), n >= 64.
  *   prec     : HPFMM_FP64 / HPFMM_FP32 / HPFMM_MIXED.
- *   tol      : target relative L2 error of the potential.
+ *   tol      : target relative L2 error, of the potential and of its gradient.
  *   nsample  : number of sampled targets (>= 8) for the error estimate.
  * A probe charge vector (a hash of the point index, uniform in [-1, 1)) is
  * evaluated by the FMM and, at every (n / nsample)-th point, by hpfmm_direct in
- * double precision.  The smallest even p (4..40 in FP64, 4..20 otherwise)
- * whose sampled error meets tol is taken (met = 1); if none does, the most
- * accurate one (met = 0).  Then the leaf level (default level +-1) and the
- * subtree depth (automatic or 1..4) are chosen as the fastest
- * hpfmm_update_points + hpfmm_eval, timed with CUDA events, among the
- * configurations whose error stays within tol.  Allocates and frees its own
+ * double precision; a configuration's error is the larger of the sampled
+ * relative L2 errors of the potential and of the gradient.  For each leaf
+ * level (the default level from n / 32 and one level either side) the
+ * smallest even p (4..40) whose error meets tol is
+ * taken and hpfmm_update_points + hpfmm_eval is timed with CUDA events; the
+ * fastest wins (met = 1).  If no configuration meets tol, the most accurate
+ * one seen is returned (met = 0).  The subtree depth (automatic or 1..4) is
+ * then chosen by timing the winner.  Allocates and frees its own
  * device memory and synchronises the stream.  Use the result with
  * hpfmm_create(p, opt.levels = levels, opt.subtree_levels = subtree_levels).
  */
@@ -237,7 +251,7 @@ typedef struct {
   int met;             /* 1 if est_rel_err <= tol */
   double mean_leaf;    /* n / 4^levels */
   double est_rel_err;  /* sampled relative L2 error of the chosen configuration */
-  double ms_per_eval;  /* update_points + eval, potentials only */
+  double ms_per_eval;  /* update_points + eval, potentials and gradients */
   int nsample;
 } hpfmm_tuning;
 hpfmm_status hpfmm_autotune(const double *x, const double *y, int64_t n, double kappa_re,
@@ -330,22 +344,25 @@ hpfmm_status hpfmm_sync(hpfmm_plan *plan, void *stream);
 /*
  * hpfmm_tree_order_noalloc -- the tree ordering of hpfmm_get_order (sorted
  * 60-bit Morton keys and the permutation to the caller's order) computed
- * without any device allocation, for callers that cannot allocate device
- * memory (for example inside a stream capture that must stay free of
- * allocations, or under a runtime that owns every allocation).  The paper has
- * no counterpart: this is a service entry point of the library.
- *   x, y   : n doubles each, DEVICE memory, y > 0, finite.
+ * without any device allocation, for callers that cannot let a library
+ * allocate device memory (a runtime that owns every device allocation, or a
+ * process that must not grow its device memory use once it runs).  The paper
+ * has no counterpart: this is a service entry point of the library.
+ *   x, y   : n doubles each, device memory of the CURRENT device, y > 0,
+ *            finite.
  *   n      : 1 <= n <= 65536 (larger n is rejected with HPFMM_EINVAL).
  *   levels : leaf level used to bucket the points, 1..8 (the result does not
- *            depend on it).
- *   keys   : n uint64, perm: n int64, DEVICE memory, written in tree order.
- * All temporaries live in one static device array of 2.5 MiB that every GPU
- * holding the library keeps until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make
- * the first call before any stream capture.  Every call reuses the same
- * array: calls that overlap on the GPU (several streams, several threads)
- * race and must be serialised by the caller.  Synchronises the stream (the
- * validity check is reported synchronously).
+ *            depend on it; leaves of any size are sorted on the device).
+ *   keys   : n uint64, perm: n int64, device memory of the current device,
+ *            written in tree order.
+ * Pointers that are not device memory of the current device are rejected
+ * with HPFMM_EINVAL.  All temporaries live in one static device array of
+ * 2.5 MiB that every GPU holding the library keeps until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress).  Every call reuses the same array: calls that
+ * overlap on the GPU (several streams, several threads) race and must be
+ * serialised by the caller.  The call reads the points' validity flag back
+ * to the host, so it synchronises `stream` before it returns.
  */
 hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *y, int64_t n, int levels,
                                       uint64_t *keys, int64_t *perm, void *stream);
@@ -371,6 +388,30 @@ hpfmm_status hpfmm_selftest_wait_timeout(void *stream);
  */
 hpfmm_status hpfmm_selftest_tc_gemm(const float *A, const float *B, float *D, int n, int k,
                                     int split, void *stream);
+
+/*
+ * hpfmm_measure_alu_peaks -- throughput of the arithmetic pipes that bound the
+ * library's kernels, measured on the current device (no counterpart in the
+ * paper; the denominators of the roofline fractions the benchmark reports):
+ *   mufu_ops_per_s    special-function unit: lg2.approx.f32 + rcp.approx.f32,
+ *                     the two SFU operations of a single-precision near-field
+ *                     pair, counted as one operation each;
+ *   ffma_flops_per_s  FP32 fused multiply-add, 2 flops each;
+ *   dfma_flops_per_s  FP64 fused multiply-add, 2 flops each.
+ * Each kernel runs 8 independent chains per thread on (multiprocessors x
+ * resident blocks) blocks of 256 threads; the rate is the best of 5 timed
+ * launches (CUDA events on `stream`).  *_mhz is the effective SM clock of that
+ * launch (clock64 cycles / globaltimer ns of one block), *_per_clk_sm the
+ * rate per clock and multiprocessor.  Changes no GPU setting.  Allocates 4 KB
+ * of device memory for the duration of the call; synchronises `stream`.
+ */
+typedef struct {
+  int sms;                       /* multiprocessors of the device */
+  double mufu_ops_per_s, ffma_flops_per_s, dfma_flops_per_s;
+  double mufu_mhz, ffma_mhz, dfma_mhz;
+  double mufu_per_clk_sm, ffma_flops_per_clk_sm, dfma_flops_per_clk_sm;
+} hpfmm_alu_peaks;
+hpfmm_status hpfmm_measure_alu_peaks(hpfmm_alu_peaks *out, void *stream);
 
 const char *hpfmm_status_string(hpfmm_status s);
 const char *hpfmm_last_error(void);

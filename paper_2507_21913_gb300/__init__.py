@@ -30,7 +30,8 @@ class HpfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tau_fp64", ctypes.c_double), ("levels", ctypes.c_int),
                 ("subtree_levels", ctypes.c_int), ("m2l_mode", ctypes.c_int),
-                ("adaptive", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+                ("adaptive", ctypes.c_int), ("async_update", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1),
                 ("root_x0", ctypes.c_double),
                 ("root_side", ctypes.c_double)]
 
@@ -40,6 +41,15 @@ class Tuning(ctypes.Structure):
                 ("met", ctypes.c_int), ("mean_leaf", ctypes.c_double),
                 ("est_rel_err", ctypes.c_double), ("ms_per_eval", ctypes.c_double),
                 ("nsample", ctypes.c_int)]
+
+
+class AluPeaks(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int), ("mufu_ops_per_s", ctypes.c_double),
+                ("ffma_flops_per_s", ctypes.c_double), ("dfma_flops_per_s", ctypes.c_double),
+                ("mufu_mhz", ctypes.c_double), ("ffma_mhz", ctypes.c_double),
+                ("dfma_mhz", ctypes.c_double), ("mufu_per_clk_sm", ctypes.c_double),
+                ("ffma_flops_per_clk_sm", ctypes.c_double),
+                ("dfma_flops_per_clk_sm", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -89,6 +99,7 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_selftest_tc_gemm.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     L.hpfmm_eval_targets.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
     L.hpfmm_get_adaptive_counts.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.hpfmm_measure_alu_peaks.argtypes = [ctypes.POINTER(AluPeaks), vp]
     L.hpfmm_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hpfmm_default_options.restype = None
     for f in ("hpfmm_create", "hpfmm_eval", "hpfmm_update_points", "hpfmm_destroy", "hpfmm_direct", "hpfmm_get_info",
@@ -96,7 +107,7 @@ def lib(build_if_missing: bool = False):
               "hpfmm_selftest_wait_timeout", "hpfmm_tree_order_noalloc", "hpfmm_eval_adjoint",
               "hpfmm_batch_create", "hpfmm_eval_batched", "hpfmm_batch_captures",
               "hpfmm_batch_destroy", "hpfmm_autotune", "hpfmm_selftest_tc_gemm",
-              "hpfmm_eval_targets", "hpfmm_get_adaptive_counts"):
+              "hpfmm_eval_targets", "hpfmm_get_adaptive_counts", "hpfmm_measure_alu_peaks"):
         getattr(L, f).restype = ctypes.c_int
     L.hpfmm_status_string.argtypes = [ctypes.c_int]
     L.hpfmm_status_string.restype = ctypes.c_char_p
@@ -155,7 +166,7 @@ class Plan:
 
 
 def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau_fp64=0.05,
-                 subtree_levels=0, m2l_mode=0, root=None, adaptive=False):
+                 subtree_levels=0, m2l_mode=0, root=None, adaptive=False, async_update=False):
     """Build a plan for the points (x, y); see hpfmm_create in include/hpfmm.h."""
     x = _as_tensor(x)
     y = _as_tensor(y, x.device)
@@ -168,6 +179,7 @@ def hpfmm_create(x, y, kappa=1.0, p=12, leaf_size=32, prec="fp64", levels=0, tau
     opt.subtree_levels = int(subtree_levels)
     opt.m2l_mode = int(m2l_mode)
     opt.adaptive = 1 if adaptive else 0
+    opt.async_update = 1 if async_update else 0
     if root is not None:  # (x0, side): the tree's root square
         opt.root_x0, opt.root_side = float(root[0]), float(root[1])
     h = ctypes.c_void_p()
@@ -458,11 +470,14 @@ def hpfmm_tree_order_noalloc(x, y, levels=5):
     library (n <= 65536, device tensors); see include/hpfmm.h."""
     import torch
     x = _as_tensor(x)
-    y = _as_tensor(y, x.device)
-    keys = torch.empty(x.numel(), dtype=torch.int64, device=x.device)
-    perm = torch.empty(x.numel(), dtype=torch.int64, device=x.device)
-    _check(lib().hpfmm_tree_order_noalloc(x.data_ptr(), y.data_ptr(), x.numel(), int(levels),
-                                          keys.data_ptr(), perm.data_ptr(), _stream(x.device)))
+    dev = x.device if x.device.type == "cuda" else torch.device("cuda", torch.cuda.current_device())
+    x = _as_tensor(x, dev)
+    y = _as_tensor(y, dev)
+    keys = torch.empty(x.numel(), dtype=torch.int64, device=dev)
+    perm = torch.empty(x.numel(), dtype=torch.int64, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().hpfmm_tree_order_noalloc(x.data_ptr(), y.data_ptr(), x.numel(), int(levels),
+                                              keys.data_ptr(), perm.data_ptr(), _stream(dev)))
     return keys.cpu().numpy().view(np.uint64), perm.cpu().numpy()
 
 
@@ -476,6 +491,17 @@ def hpfmm_selftest_tc_gemm(A, B, split=True):
     _check(lib().hpfmm_selftest_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), B.shape[0],
                                         A.shape[1], 1 if split else 0, _stream(A.device)))
     return D
+
+
+def hpfmm_measure_alu_peaks(device=None):
+    """Measured SFU / FP32 FMA / FP64 FMA throughput of the device (see
+    include/hpfmm.h); returns a dict."""
+    torch = _torch()
+    dev = torch.device(device or "cuda:0")
+    r = AluPeaks()
+    with torch.cuda.device(dev):
+        _check(lib().hpfmm_measure_alu_peaks(ctypes.byref(r), _stream(dev)))
+    return {f: getattr(r, f) for f, _ in AluPeaks._fields_}
 
 
 def hpfmm_version():

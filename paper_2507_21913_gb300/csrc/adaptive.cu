@@ -927,6 +927,7 @@ hpfmm_status adaptive_prepare() { return special_init_here(); }
 hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad,
                            cudaStream_t st) {
   HP_TRY(special_init_here());
+  HP_TRY(plan_join_tables(pl, st));  // the mirror M2L reads the reaction tables
   const int p = pl->p, P1 = p + 1, n = (int)pl->n, H = pl->H, depth = pl->ad_depth;
   const size_t m2 = (size_t)P1 * P1;
   const AdGeom g = ad_geom(pl->side);

@@ -133,6 +133,11 @@ static void free_plan(hpfmm_plan *pl) {
     cudaStreamSynchronize(pl->side_stream);
     cudaStreamDestroy(pl->side_stream);
   }
+  if (pl->table_stream) {
+    cudaStreamSynchronize(pl->table_stream);
+    cudaStreamDestroy(pl->table_stream);
+  }
+  if (pl->ev_tree) cudaEventDestroy(pl->ev_tree);
   if (pl->ev_geo) cudaEventDestroy(pl->ev_geo);
   if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
@@ -151,7 +156,7 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc,
                   pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_parent, pl->ab_lvl, pl->ab_child,
                   pl->ab_cut, pl->ab_off, pl->ab_idx, pl->ab_lev, pl->ab_btot, pl->ab_lrank,
-                  pl->ab_leaf, pl->near};
+                  pl->ab_leaf, pl->near, pl->loclo, pl->dgeom, pl->tree_ctr, pl->ctr};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -176,8 +181,16 @@ static int choose_levels(int64_t n, int leaf) {
   return H;
 }
 
-// tree + tables for the points (x, y) of a plan whose buffers exist
-static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
+// tree + tables for the points (x, y) of a plan whose buffers exist.  With
+// wait, the host waits once, after the tree build, for the root square
+// (validity, host copies of the geometry); otherwise nothing waits and the
+// device reports invalid input through the status word.
+// last-block counters of the fused upward pass: one per right-hand side of a
+// multi-RHS pass set (at most 64)
+constexpr int kCtrSlots = 64;
+
+static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st,
+                            bool wait) {
   const int64_t n = pl->n;
   const double *dx = x, *dy = y;
   double *tmp = nullptr;
@@ -197,20 +210,25 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   }
   hpfmm_status s = tree_build(pl, dx, dy, st);
   if (s == HPFMM_OK) {
-    // reaction tables on the side stream, concurrent with the rest of the tree build
-    e = cudaStreamWaitEvent(pl->side_stream, pl->ev_geo, 0);
-    if (e == cudaSuccess) s = tables_build(pl, pl->side_stream);
-    if (e == cudaSuccess) e = cudaEventRecord(pl->ev_tables, pl->side_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, pl->ev_tables, 0);
+    // the geometry to the host and the reaction tables (they depend on the
+    // root square only) on the table stream, concurrent with what follows
+    e = cudaEventRecord(pl->ev_tree, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->table_stream, pl->ev_tree, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(pl->hgeo, pl->geo, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                          pl->table_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pl->ev_geo, pl->table_stream);
+    if (e == cudaSuccess) s = tables_build(pl, pl->table_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pl->ev_tables, pl->table_stream);
     if (e != cudaSuccess) {
       set_last_error("rebuild: table stream: %s", cudaGetErrorString(e));
       s = HPFMM_ECUDA;
     }
+    pl->tables_pending = true;
   }
-  // the one host wait of a rebuild: for the bounding square (validity, root
-  // geometry), right after its reduction; the rest of the build stays queued
+  const bool sync = wait || pl->adaptive;
   double hgeo[5] = {0, 0, 1, 0, 0};
-  if (s == HPFMM_OK) {
+  if (s == HPFMM_OK && sync) {
     e = cudaEventSynchronize(pl->ev_geo);
     if (e != cudaSuccess) {
       set_last_error("rebuild: %s", cudaGetErrorString(e));
@@ -219,13 +237,14 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
       memcpy(hgeo, pl->hgeo, sizeof hgeo);
     }
   }
-  hpfmm_status s2 = tree_finish(pl, hgeo, st);
+  pl->geo_pending = s == HPFMM_OK && !sync;
+  hpfmm_status s2 = tree_finish(pl, sync ? hgeo : nullptr, st);
   if (s == HPFMM_OK) s = s2;
   // the adaptive tree over the sorted points (it reads the coordinates for
   // its leaf frames, so before the staging buffer goes)
   if (s == HPFMM_OK && pl->adaptive) s = adaptive_build(pl, dx, dy, st);
   if (tmp) cudaFreeAsync(tmp, st);
-  if (s != HPFMM_OK) return s;
+  if (s != HPFMM_OK || !sync) return s;
   double kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
   if (kabs * sqrt(5.0) * pl->side > 60.0) {
     set_last_error("|kappa| * sqrt(5) * side = %g exceeds 60, the range of the device I_n "
@@ -235,13 +254,32 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   return HPFMM_OK;
 }
 
+hpfmm_status plan_host_geometry(hpfmm_plan *pl) {
+  if (!pl->geo_pending) return HPFMM_OK;
+  HP_CUDA(cudaEventSynchronize(pl->ev_geo));
+  pl->geo_pending = false;
+  if (pl->hgeo[2] == 0.0) {
+    pl->x0 = pl->hgeo[0];
+    pl->side = pl->hgeo[1];
+    pl->qscale = pl->hgeo[3];
+  }
+  return HPFMM_OK;
+}
+
+hpfmm_status plan_join_tables(hpfmm_plan *pl, cudaStream_t st) {
+  if (!pl->tables_pending) return HPFMM_OK;
+  HP_CUDA(cudaStreamWaitEvent(st, pl->ev_tables, 0));
+  pl->tables_pending = false;
+  return HPFMM_OK;
+}
+
 extern "C" hpfmm_status hpfmm_update_points(hpfmm_plan *pl, const double *x, const double *y,
                                             void *stream) {
   if (!pl || !x || !y) {
     set_last_error("hpfmm_update_points: null argument");
     return HPFMM_EINVAL;
   }
-  return rebuild(pl, x, y, (cudaStream_t)stream);
+  return rebuild(pl, x, y, (cudaStream_t)stream, !pl->async_update);
 }
 
 extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n,
@@ -292,6 +330,10 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     set_last_error("hpfmm_create: an adaptive tree has at most %d levels", kAdaptiveMaxLevel);
     return HPFMM_EINVAL;
   }
+  if (o.async_update != 0 && o.async_update != 1) {
+    set_last_error("hpfmm_create: async_update must be 0 or 1");
+    return HPFMM_EINVAL;
+  }
   if (o.levels < 0 || o.levels > 15 || !(o.tau_fp64 >= 0) || o.subtree_levels < 0 ||
       o.subtree_levels > 4 || o.m2l_mode < 0 || o.m2l_mode > 1 || !(o.root_side >= 0) ||
       !isfinite(o.root_x0) || !isfinite(o.root_side)) {
@@ -312,6 +354,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   pl->kre = kappa_re;
   pl->kim = kappa_im;
   pl->adaptive = o.adaptive;
+  pl->async_update = o.adaptive ? 0 : o.async_update;
   pl->leaf_cap = leaf_size;
   if (pl->adaptive) {
     // depth cap: the uniform depth for this leaf size plus five levels of
@@ -348,6 +391,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->leaf_start, sizeof(int) * (pl->nleaf + 1));
   if (f32) ALLOC(pl->loc32, sizeof(float2) * n);
   if (f32) ALLOC(pl->yabs, sizeof(float) * n);
+  if (f32 && !pl->adaptive) ALLOC(pl->loclo, sizeof(float2) * n);
   if (f32 && !pl->adaptive) ALLOC(pl->near, sizeof(float4) * n);
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
@@ -367,6 +411,9 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   }
   ALLOC(pl->status, sizeof(int));
   ALLOC(pl->geo, 8 * sizeof(double));
+  ALLOC(pl->dgeom, sizeof(DevGeom));
+  ALLOC(pl->tree_ctr, sizeof(unsigned));
+  ALLOC(pl->ctr, kCtrSlots * sizeof(int));
 #undef ALLOC
   if (pl->adaptive) {
     s = adaptive_alloc(pl);
@@ -383,6 +430,8 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     cudaError_t ce = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->side_stream, cudaStreamNonBlocking, prio_hi);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->table_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tree, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_geo, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
@@ -395,13 +444,15 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     }
   }
   cudaError_t e = cudaMemsetAsync(pl->status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->tree_ctr, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->ctr, 0, kCtrSlots * sizeof(int), st);
   if (e != cudaSuccess) {
     set_last_error("hpfmm_create: %s", cudaGetErrorString(e));
     free_plan(pl);
     return HPFMM_ECUDA;
   }
   s = tables_static(pl, st);
-  if (s == HPFMM_OK) s = rebuild(pl, x, y, st);
+  if (s == HPFMM_OK) s = rebuild(pl, x, y, st, true);  // creation always validates
   if (s != HPFMM_OK) {
     cudaStreamSynchronize(st);
     free_plan(pl);
@@ -527,6 +578,7 @@ extern "C" hpfmm_status hpfmm_eval_targets(hpfmm_plan *pl, const double *q, cons
     return HPFMM_EUNSUPPORTED;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  HP_TRY(plan_host_geometry(pl));
   const bool single = pl->prec != HPFMM_FP64;
   if (!pl->tflag) HP_TRY(plan_dalloc(pl, (void **)&pl->tflag, 2 * sizeof(int)));
   if (single && nt > pl->tlist_cap) {
@@ -569,6 +621,7 @@ extern "C" hpfmm_status hpfmm_get_info(const hpfmm_plan *pl, hpfmm_plan_info *in
     set_last_error("hpfmm_get_info: null argument");
     return HPFMM_EINVAL;
   }
+  HP_TRY(plan_host_geometry(const_cast<hpfmm_plan *>(pl)));
   info->n = pl->n;
   info->levels = pl->H;
   info->p = pl->p;
@@ -603,9 +656,23 @@ extern "C" hpfmm_status hpfmm_sync(hpfmm_plan *pl, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   HP_CUDA(cudaMemcpyAsync(&hs, pl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   HP_CUDA(cudaStreamSynchronize(st));
-  if (hs != 0) {
-    set_last_error("device status word = %d", hs);
+  HP_TRY(plan_host_geometry(pl));
+  if (hs == 0) return HPFMM_OK;
+  // reported once: the word is cleared (and, after a timeout, the fused
+  // upward pass's counters reset) so that the plan can be used again
+  HP_CUDA(cudaMemsetAsync(pl->status, 0, sizeof(int), st));
+  if (hs & HPFMM_DEV_TIMEOUT) HP_CUDA(cudaMemsetAsync(pl->ctr, 0, kCtrSlots * sizeof(int), st));
+  HP_CUDA(cudaStreamSynchronize(st));
+  if (hs & HPFMM_DEV_TIMEOUT) {
+    set_last_error("device status word = %d: a bounded device wait gave up", hs);
     return HPFMM_ETIMEOUT;
   }
-  return HPFMM_OK;
+  if (hs & HPFMM_DEV_EINVAL) {
+    set_last_error("asynchronous rebuild: points must be finite with y > 0 (or the root square "
+                   "does not contain them)");
+    return HPFMM_EINVAL;
+  }
+  set_last_error("asynchronous rebuild: |kappa| * sqrt(5) * side exceeds 60, the range of the "
+                 "device I_n evaluation");
+  return HPFMM_EUNSUPPORTED;
 }

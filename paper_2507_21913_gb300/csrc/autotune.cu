@@ -8,9 +8,11 @@
 // a probe charge vector (a counter-based hash of the point index, uniform in
 // [-1, 1)) is evaluated by the FMM and, at a sample of targets, by the
 // device direct sum in double precision (hpfmm_direct); the first order whose
-// relative L2 error on the sample meets the tolerance is taken.  Then the
-// tree depth and subtree tile are chosen by timing update_points + eval with
-// CUDA events among the candidates whose error still meets the tolerance.
+// relative L2 errors on the sample -- of the potential and of its gradient,
+// the larger of the two -- meet the tolerance is taken, for each candidate
+// tree depth (the depth from the leaf size and one level either side).  The
+// fastest of these (update_points + eval timed with CUDA events) wins, and its
+// subtree tile depth is then chosen by timing too.
 #include <math.h>
 
 #include <algorithm>
@@ -44,9 +46,15 @@ __global__ void k_take(int64_t m, int64_t stride, const double *x, const double 
   idx[k] = i;
 }
 
-__global__ void k_take_pot(int64_t m, int64_t stride, const double2 *pot, double2 *out) {
+// the sampled potentials (out[0 .. m)) and gradients (out[m .. 3m), x then
+// y derivative per target)
+__global__ void k_take_pot(int64_t m, int64_t stride, const double2 *pot, const double2 *grad,
+                           double2 *out) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < m) out[k] = pot[k * stride];
+  if (k >= m) return;
+  out[k] = pot[k * stride];
+  out[m + 2 * k] = grad[2 * k * stride];
+  out[m + 2 * k + 1] = grad[2 * k * stride + 1];
 }
 
 struct Dev {
@@ -70,14 +78,16 @@ struct Dev {
 struct Probe {
   const double *x, *y, *q;
   int64_t n, m, stride;
-  double *pot;      // n complex
-  double2 *sample;  // m complex (device)
-  std::vector<double2> ref;
+  double *pot, *grad;  // n complex, 2n complex
+  double2 *sample;     // 3m complex (device): potentials, then gradients
+  std::vector<double2> ref;  // 3m: the direct sum's potentials and gradients
 };
 
-double rel_err(const std::vector<double2> &a, const std::vector<double2> &b) {
+// relative L2 error of a[k0, k1) against b[k0, k1)
+double rel_err(const std::vector<double2> &a, const std::vector<double2> &b, size_t k0,
+               size_t k1) {
   double num = 0, den = 0;
-  for (size_t k = 0; k < a.size(); ++k) {
+  for (size_t k = k0; k < k1; ++k) {
     const double dx = a[k].x - b[k].x, dy = a[k].y - b[k].y;
     num += dx * dx + dy * dy;
     den += b[k].x * b[k].x + b[k].y * b[k].y;
@@ -95,18 +105,19 @@ hpfmm_status try_config(Probe &pr, double kre, double kim, int prec, int p, int 
   o.subtree_levels = subtree;
   *plan = nullptr;
   HP_TRY(hpfmm_create(pr.x, pr.y, pr.n, kre, kim, p, 32, &o, st, plan));
-  hpfmm_status s = hpfmm_eval(*plan, pr.q, 1, pr.pot, nullptr, st);
+  hpfmm_status s = hpfmm_eval(*plan, pr.q, 1, pr.pot, pr.grad, st);
   if (s == HPFMM_OK) {
-    k_take_pot<<<(unsigned)((pr.m + 255) / 256), 256, 0, st>>>(pr.m, pr.stride,
-                                                                 (const double2 *)pr.pot, pr.sample);
-    std::vector<double2> got(pr.m);
-    if (cudaMemcpyAsync(got.data(), pr.sample, sizeof(double2) * pr.m, cudaMemcpyDeviceToHost,
-                        st) != cudaSuccess ||
+    k_take_pot<<<(unsigned)((pr.m + 255) / 256), 256, 0, st>>>(
+        pr.m, pr.stride, (const double2 *)pr.pot, (const double2 *)pr.grad, pr.sample);
+    std::vector<double2> got(3 * pr.m);
+    if (cudaMemcpyAsync(got.data(), pr.sample, sizeof(double2) * 3 * pr.m,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       set_last_error("hpfmm_autotune: %s", cudaGetErrorString(cudaGetLastError()));
       s = HPFMM_ECUDA;
     } else {
-      *err = rel_err(got, pr.ref);
+      const double ep = rel_err(got, pr.ref, 0, pr.m), eg = rel_err(got, pr.ref, pr.m, 3 * pr.m);
+      *err = ep > eg ? ep : eg;
     }
   }
   if (s == HPFMM_OK) s = hpfmm_sync(*plan, st);
@@ -122,11 +133,11 @@ hpfmm_status time_plan(hpfmm_plan *plan, Probe &pr, cudaStream_t st, int reps, d
   HP_CUDA(cudaEventCreate(&a));
   HP_CUDA(cudaEventCreate(&b));
   hpfmm_status s = hpfmm_update_points(plan, pr.x, pr.y, st);
-  if (s == HPFMM_OK) s = hpfmm_eval(plan, pr.q, 1, pr.pot, nullptr, st);
+  if (s == HPFMM_OK) s = hpfmm_eval(plan, pr.q, 1, pr.pot, pr.grad, st);
   if (s == HPFMM_OK && cudaEventRecord(a, st) != cudaSuccess) s = HPFMM_ECUDA;
   for (int r = 0; s == HPFMM_OK && r < reps; ++r) {
     s = hpfmm_update_points(plan, pr.x, pr.y, st);
-    if (s == HPFMM_OK) s = hpfmm_eval(plan, pr.q, 1, pr.pot, nullptr, st);
+    if (s == HPFMM_OK) s = hpfmm_eval(plan, pr.q, 1, pr.pot, pr.grad, st);
   }
   float t = 0.f;
   if (s == HPFMM_OK && (cudaEventRecord(b, st) != cudaSuccess ||
@@ -167,93 +178,112 @@ extern "C" hpfmm_status hpfmm_autotune(const double *x, const double *y, int64_t
   int64_t *idx;
   HP_TRY(mem.alloc(&q, n));
   HP_TRY(mem.alloc(&pr.pot, 2 * n));
+  HP_TRY(mem.alloc(&pr.grad, 4 * n));
   HP_TRY(mem.alloc(&xt, pr.m));
   HP_TRY(mem.alloc(&yt, pr.m));
   HP_TRY(mem.alloc(&idx, pr.m));
-  HP_TRY(mem.alloc(&ref, 2 * pr.m));
-  HP_TRY(mem.alloc(&pr.sample, pr.m));
+  HP_TRY(mem.alloc(&ref, 6 * pr.m));
+  HP_TRY(mem.alloc(&pr.sample, 3 * pr.m));
   pr.q = q;
   k_probe_charges<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, q);
   k_take<<<(unsigned)((pr.m + 255) / 256), 256, 0, st>>>(pr.m, pr.stride, x, y, xt, yt, idx);
   HP_LAUNCH_CHECK();
   // reference: the direct sum in double precision at the sampled targets
-  HP_TRY(hpfmm_direct(x, y, q, n, xt, yt, idx, pr.m, kappa_re, kappa_im, ref, nullptr, st));
-  pr.ref.resize(pr.m);
-  HP_CUDA(cudaMemcpyAsync(pr.ref.data(), ref, sizeof(double2) * pr.m, cudaMemcpyDeviceToHost, st));
+  HP_TRY(hpfmm_direct(x, y, q, n, xt, yt, idx, pr.m, kappa_re, kappa_im, ref, ref + 2 * pr.m,
+                      st));
+  pr.ref.resize(3 * pr.m);
+  HP_CUDA(cudaMemcpyAsync(pr.ref.data(), ref, sizeof(double2) * 3 * pr.m, cudaMemcpyDeviceToHost,
+                          st));
   HP_CUDA(cudaStreamSynchronize(st));
 
-  // 1. order: the smallest p (even, so that the single-precision fast M2L
-  // applies) whose sampled error meets tol at the default tree
-  const int pmax = prec == HPFMM_FP64 ? 40 : 20;
-  int best_p = -1;
-  double best_err = INFINITY;
-  int chosen_p = -1;
-  double chosen_err = INFINITY;
-  for (int p = 4; p <= pmax; p += 2) {
-    hpfmm_plan *plan = nullptr;
-    double err = INFINITY;
-    hpfmm_status s = try_config(pr, kappa_re, kappa_im, prec, p, 0, 0, st, &plan, &err);
-    if (s == HPFMM_EUNSUPPORTED) break;  // kappa * box side out of the I_n range
-    HP_TRY(s);
-    hpfmm_destroy(plan);
-    if (err < best_err) {
-      best_err = err;
-      best_p = p;
-    }
-    if (err <= tol) {
-      chosen_p = p;
-      chosen_err = err;
-      break;
-    }
-    // single precision stops improving at its rounding floor
-    if (prec != HPFMM_FP64 && p >= 8 && err > 0.7 * best_err && best_p < p) break;
-  }
-  if (best_p < 0) {
-    set_last_error("hpfmm_autotune: no order could be evaluated");
-    return HPFMM_EUNSUPPORTED;
-  }
-  const bool met = chosen_p > 0;
-  if (!met) {
-    chosen_p = best_p;
-    chosen_err = best_err;
-  }
-  const double accept = met ? tol : chosen_err * 1.5;
-
-  // 2. tree depth and subtree tile: the fastest configuration whose error
-  // stays acceptable
+  // 1. for each candidate tree depth, the smallest even p whose sampled error
+  // meets tol, timed
   hpfmm_plan_info info;
   {
     hpfmm_options o;
     hpfmm_default_options(&o);
     o.prec = (hpfmm_precision)prec;
     hpfmm_plan *plan = nullptr;
-    HP_TRY(hpfmm_create(x, y, n, kappa_re, kappa_im, chosen_p, 32, &o, st, &plan));
+    HP_TRY(hpfmm_create(x, y, n, kappa_re, kappa_im, 8, 32, &o, st, &plan));
     hpfmm_get_info(plan, &info);
     hpfmm_destroy(plan);
   }
   const int H0 = info.levels;
-  double best_ms = INFINITY;
-  int best_H = H0, best_k = 0;
-  double best_cfg_err = chosen_err;
+  const int pmax = 40;
+  int best_p = -1, best_H = H0;
+  double best_ms = INFINITY, best_cfg_err = INFINITY;
+  // when no order meets tol: the most accurate configuration seen
+  int floor_p = -1, floor_H = H0;
+  double floor_err = INFINITY;
   for (int H = std::max(2, H0 - 1); H <= std::min(12, H0 + 1); ++H) {
-    for (int k = 0; k <= 4; ++k) {
-      if (k > 0 && k > H - 1) break;
+    double hbest = INFINITY;
+    int hbest_p = -1;
+    for (int p = 4; p <= pmax; p += 2) {
       hpfmm_plan *plan = nullptr;
       double err = INFINITY;
-      hpfmm_status s = try_config(pr, kappa_re, kappa_im, prec, chosen_p, H, k, st, &plan, &err);
+      hpfmm_status s = try_config(pr, kappa_re, kappa_im, prec, p, H, 0, st, &plan, &err);
+      if (s == HPFMM_EUNSUPPORTED || s == HPFMM_ENOMEM) break;
+      HP_TRY(s);
+      if (err < floor_err) {
+        floor_err = err;
+        floor_p = p;
+        floor_H = H;
+      }
+      if (err <= tol) {
+        double ms = INFINITY;
+        s = time_plan(plan, pr, st, 3, &ms);
+        hpfmm_destroy(plan);
+        HP_TRY(s);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_p = p;
+          best_H = H;
+          best_cfg_err = err;
+        }
+        break;
+      }
+      hpfmm_destroy(plan);
+      if (err < hbest) {
+        hbest = err;
+        hbest_p = p;
+      }
+      // single precision stops improving at its rounding floor
+      if (prec != HPFMM_FP64 && p >= 8 && err > 0.7 * hbest && hbest_p < p) break;
+    }
+  }
+  if (floor_p < 0) {
+    set_last_error("hpfmm_autotune: no order could be evaluated");
+    return HPFMM_EUNSUPPORTED;
+  }
+  const bool met = best_p > 0;
+  if (!met) {  // tol out of reach: the most accurate configuration, timed
+    best_p = floor_p;
+    best_H = floor_H;
+    best_cfg_err = floor_err;
+  }
+  const int chosen_p = best_p;
+  // 2. subtree tile depth of the fused upward / downward passes, by timing
+  int best_k = 0;
+  {
+    double kbest = INFINITY;
+    for (int k = 0; k <= 4; ++k) {
+      if (k > 0 && k > best_H - 1) break;
+      hpfmm_plan *plan = nullptr;
+      double err = INFINITY;
+      hpfmm_status s = try_config(pr, kappa_re, kappa_im, prec, chosen_p, best_H, k, st, &plan,
+                                  &err);
       if (s == HPFMM_EUNSUPPORTED || s == HPFMM_ENOMEM) continue;
       HP_TRY(s);
       double ms = INFINITY;
-      if (err <= accept) s = time_plan(plan, pr, st, 3, &ms);
+      s = time_plan(plan, pr, st, 3, &ms);
       hpfmm_destroy(plan);
       HP_TRY(s);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_H = H;
+      if (ms < kbest) {
+        kbest = ms;
         best_k = k;
-        best_cfg_err = err;
       }
     }
+    best_ms = kbest;
   }
   out->p = chosen_p;
   out->levels = best_H;

@@ -179,11 +179,18 @@ extern "C" hpfmm_status hpfmm_eval_batched(hpfmm_batch *b, const double *const *
       return HPFMM_EINVAL;
     }
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  // the graph replays kernels only: the reaction tables of the plans' last
+  // rebuilds are joined here, outside the capture, and the root squares the
+  // capture used are compared with the current ones
+  for (int i = 0; i < np; ++i) {
+    HP_TRY(plan_join_tables(b->plans[i], st));
+    HP_TRY(plan_host_geometry(b->plans[i]));
+  }
   bool same = b->exec != nullptr;
   for (int i = 0; same && i < np; ++i)
     same = b->q[i] == q[i] && b->pot[i] == pot[i] && b->grad[i] == (grad ? grad[i] : nullptr) &&
            b->geom[2 * i] == b->plans[i]->x0 && b->geom[2 * i + 1] == b->plans[i]->side;
-  cudaStream_t st = (cudaStream_t)stream;
   // the graph reads the plans' trees: order the capture stream after the caller's work
   HP_CUDA(cudaEventRecord(b->pre, st));
   HP_CUDA(cudaStreamWaitEvent(b->origin, b->pre, 0));

@@ -139,8 +139,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
   }
   return false;
 }
-// device status bits (the plan's status word)
-enum { HPFMM_DEV_TIMEOUT = 1 };
+// device status bits (the plan's status word): a bounded wait gave up;
+// (asynchronous rebuilds) the points were invalid; |kappa| sqrt(5) side was
+// beyond the range of the device I_n evaluation
+enum { HPFMM_DEV_TIMEOUT = 1, HPFMM_DEV_EINVAL = 2, HPFMM_DEV_RANGE = 4 };
+
+// Geometry of a uniform tree as the evaluation kernels read it: written on
+// the device by the tree build, so that nothing between a rebuild and an
+// evaluation waits for the host to learn the root square.  Level l has box
+// side d_l = side 2^-l; d[l] is d_l rounded to single precision and dlo[l]
+// the rest (d_l = d[l] + dlo[l] to about 2^-48 relative), so that offsets
+// between single-precision leaf frames stay exact.
+struct DevGeom {
+  double x0, side, qscale;
+  double logd[16];
+  float d[16], invd[16], dlo[16];
+};
 
 // ---------------------------------------------------------------------------
 // Morton geometry.  Key bit 2b holds bit b of ix, bit 2b+1 bit b of iy; the
@@ -264,6 +278,7 @@ struct hpfmm_plan {
   uint64_t *keys = nullptr;             // sorted keys
   int *leaf_start = nullptr;            // nleaf + 1 offsets into the sorted order
   float2 *loc32 = nullptr;              // FP32 path: (x, y) relative to the leaf centre
+  float2 *loclo = nullptr;              // FP32 path: the rest, (x, y) - centre - loc32
   float *yabs = nullptr;                // FP32 path: y itself (bottom-row image/reaction pairs)
 
   // tables (device, double); FP32 copies when prec != FP64
@@ -299,12 +314,23 @@ struct hpfmm_plan {
   // rebuild's synchronisation
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_geo = nullptr, ev_tables = nullptr;
+  // the geometry copy to the host and the reaction tables of a rebuild run on
+  // table_stream after the tree build (ev_tree); the tables are joined into
+  // the evaluation's stream right before the mirror M2L that reads them
+  cudaStream_t table_stream = nullptr;
+  cudaEvent_t ev_tree = nullptr;
+  bool tables_pending = false;
   // fork / join of the near field on the side stream (single precision)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   float4 *near = nullptr;  // near-field sums per point (sorted order)
   double *hgeo = nullptr;  // pinned host copy of geo, written by the tree build
   int *status = nullptr;  // device status word
   double *geo = nullptr;  // device: x0, side, invalid flag, 2^30/side, largest leaf (int)
+  DevGeom *dgeom = nullptr;  // device: level geometry of the current tree
+  unsigned *tree_ctr = nullptr;  // device: last-block counter of the tree build
+  int *ctr = nullptr;     // device: last-block counters of the fused upward pass, one per RHS
+  int async_update = 0;   // hpfmm_options.async_update
+  bool geo_pending = false;  // host copies x0 / side / qscale wait for ev_geo
   void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
   int64_t tree_tmp_bytes = 0;
   int64_t workspace_bytes = 0;
@@ -376,3 +402,8 @@ hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot
                             void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st);
 bool is_device_pointer(const void *p);
 hpfmm_status plan_dalloc(hpfmm_plan *pl, void **p, size_t bytes);
+// host copies of the root square (x0, side, qscale) of the current tree: waits
+// for the geometry of an asynchronous rebuild when it has not arrived yet
+hpfmm_status plan_host_geometry(hpfmm_plan *pl);
+// order `st` after the reaction tables of the last rebuild (once per rebuild)
+hpfmm_status plan_join_tables(hpfmm_plan *pl, cudaStream_t st);

@@ -36,36 +36,16 @@
 #include "special.cuh"
 #include "near32.cuh"
 #include "tc.cuh"
+#include "m2l_patch.cuh"
 
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
 
-// box side, its reciprocal and log per level, computed once on the host and
-// passed by value, so that no kernel repeats double-precision set-up
-// arithmetic per thread (GB300's FP64 pipe is narrow)
-// strides between the right-hand sides of a multi-RHS evaluation (blockIdx.y
-// = RHS index): q in charges, m in expansion coefficients, out in doubles of
-// the potential (the gradient has twice that)
-struct RhsStride {
-  int64_t q, m, out;
-};
+// Box side, its reciprocal and log per level come from the plan's DevGeom
+// record, written on the device by the tree build (no kernel repeats
+// double-precision set-up arithmetic per thread: GB300's FP64 pipe is narrow).
 
-struct LevelGeom {
-  float d[16], invd[16];
-  double logd[16];
-};
-LevelGeom level_geom(double side, int H) {
-  LevelGeom g;
-  for (int l = 0; l < 16; ++l) {
-    const double d = ldexp(side, -l);
-    g.d[l] = (float)d;
-    g.invd[l] = (float)(1.0 / d);
-    g.logd[l] = log(d);
-  }
-  (void)H;
-  return g;
-}
 
 template <typename R>
 __device__ __forceinline__ cpx<R> ldc(const cpx<R> *p) {
@@ -119,7 +99,8 @@ struct LeafPoints<float> {
 template <typename R>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_p2m(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
-      double x0, double side, int p, cpx<R> *__restrict__ M) {
+      const DevGeom *__restrict__ dg, int p, cpx<R> *__restrict__ M) {
+  const double x0 = dg->x0, side = dg->side;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int P1 = p + 1;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,7 +160,7 @@ constexpr int kS2mGroup = 4;  // orders per thread of the single-precision S2M
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
-             int H, double x0, double side, R invd_leaf, int p, cpx<R> *__restrict__ M,
+             int H, const DevGeom *__restrict__ dg, int p, cpx<R> *__restrict__ M,
              RhsStride rs) {
   // one thread per leaf and group of kS2mGroup consecutive orders n0 .. n0+3:
   // w^n0 = (w^4)^(n0/4) from two squarings, then one product per further n
@@ -194,9 +175,7 @@ k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict_
   const int nb = (int)(t - leaf * (unsigned)NB), n0 = G * nb;
   // (the single-precision points are already relative to the leaf centre)
   const double cx = 0.0, cy = 0.0;
-  const R invd = invd_leaf;
-  (void)x0;
-  (void)side;
+  const R invd = (R)dg->invd[H];
   const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
   // compensated (Kahan) summation: the moments of a leaf are sums of up to
   // hundreds of terms of both signs, and their rounding error is inherited
@@ -233,9 +212,10 @@ k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict_
 template <int RC>
 __global__ void __launch_bounds__(256)
 k_s2m_multi(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp, int nr,
-            const int *__restrict__ leaf_start, int H, float invd, int p, cf *__restrict__ M,
-            RhsStride rs) {
+            const int *__restrict__ leaf_start, int H, const DevGeom *__restrict__ dg, int p,
+            cf *__restrict__ M, RhsStride rs) {
   const int P1 = p + 1;
+  const float invd = dg->invd[H];
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nleaf = 1u << (2 * H);
   if (t >= nleaf * (unsigned)P1) return;
@@ -271,46 +251,61 @@ k_s2m_multi(const float2 *__restrict__ loc, const float *__restrict__ qsm, int r
 }
 
 // --------------------------------------------------------------------------
-// Fused upward pass.  The tree below level l0 = H - k (k = min(3, H - 1)) is
-// split into subtrees of 4^k leaves; one block per subtree forms the leaf
-// moments (S2M: M_n = sum_j Q_j ((z_j - z_c)/d)^n, one warp per leaf, lanes
-// over points, a shuffle reduction per n) and merges them level by level up
-// to l0 with the M2M shift (Eq. metome) in shared memory.  Levels l0 - 1 .. 1
-// are then done by one single-block kernel.
+// Fused upward pass.  The tree below level l0 = H - k is split into subtrees
+// of 4^k leaves; one block per subtree takes the leaf moments (S2M kernel) and
+// merges them level by level up to l0 with the M2M shift (Eq. metome) in
+// shared memory.  When the levels above l0 are small (l0 <= kCoarseBig), the
+// block that finishes last (a counter in global memory) also runs them, l0 - 1
+// down to 1, so the upward pass needs no further launch; deeper trees run
+// them as separate launches.
+constexpr int kCoarseBig = 5;  // coarse levels with at least 4^5 boxes get a multi-block launch
+
 template <typename R>
 __device__ __forceinline__ R wsum(R v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+// a complex number read past L1 (written by another block of the same launch)
+__device__ __forceinline__ cf ldcg_c(const cf *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return mk(v.x, v.y);
+}
+__device__ __forceinline__ cd ldcg_c(const cd *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return mk(v.x, v.y);
+}
+
+// M2M of output (box b, order n) of level l from its four children (Eq.
+// metome); children read past L1 (they may come from other blocks)
 template <typename R>
-__global__ void __launch_bounds__(256)
-k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start, int H,
-         int k, double x0, double side, int p, const cpx<R> *__restrict__ Tm2m,
-         cpx<R> *__restrict__ M, RhsStride rs) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int P1 = p + 1;
-  M += blockIdx.y * rs.m;
-  cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
-  cpx<R> *Ms = T + 4 * P1 * P1;                       // subtree boxes, level by level
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tm2m[e];
-  const int nl = 1 << (2 * k);                 // leaves per subtree
-  const int64_t first_leaf = (int64_t)blockIdx.x * nl;  // Morton order: subtree = contiguous
-  const double d = ldexp(side, -H);
-  const R invd = (R)(1.0 / d);
-  // leaf moments (computed by the S2M kernel) into shared memory
-  for (int e = threadIdx.x; e < nl * P1; e += blockDim.x)
-    Ms[e] = M[(size_t)(level_offset(H) + first_leaf) * P1 + e];
-  (void)pts; (void)qs; (void)leaf_start; (void)x0; (void)side; (void)warp; (void)lane; (void)nw;
-  __syncthreads();
-  // M2M inside the subtree: level H-1 .. H-k
-  cpx<R> *child = Ms;
-  int nchild = nl;
-  for (int l = H - 1; l >= H - k; --l) {
+__device__ __forceinline__ void m2m_item(int l, int e, int P1, const cpx<R> *__restrict__ Tm2m,
+                                         cpx<R> *__restrict__ M) {
+  const int b = e / P1, n = e % P1;
+  const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * (int64_t)b) * P1;
+  cpx<R> acc = mk<R>(0, 0);
+  for (int c = 0; c < 4; ++c) {
+    const cpx<R> *Tc = Tm2m + (size_t)c * P1 * P1 + (size_t)n * P1;
+    for (int m = 0; m <= n; ++m) {
+      const cpx<R> v = ldcg_c(&child[(size_t)c * P1 + m]);
+      cfma(acc, Tc[m], v);
+    }
+  }
+  M[(size_t)(level_offset(l) + b) * P1 + n] = acc;
+}
+
+// M2M in shared memory from nchild boxes of level lc (child, Morton order
+// from box `first` << 2) up to level lto: each level's boxes written after
+// the previous ones in smem and to M
+template <typename R>
+__device__ __forceinline__ void m2m_levels_smem(cpx<R> *child, int nchild, int lc, int lto,
+                                                int64_t first_child, int P1,
+                                                const cpx<R> *__restrict__ T,
+                                                cpx<R> *__restrict__ M) {
+  for (int l = lc - 1; l >= lto; --l) {
     cpx<R> *par = child + (size_t)nchild * P1;
     const int npar = nchild >> 2;
-    const int64_t first = first_leaf >> (2 * (H - l));
+    const int64_t first = first_child >> (2 * (lc - l));
     for (int e = threadIdx.x; e < npar * P1; e += blockDim.x) {
       const int b = e / P1, n = e % P1;
       cpx<R> acc = mk<R>(0, 0);
@@ -328,21 +323,42 @@ k_upward(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ le
   }
 }
 
-// coarse levels with at least 4^kCoarseBig boxes get a multi-block launch each
-constexpr int kCoarseBig = 5;
-
-// M2M of output (box b, order n) of level l from its four children (Eq. metome)
 template <typename R>
-__device__ __forceinline__ void m2m_item(int l, int e, int P1, const cpx<R> *__restrict__ Tm2m,
-                                         cpx<R> *__restrict__ M) {
-  const int b = e / P1, n = e % P1;
-  const cpx<R> *child = M + (size_t)(level_offset(l + 1) + 4 * (int64_t)b) * P1;
-  cpx<R> acc = mk<R>(0, 0);
-  for (int c = 0; c < 4; ++c) {
-    const cpx<R> *Tc = Tm2m + (size_t)c * P1 * P1 + (size_t)n * P1;
-    for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], child[(size_t)c * P1 + m]);
-  }
-  M[(size_t)(level_offset(l) + b) * P1 + n] = acc;
+__global__ void __launch_bounds__(256)
+k_upward(int H, int k, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ M,
+         RhsStride rs, int *__restrict__ ctr) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_last;
+  const int P1 = p + 1;
+  M += blockIdx.y * rs.m;
+  cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
+  cpx<R> *Ms = T + 4 * P1 * P1;                       // subtree boxes, level by level
+  for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tm2m[e];
+  const int nl = 1 << (2 * k);                 // leaves per subtree
+  const int64_t first_leaf = (int64_t)blockIdx.x * nl;  // Morton order: subtree = contiguous
+  // leaf moments (computed by the S2M kernel) into shared memory
+  for (int e = threadIdx.x; e < nl * P1; e += blockDim.x)
+    Ms[e] = M[(size_t)(level_offset(H) + first_leaf) * P1 + e];
+  __syncthreads();
+  // M2M inside the subtree: level H-1 .. H-k
+  m2m_levels_smem<R>(Ms, nl, H, H - k, first_leaf, P1, T, M);
+  // the coarse levels l0 - 1 .. 1, by the last block to finish, from the
+  // 4^l0 moments of level l0 staged in shared memory (l0 <= k: they fit where
+  // the subtree was)
+  const int l0 = H - k;
+  if (!ctr || l0 <= 1) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr + blockIdx.y, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nb0 = 1 << (2 * l0);
+  for (int e = threadIdx.x; e < nb0 * P1; e += blockDim.x)
+    Ms[e] = ldcg_c(M + (size_t)level_offset(l0) * P1 + e);
+  __syncthreads();
+  m2m_levels_smem<R>(Ms, nb0, l0, 1, 0, P1, T, M);
+  if (threadIdx.x == 0) ctr[blockIdx.y] = 0;  // ready for the next launch
 }
 
 // M2M for the small coarse levels lhi .. 1, one block, level by level
@@ -369,79 +385,86 @@ k_m2m_level(int l, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ 
   if (e < ((int64_t)1 << (2 * l)) * P1) m2m_item<R>(l, (int)e, P1, Tm2m, M);
 }
 
-// L2L (Eq. letole1) of coefficient (box b, order m) of level l from its parent
-template <typename R>
-__device__ __forceinline__ void l2l_item(int l, int e, int P1, const cpx<R> *__restrict__ Tl2l,
-                                         cpx<R> *__restrict__ A, cpx<R> *__restrict__ B) {
-  const int b = e / P1, m = e % P1, c = b & 3;
-  const size_t pe = (size_t)(level_offset(l - 1) + (b >> 2)) * P1;
-  const size_t ce = (size_t)(level_offset(l) + b) * P1;
-  const cpx<R> *Tc = Tl2l + (size_t)c * P1 * P1 + (size_t)m * P1;
-  cpx<R> sa = A[ce + m], sb = B[ce + m];
-  for (int n = m; n < P1; ++n) {
-    cfma(sa, Tc[n], A[pe + n]);
-    cfma(sb, conj(Tc[n]), B[pe + n]);
-  }
-  A[ce + m] = sa;
-  B[ce + m] = sb;
-}
+// Fused downward pass.  One block per box of level l0 = H - k (the root of a
+// subtree of 4^k leaves).  The block first forms the final local expansion of
+// its root from the chain of its ancestors: the level-1 expansion (mirror
+// M2L only) shifted down by L2L (Eq. letole1) and added to each ancestor's own
+// M2L result, level by level -- a few small matrix-vector products per block,
+// instead of launches for the coarse levels.  It then pushes the expansions
+// down the subtree in shared memory (child = L2L(parent) + the child's own M2L
+// result).  Without EVAL the leaf expansions are written to global memory;
+// with EVAL (single-precision split evaluation) they stay in shared memory and
+// the block evaluates them at its points (L2P, Eq. truncatedLE), adds the
+// near-field sums of k_eval32p<1> and writes the outputs.
+struct DownEval {
+  const float2 *loc;
+  const float4 *near;
+  const int64_t *perm;
+  const DevGeom *dg;
+  double *pot, *grad;
+};
 
-// L2L for the small coarse levels 2 .. lhi, one block, level by level
-template <typename R>
-__global__ void __launch_bounds__(1024)
-k_l2l_coarse(int lhi, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
-             cpx<R> *__restrict__ B, RhsStride rs) {
-  const int P1 = p + 1;
-  A += blockIdx.y * rs.m;
-  B += blockIdx.y * rs.m;
-  for (int l = 2; l <= lhi; ++l) {
-    const int nb = 1 << (2 * l);
-    for (int e = threadIdx.x; e < nb * P1; e += blockDim.x) l2l_item<R>(l, e, P1, Tl2l, A, B);
-    __syncthreads();
-  }
-}
-
-// the same for one level with many boxes, one thread per (box, m) over many blocks
-template <typename R>
-__global__ void __launch_bounds__(256)
-k_l2l_level(int l, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
-            cpx<R> *__restrict__ B, RhsStride rs) {
-  const int P1 = p + 1;
-  A += blockIdx.y * rs.m;
-  B += blockIdx.y * rs.m;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < ((int64_t)1 << (2 * l)) * P1) l2l_item<R>(l, (int)e, P1, Tl2l, A, B);
-}
-
-// Fused downward pass below l0: one block per level-l0 box pushes its local
-// expansions down k levels in shared memory (child = L2L(parent) + the
-// child's own M2L result) and writes the leaf expansions only.
-template <typename R>
+template <typename R, bool EVAL>
 __global__ void __launch_bounds__(256)
 k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
            cpx<R> *__restrict__ B, RhsStride rs, const int *__restrict__ leaf_start,
-           int skip_empty) {
+           int skip_empty, DownEval ev) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int P1 = p + 1;
+  const int64_t root = blockIdx.x;
+  const int l0 = H - k;
+  const int64_t lf0 = root << (2 * k);
+  const int nl = 1 << (2 * k);
   if (skip_empty) {  // a subtree without points needs no leaf expansions
-    const int64_t lf0 = (int64_t)blockIdx.x << (2 * k);
-    if (leaf_start[lf0 + (int64_t(1) << (2 * k))] == leaf_start[lf0]) return;
+    if (leaf_start[lf0 + nl] == leaf_start[lf0]) return;
   }
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
-  cpx<R> *buf = T + 4 * P1 * P1;  // two ping-pong regions of 4^(k-1) boxes x (A, B);
-                                  // the leaf level goes straight to global memory
-  const int nmax = 1 << (2 * (k - 1));
-  cpx<R> *cur = buf, *nxt = buf + (size_t)2 * nmax * P1;
+  // two ping-pong regions of nbuf boxes x (A, B): the leaf level stays in
+  // shared memory with EVAL, else goes straight to global memory
+  const int nbuf = EVAL ? nl : (1 << (2 * (k > 0 ? k - 1 : 0)));
+  cpx<R> *cur = T + 4 * P1 * P1, *nxt = cur + (size_t)2 * nbuf * P1;
   for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tl2l[e];
-  const int l0 = H - k;
-  const int64_t root = blockIdx.x;
+  // ancestor chain: levels 1 .. l0 (level 0 has no expansion)
+  const int64_t a1 = root >> (2 * (l0 - 1));
   for (int e = threadIdx.x; e < P1; e += blockDim.x) {
-    cur[e] = A[(size_t)(level_offset(l0) + root) * P1 + e];
-    cur[P1 + e] = B[(size_t)(level_offset(l0) + root) * P1 + e];
+    cur[e] = A[(size_t)(level_offset(1) + a1) * P1 + e];
+    cur[P1 + e] = B[(size_t)(level_offset(1) + a1) * P1 + e];
   }
   __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, part = threadIdx.x & 7;
+    const unsigned gmask = 0xffu << (lane & 24);
+    for (int l = 2; l <= l0; ++l) {
+      const int64_t bl = root >> (2 * (l0 - l));
+      const int c = (int)(bl & 3);
+      const size_t ce = (size_t)(level_offset(l) + bl) * P1;
+      // output o (A then B) by a group of 8 threads, each a strided part of
+      // the sum over n, combined by shuffles within the group
+      for (int o0 = 0; o0 < 2 * P1; o0 += (int)blockDim.x >> 3) {
+        const int o = o0 + ((int)threadIdx.x >> 3);
+        const bool act = o < 2 * P1;
+        const bool isb = o >= P1;
+        const int m = isb ? o - P1 : o;
+        cpx<R> acc = mk<R>(0, 0);
+        if (act) {
+          const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
+          const cpx<R> *src = cur + (isb ? P1 : 0);
+          for (int n = m + part; n < P1; n += 8) cfma(acc, isb ? conj(Tc[n]) : Tc[n], src[n]);
+        }
+#pragma unroll
+        for (int w = 1; w < 8; w <<= 1) {
+          acc.x += __shfl_xor_sync(gmask, acc.x, w);
+          acc.y += __shfl_xor_sync(gmask, acc.y, w);
+        }
+        if (act && part == 0) nxt[o] = acc + (isb ? B[ce + m] : A[ce + m]);
+      }
+      __syncthreads();
+      cpx<R> *t = cur; cur = nxt; nxt = t;
+    }
+  }
+  // the subtree, level l0 + 1 .. H
   int np = 1;
   for (int l = l0 + 1; l <= H; ++l) {
     const int nc = np * 4;
@@ -457,7 +480,7 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
         cfma(sa, Tc[n], pa[n]);
         cfma(sb, conj(Tc[n]), pb[n]);
       }
-      if (l == H) {
+      if (l == H && !EVAL) {
         A[ce] = sa;
         B[ce] = sb;
       } else {
@@ -468,6 +491,55 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
     __syncthreads();
     cpx<R> *t = cur; cur = nxt; nxt = t;
     np = nc;
+  }
+  if constexpr (EVAL) {
+    // L2P at the subtree's points (contiguous in tree order), plus the near
+    // sums; cur holds the leaf expansions (when k = 0, the root's)
+    int *lsb = reinterpret_cast<int *>(T + 4 * P1 * P1 + (size_t)4 * nbuf * P1);  // [nl + 1]
+    for (int e = threadIdx.x; e <= nl; e += blockDim.x) lsb[e] = leaf_start[lf0 + e];
+    __syncthreads();
+    const float invd = ev.dg->invd[H];
+    const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
+    const float i2pi = (float)(1.0 / HP_TWO_PI);
+    const int i1 = lsb[nl];
+    for (int i = lsb[0] + threadIdx.x; i < i1; i += blockDim.x) {
+      int lo = 0, hi = nl;  // lsb[lo] <= i < lsb[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (lsb[mid] <= i) lo = mid; else hi = mid;
+      }
+      const cf *Al = reinterpret_cast<const cf *>(cur) + (size_t)lo * 2 * P1;
+      const cf *Bl = Al + P1;
+      const float2 me = ev.loc[i];
+      const float4 nv = ev.near[i];
+      const cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
+      cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
+      for (int n = p - 1; n >= 0; --n) {
+        da = da * w + va;
+        va = va * w + Al[n];
+        db = db * wb + vb;
+        vb = vb * wb + Bl[n];
+      }
+      const float ur_ = va.x + vb.x - nv.x * c4;
+      const float ui_ = va.y + vb.y;
+      const cf gxo = invd * (da + db) + mk(-nv.y * i2pi, 0.f);
+      const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-nv.z * i2pi, 0.f);
+      const int64_t o = ev.perm[i];
+      double2 pv = make_double2(f2d(ur_), f2d(ui_));
+      double4_16a gv;
+      gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
+      if (box_iy((uint64_t)(lf0 + lo)) == 0) {  // bottom row: image/reaction sums already there
+        const double2 pm = reinterpret_cast<const double2 *>(ev.pot)[o];
+        pv.x += pm.x;
+        pv.y += pm.y;
+        if (ev.grad) {
+          const double4_16a gm = reinterpret_cast<const double4_16a *>(ev.grad)[o];
+          gv.x += gm.x; gv.y += gm.y; gv.z += gm.z; gv.w += gm.w;
+        }
+      }
+      reinterpret_cast<double2 *>(ev.pot)[o] = pv;
+      if (ev.grad) reinterpret_cast<double4_16a *>(ev.grad)[o] = gv;
+    }
   }
 }
 
@@ -480,9 +552,11 @@ size_t upward_smem(int p, int k) {
   return sizeof(cpx<R>) * (4 * P1 * P1 + nb * P1);
 }
 template <typename R>
-size_t downward_smem(int p, int k) {
-  size_t P1 = p + 1;
-  return sizeof(cpx<R>) * (4 * P1 * P1 + 4 * (size_t(1) << (2 * (k > 0 ? k - 1 : 0))) * P1);
+size_t downward_smem(int p, int k, bool eval) {
+  const size_t P1 = p + 1;
+  const size_t nbuf = eval ? (size_t(1) << (2 * k)) : (size_t(1) << (2 * (k > 0 ? k - 1 : 0)));
+  return sizeof(cpx<R>) * (4 * P1 * P1 + 4 * nbuf * P1) +
+         (eval ? sizeof(int) * ((size_t(1) << (2 * k)) + 1) : 0);
 }
 
 // --------------------------------------------------------------------------
@@ -496,7 +570,7 @@ constexpr int kM2LMaxRows = (HPFMM_MAX_P + 1 + 3) / 4;
 
 template <typename R>
 __global__ void __launch_bounds__(128)
-k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
+k_m2l_free(int l, int p, const DevGeom *__restrict__ dg, const cpx<R> *__restrict__ Tfree,
            const cd *__restrict__ logt, const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A,
            cpx<R> *__restrict__ B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -550,7 +624,7 @@ k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
                         // cancelling between A and B) is left out
         cd lt = logt[cls];
         R m0 = Ms[lane].x;  // M_0 is real for real charges
-        acc[0].x += m0 * (R)(lt.x + logd);
+        acc[0].x += m0 * (R)(lt.x + dg->logd[l]);
       }
     }
   }
@@ -573,228 +647,20 @@ k_m2l_free(int l, int p, double logd, const cpx<R> *__restrict__ Tfree,
 }
 
 // --------------------------------------------------------------------------
-// Patch form of the free-space M2L, used when everything fits in shared
-// memory.  A block owns an 8 x 8 patch of parent boxes of one level (so 64
-// target boxes of each child type); it stages the 20 x 20 patch of source
-// boxes' multipoles and the 40 translation matrices once, then warp w applies
-// the 27 offsets of child type w to its 64 targets (two per lane): the matrix
-// entry T[l][k] is a broadcast read shared by the warp, the source moment a
-// per-lane read.  All levels 2..H are processed by one launch.
-constexpr int kPatch = 8;                  // parents per block in x
-constexpr int kPatchRows = 4;              // parents per block in y
-constexpr int kPatchSrc = 2 * kPatch + 4;  // source boxes per block in x
-constexpr int kSrcRows = 2 * kPatchRows + 4;  // source boxes per block in y
-__constant__ signed char c_slot[49];      // 7x7 offset class -> 0..39, -1 for the near 3x3
-
-template <typename R, int P1>
-__global__ void __launch_bounds__(128)
-k_m2l_free_patch(int H, LevelGeom lgm, const cpx<R> *__restrict__ Tpad,
-                 const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
-                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status,
-                 RhsStride rs, const int *__restrict__ leaf_start, int skip_empty) {
-  M += blockIdx.y * rs.m;
-  A += blockIdx.y * rs.m;
-  B += blockIdx.y * rs.m;
-  // The translation of each class is applied in its Hankel form (see the
-  // table builder): moments scaled by 1/k! when staged, T'[l][k] = g_{l+k},
-  // outputs scaled by (-1)^{l+1}/l!.  Moment rows are padded to an even length
-  // PP so that k, k+1 pairs are one 16-byte (single precision) shared-memory
-  // load, and so are (g_j, g_{j+1}) -- from the second, shifted copy of g when
-  // j is odd.  The source patch is stored with even columns first, so that the
-  // sources of a warp's x-consecutive targets (all of one column parity) are
-  // consecutive boxes.
-  constexpr int PP = (P1 + 1) & ~1;
-  constexpr int GP = 2 * P1;
-  constexpr int HALF = kPatchSrc / 2;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ R fac_in[P1], fac_out[P1];                    // 1/k!, (-1)^{l+1}/l!
-  __shared__ unsigned char sempty[kPatchSrc * kSrcRows];  // source box holds no point
-  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][2][GP]
-  cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [12][20][PP]
-  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kSrcRows * PP);  // [40] ln|t d|
-  // level and patch of this block: kPatch x kPatchRows parents, whose four
-  // children of each type are the block's targets (one per thread)
-  int b = blockIdx.x, l = 2;
-  for (; l <= H; ++l) {
-    const int nps = 1 << (l - 1);
-    const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
-    if (b < npx * npy) break;
-    b -= npx * npy;
-  }
-  const int npx = (1 << (l - 1)) / kPatch < 1 ? 1 : (1 << (l - 1)) / kPatch;
-  const int px0 = (b % npx) * kPatch, py0 = (b / npx) * kPatchRows;
-  const int nparent_side = 1 << (l - 1), nside = 1 << l;
-  const int64_t off = level_offset(l);
-  const R logd = (R)lgm.logd[l];
-  // the 40 Hankel vectors: one bulk copy (TMA) from the table
-  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * 2 * GP);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, tbytes);
-    bulk_g2s(Ts, Tpad, tbytes, &bar);
-  }
-  for (int c = threadIdx.x; c < 49; c += blockDim.x)
-    if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
-  if (threadIdx.x < P1) {
-    double f = 1.0;
-    for (int i = 2; i <= (int)threadIdx.x; ++i) f *= (double)i;
-    fac_in[threadIdx.x] = (R)(1.0 / f);
-    fac_out[threadIdx.x] = (R)(((threadIdx.x & 1) ? 1.0 : -1.0) / f);
-  }
-  __syncthreads();
-  // source patch: one box per thread and iteration, P1 independent loads each
-  const int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
-  for (int sb = threadIdx.x; sb < kPatchSrc * kSrcRows; sb += blockDim.x) {
-    const int row = sb / kPatchSrc, colp = sb % kPatchSrc;  // colp: parity-split column
-    const int col = (colp < HALF) ? 2 * colp : 2 * (colp - HALF) + 1;
-    const int sx = sx0 + col, sy = sy0 + row;
-    cpx<R> *dst = Mp + (size_t)sb * PP;
-    bool empty = true;
-    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
-      // points of the box: its leaves are contiguous in Morton order
-      const uint64_t mb = box_morton(sx, sy);
-      const int sh = 2 * (H - l);
-      empty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
-    }
-    sempty[sb] = empty ? 1 : 0;
-    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
-      const cpx<R> *src = M + (size_t)(off + box_morton(sx, sy)) * P1;
-      cpx<R> v[P1];
-#pragma unroll
-      for (int k = 0; k < P1; ++k) v[k] = src[k];
-#pragma unroll
-      for (int k = 0; k < P1; ++k) dst[k] = fac_in[k] * v[k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < P1; ++k) dst[k] = mk<R>(0, 0);
-    }
-    if (PP > P1) dst[PP - 1] = mk<R>(0, 0);
-  }
-  __syncthreads();  // also publishes the mbarrier initialisation
-  if (!mbar_wait_bounded(&bar, 0)) {
-    if (threadIdx.x == 0) atomicOr(status, HPFMM_DEV_TIMEOUT);
-    mbar_wait_bounded(&bar, 0);  // give the copy a second bounded chance to land
-    return;
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int a = warp & 1, bb = warp >> 1;  // child type handled by this warp
-  const int pxA = px0 + (lane & 7), pyA = py0 + (lane >> 3);
-  const bool vA = pxA < nparent_side && pyA < nparent_side;
-  const int txA = 2 * pxA + a, tyA = 2 * pyA + bb;
-  cpx<R> accA[P1];
-#pragma unroll
-  for (int r = 0; r < P1; ++r) accA[r] = mk<R>(0, 0);
-  // boxes holding no point need no local expansion (nothing is evaluated in
-  // them or below them); a warp whose targets are all empty skips the
-  // translations, and so does a warp whose sources of a class are all empty
-  // (their moments are zero).  Not for evaluation at separate targets, which
-  // may lie in empty boxes.
-  bool tempty = true;
-  if (skip_empty && vA) {
-    const int sh = 2 * (H - l);
-    const uint64_t mb = box_morton(txA, tyA);
-    tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
-  }
-  const bool skip_warp = skip_empty && __all_sync(0xffffffffu, tempty);
-  for (int dy = -2 - bb; dy <= 3 - bb && !skip_warp; ++dy) {
-    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
-      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-      const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
-      const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
-      const int colA = txA + dx - sx0;
-      const int cpA = (colA & 1) * HALF + (colA >> 1);
-      const int sbA = (tyA + dy - sy0) * kPatchSrc + cpA;
-      if (skip_empty && __all_sync(0xffffffffu, sempty[sbA])) continue;
-      const cpx<R> *mA = Mp + sbA * PP;
-#pragma unroll 1
-      for (int k = 0; k < PP; k += 2) {
-        const cpx<R> ma0 = mA[k], ma1 = mA[k + 1];
-#pragma unroll
-        for (int r = 0; r < P1; ++r) {
-          // (g_{r+k}, g_{r+k+1}): an aligned pair of copy 0 (r even) or copy 1 (r odd)
-          const cpx<R> *gp = (r & 1) ? G1 + (r + k - 1) : G0 + (r + k);
-          const cpx<R> t0 = gp[0], t1 = gp[1];
-          cfma(accA[r], t0, ma0);
-          cfma(accA[r], t1, ma1);
-        }
-      }
-      // M_0 ln|t d| on Re L_0, in the scaled outputs (L_0 = -L'_0; M'_0 = M_0)
-      accA[0].x -= mA[0].x * lg[slot];
-    }
-  }
-  const R s = (R)(-0.5 / HP_TWO_PI);
-  if (vA) {
-    const size_t e0 = (size_t)(off + box_morton(txA, tyA)) * P1;
-#pragma unroll
-    for (int r = 0; r < P1; ++r) {
-      const cpx<R> v = (s * fac_out[r]) * accA[r];
-      A[e0 + r] = v;
-      B[e0 + r] = conj(v);
-    }
-  }
-}
-
-template <typename R, int P1>
-size_t patch_smem() {
-  constexpr int PP = (P1 + 1) & ~1;
-  return sizeof(cpx<R>) * (40 * 2 * 2 * P1 + kPatchSrc * kSrcRows * PP) + sizeof(R) * 40;
-}
-
-int patch_blocks(int H) {
-  int nb = 0;
-  for (int l = 2; l <= H; ++l) {
-    const int nps = 1 << (l - 1);
-    const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
-    nb += npx * npy;
-  }
-  return nb;
-}
-
-// dispatch on the (compile-time) order; returns false when no patch kernel
-// exists for this order / precision or it does not fit in shared memory
+// The patch form of the free-space M2L (m2l_patch.cuh) is instantiated for
+// every order in two translation units; this dispatches on p.
 template <typename R>
-bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, const cd *logt,
+bool launch_m2l_patch(int p, int H, const DevGeom *dg, const cpx<R> *Tpad, const cd *logt,
                       const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st,
                       int nr, RhsStride rs, const int *leaf_start, int skip_empty) {
   if constexpr (sizeof(R) == 8) {
     return false;  // the patch form is the single-precision path only
   } else {
-  if (!Tpad) return false;
-  int nb = patch_blocks(H);
-  // the shared-memory attribute is set once per device and order (so that a
-  // stream capture of an evaluation issues launches only)
-  static std::mutex mu;
-  static signed char attr[64][2][41];  // 0 unknown, 1 set, -1 failed
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || p < 0 || p > 40) return false;
-  const int pr = sizeof(R) == 8 ? 1 : 0;
-#define HP_PATCH_CASE(PP)                                                                 \
-  case PP: {                                                                              \
-    size_t sm = patch_smem<R, PP + 1>();                                                  \
-    if (sm > 227 * 1024) return false;                                                    \
-    {                                                                                     \
-      std::lock_guard<std::mutex> lock(mu);                                               \
-      if (attr[dev][pr][p] == 0) {                                                        \
-        bool ok = cudaFuncSetAttribute(k_m2l_free_patch<R, PP + 1>,                       \
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                       (int)sm) == cudaSuccess;                           \
-        if (!ok) cudaGetLastError();                                                      \
-        attr[dev][pr][p] = ok ? 1 : -1;                                                   \
-      }                                                                                   \
-      if (attr[dev][pr][p] < 0) return false;                                             \
-    }                                                                                     \
-    k_m2l_free_patch<R, PP + 1><<<dim3(nb, nr), 128, sm, st>>>(                           \
-        H, lgm, Tpad, logt, M, A, B, status, rs, leaf_start, skip_empty);                    \
-    return true;                                                                          \
-  }
-  switch (p) {
-    HP_PATCH_CASE(4) HP_PATCH_CASE(6) HP_PATCH_CASE(8) HP_PATCH_CASE(10) HP_PATCH_CASE(12)
-    HP_PATCH_CASE(14) HP_PATCH_CASE(16) HP_PATCH_CASE(18) HP_PATCH_CASE(20)
-    default: return false;
-  }
-#undef HP_PATCH_CASE
+    if (p <= kPatchSplitP)
+      return m2l_patch_launch_lo(p, H, dg, Tpad, logt, M, A, B, status, st, nr, rs, leaf_start,
+                                 skip_empty);
+    return m2l_patch_launch_hi(p, H, dg, Tpad, logt, M, A, B, status, st, nr, rs, leaf_start,
+                               skip_empty);
   }
 }
 
@@ -816,7 +682,8 @@ bool launch_m2l_patch(int p, int H, const LevelGeom &lgm, const cpx<R> *Tpad, co
 // every thread waits (bounded) before the buffers are reused.
 template <int P1>
 __global__ void __launch_bounds__(128)
-k_m2l_free_tc(int l, int rct, int nr, float logd, const float *__restrict__ Btab,
+k_m2l_free_tc(int l, int rct, int nr, const DevGeom *__restrict__ dg,
+              const float *__restrict__ Btab,
               const cd *__restrict__ logt, const cf *__restrict__ M, cf *__restrict__ A,
               cf *__restrict__ B, RhsStride rs, int *__restrict__ status) {
   constexpr int KP = tc_kp(P1), NP = tc_np(P1);
@@ -830,6 +697,7 @@ k_m2l_free_tc(int l, int rct, int nr, float logd, const float *__restrict__ Btab
   __shared__ unsigned tslot;
   __shared__ int failed;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const float logd = (float)dg->logd[l];
   const int G = 128 / rct;
   const int type = blockIdx.x & 3, grp = blockIdx.x >> 2;
   const int a = type & 1, bb = type >> 1;
@@ -977,7 +845,7 @@ size_t m2l_tc_smem() {
 int m2l_tc_rct(int nr) { return nr > 32 ? 64 : (nr > 16 ? 32 : 16); }
 
 // launches the tensor-core M2L for levels 2..H; false if p has no instance
-bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const float *Btab, const cd *logt,
+bool launch_m2l_tc(int p, int H, const DevGeom *dg, const float *Btab, const cd *logt,
                    const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
                    RhsStride rs) {
   if (!Btab) return false;
@@ -1005,7 +873,7 @@ bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const float *Btab, const 
     for (int l = 2; l <= H; ++l) {                                                          \
       const int npar = 1 << (2 * (l - 1));                                                  \
       const unsigned nx = (unsigned)(4 * ((npar + G - 1) / G));                             \
-      k_m2l_free_tc<PP + 1><<<dim3(nx, ny), 128, sm, st>>>(l, rct, nr, (float)lgm.logd[l],  \
+      k_m2l_free_tc<PP + 1><<<dim3(nx, ny), 128, sm, st>>>(l, rct, nr, dg,                  \
                                                            Btab, logt, M, A, B, rs, status); \
     }                                                                                       \
     return true;                                                                            \
@@ -1025,7 +893,7 @@ bool launch_m2l_tc(int p, int H, const LevelGeom &lgm, const float *Btab, const 
 // levels add to the free-space result.
 template <typename R>
 __global__ void __launch_bounds__(128)
-k_m2l_mirror_all(int H, int p, LevelGeom lgm, const cpx<R> *__restrict__ Timg,
+k_m2l_mirror_all(int H, int p, const DevGeom *__restrict__ dg, const cpx<R> *__restrict__ Timg,
                  const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
                  const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B,
                  RhsStride rs) {
@@ -1045,7 +913,7 @@ k_m2l_mirror_all(int H, int p, LevelGeom lgm, const cpx<R> *__restrict__ Timg,
   const int ixt = t % nx, iyt = t / nx, px = ixt >> 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t off = level_offset(l);
-  const R logd = (R)lgm.logd[l];
+  const R logd = (R)dg->logd[l];
   cpx<R> *ms = msh + warp * P1;
   cpx<R> aL[2], aC[2], aD[2];
   for (int r = 0; r < 2; ++r) aL[r] = aC[r] = aD[r] = mk<R>(0, 0);
@@ -1121,10 +989,11 @@ struct SrcPt64 { double x, y, q; };
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_eval64(const double *__restrict__ xs, const double *__restrict__ ys,
          const double *__restrict__ qs, const int64_t *__restrict__ perm,
-         const int *__restrict__ leaf_start, int H, double x0, double side, int p, cd kappa,
-         const cd *__restrict__ A, const cd *__restrict__ B, double *__restrict__ pot,
+         const int *__restrict__ leaf_start, int H, const DevGeom *__restrict__ dg, int p,
+         cd kappa, const cd *__restrict__ A, const cd *__restrict__ B, double *__restrict__ pot,
          double *__restrict__ grad) {
   __shared__ SrcPt64 sp[kWarpsPerBlock][32];
+  const double x0 = dg->x0, side = dg->side;
   int P1 = p + 1;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int leaf = blockIdx.x * kWarpsPerBlock + warp;
@@ -1230,32 +1099,49 @@ __device__ __forceinline__ float xsum(float v, int from) {
 // tile geometry of the single-precision leaf kernel
 constexpr int kTl = 4;             // target leaves per tile side
 constexpr int kTlP = kTl + 2;      // patch leaves per side
-constexpr int kTlCap = 3072;       // staged points per block
+constexpr int kTlCap = 2560;       // staged points per block
 constexpr int kLsBytes = 80;       // tile leaf starts (kTl^2 + 1 ints), 16-byte padded
 
 // Single-precision leaf evaluation with one target per lane.  A block takes
 // a 4 x 4 tile of leaves -- 16 consecutive Morton leaves, so its targets are
 // one contiguous range of the sorted points -- and stages the 6 x 6 leaves
-// around it in shared memory as (x, y, q) in each point's own leaf frame.
-// Warps take 32 consecutive targets of the tile at a time; a lane finds its
-// target's leaf and sums over that leaf's 3 x 3 neighbourhood in the staged
-// patch (each neighbour range shifted by its exact leaf offset), skipping
-// itself by index.  Lanes of one warp may belong to two or three leaves: they
-// run the same loops with their own bounds.  No per-group split of the
-// sources and no cross-lane reduction.  Then L2P with the target's leaf
-// expansions.  Patches larger than the buffer read from global memory.
-__device__ __forceinline__ void pair_loop(const float4 *__restrict__ src, int lo, int hi,
-                                          float sx, float sy, float &lf, float &gx, float &gy) {
+// around it in shared memory: the leaf-frame position of each point as a
+// float pair (hi, lo) and its charge.  Warps take 32 consecutive targets of
+// the tile at a time; a lane finds its target's leaf and sums over that
+// leaf's 3 x 3 neighbourhood in the staged patch, skipping itself by index.
+// The target is moved into each neighbour's frame by that leaf's exact
+// offset (the leaf side as hi + lo, the hi part added by an error-free sum),
+// so that a pair difference (x_i - x_j) is exact up to one rounding: without
+// the lo parts the float leaf frames would cost close pairs their relative
+// precision (an absolute error of about 2^-25 d in every difference).  Lanes
+// of one warp may belong to two or three leaves: they run the same loops with
+// their own bounds.  Then L2P with the target's leaf expansions.  Patches
+// larger than the buffer read from global memory.
+__device__ __forceinline__ void pair_loop(const float4 *__restrict__ src,
+                                          const float *__restrict__ srcq, int lo, int hi,
+                                          float sxh, float sxl, float syh, float syl, float &lf,
+                                          float &gx, float &gy) {
 #pragma unroll 4
   for (int k = lo; k < hi; ++k) {
     const float4 s = src[k];
-    const float dx = sx - s.x, dy = sy - s.y;
+    const float q = srcq[k];
+    const float dx = (sxh - s.x) + (sxl - s.z);
+    const float dy = (syh - s.y) + (syl - s.w);
     const float r2 = fmaf(dx, dx, dy * dy);
-    const float qi = s.z * fast_rcp(r2);
-    lf = fmaf(s.z, fast_lg2(r2), lf);
+    const float qi = q * fast_rcp(r2);
+    lf = fmaf(q, fast_lg2(r2), lf);
     gx = fmaf(qi, dx, gx);
     gy = fmaf(qi, dy, gy);
   }
+}
+
+// the target (hi, lo) shifted by -c leaf sides, as hi + lo: |c d| >= |hi|
+// for c != 0, so the fast two-sum is exact (c = 0 leaves it unchanged)
+__device__ __forceinline__ void frame_shift(float hi, float lo, int c, float d, float dlo,
+                                            float &sh, float &sl) {
+  const float b = -(float)c * d;
+  sh = b + hi;
+  sl = (hi - (sh - b)) + (lo - (float)c * dlo);
 }
 
 // MODE 1: the near field only, its three sums per point (sorted order)
@@ -1264,16 +1150,19 @@ __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src, int lo
 constexpr int kEvNear = 1, kEvFar = 2;
 template <int MODE>
 __global__ void __launch_bounds__(kEvWarps * 32, 4)
-k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
-          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
-          float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B,
-          double *__restrict__ pot, double *__restrict__ grad, float4 *__restrict__ near) {
+k_eval32p(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
+          const float *__restrict__ qs, const int64_t *__restrict__ perm,
+          const int *__restrict__ leaf_start, int H, const DevGeom *__restrict__ dg, int p,
+          const cf *__restrict__ A, const cf *__restrict__ B, double *__restrict__ pot,
+          double *__restrict__ grad, float4 *__restrict__ near) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int *ls = reinterpret_cast<int *>(smem_raw);         // [kTl^2 + 1] tile leaf starts
-  float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap]
-  int *pst = reinterpret_cast<int *>(src + kTlCap);    // [kTlP^2 + 1]
+  float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap] (hi, lo)
+  float *srcq = reinterpret_cast<float *>(src + kTlCap);          // [kTlCap] charges
+  int *pst = reinterpret_cast<int *>(srcq + kTlCap);   // [kTlP^2 + 1]
   int *pbeg = pst + kTlP * kTlP + 1;                   // [kTlP^2]
   const int P1 = p + 1;
+  const float d = dg->d[H], dlo = dg->dlo[H], invd = dg->invd[H];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = 1 << H;
   const int tps = nx >= kTl ? nx / kTl : 1;
@@ -1314,8 +1203,9 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     for (int pi = warp; pi < kTlP * kTlP; pi += kEvWarps) {
       const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
       for (int j = lane; j < cnt; j += 32) {
-        const float2 v = loc[b0 + j];
-        src[o + j] = make_float4(v.x, v.y, qs[b0 + j], 0.f);
+        const float2 v = loc[b0 + j], w = loclo[b0 + j];
+        src[o + j] = make_float4(v.x, v.y, w.x, w.y);
+        srcq[o + j] = qs[b0 + j];
       }
     }
   }
@@ -1337,40 +1227,49 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     float2 me = make_float2(0.f, 0.f);
     if (staged) {
       const int kself = pst[py * kTlP + px] + (i - ls[li]);
+      float2 ml = make_float2(0.f, 0.f);
       if (act) {
         const float4 m4 = src[kself];
         me = make_float2(m4.x, m4.y);
+        ml = make_float2(m4.z, m4.w);
       }
 #pragma unroll 1
       for (int r = -1; r <= 1; ++r) {
+        float syh, syl;
+        frame_shift(me.y, ml.y, r, d, dlo, syh, syl);
 #pragma unroll 1
         for (int c = -1; c <= 1; ++c) {
           const int pi = (py + r) * kTlP + (px + c);
           int lo = pst[pi], hi = pst[pi + 1];
           if (!act) hi = lo;
-          const float sx = me.x - (float)c * d, sy = me.y - (float)r * d;
+          float sxh, sxl;
+          frame_shift(me.x, ml.x, c, d, dlo, sxh, sxl);
           if (r == 0 && c == 0) {
-            pair_loop(src, lo, act ? kself : lo, sx, sy, lf, gx, gy);
-            pair_loop(src, act ? kself + 1 : hi, hi, sx, sy, lf, gx, gy);
+            pair_loop(src, srcq, lo, act ? kself : lo, sxh, sxl, syh, syl, lf, gx, gy);
+            pair_loop(src, srcq, act ? kself + 1 : hi, hi, sxh, sxl, syh, syl, lf, gx, gy);
           } else {
-            pair_loop(src, lo, hi, sx, sy, lf, gx, gy);
+            pair_loop(src, srcq, lo, hi, sxh, sxl, syh, syl, lf, gx, gy);
           }
         }
       }
     } else if (MODE != kEvFar && act) {
       me = loc[i];
+      const float2 ml = loclo[i];
       for (int r = -1; r <= 1; ++r) {
+        float syh, syl;
+        frame_shift(me.y, ml.y, r, d, dlo, syh, syl);
         for (int c = -1; c <= 1; ++c) {
           const int mx = ix + c, my = iy + r;
           if (mx < 0 || my < 0 || mx >= nx || my >= nx) continue;
           const uint64_t sl = box_morton(mx, my);
           const int s0 = leaf_start[sl], s1 = leaf_start[sl + 1];
-          const float sx = me.x - (float)c * d, sy = me.y - (float)r * d;
+          float sxh, sxl;
+          frame_shift(me.x, ml.x, c, d, dlo, sxh, sxl);
           for (int k = s0; k < s1; ++k) {
             if (k == i) continue;
-            const float2 v = loc[k];
+            const float2 v = loc[k], w = loclo[k];
             const float q = qs[k];
-            const float dx = sx - v.x, dy = sy - v.y;
+            const float dx = (sxh - v.x) + (sxl - w.x), dy = (syh - v.y) + (syl - w.y);
             const float r2 = fmaf(dx, dx, dy * dy);
             const float qi = q * fast_rcp(r2);
             lf = fmaf(q, fast_lg2(r2), lf);
@@ -1423,7 +1322,8 @@ k_eval32p(const float2 *__restrict__ loc, const float *__restrict__ qs,
     if (grad) reinterpret_cast<double4_16a *>(grad)[o] = gv;
   }
 }
-constexpr size_t kTpSmem = kLsBytes + sizeof(float4) * kTlCap + sizeof(int) * (2 * kTlP * kTlP + 1);
+constexpr size_t kTpSmem = kLsBytes + (sizeof(float4) + sizeof(float)) * kTlCap +
+                           sizeof(int) * (2 * kTlP * kTlP + 1);
 
 // Multi-RHS leaf evaluation (single precision).  The free-space near-field
 // pair kernel -- log2 r^2 and (dx, dy) / r^2 -- is formed once per pair and
@@ -1483,10 +1383,12 @@ __device__ __forceinline__ void multi_range(const float2 *pos, const float4 *qv,
 template <int RC>
 __global__ void __launch_bounds__(kEvWarps * 32, 2)
 k_eval32m(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp, int nr,
-          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H, float d,
-          float invd, int p, const cf *__restrict__ A, const cf *__restrict__ B, RhsStride rs,
-          double *__restrict__ pot, double *__restrict__ grad) {
+          const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
+          const DevGeom *__restrict__ dg, int p, const cf *__restrict__ A,
+          const cf *__restrict__ B, RhsStride rs, double *__restrict__ pot,
+          double *__restrict__ grad) {
   constexpr int NP = kMpW * kMpH;
+  const float d = dg->d[H], invd = dg->invd[H];
   __shared__ float2 spos[kMpCap];
   __shared__ float4 sq[kMpCap * (RC / 4)];
   __shared__ int pst[NP + 1], pbeg[NP];
@@ -1809,8 +1711,9 @@ __global__ void __launch_bounds__(kEvWarps * 32)
 k_mirror32(const float2 *__restrict__ loc, const float *__restrict__ yabs,
            const float *__restrict__ qs,
            const int64_t *__restrict__ perm, const int *__restrict__ leaf_start, int H,
-           float d, KappaLog K, float tau, double *__restrict__ pot, double *__restrict__ grad,
-           RhsStride rs, int assign) {
+           const DevGeom *__restrict__ dg, KappaLog K, float tau, double *__restrict__ pot,
+           double *__restrict__ grad, RhsStride rs, int assign) {
+  const float d = dg->d[H];
   qs += blockIdx.y * rs.q;
   pot += blockIdx.y * rs.out;
   if (grad) grad += blockIdx.y * 2 * rs.out;
@@ -2005,7 +1908,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     set_last_error("multi-RHS passes need the single-precision path and >= 2 levels");
     return HPFMM_EUNSUPPORTED;
   }
-  const LevelGeom lg = level_geom(pl->side, H);
+  const DevGeom *dg = pl->dgeom;
 
   pass_begin(pl, st, PASS_GATHER);
   k_gather_q<R><<<dim3(cdiv_u(n, 256), nr), 256, 0, st>>>(
@@ -2030,14 +1933,14 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     fs = pl->side_stream;
     pass_begin(pl, st, PASS_EVAL);
     k_eval32p<kEvNear><<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
-        pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
+        pl->loc32, pl->loclo, (const float *)qs, pl->perm, pl->leaf_start, H, dg, p,
         (const cf *)A, (const cf *)B, pot, grad, pl->near);
     pass_end(pl, st, PASS_EVAL, 1);
     // the bottom-row image/reaction sums need only the sources too: written
     // now, added by the L2P kernel
     pass_begin(pl, st, PASS_NEAR_MIRROR);
     k_mirror32<<<dim3((unsigned)(1 << H), 1, kMirSplit), 32 * kEvWarps, 0, st>>>(
-        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
+        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, dg,
         kappa_log(pl->kre, pl->kim), pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f, pot,
         grad, rs, 1);
     pass_end(pl, st, PASS_NEAR_MIRROR, 1);
@@ -2048,52 +1951,48 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (ksub > 4) ksub = 4;
   if (ksub < 1) ksub = H - 1 < 1 ? H - 1 : 1;
   if (pl->subtree > 0) ksub = pl->subtree < H - 1 ? pl->subtree : H - 1;
-  while (ksub > 1 && (upward_smem<R>(p, ksub) > kFusedSmem || downward_smem<R>(p, ksub) > kFusedSmem))
+  while (ksub > 1 &&
+         (upward_smem<R>(p, ksub) > kFusedSmem || downward_smem<R>(p, ksub, false) > kFusedSmem))
     --ksub;
   const int l0 = H - ksub;
   if (sizeof(R) == 8) {
-    LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
+    LeafPoints<double> lp{pl->xs, pl->ys, 0.0};
     size_t shp2m = sizeof(cd) * P1 * 33 * kWarpsPerBlock;
     k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, fs>>>(
-        lp, (const double *)qs, pl->leaf_start, H, pl->x0, pl->side, p, (cd *)M);
+        lp, (const double *)qs, pl->leaf_start, H, dg, p, (cd *)M);
   } else {
     LeafPoints<float> lp{pl->loc32};
     if (mw)
       k_s2m_multi<kRhsChunk><<<dim3(cdiv_u((int64_t)pl->nleaf * P1, 256), mw->rp / kRhsChunk),
                                256, 0, fs>>>(pl->loc32, (const float *)mw->qsm, mw->rp, nr,
-                                             pl->leaf_start, H, lg.invd[H], p, (cf *)M, rs);
+                                             pl->leaf_start, H, dg, p, (cf *)M, rs);
     else
       k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * ((P1 + kS2mGroup - 1) / kS2mGroup), 256),
                             256, 0, fs>>>(
-          lp, (const float *)qs, pl->leaf_start, H, pl->x0, pl->side, lg.invd[H], p, (cf *)M, rs);
+          lp, (const float *)qs, pl->leaf_start, H, dg, p, (cf *)M, rs);
   }
   pass_end(pl, fs, PASS_P2M, 1);
   pass_begin(pl, fs, PASS_M2M);
+  // the subtree blocks; when every level above them is small, the last of
+  // them also runs those (levels l0 - 1 .. 1), otherwise the levels of 1024
+  // boxes and more get one launch each and the small top levels one block
+  const bool coarse_in_upward = ksub > 0 && l0 <= ksub;
   if (ksub > 0) {
     size_t sm = upward_smem<R>(p, ksub);
     unsigned nb = (unsigned)(int64_t(1) << (2 * l0));
-    if (sizeof(R) == 8) {
-      LeafPoints<double> lp{pl->xs, pl->ys, pl->x0};
-      k_upward<double><<<nb, 256, sm, fs>>>(lp, (const double *)qs, pl->leaf_start, H, ksub,
-                                            pl->x0, pl->side, p, (const cd *)Tm2m, (cd *)M, rs);
-    } else {
-      LeafPoints<float> lp{pl->loc32};
-      k_upward<float><<<dim3(nb, nr), 256, sm, fs>>>(lp, (const float *)qs, pl->leaf_start, H,
-                                                     ksub, pl->x0, pl->side, p,
-                                                     (const cf *)Tm2m, (cf *)M, rs);
-    }
+    k_upward<R><<<dim3(nb, nr), 256, sm, fs>>>(H, ksub, p, Tm2m, M, rs,
+                                               coarse_in_upward ? pl->ctr : nullptr);
   }
-
-  // coarse levels l0 - 1 .. 1: levels of 1024 boxes and more one launch each,
-  // the small top levels in one block
   int nm2m = ksub > 0 ? 1 : 0;
-  for (int l = l0 - 1; l >= kCoarseBig; --l, ++nm2m)
-    k_m2m_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, fs>>>(
-        l, p, Tm2m, M, rs);
-  const int lsmall = l0 - 1 < kCoarseBig - 1 ? l0 - 1 : kCoarseBig - 1;
-  if (lsmall >= 1) {
-    k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, fs>>>(lsmall, p, Tm2m, M, rs);
-    ++nm2m;
+  if (!coarse_in_upward) {
+    for (int l = l0 - 1; l >= kCoarseBig; --l, ++nm2m)
+      k_m2m_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, fs>>>(
+          l, p, Tm2m, M, rs);
+    const int lsmall = l0 - 1 < kCoarseBig - 1 ? l0 - 1 : kCoarseBig - 1;
+    if (lsmall >= 1) {
+      k_m2m_coarse<R><<<dim3(1, nr), 1024, 0, fs>>>(lsmall, p, Tm2m, M, rs);
+      ++nm2m;
+    }
   }
   pass_end(pl, fs, PASS_M2M, nm2m);
   // downward pass: M2L at every level (free V-list from level 2, mirror list
@@ -2103,55 +2002,64 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (H >= 2 && sizeof(R) == 4) {
     pass_begin(pl, fs, PASS_M2L_FREE);
     if (mw && nr >= 16 && pl->m2l_mode == 1)
-      tc_m2l = patched = launch_m2l_tc(p, H, lg, (const float *)pl->t_m2l_tc, logs, (const cf *)M, (cf *)A,
+      tc_m2l = patched = launch_m2l_tc(p, H, dg, (const float *)pl->t_m2l_tc, logs, (const cf *)M, (cf *)A,
                               (cf *)B, pl->status, fs, nr, rs);
     if (!patched)
-      patched = launch_m2l_patch<R>(p, H, lg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
+      patched = launch_m2l_patch<R>(p, H, dg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
                                     pl->status, fs, nr, rs, pl->leaf_start, tw ? 0 : 1);
     pass_end(pl, fs, PASS_M2L_FREE, patched ? (tc_m2l ? H - 1 : 1) : 0);
   }
   if (mw && !patched) {
-    set_last_error("multi-RHS passes need the patch M2L kernel (even p in 4..20)");
+    set_last_error("multi-RHS passes need the patch M2L kernel (2 <= p <= %d)", HPFMM_MAX_P);
     return HPFMM_EUNSUPPORTED;
   }
   for (int l = 1; l <= H; ++l) {
-    double logd = log(pl->side / (double)(1 << l));
     if (l >= 2 && !patched) {
       dim3 g(cdiv_u(int64_t(1) << (2 * (l - 1)), 32), 4);
       pass_begin(pl, fs, PASS_M2L_FREE);
-      k_m2l_free<R><<<g, 128, shfree, fs>>>(l, p, logd, Tfree, logs, M, A, B);
+      k_m2l_free<R><<<g, 128, shfree, fs>>>(l, p, dg, Tfree, logs, M, A, B);
       pass_end(pl, fs, PASS_M2L_FREE, 1);
     }
   }
-  // the mirror M2L of all levels, after the free-space M2L it adds to
+  // the mirror M2L of all levels, after the free-space M2L it adds to; it
+  // reads the reaction tables of the last rebuild
+  HP_TRY(plan_join_tables(pl, fs));
   pass_begin(pl, fs, PASS_M2L_MIRROR);
   {
     unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
     size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
-    k_m2l_mirror_all<R><<<dim3(nb, nr), 128, sm, fs>>>(H, p, lg, Timg, logs + 49, Treact, M, A,
+    k_m2l_mirror_all<R><<<dim3(nb, nr), 128, sm, fs>>>(H, p, dg, Timg, logs + 49, Treact, M, A,
                                                          B, rs);
   }
   pass_end(pl, fs, PASS_M2L_MIRROR, 1);
-  pass_begin(pl, fs, PASS_L2L);
-  int nl2l = 0;
-  {
-    const int lsmall2 = l0 < kCoarseBig - 1 ? l0 : kCoarseBig - 1;
-    if (lsmall2 >= 2) {
-      k_l2l_coarse<R><<<dim3(1, nr), 1024, 0, fs>>>(lsmall2, p, Tl2l, A, B, rs);
-      ++nl2l;
-    }
-    for (int l = kCoarseBig; l <= l0; ++l, ++nl2l)
-      k_l2l_level<R><<<dim3(cdiv_u((int64_t(1) << (2 * l)) * P1, 256), nr), 256, 0, fs>>>(
-          l, p, Tl2l, A, B, rs);
+  // downward pass: L2L from level 1 to the leaves, each block of subtrees
+  // forming its root's expansion from its ancestors.  Split single precision:
+  // after the near field has joined, the same kernel evaluates the leaf
+  // expansions at the points (on the caller's stream); otherwise the leaf
+  // expansions go to memory for the leaf kernels below.
+  const DownEval noev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (split) {
+    HP_CUDA(cudaEventRecord(pl->ev_join, fs));
+    HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
+    int kd = H - 1 < 3 ? H - 1 : 3;  // subtrees of 64 leaves: 4^(H-3) blocks
+    while (kd > 0 && downward_smem<R>(p, kd, true) > kFusedSmem) --kd;
+    pass_begin(pl, st, PASS_L2L);
+    const DownEval ev{pl->loc32, pl->near, pl->perm, dg, pot, grad};
+    k_downward<R, true><<<dim3((unsigned)(int64_t(1) << (2 * (H - kd))), 1), 256,
+                          downward_smem<R>(p, kd, true), st>>>(H, kd, p, Tl2l, A, B, rs,
+                                                               pl->leaf_start, 1, ev);
+    pass_end(pl, st, PASS_L2L, 1);
+    HP_LAUNCH_CHECK();
+    return HPFMM_OK;
   }
+  pass_begin(pl, fs, PASS_L2L);
   if (ksub > 0)
-    k_downward<R><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256, downward_smem<R>(p, ksub),
-                    fs>>>(H, ksub, p, Tl2l, A, B, rs, pl->leaf_start, tw ? 0 : 1);
-  pass_end(pl, fs, PASS_L2L, nl2l + (ksub > 0 ? 1 : 0));
-  if (split) HP_CUDA(cudaEventRecord(pl->ev_join, fs));
-  // (split: the final L2P is timed with the downward pass, the near field on
-  // the side stream as the evaluation pass)
-  pass_begin(pl, st, split ? PASS_L2L : PASS_EVAL);
+    k_downward<R, false><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256,
+                           downward_smem<R>(p, ksub, false), fs>>>(H, ksub, p, Tl2l, A, B, rs,
+                                                                   pl->leaf_start, tw ? 0 : 1,
+                                                                   noev);
+  pass_end(pl, fs, PASS_L2L, ksub > 0 ? 1 : 0);
+  pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
   cd kappa = mk(pl->kre, pl->kim);
   if (tw) {
@@ -2173,29 +2081,25 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   }
   if (sizeof(R) == 8) {
     k_eval64<<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, st>>>(
-        pl->xs, pl->ys, (const double *)qs, pl->perm, pl->leaf_start, H, pl->x0, pl->side, p,
+        pl->xs, pl->ys, (const double *)qs, pl->perm, pl->leaf_start, H, dg, p,
         kappa, (const cd *)A, (const cd *)B, pot, grad);
   } else {
     float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
     if (mw) {
       k_eval32m<kRhsChunk><<<dim3(cdiv_u(pl->nleaf, kEvWarps), mw->rp / kRhsChunk),
                              32 * kEvWarps, 0, st>>>(
-          pl->loc32, (const float *)mw->qsm, mw->rp, nr, pl->perm, pl->leaf_start, H, lg.d[H],
-          lg.invd[H], p, (const cf *)A, (const cf *)B, rs, pot, grad);
+          pl->loc32, (const float *)mw->qsm, mw->rp, nr, pl->perm, pl->leaf_start, H, dg, p,
+          (const cf *)A, (const cf *)B, rs, pot, grad);
     } else {
-      HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
-      k_eval32p<kEvFar><<<(unsigned)(tps * tps), 32 * kEvWarps, kLsBytes, st>>>(
-          pl->loc32, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H], lg.invd[H], p,
-          (const cf *)A, (const cf *)B, pot, grad, pl->near);
+      set_last_error("single-RHS single-precision evaluation outside the split path");
+      return HPFMM_ECUDA;
     }
-    pass_end(pl, st, split ? PASS_L2L : PASS_EVAL, 1);
-    if (!split) {
-      pass_begin(pl, st, PASS_NEAR_MIRROR);
-      k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
-          pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, lg.d[H],
-          kappa_log(pl->kre, pl->kim), tau, pot, grad, rs, 0);
-      pass_end(pl, st, PASS_NEAR_MIRROR, 1);
-    }
+    pass_end(pl, st, PASS_EVAL, 1);
+    pass_begin(pl, st, PASS_NEAR_MIRROR);
+    k_mirror32<<<dim3((unsigned)(1 << H), nr, kMirSplit), 32 * kEvWarps, 0, st>>>(
+        pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, dg,
+        kappa_log(pl->kre, pl->kim), tau, pot, grad, rs, 0);
+    pass_end(pl, st, PASS_NEAR_MIRROR, 1);
   }
   if (sizeof(R) == 8) pass_end(pl, st, PASS_EVAL, 1);
   HP_LAUNCH_CHECK();
@@ -2212,29 +2116,22 @@ size_t fmm_shared_bytes_max(int p, bool fp64) {
 }
 
 hpfmm_status fmm_set_smem_limits(int p) {
-  signed char slot[49];
-  int k = 0;
-  for (int c = 0; c < 49; ++c) {
-    int dx = c % 7 - 3, dy = c / 7 - 3;
-    slot[c] = (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) ? -1 : (signed char)k++;
-  }
-  HP_CUDA(cudaMemcpyToSymbol(c_slot, slot, sizeof slot));
   size_t s64 = fmm_shared_bytes_max(p, true), s32 = fmm_shared_bytes_max(p, false);
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvNear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTpSmem));
-  HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvFar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFusedSmem));
-  HP_CUDA(cudaFuncSetAttribute(k_downward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kFusedSmem));
-  HP_CUDA(cudaFuncSetAttribute(k_downward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kFusedSmem));
+  HP_CUDA(cudaFuncSetAttribute(k_downward<double, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem));
+  HP_CUDA(cudaFuncSetAttribute(k_downward<float, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem));
+  HP_CUDA(cudaFuncSetAttribute(k_downward<float, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   return HPFMM_OK;
 }
@@ -2250,7 +2147,8 @@ hpfmm_status fmm_eval(hpfmm_plan *pl, const double *q, double *pot, double *grad
 }
 
 bool fmm_multi_supported(const hpfmm_plan *pl) {
-  return !pl->adaptive && pl->prec != HPFMM_FP64 && pl->H >= 2 && pl->p >= 4 && pl->p <= 20 && pl->p % 2 == 0;
+  return !pl->adaptive && pl->prec != HPFMM_FP64 && pl->H >= 2 && pl->p >= 2 &&
+         pl->p <= HPFMM_MAX_P;
 }
 
 int fmm_multi_rp(int nr) { return (nr + kRhsChunk - 1) / kRhsChunk * kRhsChunk; }
@@ -2268,7 +2166,7 @@ hpfmm_status fmm_eval_multi(hpfmm_plan *pl, const double *q, int nr, double *pot
                             void *qs, void *qsm, void *M, void *A, void *B, cudaStream_t st) {
   HP_TRY(special_init_here());
   if (!fmm_multi_supported(pl)) {
-    set_last_error("multi-RHS passes need single precision, >= 2 levels and even p in 4..20");
+    set_last_error("multi-RHS passes need single precision, >= 2 levels and p >= 2");
     return HPFMM_EUNSUPPORTED;
   }
   const MultiWork mw{nr, fmm_multi_rp(nr), qs, qsm, M, A, B};

@@ -1,0 +1,257 @@
+// m2l_patch.cuh -- the patch form of the free-space M2L (Eq. truncatedM2Lcoef
+// for the log kernel, the classic 2-D form the paper's Remark reduces to),
+// single precision, shared by the translation units that instantiate it for
+// each expansion order (m2l_patch_lo.cu: p <= kPatchSplitP, m2l_patch_hi.cu:
+// the higher orders), so that the orders compile in parallel.
+#pragma once
+
+#include <mutex>
+
+#include "common.cuh"
+#include "special.cuh"
+
+// strides between the right-hand sides of a multi-RHS evaluation (blockIdx.y
+// = RHS index): q in charges, m in expansion coefficients, out in doubles of
+// the potential (the gradient has twice that)
+struct RhsStride {
+  int64_t q, m, out;
+};
+
+// orders up to kPatchSplitP are instantiated in m2l_patch_lo.cu, the rest up
+// to HPFMM_MAX_P in m2l_patch_hi.cu; both return false when the order has no
+// instance or its shared memory does not fit
+constexpr int kPatchSplitP = 20;
+bool m2l_patch_launch_lo(int p, int H, const DevGeom *dg, const cf *Tpad, const cd *logt,
+                         const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
+                         RhsStride rs, const int *leaf_start, int skip_empty);
+bool m2l_patch_launch_hi(int p, int H, const DevGeom *dg, const cf *Tpad, const cd *logt,
+                         const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
+                         RhsStride rs, const int *leaf_start, int skip_empty);
+
+namespace {
+
+// A block owns a patch of kPatch x kPatchRows parent boxes of one level;
+// their four children of each type are its 128 targets, one per thread
+// (warp w: child type w).  It stages the (2 kPatch + 4) x (2 kPatchRows + 4)
+// source boxes' multipoles and the 40 translation vectors once; then each
+// thread applies the 27 V-list offsets of its child type to its target: the
+// vector entries are warp-uniform (broadcast) reads, the source moments
+// per-lane reads.  All levels 2..H are processed by one launch.
+constexpr int kPatch = 8;                  // parents per block in x
+constexpr int kPatchRows = 4;              // parents per block in y
+constexpr int kPatchSrc = 2 * kPatch + 4;  // source boxes per block in x
+constexpr int kSrcRows = 2 * kPatchRows + 4;  // source boxes per block in y
+// The Hankel factors are scaled by powers of R = 2^kHankelLog2R -- the
+// vector entries g_j by R^-j, the moment and output factors 1/k! and 1/l! by
+// R^k and R^l -- which leaves every product, and so every result, unchanged
+// bit for bit (powers of two scale exactly) but keeps the factors within the
+// single-precision range up to p = 40: (2p - 1)! alone overflows past p = 21
+// and 1/p! underflows past p = 33.  The table builder applies the same R.
+constexpr int kHankelLog2R = 4;
+
+// 7 x 7 offset class (dy + 3) * 7 + (dx + 3) -> its index among the 40 far
+// classes, -1 for the near 3 x 3
+__constant__ signed char c_slot[49] = {
+    0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, -1, -1, -1, 16, 17, 18, 19, -1, -1,
+    -1, 20, 21, 22, 23, -1, -1, -1, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39};
+
+template <typename R, int P1>
+__global__ void __launch_bounds__(128)
+k_m2l_free_patch(int H, const DevGeom *__restrict__ dg, const cpx<R> *__restrict__ Tpad,
+                 const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
+                 cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status,
+                 RhsStride rs, const int *__restrict__ leaf_start, int skip_empty) {
+  M += blockIdx.y * rs.m;
+  A += blockIdx.y * rs.m;
+  B += blockIdx.y * rs.m;
+  // The translation of each class is applied in its Hankel form (see the
+  // table builder): moments scaled by 16^k/k! when staged, T'[l][k] = g_{l+k},
+  // outputs scaled by (-1)^{l+1} 16^l/l!.  Moment rows are padded to an even length
+  // PP so that k, k+1 pairs are one 16-byte (single precision) shared-memory
+  // load, and so are (g_j, g_{j+1}) -- from the second, shifted copy of g when
+  // j is odd.  The source patch is stored with even columns first, so that the
+  // sources of a warp's x-consecutive targets (all of one column parity) are
+  // consecutive boxes.  The row stride PS is an odd number of 16-byte units,
+  // so that the 8 lanes of a quarter-warp (consecutive source boxes) hit 8
+  // different bank groups with their 16-byte (k, k+1) loads.
+  constexpr int PP = (P1 + 1) & ~1;
+  constexpr int PS = ((PP / 2) & 1) ? PP : PP + 2;
+  constexpr int GP = 2 * P1;
+  constexpr int HALF = kPatchSrc / 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ R fac_in[P1], fac_out[P1];  // 16^k / k!, (-1)^{l+1} 16^l / l!
+  __shared__ unsigned char sempty[kPatchSrc * kSrcRows];  // source box holds no point
+  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][2][GP]
+  cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [12][20][PS]
+  R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kSrcRows * PS);  // [40] ln|t d|
+  // level and patch of this block: kPatch x kPatchRows parents, whose four
+  // children of each type are the block's targets (one per thread)
+  int b = blockIdx.x, l = 2;
+  for (; l <= H; ++l) {
+    const int nps = 1 << (l - 1);
+    const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
+    if (b < npx * npy) break;
+    b -= npx * npy;
+  }
+  const int npx = (1 << (l - 1)) / kPatch < 1 ? 1 : (1 << (l - 1)) / kPatch;
+  const int px0 = (b % npx) * kPatch, py0 = (b / npx) * kPatchRows;
+  const int nparent_side = 1 << (l - 1), nside = 1 << l;
+  const int64_t off = level_offset(l);
+  const R logd = (R)dg->logd[l];
+  // the 40 Hankel vectors: one bulk copy (TMA) from the table
+  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * 2 * GP);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, tbytes);
+    bulk_g2s(Ts, Tpad, tbytes, &bar);
+  }
+  for (int c = threadIdx.x; c < 49; c += blockDim.x)
+    if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
+  if (threadIdx.x < P1) {
+    double f = 1.0;
+    for (int i = 2; i <= (int)threadIdx.x; ++i) f *= (double)i;
+    const double r = ldexp(1.0, kHankelLog2R * (int)threadIdx.x);
+    fac_in[threadIdx.x] = (R)(r / f);
+    fac_out[threadIdx.x] = (R)(((threadIdx.x & 1) ? r : -r) / f);
+  }
+  __syncthreads();
+  // source patch: one box per thread and iteration, P1 independent loads each
+  const int sx0 = 2 * px0 - 2, sy0 = 2 * py0 - 2;
+  for (int sb = threadIdx.x; sb < kPatchSrc * kSrcRows; sb += blockDim.x) {
+    const int row = sb / kPatchSrc, colp = sb % kPatchSrc;  // colp: parity-split column
+    const int col = (colp < HALF) ? 2 * colp : 2 * (colp - HALF) + 1;
+    const int sx = sx0 + col, sy = sy0 + row;
+    cpx<R> *dst = Mp + (size_t)sb * PS;
+    bool empty = true;
+    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
+      // points of the box: its leaves are contiguous in Morton order
+      const uint64_t mb = box_morton(sx, sy);
+      const int sh = 2 * (H - l);
+      empty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
+    }
+    sempty[sb] = empty ? 1 : 0;
+    if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
+      const cpx<R> *src = M + (size_t)(off + box_morton(sx, sy)) * P1;
+      cpx<R> v[P1];
+#pragma unroll
+      for (int k = 0; k < P1; ++k) v[k] = src[k];
+#pragma unroll
+      for (int k = 0; k < P1; ++k) dst[k] = fac_in[k] * v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < P1; ++k) dst[k] = mk<R>(0, 0);
+    }
+    if (PP > P1) dst[PP - 1] = mk<R>(0, 0);
+  }
+  __syncthreads();  // also publishes the mbarrier initialisation
+  if (!mbar_wait_bounded(&bar, 0)) {
+    if (threadIdx.x == 0) atomicOr(status, HPFMM_DEV_TIMEOUT);
+    mbar_wait_bounded(&bar, 0);  // give the copy a second bounded chance to land
+    return;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = warp & 1, bb = warp >> 1;  // child type handled by this warp
+  const int pxA = px0 + (lane & 7), pyA = py0 + (lane >> 3);
+  const bool vA = pxA < nparent_side && pyA < nparent_side;
+  const int txA = 2 * pxA + a, tyA = 2 * pyA + bb;
+  cpx<R> accA[P1];
+#pragma unroll
+  for (int r = 0; r < P1; ++r) accA[r] = mk<R>(0, 0);
+  // boxes holding no point need no local expansion (nothing is evaluated in
+  // them or below them); a warp whose targets are all empty skips the
+  // translations, and so does a warp whose sources of a class are all empty
+  // (their moments are zero).  Not for evaluation at separate targets, which
+  // may lie in empty boxes.
+  bool tempty = true;
+  if (skip_empty && vA) {
+    const int sh = 2 * (H - l);
+    const uint64_t mb = box_morton(txA, tyA);
+    tempty = leaf_start[(mb + 1) << sh] == leaf_start[mb << sh];
+  }
+  const bool skip_warp = skip_empty && __all_sync(0xffffffffu, tempty);
+  for (int dy = -2 - bb; dy <= 3 - bb && !skip_warp; ++dy) {
+    for (int dx = -2 - a; dx <= 3 - a; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
+      const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
+      const int colA = txA + dx - sx0;
+      const int cpA = (colA & 1) * HALF + (colA >> 1);
+      const int sbA = (tyA + dy - sy0) * kPatchSrc + cpA;
+      if (skip_empty && __all_sync(0xffffffffu, sempty[sbA])) continue;
+      const cpx<R> *mA = Mp + sbA * PS;
+#pragma unroll 1
+      for (int k = 0; k < PP; k += 2) {
+        const cpx<R> ma0 = mA[k], ma1 = mA[k + 1];
+#pragma unroll
+        for (int r = 0; r < P1; ++r) {
+          // (g_{r+k}, g_{r+k+1}): an aligned pair of copy 0 (r even) or copy 1 (r odd)
+          const cpx<R> *gp = (r & 1) ? G1 + (r + k - 1) : G0 + (r + k);
+          const cpx<R> t0 = gp[0], t1 = gp[1];
+          cfma(accA[r], t0, ma0);
+          cfma(accA[r], t1, ma1);
+        }
+      }
+      // M_0 ln|t d| on Re L_0, in the scaled outputs (L_0 = -L'_0; M'_0 = M_0)
+      accA[0].x -= mA[0].x * lg[slot];
+    }
+  }
+  const R s = (R)(-0.5 / HP_TWO_PI);
+  if (vA) {
+    const size_t e0 = (size_t)(off + box_morton(txA, tyA)) * P1;
+#pragma unroll
+    for (int r = 0; r < P1; ++r) {
+      const cpx<R> v = (s * fac_out[r]) * accA[r];
+      A[e0 + r] = v;
+      B[e0 + r] = conj(v);
+    }
+  }
+}
+
+template <typename R, int P1>
+size_t patch_smem() {
+  constexpr int PP = (P1 + 1) & ~1;
+  constexpr int PS = ((PP / 2) & 1) ? PP : PP + 2;
+  return sizeof(cpx<R>) * (40 * 2 * 2 * P1 + kPatchSrc * kSrcRows * PS) + sizeof(R) * 40;
+}
+
+int patch_blocks(int H) {
+  int nb = 0;
+  for (int l = 2; l <= H; ++l) {
+    const int nps = 1 << (l - 1);
+    const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
+    nb += npx * npy;
+  }
+  return nb;
+}
+
+// one order: sets the kernel's shared-memory limit once per device and
+// launches; false when it does not fit
+template <int P1>
+bool patch_launch_order(int H, const DevGeom *dg, const cf *Tpad, const cd *logt, const cf *M,
+                        cf *A, cf *B, int *status, cudaStream_t st, int nr, RhsStride rs,
+                        const int *leaf_start, int skip_empty) {
+  static std::mutex mu;
+  static signed char attr[64] = {};  // per device: 0 unknown, 1 set, -1 failed
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  const size_t sm = patch_smem<float, P1>();
+  if (sm > 227 * 1024) return false;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (attr[dev] == 0) {
+      const bool ok = cudaFuncSetAttribute(k_m2l_free_patch<float, P1>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm) == cudaSuccess;
+      if (!ok) cudaGetLastError();
+      attr[dev] = ok ? 1 : -1;
+    }
+    if (attr[dev] < 0) return false;
+  }
+  k_m2l_free_patch<float, P1><<<dim3(patch_blocks(H), nr), 128, sm, st>>>(
+      H, dg, Tpad, logt, M, A, B, status, rs, leaf_start, skip_empty);
+  return true;
+}
+
+}  // namespace

@@ -268,7 +268,8 @@ struct LeafGather {
   double *xs, *ys;
   int64_t *perm;
   float2 *loc32;
-  float *yabs;  // y rounded to single precision (with loc32)
+  float *yabs;    // y rounded to single precision (with loc32)
+  float2 *loclo;  // with loc32: the rest of the leaf-frame position
 };
 
 // centre of a leaf (double precision; the leaf side d = side / 2^H is exact)
@@ -284,7 +285,12 @@ __device__ __forceinline__ void gather_one(const LeafGather &g, double2 c, int k
   }
   g.perm[k] = j;
   if (g.loc32) {
-    g.loc32[k] = make_float2((float)(a - c.x), (float)(b - c.y));
+    // the leaf-frame position as a pair of floats (hi + lo), so that
+    // differences of nearby points keep their relative precision
+    const double rx = a - c.x, ry = b - c.y;
+    const float hx = (float)rx, hy = (float)ry;
+    g.loc32[k] = make_float2(hx, hy);
+    if (g.loclo) g.loclo[k] = make_float2((float)(rx - (double)hx), (float)(ry - (double)hy));
     g.yabs[k] = (float)b;
   }
 }
@@ -323,13 +329,12 @@ __device__ __forceinline__ void warp_sort_leaf(int b0, int m, int lane, uint64_t
   }
 }
 
-__global__ void __launch_bounds__(256)
-leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
-               int *__restrict__ vals, int *__restrict__ big, int *__restrict__ nbig,
-               LeafGather g) {
-  const int lane = threadIdx.x & 31;
-  const int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (leaf >= nleaf) return;
+// one leaf of at most 128 points by one warp; larger leaves are appended to
+// big[] (count in *nbig) for the block sort
+__device__ __forceinline__ void sort_small_leaf(int leaf, int lane, const int *__restrict__ start,
+                                                uint64_t *__restrict__ keys, int *__restrict__ vals,
+                                                int *__restrict__ big, int *__restrict__ nbig,
+                                                const LeafGather &g) {
   const int b0 = start[leaf], m = start[leaf + 1] - b0;
   if (m > 128) {
     if (lane == 0 && big) big[atomicAdd(nbig, 1)] = leaf;
@@ -343,6 +348,16 @@ leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ 
   if (m <= 32) warp_sort_leaf<1>(b0, m, lane, keys, vals, g, leaf);
   else if (m <= 64) warp_sort_leaf<2>(b0, m, lane, keys, vals, g, leaf);
   else warp_sort_leaf<4>(b0, m, lane, keys, vals, g, leaf);
+}
+
+__global__ void __launch_bounds__(256)
+leaf_sort_warp(const int *__restrict__ start, int nleaf, uint64_t *__restrict__ keys,
+               int *__restrict__ vals, int *__restrict__ big, int *__restrict__ nbig,
+               LeafGather g) {
+  const int lane = threadIdx.x & 31;
+  const int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (leaf >= nleaf) return;
+  sort_small_leaf(leaf, lane, start, keys, vals, big, nbig, g);
 }
 
 // sort the leaf buckets of more than 128 points, one block per leaf (blocks
@@ -389,42 +404,499 @@ __device__ void sort_leaf_global(uint64_t *__restrict__ keys, int *__restrict__ 
     }
   }
 }
+// one leaf of more than 128 points by the whole block (sk, sv: kLeafSort
+// entries of shared memory)
+__device__ void sort_big_leaf(int leaf, const int *__restrict__ start, uint64_t *__restrict__ keys,
+                              int *__restrict__ vals, const LeafGather &g, uint64_t *sk, int *sv) {
+  const int b0 = start[leaf], b1 = start[leaf + 1], m = b1 - b0;
+  if (m <= 128) return;
+  if (m > kLeafSort) {
+    __syncthreads();
+    sort_leaf_global(keys + b0, vals + b0, m);
+    if (g.x) {
+      const double2 c = g.loc32 ? leaf_centre(g, leaf) : make_double2(0, 0);
+      for (int e = threadIdx.x; e < m; e += blockDim.x) gather_one(g, c, b0 + e, vals[b0 + e]);
+    }
+    return;
+  }
+  int np2 = 1;
+  while (np2 < m) np2 <<= 1;
+  __syncthreads();
+  for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+    sk[e] = e < m ? keys[b0 + e] : ~0ull;
+    sv[e] = e < m ? vals[b0 + e] : 0x7fffffff;
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= np2; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+        int o = e ^ j;
+        if (o > e) {
+          bool up = (e & kk) == 0;
+          uint64_t ka = sk[e], kb = sk[o];
+          int va = sv[e], vb = sv[o];
+          bool gt = ka > kb || (ka == kb && va > vb);
+          if (gt == up) {
+            sk[e] = kb; sk[o] = ka;
+            sv[e] = vb; sv[o] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const double2 c = (g.x && g.loc32) ? leaf_centre(g, leaf) : make_double2(0, 0);
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    keys[b0 + e] = sk[e];
+    vals[b0 + e] = sv[e];
+    if (g.x) gather_one(g, c, b0 + e, sv[e]);
+  }
+}
+
 __global__ void __launch_bounds__(256)
 leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int *__restrict__ nbig,
           uint64_t *__restrict__ keys, int *__restrict__ vals, LeafGather g) {
   __shared__ uint64_t sk[kLeafSort];
   __shared__ int sv[kLeafSort];
   const int nb = *nbig;
-  for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {
-    const int leaf = big[bi];
-    int b0 = start[leaf], b1 = start[leaf + 1], m = b1 - b0;
-    if (m <= 128) continue;
-    if (m > kLeafSort) {
+  for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) sort_big_leaf(big[bi], start, keys, vals, g, sk, sv);
+}
+
+// ---------------------------------------------------------------------------
+// The tree build: six kernels at full occupancy, one thread per point or
+// bucket, with nothing waiting for the host.  Buckets are the boxes of a
+// level Hb >= H chosen so that they hold about one point each, so that
+// sorting a bucket is a few comparisons in one thread.
+//   k_tb_bbox     bounding-square partials per block; the last block to finish
+//                 reduces them, publishes the root square and the level
+//                 geometry (and, for asynchronous rebuilds, the validity flags
+//                 in the status word); the bucket counters are cleared
+//   k_tb_keys     Morton keys; bucket counts (the atomic's return value is the
+//                 point's slot in its bucket)
+//   k_tb_scan     exclusive scan of the counts within chunks of kScanChunk
+//                 buckets, chunk totals and maxima
+//   k_tb_scatter  chunk offsets (each block scans the chunk totals); bucket and
+//                 leaf starts; leaf centres; points scattered into buckets
+//   k_tb_sort     each bucket of up to kTinyBucket points sorted by (key, index)
+//                 in one thread (rank sort), with the gather into tree order;
+//                 larger buckets listed
+//   k_tb_big      the listed buckets: a warp each up to 128 points, else a block
+constexpr int kTinyBucket = 16;
+constexpr int kScanChunk = 4096;  // buckets per block of the scan (1024 threads x 4)
+constexpr int kBboxThreads = 512;
+
+struct TreeBuild {
+  const double *x, *y;
+  int64_t n;
+  int H, nleaf;         // leaf level of the outputs, 4^H
+  int Hb, nbucket;      // bucket level (>= H), 4^Hb
+  int nchunk;           // nbucket / kScanChunk, rounded up
+  double root_x0, root_side;
+  double kabs;          // |kappa|: the I_n range check of an asynchronous rebuild
+  int report;           // record invalid input / range in the status word
+  double *geo;          // x0, side, invalid flag, 2^30 / side, largest bucket (int)
+  DevGeom *dg;          // level geometry
+  uint64_t *keys;       // sorted keys
+  int *leaf_start;      // nleaf + 1
+  LeafGather g;
+  Geom *part;           // [bbox grid]
+  unsigned *ticket;     // last-block counter of k_tb_bbox
+  uint64_t *kb;         // [n] keys in input order
+  uint64_t *kt;         // [n] keys bucketed (sorted within a bucket by k_tb_sort)
+  int *slot, *vt;       // [n]: slot in the bucket; caller index, bucketed
+  int *bcount;          // [nbucket + 1]: counts, then chunk prefixes; [nbucket]: big buckets
+  int *bstart;          // [nbucket + 1] bucket starts
+  double2 *centre;      // [nleaf] leaf centres
+  int *ctot;            // [2 nchunk]: chunk totals, chunk maxima
+  int *big;             // [nbucket]
+  int *status;
+};
+
+// v as a pair of floats: hi = v rounded to single precision (to nearest,
+// ties to even) and lo = the rest (v - hi, exact in double) rounded; by
+// integer operations on the encodings, since the double-precision pipe and
+// its conversions are narrow on this GPU.  Exponents outside [-70, 100]
+// (zero, values a leaf frame cannot hold) take the plain conversions.
+__device__ __forceinline__ float2 split_to_floats(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < -70 || e > 100) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  }
+  const unsigned long long full = (b & 0xfffffffffffffull) | (1ull << 52);  // 53 bits
+  unsigned long long top = full >> 29;                                      // 24 bits
+  const unsigned rem = (unsigned)(full & 0x1fffffffull);                    // 29 bits
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (top & 1ull));
+  top += up ? 1ull : 0ull;
+  const int r = up ? (int)rem - (1 << 29) : (int)rem;  // v - hi in units of 2^(e-52)
+  int fe = e + 127;
+  if (top >> 24) {  // the rounding carried into the next binade
+    top >>= 1;
+    ++fe;
+  }
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)top & 0x7fffffu));
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);  // 2^(e-52), normal
+  const float lo = __int2float_rn(r) * scale;
+  return make_float2(hi, sign ? -lo : lo);
+}
+
+// v rounded to single precision by the same integer operations
+__device__ __forceinline__ float round_to_float(double v) { return split_to_floats(v).x; }
+
+// the gather of one point into tree order (the leaf centre precomputed)
+__device__ __forceinline__ void gather_point(const LeafGather &g, double2 c, int k, int j) {
+  const double a = g.x[j], b = g.y[j];
+  if (g.xs) {
+    g.xs[k] = a;
+    g.ys[k] = b;
+  }
+  g.perm[k] = j;
+  if (g.loc32) {
+    const float2 sx = split_to_floats(a - c.x), sy = split_to_floats(b - c.y);
+    g.loc32[k] = make_float2(sx.x, sy.x);
+    g.loclo[k] = make_float2(sx.y, sy.y);
+    g.yabs[k] = round_to_float(b);
+  }
+}
+
+__global__ void __launch_bounds__(kBboxThreads)
+k_tb_bbox(TreeBuild a) {
+  constexpr int NT = kBboxThreads;
+  __shared__ long long s0[NT], s1[NT], s2[NT];
+  __shared__ int sb[NT];
+  __shared__ int s_last;
+  const int64_t T = (int64_t)gridDim.x * NT;
+  const int64_t tid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  // the bucket counters start at zero for k_tb_keys
+  for (int64_t l = tid; l <= a.nbucket; l += T) a.bcount[l] = 0;
+  // partials: order-preserving integer images of the doubles (min / max on
+  // the integer pipe)
+  long long xmn = LLONG_MAX, xmx = LLONG_MIN, ymx = LLONG_MIN;
+  int bad = 0;
+  for (int64_t i = tid; i < a.n; i += T) {
+    const long long u = __double_as_longlong(a.x[i]), v = __double_as_longlong(a.y[i]);
+    const bool fin = ((u >> 52) & 0x7ff) != 0x7ff && ((v >> 52) & 0x7ff) != 0x7ff;
+    if (!fin || v <= 0) bad = 1;
+    const long long ku = u >= 0 ? u : (u ^ 0x7fffffffffffffffll);
+    xmn = min(xmn, ku);
+    xmx = max(xmx, ku);
+    ymx = max(ymx, v);
+  }
+  auto reduce = [&]() {
+    s0[threadIdx.x] = xmn;
+    s1[threadIdx.x] = xmx;
+    s2[threadIdx.x] = ymx;
+    sb[threadIdx.x] = bad;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        s0[threadIdx.x] = min(s0[threadIdx.x], s0[threadIdx.x + w]);
+        s1[threadIdx.x] = max(s1[threadIdx.x], s1[threadIdx.x + w]);
+        s2[threadIdx.x] = max(s2[threadIdx.x], s2[threadIdx.x + w]);
+        sb[threadIdx.x] |= sb[threadIdx.x + w];
+      }
       __syncthreads();
-      sort_leaf_global(keys + b0, vals + b0, m);
-      if (g.x) {
-        const double2 c = g.loc32 ? leaf_centre(g, leaf) : make_double2(0, 0);
-        for (int e = threadIdx.x; e < m; e += blockDim.x) gather_one(g, c, b0 + e, vals[b0 + e]);
+    }
+  };
+  reduce();
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = Geom{dkey_inv(s0[0]), dkey_inv(s1[0]), dkey_inv(s2[0]), sb[0]};
+    __threadfence();
+    s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // the last block: all partials, read past L1
+  __threadfence();
+  xmn = LLONG_MAX;
+  xmx = LLONG_MIN;
+  ymx = LLONG_MIN;
+  bad = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
+    const volatile Geom *pg = a.part + b;
+    const long long u = __double_as_longlong(pg->xmin), v = __double_as_longlong(pg->xmax);
+    xmn = min(xmn, u >= 0 ? u : (u ^ 0x7fffffffffffffffll));
+    xmx = max(xmx, v >= 0 ? v : (v ^ 0x7fffffffffffffffll));
+    ymx = max(ymx, __double_as_longlong(pg->ymax));
+    bad |= pg->bad;
+  }
+  __syncthreads();
+  reduce();
+  __shared__ double sg[4];
+  if (threadIdx.x == 0) {
+    *a.ticket = 0;  // ready for the next build
+    const double xmin = dkey_inv(s0[0]), xmax = dkey_inv(s1[0]), ymax = dkey_inv(s2[0]);
+    const double w = __dsub_rn(xmax, xmin);
+    double L = (w > ymax) ? w : ymax;
+    L = __dmul_rn(L, 1.0 + 0x1p-40);
+    double x0 = xmin, flag = sb[0] ? 1.0 : 0.0;
+    if (a.root_side > 0) {  // caller's root square: it must contain the points
+      const bool inside = a.root_x0 <= xmin && xmax <= a.root_x0 + a.root_side &&
+                          ymax <= a.root_side;
+      if (!inside && flag == 0.0) flag = 2.0;
+      x0 = a.root_x0;
+      L = a.root_side;
+    }
+    sg[0] = x0;
+    sg[1] = L;
+    sg[2] = flag;
+    sg[3] = __ddiv_rn(1073741824.0, L);
+    if (a.report) {
+      if (flag != 0.0) atomicOr(a.status, HPFMM_DEV_EINVAL);
+      else if (a.kabs * sqrt(5.0) * L > 60.0) atomicOr(a.status, HPFMM_DEV_RANGE);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) a.geo[threadIdx.x] = sg[threadIdx.x];
+  if (a.dg && threadIdx.x < 16) {
+    const int l = threadIdx.x;
+    const double d = ldexp(sg[1], -l);
+    const float dh = (float)d;
+    a.dg->d[l] = dh;
+    a.dg->dlo[l] = (float)(d - (double)dh);
+    a.dg->invd[l] = (float)(1.0 / d);
+    a.dg->logd[l] = log(d);
+    if (l == 0) {
+      a.dg->x0 = sg[0];
+      a.dg->side = sg[1];
+      a.dg->qscale = sg[3];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_tb_keys(TreeBuild a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double x0 = a.geo[0], L = a.geo[1], sc = a.geo[3];
+  const uint64_t ix = quantise(__dsub_rn(a.x[i], x0), L, sc);
+  const uint64_t iy = quantise(a.y[i], L, sc);
+  const uint64_t k = spread1((uint32_t)ix) | (spread1((uint32_t)iy) << 1);
+  a.kb[i] = k;
+  a.slot[i] = atomicAdd(&a.bcount[k >> (60 - 2 * a.Hb)], 1);
+}
+
+__global__ void __launch_bounds__(1024)
+k_tb_scan(TreeBuild a) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  int v[4], sum = 0, mx = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = c0 + j < a.nbucket ? a.bcount[c0 + j] : 0;
+    sum += v[j];
+    mx = max(mx, v[j]);
+  }
+  int x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  int wpre = 0, tot = 0;
+  for (int w = 0; w < 32; ++w) {
+    if (w < warp) wpre += ws[w];
+    tot += ws[w];
+  }
+  __syncthreads();
+  if (lane == 0) ws[warp] = mx;
+  __syncthreads();
+  int run = wpre + x - sum;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (c0 + j < a.nbucket) a.bcount[c0 + j] = run;
+    run += v[j];
+  }
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < 32; ++w) m = max(m, ws[w]);
+    a.ctot[blockIdx.x] = tot;
+    a.ctot[a.nchunk + blockIdx.x] = m;
+  }
+}
+
+// chunk offsets in shared memory: the exclusive scan of the chunk totals
+// (every block, nchunk <= kMaxChunks); returns the grand total, *mx the
+// largest bucket
+constexpr int kMaxChunks = 4096;
+__device__ int chunk_offsets(const TreeBuild &a, int *off, int *ws, int *mx) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = (a.nchunk + blockDim.x - 1) / blockDim.x;
+  const int t0 = min((int)threadIdx.x * per, a.nchunk), t1 = min(t0 + per, a.nchunk);
+  int sum = 0, m = 0;
+  for (int c = t0; c < t1; ++c) {
+    sum += a.ctot[c];
+    m = max(m, a.ctot[a.nchunk + c]);
+  }
+  int x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 31) ws[warp] = x;
+  if (lane == 0) ws[32 + warp] = m;
+  __syncthreads();
+  int wpre = 0, tot = 0, mm = 0;
+  for (int w = 0; w < nw; ++w) {
+    if (w < warp) wpre += ws[w];
+    tot += ws[w];
+    mm = max(mm, ws[32 + w]);
+  }
+  int run = wpre + x - sum;
+  for (int c = t0; c < t1; ++c) {
+    off[c] = run;
+    run += a.ctot[c];
+  }
+  __syncthreads();
+  *mx = mm;
+  return tot;
+}
+
+__global__ void __launch_bounds__(256)
+k_tb_scatter(TreeBuild a) {
+  __shared__ int off[kMaxChunks];
+  __shared__ int ws[64];
+  int maxbucket;
+  const int total = chunk_offsets(a, off, ws, &maxbucket);
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lsh = 2 * (a.Hb - a.H);
+  for (int64_t b = tid; b < a.nbucket; b += T) {
+    const int s = a.bcount[b] + off[b / kScanChunk];
+    a.bstart[b] = s;
+    if ((b & ((1 << lsh) - 1)) == 0) a.leaf_start[b >> lsh] = s;
+  }
+  if (tid == 0) {
+    a.bstart[a.nbucket] = total;
+    a.leaf_start[a.nleaf] = total;
+    int *mxp = (int *)(a.geo + 4);
+    *mxp = maxbucket;
+  }
+  if (a.g.loc32) {  // leaf centres (double precision, explicit roundings)
+    const double x0 = a.geo[0], d = ldexp(a.geo[1], -a.H);
+    for (int64_t l = tid; l < a.nleaf; l += T)
+      a.centre[l] = leaf_centre_at(x0, d, box_ix((uint64_t)l), box_iy((uint64_t)l));
+  }
+  const int sh = 60 - 2 * a.Hb;
+  for (int64_t i = tid; i < a.n; i += T) {
+    const uint64_t k = a.kb[i];
+    const int bk = (int)(k >> sh);
+    const int pos = a.bcount[bk] + off[bk / kScanChunk] + a.slot[i];
+    a.kt[pos] = k;
+    a.vt[pos] = (int)i;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_tb_sort(TreeBuild a) {
+  const int64_t bk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bk >= a.nbucket) return;
+  const int b0 = a.bstart[bk], m = a.bstart[bk + 1] - b0;
+  if (m == 0) return;
+  if (m > kTinyBucket) {
+    a.big[atomicAdd(a.bcount + a.nbucket, 1)] = (int)bk;
+    return;
+  }
+  const int sh = 60 - 2 * a.H;
+  for (int j = 0; j < m; ++j) {
+    const uint64_t kj = a.kt[b0 + j];
+    const int vj = a.vt[b0 + j];
+    int r = 0;
+    for (int i = 0; i < m; ++i) {
+      const uint64_t ki = a.kt[b0 + i];
+      const int vi = a.vt[b0 + i];
+      r += (ki < kj || (ki == kj && vi < vj)) ? 1 : 0;
+    }
+    a.keys[b0 + r] = kj;
+    const double2 c = a.g.loc32 ? a.centre[kj >> sh] : make_double2(0.0, 0.0);
+    gather_point(a.g, c, b0 + r, vj);
+  }
+}
+
+// buckets of more than kTinyBucket points: sorted in place in (kt, vt) by a
+// warp (up to 128 points, bitonic network in registers) or by the block (up
+// to kLeafSort in shared memory, larger ones in global memory), then the
+// sorted keys written to kout and the points gathered into tree order
+template <int E>
+__device__ __forceinline__ void warp_sort_bucket(int b0, int m, int lane, const uint64_t *kt,
+                                                 const int *vt, uint64_t *kout,
+                                                 const LeafGather &g, const double2 *centre,
+                                                 int sh) {
+  uint64_t k[E];
+  int v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * 32 + lane;
+    k[e] = i < m ? kt[b0 + i] : ~0ull;
+    v[e] = i < m ? vt[b0 + i] : 0x7fffffff;
+  }
+  warp_bitonic<E>(k, v, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * 32 + lane;
+    if (i < m) {
+      kout[b0 + i] = k[e];
+      gather_point(g, g.loc32 ? centre[k[e] >> sh] : make_double2(0.0, 0.0), b0 + i, v[e]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_tb_big(TreeBuild a) {
+  __shared__ uint64_t sk[kLeafSort];
+  __shared__ int sv[kLeafSort];
+  const int *maxb = (const int *)(a.geo + 4);
+  if (*maxb <= kTinyBucket) return;
+  const int nbig = a.bcount[a.nbucket];
+  const int sh = 60 - 2 * a.H;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t bi = gw; bi < nbig; bi += nw) {
+    const int bk = a.big[bi];
+    const int b0 = a.bstart[bk], m = a.bstart[bk + 1] - b0;
+    if (m > 128) continue;
+    if (m <= 32) warp_sort_bucket<1>(b0, m, lane, a.kt, a.vt, a.keys, a.g, a.centre, sh);
+    else if (m <= 64) warp_sort_bucket<2>(b0, m, lane, a.kt, a.vt, a.keys, a.g, a.centre, sh);
+    else warp_sort_bucket<4>(b0, m, lane, a.kt, a.vt, a.keys, a.g, a.centre, sh);
+  }
+  for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const int bk = a.big[bi];
+    const int b0 = a.bstart[bk], m = a.bstart[bk + 1] - b0;
+    if (m <= 128) continue;
+    __syncthreads();
+    if (m > kLeafSort) {
+      sort_leaf_global(a.kt + b0, a.vt + b0, m);
+      for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        const uint64_t k = a.kt[b0 + e];
+        a.keys[b0 + e] = k;
+        gather_point(a.g, a.g.loc32 ? a.centre[k >> sh] : make_double2(0.0, 0.0), b0 + e,
+                     a.vt[b0 + e]);
       }
       continue;
     }
     int np2 = 1;
     while (np2 < m) np2 <<= 1;
-    __syncthreads();
     for (int e = threadIdx.x; e < np2; e += blockDim.x) {
-      sk[e] = e < m ? keys[b0 + e] : ~0ull;
-      sv[e] = e < m ? vals[b0 + e] : 0x7fffffff;
+      sk[e] = e < m ? a.kt[b0 + e] : ~0ull;
+      sv[e] = e < m ? a.vt[b0 + e] : 0x7fffffff;
     }
     __syncthreads();
     for (int kk = 2; kk <= np2; kk <<= 1) {
       for (int j = kk >> 1; j > 0; j >>= 1) {
         for (int e = threadIdx.x; e < np2; e += blockDim.x) {
-          int o = e ^ j;
+          const int o = e ^ j;
           if (o > e) {
-            bool up = (e & kk) == 0;
-            uint64_t ka = sk[e], kb = sk[o];
-            int va = sv[e], vb = sv[o];
-            bool gt = ka > kb || (ka == kb && va > vb);
+            const bool up = (e & kk) == 0;
+            const uint64_t ka = sk[e], kb = sk[o];
+            const int va = sv[e], vb = sv[o];
+            const bool gt = ka > kb || (ka == kb && va > vb);
             if (gt == up) {
               sk[e] = kb; sk[o] = ka;
               sv[e] = vb; sv[o] = va;
@@ -434,211 +906,128 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
         __syncthreads();
       }
     }
-    const double2 c = (g.x && g.loc32) ? leaf_centre(g, leaf) : make_double2(0, 0);
     for (int e = threadIdx.x; e < m; e += blockDim.x) {
-      keys[b0 + e] = sk[e];
-      vals[b0 + e] = sv[e];
-      if (g.x) gather_one(g, c, b0 + e, sv[e]);
+      a.keys[b0 + e] = sk[e];
+      gather_point(a.g, a.g.loc32 ? a.centre[sk[e] >> sh] : make_double2(0.0, 0.0), b0 + e,
+                   sv[e]);
     }
   }
 }
-
-// ---------------------------------------------------------------------------
-// Stable LSD radix sort of (uint64 key, int value), 8-bit digits.
-// A tile of kTile = 256 x 8 elements per block; elements are taken in rounds
-// of 256 (one per thread, in order), so ranking by (round, warp, lane) keeps
-// the input order among equal digits.
-constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 8;
-constexpr int kTile = kSortThreads * kSortRounds;
-constexpr int kWarps = kSortThreads / 32;
-
-__global__ void __launch_bounds__(kSortThreads)
-radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, int nblocks,
-           unsigned *__restrict__ counts) {
-  __shared__ unsigned h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * kTile;
-  for (int r = 0; r < kSortRounds; ++r) {
-    int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];  // digit-major
-}
-
-// exclusive scan of the per-block counts of each digit (block d scans row d of
-// the digit-major table in place) and the digit totals
-__global__ void __launch_bounds__(256)
-radix_scan_digit(unsigned *__restrict__ counts, int nblocks, unsigned *__restrict__ totals) {
-  __shared__ unsigned ws[8];
-  unsigned *row = counts + (int64_t)blockIdx.x * nblocks;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned carry = 0;
-  for (int base = 0; base < nblocks; base += 256) {
-    int i = base + threadIdx.x;
-    unsigned v = (i < nblocks) ? row[i] : 0u;
-    unsigned x = v;  // inclusive warp scan
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[warp] = x;
-    __syncthreads();
-    unsigned wpre = 0, tot = 0;
-    for (int w = 0; w < 8; ++w) {
-      if (w < warp) wpre += ws[w];
-      tot += ws[w];
-    }
-    if (i < nblocks) row[i] = carry + wpre + x - v;
-    carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
-}
-
-__global__ void __launch_bounds__(kSortThreads)
-radix_scatter(const uint64_t *__restrict__ kin, const int *__restrict__ vin, int64_t n, int shift,
-              int nblocks, const unsigned *__restrict__ offs, const unsigned *__restrict__ totals,
-              uint64_t *__restrict__ kout, int *__restrict__ vout) {
-  __shared__ unsigned base_off[256];
-  __shared__ unsigned whist[kWarps][256];
-  __shared__ unsigned wsum[kWarps];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  {  // digit base = exclusive prefix of the digit totals
-    unsigned t = totals[threadIdx.x], x = t;
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    unsigned pre = 0;
-    for (int w = 0; w < warp; ++w) pre += wsum[w];
-    base_off[threadIdx.x] = pre + x - t + offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
-  }
-  int64_t tile = (int64_t)blockIdx.x * kTile;
-  unsigned lt_mask = (1u << lane) - 1u;
-  for (int r = 0; r < kSortRounds; ++r) {
-    for (int w = 0; w < kWarps; ++w) whist[w][threadIdx.x] = 0;
-    __syncthreads();
-    int64_t i = tile + r * kSortThreads + threadIdx.x;
-    bool valid = i < n;
-    uint64_t key = valid ? kin[i] : 0;
-    int val = valid ? vin[i] : 0;
-    unsigned d = valid ? (unsigned)((key >> shift) & 255u) : 256u;  // 256: no digit
-    unsigned same = __match_any_sync(0xffffffffu, d);
-    unsigned rank_in_warp = __popc(same & lt_mask);
-    if (valid && rank_in_warp == 0) whist[warp][d] = __popc(same);
-    __syncthreads();
-    if (valid) {
-      unsigned before = 0;
-      for (int w = 0; w < warp; ++w) before += whist[w][d];
-      unsigned pos = base_off[d] + before + rank_in_warp;
-      kout[pos] = key;
-      vout[pos] = val;
-    }
-    __syncthreads();
-    unsigned tot = 0;
-    for (int w = 0; w < kWarps; ++w) tot += whist[w][threadIdx.x];
-    base_off[threadIdx.x] += tot;
-    __syncthreads();
-  }
-}
-
-
 
 }  // namespace
 
-// Build (or rebuild) the tree of pl for the n points (x, y) (device pointers).
-// Leaves pl->xs, ys, perm, keys, leaf_start, loc32 filled and pl->geo (x0,
-// side, invalid flag, 2^30/side, largest leaf) on the device, and a copy of
-// geo in the plan's pinned host buffer followed by the event ev_geo; the host
-// values pl->x0 / side are set by tree_finish once that event has completed.
-//
-// Order: keys and leaf counts -> leaf offsets (scan) -> points bucketed by leaf
-// -> each bucket sorted by (key, index).  The result is the stable order by
-// (key, index) over all points.  Nothing waits for the host: leaves of any
-// size are sorted on the device.
+// Build (or rebuild) the tree of pl for the n points (x, y) (device pointers):
+// the six kernels above on `st`.  Leaves pl->keys, perm, leaf_start, the
+// tree-order coordinates (loc32 / loclo / yabs or xs / ys), pl->geo and
+// pl->dgeom filled on the device.  The host copies of the root square are set
+// by tree_finish.
 namespace {
 struct TreeTmp {
   char *base = nullptr;
   Geom *part;
-  uint64_t *kb;
-  int *va, *vb, *slot, *lcount, *btot, *bmax, *big;
-  unsigned *counts, *totals;
-  int nbR, nblocks;
+  uint64_t *kb, *kt;
+  int *vt, *slot, *bcount, *bstart, *ctot, *big;
+  double2 *centre;
+  int nbbox, Hb, nchunk;
 };
+
+// bucket level: about one point per bucket (level round(log4 n)), at least
+// the leaf level, at most level 11 (4M buckets) unless the leaves are deeper
+int bucket_level(int64_t n, int H) {
+  int hb = (int)floor(log((double)(n > 1 ? n : 1)) / log(4.0) + 0.5);
+  if (hb > 11) hb = 11;
+  return hb > H ? hb : H;
+}
 }  // namespace
 
 static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
   const int64_t n = pl->n;
   const int nleaf = pl->nleaf;
-  int64_t nbR64 = (n + kRedThreads - 1) / kRedThreads;
-  t.nbR = nbR64 < 1024 ? (int)nbR64 : 1024;
-  t.nblocks = (int)((n + kTile - 1) / kTile);
-  const int nsb = (nleaf + 1023) / 1024;
-  size_t bytes = sizeof(Geom) * t.nbR + sizeof(uint64_t) * n + 4 * sizeof(int) * n +
-                 sizeof(int) * (2 * (size_t)nleaf + 2) + 2 * sizeof(int) * nsb +
-                 sizeof(unsigned) * 256 * ((size_t)t.nblocks + 1);
-  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 13 * 256, st));
+  t.Hb = bucket_level(n, pl->Hsort);
+  const size_t nb = size_t(1) << (2 * t.Hb);
+  t.nchunk = (int)((nb + kScanChunk - 1) / kScanChunk);
+  if (t.nchunk > kMaxChunks) {
+    set_last_error("tree build: %d leaf levels exceed the bucket scan", pl->Hsort);
+    return HPFMM_EUNSUPPORTED;
+  }
+  int64_t nbb = (n + 4 * kBboxThreads - 1) / (4 * kBboxThreads);
+  t.nbbox = (int)(nbb < 1 ? 1 : (nbb > 1024 ? 1024 : nbb));
+  size_t bytes = sizeof(Geom) * t.nbbox + 2 * sizeof(uint64_t) * n + 2 * sizeof(int) * n +
+                 sizeof(int) * (3 * nb + 3) + sizeof(double2) * (size_t)nleaf +
+                 2 * sizeof(int) * (size_t)t.nchunk;
+  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 12 * 256, st));
   char *c = t.base;
   auto carve = [&](size_t b) {
     char *r = c;
     c += (b + 255) & ~size_t(255);
     return r;
   };
-  t.part = (Geom *)carve(sizeof(Geom) * t.nbR);
+  t.part = (Geom *)carve(sizeof(Geom) * t.nbbox);
   t.kb = (uint64_t *)carve(sizeof(uint64_t) * n);
-  t.va = (int *)carve(sizeof(int) * n);
-  t.vb = (int *)carve(sizeof(int) * n);
+  t.kt = (uint64_t *)carve(sizeof(uint64_t) * n);
+  t.vt = (int *)carve(sizeof(int) * n);
   t.slot = (int *)carve(sizeof(int) * n);
-  t.lcount = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));  // [nleaf] = big-leaf count
-  t.big = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
-  t.btot = (int *)carve(sizeof(int) * nsb);
-  t.bmax = (int *)carve(sizeof(int) * nsb);
-  t.counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)t.nblocks);
-  t.totals = (unsigned *)carve(sizeof(unsigned) * 256);
+  t.bcount = (int *)carve(sizeof(int) * (nb + 1));
+  t.bstart = (int *)carve(sizeof(int) * (nb + 1));
+  t.big = (int *)carve(sizeof(int) * (nb + 1));
+  t.centre = (double2 *)carve(sizeof(double2) * (size_t)nleaf);
+  t.ctot = (int *)carve(2 * sizeof(int) * (size_t)t.nchunk);
   return HPFMM_OK;
 }
 
 hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaStream_t st) {
-  const int64_t n = pl->n;
-  const int H = pl->Hsort, nleaf = pl->nleaf;
   TreeTmp t;
   HP_TRY(tree_alloc(pl, t, st));
-  pl->tree_tmp_bytes = 0;
-  int tb = 256;
-  unsigned gb = (unsigned)((n + tb - 1) / tb);
-  const int nsb = (nleaf + 1023) / 1024;
-  double *geo = pl->geo;
-  int *maxleaf = (int *)(geo + 4);
+  TreeBuild a;
+  a.x = x;
+  a.y = y;
+  a.n = pl->n;
+  a.H = pl->Hsort;
+  a.nleaf = pl->nleaf;
+  a.Hb = t.Hb;
+  a.nbucket = 1 << (2 * t.Hb);
+  a.nchunk = t.nchunk;
+  a.root_x0 = pl->root_x0;
+  a.root_side = pl->root_side;
+  a.kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
+  a.report = pl->async_update;
+  a.geo = pl->geo;
+  a.dg = pl->dgeom;
+  a.keys = pl->keys;
+  a.leaf_start = pl->leaf_start;
+  // the sorts also put the points into tree order (permutation, coordinates);
+  // adaptive plans: only the permutation, their leaf frames follow the
+  // adaptive build
+  a.g = pl->adaptive ? LeafGather{x, y, pl->geo, a.H, nullptr, nullptr, pl->perm, nullptr, nullptr,
+                                  nullptr}
+                     : LeafGather{x, y, pl->geo, a.H, pl->xs, pl->ys, pl->perm, pl->loc32,
+                                  pl->yabs, pl->loclo};
+  a.part = t.part;
+  a.ticket = pl->tree_ctr;
+  a.kb = t.kb;
+  a.kt = t.kt;
+  a.slot = t.slot;
+  a.vt = t.vt;
+  a.bcount = t.bcount;
+  a.bstart = t.bstart;
+  a.centre = t.centre;
+  a.ctot = t.ctot;
+  a.big = t.big;
+  a.status = pl->status;
+  const int64_t n = pl->n;
+  const unsigned gp = (unsigned)((n + 255) / 256);
+  const unsigned gb = (unsigned)(((int64_t)a.nbucket + 255) / 256);
   pass_begin(pl, st, PASS_TREE);
-  bbox_partial<<<t.nbR, kRedThreads, 0, st>>>(x, y, n, t.part);
-  bbox_final<<<1, kRedThreads, 0, st>>>(t.part, t.nbR, geo, pl->root_x0, pl->root_side);
-  // the geometry, for the host and for the table stream, is known from here on
-  cudaError_t e = cudaSuccess;
-  if (pl->hgeo) e = cudaMemcpyAsync(pl->hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && pl->ev_geo) e = cudaEventRecord(pl->ev_geo, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(t.lcount, 0, sizeof(int) * ((size_t)nleaf + 1), st);
-  morton_keys<<<gb, tb, 0, st>>>(x, y, n, geo, H, t.kb, t.va, t.lcount, t.slot);
-  scan_part<<<nsb, 1024, 0, st>>>(t.lcount, nleaf, pl->leaf_start, t.btot, t.bmax);
-  scan_top<<<1, 1024, 0, st>>>(t.btot, t.bmax, nsb, nleaf, pl->leaf_start, maxleaf);
-  scan_add<<<nsb, 1024, 0, st>>>(t.btot, nleaf, pl->leaf_start);
-  bucket_scatter<<<gb, tb, 0, st>>>(t.kb, t.slot, n, H, pl->leaf_start, pl->keys, t.vb);
-  // the leaf sorts also put the points into tree order (permutation, coordinates)
-  // (adaptive plans: only the permutation; their leaf frames follow the adaptive build)
-  const LeafGather lg = pl->adaptive
-                            ? LeafGather{x, y, geo, H, nullptr, nullptr, pl->perm, nullptr, nullptr}
-                            : LeafGather{x, y, geo, H, pl->xs, pl->ys, pl->perm, pl->loc32, pl->yabs};
-  leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
-      pl->leaf_start, nleaf, pl->keys, t.vb, t.big, t.lcount + nleaf, lg);
-  leaf_sort<<<160, 256, 0, st>>>(pl->leaf_start, t.big, t.lcount + nleaf, pl->keys, t.vb, lg);
-  pass_end(pl, st, PASS_TREE, 9);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  k_tb_bbox<<<t.nbbox, kBboxThreads, 0, st>>>(a);
+  k_tb_keys<<<gp, 256, 0, st>>>(a);
+  k_tb_scan<<<t.nchunk, 1024, 0, st>>>(a);
+  k_tb_scatter<<<(unsigned)(gp < 1216 ? gp : 1216), 256, 0, st>>>(a);
+  k_tb_sort<<<gb, 256, 0, st>>>(a);
+  k_tb_big<<<608, 256, 0, st>>>(a);
+  pass_end(pl, st, PASS_TREE, 6);
   // released (stream-ordered) by tree_finish
   pl->tree_tmp = t.base;
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error("tree_build launch: %s", cudaGetErrorString(e));
     return HPFMM_ECUDA;
@@ -646,19 +1035,21 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   return HPFMM_OK;
 }
 
-// Once the geometry has reached the host (hgeo): invalid-input check, host
-// copies of the root square, stream-ordered release of the temporaries.  Leaves
-// of any size are sorted on the device, so nothing here waits for the sort.
+// Stream-ordered release of the build temporaries, and (hgeo != nullptr,
+// the geometry has reached the host) the invalid-input check and the host
+// copies of the root square.
 hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st) {
   hpfmm_status s = HPFMM_OK;
-  if (hgeo[2] != 0.0) {
-    set_last_error(hgeo[2] == 2.0 ? "the root square does not contain the points"
-                                  : "points must be finite with y > 0");
-    s = HPFMM_EINVAL;
-  } else {
-    pl->x0 = hgeo[0];
-    pl->side = hgeo[1];
-    pl->qscale = hgeo[3];
+  if (hgeo) {
+    if (hgeo[2] != 0.0) {
+      set_last_error(hgeo[2] == 2.0 ? "the root square does not contain the points"
+                                    : "points must be finite with y > 0");
+      s = HPFMM_EINVAL;
+    } else {
+      pl->x0 = hgeo[0];
+      pl->side = hgeo[1];
+      pl->qscale = hgeo[3];
+    }
   }
   if (pl->tree_tmp) cudaFreeAsync(pl->tree_tmp, st);
   pl->tree_tmp = nullptr;
@@ -667,12 +1058,14 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the tree ordering, for callers that cannot call
-// cudaMalloc (for example code running inside a CUDA-graph capture that must
-// not allocate, or an embedding runtime that owns every device allocation and
-// forbids others).  It runs the same kernels as tree_build on up to
-// kNoAllocMaxN points, with every temporary carved from one file-scope device
-// array of kNoAllocBytes.  That array is part of the library image, so every
-// GPU on which the library is loaded holds it until the process exits.
+// cudaMalloc (an embedding runtime that owns every device allocation and
+// forbids others, or code that must not grow the device's memory use).  It
+// runs the multi-kernel form of the ordering (bounding square, keys, leaf
+// counts, scan, bucket scatter, per-leaf sorts; leaves of any size are sorted
+// on the device) on up to kNoAllocMaxN points, with every temporary carved
+// from one file-scope device array of kNoAllocBytes.  That array is part of
+// the library image, so every GPU on which the library is loaded holds it
+// until the process exits.
 namespace {
 constexpr int64_t kNoAllocMaxN = 65536;
 constexpr int kNoAllocMaxLevels = 8;
@@ -684,13 +1077,13 @@ __global__ void write_perm(const int *__restrict__ v, int64_t n, int64_t *__rest
   if (k < n) perm[k] = v[k];
 }
 
-// device address of g_noalloc_scratch on the current device (host code only
-// sees a host-side stand-in for the symbol); looked up once per device
-void *noalloc_scratch_address() {
+// device address of g_noalloc_scratch on device `dev` (current when called;
+// host code only sees a host-side stand-in for the symbol); looked up once
+// per device
+void *noalloc_scratch_address(int dev) {
   static std::mutex mu;
   static void *addr[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
   if (!addr[dev]) {
     void *p = nullptr;
@@ -701,6 +1094,16 @@ void *noalloc_scratch_address() {
     addr[dev] = p;
   }
   return addr[dev];
+}
+
+// device of a device pointer, -1 for anything else
+int pointer_device(const void *p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? at.device : -1;
 }
 }  // namespace
 
@@ -717,12 +1120,24 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
                    (long long)kNoAllocMaxN, kNoAllocMaxLevels, (long long)n, levels);
     return HPFMM_EINVAL;
   }
-  if (!is_device_pointer(x) || !is_device_pointer(y) || !is_device_pointer(keys) ||
-      !is_device_pointer(perm)) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("hpfmm_tree_order_noalloc: no current device");
+    return HPFMM_ECUDA;
+  }
+  const int dx = pointer_device(x), dy = pointer_device(y), dk = pointer_device(keys),
+            dp = pointer_device(perm);
+  if (dx < 0 || dy < 0 || dk < 0 || dp < 0) {
     set_last_error("hpfmm_tree_order_noalloc: x, y, keys and perm must be device memory");
     return HPFMM_EINVAL;
   }
-  char *base = (char *)noalloc_scratch_address();
+  if (dx != cur || dy != cur || dk != cur || dp != cur) {
+    set_last_error("hpfmm_tree_order_noalloc: x, y, keys and perm must be on the current "
+                   "device (%d)", cur);
+    return HPFMM_EINVAL;
+  }
+  char *base = (char *)noalloc_scratch_address(cur);
   if (!base) {
     set_last_error("hpfmm_tree_order_noalloc: cannot resolve the scratch array's device address");
     return HPFMM_ECUDA;
@@ -730,7 +1145,6 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
   cudaStream_t st = (cudaStream_t)stream;
   const int H = levels, nleaf = 1 << (2 * H);
   const int nbR = (int)((n + kRedThreads - 1) / kRedThreads);
-  const int nblocks = (int)((n + kTile - 1) / kTile);
   const int nsb = (nleaf + 1023) / 1024;
   char *c = base;
   auto carve = [&](size_t b) {
@@ -749,8 +1163,6 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
   int *lstart = (int *)carve(sizeof(int) * ((size_t)nleaf + 1));
   int *btot = (int *)carve(sizeof(int) * nsb);
   int *bmax = (int *)carve(sizeof(int) * nsb);
-  unsigned *counts = (unsigned *)carve(sizeof(unsigned) * 256 * (size_t)nblocks);
-  unsigned *totals = (unsigned *)carve(sizeof(unsigned) * 256);
   if ((size_t)(c - base) > kNoAllocBytes) {
     set_last_error("hpfmm_tree_order_noalloc: scratch layout exceeds %zu bytes", kNoAllocBytes);
     return HPFMM_EUNSUPPORTED;
@@ -765,11 +1177,17 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
   scan_top<<<1, 1024, 0, st>>>(btot, bmax, nsb, nleaf, lstart, (int *)(geo + 4));
   scan_add<<<nsb, 1024, 0, st>>>(btot, nleaf, lstart);
   bucket_scatter<<<gb, 256, 0, st>>>(kb, slot, n, H, lstart, keys, vb);
-  const LeafGather none{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // leaves of any size are sorted here: up to 128 points by a warp, up to
+  // kLeafSort in shared memory, larger ones in place in global memory
+  const LeafGather none{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                        nullptr};
   leaf_sort_warp<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, st>>>(
       lstart, nleaf, keys, vb, big, lcount + nleaf, none);
   leaf_sort<<<160, 256, 0, st>>>(lstart, big, lcount + nleaf, keys, vb, none);
+  write_perm<<<gb, 256, 0, st>>>(vb, n, perm);
   HP_LAUNCH_CHECK();
+  // the validity flag of the points comes back to the host: the call waits
+  // for the stream
   double hgeo[5];
   HP_CUDA(cudaMemcpyAsync(hgeo, geo, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
   HP_CUDA(cudaStreamSynchronize(st));
@@ -777,25 +1195,5 @@ extern "C" hpfmm_status hpfmm_tree_order_noalloc(const double *x, const double *
     set_last_error("hpfmm_tree_order_noalloc: points must be finite with y > 0");
     return HPFMM_EINVAL;
   }
-  int hmax = 0;
-  memcpy(&hmax, &hgeo[4], sizeof(int));
-  const int *sorted = vb;
-  if (hmax > kLeafSort) {  // a leaf too large for the in-block sort: full radix sort
-    morton_keys<<<gb, 256, 0, st>>>(x, y, n, geo, H, kb, va, nullptr, nullptr);
-    uint64_t *kin = kb, *kout = keys;
-    int *vin = va, *vout = vb;
-    for (int shift = 0; shift < 60; shift += 8) {
-      radix_hist<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, nblocks, counts);
-      radix_scan_digit<<<256, 256, 0, st>>>(counts, nblocks, totals);
-      radix_scatter<<<nblocks, kSortThreads, 0, st>>>(kin, vin, n, shift, nblocks, counts, totals,
-                                                       kout, vout);
-      uint64_t *tk = kin; kin = kout; kout = tk;
-      int *tv = vin; vin = vout; vout = tv;
-    }
-    HP_CUDA(cudaMemcpyAsync(keys, kb, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
-    sorted = va;
-  }
-  write_perm<<<gb, 256, 0, st>>>(sorted, n, perm);
-  HP_LAUNCH_CHECK();
   return HPFMM_OK;
 }

@@ -73,7 +73,7 @@ int main(void) {
   printf("hpfmm_options size %zu\n", sizeof(hpfmm_options));
   F(hpfmm_options, prec); F(hpfmm_options, tau_fp64); F(hpfmm_options, levels);
   F(hpfmm_options, subtree_levels); F(hpfmm_options, m2l_mode); F(hpfmm_options, adaptive);
-  F(hpfmm_options, reserved); F(hpfmm_options, root_x0); F(hpfmm_options, root_side);
+  F(hpfmm_options, async_update); F(hpfmm_options, reserved); F(hpfmm_options, root_x0); F(hpfmm_options, root_side);
   printf("hpfmm_plan_info size %zu\n", sizeof(hpfmm_plan_info));
   F(hpfmm_plan_info, n); F(hpfmm_plan_info, levels); F(hpfmm_plan_info, p);
   F(hpfmm_plan_info, prec); F(hpfmm_plan_info, x0); F(hpfmm_plan_info, side);
@@ -82,6 +82,12 @@ int main(void) {
   F(hpfmm_tuning, p); F(hpfmm_tuning, levels); F(hpfmm_tuning, subtree_levels);
   F(hpfmm_tuning, met); F(hpfmm_tuning, mean_leaf); F(hpfmm_tuning, est_rel_err);
   F(hpfmm_tuning, ms_per_eval); F(hpfmm_tuning, nsample);
+  printf("hpfmm_alu_peaks size %zu\n", sizeof(hpfmm_alu_peaks));
+  F(hpfmm_alu_peaks, sms); F(hpfmm_alu_peaks, mufu_ops_per_s);
+  F(hpfmm_alu_peaks, ffma_flops_per_s); F(hpfmm_alu_peaks, dfma_flops_per_s);
+  F(hpfmm_alu_peaks, mufu_mhz); F(hpfmm_alu_peaks, ffma_mhz); F(hpfmm_alu_peaks, dfma_mhz);
+  F(hpfmm_alu_peaks, mufu_per_clk_sm); F(hpfmm_alu_peaks, ffma_flops_per_clk_sm);
+  F(hpfmm_alu_peaks, dfma_flops_per_clk_sm);
   return 0;
 }
 """
@@ -102,7 +108,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         t, f, v = line.split()
         c[(t, f)] = int(v)
     for cname, py in (("hpfmm_options", hp.Options), ("hpfmm_plan_info", hp.PlanInfo),
-                      ("hpfmm_tuning", hp.Tuning)):
+                      ("hpfmm_tuning", hp.Tuning), ("hpfmm_alu_peaks", hp.AluPeaks)):
         assert ctypes.sizeof(py) == c[(cname, "size")], cname
         for f, _ in py._fields_:
             assert getattr(py, f).offset == c[(cname, f)], (cname, f)
@@ -123,4 +129,4 @@ def test_adaptive_option_checks_without_gpu(library):
     assert e.value.status == hp.HPFMM_EUNSUPPORTED
     opt = hp.Options()
     library.hpfmm_default_options(__import__("ctypes").byref(opt))
-    assert opt.adaptive == 0 and list(opt.reserved) == [0, 0]
+    assert opt.adaptive == 0 and opt.async_update == 0 and list(opt.reserved) == [0]

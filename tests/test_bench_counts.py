@@ -61,24 +61,30 @@ def test_vlist_translations_brute_force(H):
 
 def test_roofline_arithmetic():
     """achieved = algorithmic work per launch / per-launch time, frac =
-    achieved / peak; the dominant single-kernel pass is the one reported."""
+    achieved / peak (the measured pipe peak); the dominant single-kernel pass
+    is the one reported, the others under "others"."""
     class A:
         n, p, prec = 1_000_000, 12, "fp32"
-    launches = {"eval": 10, "m2l_free": 10, "m2m": 20}
-    passes = {"eval": 1.5, "m2l_free": 1.2, "m2m": 3.0}  # ms over 10 steps; m2m is not single-kernel
-    peaks = {"sm_max_mhz": 2000.0}
+    launches = {"eval": 10, "m2l_free": 10, "m2m": 20, "tree": 10}
+    passes = {"eval": 1.5, "m2l_free": 1.2, "m2m": 3.0, "tree": 0.5}  # ms over 10 steps
+    alu = {"sms": 152, "mufu_ops_per_s": 5.0e12, "ffma_flops_per_s": 78e12,
+           "mufu_mhz": 2070.0, "ffma_mhz": 2070.0}
     npairs = 100_000_000
-    r = bench.roofline(passes, launches, A, npairs, 8, peaks)
+    r = bench.roofline(passes, launches, A, npairs, 8, alu, 6800.0)
     t = 1.5e-3 / 10
-    assert r["kernel"].startswith(bench.SINGLE_KERNEL["eval"][0])
+    assert r["kernel"] == bench.SINGLE_KERNEL["eval"][0]
     assert r["achieved"] == pytest.approx(2.0 * npairs / t / 1e12)
-    assert r["peak"] == pytest.approx(16 * 152 * 2.0e9 / 1e12)
+    assert r["peak"] == pytest.approx(5.0)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["per_launch_ms"] == pytest.approx(0.15)
-    assert r["traffic"] == bench.NCU_TRAFFIC[(bench.SINGLE_KERNEL["eval"][0], A.n, A.p, 8, A.prec)]
+    assert set(r["others"]) == {"m2l_free", "tree"}  # m2m is not a single-kernel pass
+    tr = r["others"]["tree"]
+    assert tr["bound"] == "hbm" and tr["peak"] == 6800.0
+    per = 16 + 8 + 8 + 20
+    assert tr["achieved"] == pytest.approx((per * A.n + 4 * (4 ** 8 + 1)) / 0.05e-3 / 1e9)
     # M2L dominant: 8 (p+1)^2 flops per translation against the FP32 FMA peak
     passes = {"eval": 1.0, "m2l_free": 1.2}
-    r = bench.roofline(passes, launches, A, npairs, 8, peaks)
+    r = bench.roofline(passes, launches, A, npairs, 8, alu, 6800.0)
     t = 1.2e-3 / 10
     assert r["achieved"] == pytest.approx(8.0 * 13 * 13 * bench.vlist_translations(8) / t / 1e12)
-    assert r["peak"] == pytest.approx(128 * 2 * 152 * 2.0e9 / 1e12)
+    assert r["peak"] == pytest.approx(78.0)
