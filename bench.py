@@ -190,13 +190,15 @@ def vlist_translations(H):
     return tot
 
 
-# kernels that make up a pass with one launch per step (the candidates for the
-# dominant-kernel roofline)
-SINGLE_KERNEL = {"eval": ("k_eval32p<1>", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
-                 "m2l_mirror": ("k_m2l_mirror_all", "k_m2l_mirror_all"),
-                 "p2m": ("k_s2m_thread", "k_p2m"), "near_mirror": ("k_mirror32", None),
-                 "tree": ("k_tree_coop", "k_tree_coop"),
-                 "l2l": ("k_downward<float, true>", "k_downward<double, false>")}
+# the kernels of each pass whose work bench.py can count (the candidates for
+# the dominant-kernel roofline); a pass may take several launches per step (the
+# leaf-level M2L runs apart from the coarser levels, the tree build is six
+# kernels), and its work per launch is then the step's work over its launches
+PASS_KERNELS = {"eval": ("k_near32", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
+                "m2l_mirror": ("k_m2l_mirror_all", "k_m2l_mirror_all"),
+                "p2m": ("k_s2m_thread", "k_p2m"), "near_mirror": ("k_mirror32", None),
+                "tree": ("k_tb_* (tree build: bbox, keys, scan, scatter, sort, big-leaf sort)",) * 2,
+                "l2l": ("k_downward<float, true>", "k_downward<double, false>")}
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
@@ -210,21 +212,22 @@ def _traffic(name, args, H):
 
 
 def roofline_entries(passes_ms, launches, args, npairs, H, alu, hbm_gbs):
-    """Roofline entries of the single-kernel passes: achieved = the kernel's
-    algorithmic work per launch / its per-launch CUDA-event duration in the
-    timed steps, against the peak of the pipe (or memory) that bounds it,
-    measured on this device (hpfmm_measure_alu_peaks; HBM from the driver's
-    copy measurement)."""
+    """Roofline entries of the passes with countable work: achieved = the
+    pass's algorithmic work per step / its CUDA-event device time per step
+    (equal to work per launch / average launch duration), against the peak of
+    the pipe (or memory) that bounds it, measured on this device
+    (hpfmm_measure_alu_peaks; HBM from the driver's copy measurement)."""
     n, P1 = args.n, args.p + 1
     out = {}
-    for dom, names in SINGLE_KERNEL.items():
+    for dom, names in PASS_KERNELS.items():
         if launches.get(dom, 0) <= 0 or passes_ms.get(dom, 0) <= 0:
             continue
         name = names[0 if args.prec != "fp64" else 1]
         if name is None:
             continue
-        t = passes_ms[dom] / 1e3 / launches[dom]  # seconds per launch
-        e = {"kernel": name, "per_launch_ms": t * 1e3}
+        t = passes_ms[dom] / 1e3  # seconds per step
+        e = {"kernel": name, "per_launch_ms": t * 1e3 / launches[dom],
+             "launches_per_step": launches[dom]}
         if dom == "eval" and args.prec != "fp64":
             ops = 2.0 * npairs
             e.update(bound="alu", unit="TOP/s", achieved=ops / t / 1e12,
@@ -261,7 +264,7 @@ def roofline_entries(passes_ms, launches, args, npairs, H, alu, hbm_gbs):
                           "and gradient out)" % per,
                      peak_source="MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)")
         else:
-            e.update(bound="alu", unit="ms", achieved=t * 1e3, peak=None)
+            e.update(bound="alu", unit="ms", achieved=t * 1e3 / launches[dom], peak=None)
         e["frac"] = e["achieved"] / e["peak"] if e.get("peak") else None
         e["traffic"] = _traffic(name, args, H)
         out[dom] = e

@@ -409,8 +409,9 @@ k_ad_m2l(int bfirst, int blast, int nbox, int p, AdGeom g, const cf *__restrict_
   B[e] = B[e] + conj(v);
 }
 
-// Free-space M2L in Hankel form (even p up to 20): moments scaled by 1/k!,
-// T'[r][k] = g_{r+k} of the offset class, outputs scaled by (-1)^{r+1}/r!
+// Free-space M2L in Hankel form (even p up to 20): moments scaled by 16^k/k!,
+// T'[r][k] = g_{r+k} of the offset class (scaled by 16^-(r+k) in the table),
+// outputs scaled by (-1)^{r+1} 16^r/r!
 // (the uniform tree's class vectors, staged in shared memory).  A block of
 // four warps takes 32 parent boxes and warp w their children of type w, so
 // that the lanes of a warp share every source offset and class vector (a
@@ -437,8 +438,11 @@ k_ad_m2l_hk(int pfirst, int plast, int nbox, AdGeom g, const cf *__restrict__ Tp
   if (threadIdx.x < P1) {
     double f = 1.0;
     for (int i = 2; i <= (int)threadIdx.x; ++i) f *= (double)i;
-    fac_in[threadIdx.x] = (float)(1.0 / f);
-    fac_out[threadIdx.x] = (float)(((threadIdx.x & 1) ? 1.0 : -1.0) / f);
+    // the table's entries carry 16^-j (the single-precision range scaling of
+    // m2l_patch.cuh), so the moment and output factors carry 16^k and 16^r
+    const double rr = ldexp(1.0, kHankelLog2R * (int)threadIdx.x);
+    fac_in[threadIdx.x] = (float)(rr / f);
+    fac_out[threadIdx.x] = (float)(((threadIdx.x & 1) ? rr : -rr) / f);
   }
   for (int c = threadIdx.x; c < 49; c += blockDim.x) lgt[c] = (float)logt[c].x;
   __syncthreads();

@@ -137,6 +137,14 @@ static void free_plan(hpfmm_plan *pl) {
     cudaStreamSynchronize(pl->table_stream);
     cudaStreamDestroy(pl->table_stream);
   }
+  if (pl->m2l_stream) {
+    cudaStreamSynchronize(pl->m2l_stream);
+    cudaStreamDestroy(pl->m2l_stream);
+  }
+  if (pl->ev_s2m) cudaEventDestroy(pl->ev_s2m);
+  if (pl->ev_up) cudaEventDestroy(pl->ev_up);
+  if (pl->ev_mirror) cudaEventDestroy(pl->ev_mirror);
+  if (pl->ev_m2lh) cudaEventDestroy(pl->ev_m2lh);
   if (pl->ev_tree) cudaEventDestroy(pl->ev_tree);
   if (pl->ev_geo) cudaEventDestroy(pl->ev_geo);
   if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
@@ -156,7 +164,7 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc,
                   pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_parent, pl->ab_lvl, pl->ab_child,
                   pl->ab_cut, pl->ab_off, pl->ab_idx, pl->ab_lev, pl->ab_btot, pl->ab_lrank,
-                  pl->ab_leaf, pl->near, pl->loclo, pl->dgeom, pl->tree_ctr, pl->ctr};
+                  pl->ab_leaf, pl->near, pl->loclo, pl->dgeom, pl->tree_ctr, pl->ctr, pl->mir_A, pl->mir_B};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -393,6 +401,10 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   if (f32) ALLOC(pl->yabs, sizeof(float) * n);
   if (f32 && !pl->adaptive) ALLOC(pl->loclo, sizeof(float2) * n);
   if (f32 && !pl->adaptive) ALLOC(pl->near, sizeof(float4) * n);
+  if (f32 && !pl->adaptive) {  // mirror M2L results: rows 0 and 1 of levels 1..H
+    ALLOC(pl->mir_A, sizeof(cf) * 4 * (((size_t)1 << pl->H) - 1) * P1);
+    ALLOC(pl->mir_B, sizeof(cf) * 4 * (((size_t)1 << pl->H) - 1) * P1);
+  }
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);
@@ -431,6 +443,12 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->side_stream, cudaStreamNonBlocking, prio_hi);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->table_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess)
+      ce = cudaStreamCreateWithPriority(&pl->m2l_stream, cudaStreamNonBlocking, prio_hi);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_s2m, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_m2lh, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_up, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_mirror, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tree, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_geo, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);

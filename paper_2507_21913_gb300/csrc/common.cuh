@@ -223,6 +223,16 @@ __device__ __forceinline__ double2 leaf_centre_at(double x0, double d, int ix, i
   return make_double2(__fma_rn(ix + 0.5, d, x0), __dmul_rn(iy + 0.5, d));
 }
 
+// The single-precision Hankel form of the free-space M2L (the patch kernels
+// of the uniform tree and the adaptive tree's kernel) scales its factors by
+// powers of R = 2^kHankelLog2R -- the class vector entries g_j by R^-j (in
+// the table), the moment and output factors 1/k! and 1/l! by R^k and R^l --
+// which leaves every product, and so every result, unchanged bit for bit
+// (powers of two scale exactly) but keeps the factors within the single-
+// precision range up to p = 40: (2p - 1)! alone overflows past p = 21 and
+// 1/p! underflows past p = 33.
+constexpr int kHankelLog2R = 4;
+
 // deepest level of an adaptive tree (its dense per-level box index has
 // (4^(L+1) - 1) / 3 entries)
 constexpr int kAdaptiveMaxLevel = 13;
@@ -322,6 +332,15 @@ struct hpfmm_plan {
   bool tables_pending = false;
   // fork / join of the near field on the side stream (single precision)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the leaf level's M2L on its own stream, after the S2M (ev_s2m), joined
+  // before the mirror M2L (ev_m2lh)
+  cudaStream_t m2l_stream = nullptr;
+  cudaEvent_t ev_s2m = nullptr, ev_m2lh = nullptr;
+  // the mirror M2L on the table stream after the upward pass (ev_up), into
+  // mir_A / mir_B (rows 0 and 1 of every level), joined before the downward
+  // pass (ev_mirror); single-precision uniform plans
+  cudaEvent_t ev_up = nullptr, ev_mirror = nullptr;
+  void *mir_A = nullptr, *mir_B = nullptr;
   float4 *near = nullptr;  // near-field sums per point (sorted order)
   double *hgeo = nullptr;  // pinned host copy of geo, written by the tree build
   int *status = nullptr;  // device status word

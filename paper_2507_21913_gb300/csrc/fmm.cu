@@ -395,7 +395,7 @@ k_m2m_level(int l, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restrict__ 
 // result).  Without EVAL the leaf expansions are written to global memory;
 // with EVAL (single-precision split evaluation) they stay in shared memory and
 // the block evaluates them at its points (L2P, Eq. truncatedLE), adds the
-// near-field sums of k_eval32p<1> and writes the outputs.
+// near-field sums of k_near32 and writes the outputs.
 struct DownEval {
   const float2 *loc;
   const float4 *near;
@@ -404,11 +404,19 @@ struct DownEval {
   double *pot, *grad;
 };
 
+// slot of box (ix, iy <= 1) of level l >= 1 in the mirror M2L's separate
+// outputs: the launch's block index, levels in order, rows 0 and 1 of 2^l
+// boxes each
+__host__ __device__ __forceinline__ int64_t mirror_slot(int l, int ix, int iy) {
+  return ((int64_t(2) << l) - 4) + ((int64_t)iy << l) + ix;
+}
+
 template <typename R, bool EVAL>
 __global__ void __launch_bounds__(256)
 k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restrict__ A,
            cpx<R> *__restrict__ B, RhsStride rs, const int *__restrict__ leaf_start,
-           int skip_empty, DownEval ev) {
+           int skip_empty, DownEval ev, const cpx<R> *__restrict__ Amir,
+           const cpx<R> *__restrict__ Bmir) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int P1 = p + 1;
   const int64_t root = blockIdx.x;
@@ -426,11 +434,18 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
   const int nbuf = EVAL ? nl : (1 << (2 * (k > 0 ? k - 1 : 0)));
   cpx<R> *cur = T + 4 * P1 * P1, *nxt = cur + (size_t)2 * nbuf * P1;
   for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tl2l[e];
-  // ancestor chain: levels 1 .. l0 (level 0 has no expansion)
+  // ancestor chain: levels 1 .. l0 (level 0 has no expansion; level 1 has
+  // the mirror M2L's result only)
   const int64_t a1 = root >> (2 * (l0 - 1));
   for (int e = threadIdx.x; e < P1; e += blockDim.x) {
-    cur[e] = A[(size_t)(level_offset(1) + a1) * P1 + e];
-    cur[P1 + e] = B[(size_t)(level_offset(1) + a1) * P1 + e];
+    if (Amir) {
+      const int64_t ms = mirror_slot(1, box_ix((uint64_t)a1), box_iy((uint64_t)a1)) * P1 + e;
+      cur[e] = Amir[ms];
+      cur[P1 + e] = Bmir[ms];
+    } else {
+      cur[e] = A[(size_t)(level_offset(1) + a1) * P1 + e];
+      cur[P1 + e] = B[(size_t)(level_offset(1) + a1) * P1 + e];
+    }
   }
   __syncthreads();
   {
@@ -440,6 +455,8 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
       const int64_t bl = root >> (2 * (l0 - l));
       const int c = (int)(bl & 3);
       const size_t ce = (size_t)(level_offset(l) + bl) * P1;
+      const int iyb = box_iy((uint64_t)bl);
+      const int64_t msb = (Amir && iyb <= 1) ? mirror_slot(l, box_ix((uint64_t)bl), iyb) * P1 : -1;
       // output o (A then B) by a group of 8 threads, each a strided part of
       // the sum over n, combined by shuffles within the group
       for (int o0 = 0; o0 < 2 * P1; o0 += (int)blockDim.x >> 3) {
@@ -458,7 +475,11 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
           acc.x += __shfl_xor_sync(gmask, acc.x, w);
           acc.y += __shfl_xor_sync(gmask, acc.y, w);
         }
-        if (act && part == 0) nxt[o] = acc + (isb ? B[ce + m] : A[ce + m]);
+        if (act && part == 0) {
+          cpx<R> own = isb ? B[ce + m] : A[ce + m];
+          if (msb >= 0) own = own + (isb ? Bmir[msb + m] : Amir[msb + m]);
+          nxt[o] = acc + own;
+        }
       }
       __syncthreads();
       cpx<R> *t = cur; cur = nxt; nxt = t;
@@ -476,6 +497,15 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
       const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
       const size_t ce = (size_t)(level_offset(l) + first + b) * P1 + m;
       cpx<R> sa = A[ce], sb = B[ce];
+      if (Amir) {
+        const uint64_t bx = (uint64_t)(first + b);
+        const int iyb = box_iy(bx);
+        if (iyb <= 1) {
+          const int64_t ms = mirror_slot(l, box_ix(bx), iyb) * P1 + m;
+          sa = sa + Amir[ms];
+          sb = sb + Bmir[ms];
+        }
+      }
       for (int n = m; n < P1; ++n) {
         cfma(sa, Tc[n], pa[n]);
         cfma(sb, conj(Tc[n]), pb[n]);
@@ -650,17 +680,18 @@ k_m2l_free(int l, int p, const DevGeom *__restrict__ dg, const cpx<R> *__restric
 // The patch form of the free-space M2L (m2l_patch.cuh) is instantiated for
 // every order in two translation units; this dispatches on p.
 template <typename R>
-bool launch_m2l_patch(int p, int H, const DevGeom *dg, const cpx<R> *Tpad, const cd *logt,
-                      const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status, cudaStream_t st,
-                      int nr, RhsStride rs, const int *leaf_start, int skip_empty) {
+bool launch_m2l_patch(int p, int H, int lmin, int lmax, const DevGeom *dg, const cpx<R> *Tpad,
+                      const cd *logt, const cpx<R> *M, cpx<R> *A, cpx<R> *B, int *status,
+                      cudaStream_t st, int nr, RhsStride rs, const int *leaf_start,
+                      int skip_empty) {
   if constexpr (sizeof(R) == 8) {
     return false;  // the patch form is the single-precision path only
   } else {
     if (p <= kPatchSplitP)
-      return m2l_patch_launch_lo(p, H, dg, Tpad, logt, M, A, B, status, st, nr, rs, leaf_start,
-                                 skip_empty);
-    return m2l_patch_launch_hi(p, H, dg, Tpad, logt, M, A, B, status, st, nr, rs, leaf_start,
-                               skip_empty);
+      return m2l_patch_launch_lo(p, H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st, nr, rs,
+                                 leaf_start, skip_empty);
+    return m2l_patch_launch_hi(p, H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st, nr, rs,
+                               leaf_start, skip_empty);
   }
 }
 
@@ -889,14 +920,16 @@ bool launch_m2l_tc(int p, int H, const DevGeom *dg, const float *Btab, const cd 
 // All-levels form of the mirror M2L: one block of 4 warps per target box of
 // rows 0 and 1 of every level 1..H; the warps split the (at most 12) sources
 // of the mirror list, lanes run over the output index, and the four partial
-// sums are reduced in shared memory.  Level 1 initialises A and B, deeper
-// levels add to the free-space result.
+// sums are reduced in shared memory.  Without Amir / Bmir, level 1
+// initialises A and B and deeper levels add to the free-space result; with
+// them, the results go there instead (box t of the launch at t (p+1), see
+// mirror_slot), so that this kernel need not wait for the free-space M2L.
 template <typename R>
 __global__ void __launch_bounds__(128)
 k_m2l_mirror_all(int H, int p, const DevGeom *__restrict__ dg, const cpx<R> *__restrict__ Timg,
                  const cd *__restrict__ logimg, const cpx<R> *__restrict__ Treact,
                  const cpx<R> *__restrict__ M, cpx<R> *__restrict__ A, cpx<R> *__restrict__ B,
-                 RhsStride rs) {
+                 RhsStride rs, cpx<R> *__restrict__ Amir, cpx<R> *__restrict__ Bmir) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int P1 = p + 1;
   M += blockIdx.y * rs.m;
@@ -967,6 +1000,11 @@ k_m2l_mirror_all(int H, int p, const DevGeom *__restrict__ dg, const cpx<R> *__r
     }
     L = sc * L;
     const cpx<R> va = L + C, vb = conj(L) + D;
+    if (Amir) {
+      Amir[(size_t)blockIdx.x * P1 + n] = va;
+      Bmir[(size_t)blockIdx.x * P1 + n] = vb;
+      continue;
+    }
     const size_t e = (size_t)m * P1 + n;
     if (l >= 2) {
       A[e] = A[e] + va;
@@ -1102,21 +1140,22 @@ constexpr int kTlP = kTl + 2;      // patch leaves per side
 constexpr int kTlCap = 2560;       // staged points per block
 constexpr int kLsBytes = 80;       // tile leaf starts (kTl^2 + 1 ints), 16-byte padded
 
-// Single-precision leaf evaluation with one target per lane.  A block takes
-// a 4 x 4 tile of leaves -- 16 consecutive Morton leaves, so its targets are
-// one contiguous range of the sorted points -- and stages the 6 x 6 leaves
-// around it in shared memory: the leaf-frame position of each point as a
-// float pair (hi, lo) and its charge.  Warps take 32 consecutive targets of
-// the tile at a time; a lane finds its target's leaf and sums over that
-// leaf's 3 x 3 neighbourhood in the staged patch, skipping itself by index.
-// The target is moved into each neighbour's frame by that leaf's exact
-// offset (the leaf side as hi + lo, the hi part added by an error-free sum),
-// so that a pair difference (x_i - x_j) is exact up to one rounding: without
-// the lo parts the float leaf frames would cost close pairs their relative
-// precision (an absolute error of about 2^-25 d in every difference).  Lanes
-// of one warp may belong to two or three leaves: they run the same loops with
-// their own bounds.  Then L2P with the target's leaf expansions.  Patches
-// larger than the buffer read from global memory.
+// Single-precision free-space near field (the j != i sum of Eq. 1.2 over the
+// 3 x 3 leaf neighbourhood of each target), one target per lane.  A block
+// takes a 4 x 4 tile of leaves -- 16 consecutive Morton leaves, so its
+// targets are one contiguous range of the sorted points -- and stages the
+// 6 x 6 leaves around it in shared memory, row by row: each point's position
+// in the frame of the tile's first leaf as a float pair (hi, lo), converted
+// once from its leaf frame by an exact two-sum with the leaf's offset (a
+// multiple of the leaf side, itself split into hi + lo), and its charge.  A
+// row of a target's neighbourhood is then one contiguous range of the staged
+// points, and a pair difference (x_i - x_j) = (hi_i - hi_j) + (lo_i - lo_j)
+// is exact up to its one rounding: without the lo parts the float frames
+// would cost close pairs their relative precision (an absolute error of
+// about 2^-25 d in every difference).  The target's own point is skipped by
+// index.  Lanes of one warp may belong to two or three leaves: they run the
+// same loops with their own bounds.  Patches larger than the buffer read
+// from global memory, leaf by leaf in leaf frames.
 __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src,
                                           const float *__restrict__ srcq, int lo, int hi,
                                           float sxh, float sxl, float syh, float syl, float &lf,
@@ -1144,32 +1183,35 @@ __device__ __forceinline__ void frame_shift(float hi, float lo, int c, float d, 
   sl = (hi - (sh - b)) + (lo - (float)c * dlo);
 }
 
-// MODE 1: the near field only, its three sums per point (sorted order)
-// written to near[].  MODE 2: L2P plus near[], outputs written (no staging).
-// The split lets the near field run concurrently with the far-field passes.
-constexpr int kEvNear = 1, kEvFar = 2;
-template <int MODE>
+// (h, l) + (oh, ol) as hi + lo: the two-sum of h and oh (exact for any
+// magnitudes), the low parts added
+__device__ __forceinline__ void add_hilo(float h, float l, float oh, float ol, float &sh,
+                                         float &sl) {
+  sh = h + oh;
+  const float bv = sh - h;
+  const float e = (h - (sh - bv)) + (oh - bv);
+  sl = (l + ol) + e;
+}
+
 __global__ void __launch_bounds__(kEvWarps * 32, 4)
-k_eval32p(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
-          const float *__restrict__ qs, const int64_t *__restrict__ perm,
-          const int *__restrict__ leaf_start, int H, const DevGeom *__restrict__ dg, int p,
-          const cf *__restrict__ A, const cf *__restrict__ B, double *__restrict__ pot,
-          double *__restrict__ grad, float4 *__restrict__ near) {
+k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
+         const float *__restrict__ qs, const int *__restrict__ leaf_start, int H,
+         const DevGeom *__restrict__ dg, float4 *__restrict__ near) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int *ls = reinterpret_cast<int *>(smem_raw);         // [kTl^2 + 1] tile leaf starts
   float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap] (hi, lo)
   float *srcq = reinterpret_cast<float *>(src + kTlCap);          // [kTlCap] charges
   int *pst = reinterpret_cast<int *>(srcq + kTlCap);   // [kTlP^2 + 1]
   int *pbeg = pst + kTlP * kTlP + 1;                   // [kTlP^2]
-  const int P1 = p + 1;
-  const float d = dg->d[H], dlo = dg->dlo[H], invd = dg->invd[H];
+  __shared__ float offh[kTlP], offl[kTlP];             // (c - 1) d as hi + lo, c = 0..5
+  const float d = dg->d[H], dlo = dg->dlo[H];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = 1 << H;
   const int tps = nx >= kTl ? nx / kTl : 1;
   const int tx0 = (blockIdx.x % tps) * kTl, ty0 = (blockIdx.x / tps) * kTl;
   const int side = nx < kTl ? nx : kTl, nlt = side * side;
   const uint64_t L0 = box_morton(tx0, ty0);
-  if (MODE != kEvFar && warp == 0) {
+  if (warp == 0) {
     int c0 = 0, c1 = 0;
     for (int h = 0; h < 2; ++h) {
       const int pi = lane + 32 * h;
@@ -1196,23 +1238,32 @@ k_eval32p(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
     if (lane == kTlP * kTlP - 32 - 1) pst[kTlP * kTlP] = tot0 + i1;
   } else if (warp == 1 && lane <= nlt) {
     ls[lane] = leaf_start[L0 + lane];
+  } else if (warp == 2 && lane < kTlP) {
+    // the offsets of the patch columns / rows from the tile's first leaf
+    const double o = (double)(lane - 1) * ((double)d + (double)dlo);
+    const float oh = (float)o;
+    offh[lane] = oh;
+    offl[lane] = (float)(o - (double)oh);
   }
   __syncthreads();
-  const bool staged = MODE != kEvFar && pst[kTlP * kTlP] <= kTlCap;
+  const bool staged = pst[kTlP * kTlP] <= kTlCap;
   if (staged) {
     for (int pi = warp; pi < kTlP * kTlP; pi += kEvWarps) {
       const int b0 = pbeg[pi], cnt = pst[pi + 1] - pst[pi], o = pst[pi];
+      const float ohx = offh[pi % kTlP], olx = offl[pi % kTlP];
+      const float ohy = offh[pi / kTlP], oly = offl[pi / kTlP];
       for (int j = lane; j < cnt; j += 32) {
         const float2 v = loc[b0 + j], w = loclo[b0 + j];
-        src[o + j] = make_float4(v.x, v.y, w.x, w.y);
+        float hx, lx, hy, ly;
+        add_hilo(v.x, w.x, ohx, olx, hx, lx);
+        add_hilo(v.y, w.y, ohy, oly, hy, ly);
+        src[o + j] = make_float4(hx, hy, lx, ly);
         srcq[o + j] = qs[b0 + j];
       }
     }
   }
   __syncthreads();
   const int t0 = ls[0], t1 = ls[nlt];
-  const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
-  const float i2pi = (float)(1.0 / HP_TWO_PI);
   for (int tb = t0 + 32 * warp; tb < t1; tb += 32 * kEvWarps) {
     const int i = tb + lane;
     const bool act = i < t1;
@@ -1224,37 +1275,24 @@ k_eval32p(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
     const int ix = box_ix(leaf), iy = box_iy(leaf);
     const int px = ix - tx0 + 1, py = iy - ty0 + 1;
     float lf = 0.f, gx = 0.f, gy = 0.f;
-    float2 me = make_float2(0.f, 0.f);
     if (staged) {
       const int kself = pst[py * kTlP + px] + (i - ls[li]);
-      float2 ml = make_float2(0.f, 0.f);
-      if (act) {
-        const float4 m4 = src[kself];
-        me = make_float2(m4.x, m4.y);
-        ml = make_float2(m4.z, m4.w);
-      }
+      float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (act) me = src[kself];
 #pragma unroll 1
       for (int r = -1; r <= 1; ++r) {
-        float syh, syl;
-        frame_shift(me.y, ml.y, r, d, dlo, syh, syl);
-#pragma unroll 1
-        for (int c = -1; c <= 1; ++c) {
-          const int pi = (py + r) * kTlP + (px + c);
-          int lo = pst[pi], hi = pst[pi + 1];
-          if (!act) hi = lo;
-          float sxh, sxl;
-          frame_shift(me.x, ml.x, c, d, dlo, sxh, sxl);
-          if (r == 0 && c == 0) {
-            pair_loop(src, srcq, lo, act ? kself : lo, sxh, sxl, syh, syl, lf, gx, gy);
-            pair_loop(src, srcq, act ? kself + 1 : hi, hi, sxh, sxl, syh, syl, lf, gx, gy);
-          } else {
-            pair_loop(src, srcq, lo, hi, sxh, sxl, syh, syl, lf, gx, gy);
-          }
+        const int pi = (py + r) * kTlP + px;
+        const int lo = pst[pi - 1];
+        const int hi = act ? pst[pi + 2] : lo;
+        if (r == 0) {
+          pair_loop(src, srcq, lo, act ? kself : lo, me.x, me.z, me.y, me.w, lf, gx, gy);
+          pair_loop(src, srcq, act ? kself + 1 : hi, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
+        } else {
+          pair_loop(src, srcq, lo, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
         }
       }
-    } else if (MODE != kEvFar && act) {
-      me = loc[i];
-      const float2 ml = loclo[i];
+    } else if (act) {
+      const float2 me = loc[i], ml = loclo[i];
       for (int r = -1; r <= 1; ++r) {
         float syh, syl;
         frame_shift(me.y, ml.y, r, d, dlo, syh, syl);
@@ -1279,47 +1317,7 @@ k_eval32p(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
         }
       }
     }
-    if (!act) continue;
-    if (MODE == kEvNear) {
-      near[i] = make_float4(lf, gx, gy, 0.f);
-      continue;
-    }
-    if (MODE == kEvFar) {
-      const float4 nv = near[i];
-      me = loc[i];
-      lf = nv.x;
-      gx = nv.y;
-      gy = nv.z;
-    }
-    const cf *Al = A + (size_t)(level_offset(H) + leaf) * P1;
-    const cf *Bl = B + (size_t)(level_offset(H) + leaf) * P1;
-    const cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
-    cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
-    for (int n = p - 1; n >= 0; --n) {
-      da = da * w + va;
-      va = va * w + Al[n];
-      db = db * wb + vb;
-      vb = vb * wb + Bl[n];
-    }
-    const float ur_ = va.x + vb.x - lf * c4;
-    const float ui_ = va.y + vb.y;
-    const cf gxo = invd * (da + db) + mk(-gx * i2pi, 0.f);
-    const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-gy * i2pi, 0.f);
-    const int64_t o = perm[i];
-    double2 pv = make_double2(f2d(ur_), f2d(ui_));
-    double4_16a gv;
-    gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
-    if (MODE == kEvFar && iy == 0) {  // bottom row: the image/reaction sums are already there
-      const double2 pm = reinterpret_cast<const double2 *>(pot)[o];
-      pv.x += pm.x;
-      pv.y += pm.y;
-      if (grad) {
-        const double4_16a gm = reinterpret_cast<const double4_16a *>(grad)[o];
-        gv.x += gm.x; gv.y += gm.y; gv.z += gm.z; gv.w += gm.w;
-      }
-    }
-    reinterpret_cast<double2 *>(pot)[o] = pv;
-    if (grad) reinterpret_cast<double4_16a *>(grad)[o] = gv;
+    if (act) near[i] = make_float4(lf, gx, gy, 0.f);
   }
 }
 constexpr size_t kTpSmem = kLsBytes + (sizeof(float4) + sizeof(float)) * kTlCap +
@@ -1932,9 +1930,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     HP_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0));
     fs = pl->side_stream;
     pass_begin(pl, st, PASS_EVAL);
-    k_eval32p<kEvNear><<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
-        pl->loc32, pl->loclo, (const float *)qs, pl->perm, pl->leaf_start, H, dg, p,
-        (const cf *)A, (const cf *)B, pot, grad, pl->near);
+    k_near32<<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
+        pl->loc32, pl->loclo, (const float *)qs, pl->leaf_start, H, dg, pl->near);
     pass_end(pl, st, PASS_EVAL, 1);
     // the bottom-row image/reaction sums need only the sources too: written
     // now, added by the L2P kernel
@@ -1972,6 +1969,22 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
           lp, (const float *)qs, pl->leaf_start, H, dg, p, (cf *)M, rs);
   }
   pass_end(pl, fs, PASS_P2M, 1);
+  // split single precision: the M2L of the leaf level needs only the leaf
+  // moments, so it runs on its own stream concurrently with the upward pass
+  // and the coarser levels' M2L (it holds about three quarters of the
+  // translations)
+  const bool leaf_m2l_apart = split && H >= 3 && pl->m2l_stream && pl->ev_s2m && pl->ev_m2lh;
+  bool leaf_m2l_done = false;
+  if (leaf_m2l_apart) {
+    HP_CUDA(cudaEventRecord(pl->ev_s2m, fs));
+    HP_CUDA(cudaStreamWaitEvent(pl->m2l_stream, pl->ev_s2m, 0));
+    pass_begin(pl, pl->m2l_stream, PASS_M2L_FREE);
+    leaf_m2l_done = launch_m2l_patch<R>(p, H, H, H, dg, (const cpx<R> *)pl->t_m2l_pad, logs, M,
+                                        A, B, pl->status, pl->m2l_stream, 1, rs, pl->leaf_start,
+                                        1);
+    pass_end(pl, pl->m2l_stream, PASS_M2L_FREE, leaf_m2l_done ? 1 : 0);
+    HP_CUDA(cudaEventRecord(pl->ev_m2lh, pl->m2l_stream));
+  }
   pass_begin(pl, fs, PASS_M2M);
   // the subtree blocks; when every level above them is small, the last of
   // them also runs those (levels l0 - 1 .. 1), otherwise the levels of 1024
@@ -1995,6 +2008,23 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     }
   }
   pass_end(pl, fs, PASS_M2M, nm2m);
+  // split single precision: the mirror M2L needs only the moments and the
+  // reaction tables; it runs on the table stream (after the tables, in stream
+  // order) concurrently with the free-space M2L, into its own small arrays,
+  // which the downward pass adds
+  const bool mirror_apart = split && pl->mir_A && pl->ev_up && pl->ev_mirror;
+  if (mirror_apart) {
+    HP_CUDA(cudaEventRecord(pl->ev_up, fs));
+    HP_CUDA(cudaStreamWaitEvent(pl->table_stream, pl->ev_up, 0));
+    pass_begin(pl, pl->table_stream, PASS_M2L_MIRROR);
+    unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
+    size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
+    k_m2l_mirror_all<R><<<dim3(nb, 1), 128, sm, pl->table_stream>>>(
+        H, p, dg, Timg, logs + 49, Treact, M, A, B, rs, (cpx<R> *)pl->mir_A, (cpx<R> *)pl->mir_B);
+    pass_end(pl, pl->table_stream, PASS_M2L_MIRROR, 1);
+    HP_CUDA(cudaEventRecord(pl->ev_mirror, pl->table_stream));
+    pl->tables_pending = false;  // the caller's stream joins ev_mirror below
+  }
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
@@ -2005,9 +2035,17 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
       tc_m2l = patched = launch_m2l_tc(p, H, dg, (const float *)pl->t_m2l_tc, logs, (const cf *)M, (cf *)A,
                               (cf *)B, pl->status, fs, nr, rs);
     if (!patched)
-      patched = launch_m2l_patch<R>(p, H, dg, (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B,
-                                    pl->status, fs, nr, rs, pl->leaf_start, tw ? 0 : 1);
+      patched = launch_m2l_patch<R>(p, H, 2, leaf_m2l_done ? H - 1 : H, dg,
+                                    (const cpx<R> *)pl->t_m2l_pad, logs, M, A, B, pl->status, fs,
+                                    nr, rs, pl->leaf_start, tw ? 0 : 1);
     pass_end(pl, fs, PASS_M2L_FREE, patched ? (tc_m2l ? H - 1 : 1) : 0);
+  }
+  // the leaf level's M2L joins the chain here (the mirror M2L below adds to
+  // its result, when it runs in place)
+  if (leaf_m2l_apart) HP_CUDA(cudaStreamWaitEvent(fs, pl->ev_m2lh, 0));
+  if (leaf_m2l_apart && !leaf_m2l_done) {
+    set_last_error("leaf-level M2L: no patch kernel for p = %d", p);
+    return HPFMM_EUNSUPPORTED;
   }
   if (mw && !patched) {
     set_last_error("multi-RHS passes need the patch M2L kernel (2 <= p <= %d)", HPFMM_MAX_P);
@@ -2021,17 +2059,17 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
       pass_end(pl, fs, PASS_M2L_FREE, 1);
     }
   }
-  // the mirror M2L of all levels, after the free-space M2L it adds to; it
-  // reads the reaction tables of the last rebuild
-  HP_TRY(plan_join_tables(pl, fs));
-  pass_begin(pl, fs, PASS_M2L_MIRROR);
-  {
+  // otherwise the mirror M2L of all levels, after the free-space M2L it adds
+  // to; it reads the reaction tables of the last rebuild
+  if (!mirror_apart) {
+    HP_TRY(plan_join_tables(pl, fs));
+    pass_begin(pl, fs, PASS_M2L_MIRROR);
     unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
     size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
     k_m2l_mirror_all<R><<<dim3(nb, nr), 128, sm, fs>>>(H, p, dg, Timg, logs + 49, Treact, M, A,
-                                                         B, rs);
+                                                         B, rs, nullptr, nullptr);
+    pass_end(pl, fs, PASS_M2L_MIRROR, 1);
   }
-  pass_end(pl, fs, PASS_M2L_MIRROR, 1);
   // downward pass: L2L from level 1 to the leaves, each block of subtrees
   // forming its root's expansion from its ancestors.  Split single precision:
   // after the near field has joined, the same kernel evaluates the leaf
@@ -2041,13 +2079,16 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (split) {
     HP_CUDA(cudaEventRecord(pl->ev_join, fs));
     HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
+    if (mirror_apart) HP_CUDA(cudaStreamWaitEvent(st, pl->ev_mirror, 0));
     int kd = H - 1 < 3 ? H - 1 : 3;  // subtrees of 64 leaves: 4^(H-3) blocks
     while (kd > 0 && downward_smem<R>(p, kd, true) > kFusedSmem) --kd;
     pass_begin(pl, st, PASS_L2L);
     const DownEval ev{pl->loc32, pl->near, pl->perm, dg, pot, grad};
     k_downward<R, true><<<dim3((unsigned)(int64_t(1) << (2 * (H - kd))), 1), 256,
-                          downward_smem<R>(p, kd, true), st>>>(H, kd, p, Tl2l, A, B, rs,
-                                                               pl->leaf_start, 1, ev);
+                          downward_smem<R>(p, kd, true), st>>>(
+        H, kd, p, Tl2l, A, B, rs, pl->leaf_start, 1, ev,
+        mirror_apart ? (const cpx<R> *)pl->mir_A : nullptr,
+        mirror_apart ? (const cpx<R> *)pl->mir_B : nullptr);
     pass_end(pl, st, PASS_L2L, 1);
     HP_LAUNCH_CHECK();
     return HPFMM_OK;
@@ -2057,7 +2098,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     k_downward<R, false><<<dim3((unsigned)(int64_t(1) << (2 * l0)), nr), 256,
                            downward_smem<R>(p, ksub, false), fs>>>(H, ksub, p, Tl2l, A, B, rs,
                                                                    pl->leaf_start, tw ? 0 : 1,
-                                                                   noev);
+                                                                   noev, nullptr, nullptr);
   pass_end(pl, fs, PASS_L2L, ksub > 0 ? 1 : 0);
   pass_begin(pl, st, PASS_EVAL);
   // evaluation at the leaves + near field
@@ -2120,7 +2161,7 @@ hpfmm_status fmm_set_smem_limits(int p) {
   HP_CUDA(cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   HP_CUDA(cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
   HP_CUDA(cudaFuncSetAttribute(k_m2l_free<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
-  HP_CUDA(cudaFuncSetAttribute(k_eval32p<kEvNear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HP_CUDA(cudaFuncSetAttribute(k_near32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTpSmem));
   HP_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kFusedSmem));

@@ -21,34 +21,37 @@ struct RhsStride {
 // to HPFMM_MAX_P in m2l_patch_hi.cu; both return false when the order has no
 // instance or its shared memory does not fit
 constexpr int kPatchSplitP = 20;
-bool m2l_patch_launch_lo(int p, int H, const DevGeom *dg, const cf *Tpad, const cd *logt,
-                         const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
-                         RhsStride rs, const int *leaf_start, int skip_empty);
-bool m2l_patch_launch_hi(int p, int H, const DevGeom *dg, const cf *Tpad, const cd *logt,
-                         const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
-                         RhsStride rs, const int *leaf_start, int skip_empty);
+// (levels lmin .. lmax of a tree with leaf level H in one launch)
+bool m2l_patch_launch_lo(int p, int H, int lmin, int lmax, const DevGeom *dg, const cf *Tpad,
+                         const cd *logt, const cf *M, cf *A, cf *B, int *status, cudaStream_t st,
+                         int nr, RhsStride rs, const int *leaf_start, int skip_empty);
+bool m2l_patch_launch_hi(int p, int H, int lmin, int lmax, const DevGeom *dg, const cf *Tpad,
+                         const cd *logt, const cf *M, cf *A, cf *B, int *status, cudaStream_t st,
+                         int nr, RhsStride rs, const int *leaf_start, int skip_empty);
 
 namespace {
 
 // A block owns a patch of kPatch x kPatchRows parent boxes of one level;
-// their four children of each type are its 128 targets, one per thread
-// (warp w: child type w).  It stages the (2 kPatch + 4) x (2 kPatchRows + 4)
+// their four children of each type are its 128 targets, one per thread (warp
+// w: child type w).  The block stages the (2 kPatch + 4) x (2 kPatchRows + 4)
 // source boxes' multipoles and the 40 translation vectors once; then each
-// thread applies the 27 V-list offsets of its child type to its target: the
-// vector entries are warp-uniform (broadcast) reads, the source moments
-// per-lane reads.  All levels 2..H are processed by one launch.
-constexpr int kPatch = 8;                  // parents per block in x
-constexpr int kPatchRows = 4;              // parents per block in y
+// thread applies the 27 V-list offsets of its child type to its target.
+//
+// A class translation in Hankel form is L'_r += sum_k g_{r+k} M'_k.  Up to
+// p = kDiagMaxP1 - 1 a thread holds its source's moments and its outputs in
+// registers and walks the anti-diagonals j = r + k: each g_j is read once
+// (a warp-uniform broadcast, two per 16-byte load) and applied to every
+// (r, k) with r + k = j -- 2p + 1 vector reads per class instead of one per
+// (r, k pair), the loop fully unrolled at compile time.  Above that order the
+// unrolled body would outgrow the instruction cache, and a thread walks the
+// k pairs instead, reading (g_{r+k}, g_{r+k+1}) for every r.
+// All levels lmin..lmax are processed by one launch.
+constexpr int kPatch = 8;      // parents per block in x
+constexpr int kPatchRows = 4;  // parents per block in y
+constexpr int kPatchThreads = 128;
+constexpr int kDiagMaxP1 = 21;
 constexpr int kPatchSrc = 2 * kPatch + 4;  // source boxes per block in x
 constexpr int kSrcRows = 2 * kPatchRows + 4;  // source boxes per block in y
-// The Hankel factors are scaled by powers of R = 2^kHankelLog2R -- the
-// vector entries g_j by R^-j, the moment and output factors 1/k! and 1/l! by
-// R^k and R^l -- which leaves every product, and so every result, unchanged
-// bit for bit (powers of two scale exactly) but keeps the factors within the
-// single-precision range up to p = 40: (2p - 1)! alone overflows past p = 21
-// and 1/p! underflows past p = 33.  The table builder applies the same R.
-constexpr int kHankelLog2R = 4;
-
 // 7 x 7 offset class (dy + 3) * 7 + (dx + 3) -> its index among the 40 far
 // classes, -1 for the near 3 x 3
 __constant__ signed char c_slot[49] = {
@@ -56,8 +59,9 @@ __constant__ signed char c_slot[49] = {
     -1, 20, 21, 22, 23, -1, -1, -1, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39};
 
 template <typename R, int P1>
-__global__ void __launch_bounds__(128)
-k_m2l_free_patch(int H, const DevGeom *__restrict__ dg, const cpx<R> *__restrict__ Tpad,
+__global__ void __launch_bounds__(kPatchThreads)
+k_m2l_free_patch(int H, int lmin, int lmax, const DevGeom *__restrict__ dg,
+                 const cpx<R> *__restrict__ Tpad,
                  const cd *__restrict__ logt, const cpx<R> *__restrict__ M,
                  cpx<R> *__restrict__ A, cpx<R> *__restrict__ B, int *__restrict__ status,
                  RhsStride rs, const int *__restrict__ leaf_start, int skip_empty) {
@@ -78,17 +82,19 @@ k_m2l_free_patch(int H, const DevGeom *__restrict__ dg, const cpx<R> *__restrict
   constexpr int PS = ((PP / 2) & 1) ? PP : PP + 2;
   constexpr int GP = 2 * P1;
   constexpr int HALF = kPatchSrc / 2;
+  constexpr bool kDiag = P1 <= kDiagMaxP1;
+  constexpr int NCOPY = kDiag ? 1 : 2;  // the diagonal form reads copy 0 only
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ R fac_in[P1], fac_out[P1];  // 16^k / k!, (-1)^{l+1} 16^l / l!
   __shared__ unsigned char sempty[kPatchSrc * kSrcRows];  // source box holds no point
-  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][2][GP]
-  cpx<R> *Mp = Ts + 40 * 2 * GP;                           // [12][20][PS]
+  cpx<R> *Ts = reinterpret_cast<cpx<R> *>(smem_raw);      // [40][NCOPY][GP]
+  cpx<R> *Mp = Ts + 40 * NCOPY * GP;                       // [12][20][PS]
   R *lg = reinterpret_cast<R *>(Mp + kPatchSrc * kSrcRows * PS);  // [40] ln|t d|
   // level and patch of this block: kPatch x kPatchRows parents, whose four
   // children of each type are the block's targets (one per thread)
-  int b = blockIdx.x, l = 2;
-  for (; l <= H; ++l) {
+  int b = blockIdx.x, l = lmin;
+  for (; l <= lmax; ++l) {
     const int nps = 1 << (l - 1);
     const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
     if (b < npx * npy) break;
@@ -99,12 +105,18 @@ k_m2l_free_patch(int H, const DevGeom *__restrict__ dg, const cpx<R> *__restrict
   const int nparent_side = 1 << (l - 1), nside = 1 << l;
   const int64_t off = level_offset(l);
   const R logd = (R)dg->logd[l];
-  // the 40 Hankel vectors: one bulk copy (TMA) from the table
-  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * 2 * GP);
+  // the 40 Hankel vectors by bulk copies (TMA) from the table ([40][2][GP]):
+  // all of it, or copy 0 of each class (16 p + 16 bytes, 16-byte aligned)
+  const unsigned tbytes = (unsigned)(sizeof(cpx<R>) * 40 * NCOPY * GP);
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_expect_tx(&bar, tbytes);
-    bulk_g2s(Ts, Tpad, tbytes, &bar);
+    if (kDiag) {
+      for (int c = 0; c < 40; ++c)
+        bulk_g2s(Ts + c * GP, Tpad + (size_t)c * 2 * GP, (unsigned)(sizeof(cpx<R>) * GP), &bar);
+    } else {
+      bulk_g2s(Ts, Tpad, tbytes, &bar);
+    }
   }
   for (int c = threadIdx.x; c < 49; c += blockDim.x)
     if (c_slot[c] >= 0) lg[c_slot[c]] = (R)logt[c].x + logd;
@@ -175,26 +187,43 @@ k_m2l_free_patch(int H, const DevGeom *__restrict__ dg, const cpx<R> *__restrict
     for (int dx = -2 - a; dx <= 3 - a; ++dx) {
       if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
       const int slot = c_slot[(dy + 3) * 7 + (dx + 3)];
-      const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
       const int colA = txA + dx - sx0;
       const int cpA = (colA & 1) * HALF + (colA >> 1);
       const int sbA = (tyA + dy - sy0) * kPatchSrc + cpA;
       if (skip_empty && __all_sync(0xffffffffu, sempty[sbA])) continue;
       const cpx<R> *mA = Mp + sbA * PS;
-#pragma unroll 1
-      for (int k = 0; k < PP; k += 2) {
-        const cpx<R> ma0 = mA[k], ma1 = mA[k + 1];
+      if constexpr (kDiag) {
+        cpx<R> m[P1];
 #pragma unroll
-        for (int r = 0; r < P1; ++r) {
-          // (g_{r+k}, g_{r+k+1}): an aligned pair of copy 0 (r even) or copy 1 (r odd)
-          const cpx<R> *gp = (r & 1) ? G1 + (r + k - 1) : G0 + (r + k);
-          const cpx<R> t0 = gp[0], t1 = gp[1];
-          cfma(accA[r], t0, ma0);
-          cfma(accA[r], t1, ma1);
+        for (int k = 0; k < P1; ++k) m[k] = mA[k];
+        const cpx<R> *G = Ts + slot * GP;
+#pragma unroll
+        for (int j = 0; j < 2 * P1 - 1; j += 2) {
+          const cpx<R> g0 = G[j], g1 = G[j + 1];  // one 16-byte broadcast read
+#pragma unroll
+          for (int r = 0; r < P1; ++r) {
+            if (j - r >= 0 && j - r < P1) cfma(accA[r], g0, m[j - r]);
+            if (j + 1 - r >= 0 && j + 1 - r < P1) cfma(accA[r], g1, m[j + 1 - r]);
+          }
         }
+        // M_0 ln|t d| on Re L_0, in the scaled outputs (L_0 = -L'_0; M'_0 = M_0)
+        accA[0].x -= m[0].x * lg[slot];
+      } else {
+        const cpx<R> *G0 = Ts + slot * 2 * GP, *G1 = G0 + GP;
+#pragma unroll 1
+        for (int k = 0; k < PP; k += 2) {
+          const cpx<R> ma0 = mA[k], ma1 = mA[k + 1];
+#pragma unroll
+          for (int r = 0; r < P1; ++r) {
+            // (g_{r+k}, g_{r+k+1}): an aligned pair of copy 0 (r even) or copy 1 (r odd)
+            const cpx<R> *gp = (r & 1) ? G1 + (r + k - 1) : G0 + (r + k);
+            const cpx<R> t0 = gp[0], t1 = gp[1];
+            cfma(accA[r], t0, ma0);
+            cfma(accA[r], t1, ma1);
+          }
+        }
+        accA[0].x -= mA[0].x * lg[slot];
       }
-      // M_0 ln|t d| on Re L_0, in the scaled outputs (L_0 = -L'_0; M'_0 = M_0)
-      accA[0].x -= mA[0].x * lg[slot];
     }
   }
   const R s = (R)(-0.5 / HP_TWO_PI);
@@ -213,12 +242,13 @@ template <typename R, int P1>
 size_t patch_smem() {
   constexpr int PP = (P1 + 1) & ~1;
   constexpr int PS = ((PP / 2) & 1) ? PP : PP + 2;
-  return sizeof(cpx<R>) * (40 * 2 * 2 * P1 + kPatchSrc * kSrcRows * PS) + sizeof(R) * 40;
+  constexpr int NCOPY = P1 <= kDiagMaxP1 ? 1 : 2;
+  return sizeof(cpx<R>) * (40 * NCOPY * 2 * P1 + kPatchSrc * kSrcRows * PS) + sizeof(R) * 40;
 }
 
-int patch_blocks(int H) {
+int patch_blocks(int lmin, int lmax) {
   int nb = 0;
-  for (int l = 2; l <= H; ++l) {
+  for (int l = lmin; l <= lmax; ++l) {
     const int nps = 1 << (l - 1);
     const int npx = nps / kPatch < 1 ? 1 : nps / kPatch, npy = nps / kPatchRows < 1 ? 1 : nps / kPatchRows;
     nb += npx * npy;
@@ -229,9 +259,9 @@ int patch_blocks(int H) {
 // one order: sets the kernel's shared-memory limit once per device and
 // launches; false when it does not fit
 template <int P1>
-bool patch_launch_order(int H, const DevGeom *dg, const cf *Tpad, const cd *logt, const cf *M,
-                        cf *A, cf *B, int *status, cudaStream_t st, int nr, RhsStride rs,
-                        const int *leaf_start, int skip_empty) {
+bool patch_launch_order(int H, int lmin, int lmax, const DevGeom *dg, const cf *Tpad,
+                        const cd *logt, const cf *M, cf *A, cf *B, int *status, cudaStream_t st,
+                        int nr, RhsStride rs, const int *leaf_start, int skip_empty) {
   static std::mutex mu;
   static signed char attr[64] = {};  // per device: 0 unknown, 1 set, -1 failed
   int dev = 0;
@@ -249,8 +279,10 @@ bool patch_launch_order(int H, const DevGeom *dg, const cf *Tpad, const cd *logt
     }
     if (attr[dev] < 0) return false;
   }
-  k_m2l_free_patch<float, P1><<<dim3(patch_blocks(H), nr), 128, sm, st>>>(
-      H, dg, Tpad, logt, M, A, B, status, rs, leaf_start, skip_empty);
+  if (lmin < 2) lmin = 2;
+  if (lmax < lmin) return true;  // no level to translate
+  k_m2l_free_patch<float, P1><<<dim3(patch_blocks(lmin, lmax), nr), kPatchThreads, sm, st>>>(
+      H, lmin, lmax, dg, Tpad, logt, M, A, B, status, rs, leaf_start, skip_empty);
   return true;
 }
 

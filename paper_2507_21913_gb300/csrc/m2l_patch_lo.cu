@@ -4,49 +4,49 @@
 
 #include "m2l_patch.cuh"
 
-bool m2l_patch_launch_lo(int p, int H, const DevGeom *dg, const cf *Tpad, const cd *logt,
-                         const cf *M, cf *A, cf *B, int *status, cudaStream_t st, int nr,
-                         RhsStride rs, const int *leaf_start, int skip_empty) {
+bool m2l_patch_launch_lo(int p, int H, int lmin, int lmax, const DevGeom *dg, const cf *Tpad,
+                         const cd *logt, const cf *M, cf *A, cf *B, int *status, cudaStream_t st,
+                         int nr, RhsStride rs, const int *leaf_start, int skip_empty) {
   if (!Tpad) return false;
   switch (p) {
-    case 2: return patch_launch_order<3>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 3: return patch_launch_order<4>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 4: return patch_launch_order<5>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 5: return patch_launch_order<6>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 6: return patch_launch_order<7>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 7: return patch_launch_order<8>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 8: return patch_launch_order<9>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 9: return patch_launch_order<10>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 10: return patch_launch_order<11>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 11: return patch_launch_order<12>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 12: return patch_launch_order<13>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 13: return patch_launch_order<14>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 14: return patch_launch_order<15>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 15: return patch_launch_order<16>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 16: return patch_launch_order<17>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 17: return patch_launch_order<18>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 18: return patch_launch_order<19>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 19: return patch_launch_order<20>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
-    case 20: return patch_launch_order<21>(H, dg, Tpad, logt, M, A, B, status, st, nr, rs,
-                                           leaf_start, skip_empty);
+    case 2: return patch_launch_order<3>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 3: return patch_launch_order<4>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 4: return patch_launch_order<5>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 5: return patch_launch_order<6>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 6: return patch_launch_order<7>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 7: return patch_launch_order<8>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 8: return patch_launch_order<9>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 9: return patch_launch_order<10>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 10: return patch_launch_order<11>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 11: return patch_launch_order<12>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 12: return patch_launch_order<13>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 13: return patch_launch_order<14>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 14: return patch_launch_order<15>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 15: return patch_launch_order<16>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 16: return patch_launch_order<17>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 17: return patch_launch_order<18>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 18: return patch_launch_order<19>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 19: return patch_launch_order<20>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
+    case 20: return patch_launch_order<21>(H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st,
+                                           nr, rs, leaf_start, skip_empty);
     default: return false;
   }
 }

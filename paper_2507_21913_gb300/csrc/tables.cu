@@ -195,9 +195,9 @@ __global__ void k_m2l_pad(int p, cf *out) {
         for (int i = 1; i <= j; ++i) g = g * ti;  // t^{-j}
         double f = 1.0;
         for (int i = 2; i < j; ++i) f *= (double)i;  // (j-1)!
-        // (j-1)! t^-j R^-j with R = 16: the scaling of the single-precision
-        // patch M2L, which keeps the factors in range up to p = 40
-        g = ldexp(f, -4 * j) * g;
+        // (j-1)! t^-j R^-j with R = 2^kHankelLog2R: the range scaling of the
+        // single-precision Hankel M2L kernels
+        g = ldexp(f, -kHankelLog2R * j) * g;
       }
       out[(size_t)slot * 2 * GP + e] = to<float>(g);
     }

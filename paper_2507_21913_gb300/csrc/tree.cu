@@ -465,9 +465,10 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
 // ---------------------------------------------------------------------------
 // The tree build: six kernels at full occupancy, one thread per point or
 // bucket, with nothing waiting for the host.  Buckets are the boxes of a
-// level Hb >= H chosen so that they hold about one point each, so that
+// level Hb >= H chosen so that they hold about four points each, so that
 // sorting a bucket is a few comparisons in one thread.
-//   k_tb_bbox     bounding-square partials per block; the last block to finish
+//   k_tb_bbox     bounding-square partials per block (4 points a thread, warp
+//                 shuffle reductions); the last block to finish
 //                 reduces them, publishes the root square and the level
 //                 geometry (and, for asynchronous rebuilds, the validity flags
 //                 in the status word); the bucket counters are cleared
@@ -475,15 +476,25 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
 //                 point's slot in its bucket)
 //   k_tb_scan     exclusive scan of the counts within chunks of kScanChunk
 //                 buckets, chunk totals and maxima
-//   k_tb_scatter  chunk offsets (each block scans the chunk totals); bucket and
-//                 leaf starts; leaf centres; points scattered into buckets
-//   k_tb_sort     each bucket of up to kTinyBucket points sorted by (key, index)
-//                 in one thread (rank sort), with the gather into tree order;
-//                 larger buckets listed
+//   k_tb_scatter  one thread per point, bucket and leaf: chunk offsets (each
+//                 block scans the chunk totals); the point scattered into its
+//                 bucket with its coordinates; bucket and leaf starts; leaf centres
+//   k_tb_sort     one thread per point: its rank by (key, index) within its
+//                 bucket of up to kTinyBucket points, then its outputs in tree
+//                 order; larger buckets listed
 //   k_tb_big      the listed buckets: a warp each up to 128 points, else a block
 constexpr int kTinyBucket = 16;
 constexpr int kScanChunk = 4096;  // buckets per block of the scan (1024 threads x 4)
-constexpr int kBboxThreads = 512;
+constexpr int kBboxThreads = 256;
+constexpr int kBboxPer = 4;  // points per thread of k_tb_bbox
+
+// a point in its bucket: one 32-byte record (a single full-sector store by
+// the scatter, contiguous reads by the sort)
+struct alignas(32) BRec {
+  uint64_t key;
+  double x, y;
+  int v, pad;
+};
 
 struct TreeBuild {
   const double *x, *y;
@@ -502,8 +513,8 @@ struct TreeBuild {
   Geom *part;           // [bbox grid]
   unsigned *ticket;     // last-block counter of k_tb_bbox
   uint64_t *kb;         // [n] keys in input order
-  uint64_t *kt;         // [n] keys bucketed (sorted within a bucket by k_tb_sort)
-  int *slot, *vt;       // [n]: slot in the bucket; caller index, bucketed
+  BRec *rec;            // [n] the points bucketed: key, coordinates, caller index
+  int *slot;            // [n] slot in the bucket
   int *bcount;          // [nbucket + 1]: counts, then chunk prefixes; [nbucket]: big buckets
   int *bstart;          // [nbucket + 1] bucket starts
   double2 *centre;      // [nleaf] leaf centres
@@ -545,9 +556,10 @@ __device__ __forceinline__ float2 split_to_floats(double v) {
 // v rounded to single precision by the same integer operations
 __device__ __forceinline__ float round_to_float(double v) { return split_to_floats(v).x; }
 
-// the gather of one point into tree order (the leaf centre precomputed)
-__device__ __forceinline__ void gather_point(const LeafGather &g, double2 c, int k, int j) {
-  const double a = g.x[j], b = g.y[j];
+// one point into tree order, its coordinates (a, b) given (the leaf centre
+// precomputed)
+__device__ __forceinline__ void place_point(const LeafGather &g, double2 c, int k, int j, double a,
+                                            double b) {
   if (g.xs) {
     g.xs[k] = a;
     g.ys[k] = b;
@@ -561,48 +573,73 @@ __device__ __forceinline__ void gather_point(const LeafGather &g, double2 c, int
   }
 }
 
+// the same, reading the coordinates of caller index j
+__device__ __forceinline__ void gather_point(const LeafGather &g, double2 c, int k, int j) {
+  place_point(g, c, k, j, g.x[j], g.y[j]);
+}
+
+// block-wide reduction of the bounding-square partials (warp shuffles, then
+// the warps' results in shared memory); the block's result in lane 0 of warp 0
+struct BoxAcc {
+  long long xmn, xmx, ymx;
+  int bad;
+};
+__device__ __forceinline__ BoxAcc box_reduce(BoxAcc v, BoxAcc *ws) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.xmn = min(v.xmn, __shfl_xor_sync(0xffffffffu, v.xmn, o));
+    v.xmx = max(v.xmx, __shfl_xor_sync(0xffffffffu, v.xmx, o));
+    v.ymx = max(v.ymx, __shfl_xor_sync(0xffffffffu, v.ymx, o));
+    v.bad |= __shfl_xor_sync(0xffffffffu, v.bad, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? ws[lane] : BoxAcc{LLONG_MAX, LLONG_MIN, LLONG_MIN, 0};
+    for (int o = 16; o > 0; o >>= 1) {
+      v.xmn = min(v.xmn, __shfl_xor_sync(0xffffffffu, v.xmn, o));
+      v.xmx = max(v.xmx, __shfl_xor_sync(0xffffffffu, v.xmx, o));
+      v.ymx = max(v.ymx, __shfl_xor_sync(0xffffffffu, v.ymx, o));
+      v.bad |= __shfl_xor_sync(0xffffffffu, v.bad, o);
+    }
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(kBboxThreads)
 k_tb_bbox(TreeBuild a) {
-  constexpr int NT = kBboxThreads;
-  __shared__ long long s0[NT], s1[NT], s2[NT];
-  __shared__ int sb[NT];
+  __shared__ BoxAcc ws[kBboxThreads / 32];
   __shared__ int s_last;
-  const int64_t T = (int64_t)gridDim.x * NT;
-  const int64_t tid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  __shared__ double sg[4];
+  const int64_t T = (int64_t)gridDim.x * kBboxThreads;
+  const int64_t tid = (int64_t)blockIdx.x * kBboxThreads + threadIdx.x;
   // the bucket counters start at zero for k_tb_keys
   for (int64_t l = tid; l <= a.nbucket; l += T) a.bcount[l] = 0;
   // partials: order-preserving integer images of the doubles (min / max on
-  // the integer pipe)
-  long long xmn = LLONG_MAX, xmx = LLONG_MIN, ymx = LLONG_MIN;
-  int bad = 0;
-  for (int64_t i = tid; i < a.n; i += T) {
-    const long long u = __double_as_longlong(a.x[i]), v = __double_as_longlong(a.y[i]);
-    const bool fin = ((u >> 52) & 0x7ff) != 0x7ff && ((v >> 52) & 0x7ff) != 0x7ff;
-    if (!fin || v <= 0) bad = 1;
-    const long long ku = u >= 0 ? u : (u ^ 0x7fffffffffffffffll);
-    xmn = min(xmn, ku);
-    xmx = max(xmx, ku);
-    ymx = max(ymx, v);
-  }
-  auto reduce = [&]() {
-    s0[threadIdx.x] = xmn;
-    s1[threadIdx.x] = xmx;
-    s2[threadIdx.x] = ymx;
-    sb[threadIdx.x] = bad;
-    __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) {
-        s0[threadIdx.x] = min(s0[threadIdx.x], s0[threadIdx.x + w]);
-        s1[threadIdx.x] = max(s1[threadIdx.x], s1[threadIdx.x + w]);
-        s2[threadIdx.x] = max(s2[threadIdx.x], s2[threadIdx.x + w]);
-        sb[threadIdx.x] |= sb[threadIdx.x + w];
-      }
-      __syncthreads();
+  // the integer pipe); kBboxPer independent loads a thread
+  BoxAcc v{LLONG_MAX, LLONG_MIN, LLONG_MIN, 0};
+  for (int64_t i0 = tid; i0 < a.n; i0 += T * kBboxPer) {
+    long long u[kBboxPer], w[kBboxPer];
+#pragma unroll
+    for (int j = 0; j < kBboxPer; ++j) {
+      const int64_t i = i0 + j * T;
+      u[j] = i < a.n ? __double_as_longlong(a.x[i]) : 0ll;
+      w[j] = i < a.n ? __double_as_longlong(a.y[i]) : 0x3ff0000000000000ll;  // 1.0
     }
-  };
-  reduce();
+#pragma unroll
+    for (int j = 0; j < kBboxPer; ++j) {
+      if (i0 + j * T >= a.n) continue;
+      const bool fin = ((u[j] >> 52) & 0x7ff) != 0x7ff && ((w[j] >> 52) & 0x7ff) != 0x7ff;
+      if (!fin || w[j] <= 0) v.bad = 1;
+      const long long ku = u[j] >= 0 ? u[j] : (u[j] ^ 0x7fffffffffffffffll);
+      v.xmn = min(v.xmn, ku);
+      v.xmx = max(v.xmx, ku);
+      v.ymx = max(v.ymx, w[j]);
+    }
+  }
+  v = box_reduce(v, ws);
   if (threadIdx.x == 0) {
-    a.part[blockIdx.x] = Geom{dkey_inv(s0[0]), dkey_inv(s1[0]), dkey_inv(s2[0]), sb[0]};
+    a.part[blockIdx.x] = Geom{dkey_inv(v.xmn), dkey_inv(v.xmx), dkey_inv(v.ymx), v.bad};
     __threadfence();
     s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
   }
@@ -610,28 +647,24 @@ k_tb_bbox(TreeBuild a) {
   if (!s_last) return;
   // the last block: all partials, read past L1
   __threadfence();
-  xmn = LLONG_MAX;
-  xmx = LLONG_MIN;
-  ymx = LLONG_MIN;
-  bad = 0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
+  v = BoxAcc{LLONG_MAX, LLONG_MIN, LLONG_MIN, 0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kBboxThreads) {
     const volatile Geom *pg = a.part + b;
-    const long long u = __double_as_longlong(pg->xmin), v = __double_as_longlong(pg->xmax);
-    xmn = min(xmn, u >= 0 ? u : (u ^ 0x7fffffffffffffffll));
-    xmx = max(xmx, v >= 0 ? v : (v ^ 0x7fffffffffffffffll));
-    ymx = max(ymx, __double_as_longlong(pg->ymax));
-    bad |= pg->bad;
+    const long long u = __double_as_longlong(pg->xmin), w = __double_as_longlong(pg->xmax);
+    v.xmn = min(v.xmn, u >= 0 ? u : (u ^ 0x7fffffffffffffffll));
+    v.xmx = max(v.xmx, w >= 0 ? w : (w ^ 0x7fffffffffffffffll));
+    v.ymx = max(v.ymx, __double_as_longlong(pg->ymax));
+    v.bad |= pg->bad;
   }
   __syncthreads();
-  reduce();
-  __shared__ double sg[4];
+  v = box_reduce(v, ws);
   if (threadIdx.x == 0) {
     *a.ticket = 0;  // ready for the next build
-    const double xmin = dkey_inv(s0[0]), xmax = dkey_inv(s1[0]), ymax = dkey_inv(s2[0]);
+    const double xmin = dkey_inv(v.xmn), xmax = dkey_inv(v.xmx), ymax = dkey_inv(v.ymx);
     const double w = __dsub_rn(xmax, xmin);
     double L = (w > ymax) ? w : ymax;
     L = __dmul_rn(L, 1.0 + 0x1p-40);
-    double x0 = xmin, flag = sb[0] ? 1.0 : 0.0;
+    double x0 = xmin, flag = v.bad ? 1.0 : 0.0;
     if (a.root_side > 0) {  // caller's root square: it must contain the points
       const bool inside = a.root_x0 <= xmin && xmax <= a.root_x0 + a.root_side &&
                           ymax <= a.root_side;
@@ -764,77 +797,81 @@ k_tb_scatter(TreeBuild a) {
   __shared__ int ws[64];
   int maxbucket;
   const int total = chunk_offsets(a, off, ws, &maxbucket);
-  const int64_t T = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lsh = 2 * (a.Hb - a.H);
-  for (int64_t b = tid; b < a.nbucket; b += T) {
-    const int s = a.bcount[b] + off[b / kScanChunk];
-    a.bstart[b] = s;
-    if ((b & ((1 << lsh) - 1)) == 0) a.leaf_start[b >> lsh] = s;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // point t into its bucket, with its coordinates
+  if (t < a.n) {
+    const uint64_t k = a.kb[t];
+    const int bk = (int)(k >> (60 - 2 * a.Hb));
+    const int pos = a.bcount[bk] + off[bk / kScanChunk] + a.slot[t];
+    BRec r;
+    r.key = k;
+    r.x = a.x[t];
+    r.y = a.y[t];
+    r.v = (int)t;
+    r.pad = 0;
+    a.rec[pos] = r;
   }
-  if (tid == 0) {
+  // bucket t's start (and its leaf's, for the first bucket of a leaf)
+  const int lsh = 2 * (a.Hb - a.H);
+  if (t < a.nbucket) {
+    const int s0 = a.bcount[t] + off[t / kScanChunk];
+    a.bstart[t] = s0;
+    if ((t & ((1 << lsh) - 1)) == 0) a.leaf_start[t >> lsh] = s0;
+  }
+  if (t == 0) {
     a.bstart[a.nbucket] = total;
     a.leaf_start[a.nleaf] = total;
     int *mxp = (int *)(a.geo + 4);
     *mxp = maxbucket;
   }
-  if (a.g.loc32) {  // leaf centres (double precision, explicit roundings)
-    const double x0 = a.geo[0], d = ldexp(a.geo[1], -a.H);
-    for (int64_t l = tid; l < a.nleaf; l += T)
-      a.centre[l] = leaf_centre_at(x0, d, box_ix((uint64_t)l), box_iy((uint64_t)l));
-  }
-  const int sh = 60 - 2 * a.Hb;
-  for (int64_t i = tid; i < a.n; i += T) {
-    const uint64_t k = a.kb[i];
-    const int bk = (int)(k >> sh);
-    const int pos = a.bcount[bk] + off[bk / kScanChunk] + a.slot[i];
-    a.kt[pos] = k;
-    a.vt[pos] = (int)i;
-  }
+  // leaf t's centre (double precision, explicit roundings)
+  if (a.g.loc32 && t < a.nleaf)
+    a.centre[t] = leaf_centre_at(a.geo[0], ldexp(a.geo[1], -a.H), box_ix((uint64_t)t),
+                                 box_iy((uint64_t)t));
 }
 
 __global__ void __launch_bounds__(256)
 k_tb_sort(TreeBuild a) {
-  const int64_t bk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (bk >= a.nbucket) return;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // bucketed position
+  if (q >= a.n) return;
+  const BRec rq = a.rec[q];
+  const uint64_t kq = rq.key;
+  const int vq = rq.v;
+  const int64_t bk = (int64_t)(kq >> (60 - 2 * a.Hb));
   const int b0 = a.bstart[bk], m = a.bstart[bk + 1] - b0;
-  if (m == 0) return;
-  if (m > kTinyBucket) {
-    a.big[atomicAdd(a.bcount + a.nbucket, 1)] = (int)bk;
+  if (m > kTinyBucket) {  // listed once, by its first position
+    if (q == b0) a.big[atomicAdd(a.bcount + a.nbucket, 1)] = (int)bk;
     return;
   }
-  const int sh = 60 - 2 * a.H;
-  for (int j = 0; j < m; ++j) {
-    const uint64_t kj = a.kt[b0 + j];
-    const int vj = a.vt[b0 + j];
-    int r = 0;
-    for (int i = 0; i < m; ++i) {
-      const uint64_t ki = a.kt[b0 + i];
-      const int vi = a.vt[b0 + i];
-      r += (ki < kj || (ki == kj && vi < vj)) ? 1 : 0;
-    }
-    a.keys[b0 + r] = kj;
-    const double2 c = a.g.loc32 ? a.centre[kj >> sh] : make_double2(0.0, 0.0);
-    gather_point(a.g, c, b0 + r, vj);
+  // rank by (key, index) among the bucket's points
+  int r = 0;
+  for (int i = b0; i < b0 + m; ++i) {
+    const uint64_t ki = a.rec[i].key;
+    const int vi = a.rec[i].v;
+    r += (ki < kq || (ki == kq && vi < vq)) ? 1 : 0;
   }
+  const int k = b0 + r;
+  a.keys[k] = kq;
+  const double2 c = a.g.loc32 ? a.centre[kq >> (60 - 2 * a.H)] : make_double2(0.0, 0.0);
+  place_point(a.g, c, k, vq, rq.x, rq.y);
 }
 
-// buckets of more than kTinyBucket points: sorted in place in (kt, vt) by a
-// warp (up to 128 points, bitonic network in registers) or by the block (up
-// to kLeafSort in shared memory, larger ones in global memory), then the
-// sorted keys written to kout and the points gathered into tree order
+// buckets of more than kTinyBucket points: sorted by a warp (up to 128
+// points, bitonic network in registers) or by the block (up to kLeafSort in
+// shared memory, larger ones in place in global memory, in the input-order
+// key and slot arrays, free by then), then the sorted keys written and the
+// points gathered into tree order
 template <int E>
-__device__ __forceinline__ void warp_sort_bucket(int b0, int m, int lane, const uint64_t *kt,
-                                                 const int *vt, uint64_t *kout,
-                                                 const LeafGather &g, const double2 *centre,
-                                                 int sh) {
+__device__ __forceinline__ void warp_sort_bucket(int b0, int m, int lane, const BRec *rec,
+                                                 uint64_t *kout, const LeafGather &g,
+                                                 const double2 *centre, int sh) {
   uint64_t k[E];
   int v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int i = e * 32 + lane;
-    k[e] = i < m ? kt[b0 + i] : ~0ull;
-    v[e] = i < m ? vt[b0 + i] : 0x7fffffff;
+    k[e] = i < m ? rec[b0 + i].key : ~0ull;
+    v[e] = i < m ? rec[b0 + i].v : 0x7fffffff;
   }
   warp_bitonic<E>(k, v, lane);
 #pragma unroll
@@ -862,9 +899,9 @@ k_tb_big(TreeBuild a) {
     const int bk = a.big[bi];
     const int b0 = a.bstart[bk], m = a.bstart[bk + 1] - b0;
     if (m > 128) continue;
-    if (m <= 32) warp_sort_bucket<1>(b0, m, lane, a.kt, a.vt, a.keys, a.g, a.centre, sh);
-    else if (m <= 64) warp_sort_bucket<2>(b0, m, lane, a.kt, a.vt, a.keys, a.g, a.centre, sh);
-    else warp_sort_bucket<4>(b0, m, lane, a.kt, a.vt, a.keys, a.g, a.centre, sh);
+    if (m <= 32) warp_sort_bucket<1>(b0, m, lane, a.rec, a.keys, a.g, a.centre, sh);
+    else if (m <= 64) warp_sort_bucket<2>(b0, m, lane, a.rec, a.keys, a.g, a.centre, sh);
+    else warp_sort_bucket<4>(b0, m, lane, a.rec, a.keys, a.g, a.centre, sh);
   }
   for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
     const int bk = a.big[bi];
@@ -872,20 +909,27 @@ k_tb_big(TreeBuild a) {
     if (m <= 128) continue;
     __syncthreads();
     if (m > kLeafSort) {
-      sort_leaf_global(a.kt + b0, a.vt + b0, m);
+      uint64_t *kw = a.kb + b0;
+      int *vw = a.slot + b0;
       for (int e = threadIdx.x; e < m; e += blockDim.x) {
-        const uint64_t k = a.kt[b0 + e];
+        kw[e] = a.rec[b0 + e].key;
+        vw[e] = a.rec[b0 + e].v;
+      }
+      __threadfence_block();
+      __syncthreads();
+      sort_leaf_global(kw, vw, m);
+      for (int e = threadIdx.x; e < m; e += blockDim.x) {
+        const uint64_t k = kw[e];
         a.keys[b0 + e] = k;
-        gather_point(a.g, a.g.loc32 ? a.centre[k >> sh] : make_double2(0.0, 0.0), b0 + e,
-                     a.vt[b0 + e]);
+        gather_point(a.g, a.g.loc32 ? a.centre[k >> sh] : make_double2(0.0, 0.0), b0 + e, vw[e]);
       }
       continue;
     }
     int np2 = 1;
     while (np2 < m) np2 <<= 1;
     for (int e = threadIdx.x; e < np2; e += blockDim.x) {
-      sk[e] = e < m ? a.kt[b0 + e] : ~0ull;
-      sv[e] = e < m ? a.vt[b0 + e] : 0x7fffffff;
+      sk[e] = e < m ? a.rec[b0 + e].key : ~0ull;
+      sv[e] = e < m ? a.rec[b0 + e].v : 0x7fffffff;
     }
     __syncthreads();
     for (int kk = 2; kk <= np2; kk <<= 1) {
@@ -925,16 +969,18 @@ namespace {
 struct TreeTmp {
   char *base = nullptr;
   Geom *part;
-  uint64_t *kb, *kt;
-  int *vt, *slot, *bcount, *bstart, *ctot, *big;
+  uint64_t *kb;
+  BRec *rec;
+  int *slot, *bcount, *bstart, *ctot, *big;
   double2 *centre;
   int nbbox, Hb, nchunk;
 };
 
-// bucket level: about one point per bucket (level round(log4 n)), at least
-// the leaf level, at most level 11 (4M buckets) unless the leaves are deeper
+// bucket level: about four points per bucket (level round(log4 n) - 1), at
+// least the leaf level, at most level 11 (4M buckets) unless the leaves are
+// deeper
 int bucket_level(int64_t n, int H) {
-  int hb = (int)floor(log((double)(n > 1 ? n : 1)) / log(4.0) + 0.5);
+  int hb = (int)floor(log((double)(n > 1 ? n : 1)) / log(4.0) + 0.5) - 1;
   if (hb > 11) hb = 11;
   return hb > H ? hb : H;
 }
@@ -950,12 +996,13 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
     set_last_error("tree build: %d leaf levels exceed the bucket scan", pl->Hsort);
     return HPFMM_EUNSUPPORTED;
   }
-  int64_t nbb = (n + 4 * kBboxThreads - 1) / (4 * kBboxThreads);
-  t.nbbox = (int)(nbb < 1 ? 1 : (nbb > 1024 ? 1024 : nbb));
-  size_t bytes = sizeof(Geom) * t.nbbox + 2 * sizeof(uint64_t) * n + 2 * sizeof(int) * n +
+  int64_t nbb = (n + kBboxPer * kBboxThreads - 1) / (kBboxPer * kBboxThreads);
+  t.nbbox = (int)(nbb < 1 ? 1 : (nbb > 2048 ? 2048 : nbb));
+  size_t bytes = sizeof(Geom) * t.nbbox + sizeof(uint64_t) * n + sizeof(BRec) * n +
+                 sizeof(int) * n +
                  sizeof(int) * (3 * nb + 3) + sizeof(double2) * (size_t)nleaf +
                  2 * sizeof(int) * (size_t)t.nchunk;
-  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 12 * 256, st));
+  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 14 * 256, st));
   char *c = t.base;
   auto carve = [&](size_t b) {
     char *r = c;
@@ -964,8 +1011,7 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
   };
   t.part = (Geom *)carve(sizeof(Geom) * t.nbbox);
   t.kb = (uint64_t *)carve(sizeof(uint64_t) * n);
-  t.kt = (uint64_t *)carve(sizeof(uint64_t) * n);
-  t.vt = (int *)carve(sizeof(int) * n);
+  t.rec = (BRec *)carve(sizeof(BRec) * n);
   t.slot = (int *)carve(sizeof(int) * n);
   t.bcount = (int *)carve(sizeof(int) * (nb + 1));
   t.bstart = (int *)carve(sizeof(int) * (nb + 1));
@@ -1005,9 +1051,8 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   a.part = t.part;
   a.ticket = pl->tree_ctr;
   a.kb = t.kb;
-  a.kt = t.kt;
+  a.rec = t.rec;
   a.slot = t.slot;
-  a.vt = t.vt;
   a.bcount = t.bcount;
   a.bstart = t.bstart;
   a.centre = t.centre;
@@ -1016,13 +1061,14 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   a.status = pl->status;
   const int64_t n = pl->n;
   const unsigned gp = (unsigned)((n + 255) / 256);
-  const unsigned gb = (unsigned)(((int64_t)a.nbucket + 255) / 256);
+  const int64_t nitem = n > a.nbucket ? n : (int64_t)a.nbucket;
+  const unsigned gs = (unsigned)((nitem + 255) / 256);
   pass_begin(pl, st, PASS_TREE);
   k_tb_bbox<<<t.nbbox, kBboxThreads, 0, st>>>(a);
   k_tb_keys<<<gp, 256, 0, st>>>(a);
   k_tb_scan<<<t.nchunk, 1024, 0, st>>>(a);
-  k_tb_scatter<<<(unsigned)(gp < 1216 ? gp : 1216), 256, 0, st>>>(a);
-  k_tb_sort<<<gb, 256, 0, st>>>(a);
+  k_tb_scatter<<<gs, 256, 0, st>>>(a);
+  k_tb_sort<<<gp, 256, 0, st>>>(a);
   k_tb_big<<<608, 256, 0, st>>>(a);
   pass_end(pl, st, PASS_TREE, 6);
   // released (stream-ordered) by tree_finish

@@ -60,31 +60,37 @@ def test_vlist_translations_brute_force(H):
 
 
 def test_roofline_arithmetic():
-    """achieved = algorithmic work per launch / per-launch time, frac =
-    achieved / peak (the measured pipe peak); the dominant single-kernel pass
-    is the one reported, the others under "others"."""
+    """achieved = algorithmic work per step / device time per step (= work
+    per launch / average launch duration), frac = achieved / peak (the
+    measured pipe peak); the pass with the largest device time is the one
+    reported, the others under "others".  A pass of several launches (the
+    split M2L, the six tree kernels) counts its step's work once."""
     class A:
         n, p, prec = 1_000_000, 12, "fp32"
-    launches = {"eval": 10, "m2l_free": 10, "m2m": 20, "tree": 10}
-    passes = {"eval": 1.5, "m2l_free": 1.2, "m2m": 3.0, "tree": 0.5}  # ms over 10 steps
+    launches = {"eval": 1, "m2l_free": 2, "m2m": 2, "tree": 6}  # per step
+    passes = {"eval": 0.15, "m2l_free": 0.12, "m2m": 0.3, "tree": 0.05}  # ms per step
     alu = {"sms": 152, "mufu_ops_per_s": 5.0e12, "ffma_flops_per_s": 78e12,
            "mufu_mhz": 2070.0, "ffma_mhz": 2070.0}
     npairs = 100_000_000
     r = bench.roofline(passes, launches, A, npairs, 8, alu, 6800.0)
-    t = 1.5e-3 / 10
-    assert r["kernel"] == bench.SINGLE_KERNEL["eval"][0]
+    t = 0.15e-3
+    assert r["kernel"] == bench.PASS_KERNELS["eval"][0]
     assert r["achieved"] == pytest.approx(2.0 * npairs / t / 1e12)
     assert r["peak"] == pytest.approx(5.0)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["per_launch_ms"] == pytest.approx(0.15)
-    assert set(r["others"]) == {"m2l_free", "tree"}  # m2m is not a single-kernel pass
+    assert set(r["others"]) == {"m2l_free", "tree"}  # m2m has no countable work here
     tr = r["others"]["tree"]
     assert tr["bound"] == "hbm" and tr["peak"] == 6800.0
+    assert tr["per_launch_ms"] == pytest.approx(0.05 / 6)
     per = 16 + 8 + 8 + 20
     assert tr["achieved"] == pytest.approx((per * A.n + 4 * (4 ** 8 + 1)) / 0.05e-3 / 1e9)
-    # M2L dominant: 8 (p+1)^2 flops per translation against the FP32 FMA peak
-    passes = {"eval": 1.0, "m2l_free": 1.2}
+    # the two M2L launches share the step's 8 (p+1)^2 flops per translation
+    mf = r["others"]["m2l_free"]
+    assert mf["per_launch_ms"] == pytest.approx(0.06)
+    assert mf["achieved"] == pytest.approx(8.0 * 13 * 13 * bench.vlist_translations(8) / 0.12e-3 / 1e12)
+    # M2L dominant: against the FP32 FMA peak
+    passes = {"eval": 0.1, "m2l_free": 0.12}
     r = bench.roofline(passes, launches, A, npairs, 8, alu, 6800.0)
-    t = 1.2e-3 / 10
-    assert r["achieved"] == pytest.approx(8.0 * 13 * 13 * bench.vlist_translations(8) / t / 1e12)
+    assert r["kernel"] == bench.PASS_KERNELS["m2l_free"][0]
     assert r["peak"] == pytest.approx(78.0)

@@ -60,9 +60,9 @@ def test_multi_rhs_matches_one_at_a_time(n, nrhs, levels):
 
 
 def test_multi_rhs_potentials_only_and_odd_order():
-    """grad=None in the shared passes; an odd order uses one pass set per RHS
-    (the shared passes need the even-order M2L kernel) and is then bitwise
-    equal to one-at-a-time evaluation."""
+    """grad=None in the shared passes; an odd order shares the passes too (the
+    patch M2L exists for every order) and agrees with one-at-a-time
+    evaluation to single-precision rounding."""
     x, y, _ = workloads.uniform(4000, seed=2)
     Q = charges(9, 4000, 7)
     plan = hp.hpfmm_create(t(x), t(y), kappa=1.0, p=12, leaf_size=32, prec="fp32")
@@ -74,7 +74,10 @@ def test_multi_rhs_potentials_only_and_odd_order():
     u, g = hp.hpfmm_eval(plan, t(Q[:3]))
     for r in range(3):
         u1, g1 = hp.hpfmm_eval(plan, t(Q[r]))
-        assert torch.equal(u[r], u1) and torch.equal(g[r], g1)
+        assert rel(u[r].cpu().numpy(), u1.cpu().numpy()) < 2e-6
+        assert rel(g[r].cpu().numpy(), g1.cpu().numpy()) < 2e-5
+    u_ref, _ = oracle.direct(x, y, Q[1], kappa=1.0, grad=False)
+    assert rel(u[1].cpu().numpy(), u_ref) < 5e-6
 
 
 def test_multi_rhs_workload_64_on_500k():
