@@ -196,7 +196,7 @@ def vlist_translations(H):
 # kernels), and its work per launch is then the step's work over its launches
 PASS_KERNELS = {"eval": ("k_near32", "k_eval64"), "m2l_free": ("k_m2l_free_patch", None),
                 "m2l_mirror": ("k_m2l_mirror_all", "k_m2l_mirror_all"),
-                "p2m": ("k_s2m_thread", "k_p2m"), "near_mirror": ("k_mirror32", None),
+                "p2m": ("k_s2m_tile", "k_p2m"), "near_mirror": ("k_mirror32", None),
                 "tree": ("k_tb_* (tree build: bbox, keys, scan, scatter, sort, big-leaf sort)",) * 2,
                 "l2l": ("k_downward<float, true>", "k_downward<double, false>")}
 

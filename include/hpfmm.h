@@ -337,6 +337,20 @@ hpfmm_status hpfmm_get_order(const hpfmm_plan *plan, uint64_t *keys, int64_t *pe
 hpfmm_status hpfmm_set_timing(hpfmm_plan *plan, int enable);
 hpfmm_status hpfmm_read_timing(hpfmm_plan *plan, double ms[10], int64_t launches[10]);
 
+/*
+ * The same records as a timeline: for each pass interval recorded since the
+ * previous read (in recording order, at most cap of them), its pass id and
+ * its begin and end in device milliseconds from the earliest recorded begin.
+ * The passes run on several streams, so intervals overlap where passes run
+ * concurrently; the gaps and the longest chain show the step's critical
+ * path.  Synchronises with the recorded events and consumes the records as
+ * hpfmm_read_timing does (read one or the other).  *count = the number of
+ * intervals written.  EINVAL for a NULL plan or count, or NULL arrays with
+ * cap > 0.
+ */
+hpfmm_status hpfmm_read_timeline(hpfmm_plan *plan, int cap, int *pass, double *begin_ms,
+                                 double *end_ms, int *count);
+
 /* Wait for the plan's outstanding work on `stream` and report any device-side
  * status (HPFMM_ETIMEOUT) recorded by its kernels. */
 hpfmm_status hpfmm_sync(hpfmm_plan *plan, void *stream);

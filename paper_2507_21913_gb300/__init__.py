@@ -90,6 +90,7 @@ def lib(build_if_missing: bool = False):
     L.hpfmm_selftest_wait_timeout.argtypes = [vp]
     L.hpfmm_tree_order_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
     L.hpfmm_read_timing.argtypes = [vp, vp, vp]
+    L.hpfmm_read_timeline.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
     L.hpfmm_eval_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.hpfmm_batch_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
     L.hpfmm_eval_batched.argtypes = [vp, vp, vp, vp, vp]
@@ -451,6 +452,18 @@ def hpfmm_read_timing(plan):
     ln = np.zeros(len(PASS_NAMES), np.int64)
     _check(lib().hpfmm_read_timing(plan.handle, ms.ctypes.data, ln.ctypes.data))
     return dict(zip(PASS_NAMES, ms.tolist())), dict(zip(PASS_NAMES, ln.tolist()))
+
+
+def hpfmm_read_timeline(plan, cap=4096):
+    """[(pass name, begin ms, end ms)] of the pass intervals recorded since the
+    last read, offsets from the earliest begin (see include/hpfmm.h)."""
+    ps = np.zeros(cap, np.int32)
+    b = np.zeros(cap)
+    e = np.zeros(cap)
+    cnt = ctypes.c_int32(0)
+    _check(lib().hpfmm_read_timeline(plan.handle, cap, ps.ctypes.data, b.ctypes.data,
+                                     e.ctypes.data, ctypes.byref(cnt)))
+    return [(PASS_NAMES[int(ps[i])], float(b[i]), float(e[i])) for i in range(cnt.value)]
 
 
 def hpfmm_sync(plan):

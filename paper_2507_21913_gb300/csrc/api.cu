@@ -127,6 +127,44 @@ extern "C" hpfmm_status hpfmm_read_timing(hpfmm_plan *pl, double ms[10], int64_t
   return HPFMM_OK;
 }
 
+extern "C" hpfmm_status hpfmm_read_timeline(hpfmm_plan *pl, int cap, int *pass, double *begin_ms,
+                                            double *end_ms, int *count) {
+  if (!pl || !count || cap < 0 || (cap > 0 && (!pass || !begin_ms || !end_ms))) {
+    set_last_error("hpfmm_read_timeline: null plan, count or output arrays");
+    return HPFMM_EINVAL;
+  }
+  *count = 0;
+  TimingState *ts = (TimingState *)pl->tstate;
+  if (!ts || ts->recs.empty()) return HPFMM_OK;
+  // the events sit on several streams: wait for each before reading offsets
+  for (auto &r : ts->recs) {
+    HP_CUDA(cudaEventSynchronize(ts->pool[r.a]));
+    HP_CUDA(cudaEventSynchronize(ts->pool[r.b]));
+  }
+  // the origin: the earliest begin event
+  size_t o = ts->recs.front().a;
+  for (auto &r : ts->recs) {
+    float t = 0.f;
+    HP_CUDA(cudaEventElapsedTime(&t, ts->pool[o], ts->pool[r.a]));
+    if (t < 0.f) o = r.a;
+  }
+  int k = 0;
+  for (auto &r : ts->recs) {
+    if (k >= cap) break;
+    float ta = 0.f, tb = 0.f;
+    HP_CUDA(cudaEventElapsedTime(&ta, ts->pool[o], ts->pool[r.a]));
+    HP_CUDA(cudaEventElapsedTime(&tb, ts->pool[o], ts->pool[r.b]));
+    pass[k] = r.pass;
+    begin_ms[k] = ta;
+    end_ms[k] = tb;
+    ++k;
+  }
+  *count = k;
+  ts->recs.clear();
+  ts->used = 0;
+  return HPFMM_OK;
+}
+
 static void free_plan(hpfmm_plan *pl) {
   if (!pl) return;
   if (pl->side_stream) {
@@ -164,7 +202,8 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->mM, pl->mA, pl->mB, pl->tflag, pl->tlist, pl->t_m2l_tc,
                   pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_parent, pl->ab_lvl, pl->ab_child,
                   pl->ab_cut, pl->ab_off, pl->ab_idx, pl->ab_lev, pl->ab_btot, pl->ab_lrank,
-                  pl->ab_leaf, pl->near, pl->loclo, pl->dgeom, pl->tree_ctr, pl->ctr, pl->mir_A, pl->mir_B};
+                  pl->ab_leaf, pl->near, pl->loclo, pl->dgeom, pl->tree_ctr, pl->ctr, pl->mir_A, pl->mir_B,
+                  pl->tree_tmp};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -220,8 +259,8 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   if (s == HPFMM_OK) {
     // the geometry to the host and the reaction tables (they depend on the
     // root square only) on the table stream, concurrent with what follows
-    e = cudaEventRecord(pl->ev_tree, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->table_stream, pl->ev_tree, 0);
+    // (ev_tree: recorded by tree_build once the root square is known)
+    e = cudaStreamWaitEvent(pl->table_stream, pl->ev_tree, 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(pl->hgeo, pl->geo, 5 * sizeof(double), cudaMemcpyDeviceToHost,
                           pl->table_stream);
@@ -350,7 +389,15 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     return HPFMM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("hpfmm_create: no usable CUDA device");
+    return HPFMM_ECUDA;
+  }
   hpfmm_plan *pl = new hpfmm_plan();
+  pl->sms = sms;
   pl->n = n;
   pl->p = p;
   pl->prec = o.prec;
@@ -408,7 +455,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->t_m2m, tf * 4 * m2);
   ALLOC(pl->t_l2l, tf * 4 * m2);
   ALLOC(pl->t_m2l, tf * 49 * m2);
-  if (f32) ALLOC(pl->t_m2l_pad, sizeof(cf) * 40 * 2 * 2 * (size_t)P1);
+  if (!pl->adaptive || f32) ALLOC(pl->t_m2l_pad, csz * 40 * 2 * 2 * (size_t)P1);
   if (f32 && pl->m2l_mode == 1)
     ALLOC(pl->t_m2l_tc, sizeof(float) * 40 * 2 * (size_t)tc_np(P1) * tc_kp(P1));
   ALLOC(pl->t_rlog, tf * 21 * m2);
@@ -436,13 +483,18 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   if (s == HPFMM_OK) s = adaptive_prepare();
   if (s != HPFMM_OK) { free_plan(pl); return s; }
   {
-    // the side stream carries the reaction tables of a rebuild and the
-    // far-field chain of a split evaluation: the greatest priority
+    // the plan's streams -- side (far-field chain of a split evaluation),
+    // m2l (its leaf-level M2L), table (reaction tables of a rebuild, the
+    // bottom-row image/reaction pairs and the mirror M2L) -- take the
+    // greatest priority: their short dependent kernels then take SMs before
+    // the blocks of the near field on the caller's stream, which fills the
+    // rest and ends the chain
     int prio_lo = 0, prio_hi = 0;
     cudaError_t ce = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->side_stream, cudaStreamNonBlocking, prio_hi);
-    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->table_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess)
+      ce = cudaStreamCreateWithPriority(&pl->table_stream, cudaStreamNonBlocking, prio_hi);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->m2l_stream, cudaStreamNonBlocking, prio_hi);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_s2m, cudaEventDisableTiming);

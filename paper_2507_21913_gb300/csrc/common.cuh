@@ -350,8 +350,9 @@ struct hpfmm_plan {
   int *ctr = nullptr;     // device: last-block counters of the fused upward pass, one per RHS
   int async_update = 0;   // hpfmm_options.async_update
   bool geo_pending = false;  // host copies x0 / side / qscale wait for ev_geo
-  void *tree_tmp = nullptr;  // tree-build temporaries awaiting tree_finish
+  void *tree_tmp = nullptr;  // tree-build temporaries, kept for the rebuilds of the plan
   int64_t tree_tmp_bytes = 0;
+  int sms = 0;               // streaming multiprocessors of the plan's device
   int64_t workspace_bytes = 0;
 
   // pass timing (events on the caller's stream) and launch counts

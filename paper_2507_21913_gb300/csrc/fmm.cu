@@ -141,9 +141,10 @@ k_p2m(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_
 }
 
 // --------------------------------------------------------------------------
-// S2M with one thread per (leaf, n): M_n = sum_j Q_j w_j^n, w_j = (z_j - z_c)/d,
-// w^n by repeated squaring.  No cross-thread reduction, so the short leaves
-// of a deep tree keep every lane busy.
+// Single-precision S2M, M_n = sum_j Q_j w_j^n with w_j = (z_j - z_c)/d: one
+// thread per (leaf, n) or (leaf, group of orders), with no cross-thread
+// reduction, so the short leaves of a deep tree keep every lane busy.  w^n by
+// repeated squaring.
 template <typename R>
 __device__ __forceinline__ cpx<R> cpow_int(cpx<R> w, int n) {
   cpx<R> r = mk<R>(1, 0);
@@ -155,60 +156,77 @@ __device__ __forceinline__ cpx<R> cpow_int(cpx<R> w, int n) {
   return r;
 }
 
-constexpr int kS2mGroup = 4;  // orders per thread of the single-precision S2M
+constexpr int kS2mGroup = 8;  // orders per thread of the single-precision S2M (a power of 2)
 
-template <typename R>
-__global__ void __launch_bounds__(256)
-k_s2m_thread(LeafPoints<R> pts, const R *__restrict__ qs, const int *__restrict__ leaf_start,
-             int H, const DevGeom *__restrict__ dg, int p, cpx<R> *__restrict__ M,
-             RhsStride rs) {
-  // one thread per leaf and group of kS2mGroup consecutive orders n0 .. n0+3:
-  // w^n0 = (w^4)^(n0/4) from two squarings, then one product per further n
+// Single-precision S2M over a tile of kS2mLeaves consecutive leaves per block.
+// The tile's points are contiguous in tree order, so the block first copies
+// their leaf-frame positions and charges into shared memory with coalesced
+// loads (a per-thread loop over global memory would wait on one load per
+// point); a tile of more than kS2mCap points reads them from global memory
+// instead.  Each thread then takes items (leaf, group of kS2mGroup = G
+// consecutive orders n0 .. n0+G-1): w^n0 = (w^G)^(n0/G) from log2 G
+// squarings, then one product per further n.  The sums are compensated (Kahan): the moments of a
+// leaf are sums of up to hundreds of terms of both signs, and their rounding
+// error is inherited by every far-field coefficient built from them.
+constexpr int kS2mLeaves = 64, kS2mCap = 2048, kS2mThreads = 128;
+
+__global__ void __launch_bounds__(kS2mThreads)
+k_s2m_tile(const float2 *__restrict__ loc, const float *__restrict__ qs,
+           const int *__restrict__ leaf_start, int H, const DevGeom *__restrict__ dg, int p,
+           cf *__restrict__ M, RhsStride rs) {
   constexpr int G = kS2mGroup;
+  __shared__ float2 sp[kS2mCap];
+  __shared__ float sq[kS2mCap];
   const int P1 = p + 1, NB = (P1 + G - 1) / G;
   qs += blockIdx.y * rs.q;
   M += blockIdx.y * rs.m;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < 4^12 * 11 < 2^32
-  const unsigned nleaf = 1u << (2 * H);
-  if (t >= nleaf * (unsigned)NB) return;
-  const unsigned leaf = t / (unsigned)NB;
-  const int nb = (int)(t - leaf * (unsigned)NB), n0 = G * nb;
-  // (the single-precision points are already relative to the leaf centre)
-  const double cx = 0.0, cy = 0.0;
-  const R invd = (R)dg->invd[H];
-  const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-  // compensated (Kahan) summation: the moments of a leaf are sums of up to
-  // hundreds of terms of both signs, and their rounding error is inherited
-  // by every far-field coefficient built from them
-  cpx<R> acc[G], cmp[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) acc[g] = cmp[g] = mk<R>(0, 0);
-  for (int j = b0; j < b1; ++j) {
-    R rx, ry;
-    pts.rel(j, cx, cy, rx, ry);
-    const cpx<R> w = mk<R>(rx * invd, ry * invd);
-    const cpx<R> w2 = w * w, w4 = w2 * w2;
-    cpx<R> wn = mk<R>(qs[j], 0);
-    for (int i = 0; i < nb; ++i) wn = wn * w4;  // q w^n0
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const cpx<R> yv = wn - cmp[g];
-      const cpx<R> tv = acc[g] + yv;
-      cmp[g] = (tv - acc[g]) - yv;
-      acc[g] = tv;
-      wn = wn * w;
+  const int nleaf = 1 << (2 * H);
+  const int L0 = blockIdx.x * kS2mLeaves, L1 = min(L0 + kS2mLeaves, nleaf);
+  const int t0 = leaf_start[L0], t1 = leaf_start[L1];
+  const bool staged = t1 - t0 <= kS2mCap;
+  if (staged) {
+    for (int i = threadIdx.x; i < t1 - t0; i += blockDim.x) {
+      sp[i] = loc[t0 + i];
+      sq[i] = qs[t0 + i];
     }
   }
-  const size_t e0 = ((size_t)level_offset(H) + leaf) * P1;
+  __syncthreads();
+  const float invd = dg->invd[H];
+  for (int it = threadIdx.x; it < (L1 - L0) * NB; it += blockDim.x) {
+    const int leaf = L0 + it / NB, nb = it % NB, n0 = G * nb;
+    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    cf acc[G], cmp[G];
 #pragma unroll
-  for (int g = 0; g < G; ++g)
-    if (n0 + g < P1) M[e0 + n0 + g] = acc[g];
+    for (int g = 0; g < G; ++g) acc[g] = cmp[g] = mk(0.f, 0.f);
+    for (int j = b0; j < b1; ++j) {
+      const float2 v = staged ? sp[j - t0] : loc[j];
+      const float qj = staged ? sq[j - t0] : qs[j];
+      const cf w = mk(v.x * invd, v.y * invd);
+      cf wg = w;  // w^G by squarings
+#pragma unroll
+      for (int g = 1; g < G; g <<= 1) wg = wg * wg;
+      cf wn = mk(qj, 0.f);
+      for (int i = 0; i < nb; ++i) wn = wn * wg;  // q w^n0
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const cf yv = wn - cmp[g];
+        const cf tv = acc[g] + yv;
+        cmp[g] = (tv - acc[g]) - yv;
+        acc[g] = tv;
+        wn = wn * w;
+      }
+    }
+    const size_t e0 = ((size_t)level_offset(H) + leaf) * P1;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (n0 + g < P1) M[e0 + n0 + g] = acc[g];
+  }
 }
 
 // Multi-RHS S2M (single precision): the powers ((z_j - z_c)/d)^n of a point
 // are formed once and applied to RC charge vectors (blockIdx.y selects RHS
 // r0 .. r0 + RC - 1; charges point-major, qsm[k * rp + r]), with the same
-// compensated summation per RHS as k_s2m_thread.
+// compensated summation per RHS as k_s2m_tile.
 template <int RC>
 __global__ void __launch_bounds__(256)
 k_s2m_multi(const float2 *__restrict__ loc, const float *__restrict__ qsm, int rp, int nr,
@@ -294,30 +312,57 @@ __device__ __forceinline__ void m2m_item(int l, int e, int P1, const cpx<R> *__r
   M[(size_t)(level_offset(l) + b) * P1 + n] = acc;
 }
 
-// M2M in shared memory from nchild boxes of level lc (child, Morton order
-// from box `first` << 2) up to level lto: each level's boxes written after
-// the previous ones in smem and to M
+// Shared-memory layout of a level's moments in the fused upward pass: boxes
+// grouped by parent, [b / 4][b % 4][m], with a padded group stride GS = 4 P1
+// + pad chosen so that the groups of consecutive parents start in different
+// shared-memory banks (GS = 1 mod 16 complex floats, 1 mod 8 complex
+// doubles): the lanes of a warp, one parent each, then read their children
+// without bank conflicts.
+template <typename R>
+__host__ __device__ __forceinline__ int m2m_group_stride(int P1) {
+  const int mod = sizeof(R) == 4 ? 16 : 8;
+  const int g = 4 * P1;
+  return g + ((1 - g) % mod + mod) % mod;
+}
+template <typename R>
+__host__ __device__ __forceinline__ size_t m2m_slot(int b, int m, int P1) {
+  return (size_t)(b >> 2) * m2m_group_stride<R>(P1) + (size_t)(b & 3) * P1 + m;
+}
+
+// M2M in shared memory from nchild boxes of level lc (child, grouped layout,
+// Morton order from box `first` << 2) up to level lto: each level's boxes
+// written after the previous ones in smem (grouped layout) and to M.  Item
+// (order n, parent b) with the lanes over parents, so that the lanes of a
+// warp share n and the length of the sum over m; then a coalesced copy of
+// the level to M.
 template <typename R>
 __device__ __forceinline__ void m2m_levels_smem(cpx<R> *child, int nchild, int lc, int lto,
                                                 int64_t first_child, int P1,
                                                 const cpx<R> *__restrict__ T,
                                                 cpx<R> *__restrict__ M) {
+  const int GS = m2m_group_stride<R>(P1);
   for (int l = lc - 1; l >= lto; --l) {
-    cpx<R> *par = child + (size_t)nchild * P1;
+    cpx<R> *par = child + (size_t)((nchild + 3) >> 2) * GS;
     const int npar = nchild >> 2;
     const int64_t first = first_child >> (2 * (lc - l));
     for (int e = threadIdx.x; e < npar * P1; e += blockDim.x) {
-      const int b = e / P1, n = e % P1;
+      const int n = e / npar, b = e - n * npar;
       cpx<R> acc = mk<R>(0, 0);
+      const cpx<R> *mg = child + (size_t)b * GS;  // the four children of parent b
+#pragma unroll
       for (int c = 0; c < 4; ++c) {
         const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)n * P1;
-        const cpx<R> *mc = child + (size_t)(4 * b + c) * P1;
+        const cpx<R> *mc = mg + c * P1;
         for (int m = 0; m <= n; ++m) cfma(acc, Tc[m], mc[m]);
       }
-      par[e] = acc;
-      M[(size_t)(level_offset(l) + first + b) * P1 + n] = acc;
+      par[m2m_slot<R>(b, n, P1)] = acc;
     }
     __syncthreads();
+    const size_t o = (size_t)(level_offset(l) + first) * P1;
+    for (int e = threadIdx.x; e < npar * P1; e += blockDim.x) {
+      const int b = e / P1, n = e - b * P1;
+      M[o + e] = par[m2m_slot<R>(b, n, P1)];
+    }
     child = par;
     nchild = npar;
   }
@@ -337,8 +382,10 @@ k_upward(int H, int k, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restric
   const int nl = 1 << (2 * k);                 // leaves per subtree
   const int64_t first_leaf = (int64_t)blockIdx.x * nl;  // Morton order: subtree = contiguous
   // leaf moments (computed by the S2M kernel) into shared memory
-  for (int e = threadIdx.x; e < nl * P1; e += blockDim.x)
-    Ms[e] = M[(size_t)(level_offset(H) + first_leaf) * P1 + e];
+  for (int e = threadIdx.x; e < nl * P1; e += blockDim.x) {
+    const int b = e / P1, m = e - b * P1;
+    Ms[m2m_slot<R>(b, m, P1)] = M[(size_t)(level_offset(H) + first_leaf) * P1 + e];
+  }
   __syncthreads();
   // M2M inside the subtree: level H-1 .. H-k
   m2m_levels_smem<R>(Ms, nl, H, H - k, first_leaf, P1, T, M);
@@ -354,8 +401,10 @@ k_upward(int H, int k, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restric
   if (!s_last) return;
   __threadfence();
   const int nb0 = 1 << (2 * l0);
-  for (int e = threadIdx.x; e < nb0 * P1; e += blockDim.x)
-    Ms[e] = ldcg_c(M + (size_t)level_offset(l0) * P1 + e);
+  for (int e = threadIdx.x; e < nb0 * P1; e += blockDim.x) {
+    const int b = e / P1, m = e - b * P1;
+    Ms[m2m_slot<R>(b, m, P1)] = ldcg_c(M + (size_t)level_offset(l0) * P1 + e);
+  }
   __syncthreads();
   m2m_levels_smem<R>(Ms, nb0, l0, 1, 0, P1, T, M);
   if (threadIdx.x == 0) ctr[blockIdx.y] = 0;  // ready for the next launch
@@ -400,6 +449,7 @@ struct DownEval {
   const float2 *loc;
   const float4 *near;
   const int64_t *perm;
+  const uint64_t *keys;  // sorted Morton keys: the leaf of each point
   const DevGeom *dg;
   double *pot, *grad;
 };
@@ -429,10 +479,13 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
-  // two ping-pong regions of nbuf boxes x (A, B): the leaf level stays in
-  // shared memory with EVAL, else goes straight to global memory
+  // two ping-pong regions of nbuf boxes x (A, B), BS = 2 P1 + 1 coefficients
+  // a box (an odd number of 8-byte words for single precision, so that the
+  // lanes of a warp, one box each, read different banks): the leaf level
+  // stays in shared memory with EVAL, else goes straight to global memory
   const int nbuf = EVAL ? nl : (1 << (2 * (k > 0 ? k - 1 : 0)));
-  cpx<R> *cur = T + 4 * P1 * P1, *nxt = cur + (size_t)2 * nbuf * P1;
+  const int BS = 2 * P1 + 1;
+  cpx<R> *cur = T + 4 * P1 * P1, *nxt = cur + (size_t)nbuf * BS;
   for (int e = threadIdx.x; e < 4 * P1 * P1; e += blockDim.x) T[e] = Tl2l[e];
   // ancestor chain: levels 1 .. l0 (level 0 has no expansion; level 1 has
   // the mirror M2L's result only)
@@ -490,9 +543,48 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
   for (int l = l0 + 1; l <= H; ++l) {
     const int nc = np * 4;
     const int64_t first = root << (2 * (l - l0));
+    if (EVAL || l < H) {
+      // the level's own (M2L) coefficients into nxt, read coalesced, then
+      // the L2L with lanes over boxes: the lanes of a warp share the output
+      // order m (and the length of the sum over n) once a level has 32 boxes
+      for (int e = threadIdx.x; e < nc * P1; e += blockDim.x) {
+        const int b = e / P1, m = e % P1;
+        const size_t ce = (size_t)(level_offset(l) + first) * P1 + e;
+        cpx<R> sa = A[ce], sb = B[ce];
+        if (Amir) {
+          const uint64_t bx = (uint64_t)(first + b);
+          const int iyb = box_iy(bx);
+          if (iyb <= 1) {
+            const int64_t ms = mirror_slot(l, box_ix(bx), iyb) * P1 + m;
+            sa = sa + Amir[ms];
+            sb = sb + Bmir[ms];
+          }
+        }
+        nxt[(size_t)b * BS + m] = sa;
+        nxt[(size_t)b * BS + P1 + m] = sb;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nc * P1; e += blockDim.x) {
+        const int m = e / nc, b = e - m * nc, c = b & 3;
+        const cpx<R> *pa = cur + (size_t)(b >> 2) * BS;
+        const cpx<R> *pb = pa + P1;
+        const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
+        cpx<R> sa = nxt[(size_t)b * BS + m], sb = nxt[(size_t)b * BS + P1 + m];
+        for (int n = m; n < P1; ++n) {
+          cfma(sa, Tc[n], pa[n]);
+          cfma(sb, conj(Tc[n]), pb[n]);
+        }
+        nxt[(size_t)b * BS + m] = sa;
+        nxt[(size_t)b * BS + P1 + m] = sb;
+      }
+      __syncthreads();
+      cpx<R> *t = cur; cur = nxt; nxt = t;
+      np = nc;
+      continue;
+    }
     for (int e = threadIdx.x; e < nc * P1; e += blockDim.x) {
       const int b = e / P1, m = e % P1, c = b & 3;
-      const cpx<R> *pa = cur + (size_t)(b >> 2) * 2 * P1;
+      const cpx<R> *pa = cur + (size_t)(b >> 2) * BS;
       const cpx<R> *pb = pa + P1;
       const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
       const size_t ce = (size_t)(level_offset(l) + first + b) * P1 + m;
@@ -510,13 +602,8 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
         cfma(sa, Tc[n], pa[n]);
         cfma(sb, conj(Tc[n]), pb[n]);
       }
-      if (l == H && !EVAL) {
-        A[ce] = sa;
-        B[ce] = sb;
-      } else {
-        nxt[(size_t)b * 2 * P1 + m] = sa;
-        nxt[(size_t)b * 2 * P1 + P1 + m] = sb;
-      }
+      A[ce] = sa;  // the leaf level without EVAL
+      B[ce] = sb;
     }
     __syncthreads();
     cpx<R> *t = cur; cur = nxt; nxt = t;
@@ -525,20 +612,14 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
   if constexpr (EVAL) {
     // L2P at the subtree's points (contiguous in tree order), plus the near
     // sums; cur holds the leaf expansions (when k = 0, the root's)
-    int *lsb = reinterpret_cast<int *>(T + 4 * P1 * P1 + (size_t)4 * nbuf * P1);  // [nl + 1]
-    for (int e = threadIdx.x; e <= nl; e += blockDim.x) lsb[e] = leaf_start[lf0 + e];
-    __syncthreads();
     const float invd = ev.dg->invd[H];
     const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
     const float i2pi = (float)(1.0 / HP_TWO_PI);
-    const int i1 = lsb[nl];
-    for (int i = lsb[0] + threadIdx.x; i < i1; i += blockDim.x) {
-      int lo = 0, hi = nl;  // lsb[lo] <= i < lsb[hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (lsb[mid] <= i) lo = mid; else hi = mid;
-      }
-      const cf *Al = reinterpret_cast<const cf *>(cur) + (size_t)lo * 2 * P1;
+    const int i0 = leaf_start[lf0], i1 = leaf_start[lf0 + nl];
+    const int ksh = 60 - 2 * H;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int lo = (int)((int64_t)(ev.keys[i] >> ksh) - lf0);  // the point's leaf in the subtree
+      const cf *Al = reinterpret_cast<const cf *>(cur) + (size_t)lo * BS;
       const cf *Bl = Al + P1;
       const float2 me = ev.loc[i];
       const float4 nv = ev.near[i];
@@ -577,16 +658,16 @@ constexpr size_t kFusedSmem = 200 * 1024;
 
 template <typename R>
 size_t upward_smem(int p, int k) {
-  size_t P1 = p + 1, nb = 0;
-  for (int j = 0; j <= k; ++j) nb += size_t(1) << (2 * j);
-  return sizeof(cpx<R>) * (4 * P1 * P1 + nb * P1);
+  const int P1 = p + 1;
+  size_t ng = 0;  // parent groups of the levels (a single root box: one group)
+  for (int j = 0; j <= k; ++j) ng += (size_t(1) << (2 * j) >> 2) > 0 ? (size_t(1) << (2 * j)) >> 2 : 1;
+  return sizeof(cpx<R>) * (4 * (size_t)P1 * P1 + ng * m2m_group_stride<R>(P1));
 }
 template <typename R>
 size_t downward_smem(int p, int k, bool eval) {
   const size_t P1 = p + 1;
   const size_t nbuf = eval ? (size_t(1) << (2 * k)) : (size_t(1) << (2 * (k > 0 ? k - 1 : 0)));
-  return sizeof(cpx<R>) * (4 * P1 * P1 + 4 * nbuf * P1) +
-         (eval ? sizeof(int) * ((size_t(1) << (2 * k)) + 1) : 0);
+  return sizeof(cpx<R>) * (4 * P1 * P1 + 2 * nbuf * (2 * P1 + 1));
 }
 
 // --------------------------------------------------------------------------
@@ -685,7 +766,8 @@ bool launch_m2l_patch(int p, int H, int lmin, int lmax, const DevGeom *dg, const
                       cudaStream_t st, int nr, RhsStride rs, const int *leaf_start,
                       int skip_empty) {
   if constexpr (sizeof(R) == 8) {
-    return false;  // the patch form is the single-precision path only
+    return m2l_patch_launch_64(p, H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st, nr, rs,
+                               leaf_start, skip_empty);
   } else {
     if (p <= kPatchSplitP)
       return m2l_patch_launch_lo(p, H, lmin, lmax, dg, Tpad, logt, M, A, B, status, st, nr, rs,
@@ -1174,6 +1256,31 @@ __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src,
   }
 }
 
+// the same over a range holding the target itself: the pair with r^2 = 0
+// (the target, or a distinct point at the same position) contributes nothing
+// (the free part excludes j = i and coincident points), one loop instead of
+// two around the target's own index, so that the lanes of a warp -- whose
+// targets sit at different positions in the range -- run one trip count
+__device__ __forceinline__ void pair_loop_self(const float4 *__restrict__ src,
+                                               const float *__restrict__ srcq, int lo, int hi,
+                                               float sxh, float sxl, float syh, float syl,
+                                               float &lf, float &gx, float &gy) {
+#pragma unroll 4
+  for (int k = lo; k < hi; ++k) {
+    const float4 s = src[k];
+    const float dx = (sxh - s.x) + (sxl - s.z);
+    const float dy = (syh - s.y) + (syl - s.w);
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const bool ok = r2 > 0.f;
+    const float q = ok ? srcq[k] : 0.f;
+    const float rr = ok ? r2 : 1.f;
+    const float qi = q * fast_rcp(rr);
+    lf = fmaf(q, fast_lg2(rr), lf);
+    gx = fmaf(qi, dx, gx);
+    gy = fmaf(qi, dy, gy);
+  }
+}
+
 // the target (hi, lo) shifted by -c leaf sides, as hi + lo: |c d| >= |hi|
 // for c != 0, so the fast two-sum is exact (c = 0 leaves it unchanged)
 __device__ __forceinline__ void frame_shift(float hi, float lo, int c, float d, float dlo,
@@ -1285,8 +1392,7 @@ k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
         const int lo = pst[pi - 1];
         const int hi = act ? pst[pi + 2] : lo;
         if (r == 0) {
-          pair_loop(src, srcq, lo, act ? kself : lo, me.x, me.z, me.y, me.w, lf, gx, gy);
-          pair_loop(src, srcq, act ? kself + 1 : hi, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
+          pair_loop_self(src, srcq, lo, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
         } else {
           pair_loop(src, srcq, lo, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
         }
@@ -1304,11 +1410,11 @@ k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
           float sxh, sxl;
           frame_shift(me.x, ml.x, c, d, dlo, sxh, sxl);
           for (int k = s0; k < s1; ++k) {
-            if (k == i) continue;
             const float2 v = loc[k], w = loclo[k];
-            const float q = qs[k];
             const float dx = (sxh - v.x) + (sxl - w.x), dy = (syh - v.y) + (syl - w.y);
             const float r2 = fmaf(dx, dx, dy * dy);
+            if (!(r2 > 0.f)) continue;  // j = i, or a coincident point
+            const float q = qs[k];
             const float qi = q * fast_rcp(r2);
             lf = fmaf(q, fast_lg2(r2), lf);
             gx = fmaf(qi, dx, gx);
@@ -1925,6 +2031,10 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // that its short dependent kernels take SMs first and the near field fills
   // the rest
   cudaStream_t fs = st;
+  // split: the mirror M2L (and the bottom-row image/reaction pairs) on the
+  // table stream, into separate arrays that the downward pass adds
+  const bool mirror_apart =
+      split && pl->mir_A && pl->ev_up && pl->ev_mirror && pl->table_stream;
   if (split) {
     HP_CUDA(cudaEventRecord(pl->ev_fork, st));
     HP_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0));
@@ -1934,13 +2044,17 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         pl->loc32, pl->loclo, (const float *)qs, pl->leaf_start, H, dg, pl->near);
     pass_end(pl, st, PASS_EVAL, 1);
     // the bottom-row image/reaction sums need only the sources too: written
-    // now, added by the L2P kernel
-    pass_begin(pl, st, PASS_NEAR_MIRROR);
-    k_mirror32<<<dim3((unsigned)(1 << H), 1, kMirSplit), 32 * kEvWarps, 0, st>>>(
+    // now, added by the L2P kernel.  On the table stream (idle between the
+    // reaction tables and the mirror M2L, whose event the caller's stream
+    // joins before the L2P), off the near field's stream.
+    cudaStream_t ms = mirror_apart ? pl->table_stream : st;
+    if (ms != st) HP_CUDA(cudaStreamWaitEvent(ms, pl->ev_fork, 0));
+    pass_begin(pl, ms, PASS_NEAR_MIRROR);
+    k_mirror32<<<dim3((unsigned)(1 << H), 1, kMirSplit), 32 * kEvWarps, 0, ms>>>(
         pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, dg,
         kappa_log(pl->kre, pl->kim), pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f, pot,
         grad, rs, 1);
-    pass_end(pl, st, PASS_NEAR_MIRROR, 1);
+    pass_end(pl, ms, PASS_NEAR_MIRROR, 1);
   }
   pass_begin(pl, fs, PASS_P2M);
   // upward pass (Algorithm 1): S2M at the leaves, M2M up to level 1
@@ -1958,15 +2072,13 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     k_p2m<double><<<cdiv_u(pl->nleaf, kWarpsPerBlock), 32 * kWarpsPerBlock, shp2m, fs>>>(
         lp, (const double *)qs, pl->leaf_start, H, dg, p, (cd *)M);
   } else {
-    LeafPoints<float> lp{pl->loc32};
     if (mw)
       k_s2m_multi<kRhsChunk><<<dim3(cdiv_u((int64_t)pl->nleaf * P1, 256), mw->rp / kRhsChunk),
                                256, 0, fs>>>(pl->loc32, (const float *)mw->qsm, mw->rp, nr,
                                              pl->leaf_start, H, dg, p, (cf *)M, rs);
     else
-      k_s2m_thread<float><<<cdiv_u((int64_t)pl->nleaf * ((P1 + kS2mGroup - 1) / kS2mGroup), 256),
-                            256, 0, fs>>>(
-          lp, (const float *)qs, pl->leaf_start, H, dg, p, (cf *)M, rs);
+      k_s2m_tile<<<cdiv_u(pl->nleaf, kS2mLeaves), kS2mThreads, 0, fs>>>(
+          pl->loc32, (const float *)qs, pl->leaf_start, H, dg, p, (cf *)M, rs);
   }
   pass_end(pl, fs, PASS_P2M, 1);
   // split single precision: the M2L of the leaf level needs only the leaf
@@ -2012,7 +2124,6 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // reaction tables; it runs on the table stream (after the tables, in stream
   // order) concurrently with the free-space M2L, into its own small arrays,
   // which the downward pass adds
-  const bool mirror_apart = split && pl->mir_A && pl->ev_up && pl->ev_mirror;
   if (mirror_apart) {
     HP_CUDA(cudaEventRecord(pl->ev_up, fs));
     HP_CUDA(cudaStreamWaitEvent(pl->table_stream, pl->ev_up, 0));
@@ -2029,7 +2140,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // from level 1), then L2L from level 1 down to the leaves
   size_t shfree = sizeof(cpx<R>) * (m2 + (size_t)P1 * 33);
   bool patched = false, tc_m2l = false;
-  if (H >= 2 && sizeof(R) == 4) {
+  if (H >= 2) {
     pass_begin(pl, fs, PASS_M2L_FREE);
     if (mw && nr >= 16 && pl->m2l_mode == 1)
       tc_m2l = patched = launch_m2l_tc(p, H, dg, (const float *)pl->t_m2l_tc, logs, (const cf *)M, (cf *)A,
@@ -2075,7 +2186,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // after the near field has joined, the same kernel evaluates the leaf
   // expansions at the points (on the caller's stream); otherwise the leaf
   // expansions go to memory for the leaf kernels below.
-  const DownEval noev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const DownEval noev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (split) {
     HP_CUDA(cudaEventRecord(pl->ev_join, fs));
     HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
@@ -2083,7 +2194,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     int kd = H - 1 < 3 ? H - 1 : 3;  // subtrees of 64 leaves: 4^(H-3) blocks
     while (kd > 0 && downward_smem<R>(p, kd, true) > kFusedSmem) --kd;
     pass_begin(pl, st, PASS_L2L);
-    const DownEval ev{pl->loc32, pl->near, pl->perm, dg, pot, grad};
+    const DownEval ev{pl->loc32, pl->near, pl->perm, pl->keys, dg, pot, grad};
     k_downward<R, true><<<dim3((unsigned)(int64_t(1) << (2 * (H - kd))), 1), 256,
                           downward_smem<R>(p, kd, true), st>>>(
         H, kd, p, Tl2l, A, B, rs, pl->leaf_start, 1, ev,

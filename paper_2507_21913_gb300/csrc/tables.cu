@@ -174,7 +174,8 @@ __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd 
 // the second shifted by one (g_{j+1}), each padded to 2(p+1) entries, so that
 // the pairs (g_j, g_{j+1}) the kernel reads are 16-byte aligned for either
 // parity of j.  Computed in double and rounded.
-__global__ void k_m2l_pad(int p, cf *out) {
+template <typename R>
+__global__ void k_m2l_pad(int p, cpx<R> *out) {
   const int P1 = p + 1, GP = 2 * P1;
   const int slot = blockIdx.x;  // one block per far class
   int c = 0, k40 = -1;
@@ -199,7 +200,7 @@ __global__ void k_m2l_pad(int p, cf *out) {
         // single-precision Hankel M2L kernels
         g = ldexp(f, -kHankelLog2R * j) * g;
       }
-      out[(size_t)slot * 2 * GP + e] = to<float>(g);
+      out[(size_t)slot * 2 * GP + e] = to<R>(g);
     }
   }
 }
@@ -264,8 +265,11 @@ hpfmm_status tables_static(hpfmm_plan *pl, cudaStream_t st) {
                                                {pl->t_m2l, 49 * m2}, {pl->t_rlog, 21 * m2}};
     for (auto &e : t)
       k_to_float<<<64, 256, 0, st>>>((const cd *)e.base, (cf *)((cd *)e.base + e.n), e.n);
-    if (pl->t_m2l_pad) k_m2l_pad<<<40, 64, 0, st>>>(p, (cf *)pl->t_m2l_pad);
+    if (pl->t_m2l_pad) k_m2l_pad<float><<<40, 64, 0, st>>>(p, (cf *)pl->t_m2l_pad);
     if (pl->t_m2l_tc) k_m2l_tc_table<<<40, 256, 0, st>>>(p, fm2l, (float *)pl->t_m2l_tc);
+    HP_LAUNCH_CHECK();
+  } else if (pl->t_m2l_pad) {
+    k_m2l_pad<double><<<40, 64, 0, st>>>(p, (cd *)pl->t_m2l_pad);
     HP_LAUNCH_CHECK();
   }
   return HPFMM_OK;

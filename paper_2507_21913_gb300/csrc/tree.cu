@@ -486,15 +486,21 @@ leaf_sort(const int *__restrict__ start, const int *__restrict__ big, const int 
 constexpr int kTinyBucket = 16;
 constexpr int kScanChunk = 4096;  // buckets per block of the scan (1024 threads x 4)
 constexpr int kBboxThreads = 256;
-constexpr int kBboxPer = 4;  // points per thread of k_tb_bbox
+constexpr int kBboxPer = 8;  // points per thread and grid-stride step of k_tb_bbox
 
 // a point in its bucket: one 32-byte record (a single full-sector store by
 // the scatter, contiguous reads by the sort)
 struct alignas(32) BRec {
   uint64_t key;
+  int v, pad;  // caller index
   double x, y;
-  int v, pad;
 };
+// key and caller index of a record: one 16-byte load
+__device__ __forceinline__ void rec_kv(const BRec *r, uint64_t &k, int &v) {
+  const uint4 u = *reinterpret_cast<const uint4 *>(r);
+  k = ((uint64_t)u.y << 32) | u.x;
+  v = (int)u.z;
+}
 
 struct TreeBuild {
   const double *x, *y;
@@ -846,8 +852,9 @@ k_tb_sort(TreeBuild a) {
   // rank by (key, index) among the bucket's points
   int r = 0;
   for (int i = b0; i < b0 + m; ++i) {
-    const uint64_t ki = a.rec[i].key;
-    const int vi = a.rec[i].v;
+    uint64_t ki;
+    int vi;
+    rec_kv(a.rec + i, ki, vi);
     r += (ki < kq || (ki == kq && vi < vq)) ? 1 : 0;
   }
   const int k = b0 + r;
@@ -870,8 +877,9 @@ __device__ __forceinline__ void warp_sort_bucket(int b0, int m, int lane, const 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int i = e * 32 + lane;
-    k[e] = i < m ? rec[b0 + i].key : ~0ull;
-    v[e] = i < m ? rec[b0 + i].v : 0x7fffffff;
+    k[e] = ~0ull;
+    v[e] = 0x7fffffff;
+    if (i < m) rec_kv(rec + b0 + i, k[e], v[e]);
   }
   warp_bitonic<E>(k, v, lane);
 #pragma unroll
@@ -912,8 +920,7 @@ k_tb_big(TreeBuild a) {
       uint64_t *kw = a.kb + b0;
       int *vw = a.slot + b0;
       for (int e = threadIdx.x; e < m; e += blockDim.x) {
-        kw[e] = a.rec[b0 + e].key;
-        vw[e] = a.rec[b0 + e].v;
+        rec_kv(a.rec + b0 + e, kw[e], vw[e]);
       }
       __threadfence_block();
       __syncthreads();
@@ -928,8 +935,15 @@ k_tb_big(TreeBuild a) {
     int np2 = 1;
     while (np2 < m) np2 <<= 1;
     for (int e = threadIdx.x; e < np2; e += blockDim.x) {
-      sk[e] = e < m ? a.rec[b0 + e].key : ~0ull;
-      sv[e] = e < m ? a.rec[b0 + e].v : 0x7fffffff;
+      sk[e] = ~0ull;
+      sv[e] = 0x7fffffff;
+      if (e < m) {
+        uint64_t kk;
+        int vv;
+        rec_kv(a.rec + b0 + e, kk, vv);
+        sk[e] = kk;
+        sv[e] = vv;
+      }
     }
     __syncthreads();
     for (int kk = 2; kk <= np2; kk <<= 1) {
@@ -963,8 +977,9 @@ k_tb_big(TreeBuild a) {
 // Build (or rebuild) the tree of pl for the n points (x, y) (device pointers):
 // the six kernels above on `st`.  Leaves pl->keys, perm, leaf_start, the
 // tree-order coordinates (loc32 / loclo / yabs or xs / ys), pl->geo and
-// pl->dgeom filled on the device.  The host copies of the root square are set
-// by tree_finish.
+// pl->dgeom filled on the device.  The temporaries live in one workspace of
+// the plan, allocated by the first build.  The host copies of the root square
+// are set by tree_finish.
 namespace {
 struct TreeTmp {
   char *base = nullptr;
@@ -996,13 +1011,29 @@ static hpfmm_status tree_alloc(hpfmm_plan *pl, TreeTmp &t, cudaStream_t st) {
     set_last_error("tree build: %d leaf levels exceed the bucket scan", pl->Hsort);
     return HPFMM_EUNSUPPORTED;
   }
+  // one wave of bounding-square blocks: kBboxPer points a thread, at most
+  // four blocks per SM (a grid-stride loop covers the rest)
   int64_t nbb = (n + kBboxPer * kBboxThreads - 1) / (kBboxPer * kBboxThreads);
-  t.nbbox = (int)(nbb < 1 ? 1 : (nbb > 2048 ? 2048 : nbb));
+  const int64_t cap = 4 * (int64_t)(pl->sms > 0 ? pl->sms : 1);
+  t.nbbox = (int)(nbb < 1 ? 1 : (nbb > cap ? cap : nbb));
   size_t bytes = sizeof(Geom) * t.nbbox + sizeof(uint64_t) * n + sizeof(BRec) * n +
                  sizeof(int) * n +
                  sizeof(int) * (3 * nb + 3) + sizeof(double2) * (size_t)nleaf +
                  2 * sizeof(int) * (size_t)t.nchunk;
-  HP_CUDA(cudaMallocAsync((void **)&t.base, bytes + 14 * 256, st));
+  bytes += 14 * 256;
+  // the workspace stays with the plan: rebuilds of the same size reuse it
+  if (!pl->tree_tmp || pl->tree_tmp_bytes < (int64_t)bytes) {
+    if (pl->tree_tmp) {
+      HP_CUDA(cudaStreamSynchronize(st));
+      cudaFree(pl->tree_tmp);
+      pl->workspace_bytes -= pl->tree_tmp_bytes;
+      pl->tree_tmp = nullptr;
+      pl->tree_tmp_bytes = 0;
+    }
+    HP_TRY(plan_dalloc(pl, &pl->tree_tmp, bytes));
+    pl->tree_tmp_bytes = (int64_t)bytes;
+  }
+  t.base = (char *)pl->tree_tmp;
   char *c = t.base;
   auto carve = [&](size_t b) {
     char *r = c;
@@ -1066,13 +1097,22 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   pass_begin(pl, st, PASS_TREE);
   k_tb_bbox<<<t.nbbox, kBboxThreads, 0, st>>>(a);
   k_tb_keys<<<gp, 256, 0, st>>>(a);
+  // the root square and the level geometry are final since k_tb_bbox: the
+  // reaction tables and the host copy of the square (table stream) start
+  // now, concurrently with the rest of the build (after the keys, whose
+  // double-precision quantisation would share the FP64 pipe with the tables)
+  if (pl->ev_tree) {
+    cudaError_t e = cudaEventRecord(pl->ev_tree, st);
+    if (e != cudaSuccess) {
+      set_last_error("tree_build: %s", cudaGetErrorString(e));
+      return HPFMM_ECUDA;
+    }
+  }
   k_tb_scan<<<t.nchunk, 1024, 0, st>>>(a);
   k_tb_scatter<<<gs, 256, 0, st>>>(a);
   k_tb_sort<<<gp, 256, 0, st>>>(a);
   k_tb_big<<<608, 256, 0, st>>>(a);
   pass_end(pl, st, PASS_TREE, 6);
-  // released (stream-ordered) by tree_finish
-  pl->tree_tmp = t.base;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error("tree_build launch: %s", cudaGetErrorString(e));
@@ -1081,10 +1121,10 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   return HPFMM_OK;
 }
 
-// Stream-ordered release of the build temporaries, and (hgeo != nullptr,
-// the geometry has reached the host) the invalid-input check and the host
-// copies of the root square.
-hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st) {
+// With hgeo != nullptr (the geometry has reached the host): the invalid-input
+// check and the host copies of the root square.  The build's workspace stays
+// with the plan (freed with it).
+hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t) {
   hpfmm_status s = HPFMM_OK;
   if (hgeo) {
     if (hgeo[2] != 0.0) {
@@ -1097,8 +1137,6 @@ hpfmm_status tree_finish(hpfmm_plan *pl, const double *hgeo, cudaStream_t st) {
       pl->qscale = hgeo[3];
     }
   }
-  if (pl->tree_tmp) cudaFreeAsync(pl->tree_tmp, st);
-  pl->tree_tmp = nullptr;
   return s;
 }
 

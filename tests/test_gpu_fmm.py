@@ -220,3 +220,34 @@ def test_deep_tree_coarse_levels(prec, p, tol):
     u, g, plan = run(x, y, q, 1.0, p, 32, prec=prec, levels=10)
     assert rel(u[idx], u_ref) < tol
     assert rel(g[idx], g_ref) < 20 * tol
+
+
+def test_pass_timeline_follows_the_dependencies():
+    """hpfmm_read_timeline: the pass intervals of one single-precision
+    rebuild + evaluation, from the earliest begin, respect the schedule's
+    dependencies: P2M after the tree, the downward pass (l2l) after every
+    free and mirror M2L interval."""
+    n = 200_000
+    x, y, q = workloads.uniform(n, seed=3)
+    t = lambda a: torch.tensor(a, device=DEV)
+    xd, yd, qd = t(x), t(y), t(q)
+    plan = hp.hpfmm_create(xd, yd, kappa=1.0, p=12, leaf_size=16, prec="fp32", levels=7,
+                           async_update=True)
+    hp.hpfmm_eval(plan, qd)
+    hp.hpfmm_sync(plan)
+    hp.hpfmm_set_timing(plan, True)
+    hp.hpfmm_update_points(plan, xd, yd)
+    hp.hpfmm_eval(plan, qd)
+    tl = hp.hpfmm_read_timeline(plan)
+    hp.hpfmm_set_timing(plan, False)
+    names = {p for p, _, _ in tl}
+    for p in ("tree", "tables", "gather", "p2m", "m2m", "m2l_free", "m2l_mirror", "l2l", "eval"):
+        assert p in names, p
+    assert min(b for _, b, _ in tl) == pytest.approx(0.0, abs=1e-9)
+    assert all(e >= b for _, b, e in tl)
+    end = lambda p: max(e for q_, _, e in tl if q_ == p)
+    begin = lambda p: min(b for q_, b, _ in tl if q_ == p)
+    eps = 1e-3  # ms
+    assert begin("p2m") >= end("tree") - eps
+    assert begin("l2l") >= max(end("m2l_free"), end("m2l_mirror")) - eps
+    assert hp.hpfmm_read_timeline(plan) == []  # consumed
