@@ -39,9 +39,11 @@ UNIT = "interactions/s"
 # The timed configuration of the headline line.  tests/test_gpu_headline.py
 # checks the accuracy gate (relative L2 error <= 1e-6 of the potential and of
 # the gradient against the oracle, 256 sampled targets) at exactly these
-# settings.  p = 14: at p = 12 the truncation error of the gradient alone is
-# 8.6e-7 (FP64 run), too close to the gate.
-HEADLINE = dict(n=1_000_000, kappa=1.0, p=14, levels=8, prec="fp32", async_update=True)
+# settings.  p = 13, the smallest order that meets the gate with margin: at
+# p = 12 the truncation error of the gradient alone is 8.6e-7 (FP64 run) and
+# the single-precision total 9.3e-7; at p = 13 the measured errors are 6.2e-7
+# (potential) and 5.6e-7 (gradient).
+HEADLINE = dict(n=1_000_000, kappa=1.0, p=13, levels=8, prec="fp32", async_update=True)
 GATE = 1e-6
 
 
@@ -650,7 +652,7 @@ def run_ours(args):
     npairs, mpairs = leaf_pairs(keys, info["levels"])
     launches_per_step = {k: v / args.steps for k, v in launches.items()}
     pass_ms_step = {k: v / args.steps for k, v in pms.items()}
-    roof = roofline(pms, launches, args, npairs, info["levels"], alu, hbm_gbs)
+    roof = roofline(pass_ms_step, launches_per_step, args, npairs, info["levels"], alu, hbm_gbs)
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

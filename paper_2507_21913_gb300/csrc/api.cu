@@ -181,10 +181,15 @@ static void free_plan(hpfmm_plan *pl) {
   }
   if (pl->ev_s2m) cudaEventDestroy(pl->ev_s2m);
   if (pl->ev_up) cudaEventDestroy(pl->ev_up);
-  if (pl->ev_mirror) cudaEventDestroy(pl->ev_mirror);
   if (pl->ev_m2lh) cudaEventDestroy(pl->ev_m2lh);
   if (pl->ev_tree) cudaEventDestroy(pl->ev_tree);
   if (pl->ev_geo) cudaEventDestroy(pl->ev_geo);
+  if (pl->copy_stream) {
+    cudaStreamSynchronize(pl->copy_stream);
+    cudaStreamDestroy(pl->copy_stream);
+  }
+  for (cudaEvent_t ev : {pl->ev_qcopy, pl->ev_qfree, pl->ev_xcopy, pl->ev_xyfree, pl->ev_done})
+    if (ev) cudaEventDestroy(ev);
   if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_join) cudaEventDestroy(pl->ev_join);
@@ -203,7 +208,7 @@ static void free_plan(hpfmm_plan *pl) {
                   pl->ab_key, pl->ab_lo, pl->ab_hi, pl->ab_parent, pl->ab_lvl, pl->ab_child,
                   pl->ab_cut, pl->ab_off, pl->ab_idx, pl->ab_lev, pl->ab_btot, pl->ab_lrank,
                   pl->ab_leaf, pl->near, pl->loclo, pl->dgeom, pl->tree_ctr, pl->ctr, pl->mir_A, pl->mir_B,
-                  pl->tree_tmp};
+                  pl->tree_tmp, pl->in_xy};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete pl;
@@ -240,20 +245,26 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
                             bool wait) {
   const int64_t n = pl->n;
   const double *dx = x, *dy = y;
-  double *tmp = nullptr;
   cudaError_t e = cudaSuccess;
-  if (!is_device_pointer(x) || !is_device_pointer(y)) {
-    e = cudaMallocAsync((void **)&tmp, 2 * sizeof(double) * n, st);
+  // host coordinates: staged in a buffer of the plan, x on the copy stream
+  // and y on the caller's, concurrently
+  const bool staged = !is_device_pointer(x) || !is_device_pointer(y);
+  cudaStream_t cs = pl->copy_stream ? pl->copy_stream : st;
+  if (staged) {
+    if (!pl->in_xy) HP_TRY(plan_dalloc(pl, (void **)&pl->in_xy, 2 * sizeof(double) * n));
+    if (cs != st) e = cudaStreamWaitEvent(cs, pl->ev_xyfree, 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tmp, x, sizeof(double) * n, cudaMemcpyDefault, st);
+      e = cudaMemcpyAsync(pl->in_xy, x, sizeof(double) * n, cudaMemcpyDefault, cs);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tmp + n, y, sizeof(double) * n, cudaMemcpyDefault, st);
+      e = cudaMemcpyAsync(pl->in_xy + n, y, sizeof(double) * n, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && cs != st) e = cudaEventRecord(pl->ev_xcopy, cs);
+    if (e == cudaSuccess && cs != st) e = cudaStreamWaitEvent(st, pl->ev_xcopy, 0);
     if (e != cudaSuccess) {
       set_last_error("staging the coordinates: %s", cudaGetErrorString(e));
       return HPFMM_ECUDA;
     }
-    dx = tmp;
-    dy = tmp + n;
+    dx = pl->in_xy;
+    dy = pl->in_xy + n;
   }
   hpfmm_status s = tree_build(pl, dx, dy, st);
   if (s == HPFMM_OK) {
@@ -290,7 +301,8 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   // the adaptive tree over the sorted points (it reads the coordinates for
   // its leaf frames, so before the staging buffer goes)
   if (s == HPFMM_OK && pl->adaptive) s = adaptive_build(pl, dx, dy, st);
-  if (tmp) cudaFreeAsync(tmp, st);
+  // the next staging copy waits for this build's reads of the coordinates
+  if (staged && cs != st) cudaEventRecord(pl->ev_xyfree, st);
   if (s != HPFMM_OK || !sync) return s;
   double kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
   if (kabs * sqrt(5.0) * pl->side > 60.0) {
@@ -483,24 +495,26 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   if (s == HPFMM_OK) s = adaptive_prepare();
   if (s != HPFMM_OK) { free_plan(pl); return s; }
   {
-    // the plan's streams -- side (far-field chain of a split evaluation),
-    // m2l (its leaf-level M2L), table (reaction tables of a rebuild, the
-    // bottom-row image/reaction pairs and the mirror M2L) -- take the
-    // greatest priority: their short dependent kernels then take SMs before
-    // the blocks of the near field on the caller's stream, which fills the
-    // rest and ends the chain
+    // the far-field streams of a split evaluation -- side (S2M, M2M, coarse
+    // M2L) and m2l (leaf-level M2L, bottom-row image/reaction pairs, mirror
+    // M2L) -- take the greatest priority: their short dependent kernels then
+    // take SMs before the blocks of the near field on the caller's stream,
+    // which fills the rest.  The table stream (reaction tables of a rebuild,
+    // overlapping the tree build) keeps the default priority, so that the
+    // tree's kernels keep their SMs.
     int prio_lo = 0, prio_hi = 0;
     cudaError_t ce = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->side_stream, cudaStreamNonBlocking, prio_hi);
-    if (ce == cudaSuccess)
-      ce = cudaStreamCreateWithPriority(&pl->table_stream, cudaStreamNonBlocking, prio_hi);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->table_stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->m2l_stream, cudaStreamNonBlocking, prio_hi);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&pl->ev_qcopy, &pl->ev_qfree, &pl->ev_xcopy, &pl->ev_xyfree, &pl->ev_done})
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_s2m, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_m2lh, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_up, cudaEventDisableTiming);
-    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_mirror, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tree, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_geo, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);
@@ -581,8 +595,17 @@ extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, do
   const double *dq = q;
   double *dpot = pot, *dgrad = grad;
   if (!qd || !pd || !gd) HP_TRY(ensure_stage(pl, nrhs));
+  // host charges: copied on the copy stream, so that the copy overlaps the
+  // tree build still running on the caller's stream; the caller's stream
+  // waits for it before the passes
+  cudaStream_t cs = pl->copy_stream ? pl->copy_stream : st;
   if (!qd) {
-    HP_CUDA(cudaMemcpyAsync(pl->in_q, q, sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
+    if (cs != st) HP_CUDA(cudaStreamWaitEvent(cs, pl->ev_qfree, 0));
+    HP_CUDA(cudaMemcpyAsync(pl->in_q, q, sizeof(double) * n * nrhs, cudaMemcpyDefault, cs));
+    if (cs != st) {
+      HP_CUDA(cudaEventRecord(pl->ev_qcopy, cs));
+      HP_CUDA(cudaStreamWaitEvent(st, pl->ev_qcopy, 0));
+    }
     dq = pl->in_q;
   }
   if (!pd) dpot = (double *)pl->out_pot;
@@ -603,11 +626,22 @@ extern "C" hpfmm_status hpfmm_eval(hpfmm_plan *pl, const double *q, int nrhs, do
                       dgrad ? dgrad + (size_t)4 * r * n : nullptr, st));
     }
   }
+  // the next call's charge copy may start once this call's passes are done
+  if (!qd && cs != st) HP_CUDA(cudaEventRecord(pl->ev_qfree, st));
+  // host outputs: potential on the caller's stream, gradient on the copy
+  // stream, concurrently
+  cudaStream_t gs = st;
+  if (!gd && cs != st) {
+    HP_CUDA(cudaEventRecord(pl->ev_done, st));
+    HP_CUDA(cudaStreamWaitEvent(cs, pl->ev_done, 0));
+    gs = cs;
+  }
   if (!pd)
     HP_CUDA(cudaMemcpyAsync(pot, dpot, 2 * sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
   if (!gd)
-    HP_CUDA(cudaMemcpyAsync(grad, dgrad, 4 * sizeof(double) * n * nrhs, cudaMemcpyDefault, st));
+    HP_CUDA(cudaMemcpyAsync(grad, dgrad, 4 * sizeof(double) * n * nrhs, cudaMemcpyDefault, gs));
   if (!pd || !gd) HP_CUDA(cudaStreamSynchronize(st));
+  if (gs != st) HP_CUDA(cudaStreamSynchronize(gs));
   return HPFMM_OK;
 }
 

@@ -319,27 +319,35 @@ struct hpfmm_plan {
   int *tflag = nullptr;
   int64_t *tlist = nullptr;
   int64_t tlist_cap = 0;
-  // the reaction tables of a rebuild run on a side stream, overlapping the
-  // tree build: forked once the bounding square is known, joined before the
-  // rebuild's synchronisation
+  // the far-field chain of a split single-precision evaluation
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_geo = nullptr, ev_tables = nullptr;
   // the geometry copy to the host and the reaction tables of a rebuild run on
-  // table_stream after the tree build (ev_tree); the tables are joined into
-  // the evaluation's stream right before the mirror M2L that reads them
+  // table_stream once the root square is known (ev_tree, recorded inside the
+  // tree build); the tables are joined into the evaluation's stream before
+  // the mirror M2L that reads them
   cudaStream_t table_stream = nullptr;
   cudaEvent_t ev_tree = nullptr;
+  // host-buffer calls: their copies on copy_stream, overlapping the tree
+  // build (the charges) or each other (x and y; potential and gradient).
+  // ev_qfree / ev_xyfree: the previous call's readers of the staging buffers
+  // are done; ev_qcopy / ev_xcopy: the copies are done; ev_done: the
+  // evaluation's outputs are written
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_qcopy = nullptr, ev_qfree = nullptr, ev_xcopy = nullptr, ev_xyfree = nullptr,
+              ev_done = nullptr;
+  double *in_xy = nullptr;  // staged coordinates of a host-buffer rebuild (x, then y)
   bool tables_pending = false;
   // fork / join of the near field on the side stream (single precision)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // the leaf level's M2L on its own stream, after the S2M (ev_s2m), joined
-  // before the mirror M2L (ev_m2lh)
+  // into the far-field chain (ev_m2lh)
   cudaStream_t m2l_stream = nullptr;
   cudaEvent_t ev_s2m = nullptr, ev_m2lh = nullptr;
-  // the mirror M2L on the table stream after the upward pass (ev_up), into
-  // mir_A / mir_B (rows 0 and 1 of every level), joined before the downward
-  // pass (ev_mirror); single-precision uniform plans
-  cudaEvent_t ev_up = nullptr, ev_mirror = nullptr;
+  // the mirror M2L on the m2l stream after the upward pass (ev_up), into
+  // mir_A / mir_B (rows 0 and 1 of every level), joined with the leaf-level
+  // M2L (ev_m2lh) before the downward pass; single-precision uniform plans
+  cudaEvent_t ev_up = nullptr;
   void *mir_A = nullptr, *mir_B = nullptr;
   float4 *near = nullptr;  // near-field sums per point (sorted order)
   double *hgeo = nullptr;  // pinned host copy of geo, written by the tree build

@@ -37,6 +37,7 @@
 #include "near32.cuh"
 #include "tc.cuh"
 #include "m2l_patch.cuh"
+#include "fsplit.cuh"
 
 namespace {
 
@@ -62,7 +63,12 @@ __global__ void k_gather_q(const double *__restrict__ q, const int64_t *__restri
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int r = blockIdx.y;
-  const R v = (R)q[(size_t)r * n + perm[k]];
+  const double qd = q[(size_t)r * n + perm[k]];
+  R v;
+  if constexpr (sizeof(R) == 4)
+    v = fs_round(qd);  // the rounding by integer operations (no FP64 conversion)
+  else
+    v = qd;
   qs[(size_t)r * n + k] = v;
   if (qsm) qsm[(size_t)k * rp + r] = v;
 }
@@ -454,6 +460,22 @@ struct DownEval {
   double *pot, *grad;
 };
 
+// the per-point inputs of the fused L2P
+struct PointIn {
+  uint64_t key;
+  float2 loc;
+  float4 near;
+  int64_t perm;
+};
+__device__ __forceinline__ PointIn load_point(const DownEval &ev, int i) {
+  PointIn r;
+  r.key = __ldg(ev.keys + i);
+  r.loc = __ldg(ev.loc + i);
+  r.near = __ldcs(ev.near + i);  // read once
+  r.perm = __ldg(ev.perm + i);
+  return r;
+}
+
 // slot of box (ix, iy <= 1) of level l >= 1 in the mirror M2L's separate
 // outputs: the launch's block index, levels in order, rows 0 and 1 of 2^l
 // boxes each
@@ -473,8 +495,12 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
   const int l0 = H - k;
   const int64_t lf0 = root << (2 * k);
   const int nl = 1 << (2 * k);
-  if (skip_empty) {  // a subtree without points needs no leaf expansions
-    if (leaf_start[lf0 + nl] == leaf_start[lf0]) return;
+  const int i0 = leaf_start[lf0], i1 = leaf_start[lf0 + nl];
+  if (skip_empty && i1 == i0) return;  // a subtree without points needs no leaf expansions
+  // with EVAL: the first point's data, loaded now, used after the L2L levels
+  PointIn pf{};
+  if constexpr (EVAL) {
+    if (i0 + (int)threadIdx.x < i1) pf = load_point(ev, i0 + (int)threadIdx.x);
   }
   A += blockIdx.y * rs.m;
   B += blockIdx.y * rs.m;
@@ -615,14 +641,18 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
     const float invd = ev.dg->invd[H];
     const float c4 = (float)(0.69314718055994530942 / (4.0 * HP_PI));
     const float i2pi = (float)(1.0 / HP_TWO_PI);
-    const int i0 = leaf_start[lf0], i1 = leaf_start[lf0 + nl];
     const int ksh = 60 - 2 * H;
+    // the point data of iteration i + blockDim.x is loaded while iteration i
+    // computes (the first iteration's since the kernel's start)
+    PointIn nx = pf;
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const int lo = (int)((int64_t)(ev.keys[i] >> ksh) - lf0);  // the point's leaf in the subtree
+      const PointIn cu = nx;
+      if (i + (int)blockDim.x < i1) nx = load_point(ev, i + (int)blockDim.x);
+      const int lo = (int)((int64_t)(cu.key >> ksh) - lf0);  // the point's leaf in the subtree
       const cf *Al = reinterpret_cast<const cf *>(cur) + (size_t)lo * BS;
       const cf *Bl = Al + P1;
-      const float2 me = ev.loc[i];
-      const float4 nv = ev.near[i];
+      const float2 me = cu.loc;
+      const float4 nv = cu.near;
       const cf w = mk(me.x * invd, me.y * invd), wb = conj(w);
       cf va = Al[p], da = mk(0.f, 0.f), vb = Bl[p], db = mk(0.f, 0.f);
       for (int n = p - 1; n >= 0; --n) {
@@ -635,7 +665,7 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
       const float ui_ = va.y + vb.y;
       const cf gxo = invd * (da + db) + mk(-nv.y * i2pi, 0.f);
       const cf gyo = invd * (mul_i(da) - mul_i(db)) + mk(-nv.z * i2pi, 0.f);
-      const int64_t o = ev.perm[i];
+      const int64_t o = cu.perm;
       double2 pv = make_double2(f2d(ur_), f2d(ui_));
       double4_16a gv;
       gv.x = f2d(gxo.x); gv.y = f2d(gxo.y); gv.z = f2d(gyo.x); gv.w = f2d(gyo.y);
@@ -2031,10 +2061,12 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // that its short dependent kernels take SMs first and the near field fills
   // the rest
   cudaStream_t fs = st;
-  // split: the mirror M2L (and the bottom-row image/reaction pairs) on the
-  // table stream, into separate arrays that the downward pass adds
-  const bool mirror_apart =
-      split && pl->mir_A && pl->ev_up && pl->ev_mirror && pl->table_stream;
+  // split single precision: the leaf level's M2L, the bottom-row
+  // image/reaction pairs and the mirror M2L (into separate arrays that the
+  // downward pass adds) on the plan's high-priority m2l stream, joined into
+  // the far-field chain (ev_m2lh) before the downward pass
+  const bool leaf_m2l_apart = split && H >= 3 && pl->m2l_stream && pl->ev_s2m && pl->ev_m2lh;
+  const bool mirror_apart = leaf_m2l_apart && pl->mir_A && pl->ev_up;
   if (split) {
     HP_CUDA(cudaEventRecord(pl->ev_fork, st));
     HP_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0));
@@ -2044,10 +2076,9 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
         pl->loc32, pl->loclo, (const float *)qs, pl->leaf_start, H, dg, pl->near);
     pass_end(pl, st, PASS_EVAL, 1);
     // the bottom-row image/reaction sums need only the sources too: written
-    // now, added by the L2P kernel.  On the table stream (idle between the
-    // reaction tables and the mirror M2L, whose event the caller's stream
-    // joins before the L2P), off the near field's stream.
-    cudaStream_t ms = mirror_apart ? pl->table_stream : st;
+    // now, added by the L2P kernel.  On the m2l stream (idle until the S2M is
+    // done), off the near field's stream.
+    cudaStream_t ms = mirror_apart ? pl->m2l_stream : st;
     if (ms != st) HP_CUDA(cudaStreamWaitEvent(ms, pl->ev_fork, 0));
     pass_begin(pl, ms, PASS_NEAR_MIRROR);
     k_mirror32<<<dim3((unsigned)(1 << H), 1, kMirSplit), 32 * kEvWarps, 0, ms>>>(
@@ -2085,7 +2116,6 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   // moments, so it runs on its own stream concurrently with the upward pass
   // and the coarser levels' M2L (it holds about three quarters of the
   // translations)
-  const bool leaf_m2l_apart = split && H >= 3 && pl->m2l_stream && pl->ev_s2m && pl->ev_m2lh;
   bool leaf_m2l_done = false;
   if (leaf_m2l_apart) {
     HP_CUDA(cudaEventRecord(pl->ev_s2m, fs));
@@ -2095,7 +2125,7 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
                                         A, B, pl->status, pl->m2l_stream, 1, rs, pl->leaf_start,
                                         1);
     pass_end(pl, pl->m2l_stream, PASS_M2L_FREE, leaf_m2l_done ? 1 : 0);
-    HP_CUDA(cudaEventRecord(pl->ev_m2lh, pl->m2l_stream));
+    if (!mirror_apart) HP_CUDA(cudaEventRecord(pl->ev_m2lh, pl->m2l_stream));
   }
   pass_begin(pl, fs, PASS_M2M);
   // the subtree blocks; when every level above them is small, the last of
@@ -2121,20 +2151,20 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   }
   pass_end(pl, fs, PASS_M2M, nm2m);
   // split single precision: the mirror M2L needs only the moments and the
-  // reaction tables; it runs on the table stream (after the tables, in stream
-  // order) concurrently with the free-space M2L, into its own small arrays,
-  // which the downward pass adds
+  // reaction tables; it runs on the m2l stream after the leaf level's M2L,
+  // concurrently with the coarser levels' free-space M2L, into its own small
+  // arrays, which the downward pass adds
   if (mirror_apart) {
     HP_CUDA(cudaEventRecord(pl->ev_up, fs));
-    HP_CUDA(cudaStreamWaitEvent(pl->table_stream, pl->ev_up, 0));
-    pass_begin(pl, pl->table_stream, PASS_M2L_MIRROR);
+    HP_CUDA(cudaStreamWaitEvent(pl->m2l_stream, pl->ev_up, 0));
+    HP_TRY(plan_join_tables(pl, pl->m2l_stream));
+    pass_begin(pl, pl->m2l_stream, PASS_M2L_MIRROR);
     unsigned nb = (unsigned)(4 * ((1 << H) - 1));  // sum over l of 2 * 2^l boxes
     size_t sm = sizeof(cpx<R>) * (4 * 3 * P1 + 4 * P1);
-    k_m2l_mirror_all<R><<<dim3(nb, 1), 128, sm, pl->table_stream>>>(
+    k_m2l_mirror_all<R><<<dim3(nb, 1), 128, sm, pl->m2l_stream>>>(
         H, p, dg, Timg, logs + 49, Treact, M, A, B, rs, (cpx<R> *)pl->mir_A, (cpx<R> *)pl->mir_B);
-    pass_end(pl, pl->table_stream, PASS_M2L_MIRROR, 1);
-    HP_CUDA(cudaEventRecord(pl->ev_mirror, pl->table_stream));
-    pl->tables_pending = false;  // the caller's stream joins ev_mirror below
+    pass_end(pl, pl->m2l_stream, PASS_M2L_MIRROR, 1);
+    HP_CUDA(cudaEventRecord(pl->ev_m2lh, pl->m2l_stream));
   }
   // downward pass: M2L at every level (free V-list from level 2, mirror list
   // from level 1), then L2L from level 1 down to the leaves
@@ -2190,7 +2220,6 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (split) {
     HP_CUDA(cudaEventRecord(pl->ev_join, fs));
     HP_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
-    if (mirror_apart) HP_CUDA(cudaStreamWaitEvent(st, pl->ev_mirror, 0));
     int kd = H - 1 < 3 ? H - 1 : 3;  // subtrees of 64 leaves: 4^(H-3) blocks
     while (kd > 0 && downward_smem<R>(p, kd, true) > kFusedSmem) --kd;
     pass_begin(pl, st, PASS_L2L);

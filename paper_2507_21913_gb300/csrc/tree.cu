@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "fsplit.cuh"
 
 namespace {
 
@@ -529,39 +530,6 @@ struct TreeBuild {
   int *status;
 };
 
-// v as a pair of floats: hi = v rounded to single precision (to nearest,
-// ties to even) and lo = the rest (v - hi, exact in double) rounded; by
-// integer operations on the encodings, since the double-precision pipe and
-// its conversions are narrow on this GPU.  Exponents outside [-70, 100]
-// (zero, values a leaf frame cannot hold) take the plain conversions.
-__device__ __forceinline__ float2 split_to_floats(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if (e < -70 || e > 100) {
-    const float hi = (float)v;
-    return make_float2(hi, (float)(v - (double)hi));
-  }
-  const unsigned long long full = (b & 0xfffffffffffffull) | (1ull << 52);  // 53 bits
-  unsigned long long top = full >> 29;                                      // 24 bits
-  const unsigned rem = (unsigned)(full & 0x1fffffffull);                    // 29 bits
-  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (top & 1ull));
-  top += up ? 1ull : 0ull;
-  const int r = up ? (int)rem - (1 << 29) : (int)rem;  // v - hi in units of 2^(e-52)
-  int fe = e + 127;
-  if (top >> 24) {  // the rounding carried into the next binade
-    top >>= 1;
-    ++fe;
-  }
-  const unsigned sign = (unsigned)(b >> 63) << 31;
-  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)top & 0x7fffffu));
-  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);  // 2^(e-52), normal
-  const float lo = __int2float_rn(r) * scale;
-  return make_float2(hi, sign ? -lo : lo);
-}
-
-// v rounded to single precision by the same integer operations
-__device__ __forceinline__ float round_to_float(double v) { return split_to_floats(v).x; }
-
 // one point into tree order, its coordinates (a, b) given (the leaf centre
 // precomputed)
 __device__ __forceinline__ void place_point(const LeafGather &g, double2 c, int k, int j, double a,
@@ -572,10 +540,10 @@ __device__ __forceinline__ void place_point(const LeafGather &g, double2 c, int 
   }
   g.perm[k] = j;
   if (g.loc32) {
-    const float2 sx = split_to_floats(a - c.x), sy = split_to_floats(b - c.y);
-    g.loc32[k] = make_float2(sx.x, sy.x);
-    g.loclo[k] = make_float2(sx.y, sy.y);
-    g.yabs[k] = round_to_float(b);
+    const FsPair sx = fs_split(a - c.x), sy = fs_split(b - c.y);
+    g.loc32[k] = make_float2(sx.hi, sy.hi);
+    g.loclo[k] = make_float2(sx.lo, sy.lo);
+    g.yabs[k] = fs_round(b);
   }
 }
 
@@ -1097,10 +1065,14 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   pass_begin(pl, st, PASS_TREE);
   k_tb_bbox<<<t.nbbox, kBboxThreads, 0, st>>>(a);
   k_tb_keys<<<gp, 256, 0, st>>>(a);
-  // the root square and the level geometry are final since k_tb_bbox: the
-  // reaction tables and the host copy of the square (table stream) start
-  // now, concurrently with the rest of the build (after the keys, whose
-  // double-precision quantisation would share the FP64 pipe with the tables)
+  k_tb_scan<<<t.nchunk, 1024, 0, st>>>(a);
+  k_tb_scatter<<<gs, 256, 0, st>>>(a);
+  k_tb_sort<<<gp, 256, 0, st>>>(a);
+  k_tb_big<<<608, 256, 0, st>>>(a);
+  // the reaction tables and the host copy of the root square start on the
+  // table stream once the build is done: run during the build, their
+  // FP64-bound blocks slowed its short kernels by a third; after it they
+  // share the SMs with the near field, which leaves the FP64 pipe idle
   if (pl->ev_tree) {
     cudaError_t e = cudaEventRecord(pl->ev_tree, st);
     if (e != cudaSuccess) {
@@ -1108,10 +1080,6 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
       return HPFMM_ECUDA;
     }
   }
-  k_tb_scan<<<t.nchunk, 1024, 0, st>>>(a);
-  k_tb_scatter<<<gs, 256, 0, st>>>(a);
-  k_tb_sort<<<gp, 256, 0, st>>>(a);
-  k_tb_big<<<608, 256, 0, st>>>(a);
   pass_end(pl, st, PASS_TREE, 6);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
