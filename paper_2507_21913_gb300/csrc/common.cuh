@@ -216,6 +216,33 @@ __device__ __forceinline__ uint64_t quantise(double v, double L, double scale) {
   return f > 1073741823ull ? 1073741823ull : f;
 }
 
+// Programmatic dependent launch (chains of short dependent kernels on one
+// stream): a kernel launched by launch_dependent may be scheduled before its
+// predecessor on the stream has finished; it calls pdl_wait() before its
+// first access to memory the predecessor writes (the wait returns once the
+// predecessor has completed and its writes are visible), and each kernel of
+// the chain calls pdl_trigger() to let its successor be scheduled as its own
+// blocks finish.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // centre of leaf (ix, iy) of side d in the root square starting at x0, with
 // explicit roundings: the single-precision leaf frames of the sources and of
 // separate targets must use bit-identical centres

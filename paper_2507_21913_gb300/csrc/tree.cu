@@ -585,6 +585,7 @@ k_tb_bbox(TreeBuild a) {
   __shared__ BoxAcc ws[kBboxThreads / 32];
   __shared__ int s_last;
   __shared__ double sg[4];
+  pdl_trigger();
   const int64_t T = (int64_t)gridDim.x * kBboxThreads;
   const int64_t tid = (int64_t)blockIdx.x * kBboxThreads + threadIdx.x;
   // the bucket counters start at zero for k_tb_keys
@@ -675,6 +676,8 @@ k_tb_bbox(TreeBuild a) {
 
 __global__ void __launch_bounds__(256)
 k_tb_keys(TreeBuild a) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const double x0 = a.geo[0], L = a.geo[1], sc = a.geo[3];
@@ -687,6 +690,8 @@ k_tb_keys(TreeBuild a) {
 
 __global__ void __launch_bounds__(1024)
 k_tb_scan(TreeBuild a) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int ws[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
@@ -767,6 +772,8 @@ __device__ int chunk_offsets(const TreeBuild &a, int *off, int *ws, int *mx) {
 
 __global__ void __launch_bounds__(256)
 k_tb_scatter(TreeBuild a) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int off[kMaxChunks];
   __shared__ int ws[64];
   int maxbucket;
@@ -806,6 +813,8 @@ k_tb_scatter(TreeBuild a) {
 
 __global__ void __launch_bounds__(256)
 k_tb_sort(TreeBuild a) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // bucketed position
   if (q >= a.n) return;
   const BRec rq = a.rec[q];
@@ -862,6 +871,7 @@ __device__ __forceinline__ void warp_sort_bucket(int b0, int m, int lane, const 
 
 __global__ void __launch_bounds__(256)
 k_tb_big(TreeBuild a) {
+  pdl_wait();
   __shared__ uint64_t sk[kLeafSort];
   __shared__ int sv[kLeafSort];
   const int *maxb = (const int *)(a.geo + 4);
@@ -1064,11 +1074,18 @@ hpfmm_status tree_build(hpfmm_plan *pl, const double *x, const double *y, cudaSt
   const unsigned gs = (unsigned)((nitem + 255) / 256);
   pass_begin(pl, st, PASS_TREE);
   k_tb_bbox<<<t.nbbox, kBboxThreads, 0, st>>>(a);
-  k_tb_keys<<<gp, 256, 0, st>>>(a);
-  k_tb_scan<<<t.nchunk, 1024, 0, st>>>(a);
-  k_tb_scatter<<<gs, 256, 0, st>>>(a);
-  k_tb_sort<<<gp, 256, 0, st>>>(a);
-  k_tb_big<<<608, 256, 0, st>>>(a);
+  // the rest of the chain by programmatic dependent launches: each kernel is
+  // scheduled while its predecessor's last blocks run and waits for it
+  // (griddepcontrol) before reading its results
+  cudaError_t le = launch_dependent(k_tb_keys, dim3(gp), dim3(256), 0, st, a);
+  if (le == cudaSuccess) le = launch_dependent(k_tb_scan, dim3(t.nchunk), dim3(1024), 0, st, a);
+  if (le == cudaSuccess) le = launch_dependent(k_tb_scatter, dim3(gs), dim3(256), 0, st, a);
+  if (le == cudaSuccess) le = launch_dependent(k_tb_sort, dim3(gp), dim3(256), 0, st, a);
+  if (le == cudaSuccess) le = launch_dependent(k_tb_big, dim3(608), dim3(256), 0, st, a);
+  if (le != cudaSuccess) {
+    set_last_error("tree_build launch: %s", cudaGetErrorString(le));
+    return HPFMM_ECUDA;
+  }
   // the reaction tables and the host copy of the root square start on the
   // table stream once the build is done: run during the build, their
   // FP64-bound blocks slowed its short kernels by a third; after it they
