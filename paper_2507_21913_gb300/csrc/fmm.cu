@@ -60,6 +60,8 @@ __device__ __forceinline__ cpx<R> ldc(const cpx<R> *p) {
 template <typename R>
 __global__ void k_gather_q(const double *__restrict__ q, const int64_t *__restrict__ perm,
                            int64_t n, R *__restrict__ qs, R *__restrict__ qsm, int rp) {
+  pdl_wait();  // launched as a dependent of the tree build's last kernel
+  pdl_trigger();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int r = blockIdx.y;
@@ -183,6 +185,7 @@ k_s2m_tile(const float2 *__restrict__ loc, const float *__restrict__ qs,
   constexpr int G = kS2mGroup;
   __shared__ float2 sp[kS2mCap];
   __shared__ float sq[kS2mCap];
+  pdl_trigger();  // the upward pass may be scheduled behind it
   const int P1 = p + 1, NB = (P1 + G - 1) / G;
   qs += blockIdx.y * rs.q;
   M += blockIdx.y * rs.m;
@@ -380,6 +383,7 @@ k_upward(int H, int k, int p, const cpx<R> *__restrict__ Tm2m, cpx<R> *__restric
          RhsStride rs, int *__restrict__ ctr) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_last;
+  pdl_wait();  // launched as a dependent of the S2M
   const int P1 = p + 1;
   M += blockIdx.y * rs.m;
   cpx<R> *T = reinterpret_cast<cpx<R> *>(smem_raw);  // [4][P1][P1]
@@ -1268,21 +1272,53 @@ constexpr int kLsBytes = 80;       // tile leaf starts (kTl^2 + 1 ints), 16-byte
 // index.  Lanes of one warp may belong to two or three leaves: they run the
 // same loops with their own bounds.  Patches larger than the buffer read
 // from global memory, leaf by leaf in leaf frames.
+// Two single-precision values in one 64-bit register and the paired FP32
+// instructions of this architecture (add/sub/fma .f32x2: one issue slot for
+// two results, each rounded to nearest as the scalar instruction rounds it).
+// The near-field pair loops apply them to the (x, y) differences and to the
+// (x, y) field sums, the two halves of every pair's work that come in pairs.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2_pack(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2p v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
+  f2p d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_add(f2p a, f2p b) {
+  f2p d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// the free-space pairs of one target (tile-frame position mh + ml, as (x, y)
+// pairs) with the staged sources lo .. hi - 1: lf += q log2 r^2 and
+// g += q (dx, dy) / r^2, the differences formed as (hi - hi) + (lo - lo)
 __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src,
                                           const float *__restrict__ srcq, int lo, int hi,
-                                          float sxh, float sxl, float syh, float syl, float &lf,
-                                          float &gx, float &gy) {
+                                          f2p mh, f2p ml, float &lf, f2p &g) {
 #pragma unroll 4
   for (int k = lo; k < hi; ++k) {
     const float4 s = src[k];
     const float q = srcq[k];
-    const float dx = (sxh - s.x) + (sxl - s.z);
-    const float dy = (syh - s.y) + (syl - s.w);
+    const f2p d = f2_add(f2_sub(mh, f2_pack(s.x, s.y)), f2_sub(ml, f2_pack(s.z, s.w)));
+    float dx, dy;
+    f2_unpack(d, dx, dy);
     const float r2 = fmaf(dx, dx, dy * dy);
     const float qi = q * fast_rcp(r2);
     lf = fmaf(q, fast_lg2(r2), lf);
-    gx = fmaf(qi, dx, gx);
-    gy = fmaf(qi, dy, gy);
+    g = f2_fma(f2_pack(qi, qi), d, g);
   }
 }
 
@@ -1293,21 +1329,20 @@ __device__ __forceinline__ void pair_loop(const float4 *__restrict__ src,
 // targets sit at different positions in the range -- run one trip count
 __device__ __forceinline__ void pair_loop_self(const float4 *__restrict__ src,
                                                const float *__restrict__ srcq, int lo, int hi,
-                                               float sxh, float sxl, float syh, float syl,
-                                               float &lf, float &gx, float &gy) {
+                                               f2p mh, f2p ml, float &lf, f2p &g) {
 #pragma unroll 4
   for (int k = lo; k < hi; ++k) {
     const float4 s = src[k];
-    const float dx = (sxh - s.x) + (sxl - s.z);
-    const float dy = (syh - s.y) + (syl - s.w);
+    const f2p d = f2_add(f2_sub(mh, f2_pack(s.x, s.y)), f2_sub(ml, f2_pack(s.z, s.w)));
+    float dx, dy;
+    f2_unpack(d, dx, dy);
     const float r2 = fmaf(dx, dx, dy * dy);
     const bool ok = r2 > 0.f;
     const float q = ok ? srcq[k] : 0.f;
     const float rr = ok ? r2 : 1.f;
     const float qi = q * fast_rcp(rr);
     lf = fmaf(q, fast_lg2(rr), lf);
-    gx = fmaf(qi, dx, gx);
-    gy = fmaf(qi, dy, gy);
+    g = f2_fma(f2_pack(qi, qi), d, g);
   }
 }
 
@@ -1334,6 +1369,7 @@ __global__ void __launch_bounds__(kEvWarps * 32, 4)
 k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
          const float *__restrict__ qs, const int *__restrict__ leaf_start, int H,
          const DevGeom *__restrict__ dg, float4 *__restrict__ near) {
+  pdl_wait();  // launched as a dependent of the charge gather
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int *ls = reinterpret_cast<int *>(smem_raw);         // [kTl^2 + 1] tile leaf starts
   float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap] (hi, lo)
@@ -1416,17 +1452,20 @@ k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
       const int kself = pst[py * kTlP + px] + (i - ls[li]);
       float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
       if (act) me = src[kself];
+      const f2p mh = f2_pack(me.x, me.y), ml = f2_pack(me.z, me.w);
+      f2p g = f2_pack(0.f, 0.f);
 #pragma unroll 1
       for (int r = -1; r <= 1; ++r) {
         const int pi = (py + r) * kTlP + px;
         const int lo = pst[pi - 1];
         const int hi = act ? pst[pi + 2] : lo;
         if (r == 0) {
-          pair_loop_self(src, srcq, lo, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
+          pair_loop_self(src, srcq, lo, hi, mh, ml, lf, g);
         } else {
-          pair_loop(src, srcq, lo, hi, me.x, me.z, me.y, me.w, lf, gx, gy);
+          pair_loop(src, srcq, lo, hi, mh, ml, lf, g);
         }
       }
+      f2_unpack(g, gx, gy);
     } else if (act) {
       const float2 me = loc[i], ml = loclo[i];
       for (int r = -1; r <= 1; ++r) {
@@ -2045,8 +2084,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   const DevGeom *dg = pl->dgeom;
 
   pass_begin(pl, st, PASS_GATHER);
-  k_gather_q<R><<<dim3(cdiv_u(n, 256), nr), 256, 0, st>>>(
-      q, pl->perm, n, qs, mw ? (R *)mw->qsm : (R *)nullptr, mw ? mw->rp : 0);
+  HP_CUDA(launch_dependent(k_gather_q<R>, dim3(cdiv_u(n, 256), nr), dim3(256), 0, st, q, pl->perm,
+                           n, qs, mw ? (R *)mw->qsm : (R *)nullptr, mw ? mw->rp : 0));
   pass_end(pl, st, PASS_GATHER, 1);
   // single precision, one RHS, the sources as targets: the free-space near
   // field needs only the sorted points and charges, so it runs on the plan's
@@ -2072,8 +2111,9 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     HP_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0));
     fs = pl->side_stream;
     pass_begin(pl, st, PASS_EVAL);
-    k_near32<<<(unsigned)(tps * tps), 32 * kEvWarps, kTpSmem, st>>>(
-        pl->loc32, pl->loclo, (const float *)qs, pl->leaf_start, H, dg, pl->near);
+    HP_CUDA(launch_dependent(k_near32, dim3((unsigned)(tps * tps)), dim3(32 * kEvWarps), kTpSmem,
+                             st, pl->loc32, pl->loclo, (const float *)qs, pl->leaf_start, H, dg,
+                             pl->near));
     pass_end(pl, st, PASS_EVAL, 1);
     // the bottom-row image/reaction sums need only the sources too: written
     // now, added by the L2P kernel.  On the m2l stream (idle until the S2M is
@@ -2135,8 +2175,8 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   if (ksub > 0) {
     size_t sm = upward_smem<R>(p, ksub);
     unsigned nb = (unsigned)(int64_t(1) << (2 * l0));
-    k_upward<R><<<dim3(nb, nr), 256, sm, fs>>>(H, ksub, p, Tm2m, M, rs,
-                                               coarse_in_upward ? pl->ctr : nullptr);
+    HP_CUDA(launch_dependent(k_upward<R>, dim3(nb, nr), dim3(256), sm, fs, H, ksub, p, Tm2m, M, rs,
+                             coarse_in_upward ? pl->ctr : (int *)nullptr));
   }
   int nm2m = ksub > 0 ? 1 : 0;
   if (!coarse_in_upward) {

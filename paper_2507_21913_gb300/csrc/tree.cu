@@ -872,6 +872,7 @@ __device__ __forceinline__ void warp_sort_bucket(int b0, int m, int lane, const 
 __global__ void __launch_bounds__(256)
 k_tb_big(TreeBuild a) {
   pdl_wait();
+  pdl_trigger();  // the evaluation's charge gather may follow on the stream
   __shared__ uint64_t sk[kLeafSort];
   __shared__ int sv[kLeafSort];
   const int *maxb = (const int *)(a.geo + 4);
