@@ -216,6 +216,37 @@ __device__ __forceinline__ uint64_t quantise(double v, double L, double scale) {
   return f > 1073741823ull ? 1073741823ull : f;
 }
 
+// Two single-precision values in one 64-bit register and the paired FP32
+// instructions of this architecture (add/sub/fma .f32x2: one issue slot for
+// two results, each rounded to nearest as the scalar instruction rounds it).
+// The near-field pair loops apply them to the (x, y) differences and field
+// sums, the patch M2L to the real and imaginary halves of its complex
+// multiply-adds.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2_pack(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2p v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
+  f2p d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_add(f2p a, f2p b) {
+  f2p d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Programmatic dependent launch (chains of short dependent kernels on one
 // stream): a kernel launched by launch_dependent may be scheduled before its
 // predecessor on the stream has finished; it calls pdl_wait() before its

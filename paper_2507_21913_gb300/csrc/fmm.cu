@@ -204,9 +204,11 @@ k_s2m_tile(const float2 *__restrict__ loc, const float *__restrict__ qs,
   for (int it = threadIdx.x; it < (L1 - L0) * NB; it += blockDim.x) {
     const int leaf = L0 + it / NB, nb = it % NB, n0 = G * nb;
     const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-    cf acc[G], cmp[G];
+    // the compensated sums of the real and imaginary parts as paired FP32
+    // additions (the same roundings as the scalar form)
+    f2p acc[G], cmp[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g) acc[g] = cmp[g] = mk(0.f, 0.f);
+    for (int g = 0; g < G; ++g) acc[g] = cmp[g] = f2_pack(0.f, 0.f);
     for (int j = b0; j < b1; ++j) {
       const float2 v = staged ? sp[j - t0] : loc[j];
       const float qj = staged ? sq[j - t0] : qs[j];
@@ -218,9 +220,9 @@ k_s2m_tile(const float2 *__restrict__ loc, const float *__restrict__ qs,
       for (int i = 0; i < nb; ++i) wn = wn * wg;  // q w^n0
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const cf yv = wn - cmp[g];
-        const cf tv = acc[g] + yv;
-        cmp[g] = (tv - acc[g]) - yv;
+        const f2p yv = f2_sub(f2_pack(wn.x, wn.y), cmp[g]);
+        const f2p tv = f2_add(acc[g], yv);
+        cmp[g] = f2_sub(f2_sub(tv, acc[g]), yv);
         acc[g] = tv;
         wn = wn * w;
       }
@@ -228,7 +230,11 @@ k_s2m_tile(const float2 *__restrict__ loc, const float *__restrict__ qs,
     const size_t e0 = ((size_t)level_offset(H) + leaf) * P1;
 #pragma unroll
     for (int g = 0; g < G; ++g)
-      if (n0 + g < P1) M[e0 + n0 + g] = acc[g];
+      if (n0 + g < P1) {
+        float ax, ay;
+        f2_unpack(acc[g], ax, ay);
+        M[e0 + n0 + g] = mk(ax, ay);
+      }
   }
 }
 
@@ -1272,36 +1278,6 @@ constexpr int kLsBytes = 80;       // tile leaf starts (kTl^2 + 1 ints), 16-byte
 // index.  Lanes of one warp may belong to two or three leaves: they run the
 // same loops with their own bounds.  Patches larger than the buffer read
 // from global memory, leaf by leaf in leaf frames.
-// Two single-precision values in one 64-bit register and the paired FP32
-// instructions of this architecture (add/sub/fma .f32x2: one issue slot for
-// two results, each rounded to nearest as the scalar instruction rounds it).
-// The near-field pair loops apply them to the (x, y) differences and to the
-// (x, y) field sums, the two halves of every pair's work that come in pairs.
-typedef unsigned long long f2p;
-__device__ __forceinline__ f2p f2_pack(float a, float b) {
-  f2p r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(f2p v, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
-  f2p d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p f2_add(f2p a, f2p b) {
-  f2p d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
-  f2p d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
 // the free-space pairs of one target (tile-frame position mh + ml, as (x, y)
 // pairs) with the staged sources lo .. hi - 1: lf += q log2 r^2 and
 // g += q (dx, dy) / r^2, the differences formed as (hi - hi) + (lo - lo)
