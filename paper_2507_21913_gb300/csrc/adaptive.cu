@@ -31,6 +31,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fsplit.cuh"
 #include "near32.cuh"
 #include "special.cuh"
 
@@ -43,8 +44,8 @@ static_assert(8 * kAdaptiveMaxLevel <= 4 * 32, "ancestor-cell lookups exceed fou
 
 inline unsigned cdiv_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-struct AdGeom {  // per-level box side, its reciprocal and log
-  float d[16], invd[16];
+struct AdGeom {  // per-level box side (as float hi + lo), its reciprocal and log
+  float d[16], dlo[16], invd[16];
   double logd[16];
 };
 AdGeom ad_geom(double side) {
@@ -52,6 +53,7 @@ AdGeom ad_geom(double side) {
   for (int l = 0; l < 16; ++l) {
     const double d = ldexp(side, -l);
     g.d[l] = (float)d;
+    g.dlo[l] = (float)(d - (double)g.d[l]);
     g.invd[l] = (float)(1.0 / d);
     g.logd[l] = log(d);
   }
@@ -281,7 +283,8 @@ k_ad_frames(const double *__restrict__ x, const double *__restrict__ y,
             const int64_t *__restrict__ perm, const int *__restrict__ rank, int n, int leafcap,
             const int *__restrict__ leaf, const uint64_t *__restrict__ key,
             const int *__restrict__ lo, const int *__restrict__ hi, const int *__restrict__ lvl,
-            double x0, double side, float2 *__restrict__ loc, float *__restrict__ yabs) {
+            double x0, double side, float2 *__restrict__ loc, float2 *__restrict__ loclo,
+            float *__restrict__ yabs) {
   const int lane = threadIdx.x & 31;
   const int nl = min(rank[n], leafcap);
   for (int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); r < nl;
@@ -293,8 +296,11 @@ k_ad_frames(const double *__restrict__ x, const double *__restrict__ y,
     for (int i = max(lo[b], 0) + lane; i < e; i += 32) {
       const int64_t j = perm[i];
       const double a = x[j], v = y[j];
-      loc[i] = make_float2((float)(a - c.x), (float)(v - c.y));
-      yabs[i] = (float)v;
+      // the leaf-frame position as float hi + lo, by integer operations
+      const FsPair sx = fs_split(a - c.x), sy = fs_split(v - c.y);
+      loc[i] = make_float2(sx.hi, sy.hi);
+      loclo[i] = make_float2(sx.lo, sy.lo);
+      yabs[i] = fs_round(v);
     }
   }
 }
@@ -597,30 +603,54 @@ __device__ __forceinline__ float2 ad_offset(const AdGeom &g, int l, int cx, int 
   return make_float2((float)nx * h, (float)ny * h);
 }
 
+// the offset ad_offset() gives, as float hi + lo of its exact value n d_m / 2
+// (n the integer of ad_offset, d_m = d + dlo the level's side in two parts)
+__device__ __forceinline__ float4 ad_offset_hilo(const AdGeom &g, int l, int cx, int cy, int lt,
+                                                 int tx, int ty) {
+  const int m = l > lt ? l : lt;
+  const float nx = (float)((2 * cx + 1) * (1 << (m - l)) - (2 * tx + 1) * (1 << (m - lt)));
+  const float ny = (float)((2 * cy + 1) * (1 << (m - l)) - (2 * ty + 1) * (1 << (m - lt)));
+  const float h = 0.5f * g.d[m], hl = 0.5f * g.dlo[m];
+  const float oxh = nx * h, oyh = ny * h;
+  // the products' rounding errors (exact by FMA) plus the low part of the side
+  const float oxl = fmaf(nx, h, -oxh) + nx * hl, oyl = fmaf(ny, h, -oyh) + ny * hl;
+  return make_float4(oxh, oyh, oxl, oyl);
+}
+
+// (h, l) - (oh, ol) as hi + lo: the two-sum of h and -oh (exact for any
+// magnitudes), the low parts added
+__device__ __forceinline__ void ad_sub_hilo(float h, float l, float oh, float ol, float &sh,
+                                            float &sl) {
+  sh = h - oh;
+  const float bb = sh - h;
+  sl = ((h - (sh - bb)) + (-oh - bb)) + (l - ol);
+}
+
+// the free-space pairs of one target (its position in the source leaf's frame
+// as hi + lo pairs mh, ml) with the points lo .. hi - 1 of that leaf (frames
+// loc + loclo), the target's own index `self` skipped; the differences
+// (hi - hi) + (lo - lo) and the sums as paired FP32 instructions
 __device__ __forceinline__ void ad_free_range(const float2 *__restrict__ loc,
+                                              const float2 *__restrict__ loclo,
                                               const float *__restrict__ qs, int lo, int hi,
-                                              int self, float sx, float sy, float &lf, float &gx,
-                                              float &gy) {
+                                              int self, f2p mh, f2p ml, float &lf, f2p &g) {
   for (int k = lo; k < hi; ++k) {
     if (k == self) continue;
-    const float2 v = loc[k];
+    const float2 v = loc[k], w = loclo[k];
     const float q = qs[k];
-    const float dx = sx - v.x, dy = sy - v.y;
+    const f2p d = f2_add(f2_sub(mh, f2_pack(v.x, v.y)), f2_sub(ml, f2_pack(w.x, w.y)));
+    float dx, dy;
+    f2_unpack(d, dx, dy);
     const float r2 = fmaf(dx, dx, dy * dy);
     const float qi = q * fast_rcp(r2);
     lf = fmaf(q, fast_lg2(r2), lf);
-    gx = fmaf(qi, dx, gx);
-    gy = fmaf(qi, dy, gy);
+    g = f2_fma(f2_pack(qi, qi), d, g);
   }
 }
 
-// Leaf evaluation: L2P (Eq. truncatedLE) plus the near field of the leaf --
-// free part over the leaves of the 3 x 3 cells around it and the leaves next
-// to its ancestors, image and reaction parts over the same sets restricted
-// to row 0.  One warp per leaf, one target per lane; every lane runs the same
-// source loops.  Outputs in the caller's order.
 __global__ void __launch_bounds__(kAdWarps * 32)
-k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ qs,
+k_ad_eval(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
+          const float *__restrict__ qs,
           const int64_t *__restrict__ perm,
           const int *__restrict__ leaf, int nleaf, int nbox, const int *__restrict__ rank,
           const int *__restrict__ idx, const uint64_t *__restrict__ key,
@@ -665,6 +695,8 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ qs,
     const int i = tb + lane;
     const bool act = i < hi[D];
     const float2 me = act ? loc[i] : make_float2(0.f, 0.f);
+    const float2 mel = act ? loclo[i] : make_float2(0.f, 0.f);
+    f2p gsum = f2_pack(0.f, 0.f);
     NearAcc a;
     a.lf = a.gx = a.gy = a.li = a.gix = a.giy = 0.f;
     a.ur = a.grx = a.gry = mk(0.f, 0.f);
@@ -676,9 +708,14 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ qs,
       for (int rr = rank[lo[nb]]; rr < r1; ++rr) {
         const int C = leaf[rr];
         const uint64_t kC = key[C];
-        const float2 o = ad_offset(g, lvl[C], box_ix(kC), box_iy(kC), l, ix, iy);
-        if (act)
-          ad_free_range(loc, qs, lo[C], hi[C], i, me.x - o.x, me.y - o.y, a.lf, a.gx, a.gy);
+        const float4 o = ad_offset_hilo(g, lvl[C], box_ix(kC), box_iy(kC), l, ix, iy);
+        if (act) {
+          float sxh, sxl, syh, syl;
+          ad_sub_hilo(me.x, mel.x, o.x, o.z, sxh, sxl);
+          ad_sub_hilo(me.y, mel.y, o.y, o.w, syh, syl);
+          ad_free_range(loc, loclo, qs, lo[C], hi[C], i, f2_pack(sxh, syh), f2_pack(sxl, syl),
+                        a.lf, gsum);
+        }
       }
     }
     // coarser leaves next to an ancestor of D
@@ -690,13 +727,18 @@ k_ad_eval(const float2 *__restrict__ loc, const float *__restrict__ qs,
         const int j = rd * 32 + jl;
         const int la = l - 1 - j / 8, o = j % 8, o9 = o < 4 ? o : o + 1;
         const int cy = (iy >> (l - la)) + o9 / 3 - 1;
-        const float2 off = ad_offset(g, la, (ix >> (l - la)) + o9 % 3 - 1, cy, l, ix, iy);
-        if (act)
-          ad_free_range(loc, qs, lo[C], hi[C], -1, me.x - off.x, me.y - off.y, a.lf, a.gx,
-                        a.gy);
+        const float4 off = ad_offset_hilo(g, la, (ix >> (l - la)) + o9 % 3 - 1, cy, l, ix, iy);
+        if (act) {
+          float sxh, sxl, syh, syl;
+          ad_sub_hilo(me.x, mel.x, off.x, off.z, sxh, sxl);
+          ad_sub_hilo(me.y, mel.y, off.y, off.w, syh, syl);
+          ad_free_range(loc, loclo, qs, lo[C], hi[C], -1, f2_pack(sxh, syh), f2_pack(sxl, syl),
+                        a.lf, gsum);
+        }
       }
     }
     if (!act) continue;
+    f2_unpack(gsum, a.gx, a.gy);
     // far field: L2P with the leaf's expansions
     const cf *Al = A + (size_t)D * P1;
     const cf *Bl = B + (size_t)D * P1;
@@ -885,7 +927,7 @@ hpfmm_status adaptive_build(hpfmm_plan *pl, const double *x, const double *y, cu
   k_ad_frames<<<cdiv_u(n, 256 / 32) < 8192 ? cdiv_u(n, 256 / 32) : 8192, 256, 0, st>>>(
       x, y, pl->perm, pl->ab_lrank, n, leafcap, pl->ab_leaf, pl->ab_key, pl->ab_lo, pl->ab_hi,
       pl->ab_lvl,
-      pl->x0, pl->side, pl->loc32, pl->yabs);
+      pl->x0, pl->side, pl->loc32, pl->loclo, pl->yabs);
   launches += 6;
   pass_end(pl, st, PASS_TREE, launches);
   HP_LAUNCH_CHECK();
@@ -1010,7 +1052,7 @@ hpfmm_status adaptive_eval(hpfmm_plan *pl, const double *q, double *pot, double 
   pass_begin(pl, st, PASS_EVAL);
   const float tau = pl->prec == HPFMM_MIXED ? (float)pl->tau_fp64 : 0.f;
   k_ad_eval<<<cdiv_u((int64_t)nleaf * 32, kAdWarps * 32), kAdWarps * 32, 0, st>>>(
-      pl->loc32, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
+      pl->loc32, pl->loclo, qs, pl->perm, pl->ab_leaf, nleaf, nbox, pl->ab_lrank, pl->ab_idx,
       pl->ab_key, pl->ab_lev, pl->ab_lo, pl->ab_hi, pl->ab_lvl, pl->ab_child, g, p, A, B, pot,
       grad);
   pass_end(pl, st, PASS_EVAL, 1);

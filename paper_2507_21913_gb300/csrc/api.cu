@@ -458,7 +458,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
   ALLOC(pl->leaf_start, sizeof(int) * (pl->nleaf + 1));
   if (f32) ALLOC(pl->loc32, sizeof(float2) * n);
   if (f32) ALLOC(pl->yabs, sizeof(float) * n);
-  if (f32 && !pl->adaptive) ALLOC(pl->loclo, sizeof(float2) * n);
+  if (f32) ALLOC(pl->loclo, sizeof(float2) * n);
   if (f32 && !pl->adaptive) ALLOC(pl->near, sizeof(float4) * n);
   if (f32 && !pl->adaptive) {  // mirror M2L results: rows 0 and 1 of levels 1..H
     ALLOC(pl->mir_A, sizeof(cf) * 4 * (((size_t)1 << pl->H) - 1) * P1);

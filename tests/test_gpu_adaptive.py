@@ -87,7 +87,7 @@ def test_clustered_deep_tree_vs_oracle(leaf):
     _, leaves, depth = hp.hpfmm_get_adaptive_counts(plan, plan.info()["levels"])
     assert (leaves > 0).sum() >= 3  # leaves on several levels
     assert rel(u[idx], u_ref) < 5e-6
-    assert rel(g[idx], g_ref) < 5e-5
+    assert rel(g[idx], g_ref) < 1e-5
 
 
 def test_root_is_a_leaf():
@@ -142,12 +142,15 @@ def test_several_charge_vectors_and_adjoint():
 
 def test_clustered_4m_adaptive_mixed():
     """The clustered 4e6 workload (kappa = 1 + 0.5i, p = 20, mixed precision)
-    on the adaptive tree, at the 64 sampled points of the uniform-tree test."""
+    on the adaptive tree, at the 64 sampled points of the uniform-tree test.
+    The gradient bound holds because the near field between leaves of
+    different levels forms its differences exactly (hi + lo leaf frames and
+    offsets); with single-float offsets the error was 6.4e-6."""
     kappa = 1.0 + 0.5j
     x, y, q, idx, u_ref, g_ref = oracle_cache.clustered_sampled(4_000_000, 0, kappa)
     u, g, _ = run(x, y, q, kappa, 20, 32, prec="mixed")
     assert rel(u[idx], u_ref) < 5e-6
-    assert rel(g[idx], g_ref) < 2e-5
+    assert rel(g[idx], g_ref) < 3e-6
     m = y[idx] < 0.06
     assert rel(u[idx][m], u_ref[m]) < 5e-6
 
