@@ -218,7 +218,7 @@ def roofline_entries(passes_ms, launches, args, npairs, H, alu, hbm_gbs):
     pass's algorithmic work per step / its CUDA-event device time per step
     (equal to work per launch / average launch duration), against the peak of
     the pipe (or memory) that bounds it, measured on this device
-    (hpfmm_measure_alu_peaks; HBM from the driver's copy measurement)."""
+    (hpfmm_measure_alu_peaks; HBM from the copy bandwidth in MEASURED_PEAKS.json)."""
     n, P1 = args.n, args.p + 1
     out = {}
     for dom, names in PASS_KERNELS.items():

@@ -59,7 +59,7 @@ typedef enum {
   HPFMM_ENOMEM = 2,      /* device allocation failed */
   HPFMM_ECUDA = 3,       /* a CUDA runtime call failed */
   HPFMM_ETIMEOUT = 4,    /* a bounded device wait gave up */
-  HPFMM_EUNSUPPORTED = 5 /* valid but outside what this build implements */
+  HPFMM_EUNSUPPORTED = 5 /* valid but outside what the library implements */
 } hpfmm_status;
 
 typedef enum {

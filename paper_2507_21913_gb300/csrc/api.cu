@@ -301,7 +301,7 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   // the adaptive tree over the sorted points (it reads the coordinates for
   // its leaf frames, so before the staging buffer goes)
   if (s == HPFMM_OK && pl->adaptive) s = adaptive_build(pl, dx, dy, st);
-  // the next staging copy waits for this build's reads of the coordinates
+  // the next staging copy waits for this rebuild's reads of the coordinates
   if (staged && cs != st) cudaEventRecord(pl->ev_xyfree, st);
   if (s != HPFMM_OK || !sync) return s;
   double kabs = sqrt(pl->kre * pl->kre + pl->kim * pl->kim);
