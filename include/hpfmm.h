@@ -24,13 +24,15 @@
  * Conventions for every entry point
  *   - Pointers may be host or device memory (the library asks the CUDA
  *     runtime which); host buffers are staged through plan-owned device
- *     memory with stream-ordered copies.  All work is ordered on `stream`
- *     (a cudaStream_t, NULL = legacy default stream): parts of a rebuild
- *     (reaction tables) and of a single-precision evaluation (the far-field
- *     passes, concurrent with the near field) run on a plan-owned side stream
- *     that is forked from `stream` and joined back into it with events, so
- *     the results are complete when `stream` reaches the call's end.  A
- *     plan's calls must not run concurrently with each other.
+ *     memory (allocated by the first such call), their copies on a
+ *     plan-owned copy stream ordered against `stream` by events.  All work is
+ *     ordered on `stream` (a cudaStream_t, NULL = legacy default stream):
+ *     parts of a rebuild (reaction tables) and of a single-precision
+ *     evaluation (the far-field passes, concurrent with the near field) run
+ *     on plan-owned streams that are forked from `stream` and joined back
+ *     into it with events, so the results are complete when `stream` reaches
+ *     the call's end.  A plan's calls must not run concurrently with each
+ *     other.
  *   - Outputs are in the caller's point order.  Complex values are stored as
  *     interleaved (re, im) doubles.
  *   - The caller owns every input and output buffer; a plan owns its tree,
@@ -144,13 +146,15 @@ hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n, double ka
  * n points (same n as at creation, same kappa, p and options), reusing the
  * plan's device memory: validation, bounding square, Morton keys and sort,
  * leaf offsets and translation tables, as in hpfmm_create, without device
- * allocations (host coordinates are staged through the stream-ordered pool).
- * Returns EINVAL (synchronously) for invalid points; the plan then holds no
- * valid tree until a successful update.  The call waits only until the
- * bounding square is known on the device (its validity and size reach the
- * host through a pinned buffer); the rest of the rebuild stays queued on
- * `stream`, and the reaction tables are built on a plan-owned side stream
- * that `stream` waits for.
+ * allocations after the first call (host coordinates are staged through a
+ * plan-owned buffer, allocated by the first host-buffer call).  Without
+ * async_update, returns EINVAL (synchronously) for invalid points, the plan
+ * then holding no valid tree until a successful update, and the call waits
+ * only until the bounding square is known on the device (its validity and
+ * size reach the host through a pinned buffer); with async_update it does
+ * not wait at all (see hpfmm_options).  The rest of the rebuild stays queued
+ * on `stream`; the reaction tables are built on a plan-owned stream after
+ * the tree build, which the evaluation joins before it reads them.
  */
 hpfmm_status hpfmm_update_points(hpfmm_plan *plan, const double *x, const double *y,
                                  void *stream);
