@@ -55,6 +55,21 @@ def test_fmm_fp64_error_decays_in_p():
     assert slope < -0.3
 
 
+@pytest.mark.parametrize("p", [13, 21, 24, 29, 32, 40])
+def test_fmm_fp32_hankel_orders(p):
+    """Single precision at the orders whose patch M2L walks its anti-diagonals
+    in one register chunk (13) or in 2, 3 and 5 chunks (21 .. 40), on a tree
+    deep enough (level 4) for every V-list class to occur: at the FP32
+    floor, and within it of the FP64 plan at the same order."""
+    x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
+    u, g, _ = run(x, y, q, 1.0, p, 8, prec="fp32", levels=4)
+    u64, g64, _ = run(x, y, q, 1.0, p, 8, prec="fp64", levels=4)
+    assert rel(u, u_ref) < 3e-6
+    assert rel(g, g_ref) < 3e-5
+    assert rel(u, u64) < 3e-6
+    assert rel(u64, u_ref) < (P_BOUNDS[24] if p >= 24 else 1e-7) * 10
+
+
 @pytest.mark.parametrize("kappa", [10.0, 0.1, 1 + 0.5j])
 def test_fmm_fp64_kappas(kappa):
     x, y, q = workloads.uniform(1500, seed=8)
