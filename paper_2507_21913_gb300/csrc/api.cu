@@ -193,6 +193,7 @@ static void free_plan(hpfmm_plan *pl) {
   if (pl->ev_tables) cudaEventDestroy(pl->ev_tables);
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+  if (pl->ev_gather) cudaEventDestroy(pl->ev_gather);
   if (pl->hgeo) cudaFreeHost(pl->hgeo);
   if (pl->tstate) {
     TimingState *ts = (TimingState *)pl->tstate;
@@ -270,7 +271,7 @@ static hpfmm_status rebuild(hpfmm_plan *pl, const double *x, const double *y, cu
   if (s == HPFMM_OK) {
     // the geometry to the host and the reaction tables (they depend on the
     // root square only) on the table stream, concurrent with what follows
-    // (ev_tree: recorded by tree_build once the root square is known)
+    // (ev_tree: recorded by tree_build after its last kernel)
     e = cudaStreamWaitEvent(pl->table_stream, pl->ev_tree, 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(pl->hgeo, pl->geo, 5 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -500,13 +501,15 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     // M2L) -- take the greatest priority: their short dependent kernels then
     // take SMs before the blocks of the near field on the caller's stream,
     // which fills the rest.  The table stream (reaction tables of a rebuild,
-    // overlapping the tree build) keeps the default priority, so that the
-    // tree's kernels keep their SMs.
+    // started once the tree is built) takes it too: the mirror M2L waits for
+    // the tables, and at the default priority their blocks queued behind the
+    // near field's until it was almost done.
     int prio_lo = 0, prio_hi = 0;
     cudaError_t ce = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->side_stream, cudaStreamNonBlocking, prio_hi);
-    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->table_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess)
+      ce = cudaStreamCreateWithPriority(&pl->table_stream, cudaStreamNonBlocking, prio_hi);
     if (ce == cudaSuccess)
       ce = cudaStreamCreateWithPriority(&pl->m2l_stream, cudaStreamNonBlocking, prio_hi);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking);
@@ -520,6 +523,7 @@ extern "C" hpfmm_status hpfmm_create(const double *x, const double *y, int64_t n
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_tables, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&pl->ev_gather, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaMallocHost((void **)&pl->hgeo, 8 * sizeof(double));
     if (ce != cudaSuccess) {
       set_last_error("hpfmm_create: %s", cudaGetErrorString(ce));

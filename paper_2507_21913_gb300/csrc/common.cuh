@@ -396,8 +396,10 @@ struct hpfmm_plan {
               ev_done = nullptr;
   double *in_xy = nullptr;  // staged coordinates of a host-buffer rebuild (x, then y)
   bool tables_pending = false;
-  // fork / join of the near field on the side stream (single precision)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // fork / join of the far-field chain on the side stream (single
+  // precision); ev_gather: the charges in tree order are written (the
+  // bottom-row pairs wait for it)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_gather = nullptr;
   // the leaf level's M2L on its own stream, after the S2M (ev_s2m), joined
   // into the far-field chain (ev_m2lh)
   cudaStream_t m2l_stream = nullptr;

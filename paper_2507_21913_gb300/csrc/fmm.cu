@@ -1343,9 +1343,14 @@ __device__ __forceinline__ void add_hilo(float h, float l, float oh, float ol, f
 
 __global__ void __launch_bounds__(kEvWarps * 32, 4)
 k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
-         const float *__restrict__ qs, const int *__restrict__ leaf_start, int H,
-         const DevGeom *__restrict__ dg, float4 *__restrict__ near) {
-  pdl_wait();  // launched as a dependent of the charge gather
+         const double *__restrict__ q, const int64_t *__restrict__ perm,
+         const int *__restrict__ leaf_start, int H, const DevGeom *__restrict__ dg,
+         float4 *__restrict__ near) {
+  // launched as a dependent of the tree build's last kernel; the charges are
+  // read in the caller's order through perm and rounded as the charge gather
+  // rounds them (bit-identical to the gathered copy), so that the gather runs
+  // beside this kernel instead of before it
+  pdl_wait();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int *ls = reinterpret_cast<int *>(smem_raw);         // [kTl^2 + 1] tile leaf starts
   float4 *src = reinterpret_cast<float4 *>(smem_raw + kLsBytes);  // [kTlCap] (hi, lo)
@@ -1407,7 +1412,7 @@ k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
         add_hilo(v.x, w.x, ohx, olx, hx, lx);
         add_hilo(v.y, w.y, ohy, oly, hy, ly);
         src[o + j] = make_float4(hx, hy, lx, ly);
-        srcq[o + j] = qs[b0 + j];
+        srcq[o + j] = fs_round(q[perm[b0 + j]]);
       }
     }
   }
@@ -1459,9 +1464,9 @@ k_near32(const float2 *__restrict__ loc, const float2 *__restrict__ loclo,
             const float dx = (sxh - v.x) + (sxl - w.x), dy = (syh - v.y) + (syl - w.y);
             const float r2 = fmaf(dx, dx, dy * dy);
             if (!(r2 > 0.f)) continue;  // j = i, or a coincident point
-            const float q = qs[k];
-            const float qi = q * fast_rcp(r2);
-            lf = fmaf(q, fast_lg2(r2), lf);
+            const float qk = fs_round(q[perm[k]]);
+            const float qi = qk * fast_rcp(r2);
+            lf = fmaf(qk, fast_lg2(r2), lf);
             gx = fmaf(qi, dx, gx);
             gy = fmaf(qi, dy, gy);
           }
@@ -2059,16 +2064,13 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
   }
   const DevGeom *dg = pl->dgeom;
 
-  pass_begin(pl, st, PASS_GATHER);
-  HP_CUDA(launch_dependent(k_gather_q<R>, dim3(cdiv_u(n, 256), nr), dim3(256), 0, st, q, pl->perm,
-                           n, qs, mw ? (R *)mw->qsm : (R *)nullptr, mw ? mw->rp : 0));
-  pass_end(pl, st, PASS_GATHER, 1);
   // single precision, one RHS, the sources as targets: the free-space near
-  // field needs only the sorted points and charges, so it runs on the plan's
-  // side stream while this stream runs the far-field passes; L2P joins them
+  // field needs only the sorted points and charges, so it runs on this
+  // stream while the plan's side stream runs the far-field passes; L2P joins
+  // them
   const int nxl = 1 << H, tps = nxl >= kTl ? nxl / kTl : 1;
   const bool split = sizeof(R) == 4 && !mw && !tw;
-  if (split && !(pl->near && pl->side_stream && pl->ev_fork && pl->ev_join)) {
+  if (split && !(pl->near && pl->side_stream && pl->ev_fork && pl->ev_join && pl->ev_gather)) {
     set_last_error("single-precision plan without its near-field buffer or side stream");
     return HPFMM_ECUDA;
   }
@@ -2086,16 +2088,28 @@ hpfmm_status run_passes(hpfmm_plan *pl, const double *q, double *pot, double *gr
     HP_CUDA(cudaEventRecord(pl->ev_fork, st));
     HP_CUDA(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0));
     fs = pl->side_stream;
+  }
+  // the charges in tree order: first on the far-field chain when split (the
+  // near field reads them through perm itself)
+  pass_begin(pl, fs, PASS_GATHER);
+  if (split)
+    k_gather_q<R><<<dim3(cdiv_u(n, 256), nr), 256, 0, fs>>>(q, pl->perm, n, qs, (R *)nullptr, 0);
+  else
+    HP_CUDA(launch_dependent(k_gather_q<R>, dim3(cdiv_u(n, 256), nr), dim3(256), 0, st, q,
+                             pl->perm, n, qs, mw ? (R *)mw->qsm : (R *)nullptr, mw ? mw->rp : 0));
+  pass_end(pl, fs, PASS_GATHER, 1);
+  if (split) {
+    HP_CUDA(cudaEventRecord(pl->ev_gather, fs));
     pass_begin(pl, st, PASS_EVAL);
     HP_CUDA(launch_dependent(k_near32, dim3((unsigned)(tps * tps)), dim3(32 * kEvWarps), kTpSmem,
-                             st, pl->loc32, pl->loclo, (const float *)qs, pl->leaf_start, H, dg,
-                             pl->near));
+                             st, pl->loc32, pl->loclo, q, pl->perm,
+                             pl->leaf_start, H, dg, pl->near));
     pass_end(pl, st, PASS_EVAL, 1);
     // the bottom-row image/reaction sums need only the sources too: written
     // now, added by the L2P kernel.  On the m2l stream (idle until the S2M is
-    // done), off the near field's stream.
+    // done), off the near field's stream, after the gather.
     cudaStream_t ms = mirror_apart ? pl->m2l_stream : st;
-    if (ms != st) HP_CUDA(cudaStreamWaitEvent(ms, pl->ev_fork, 0));
+    HP_CUDA(cudaStreamWaitEvent(ms, pl->ev_gather, 0));
     pass_begin(pl, ms, PASS_NEAR_MIRROR);
     k_mirror32<<<dim3((unsigned)(1 << H), 1, kMirSplit), 32 * kEvWarps, 0, ms>>>(
         pl->loc32, pl->yabs, (const float *)qs, pl->perm, pl->leaf_start, H, dg,
