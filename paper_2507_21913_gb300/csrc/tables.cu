@@ -125,7 +125,9 @@ __global__ void k_img_m2l(int p, cd *T, cd *logt) {
 // matrix of offset -dx; so a block owns one (level, ysum, m) with
 // shat = ysum + i m, evaluates It_k = J_k(P) / (2 pi k! shat^k) (thread k,
 // series or continued fraction for that k, no recursion between threads) and
-// fills Tr[l][(ysum, dx = m)][+] and Tr[l][(ysum, dx = -m)][-].
+// fills Tr[l][(ysum, dx = m)][+] and Tr[l][(ysum, dx = -m)][-].  With a
+// single-precision copy Tf (single-precision and mixed plans, whose kernels
+// read only that copy), the J_k are evaluated to single-precision needs.
 __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd kappa,
                                const double *__restrict__ Cb, cd *Tr, cf *Tf) {
   extern __shared__ cd sh[];
@@ -140,7 +142,7 @@ __global__ void k_reaction_m2l(int p, int H, const double *__restrict__ geo, cd 
   const cd P = (d * kappa) * shat;
   const cd sinv = cinv(shat);
   for (int k = threadIdx.x; k <= K; k += blockDim.x) {
-    const cd J = jn_direct(P, k);
+    const cd J = Tf ? jn_direct_single(P, k) : jn_direct(P, k);
     cd f = mk(1.0 / HP_TWO_PI, 0.0);
     for (int j = 1; j <= k; ++j) f = c_recip[j] * (f * sinv);
     h[k] = J * f;

@@ -79,6 +79,24 @@ def test_fmm_fp64_kappas(kappa):
     assert rel(g, g_ref) < 1e-6
 
 
+@pytest.mark.parametrize("kappa", [10.0, 25.0, 10.0 + 5.0j])
+def test_fmm_fp32_kappas(kappa):
+    """Single precision at large |kappa d|: single-precision plans evaluate
+    their reaction tables' J_k by the power series wherever it keeps about
+    ten digits (|P| - Re P <= 10, |P| <= 30), by the continued fraction
+    elsewhere, while the FP64 plan keeps the series to |P| - Re P <= 1.5.
+    Levels 1..4 put |P| = |kappa d (Ysum + i m)| between 0.6 and 53 (the
+    library accepts |kappa| sqrt(5) side <= 60)."""
+    x, y, q = workloads.uniform(1500, seed=8)
+    u_ref, g_ref = oracle.direct(x, y, q, kappa=kappa)
+    u, g, _ = run(x, y, q, kappa, 24, 8, prec="fp32", levels=4)
+    u64, g64, _ = run(x, y, q, kappa, 24, 8, prec="fp64", levels=4)
+    assert rel(u, u64) < 3e-6
+    assert rel(g, g64) < 3e-5
+    assert rel(u, u_ref) < 3e-6
+    assert rel(g, g_ref) < 3e-5
+
+
 @pytest.mark.parametrize("levels", [1, 2, 4, 5])
 def test_fmm_fp64_tree_depths(levels):
     x, y, q, u_ref, g_ref = oracle_cache.uniform_direct(2000, 0, 1.0)
