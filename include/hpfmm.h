@@ -328,11 +328,12 @@ hpfmm_status hpfmm_get_order(const hpfmm_plan *plan, uint64_t *keys, int64_t *pe
 
 /*
  * Pass timing.  hpfmm_set_timing(plan, 1) makes the plan record a CUDA event
- * pair on the caller's stream around every pass it launches (tree build,
- * tables, charge gather, P2M, M2M, free M2L, mirror M2L, L2L, leaf
- * evaluation = L2P + free-space near field (+ the image and reaction near
- * field in double precision), image and reaction near field of the
- * bottom-row leaves (single precision), in this order of pass ids 0..9).
+ * pair around every pass it launches, on the stream that runs the pass (the
+ * caller's stream or one of the plan's streams).  The passes, in the order
+ * of their ids 0..9: tree build, tables, charge gather, P2M, M2M, free M2L,
+ * mirror M2L, L2L, leaf evaluation = L2P + free-space near field (+ the image
+ * and reaction near field in double precision), image and reaction near
+ * field of the bottom-row leaves (single precision).
  * hpfmm_read_timing synchronises with that work and returns, per pass, the
  * device milliseconds recorded since the previous read (ms may be NULL) and the
  * number of kernels the plan has launched in that pass since creation
