@@ -47,12 +47,6 @@ constexpr int kWarpsPerBlock = 4;
 // record, written on the device by the tree build (no kernel repeats
 // double-precision set-up arithmetic per thread: GB300's FP64 pipe is narrow).
 
-
-template <typename R>
-__device__ __forceinline__ cpx<R> ldc(const cpx<R> *p) {
-  return *p;
-}
-
 // --------------------------------------------------------------------------
 // gather the charges into tree order
 // (blockIdx.y = RHS; qsm, when given, also receives the charges point-major:
@@ -292,12 +286,6 @@ k_s2m_multi(const float2 *__restrict__ loc, const float *__restrict__ qsm, int r
 // down to 1, so the upward pass needs no further launch; deeper trees run
 // them as separate launches.
 constexpr int kCoarseBig = 5;  // coarse levels with at least 4^5 boxes get a multi-block launch
-
-template <typename R>
-__device__ __forceinline__ R wsum(R v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // a complex number read past L1 (written by another block of the same launch)
 __device__ __forceinline__ cf ldcg_c(const cf *p) {

@@ -146,28 +146,6 @@ __device__ inline cd jn_direct_single(cd P, int n) {
   return series ? jn_series(P, n) : jn_cf(P, n);
 }
 
-// J_0 .. J_K into J[0..K]
-__device__ inline void jn_range(cd P, int K, cd *J) {
-  double a = sqrt(abs2(P));
-  int ns = (int)floor(a);
-  if (ns > K) ns = K;
-  J[ns] = jn_direct(P, ns);
-  double fact = 1.0;  // (m-1)!
-  for (int k = 2; k < ns; ++k) fact *= k;
-  cd Pinv = cinv(P);
-  for (int m = ns; m >= 1; --m) {  // J_{m-1} = (J_m - (m-1)!) / P
-    J[m - 1] = Pinv * mk(J[m].x - fact, J[m].y);
-    if (m - 1 >= 1) fact /= (m - 1);
-  }
-  fact = 1.0;  // m!
-  for (int k = 2; k <= ns; ++k) fact *= k;
-  for (int m = ns; m < K; ++m) {  // J_{m+1} = m! + P J_m
-    cd v = P * J[m];
-    J[m + 1] = mk(v.x + fact, v.y);
-    fact *= (m + 1);
-  }
-}
-
 // J_0 and J_1 = 1 + P J_0 for |P| <= 1/8, double precision: the series form
 // of J_0 above, J_0 = e^{-P}[i pi - gamma - Log P - sum_{k>=1} P^k/(k k!)],
 // with e^{-P} and the sum as fixed-length polynomials in P (Horner).  At
