@@ -606,32 +606,34 @@ k_downward(int H, int k, int p, const cpx<R> *__restrict__ Tl2l, cpx<R> *__restr
       np = nc;
       continue;
     }
-    for (int e = threadIdx.x; e < nc * P1; e += blockDim.x) {
-      const int b = e / P1, m = e % P1, c = b & 3;
-      const cpx<R> *pa = cur + (size_t)(b >> 2) * BS;
-      const cpx<R> *pb = pa + P1;
-      const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
-      const size_t ce = (size_t)(level_offset(l) + first + b) * P1 + m;
-      cpx<R> sa = A[ce], sb = B[ce];
-      if (Amir) {
-        const uint64_t bx = (uint64_t)(first + b);
-        const int iyb = box_iy(bx);
-        if (iyb <= 1) {
-          const int64_t ms = mirror_slot(l, box_ix(bx), iyb) * P1 + m;
-          sa = sa + Amir[ms];
-          sb = sb + Bmir[ms];
+    if constexpr (!EVAL) {  // the leaf level without the L2P: into A, B
+      for (int e = threadIdx.x; e < nc * P1; e += blockDim.x) {
+        const int b = e / P1, m = e % P1, c = b & 3;
+        const cpx<R> *pa = cur + (size_t)(b >> 2) * BS;
+        const cpx<R> *pb = pa + P1;
+        const cpx<R> *Tc = T + (size_t)c * P1 * P1 + (size_t)m * P1;
+        const size_t ce = (size_t)(level_offset(l) + first + b) * P1 + m;
+        cpx<R> sa = A[ce], sb = B[ce];
+        if (Amir) {
+          const uint64_t bx = (uint64_t)(first + b);
+          const int iyb = box_iy(bx);
+          if (iyb <= 1) {
+            const int64_t ms = mirror_slot(l, box_ix(bx), iyb) * P1 + m;
+            sa = sa + Amir[ms];
+            sb = sb + Bmir[ms];
+          }
         }
+        for (int n = m; n < P1; ++n) {
+          cfma(sa, Tc[n], pa[n]);
+          cfma(sb, conj(Tc[n]), pb[n]);
+        }
+        A[ce] = sa;
+        B[ce] = sb;
       }
-      for (int n = m; n < P1; ++n) {
-        cfma(sa, Tc[n], pa[n]);
-        cfma(sb, conj(Tc[n]), pb[n]);
-      }
-      A[ce] = sa;  // the leaf level without EVAL
-      B[ce] = sb;
+      __syncthreads();
+      cpx<R> *t = cur; cur = nxt; nxt = t;
+      np = nc;
     }
-    __syncthreads();
-    cpx<R> *t = cur; cur = nxt; nxt = t;
-    np = nc;
   }
   if constexpr (EVAL) {
     // L2P at the subtree's points (contiguous in tree order), plus the near
