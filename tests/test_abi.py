@@ -130,3 +130,14 @@ def test_adaptive_option_checks_without_gpu(library):
     opt = hp.Options()
     library.hpfmm_default_options(__import__("ctypes").byref(opt))
     assert opt.adaptive == 0 and opt.async_update == 0 and list(opt.reserved) == [0]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library every entry point raises."""
+    import numpy as np
+    monkeypatch.setattr(hp, "_LIB", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "absent" / "libhpfmm.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        hp.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        hp.hpfmm_create(np.zeros(4), np.ones(4), kappa=1.0, p=8)
